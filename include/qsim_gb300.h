@@ -1,0 +1,235 @@
+/*
+ * qsim_gb300.h — C ABI of the GB300 (sm_103a) dense state-vector simulator.
+ *
+ * The library applies a gate sequence to a dense 2^n complex state vector
+ * held in GPU memory (Section 2.1, Eq. 1), either one gate at a time
+ * (Algorithms 1-4, Eq. 3-4) or after dependency-aware gate contraction into
+ * dense k-qubit blocks (Section 3.4, Eq. 6-7) grouped into shared-memory tile
+ * passes. It also evaluates Pauli-sum expectation values and their adjoint
+ * gradients, which the paper does not cover (textbook definitions, stated at
+ * each entry point).
+ *
+ * Conventions used by every entry point:
+ *   - Qubit q is bit q of the amplitude index (Eq. 2: U on qubit k is
+ *     I^{(x) n-k-1} (x) U (x) I^{(x) k}); qubit 0 is the least significant bit.
+ *   - Amplitudes are interleaved complex numbers: QS_C64 = (float re, float im)
+ *     = 8 bytes, QS_C128 = (double re, double im) = 16 bytes, index-major.
+ *   - All arrays passed in (gates, parameters, Pauli terms, host buffers) are
+ *     owned by the caller and only read during the call; nothing keeps a
+ *     pointer to them after return.
+ *   - Outputs are written only when the call returns QS_OK.
+ *   - Device work is ordered on the state's stream. Calls that return host
+ *     values (norm, expectation, gradient, copies to host) synchronise that
+ *     stream before returning.
+ *   - Errors: a negative qs_status; qs_last_error() returns a message for the
+ *     calling thread. Invalid arguments (qubit >= n, repeated qubit in a gate,
+ *     unknown kind, size mismatch) give QS_ERR_ARG before any device work.
+ *   - The library fails (QS_ERR_CUDA) when no CUDA device is present: there is
+ *     no CPU fallback.
+ */
+#ifndef QSIM_GB300_H
+#define QSIM_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef int qs_status;
+#define QS_OK 0
+#define QS_ERR_ARG (-1)
+#define QS_ERR_OOM (-2)
+#define QS_ERR_CUDA (-3)
+#define QS_ERR_TIMEOUT (-4)
+#define QS_ERR_UNSUPPORTED (-5)
+
+typedef enum { QS_C64 = 0, QS_C128 = 1 } qs_dtype;
+
+/* Gate kinds. Single-target: H, X, Y, Z, S, SDG, T, TDG, RX, RY, RZ, P, U1.
+ * Two-target: SWAP, U2. Any kind may carry up to two controls (the gate acts
+ * on the subspace where every control bit is 1, Section 2.1's CU form). */
+typedef enum {
+  QS_GATE_H = 1, QS_GATE_X, QS_GATE_Y, QS_GATE_Z, QS_GATE_S, QS_GATE_SDG,
+  QS_GATE_T, QS_GATE_TDG, QS_GATE_RX, QS_GATE_RY, QS_GATE_RZ, QS_GATE_P,
+  QS_GATE_U1, QS_GATE_SWAP, QS_GATE_U2
+} qs_gate_kind;
+
+/* One gate. Rotations are R_P(a) = exp(-i a P / 2); P(a) = diag(1, e^{ia}).
+ * angle = param + scale * theta[param_index] when param_index >= 0, else param.
+ * mat: U1 = 2x2, U2 = 4x4 complex row-major (re, im); for U2 local index bit 0
+ * belongs to q[0] and bit 1 to q[1] (the ordering of Eq. 6). */
+typedef struct {
+  int32_t kind;
+  int32_t nq;            /* number of targets: 1 or 2 */
+  int32_t q[2];          /* target qubits */
+  int32_t nctrl;         /* 0..2 */
+  int32_t ctrl[2];       /* control qubits */
+  int32_t param_index;   /* -1 = fixed angle */
+  double param;
+  double scale;
+  double mat[32];
+} qs_gate;
+
+/* Pauli string with coefficient: X on bits of xmask only, Z on zmask only,
+ * Y where both are set; qubits >= n must be clear. */
+typedef struct {
+  double coeff;
+  uint64_t xmask;
+  uint64_t zmask;
+} qs_pauli_term;
+
+/* Execution modes for plans. */
+typedef enum {
+  QS_MODE_PER_GATE = 0,  /* one kernel launch per gate (Algorithms 1-4) */
+  QS_MODE_FUSED = 1,     /* DAG contraction into k-qubit blocks + tile passes */
+  QS_MODE_TENSOR = 2     /* as FUSED, wide blocks on tensor cores (QS_C64 only) */
+} qs_mode;
+
+/* Planner and kernel options. Zero-initialised fields take the defaults. */
+typedef struct {
+  int32_t mode;          /* qs_mode */
+  int32_t fuse_k;        /* max qubits per fused block (1..5 on CUDA cores, 6 tensor); 0 = auto */
+  int32_t tile_qubits;   /* m: qubits staged per shared-memory tile (6..14); 0 = auto */
+  int32_t low_qubits;    /* L: qubits 0..L-1 always in the tile (coalescing); 0 = auto */
+  int32_t paper_mode;    /* 1 = contract only the merges of Section 3.4 (1q(x)1q, same-qubit, same-(c,t) CU) */
+  int32_t tc_precision;  /* tensor mode: 1 = bf16, 3 = bf16x3 split (default), 6 = bf16x6 split */
+  int32_t threads;       /* CUDA threads per tile CTA; 0 = auto */
+  int32_t reserved[9];
+} qs_plan_opts;
+
+/* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */
+typedef struct {
+  int64_t gates;         /* gates in the input circuit */
+  int64_t blocks;        /* fused blocks (or gates, per-gate mode) */
+  int64_t passes;        /* HBM sweeps-worth of kernel launches per execution */
+  int64_t launches;      /* kernel launches per execution */
+  double sweeps;         /* algorithmic state sweeps (read + write of 2^n amplitudes) */
+  double per_gate_sweeps;/* sweeps the same circuit costs one gate at a time */
+  double flops_per_amp;  /* real floating-point operations per amplitude per execution */
+  int32_t max_block_qubits;
+  int32_t tile_qubits;
+  int32_t low_qubits;
+  int32_t reserved[5];
+} qs_plan_info;
+
+typedef struct qs_state_s* qs_state_t;
+typedef struct qs_plan_s* qs_plan_t;
+
+/* ---------------- state ---------------- */
+
+/* Allocates an n-qubit state (1 <= n <= 40) on the current CUDA device and
+ * sets it to |0...0> (Section 3.1: the simulator builds the initial state).
+ * stream: a cudaStream_t (NULL = the legacy default stream) on which all work
+ * on this state is ordered. QS_ERR_OOM when the device cannot hold 2^n amps. */
+qs_status qs_state_alloc(int n, qs_dtype dtype, void* stream, qs_state_t* out);
+
+/* Wraps caller-owned device memory of 2^n amplitudes (not initialised, not
+ * freed by qs_state_free). dev_ptr must be 16-byte aligned. */
+qs_status qs_state_wrap(void* dev_ptr, int n, qs_dtype dtype, void* stream, qs_state_t* out);
+
+qs_status qs_state_free(qs_state_t s);
+qs_status qs_state_info(qs_state_t s, int* n, qs_dtype* dtype, void** dev_ptr);
+qs_status qs_state_set_stream(qs_state_t s, void* stream);
+
+/* Sets the computational basis state |x> (x < 2^n). */
+qs_status qs_state_set_basis(qs_state_t s, uint64_t x);
+
+/* Copies 2^n amplitudes (bytes = 2^n * amp size) between host and device;
+ * host memory may be pageable or pinned. */
+qs_status qs_state_copy_from_host(qs_state_t s, const void* host, size_t bytes);
+qs_status qs_state_copy_to_host(qs_state_t s, void* host, size_t bytes);
+/* dst <- src (same n and dtype), device to device. */
+qs_status qs_state_copy(qs_state_t dst, qs_state_t src);
+
+/* ---------------- circuits ---------------- */
+
+/* Plans a circuit for n qubits: resolves gate matrices (FP64), builds the gate
+ * DAG (Section 3.4: an edge from each earlier gate sharing a qubit, controls
+ * included), contracts it greedily into blocks of <= fuse_k qubits whose
+ * unitary is the ordered product (Eq. 7 for distinct qubits, M2 M1 for the
+ * same qubit), and groups blocks into tile passes. opts NULL = per-gate mode.
+ * Parametric gates are resolved at execution time from theta. */
+qs_status qs_plan_create(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates,
+                         const qs_plan_opts* opts, qs_plan_t* out);
+qs_status qs_plan_info_get(qs_plan_t p, qs_plan_info* info);
+qs_status qs_plan_free(qs_plan_t p);
+
+/* Applies a plan to a state in place: psi <- G_N ... G_1 psi. theta holds
+ * ntheta parameters (may be NULL when the circuit has none). */
+qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta);
+
+/* One-shot: plan, execute, free. */
+qs_status qs_apply_circuit(qs_state_t s, const qs_gate* gates, size_t ngates,
+                           const double* theta, size_t ntheta, const qs_plan_opts* opts);
+
+/* ---------------- observables ---------------- */
+
+/* *out = sum_i |psi_i|^2, accumulated in FP64. */
+qs_status qs_norm(qs_state_t s, double* out);
+
+/* *out = sum_j c_j <psi|P_j|psi> with P|i> = i^{#Y} (-1)^{popcount(i & z)} |i xor x>,
+ * accumulated in FP64 (terms with equal xmask share one sweep). */
+qs_status qs_expval_pauli_sum(qs_state_t s, const qs_pauli_term* terms, size_t nterms, double* out);
+
+/* out <- sum_j c_j P_j psi (out must not alias s). */
+qs_status qs_apply_pauli_sum(qs_state_t s, const qs_pauli_term* terms, size_t nterms, qs_state_t out);
+
+/* <a|b> in FP64: (*re, *im). */
+qs_status qs_inner(qs_state_t a, qs_state_t b, double* re, double* im);
+
+/* Adjoint-method gradient (Jones and Gacon, arXiv:2009.02823) of
+ * E(theta) = <psi|H|psi>, psi = C(theta) psi0, psi0 = the state s (left
+ * unchanged). grad has ntheta entries. Allocates two scratch states. */
+qs_status qs_adjoint_grad(qs_state_t s, const qs_gate* gates, size_t ngates,
+                          const double* theta, size_t ntheta,
+                          const qs_pauli_term* terms, size_t nterms,
+                          double* expval_out, double* grad_out);
+
+/* ---------------- batched execution ---------------- */
+
+/* Applies one planned circuit to B states with B parameter vectors (row b of
+ * theta, B x ntheta row-major, drives state b) and, when terms != NULL,
+ * writes <H> of each final state to expvals[b]. All states must share n,
+ * dtype and stream. The launch sequence is captured once into a CUDA graph
+ * and replayed. */
+qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B,
+                                  const double* theta, size_t ntheta,
+                                  const qs_pauli_term* terms, size_t nterms, double* expvals);
+
+/* ---------------- plan introspection (host only, no device work) ----------------
+ * A plan executes ops in order: gate ops (one input gate, applied by itself)
+ * and block ops (a contracted block: a dense 2^nq x 2^nq matrix, or 2^nq
+ * diagonal entries, over `qubits` in ascending order, local bit j = qubits[j],
+ * the Eq. 7 ordering). In per-gate mode every op is a gate op and every pass
+ * one op. */
+qs_status qs_plan_op_count(qs_plan_t p, int64_t* nops, int64_t* npasses);
+/* type: 0 = gate op, 1 = dense block, 2 = diagonal block. qubits: capacity 6.
+ * gate_index: the input gate of a gate op (-1 for blocks). mat (optional,
+ * capacity 2 * 4096 doubles): the block's entries as (re, im) pairs. */
+qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits, int32_t* nq,
+                         int32_t* gate_index, double* mat);
+/* Tile qubits of pass i (ascending, capacity 14) and its op range [op_begin, op_end). */
+qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t* m,
+                           int64_t* op_begin, int64_t* op_end);
+
+/* ---------------- measurement ----------------
+ * With timing enabled, every kernel launch issued by qs_plan_execute is
+ * bracketed by two CUDA events on the state's stream. qs_plan_timing_read
+ * waits for the recorded events, returns the summed device time of the
+ * bracketed launches (ms) and their number, and starts a new interval. */
+qs_status qs_plan_set_timing(qs_plan_t p, int enable);
+qs_status qs_plan_timing_read(qs_plan_t p, double* total_ms, int64_t* launches);
+
+/* ---------------- diagnostics ---------------- */
+
+const char* qs_last_error(void);
+/* Number of library kernel launches issued by this process so far. */
+int64_t qs_launch_count(void);
+const char* qs_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,31 @@
+// Complex helpers on float2 / double2 (x = re, y = im), shared by the kernels.
+#pragma once
+#include <cuda_runtime.h>
+
+namespace qs {
+
+template <typename R> struct V2;
+template <> struct V2<float> { using T = float2; };
+template <> struct V2<double> { using T = double2; };
+
+template <typename R> __device__ __forceinline__ typename V2<R>::T mk(R x, R y) {
+  typename V2<R>::T v; v.x = x; v.y = y; return v;
+}
+
+// a*b
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+// acc + a*b
+template <typename C> __device__ __forceinline__ C cfma(C a, C b, C acc) {
+  acc.x = fma(a.x, b.x, acc.x); acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y); acc.y = fma(a.y, b.x, acc.y);
+  return acc;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+
+template <typename R> __device__ __forceinline__ typename V2<R>::T from_d(double2 d) {
+  return mk<R>((R)d.x, (R)d.y);
+}
+
+}  // namespace qs

@@ -1,0 +1,309 @@
+// Reductions and Pauli-sum kernels (not in the paper; textbook definitions).
+//
+// Norm sum_i |psi_i|^2, inner product <a|b>, expectation of Pauli strings
+// P|i> = i^{#Y} (-1)^{popcount(i & z)} |i xor x>, H|psi>, and the fused step of
+// the adjoint gradient (Jones and Gacon, arXiv:2009.02823).
+//
+// Every reduction runs on a fixed grid (reduce_blocks() CTAs) so the partial
+// sums, and therefore the FP64 result, do not depend on timing. complex64
+// states accumulate short runs in FP32 (at most kRun terms) and carry the
+// running total in FP64; complex128 states accumulate in FP64. Partials are
+// combined in FP64 by one CTA in a fixed order.
+#include <cuda_runtime.h>
+
+#include "cplx.cuh"
+#include "qs_internal.h"
+
+namespace qs {
+
+constexpr int kRedThreads = 256;
+constexpr int kRedBlocks = 152 * 4;
+constexpr int kRun = 32;
+
+int reduce_blocks() { return kRedBlocks; }
+
+// Sum of a per-thread double across the CTA; result valid in thread 0.
+__device__ __forceinline__ double block_sum(double v) {
+  __shared__ double ws[kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) ws[w] = v;
+  __syncthreads();
+  double s = 0;
+  if (threadIdx.x == 0)
+    for (int k = 0; k < kRedThreads / 32; ++k) s += ws[k];
+  return s;
+}
+
+// Accumulator: FP32 runs folded into FP64 for float states, FP64 for double.
+template <typename R> struct Acc;
+template <> struct Acc<double> {
+  double t = 0;
+  __device__ __forceinline__ void add(double v) { t += v; }
+  __device__ __forceinline__ double total() const { return t; }
+};
+template <> struct Acc<float> {
+  double t = 0;
+  float run = 0;
+  int cnt = 0;
+  __device__ __forceinline__ void add(float v) {
+    run += v;
+    if (++cnt == kRun) { t += (double)run; run = 0; cnt = 0; }
+  }
+  __device__ __forceinline__ double total() const { return t + (double)run; }
+};
+
+// ---------------------------------------------------------------- norm / inner
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_norm(const typename V2<R>::T* __restrict__ psi, uint64_t dim,
+                                                       double* __restrict__ partials) {
+  Acc<R> acc;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+    const auto v = psi[i];
+    acc.add(v.x * v.x + v.y * v.y);
+  }
+  const double s = block_sum(acc.total());
+  if (threadIdx.x == 0) partials[blockIdx.x] = s;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_inner(const typename V2<R>::T* __restrict__ a,
+                                                        const typename V2<R>::T* __restrict__ b, uint64_t dim,
+                                                        double* __restrict__ partials) {
+  Acc<R> re, im;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+    const auto x = a[i], y = b[i];
+    re.add(x.x * y.x + x.y * y.y);   // conj(x) * y
+    im.add(x.x * y.y - x.y * y.x);
+  }
+  const double sr = block_sum(re.total());
+  const double si = block_sum(im.total());
+  if (threadIdx.x == 0) { partials[blockIdx.x] = sr; partials[kRedBlocks + blockIdx.x] = si; }
+}
+
+// out[r] = sum_c partials[r * cols + c] in a fixed order (one CTA per row).
+__global__ void __launch_bounds__(kRedThreads) k_sum_rows(const double* __restrict__ partials, int cols,
+                                                           double* __restrict__ out) {
+  const double* row = partials + (int64_t)blockIdx.x * cols;
+  double v = 0;
+  for (int c = threadIdx.x; c < cols; c += kRedThreads) v += row[c];
+  const double s = block_sum(v);
+  if (threadIdx.x == 0) out[blockIdx.x] = s;
+}
+
+cudaError_t launch_sum_rows(const double* partials, int rows, int cols, double* out, cudaStream_t st) {
+  if (rows == 0) return cudaSuccess;
+  k_sum_rows<<<rows, kRedThreads, 0, st>>>(partials, cols, out);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_norm(const void* psi, int n, qs_dtype dt, double* partials, double* out, cudaStream_t st) {
+  const uint64_t dim = 1ull << n;
+  if (dt == QS_C64) k_norm<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)psi, dim, partials);
+  else k_norm<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)psi, dim, partials);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_sum_rows(partials, 1, kRedBlocks, out, st);
+}
+
+cudaError_t launch_inner(const void* a, const void* b, int n, qs_dtype dt, double* partials, double* out2,
+                         cudaStream_t st) {
+  const uint64_t dim = 1ull << n;
+  if (dt == QS_C64)
+    k_inner<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)a, (const float2*)b, dim, partials);
+  else
+    k_inner<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)a, (const double2*)b, dim, partials);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_sum_rows(partials, 2, kRedBlocks, out2, st);
+}
+
+// ---------------------------------------------------------------- Pauli expval
+
+constexpr int kMaxZ = 8;
+
+// One sweep for all strings sharing xmask x. Pairs (i, j = i xor x) are
+// visited once (i has the highest bit of x clear). For w = conj(psi_j) psi_i:
+//   <P> contribution = i^{ny} s_i (w + (-1)^{ny} conj(w)),  s_i = (-1)^{popcount(i & z)}
+// which is s_i * 2 Re(w) * (-1)^{ny/2} for even ny and s_i * 2 Im(w) * (-1)^{(ny+1)/2}
+// for odd ny (the sign and the re/im choice are folded into coef/odd below).
+// x = 0: each index once, contribution s_i |psi_i|^2.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::T* __restrict__ psi, int n,
+                                                           uint64_t x, const uint64_t* __restrict__ zm,
+                                                           int nz, double* __restrict__ partials) {
+  __shared__ uint64_t z_s[kMaxZ];
+  __shared__ int odd_s[kMaxZ];
+  if (threadIdx.x < nz) {
+    z_s[threadIdx.x] = zm[threadIdx.x];
+    odd_s[threadIdx.x] = __popcll(x & zm[threadIdx.x]) & 1;
+  }
+  __syncthreads();
+  Acc<R> acc[kMaxZ];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  if (x == 0) {
+    const uint64_t dim = 1ull << n;
+    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+      const auto a = psi[i];
+      const R p = a.x * a.x + a.y * a.y;
+#pragma unroll
+      for (int k = 0; k < kMaxZ; ++k)
+        if (k < nz) acc[k].add((__popcll(i & z_s[k]) & 1) ? -p : p);
+    }
+  } else {
+    const int32_t hb = 63 - __clzll((long long)x);
+    const uint64_t count = 1ull << (n - 1);
+    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += stride) {
+      const uint64_t i = ((p >> hb) << (hb + 1)) | (p & ((1ull << hb) - 1));
+      const auto a = psi[i], b = psi[i ^ x];
+      const R wr = b.x * a.x + b.y * a.y;   // Re(conj(b) a)
+      const R wi = b.x * a.y - b.y * a.x;   // Im(conj(b) a)
+#pragma unroll
+      for (int k = 0; k < kMaxZ; ++k) {
+        if (k < nz) {
+          const R v = odd_s[k] ? wi : wr;
+          acc[k].add((__popcll(i & z_s[k]) & 1) ? -v : v);
+        }
+      }
+    }
+  }
+  for (int k = 0; k < nz; ++k) {
+    const double s = block_sum(acc[k].total());
+    if (threadIdx.x == 0) partials[(int64_t)k * kRedBlocks + blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_expval_x(const void* psi, int n, qs_dtype dt, uint64_t xmask, const uint64_t* zm,
+                            const double* /*coeffs*/, int nz, double* partials, double* out, cudaStream_t st) {
+  if (nz > kMaxZ) return cudaErrorInvalidValue;
+  if (dt == QS_C64)
+    k_expval_x<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)psi, n, xmask, zm, nz, partials);
+  else
+    k_expval_x<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)psi, n, xmask, zm, nz, partials);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  return launch_sum_rows(partials, nz, kRedBlocks, out, st);
+}
+
+// ---------------------------------------------------------------- H |psi>
+
+constexpr int kMaxTermsPerLaunch = 512;
+
+// out[k] = sum_j c_j i^{ny_j} (-1)^{popcount((k xor x_j) & z_j)} psi[k xor x_j]
+// (thread per output index; a warp's reads psi[k xor x] stay within one
+// aligned 32-amplitude segment, so they coalesce).
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_apply_pauli(const typename V2<R>::T* __restrict__ psi,
+                                                              typename V2<R>::T* __restrict__ out, uint64_t dim,
+                                                              const uint64_t* __restrict__ xm,
+                                                              const uint64_t* __restrict__ zm,
+                                                              const double2* __restrict__ ph, int nt,
+                                                              int accumulate) {
+  using C = typename V2<R>::T;
+  __shared__ uint64_t xs[kMaxTermsPerLaunch], zs[kMaxTermsPerLaunch];
+  __shared__ C cs[kMaxTermsPerLaunch];
+  for (int j = threadIdx.x; j < nt; j += blockDim.x) { xs[j] = xm[j]; zs[j] = zm[j]; cs[j] = from_d<R>(ph[j]); }
+  __syncthreads();
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < dim; k += stride) {
+    C acc = accumulate ? out[k] : mk<R>(0, 0);
+    for (int j = 0; j < nt; ++j) {
+      const uint64_t src = k ^ xs[j];
+      C v = psi[src];
+      if (__popcll(src & zs[j]) & 1) { v.x = -v.x; v.y = -v.y; }
+      acc = cfma(cs[j], v, acc);
+    }
+    out[k] = acc;
+  }
+}
+
+// ph[j] = c_j * i^{ny_j}, prepared on the host.
+cudaError_t launch_apply_pauli(const void* psi, void* out, int n, qs_dtype dt, const uint64_t* xm,
+                               const uint64_t* zm, const double* ph, int nt, cudaStream_t st) {
+  const uint64_t dim = 1ull << n;
+  int first = 1;
+  for (int off = 0; off < nt || first; off += kMaxTermsPerLaunch) {
+    const int cnt = nt - off < kMaxTermsPerLaunch ? nt - off : kMaxTermsPerLaunch;
+    uint64_t g = (dim + kRedThreads - 1) / kRedThreads;
+    if (g > 152ull * 16) g = 152ull * 16;
+    if (dt == QS_C64)
+      k_apply_pauli<float><<<(unsigned)g, kRedThreads, 0, st>>>((const float2*)psi, (float2*)out, dim, xm + off,
+                                                                 zm + off, (const double2*)ph + off, cnt, !first);
+    else
+      k_apply_pauli<double><<<(unsigned)g, kRedThreads, 0, st>>>((const double2*)psi, (double2*)out, dim, xm + off,
+                                                                  zm + off, (const double2*)ph + off, cnt, !first);
+    note_launch();
+    first = 0;
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    if (off + kMaxTermsPerLaunch >= nt) break;
+  }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------- adjoint step
+
+// Reverse-sweep step for one single-target gate G with controls (Jones and
+// Gacon, Alg. 1): phi <- G^dagger phi; if dmat != NULL accumulate
+// Re<lam| dG phi> over the controlled pairs (dG is zero elsewhere);
+// lam <- G^dagger lam. One read and one write of each state.
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_adjoint_step(typename V2<R>::T* __restrict__ phi,
+                                                               typename V2<R>::T* __restrict__ lam, uint64_t count,
+                                                               DevGate g, const double2* __restrict__ mat,
+                                                               const double2* __restrict__ dmat,
+                                                               double* __restrict__ partials) {
+  using C = typename V2<R>::T;
+  // adjoint of the 2x2 target matrix
+  const C a00 = cconj(from_d<R>(mat[0])), a01 = cconj(from_d<R>(mat[2]));
+  const C a10 = cconj(from_d<R>(mat[1])), a11 = cconj(from_d<R>(mat[3]));
+  const bool grad = dmat != nullptr;
+  C d00 = mk<R>(0, 0), d01 = d00, d10 = d00, d11 = d00;
+  if (grad) { d00 = from_d<R>(dmat[0]); d01 = from_d<R>(dmat[1]); d10 = from_d<R>(dmat[2]); d11 = from_d<R>(dmat[3]); }
+  const uint64_t tb = 1ull << g.t0;
+  Acc<R> acc;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += stride) {
+    const uint64_t i0 = insert_zero_bits_u<4>(p, g.ins, g.nins) | g.cmask, i1 = i0 | tb;
+    const C f0 = phi[i0], f1 = phi[i1];
+    const C p0 = cfma(a01, f1, cmul(a00, f0));
+    const C p1 = cfma(a11, f1, cmul(a10, f0));
+    phi[i0] = p0;
+    phi[i1] = p1;
+    const C l0 = lam[i0], l1 = lam[i1];
+    if (grad) {
+      const C m0 = cfma(d01, p1, cmul(d00, p0));
+      const C m1 = cfma(d11, p1, cmul(d10, p0));
+      acc.add(l0.x * m0.x + l0.y * m0.y + l1.x * m1.x + l1.y * m1.y);   // Re(conj(l) m)
+    }
+    lam[i0] = cfma(a01, l1, cmul(a00, l0));
+    lam[i1] = cfma(a11, l1, cmul(a10, l0));
+  }
+  if (grad) {
+    const double s = block_sum(acc.total());
+    if (threadIdx.x == 0) partials[blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_adjoint_step(void* phi, void* lam, int n, qs_dtype dt, const DevGate& g, const double2* mat,
+                                const double2* dmat, double* partials_row, cudaStream_t st) {
+  const uint64_t count = 1ull << (n - g.nins);
+  if (dt == QS_C64)
+    k_adjoint_step<float><<<kRedBlocks, kRedThreads, 0, st>>>((float2*)phi, (float2*)lam, count, g, mat, dmat,
+                                                               partials_row);
+  else
+    k_adjoint_step<double><<<kRedBlocks, kRedThreads, 0, st>>>((double2*)phi, (double2*)lam, count, g, mat, dmat,
+                                                                partials_row);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace qs

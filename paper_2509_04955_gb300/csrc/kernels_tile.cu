@@ -1,0 +1,251 @@
+// Tile-pass kernel: one HBM sweep applies a whole run of fused blocks.
+//
+// Section 3.4 contracts gates to cut operation counts, and Section 3.3 runs
+// several gates per kernel to raise memory throughput. On GB300 both goals are
+// met by staging a tile of 2^m amplitudes in shared memory and applying, in
+// order, every op of a pass whose qubits lie in the tile's qubit set T:
+//   T = {0 .. L-1} (contiguous runs of 2^L amplitudes: coalesced 16-byte
+//       loads) plus up to m - L arbitrary higher qubits.
+// A tile is the set of amplitudes whose bits outside T equal the tile number;
+// the high tile qubits select 2^(m-L) runs of 2^L contiguous amplitudes.
+// Tile-local index j: bits 0..L-1 = qubits 0..L-1, bits L.. = T's high qubits
+// in ascending order. Ops carry tile-local bit positions.
+//
+// Each CTA walks tiles with a grid stride; the run offsets of the high qubits
+// are computed once per CTA. Ops:
+//   OP_GATE  one original gate (forms of the per-gate kernels, Eq. 3/4/6),
+//            matrix from the gate table;
+//   OP_DENSE dense 2^k x 2^k block (Eq. 6 generalised, Eq. 7 products),
+//            matrix staged once per op in shared memory, one group of 2^k
+//            amplitudes per thread held in registers;
+//   OP_DIAG  diagonal block, 2^k phases.
+#include <cuda_runtime.h>
+
+#include "cplx.cuh"
+#include "qs_internal.h"
+
+namespace qs {
+
+constexpr int kTileThreads = 256;
+
+__device__ __forceinline__ uint32_t ins0(uint32_t x, const int32_t* pos, int npos) {
+  return insert_zero_bits_u<4, uint32_t>(x, pos, npos);
+}
+
+template <int K>
+__device__ __forceinline__ uint32_t ins0k(uint32_t x, const int32_t* pos) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const uint32_t lo = x & ((1u << pos[k]) - 1);
+    x = ((x >> pos[k]) << (pos[k] + 1)) | lo;
+  }
+  return x;
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_gate_op(typename V2<R>::T* tile, int m, const DevOp& op,
+                                              const double2* __restrict__ gtab, typename V2<R>::T* mbuf) {
+  using C = typename V2<R>::T;
+  const double2* mat = gtab + (int64_t)op.mat * 16;
+  const uint32_t count = 1u << (m - op.nins);
+  const uint32_t ta = 1u << op.t0;
+  if (op.form == FORM_DENSE2) {
+    if (threadIdx.x < 16) mbuf[threadIdx.x] = from_d<R>(mat[threadIdx.x]);
+    __syncthreads();
+    const uint32_t tb = 1u << op.t1;
+    for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+      const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+      const uint32_t idx[4] = {b, b | ta, b | tb, b | ta | tb};
+      C a[4];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) a[j] = tile[idx[j]];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) {
+        C acc = cmul(mbuf[4 * r], a[0]);
+#pragma unroll
+        for (int j = 1; j < 4; ++j) acc = cfma(mbuf[4 * r + j], a[j], acc);
+        tile[idx[r]] = acc;
+      }
+    }
+    return;
+  }
+  if (op.form == FORM_SWAP2) {
+    const uint32_t tb = 1u << op.t1;
+    for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+      const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+      const C x = tile[b | ta], y = tile[b | tb];
+      tile[b | ta] = y;
+      tile[b | tb] = x;
+    }
+    return;
+  }
+  const C m00 = from_d<R>(mat[0]), m01 = from_d<R>(mat[1]), m10 = from_d<R>(mat[2]), m11 = from_d<R>(mat[3]);
+  for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+    const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+    if (op.form == FORM_DENSE1) {
+      const C a0 = tile[b], a1 = tile[b | ta];
+      tile[b] = cfma(m01, a1, cmul(m00, a0));
+      tile[b | ta] = cfma(m11, a1, cmul(m10, a0));
+    } else if (op.form == FORM_ANTI1) {
+      const C a0 = tile[b], a1 = tile[b | ta];
+      tile[b] = cmul(m01, a1);
+      tile[b | ta] = cmul(m10, a0);
+    } else if (op.form == FORM_PHASE1) {
+      tile[b | ta] = cmul(m11, tile[b | ta]);
+    } else {  // DIAG1
+      tile[b] = cmul((b & ta) ? m11 : m00, tile[b]);
+    }
+  }
+}
+
+template <typename R, int K>
+__device__ __forceinline__ void apply_dense_op(typename V2<R>::T* tile, int m, const DevOp& op,
+                                               const double2* __restrict__ btab, typename V2<R>::T* mbuf) {
+  using C = typename V2<R>::T;
+  constexpr int D = 1 << K;
+  for (int i = threadIdx.x; i < D * D; i += kTileThreads) mbuf[i] = from_d<R>(btab[op.mat + i]);
+  __syncthreads();
+  uint32_t off[D];
+#pragma unroll
+  for (int j = 0; j < D; ++j) {
+    uint32_t o = 0;
+#pragma unroll
+    for (int b = 0; b < K; ++b) o |= ((j >> b) & 1u) << op.ins[b];
+    off[j] = o;
+  }
+  const uint32_t groups = 1u << (m - K);
+  for (uint32_t g = threadIdx.x; g < groups; g += kTileThreads) {
+    const uint32_t i0 = ins0k<K>(g, op.ins);
+    C v[D];
+#pragma unroll
+    for (int j = 0; j < D; ++j) v[j] = tile[i0 | off[j]];
+#pragma unroll
+    for (int r = 0; r < D; ++r) {
+      C acc = cmul(mbuf[r * D], v[0]);
+#pragma unroll
+      for (int j = 1; j < D; ++j) acc = cfma(mbuf[r * D + j], v[j], acc);
+      tile[i0 | off[r]] = acc;
+    }
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ void apply_diag_op(typename V2<R>::T* tile, int m, const DevOp& op,
+                                              const double2* __restrict__ btab, typename V2<R>::T* mbuf) {
+  const int D = 1 << op.k;
+  for (int i = threadIdx.x; i < D; i += kTileThreads) mbuf[i] = from_d<R>(btab[op.mat + i]);
+  __syncthreads();
+  const uint32_t size = 1u << m;
+  for (uint32_t e = threadIdx.x; e < size; e += kTileThreads) {
+    uint32_t loc = 0;
+#pragma unroll
+    for (int b = 0; b < 6; ++b)
+      if (b < op.k) loc |= ((e >> op.ins[b]) & 1u) << b;
+    tile[e] = cmul(mbuf[loc], tile[e]);
+  }
+}
+
+template <typename R, int KMAX>
+__global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __restrict__ psi, PassDesc p,
+                                                        const DevOp* __restrict__ ops,
+                                                        const double2* __restrict__ gtab,
+                                                        const double2* __restrict__ btab, uint64_t ntiles) {
+  using C = typename V2<R>::T;
+  using C2 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;  // 16-byte vector
+  constexpr int VPT = 16 / sizeof(C);                                           // amplitudes per vector
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = p.m, L = p.L, nh = p.nhigh;
+  C* tile = (C*)smem;
+  uint64_t* segoff = (uint64_t*)(tile + (1u << m));
+  C* mbuf = (C*)(segoff + (1u << nh));
+
+  for (uint32_t s = threadIdx.x; s < (1u << nh); s += kTileThreads) {
+    uint64_t o = 0;
+    for (int k = 0; k < nh; ++k) o |= (uint64_t)((s >> k) & 1u) << p.high[k];
+    segoff[s] = o;
+  }
+  __syncthreads();
+  const uint32_t size = 1u << m, lmask = (1u << L) - 1;
+  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const uint64_t base = insert_zero_bits(t << L, p.high, nh);
+    for (uint32_t e = threadIdx.x * VPT; e < size; e += kTileThreads * VPT) {
+      const uint64_t gi = base | segoff[e >> L] | (e & lmask);
+      *(C2*)(tile + e) = *(const C2*)(psi + gi);
+    }
+    __syncthreads();
+    for (int o = p.op_begin; o < p.op_end; ++o) {
+      const DevOp op = ops[o];
+      if (op.type == OP_GATE) {
+        apply_gate_op<R>(tile, m, op, gtab, mbuf);
+      } else if (op.type == OP_DIAG) {
+        apply_diag_op<R>(tile, m, op, btab, mbuf);
+      } else {
+        if (op.k == 1) apply_dense_op<R, 1>(tile, m, op, btab, mbuf);
+        else if (op.k == 2) apply_dense_op<R, 2>(tile, m, op, btab, mbuf);
+        if constexpr (KMAX >= 3) { if (op.k == 3) apply_dense_op<R, 3>(tile, m, op, btab, mbuf); }
+        if constexpr (KMAX >= 4) { if (op.k == 4) apply_dense_op<R, 4>(tile, m, op, btab, mbuf); }
+        if constexpr (KMAX >= 5) { if (op.k == 5) apply_dense_op<R, 5>(tile, m, op, btab, mbuf); }
+      }
+      __syncthreads();
+    }
+    for (uint32_t e = threadIdx.x * VPT; e < size; e += kTileThreads * VPT) {
+      const uint64_t gi = base | segoff[e >> L] | (e & lmask);
+      *(C2*)(psi + gi) = *(const C2*)(tile + e);
+    }
+    __syncthreads();
+  }
+}
+
+size_t tile_smem_bytes(int m, int nhigh, int kmax, qs_dtype dt) {
+  const size_t amp = dt == QS_C64 ? 8 : 16;
+  const int mk = kmax < 2 ? 2 : kmax;
+  return (amp << m) + (8ull << nhigh) + amp * (1u << (2 * mk));
+}
+
+template <typename R, int KMAX>
+static cudaError_t launch_tile_t(void* psi, int n, const PassDesc& p, const DevOp* ops, const double2* gtab,
+                                 const double2* btab, cudaStream_t st, size_t smem) {
+  static int configured_bytes = 0;
+  if ((int)smem > configured_bytes) {
+    cudaError_t e = cudaFuncSetAttribute(k_tile<R, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured_bytes = (int)smem;
+  }
+  int per_sm = 0;
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<R, KMAX>, kTileThreads, smem);
+  if (e != cudaSuccess) return e;
+  if (per_sm < 1) return cudaErrorInvalidConfiguration;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const uint64_t ntiles = 1ull << (n - p.m);
+  uint64_t grid = (uint64_t)sms * per_sm;
+  if (grid > ntiles) grid = ntiles;
+  k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename V2<R>::T*)psi, p, ops, gtab, btab,
+                                                                ntiles);
+  note_launch();
+  return cudaGetLastError();
+}
+
+cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
+                             const double2* gtab, const double2* btab, int /*threads*/, cudaStream_t st) {
+  const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.kmax, dt);
+  if (dt == QS_C64) {
+    switch (p.kmax) {
+      case 0: case 1: case 2: return launch_tile_t<float, 2>(psi, n, p, ops, gtab, btab, st, smem);
+      case 3: return launch_tile_t<float, 3>(psi, n, p, ops, gtab, btab, st, smem);
+      case 4: return launch_tile_t<float, 4>(psi, n, p, ops, gtab, btab, st, smem);
+      case 5: return launch_tile_t<float, 5>(psi, n, p, ops, gtab, btab, st, smem);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (p.kmax) {
+    case 0: case 1: case 2: return launch_tile_t<double, 2>(psi, n, p, ops, gtab, btab, st, smem);
+    case 3: return launch_tile_t<double, 3>(psi, n, p, ops, gtab, btab, st, smem);
+    case 4: return launch_tile_t<double, 4>(psi, n, p, ops, gtab, btab, st, smem);
+    case 5: return launch_tile_t<double, 5>(psi, n, p, ops, gtab, btab, st, smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+}  // namespace qs

@@ -1,0 +1,365 @@
+// Circuit IR resolution, gate DAG and dependency-aware gate contraction.
+//
+// Section 3.4 builds a DAG with an edge from each earlier gate that shares a
+// qubit (controls included) and merges gates greedily; it names three merges:
+// two one-qubit gates on distinct qubits into M2 (x) M1 (Eq. 7), two gates on
+// one qubit into M2 M1, and two CU gates on the same (c, t) into C(U2 U1).
+// The greedy is not spelled out; the reading implemented here (DAGC-k):
+//   1. the next block starts at the earliest gate not yet emitted;
+//   2. later gates are scanned in program order; a gate joins the block when
+//      all of its DAG predecessors are emitted or already in the block and the
+//      block's qubit set stays within k qubits; a gate that does not join
+//      blocks its qubits for the rest of the scan;
+//   3. the block's unitary is the ordered product of its gates (FP64).
+// Paper mode keeps only the three merges above (k = 2).
+// The cost rule of Section 3.4 (a merged gate must cost fewer operations than
+// its parts) decides whether a block is applied as one dense matrix or as its
+// member gates in sequence; the cost counts FMA instructions and shared-memory
+// bytes per amplitude.
+#include "planner.h"
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <stdexcept>
+
+#include "qs_error.h"
+
+namespace qs {
+
+static bool kind_is_parametric(int k) {
+  return k == QS_GATE_RX || k == QS_GATE_RY || k == QS_GATE_RZ || k == QS_GATE_P;
+}
+
+static bool kind_is_diag(int k) {
+  switch (k) {
+    case QS_GATE_Z: case QS_GATE_S: case QS_GATE_SDG: case QS_GATE_T: case QS_GATE_TDG:
+    case QS_GATE_RZ: case QS_GATE_P:
+      return true;
+    default:
+      return false;
+  }
+}
+
+static bool kind_is_phase(int k) {  // diagonal with m00 == 1 for every angle
+  return kind_is_diag(k) && k != QS_GATE_RZ;
+}
+
+static void fixed_matrix(int kind, double a, const cd* custom, cd* m) {
+  const double r2 = 1.0 / std::sqrt(2.0);
+  const cd I(0, 1);
+  const double c = std::cos(0.5 * a), s = std::sin(0.5 * a);
+  for (int i = 0; i < 16; ++i) m[i] = 0;
+  switch (kind) {
+    case QS_GATE_H: m[0] = r2; m[1] = r2; m[2] = r2; m[3] = -r2; break;
+    case QS_GATE_X: m[1] = 1; m[2] = 1; break;
+    case QS_GATE_Y: m[1] = -I; m[2] = I; break;
+    case QS_GATE_Z: m[0] = 1; m[3] = -1; break;
+    case QS_GATE_S: m[0] = 1; m[3] = I; break;
+    case QS_GATE_SDG: m[0] = 1; m[3] = -I; break;
+    case QS_GATE_T: m[0] = 1; m[3] = std::polar(1.0, M_PI / 4); break;
+    case QS_GATE_TDG: m[0] = 1; m[3] = std::polar(1.0, -M_PI / 4); break;
+    case QS_GATE_RX: m[0] = c; m[1] = -I * s; m[2] = -I * s; m[3] = c; break;
+    case QS_GATE_RY: m[0] = c; m[1] = -s; m[2] = s; m[3] = c; break;
+    case QS_GATE_RZ: m[0] = std::polar(1.0, -0.5 * a); m[3] = std::polar(1.0, 0.5 * a); break;
+    case QS_GATE_P: m[0] = 1; m[3] = std::polar(1.0, a); break;
+    case QS_GATE_U1: for (int i = 0; i < 4; ++i) m[i] = custom[i]; break;
+    case QS_GATE_SWAP: m[0] = 1; m[6] = 1; m[9] = 1; m[15] = 1; break;
+    case QS_GATE_U2: for (int i = 0; i < 16; ++i) m[i] = custom[i]; break;
+    default: throw Error(QS_ERR_ARG, "unknown gate kind");
+  }
+}
+
+void target_matrix(const HGate& g, const double* theta, cd* m) {
+  if (!g.parametric) {
+    for (int i = 0; i < 16; ++i) m[i] = g.fixed[i];
+    return;
+  }
+  const double a = g.param + g.scale * theta[g.param_index];
+  fixed_matrix(g.kind, a, g.custom, m);
+}
+
+void resolve_gates(int n, const qs_gate* gs, size_t ng, std::vector<HGate>& out) {
+  out.clear();
+  out.reserve(ng);
+  for (size_t i = 0; i < ng; ++i) {
+    const qs_gate& q = gs[i];
+    HGate g;
+    g.kind = q.kind;
+    if (q.kind < QS_GATE_H || q.kind > QS_GATE_U2)
+      throw Error(QS_ERR_ARG, "gate " + std::to_string(i) + ": unknown kind " + std::to_string(q.kind));
+    const bool two = q.kind == QS_GATE_SWAP || q.kind == QS_GATE_U2;
+    g.nt = two ? 2 : 1;
+    if (q.nq != g.nt)
+      throw Error(QS_ERR_ARG, "gate " + std::to_string(i) + ": wrong number of targets");
+    if (q.nctrl < 0 || q.nctrl > kMaxControls)
+      throw Error(QS_ERR_ARG, "gate " + std::to_string(i) + ": at most two controls");
+    g.nc = q.nctrl;
+    uint64_t seen = 0;
+    auto take = [&](int b) {
+      if (b < 0 || b >= n) throw Error(QS_ERR_ARG, "gate " + std::to_string(i) + ": qubit out of range");
+      if (seen & (1ull << b)) throw Error(QS_ERR_ARG, "gate " + std::to_string(i) + ": repeated qubit");
+      seen |= 1ull << b;
+    };
+    for (int k = 0; k < g.nt; ++k) { take(q.q[k]); g.t[k] = q.q[k]; }
+    for (int k = 0; k < g.nc; ++k) { take(q.ctrl[k]); g.c[k] = q.ctrl[k]; g.cmask |= 1ull << q.ctrl[k]; }
+    g.qmask = seen;
+    g.param = q.param;
+    g.scale = q.scale;
+    g.parametric = kind_is_parametric(q.kind) && q.param_index >= 0;
+    g.param_index = g.parametric ? q.param_index : -1;
+    for (int k = 0; k < 16; ++k) g.custom[k] = cd(q.mat[2 * k], q.mat[2 * k + 1]);
+    if (!g.parametric) fixed_matrix(g.kind, q.param, g.custom, g.fixed);
+    if (g.nt == 2) g.form = q.kind == QS_GATE_SWAP ? FORM_SWAP2 : FORM_DENSE2;
+    else if (kind_is_phase(q.kind)) g.form = FORM_PHASE1;
+    else if (kind_is_diag(q.kind)) g.form = FORM_DIAG1;
+    else if (q.kind == QS_GATE_X || q.kind == QS_GATE_Y) g.form = FORM_ANTI1;
+    else g.form = FORM_DENSE1;
+    out.push_back(g);
+  }
+}
+
+DevGate make_dev_gate(const HGate& g, bool pairs) {
+  DevGate d;
+  std::memset(&d, 0, sizeof(d));
+  d.form = g.form;
+  if (pairs && (g.form == FORM_PHASE1 || g.form == FORM_DIAG1)) d.form = FORM_DENSE1;
+  d.t0 = g.t[0];
+  d.t1 = g.nt == 2 ? g.t[1] : -1;
+  std::vector<int> ins;
+  if (d.form != FORM_DIAG1)
+    for (int k = 0; k < g.nt; ++k) ins.push_back(g.t[k]);
+  for (int k = 0; k < g.nc; ++k) ins.push_back(g.c[k]);
+  std::sort(ins.begin(), ins.end());
+  d.nins = (int)ins.size();
+  for (int k = 0; k < d.nins; ++k) d.ins[k] = ins[k];
+  d.cmask = g.cmask;
+  d.kind = g.kind;
+  d.param_index = g.param_index;
+  d.param = g.param;
+  d.scale = g.scale;
+  return d;
+}
+
+double gate_sweep_fraction(const HGate& g) {
+  const double ctl = std::ldexp(1.0, -g.nc);
+  switch (g.form) {
+    case FORM_PHASE1: return 0.5 * ctl;
+    case FORM_SWAP2: return 0.5 * ctl;
+    default: return ctl;
+  }
+}
+
+double gate_fma_per_amp(const HGate& g) {
+  const double ctl = std::ldexp(1.0, -g.nc);
+  switch (g.form) {
+    case FORM_DENSE1: return 8 * ctl;
+    case FORM_ANTI1: return 4 * ctl;
+    case FORM_DIAG1: return 4 * ctl;
+    case FORM_PHASE1: return 2 * ctl;
+    case FORM_SWAP2: return 0;
+    default: return 16 * ctl;
+  }
+}
+
+// ---------------------------------------------------------------- contraction
+
+static int popc(uint64_t v) { return __builtin_popcountll(v); }
+
+static std::vector<int> mask_bits(uint64_t m) {
+  std::vector<int> v;
+  for (int b = 0; b < 64; ++b)
+    if (m & (1ull << b)) v.push_back(b);
+  return v;
+}
+
+// Paper-mode merge test (Section 3.4): one-qubit gates on <= 2 distinct qubits,
+// or controlled one-target gates with identical (controls, target).
+static bool paper_mergeable(const HGate& a, const HGate& b, uint64_t Q) {
+  const bool a1 = a.nt == 1 && a.nc == 0, b1 = b.nt == 1 && b.nc == 0;
+  if (a1 && b1) return popc(Q | b.qmask) <= 2;
+  if (a.nt == 1 && b.nt == 1 && a.nc > 0 && b.nc > 0)
+    return a.t[0] == b.t[0] && a.cmask == b.cmask;
+  return false;
+}
+
+std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOptions& o) {
+  const int G = (int)gates.size();
+  // DAG: immediate predecessors = last earlier gate on each qubit of the gate.
+  std::vector<std::vector<int>> pred(G);
+  std::vector<int> last(n, -1);
+  for (int i = 0; i < G; ++i) {
+    for (int b : mask_bits(gates[i].qmask)) {
+      if (last[b] >= 0 && std::find(pred[i].begin(), pred[i].end(), last[b]) == pred[i].end())
+        pred[i].push_back(last[b]);
+      last[b] = i;
+    }
+  }
+  std::vector<char> done(G, 0);   // emitted
+  std::vector<int> owner(G, -1);  // block currently being built
+  std::vector<Block> blocks;
+  int first = 0;
+  const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
+  while (first < G) {
+    while (first < G && done[first]) ++first;
+    if (first >= G) break;
+    const int bid = (int)blocks.size();
+    Block blk;
+    blk.gates.push_back(first);
+    owner[first] = bid;
+    uint64_t Q = gates[first].qmask, blocked = 0;
+    const int kcap = o.paper ? 2 : std::max(o.k, popc(Q));
+    for (int h = first + 1; h < G; ++h) {
+      if (done[h]) continue;
+      const uint64_t qh = gates[h].qmask;
+      if (qh & blocked) { blocked |= qh; }
+      else {
+        bool ok = popc(Q | qh) <= kcap;
+        if (ok && o.paper) ok = paper_mergeable(gates[blk.gates[0]], gates[h], Q);
+        if (ok)
+          for (int p : pred[h])
+            if (!done[p] && owner[p] != bid) { ok = false; break; }
+        if (ok) {
+          blk.gates.push_back(h);
+          owner[h] = bid;
+          Q |= qh;
+        } else {
+          blocked |= qh;
+        }
+      }
+      if ((blocked | Q) == all && (Q & ~blocked) == 0) break;
+      if (popc(Q) >= kcap && (Q & ~blocked) == 0) break;
+    }
+    for (int g : blk.gates) done[g] = 1;
+    blk.qubits = mask_bits(Q);
+    blk.diag = true;
+    for (int g : blk.gates) {
+      blk.diag = blk.diag && (gates[g].form == FORM_PHASE1 || gates[g].form == FORM_DIAG1);
+      blk.parametric = blk.parametric || gates[g].parametric;
+    }
+    // Representation (Section 3.4's cost rule, in FMA + shared-memory bytes).
+    const int k = (int)blk.qubits.size();
+    if (blk.gates.size() == 1) {
+      blk.rep = OP_GATE;
+    } else if (o.paper) {
+      blk.rep = blk.diag ? OP_DIAG : OP_DENSE;
+    } else {
+      double sep = 0;
+      for (int g : blk.gates)
+        sep += o.fp_weight * gate_fma_per_amp(gates[g]) + 2.0 * o.amp_bytes * gate_sweep_fraction(gates[g]);
+      const double dense = o.fp_weight * 4.0 * (1 << k) + 2.0 * o.amp_bytes;
+      const double dg = o.fp_weight * 4.0 + 2.0 * o.amp_bytes;
+      if (blk.diag) blk.rep = dg < sep ? OP_DIAG : OP_GATE;
+      else blk.rep = (!o.cost_model || dense < sep) ? OP_DENSE : OP_GATE;
+    }
+    blocks.push_back(std::move(blk));
+  }
+  return blocks;
+}
+
+// Applies one gate, given in block-local bit positions, to a 2^k vector.
+static void apply_local(const HGate& g, const int* lpos_t, uint64_t lcmask, const cd* m, cd* v, int k) {
+  const uint64_t dim = 1ull << k;
+  if (g.nt == 1) {
+    const uint64_t tb = 1ull << lpos_t[0];
+    for (uint64_t i = 0; i < dim; ++i) {
+      if ((i & lcmask) != lcmask || (i & tb)) continue;
+      const cd a0 = v[i], a1 = v[i | tb];
+      v[i] = m[0] * a0 + m[1] * a1;
+      v[i | tb] = m[2] * a0 + m[3] * a1;
+    }
+  } else {
+    const uint64_t ta = 1ull << lpos_t[0], tb = 1ull << lpos_t[1];
+    for (uint64_t i = 0; i < dim; ++i) {
+      if ((i & lcmask) != lcmask || (i & (ta | tb))) continue;
+      const uint64_t idx[4] = {i, i | ta, i | tb, i | ta | tb};
+      cd a[4], r[4];
+      for (int j = 0; j < 4; ++j) a[j] = v[idx[j]];
+      for (int r_ = 0; r_ < 4; ++r_) {
+        r[r_] = 0;
+        for (int j = 0; j < 4; ++j) r[r_] += m[4 * r_ + j] * a[j];
+      }
+      for (int j = 0; j < 4; ++j) v[idx[j]] = r[j];
+    }
+  }
+}
+
+void block_matrix(const Block& b, const std::vector<HGate>& gates, const double* theta, std::vector<cd>& M) {
+  const int k = (int)b.qubits.size();
+  const uint64_t D = 1ull << k;
+  M.assign(D * D, cd(0));
+  auto local = [&](int q) {
+    for (int j = 0; j < k; ++j)
+      if (b.qubits[j] == q) return j;
+    throw Error(QS_ERR_ARG, "internal: qubit not in block");
+  };
+  std::vector<cd> col(D);
+  for (uint64_t c = 0; c < D; ++c) {
+    std::fill(col.begin(), col.end(), cd(0));
+    col[c] = 1;
+    for (int gi : b.gates) {
+      const HGate& g = gates[gi];
+      cd m[16];
+      target_matrix(g, theta, m);
+      int lt[2] = {local(g.t[0]), g.nt == 2 ? local(g.t[1]) : 0};
+      uint64_t lc = 0;
+      for (int j = 0; j < g.nc; ++j) lc |= 1ull << local(g.c[j]);
+      apply_local(g, lt, lc, m, col.data(), k);
+    }
+    for (uint64_t r = 0; r < D; ++r) M[r * D + c] = col[r];
+  }
+}
+
+// ---------------------------------------------------------------- passes
+
+std::vector<PassRec> schedule_passes(int n, const std::vector<OpRec>& ops, int m, int L,
+                                     std::vector<int>& order_out) {
+  const int N = (int)ops.size();
+  std::vector<std::vector<int>> pred(N);
+  std::vector<int> last(n, -1);
+  for (int i = 0; i < N; ++i)
+    for (int b : mask_bits(ops[i].qmask)) {
+      if (last[b] >= 0 && std::find(pred[i].begin(), pred[i].end(), last[b]) == pred[i].end())
+        pred[i].push_back(last[b]);
+      last[b] = i;
+    }
+  const uint64_t low = L >= 64 ? ~0ull : ((1ull << L) - 1);
+  std::vector<char> done(N, 0);
+  std::vector<int> owner(N, -1);
+  std::vector<PassRec> passes;
+  std::vector<int> order;   // ops reordered pass by pass
+  order.reserve(N);
+  int first = 0;
+  while (true) {
+    while (first < N && done[first]) ++first;
+    if (first >= N) break;
+    const int pid = (int)passes.size();
+    PassRec pr;
+    pr.op_begin = (int)order.size();
+    std::vector<int> members{first};
+    owner[first] = pid;
+    uint64_t Q = low | ops[first].qmask, blocked = 0;
+    for (int h = first + 1; h < N; ++h) {
+      if (done[h]) continue;
+      const uint64_t qh = ops[h].qmask;
+      if (qh & blocked) { blocked |= qh; continue; }
+      bool ok = popc(Q | qh) <= m;
+      if (ok)
+        for (int p : pred[h])
+          if (!done[p] && owner[p] != pid) { ok = false; break; }
+      if (ok) { members.push_back(h); owner[h] = pid; Q |= qh; }
+      else blocked |= qh;
+      if (popc(Q) >= m && (Q & ~blocked) == 0) break;
+    }
+    for (int h : members) { done[h] = 1; order.push_back(h); }
+    // pad the tile to m qubits with the lowest unused qubits
+    for (int b = 0; b < n && popc(Q) < m; ++b) Q |= 1ull << b;
+    pr.tile = mask_bits(Q);
+    pr.op_end = (int)order.size();
+    passes.push_back(pr);
+  }
+  order_out = order;
+  return passes;
+}
+
+}  // namespace qs

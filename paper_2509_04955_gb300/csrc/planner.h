@@ -1,0 +1,83 @@
+// Circuit IR, gate DAG and dependency-aware contraction (Section 3.4), host side, FP64.
+#pragma once
+
+#include <complex>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "qs_internal.h"
+
+namespace qs {
+
+using cd = std::complex<double>;
+
+struct HGate {
+  int kind = 0;
+  int nt = 1, t[2] = {-1, -1};
+  int nc = 0, c[2] = {-1, -1};
+  uint64_t cmask = 0, qmask = 0;
+  int param_index = -1;
+  double param = 0, scale = 1;
+  bool parametric = false;
+  int form = FORM_DENSE1;
+  cd fixed[16];              // target matrix (2x2 in the first 4) when not parametric
+  cd custom[16];             // U1 / U2 input matrix
+};
+
+// Validates and resolves the caller's gates. Throws qs::Error on bad input.
+void resolve_gates(int n, const qs_gate* g, size_t ng, std::vector<HGate>& out);
+// Target matrix (2x2 or 4x4 row-major) for given theta (may be null when not parametric).
+void target_matrix(const HGate& g, const double* theta, cd* m);
+// Device descriptor with global bit positions; `pairs` forces the pair
+// enumeration of DENSE1 (used by the adjoint step for diagonal gates).
+DevGate make_dev_gate(const HGate& g, bool pairs = false);
+// Fraction of a state sweep (read + write of all amplitudes) one gate moves
+// when applied alone: 1 for a dense one-target gate, 1/2 per control, 1/2 for
+// phase gates (only the |1> half changes), 1/2 for SWAP.
+double gate_sweep_fraction(const HGate& g);
+// FMA instructions per amplitude of one gate applied alone.
+double gate_fma_per_amp(const HGate& g);
+
+struct Block {
+  std::vector<int> gates;    // program order
+  std::vector<int> qubits;   // ascending; local bit j <-> qubits[j]
+  bool diag = false;         // every member gate is diagonal
+  bool parametric = false;   // some member depends on theta
+  int rep = OP_GATE;         // OP_GATE (members applied one by one), OP_DENSE or OP_DIAG
+};
+
+struct PlanOptions {
+  int k = 1;                 // block width
+  bool paper = false;        // only the merges of Section 3.4
+  bool cost_model = true;    // keep gates separate when the dense block costs more
+  double fp_weight = 1.0;    // cost of one FMA relative to one byte of shared-memory traffic
+  int amp_bytes = 8;
+};
+
+// DAGC-k greedy contraction. Returns blocks in emission order.
+std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOptions& o);
+
+// Dense 2^k x 2^k matrix of a block (local bit j <-> block.qubits[j]), ordered
+// product of the member gates (Eq. 7 for distinct qubits, M2 M1 on one qubit).
+void block_matrix(const Block& b, const std::vector<HGate>& gates, const double* theta, std::vector<cd>& M);
+
+struct OpRec {               // one op of the fused program (global qubit positions)
+  int type;                  // OP_GATE / OP_DENSE / OP_DIAG
+  int gate = -1;             // OP_GATE: gate index
+  int block = -1;            // OP_DENSE / OP_DIAG: block index
+  uint64_t qmask = 0;
+};
+
+struct PassRec {
+  std::vector<int> tile;     // tile qubits, ascending (contains 0..L-1)
+  int op_begin = 0, op_end = 0;
+};
+
+// Groups ops into tile passes of <= m qubits that always contain qubits
+// 0..L-1 (the same greedy over the op DAG, width m). order_out lists the op
+// indices pass by pass; a pass covers order_out[op_begin .. op_end).
+std::vector<PassRec> schedule_passes(int n, const std::vector<OpRec>& ops, int m, int L,
+                                     std::vector<int>& order_out);
+
+}  // namespace qs

@@ -1,0 +1,142 @@
+// Internal declarations shared by the host runtime (C++) and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "qsim_gb300.h"
+
+#ifdef __CUDACC__
+#define QS_HD __host__ __device__ __forceinline__
+#else
+#define QS_HD inline
+#endif
+
+namespace qs {
+
+constexpr int kMaxQubits = 40;
+constexpr int kMaxControls = 2;
+constexpr int kMaxBlockQubits = 6;   // dense block width handled by any kernel
+
+// ---------------------------------------------------------------------------
+// Gate descriptors as the kernels see them. Matrices live in a device table of
+// FP64 complex entries (16 per gate: 2x2 uses the first 4); parametric entries
+// are filled on the device from theta by k_resolve (one table per batch row).
+
+enum GateForm : int32_t {
+  FORM_DENSE1 = 0,   // 2x2 general on one target
+  FORM_ANTI1 = 1,    // 2x2 anti-diagonal (X, Y): pairs swap with phases
+  FORM_DIAG1 = 2,    // 2x2 diagonal
+  FORM_PHASE1 = 3,   // 2x2 diagonal with m00 == 1 for every angle (Z, S, T, P)
+  FORM_SWAP2 = 4,    // two-target SWAP
+  FORM_DENSE2 = 5    // two-target 4x4 general
+};
+
+struct DevGate {
+  int32_t form;
+  int32_t t0, t1;          // targets (t1 = -1 for one-target forms)
+  int32_t nins;            // number of sorted bit positions to insert (targets + controls)
+  int32_t ins[4];          // ascending bit positions of targets and controls
+  uint64_t cmask;          // control bits
+  int32_t kind;            // qs_gate_kind, for k_resolve
+  int32_t param_index;     // -1 = fixed
+  double param, scale;
+};
+
+// Op inside a tile pass, in tile-local bit positions.
+enum OpType : int32_t {
+  OP_GATE = 0,    // one original gate: form + tile-local positions, matrix from the gate table
+  OP_DENSE = 1,   // dense k-qubit block, matrix (2^k x 2^k) in the block table
+  OP_DIAG = 2     // diagonal k-qubit block, 2^k phases in the block table
+};
+
+struct DevOp {
+  int32_t type;
+  int32_t form;            // for OP_GATE
+  int32_t k;               // qubits of a block op
+  int32_t nins;            // OP_GATE: positions to insert (targets + controls), ascending
+  int32_t ins[6];          // OP_GATE: sorted insert positions; blocks: op qubit positions ascending
+  int32_t t0, t1;          // OP_GATE target positions (tile-local)
+  uint32_t cmask;          // OP_GATE control mask (tile-local)
+  int32_t mat;             // OP_GATE: gate index in the gate table; blocks: complex offset in block table
+  int32_t pad;
+};
+
+struct PassDesc {
+  int32_t m;               // tile qubits
+  int32_t L;               // low qubits 0..L-1 contained in the tile
+  int32_t nhigh;           // tile qubits above L-1
+  int32_t high[14];        // their global positions, ascending
+  int32_t kmax;            // widest dense block op in the pass (selects the kernel instance)
+  int32_t op_begin, op_end;
+};
+
+size_t tile_smem_bytes(int m, int nhigh, int kmax, qs_dtype dt);
+
+// ---------------------------------------------------------------------------
+// Bit helpers.
+
+QS_HD uint64_t insert_zero_bits(uint64_t x, const int32_t* pos, int npos) {
+  // pos ascending: make room for a zero bit at each position in turn.
+  for (int k = 0; k < npos; ++k) {
+    const uint64_t lo = x & ((1ull << pos[k]) - 1);
+    x = ((x >> pos[k]) << (pos[k] + 1)) | lo;
+  }
+  return x;
+}
+
+// Same, with the loop unrolled to MAXN steps so `pos` can stay in registers.
+template <int MAXN, typename U>
+QS_HD U insert_zero_bits_u(U x, const int32_t* pos, int npos) {
+#ifdef __CUDACC__
+#pragma unroll
+#endif
+  for (int k = 0; k < MAXN; ++k) {
+    if (k < npos) {
+      const U lo = x & ((U(1) << pos[k]) - 1);
+      x = ((x >> pos[k]) << (pos[k] + 1)) | lo;
+    }
+  }
+  return x;
+}
+
+// ---------------------------------------------------------------------------
+// Kernel launch wrappers (kernels_*.cu). All return cudaError_t of the launch.
+
+template <typename R> struct Cplx;
+template <> struct Cplx<float> { using T = float2; };
+template <> struct Cplx<double> { using T = double2; };
+
+cudaError_t launch_set_basis(void* psi, int n, qs_dtype dt, uint64_t x, cudaStream_t st);
+cudaError_t launch_resolve(const DevGate* gates, const int32_t* param_gates, int nparam_gates,
+                           const double* theta, int64_t ntheta, int batch, double2* table,
+                           int64_t table_stride, cudaStream_t st);
+cudaError_t launch_gate(void* psi, int n, qs_dtype dt, const DevGate& g, const double2* mat,
+                        bool adjoint, cudaStream_t st);
+cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
+                             const double2* gate_table, const double2* block_table, int threads,
+                             cudaStream_t st);
+
+// Reductions write FP64 partials into `partials` (capacity >= reduce_blocks()).
+int reduce_blocks();
+cudaError_t launch_norm(const void* psi, int n, qs_dtype dt, double* partials, double* out,
+                        cudaStream_t st);
+cudaError_t launch_inner(const void* a, const void* b, int n, qs_dtype dt, double* partials,
+                         double* out2, cudaStream_t st);
+cudaError_t launch_expval_x(const void* psi, int n, qs_dtype dt, uint64_t xmask,
+                            const uint64_t* zmasks, const double* coeffs, int nz, double* partials,
+                            double* out, cudaStream_t st);
+cudaError_t launch_apply_pauli(const void* psi, void* out, int n, qs_dtype dt,
+                               const uint64_t* xm, const uint64_t* zm, const double* coeff, int nt,
+                               cudaStream_t st);
+cudaError_t launch_adjoint_step(void* phi, void* lam, int n, qs_dtype dt, const DevGate& g,
+                                const double2* mat, const double2* dmat, double* partials_row,
+                                cudaStream_t st);
+cudaError_t launch_sum_rows(const double* partials, int rows, int cols, double* out,
+                            cudaStream_t st);
+
+void note_launch(int64_t k = 1);
+// While suspended (graph capture), launches are not counted; replays are.
+void suspend_launch_count(bool on);
+
+}  // namespace qs

@@ -1,0 +1,288 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Bars (written into every comparison): complex128 max |delta amp| <= 1e-12,
+complex64 max |delta amp| <= 2e-5; expectation values and gradients to the
+same absolute bars scaled by the Hamiltonian's coefficient sum.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2509_04955_gb300 as Q
+from paper_2509_04955_gb300 import build as B
+from paper_2509_04955_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+TOL = {Q.QS_C128: 1e-12, Q.QS_C64: 2e-5}
+DT = {"c128": Q.QS_C128, "c64": Q.QS_C64}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+    import torch
+    assert torch.cuda.is_available()
+
+
+def run(n, dt, gates, theta=None, psi0=None, opts=None, basis=0):
+    h = Q.qs_state_alloc(n, dt)
+    try:
+        if psi0 is not None:
+            Q.qs_state_copy_from_host(h, np.ascontiguousarray(psi0, dtype=Q.NP_DTYPE[dt]))
+        else:
+            Q.qs_state_set_basis(h, basis)
+        Q.qs_apply_circuit(h, gates, theta, opts)
+        out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+        Q.qs_state_copy_to_host(h, out)
+        return out
+    finally:
+        Q.qs_state_free(h)
+
+
+def ref(n, gates, theta=None, psi0=None, basis=0):
+    psi = O.basis(n, basis) if psi0 is None else np.asarray(psi0, dtype=np.complex128)
+    return O.apply_circuit(psi, n, gates, theta)
+
+
+FUSED = [None, Q.make_opts(fuse_k=1, tile_qubits=6, low_qubits=2), Q.make_opts(fuse_k=2, tile_qubits=8, low_qubits=3),
+         Q.make_opts(fuse_k=3), Q.make_opts(fuse_k=4, tile_qubits=10, low_qubits=4),
+         Q.make_opts(fuse_k=5, tile_qubits=11, low_qubits=3), Q.make_opts(paper_mode=1)]
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+def test_random_depth20_n12_per_gate_matches_oracle(dtname):
+    """n = 12 from |0..0>, depth-20 random layers with CNOT matchings, per-gate."""
+    dt = DT[dtname]
+    n = 12
+    gates = W.random_layered(n, 20, seed=0)
+    got = run(n, dt, gates)
+    want = ref(n, gates)
+    assert np.abs(got - want).max() <= TOL[dt]
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+@pytest.mark.parametrize("oi", range(len(FUSED)))
+def test_every_gate_kind_every_mode(dtname, oi):
+    dt = DT[dtname]
+    n = 9
+    gates = W.random_gate_mix(n, 120, seed=7 + oi) + W.random_layered(n, 3, seed=oi)
+    psi0 = W.random_state(n, 3)
+    got = run(n, dt, gates, psi0=psi0, opts=FUSED[oi])
+    assert np.abs(got - ref(n, gates, psi0=psi0)).max() <= TOL[dt]
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+@pytest.mark.parametrize("n", [1, 2, 3, 5])
+def test_tiny_states_ragged_tiles(dtname, n):
+    dt = DT[dtname]
+    gates = W.random_gate_mix(n, 40, seed=n)
+    psi0 = W.random_state(n, n)
+    for opts in (None, Q.make_opts(fuse_k=2), Q.make_opts(fuse_k=min(n, 5), tile_qubits=n, low_qubits=n)):
+        got = run(n, dt, gates, psi0=psi0, opts=opts)
+        assert np.abs(got - ref(n, gates, psi0=psi0)).max() <= TOL[dt]
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+def test_fused_random_n18_spans_many_tiles(dtname):
+    dt = DT[dtname]
+    n = 18
+    gates = W.random_layered(n, 6, seed=4)
+    want = ref(n, gates)
+    for opts in (Q.make_opts(fuse_k=4), Q.make_opts(fuse_k=2, tile_qubits=9, low_qubits=5),
+                 Q.make_opts(fuse_k=3, tile_qubits=13, low_qubits=2)):
+        got = run(n, dt, gates, opts=opts)
+        assert np.abs(got - want).max() <= TOL[dt]
+
+
+@pytest.mark.parametrize("n", [2, 7, 13])
+def test_ghz_closed_form(n):
+    gates = [W.Gate("h", (0,))] + [W.Gate("x", (q,), controls=(q - 1,)) for q in range(1, n)]
+    for opts in (None, Q.make_opts(fuse_k=3)):
+        got = run(n, Q.QS_C128, gates, opts=opts)
+        want = np.zeros(1 << n, dtype=complex)
+        want[0] = want[-1] = 1 / math.sqrt(2)
+        assert np.abs(got - want).max() <= 1e-12
+
+
+def qft_closed_form(n, x, idx):
+    return np.exp(2j * np.pi * ((x * idx) % (1 << n)) / (1 << n)) / math.sqrt(1 << n)
+
+
+def test_qft_n14_all_modes_vs_oracle_and_closed_form():
+    n = 14
+    x = W.random_basis_index(n, 1)
+    gates = W.qft(n)
+    want = ref(n, gates, basis=x)
+    y = np.arange(1 << n)
+    assert np.abs(want - qft_closed_form(n, x, y)).max() < 1e-12
+    for opts in (None, Q.make_opts(fuse_k=2), Q.make_opts(fuse_k=4), Q.make_opts(fuse_k=5)):
+        got = run(n, Q.QS_C128, gates, opts=opts, basis=x)
+        assert np.abs(got - want).max() <= 1e-12
+
+
+def test_qft_n28_c128_full_size_sampled_closed_form():
+    """QFT on 28 qubits (4 GiB complex128) from a seeded basis state; the
+    closed form gives every amplitude, checked on 2^16 sampled indices, and
+    the norm is checked on the device in FP64."""
+    n = 28
+    x = W.random_basis_index(n, 28)
+    gates = W.qft(n)
+    rng = np.random.default_rng(0)
+    idx = np.unique(rng.integers(0, 1 << n, size=1 << 16))
+    for opts in (Q.make_opts(fuse_k=4), None):
+        h = Q.qs_state_alloc(n, Q.QS_C128)
+        try:
+            Q.qs_state_set_basis(h, x)
+            Q.qs_apply_circuit(h, gates, None, opts)
+            out = np.empty(1 << n, dtype=np.complex128)
+            Q.qs_state_copy_to_host(h, out)
+            assert abs(Q.qs_norm(h) - 1) < 1e-12
+        finally:
+            Q.qs_state_free(h)
+        assert np.abs(out[idx] - qft_closed_form(n, x, idx)).max() <= 1e-12
+        assert np.abs(np.abs(out) - 2.0 ** (-n / 2)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+def test_norm_expval_pauli_apply_inner(dtname):
+    dt = DT[dtname]
+    n = 12
+    psi = W.random_state(n, 5)
+    coeff, xm, zm = W.random_pauli_sum(n, 40, seed=2)
+    # add a few diagonal and repeated-x strings
+    coeff = np.concatenate([coeff, [0.7, -0.3, 1.1]])
+    xm = np.concatenate([xm, np.array([0, 0, xm[0]], dtype=np.uint64)])
+    zm = np.concatenate([zm, np.array([5, 3, 9], dtype=np.uint64)])
+    h = Q.qs_state_alloc(n, dt)
+    h2 = Q.qs_state_alloc(n, dt)
+    try:
+        Q.qs_state_copy_from_host(h, psi.astype(Q.NP_DTYPE[dt]))
+        psi_dev = psi.astype(Q.NP_DTYPE[dt]).astype(np.complex128)   # what the device holds
+        tol = TOL[dt]
+        assert abs(Q.qs_norm(h) - O.norm2(psi_dev, n)) <= tol
+        e = Q.qs_expval_pauli_sum(h, coeff, xm, zm)
+        assert abs(e - O.expval(psi_dev, n, coeff, xm, zm).real) <= tol * np.abs(coeff).sum()
+        Q.qs_apply_pauli_sum(h, coeff, xm, zm, h2)
+        out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+        Q.qs_state_copy_to_host(h2, out)
+        assert np.abs(out - O.apply_pauli_sum(psi_dev, n, coeff, xm, zm)).max() <= tol * np.abs(coeff).sum()
+        ip = Q.qs_inner(h, h2)
+        want = np.vdot(psi_dev, O.apply_pauli_sum(psi_dev, n, coeff, xm, zm))
+        assert abs(ip - want) <= tol * np.abs(coeff).sum()
+    finally:
+        Q.qs_state_free(h)
+        Q.qs_state_free(h2)
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+@pytest.mark.parametrize("maker", ["hea", "ucc", "controlled"])
+def test_adjoint_gradient_matches_oracle(dtname, maker):
+    dt = DT[dtname]
+    n = 10
+    if maker == "hea":
+        gates, p = W.hea(n, 3)
+        theta = W.thetas_uniform(p, 1)
+    elif maker == "ucc":
+        gates, _ = W.ucc(n, 20, 2, wmin=2, wmax=6)
+        p = 20
+        theta = W.thetas_normal(p, 3, sigma=0.4)
+    else:
+        gates = W.random_layered(n, 2, 1) + [
+            W.Gate("ry", (3,), (1,), param_index=0), W.Gate("p", (2,), (5, 6), param_index=1),
+            W.Gate("rx", (0,), (9,), param_index=0, scale=-0.5), W.Gate("rz", (7,), param_index=2, scale=3.0),
+            W.Gate("swap", (2, 8)), W.Gate("u2", (1, 4), matrix=tuple(W.random_unitary(4, np.random.default_rng(1)).reshape(-1)))]
+        p = 3
+        theta = np.array([0.3, -1.1, 0.7])
+    H = W.random_pauli_sum(n, 30, seed=6)
+    h = Q.qs_state_alloc(n, dt)
+    try:
+        e, g = Q.qs_adjoint_grad(h, gates, theta, *H)
+    finally:
+        Q.qs_state_free(h)
+    e_ref, g_ref = O.adjoint_grad(O.basis(n, 0), n, gates, theta, *H)
+    scale = np.abs(H[0]).sum()
+    assert abs(e - e_ref) <= TOL[dt] * scale * 10
+    assert np.abs(g - g_ref).max() <= TOL[dt] * scale * 10
+
+
+def test_adjoint_hea_n24_full_size_against_device_parameter_shift():
+    """Hardware-efficient ansatz at its full size (24 qubits, 12 layers, 576
+    parameters, 150-term H): the adjoint gradient equals the two-term shift
+    rule evaluated with the device's own forward + expectation on 8 sampled
+    parameters (a property that holds at any size)."""
+    n = 24
+    gates, p = W.hea(n, 12)
+    theta = W.thetas_uniform(p, 4)
+    H = W.random_pauli_sum(n, 150, seed=4)
+    h = Q.qs_state_alloc(n, Q.QS_C128)
+    try:
+        e, g = Q.qs_adjoint_grad(h, gates, theta, *H)
+        plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(fuse_k=2))
+        try:
+            def f(th):
+                Q.qs_state_set_basis(h, 0)
+                Q.qs_plan_execute(plan, h, th)
+                return Q.qs_expval_pauli_sum(h, *H)
+            assert abs(f(theta) - e) < 1e-10
+            for j in np.random.default_rng(0).choice(p, size=8, replace=False):
+                tp, tm = theta.copy(), theta.copy()
+                tp[j] += math.pi / 2
+                tm[j] -= math.pi / 2
+                assert abs(0.5 * (f(tp) - f(tm)) - g[j]) < 1e-10
+        finally:
+            Q.qs_plan_free(plan)
+    finally:
+        Q.qs_state_free(h)
+
+
+@pytest.mark.parametrize("dtname", ["c64", "c128"])
+def test_batched_graph_matches_sequential_and_oracle(dtname):
+    dt = DT[dtname]
+    n, nterms, Bsz = 10, 16, 4
+    gates, _ = W.ucc(n, nterms, 5, wmin=2, wmax=6)
+    thetas = W.thetas_normal(nterms, 6, sigma=0.3, batch=Bsz)
+    H = W.random_pauli_sum(n, 25, seed=8)
+    for opts in (None, Q.make_opts(fuse_k=1)):
+        plan = Q.qs_plan_create(n, dt, gates, opts)
+        states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
+        try:
+            for rep in range(2):      # second call replays the captured graph
+                for s in states:
+                    Q.qs_state_set_basis(s, 0)
+                th = thetas if rep == 0 else thetas[::-1].copy()
+                ex = Q.qs_plan_execute_batched(plan, states, th, H)
+                for b in range(Bsz):
+                    want = O.expval_of_circuit(O.basis(n, 0), n, gates, th[b], *H)
+                    assert abs(ex[b] - want) <= TOL[dt] * np.abs(H[0]).sum() * 10
+        finally:
+            for s in states:
+                Q.qs_state_free(s)
+            Q.qs_plan_free(plan)
+
+
+def test_invalid_sizes_give_errors_not_faults():
+    h = Q.qs_state_alloc(4, Q.QS_C64)
+    try:
+        with pytest.raises(Q.QsError):
+            Q.qs_state_set_basis(h, 1 << 4)
+        with pytest.raises(Q.QsError):
+            Q.qs_state_copy_to_host(h, np.empty(8, dtype=np.complex64))
+        with pytest.raises(Q.QsError):
+            Q.qs_apply_circuit(h, [W.Gate("h", (4,))])
+        with pytest.raises(Q.QsError):
+            Q.qs_expval_pauli_sum(h, [1.0], [1 << 4], [0])
+        with pytest.raises(Q.QsError):
+            Q.qs_apply_circuit(h, [W.Gate("rx", (0,), param_index=3)], np.zeros(2))
+    finally:
+        Q.qs_state_free(h)
+    with pytest.raises(Q.QsError) as e:
+        Q.qs_state_alloc(40, Q.QS_C128)     # 16 TiB
+    assert e.value.status == Q.QS_ERR_OOM
+
+
+def test_launch_counter_moves():
+    before = Q.qs_launch_count()
+    run(8, Q.QS_C64, W.random_layered(8, 2, 0))
+    assert Q.qs_launch_count() > before

@@ -1,0 +1,166 @@
+"""Host-side checks of the CUDA library: it builds, loads, exports every entry
+point declared in include/qsim_gb300.h, validates arguments, refuses to run
+without a GPU (no CPU fallback), and its planner (gate DAG + contraction +
+tile passes, all host code) produces op sequences whose product equals the
+oracle's brute-force unitary.
+"""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2509_04955_gb300 as Q
+from paper_2509_04955_gb300 import build as B
+from paper_2509_04955_gb300 import workloads as W
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module", autouse=True)
+def built():
+    B.build()
+
+
+def header_functions():
+    src = open(os.path.join(ROOT, "include", "qsim_gb300.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(qs_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported_and_bound():
+    L = Q.lib()
+    names = header_functions()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(L, name), name
+        assert name in Q.exported_symbols(), name
+    assert "sm_103a" in Q.qs_version()
+
+
+def test_no_gpu_means_an_error_not_a_fallback():
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(Q.QsError) as e:
+        Q.qs_state_alloc(4, Q.QS_C64)
+    assert e.value.status == Q.QS_ERR_CUDA
+
+
+@pytest.mark.parametrize("bad", [
+    [W.Gate("h", (5,))],                         # qubit >= n
+    [W.Gate("x", (1,), controls=(1,))],          # repeated qubit
+    [W.Gate("swap", (0,))],                      # wrong target count
+    [W.Gate("x", (0,), controls=(1, 2, 3))],     # too many controls
+])
+def test_invalid_gates_are_rejected_before_device_work(bad):
+    with pytest.raises(Q.QsError) as e:
+        Q.qs_plan_create(4, Q.QS_C64, bad, Q.make_opts())
+    assert e.value.status == Q.QS_ERR_ARG
+
+
+def test_theta_bounds_and_options_are_validated():
+    with pytest.raises(Q.QsError):
+        Q.qs_plan_create(10, Q.QS_C128, W.qft(10), Q.make_opts(fuse_k=6))   # CUDA-core blocks: k <= 5
+    with pytest.raises(Q.QsError):
+        Q.qs_plan_create(10, Q.QS_C64, W.qft(10), Q.make_opts(tile_qubits=15))
+
+
+# ------------------------------------------------------------- planner algebra
+
+def apply_block(psi, n, qubits, M):
+    """Applies a 2^k x 2^k matrix over `qubits` (local bit j = qubits[j])."""
+    k = len(qubits)
+    others = [q for q in range(n) if q not in qubits]
+    base = np.zeros(1 << (n - k), dtype=np.int64)
+    for j, q in enumerate(others):
+        base |= ((np.arange(1 << (n - k)) >> j) & 1) << q
+    offs = np.zeros(1 << k, dtype=np.int64)
+    for j, q in enumerate(qubits):
+        offs |= ((np.arange(1 << k) >> j) & 1) << q
+    idx = base[:, None] | offs[None, :]
+    out = psi.copy()
+    out[idx] = psi[idx] @ M.T
+    return out
+
+
+def plan_unitary(n, gates, plan, theta=None):
+    ops = Q.qs_plan_ops(plan)
+    U = np.eye(1 << n, dtype=complex)
+    for op in ops:
+        if op["type"] == 0:
+            G = O.unitary(n, [gates[op["gate"]]], theta)
+        elif op["type"] == 1:
+            G = np.stack([apply_block(c, n, op["qubits"], op["matrix"]) for c in np.eye(1 << n, dtype=complex)],
+                         axis=1)
+        else:
+            G = np.stack([apply_block(c, n, op["qubits"], np.diag(op["matrix"])) for c in np.eye(1 << n, dtype=complex)],
+                         axis=1)
+        U = G @ U
+    return U, ops
+
+
+@pytest.mark.parametrize("n,k,m,L,dt", [(6, 2, 4, 1, Q.QS_C128), (7, 3, 5, 2, Q.QS_C64), (7, 4, 6, 1, Q.QS_C64),
+                                         (5, 5, 5, 1, Q.QS_C64), (3, 2, 3, 3, Q.QS_C128)])
+def test_fused_plan_equals_brute_force(n, k, m, L, dt):
+    for seed in range(3):
+        gates = W.random_gate_mix(n, 50, seed=seed) + W.random_layered(n, 2, seed)
+        plan = Q.qs_plan_create(n, dt, gates, Q.make_opts(fuse_k=k, tile_qubits=m, low_qubits=L))
+        try:
+            U, ops = plan_unitary(n, gates, plan)
+            assert np.abs(U - O.unitary(n, gates)).max() < 1e-12
+            used = sorted(op.get("gate", -1) for op in ops if op["type"] == 0)
+            assert len(set(used)) == len(used)
+            for op in ops:   # a block starts from a gate of up to 4 qubits, then grows to k
+                assert len(op["qubits"]) <= (4 if op["type"] == 0 else max(k, 4))
+            for ps in Q.qs_plan_passes(plan):
+                assert min(m, n) <= len(ps["tile"]) <= 14   # wider only when one op needs it
+                assert set(range(min(L, n))) <= set(ps["tile"])
+                b, e = ps["ops"]
+                for op in ops[b:e]:
+                    assert set(op["qubits"]) <= set(ps["tile"])
+        finally:
+            Q.qs_plan_free(plan)
+
+
+def test_parametric_plan_resolves_at_execution_only():
+    n = 5
+    gates, p = W.hea(n, 2)
+    plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(fuse_k=3, tile_qubits=5, low_qubits=1))
+    info = Q.qs_plan_info_get(plan)
+    assert info["gates"] == len(gates)
+    Q.qs_plan_free(plan)
+
+
+def test_paper_mode_compression_on_hea():
+    """Section 3.4 merges only (k = 2): 1q (x) 1q, same-qubit products, same-(c, t) CU.
+    The paper's HEA (RX, RY, RZ layers + CNOTs) compresses by tens of percent (Fig. 16)."""
+    n = 12
+    gates = []
+    for layer in range(5):
+        for kind in ("rx", "ry", "rz"):
+            for q in range(n):
+                gates.append(W.Gate(kind, (q,), angle=0.1 * (q + layer)))
+        for q in range(layer % 2, n - 1, 2):
+            gates.append(W.Gate("x", (q + 1,), controls=(q,)))
+    plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(paper_mode=1, tile_qubits=10, low_qubits=4))
+    info = Q.qs_plan_info_get(plan)
+    ratio = (info["gates"] - info["blocks"]) / info["gates"]
+    assert 0.3 < ratio < 0.95
+    U, _ = plan_unitary(6, gates[:40] if False else [g for g in gates if max(g.qubits) < 6], Q.qs_plan_create(
+        6, Q.QS_C128, [g for g in gates if max(g.qubits) < 6], Q.make_opts(paper_mode=1, tile_qubits=6, low_qubits=1)))
+    assert np.abs(U - O.unitary(6, [g for g in gates if max(g.qubits) < 6])).max() < 1e-12
+    Q.qs_plan_free(plan)
+
+
+def test_per_gate_sweep_accounting():
+    n = 8
+    gates = [W.Gate("h", (0,)), W.Gate("x", (1,), controls=(0,)), W.Gate("z", (2,), controls=(1,)),
+             W.Gate("rz", (3,), angle=0.3), W.Gate("swap", (4, 5)), W.Gate("p", (6,), angle=0.2)]
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, None)
+    info = Q.qs_plan_info_get(plan)
+    # dense 1 + CNOT 1/2 + CZ 1/4 + RZ 1 + SWAP 1/2 + P 1/2
+    assert abs(info["per_gate_sweeps"] - (1 + 0.5 + 0.25 + 1 + 0.5 + 0.5)) < 1e-12
+    assert info["launches"] == len(gates)
+    Q.qs_plan_free(plan)
