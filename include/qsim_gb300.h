@@ -96,7 +96,10 @@ typedef struct {
   int32_t paper_mode;    /* 1 = contract only the merges of Section 3.4 (1q(x)1q, same-qubit, same-(c,t) CU) */
   int32_t tc_precision;  /* tensor mode: 1 = bf16, 3 = bf16x3 split (default), 6 = bf16x6 split */
   int32_t threads;       /* CUDA threads per tile CTA; 0 = auto */
-  int32_t reserved[9];
+  int32_t fuse_parametric; /* 1 = parametric gates may join dense blocks (block matrices are then
+                              rebuilt on the host at every execution; not usable batched).
+                              0 = they stay separate ops resolved from theta on the device. */
+  int32_t reserved[8];
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */

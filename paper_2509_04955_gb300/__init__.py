@@ -50,7 +50,7 @@ class QsPauliTerm(C.Structure):
 class QsPlanOpts(C.Structure):
     _fields_ = [("mode", C.c_int32), ("fuse_k", C.c_int32), ("tile_qubits", C.c_int32),
                 ("low_qubits", C.c_int32), ("paper_mode", C.c_int32), ("tc_precision", C.c_int32),
-                ("threads", C.c_int32), ("reserved", C.c_int32 * 9)]
+                ("threads", C.c_int32), ("fuse_parametric", C.c_int32), ("reserved", C.c_int32 * 8)]
 
 
 class QsPlanInfo(C.Structure):
@@ -168,10 +168,11 @@ def _dptr(a):
     return a, a.size
 
 
-def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0):
+def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0,
+              fuse_parametric=0):
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
-    o.paper_mode, o.tc_precision = paper_mode, tc_precision
+    o.paper_mode, o.tc_precision, o.fuse_parametric = paper_mode, tc_precision, fuse_parametric
     return o
 
 

@@ -123,9 +123,11 @@ struct qs_plan_s {
   DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab;
   int gtab_rows = 0;
   qs_plan_info info{};
-  // batched graph cache
+  // batched graph cache; captured and replayed on a plan-owned stream
   cudaGraphExec_t graph = nullptr;
   std::vector<void*> graph_key;
+  cudaStream_t cap_stream = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   // measurement: events bracketing each launch of qs_plan_execute
   bool timing = false;
   std::vector<cudaEvent_t> events;
@@ -133,6 +135,9 @@ struct qs_plan_s {
   ~qs_plan_s() {
     if (graph) cudaGraphExecDestroy(graph);
     for (cudaEvent_t e : events) cudaEventDestroy(e);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (cap_stream) cudaStreamDestroy(cap_stream);
   }
   cudaEvent_t next_event() {
     if (events_used == events.size()) {
@@ -308,6 +313,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   po.paper = o.paper_mode != 0;
   po.amp_bytes = (int)amp_bytes(dt);
   po.fp_weight = dt == QS_C64 ? 1.0 : 16.0;
+  po.fuse_parametric = o.fuse_parametric != 0;
   p->blocks = contract(n, p->gates, po);
   // ops
   std::vector<OpRec> ops;
@@ -367,6 +373,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
         d.nins = (int)ins.size();
         for (int k = 0; k < d.nins; ++k) d.ins[k] = ins[k];
         d.mat = r.gate;
+        pd.mbuf_elems = std::max(pd.mbuf_elems, 16);
         in.flops_per_amp += 2 * gate_fma_per_amp(g);
         in.max_block_qubits = std::max(in.max_block_qubits, __builtin_popcountll(g.qmask));
       } else {
@@ -376,8 +383,10 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
         d.mat = (int32_t)p->block_off[r.block];
         if (r.type == OP_DENSE) {
           pd.kmax = std::max(pd.kmax, d.k);
+          pd.mbuf_elems = std::max(pd.mbuf_elems, 1 << (2 * d.k));
           in.flops_per_amp += 8.0 * (1 << d.k);
         } else {
+          pd.mbuf_elems = std::max(pd.mbuf_elems, 1 << d.k);
           in.flops_per_amp += 8.0;
         }
         in.max_block_qubits = std::max(in.max_block_qubits, d.k);
@@ -386,7 +395,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
       p->exec_ops.push_back(r);
     }
     pd.op_end = (int)p->dops.size();
-    require(tile_smem_bytes(pd.m, pd.nhigh, pd.kmax, dt) <= 227 * 1024,
+    require(tile_smem_bytes(pd.m, pd.nhigh, pd.mbuf_elems, dt) <= 227 * 1024,
             "tile does not fit in shared memory: lower tile_qubits");
     p->pdesc.push_back(pd);
     p->pass_tiles.push_back(pr.tile);
@@ -878,8 +887,16 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     }
     require(!p->btab_parametric, "batched execution needs a plan without parametric fused blocks");
     require(terms == nullptr || expvals != nullptr, "expvals is NULL");
-    cudaStream_t st = states[0]->st;
+    cudaStream_t user_st = states[0]->st;
+    if (!p->cap_stream) {
+      CK(cudaStreamCreateWithFlags(&p->cap_stream, cudaStreamNonBlocking));
+      CK(cudaEventCreateWithFlags(&p->ev_in, cudaEventDisableTiming));
+      CK(cudaEventCreateWithFlags(&p->ev_out, cudaEventDisableTiming));
+    }
+    cudaStream_t st = p->cap_stream;   // capture is not allowed on the legacy default stream
     upload(*p);
+    CK(cudaEventRecord(p->ev_in, user_st));
+    CK(cudaStreamWaitEvent(st, p->ev_in, 0));
     ensure_gtab_rows(*p, B);
     // theta upload happens outside the graph; the graph reads p->d_theta
     if (!p->pgates.empty()) {
@@ -952,9 +969,14 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     CK(cudaGraphLaunch(p->graph, st));
     note_launch((p->pgates.empty() ? 0 : 1) +
                 (int64_t)(p->info.launches + (terms && nterms ? (int64_t)P.launches.size() * 2 : 0)) * B);
+    std::vector<double> vals;
     if (terms && nterms) {
-      std::vector<double> vals(P.zlist.size() * B);
+      vals.resize(P.zlist.size() * B);
       CK(cudaMemcpyAsync(vals.data(), d_out, sizeof(double) * vals.size(), cudaMemcpyDeviceToHost, st));
+    }
+    CK(cudaEventRecord(p->ev_out, st));
+    CK(cudaStreamWaitEvent(user_st, p->ev_out, 0));
+    if (terms && nterms) {
       CK(cudaStreamSynchronize(st));
       for (int b = 0; b < B; ++b) expvals[b] = combine_expval(P, terms, vals.data() + (size_t)b * P.zlist.size());
     }

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __rest
   const int m = p.m, L = p.L, nh = p.nhigh;
   C* tile = (C*)smem;
   uint64_t* segoff = (uint64_t*)(tile + (1u << m));
-  C* mbuf = (C*)(segoff + (1u << nh));
+  C* mbuf = (C*)(segoff + ((1u << nh) < 2 ? 2 : (1u << nh)));   // keeps mbuf 16-byte aligned
 
   for (uint32_t s = threadIdx.x; s < (1u << nh); s += kTileThreads) {
     uint64_t o = 0;
@@ -196,10 +196,10 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __rest
   }
 }
 
-size_t tile_smem_bytes(int m, int nhigh, int kmax, qs_dtype dt) {
+size_t tile_smem_bytes(int m, int nhigh, int mbuf_elems, qs_dtype dt) {
   const size_t amp = dt == QS_C64 ? 8 : 16;
-  const int mk = kmax < 2 ? 2 : kmax;
-  return (amp << m) + (8ull << nhigh) + amp * (1u << (2 * mk));
+  const size_t runs = nhigh == 0 ? 2 : (1ull << nhigh);   // padded to 16 bytes
+  return (amp << m) + 8 * runs + amp * (size_t)(mbuf_elems < 16 ? 16 : mbuf_elems);
 }
 
 template <typename R, int KMAX>
@@ -229,7 +229,7 @@ static cudaError_t launch_tile_t(void* psi, int n, const PassDesc& p, const DevO
 
 cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
                              const double2* gtab, const double2* btab, int /*threads*/, cudaStream_t st) {
-  const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.kmax, dt);
+  const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.mbuf_elems, dt);
   if (dt == QS_C64) {
     switch (p.kmax) {
       case 0: case 1: case 2: return launch_tile_t<float, 2>(psi, n, p, ops, gtab, btab, st, smem);

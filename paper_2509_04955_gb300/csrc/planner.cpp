@@ -209,12 +209,14 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
     owner[first] = bid;
     uint64_t Q = gates[first].qmask, blocked = 0;
     const int kcap = o.paper ? 2 : std::max(o.k, popc(Q));
-    for (int h = first + 1; h < G; ++h) {
+    const bool lone = !o.fuse_parametric && gates[first].parametric;   // stays a gate op
+    for (int h = first + 1; h < G && !lone; ++h) {
       if (done[h]) continue;
       const uint64_t qh = gates[h].qmask;
       if (qh & blocked) { blocked |= qh; }
       else {
         bool ok = popc(Q | qh) <= kcap;
+        if (ok && !o.fuse_parametric && gates[h].parametric) ok = false;
         if (ok && o.paper) ok = paper_mergeable(gates[blk.gates[0]], gates[h], Q);
         if (ok)
           for (int p : pred[h])

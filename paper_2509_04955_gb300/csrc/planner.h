@@ -53,6 +53,7 @@ struct PlanOptions {
   bool cost_model = true;    // keep gates separate when the dense block costs more
   double fp_weight = 1.0;    // cost of one FMA relative to one byte of shared-memory traffic
   int amp_bytes = 8;
+  bool fuse_parametric = false;   // parametric gates may join multi-gate blocks
 };
 
 // DAGC-k greedy contraction. Returns blocks in emission order.

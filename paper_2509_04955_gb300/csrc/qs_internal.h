@@ -68,10 +68,12 @@ struct PassDesc {
   int32_t nhigh;           // tile qubits above L-1
   int32_t high[14];        // their global positions, ascending
   int32_t kmax;            // widest dense block op in the pass (selects the kernel instance)
+  int32_t mbuf_elems;      // matrix staging entries the pass needs (max over its ops)
   int32_t op_begin, op_end;
 };
 
-size_t tile_smem_bytes(int m, int nhigh, int kmax, qs_dtype dt);
+// Shared memory of one tile CTA: tile + run offsets + matrix staging buffer.
+size_t tile_smem_bytes(int m, int nhigh, int mbuf_elems, qs_dtype dt);
 
 // ---------------------------------------------------------------------------
 // Bit helpers.

@@ -207,6 +207,33 @@ def test_adjoint_gradient_matches_oracle(dtname, maker):
     assert np.abs(g - g_ref).max() <= TOL[dt] * scale * 10
 
 
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+def test_parametric_circuits_both_fusion_policies(dtname):
+    """Parametric rotations resolved on the device (default) or folded into
+    dense blocks rebuilt on the host at each execution (fuse_parametric=1)."""
+    dt = DT[dtname]
+    n = 11
+    gates, p = W.hea(n, 4)
+    ucc, _ = W.ucc(n, 10, 3, wmin=2, wmax=5)
+    gates = gates + [W.Gate(g.kind, g.targets, g.controls, g.angle, g.param_index + p if g.param_index >= 0 else -1,
+                            g.scale) for g in ucc]
+    theta = W.thetas_uniform(p + 10, 5)
+    want = ref(n, gates, theta)
+    for opts in (Q.make_opts(fuse_k=3), Q.make_opts(fuse_k=4, fuse_parametric=1)):
+        h = Q.qs_state_alloc(n, dt)
+        plan = Q.qs_plan_create(n, dt, gates, opts)
+        try:
+            for th, w in ((theta, want), (theta * 0.5, ref(n, gates, theta * 0.5))):
+                Q.qs_state_set_basis(h, 0)
+                Q.qs_plan_execute(plan, h, th)
+                out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+                Q.qs_state_copy_to_host(h, out)
+                assert np.abs(out - w).max() <= TOL[dt]
+        finally:
+            Q.qs_plan_free(plan)
+            Q.qs_state_free(h)
+
+
 def test_adjoint_hea_n24_full_size_against_device_parameter_shift():
     """Hardware-efficient ansatz at its full size (24 qubits, 12 layers, 576
     parameters, 150-term H): the adjoint gradient equals the two-term shift

@@ -124,12 +124,20 @@ def test_fused_plan_equals_brute_force(n, k, m, L, dt):
             Q.qs_plan_free(plan)
 
 
-def test_parametric_plan_resolves_at_execution_only():
+def test_parametric_gates_stay_separate_unless_asked():
     n = 5
     gates, p = W.hea(n, 2)
+    theta = W.thetas_uniform(p, 0)
     plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(fuse_k=3, tile_qubits=5, low_qubits=1))
-    info = Q.qs_plan_info_get(plan)
-    assert info["gates"] == len(gates)
+    ops = Q.qs_plan_ops(plan)
+    pg = {op["gate"] for op in ops if op["type"] == 0}
+    assert all(i in pg for i, g in enumerate(gates) if g.param_index >= 0)
+    U, _ = plan_unitary(n, gates, plan, theta)
+    assert np.abs(U - O.unitary(n, gates, theta)).max() < 1e-12
+    Q.qs_plan_free(plan)
+    plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(fuse_k=3, tile_qubits=5, low_qubits=1,
+                                                             fuse_parametric=1))
+    assert any(op["type"] != 0 for op in Q.qs_plan_ops(plan))
     Q.qs_plan_free(plan)
 
 
