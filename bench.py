@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-c128", action="store_true")
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi sampler (profiler runs)")
     ap.add_argument("--tune", default="auto", help="auto | k,m,L")
     return ap.parse_args()
 
@@ -256,13 +257,14 @@ def main():
     info = Q.qs_plan_info_get(plan)
     Q.qs_state_set_basis(state, 0)
 
-    clocks = ClockSampler(local)
+    clocks = ClockSampler(local) if not args.no_clocks else None
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    clocks.start()
+    if clocks:
+        clocks.start()
     ms_step, launches, kern, norms = time_steps(Q, torch, plan, state, args.steps, args.warmup, per_launch=True)
-    clk = clocks.stop()
+    clk = clocks.stop() if clocks else None
     if dist:
         t = torch.tensor([ms_step], device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
