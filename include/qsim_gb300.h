@@ -201,6 +201,30 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B,
                                   const double* theta, size_t ntheta,
                                   const qs_pauli_term* terms, size_t nterms, double* expvals);
 
+/* ---------------- allocation-free expectation value ----------------
+ * The paper has no counterpart: this is a deployment variant of
+ * qs_expval_pauli_sum for callers that cannot allocate device memory while
+ * they evaluate an observable (a host program that owns all device memory
+ * and gives this library a fixed region, an inference or control loop with a
+ * pre-reserved memory budget, code running under another framework's
+ * allocator). It computes the same value with the same kernels, but keeps all
+ * temporaries in one array compiled into the library (80 KiB of device memory
+ * on every GPU that loads it, held until the process exits) and never calls
+ * cudaMalloc or cudaFree.
+ *   dev_state: the caller's 2^n amplitudes in device memory (16-byte aligned),
+ *              read only; stream: cudaStream_t the work is ordered on (NULL =
+ *              legacy default stream); terms: host array of nterms <= 1024
+ *              Pauli strings (more gives QS_ERR_ARG before any device work);
+ *   *out: the FP64 expectation value; the call synchronises `stream`.
+ * The first call on a device looks up the array's device address on that
+ * device (make that device current); make this first call before any stream
+ * capture. All calls share the one array: calls whose device work overlaps
+ * (other threads, other streams) race on it and must be serialised by the
+ * caller. Every slot a call reads is written earlier in the same call, so no
+ * clearing is needed between calls. */
+qs_status qs_expval_pauli_sum_noalloc(const void* dev_state, int n, qs_dtype dtype, void* stream,
+                                      const qs_pauli_term* terms, size_t nterms, double* out);
+
 /* ---------------- plan introspection (host only, no device work) ----------------
  * A plan executes ops in order: gate ops (one input gate, applied by itself)
  * and block ops (a contracted block: a dense 2^nq x 2^nq matrix, or 2^nq

@@ -95,6 +95,8 @@ _SIGS = {
     "qs_plan_pass_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I64P, _I64P]),
     "qs_plan_set_timing": (C.c_int, [_VP, C.c_int]),
     "qs_plan_timing_read": (C.c_int, [_VP, _DP, _I64P]),
+    "qs_expval_pauli_sum_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.POINTER(QsPauliTerm), C.c_size_t,
+                                              _DP]),
     "qs_last_error": (C.c_char_p, []),
     "qs_launch_count": (C.c_int64, []),
     "qs_version": (C.c_char_p, []),
@@ -260,6 +262,21 @@ def qs_inner(a: int, b: int) -> complex:
 def qs_expval_pauli_sum(state: int, coeff, xmask, zmask) -> float:
     v = C.c_double()
     _check(lib().qs_expval_pauli_sum(state, pack_terms(coeff, xmask, zmask), len(coeff), C.byref(v)))
+    return v.value
+
+
+def qs_state_info(h: int) -> tuple[int, int, int]:
+    n, dt, ptr = C.c_int(), C.c_int(), _VP()
+    _check(lib().qs_state_info(h, C.byref(n), C.byref(dt), C.byref(ptr)))
+    return n.value, dt.value, ptr.value
+
+
+def qs_expval_pauli_sum_noalloc(dev_state: int, n: int, dtype: int, stream, coeff, xmask, zmask) -> float:
+    """<H> of a state given by raw device pointer, with no device allocation
+    (for callers that must not allocate; up to 1024 terms)."""
+    v = C.c_double()
+    _check(lib().qs_expval_pauli_sum_noalloc(dev_state, n, dtype, stream, pack_terms(coeff, xmask, zmask),
+                                             len(coeff), C.byref(v)))
     return v.value
 
 

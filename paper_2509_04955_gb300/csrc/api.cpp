@@ -88,6 +88,10 @@ size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
 
 }  // namespace
 
+namespace qs {
+void set_last_error(const std::string& msg) { g_err = msg; }
+}  // namespace qs
+
 struct qs_state_s {
   int n = 0;
   qs_dtype dt = QS_C64;
