@@ -43,7 +43,7 @@ def parse():
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi sampler (profiler runs)")
-    ap.add_argument("--tune", default="auto", help="auto | k,m,L")
+    ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates]")
     return ap.parse_args()
 
 
@@ -162,10 +162,13 @@ def run_reference(args):
 
 
 def tune(Q, n, dt, gates, state, cands):
+    """Device-timed search over plan options (the autotuner): each candidate
+    is planned, run once to warm up and once timed with per-launch events."""
     best = None
-    for (k, m, L) in cands:
+    trials = []
+    for kw in cands:
         try:
-            plan = Q.qs_plan_create(n, dt, gates, Q.make_opts(fuse_k=k, tile_qubits=m, low_qubits=L))
+            plan = Q.qs_plan_create(n, dt, gates, Q.make_opts(**kw))
         except Q.QsError:
             continue
         try:
@@ -177,9 +180,10 @@ def tune(Q, n, dt, gates, state, cands):
             info = Q.qs_plan_info_get(plan)
         finally:
             Q.qs_plan_free(plan)
+        trials.append(dict(kw, ms=round(ms, 3), passes=info["passes"]))
         if best is None or ms < best[0]:
-            best = (ms, (k, m, L), info)
-    return best
+            best = (ms, kw, info)
+    return best, trials
 
 
 def time_steps(Q, torch, plan, state, steps, warmup, with_norm=True, per_launch=False):
@@ -204,9 +208,13 @@ def time_steps(Q, torch, plan, state, steps, warmup, with_norm=True, per_launch=
     total = t0.elapsed_time(t1)
     kern = None
     if per_launch:
-        kern = Q.qs_plan_timing_read(plan)
+        kern = Q.qs_plan_timing_read_kinds(plan)
         Q.qs_plan_set_timing(plan, False)
     return total / steps, Q.qs_launch_count() - launches0, kern, norms
+
+
+def mode_name(Q, kw):
+    return "tensor" if kw.get("mode") == Q.QS_MODE_TENSOR else "fused"
 
 
 def main():
@@ -237,23 +245,32 @@ def main():
     if os.path.exists(pk):
         peaks = json.load(open(pk))
     hbm_peak = peaks.get("hbm_gbs", 6800.0)
+    bf16_peak = peaks.get("bf16_tflops", 1900.0)
     peak_src = "measured" if "hbm_gbs" in peaks else "fallback"
 
     n = args.n
     gates = workload(args)
     stream = torch.cuda.current_stream().cuda_stream
     state = Q.qs_state_alloc(n, Q.QS_C64, stream)
-    amp = 8
-    sweep_bytes = 2 * (1 << n) * amp
+    sweep_bytes = 2 * (1 << n) * 8
 
-    # -- fusion options: a short device-timed search (autotuner), or given
+    # -- plan options: a short device-timed search (autotuner), or given
+    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
     if args.tune == "auto":
-        cands = [(k, m, L) for k in (1, 2, 3, 4) for (m, L) in ((12, 5), (13, 5), (12, 4), (11, 4))]
-        best = tune(Q, n, Q.QS_C64, gates, state, cands)
-        kml = best[1]
+        cands = [dict(mode=F, fuse_k=k, tile_qubits=m, low_qubits=L) for k in (1, 2, 3) for (m, L) in
+                 ((12, 4), (13, 4), (13, 5))]
+        if n >= 13:
+            cands += [dict(mode=T, fuse_k=k, tile_qubits=m, low_qubits=L, tc_min_gates=g) for g in (6, 10, 16)
+                      for k in (2, 3) for (m, L) in ((13, 4), (12, 4))]
+        best, trials = tune(Q, n, Q.QS_C64, gates, state, cands)
+        kw = best[1]
     else:
-        kml = tuple(int(x) for x in args.tune.split(","))
-    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(fuse_k=kml[0], tile_qubits=kml[1], low_qubits=kml[2]))
+        parts = [int(x) for x in args.tune.split(",")]
+        kw = dict(mode=F, fuse_k=parts[0], tile_qubits=parts[1], low_qubits=parts[2])
+        if len(parts) > 3 and parts[3] > 0:
+            kw.update(mode=T, tc_min_gates=parts[3])
+        trials = None
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(**kw))
     info = Q.qs_plan_info_get(plan)
     Q.qs_state_set_basis(state, 0)
 
@@ -270,12 +287,23 @@ def main():
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms_step = float(t.item())
 
-    kern_ms = kern[0] / max(1, kern[1])           # average tile-pass launch duration
-    achieved = sweep_bytes / (kern_ms * 1e-3) / 1e9
-    circuit_ms = kern[0] / args.steps             # device time of the passes per circuit
+    # roofline of the kernel that dominates the timed region
+    tc_dom = kern["tc_ms"] > kern["tile_ms"]
+    kname = "k_tc_block (tensor-core 6-qubit block pass)" if tc_dom else "k_tile (tile pass)"
+    kms = (kern["tc_ms"] / max(1, kern["tc_launches"])) if tc_dom else (kern["tile_ms"] / max(1, kern["tile_launches"]))
+    achieved = sweep_bytes / (kms * 1e-3) / 1e9
     eff_gbps = info["sweeps"] * sweep_bytes / (ms_step * 1e-3) / 1e9
     pg_equiv_gbps = info["per_gate_sweeps"] * sweep_bytes / (ms_step * 1e-3) / 1e9
+    kern_share = {"tile_ms_per_step": kern["tile_ms"] / args.steps, "tile_launches_per_step": kern["tile_launches"] / args.steps,
+                  "tc_ms_per_step": kern["tc_ms"] / args.steps, "tc_launches_per_step": kern["tc_launches"] / args.steps}
     extra = {}
+    if tc_dom:
+        alg_tflops = 512.0 * (1 << n) / (kms * 1e-3) / 1e12     # 8 * 2^6 real flops per amplitude
+        mult = 3 if kw.get("tc_precision", 3) in (0, 3) else 1
+        extra["tensor_pipe"] = {"algorithmic_tflops": alg_tflops, "executed_bf16_tflops": alg_tflops * 2 * mult,
+                                "bf16_peak_tflops": bf16_peak, "executed_frac": alg_tflops * 2 * mult / bf16_peak,
+                                "note": "complex 64x64 block as a real 128x128 GEMM: 2x the complex flops; "
+                                        "bf16x3 runs 3 MMAs"}
 
     # -- per-gate comparator (same circuit, same state)
     if not args.no_per_gate:
@@ -284,7 +312,7 @@ def main():
         pinfo = Q.qs_plan_info_get(pplan)
         Q.qs_plan_free(pplan)
         extra["per_gate_c64"] = {"ms": pg_ms, "sweeps": pinfo["per_gate_sweeps"], "launches": pinfo["launches"],
-                                 "effective_gbps": pinfo["per_gate_sweeps"] * sweep_bytes / (pkern[0] * 1e-3) / 1e9}
+                                 "effective_gbps": pinfo["per_gate_sweeps"] * sweep_bytes / (pkern["ms"] * 1e-3) / 1e9}
         extra["speedup_fused_vs_per_gate_c64"] = pg_ms / ms_step
 
     # -- end to end through the C ABI with host buffers (pinned)
@@ -303,33 +331,48 @@ def main():
     e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
     e2e_norm = float(np.sum(np.abs(host_out.numpy().astype(np.complex128)) ** 2))
     del host_in, host_out
-    Q.qs_plan_free(plan)
-    Q.qs_state_free(state)
-    torch.cuda.empty_cache()
 
-    # -- complex128: fused (tuned k) and per-gate
+    # -- complex128: fused (tuned) and per-gate; then the error of each complex64
+    #    result against the complex128 GPU run of the same circuit from |0..0>
     if not args.no_c128:
         s128 = Q.qs_state_alloc(n, Q.QS_C128, stream)
-        best128 = tune(Q, n, Q.QS_C128, gates, s128,
-                       [(k, m, L) for k in (1, 2, 3) for (m, L) in ((11, 4), (12, 4))]) if args.tune == "auto" else None
-        k128 = best128[1] if best128 else (2, 11, 4)
-        p128 = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(fuse_k=k128[0], tile_qubits=k128[1],
-                                                                  low_qubits=k128[2]))
+        if args.tune == "auto":
+            b128, t128 = tune(Q, n, Q.QS_C128, gates, s128,
+                              [dict(mode=F, fuse_k=k, tile_qubits=m, low_qubits=L) for k in (1, 2, 3)
+                               for (m, L) in ((11, 3), (12, 4))])
+            kw128 = b128[1]
+        else:
+            kw128 = dict(mode=F, fuse_k=2, tile_qubits=11, low_qubits=3)
+        p128 = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(**kw128))
         i128 = Q.qs_plan_info_get(p128)
-        Q.qs_state_set_basis(s128, 0)
         f128_ms, _, f128k, _ = time_steps(Q, torch, p128, s128, 1, 1, per_launch=True)
-        Q.qs_plan_free(p128)
         sb128 = 2 * (1 << n) * 16
-        extra["c128_fused"] = {"ms": f128_ms, "fuse_k": k128[0], "tile_qubits": k128[1], "low_qubits": k128[2],
-                               "passes": i128["passes"], "flops_per_amp": i128["flops_per_amp"],
-                               "pass_gbps": i128["passes"] * sb128 / (f128k[0] * 1e-3) / 1e9}
+        extra["c128_fused"] = dict(kw128, ms=f128_ms, passes=i128["passes"], flops_per_amp=i128["flops_per_amp"],
+                                   pass_gbps=i128["passes"] * sb128 / (f128k["ms"] * 1e-3) / 1e9,
+                                   bound="fp64 alu (GB300 FP64 ~1.2 TFLOP/s measured)")
+        Q.qs_state_set_basis(s128, 0)
+        Q.qs_plan_execute(p128, s128)
+        Q.qs_plan_free(p128)
+        prec = {}
+        Q.qs_state_set_basis(state, 0)
+        Q.qs_plan_execute(plan, state)
+        prec["c64_" + mode_name(Q, kw)] = dict(zip(("max_abs", "l2"), Q.qs_state_diff(state, s128)))
         if not args.no_per_gate:
+            pplan = Q.qs_plan_create(n, Q.QS_C64, gates, None)
+            Q.qs_state_set_basis(state, 0)
+            Q.qs_plan_execute(pplan, state)
+            Q.qs_plan_free(pplan)
+            prec["c64_per_gate"] = dict(zip(("max_abs", "l2"), Q.qs_state_diff(state, s128)))
             pp = Q.qs_plan_create(n, Q.QS_C128, gates, None)
-            pg128, _, pk128, _ = time_steps(Q, torch, pp, s128, 1, 0, per_launch=True)
+            pg128, _, _, _ = time_steps(Q, torch, pp, s128, 1, 0, per_launch=False)
             Q.qs_plan_free(pp)
             extra["c128_per_gate"] = {"ms": pg128}
             extra["speedup_fused_vs_per_gate_c128"] = pg128 / f128_ms
+        extra["precision_vs_c128_gpu_run"] = prec
         Q.qs_state_free(s128)
+    Q.qs_plan_free(plan)
+    Q.qs_state_free(state)
+    torch.cuda.empty_cache()
 
     cpu = None
     if rank == 0 and not args.no_cpu:
@@ -337,36 +380,38 @@ def main():
         cpu = {"value": ms_cpu, "unit": "ms", "cores": 1, "kind": "oracle", "sample": desc}
 
     total_ms = ms_step / world       # job time per circuit with `world` replicas
-    prof = os.path.join(ROOT, "profiles", "traffic_k_tile.json")
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
     traffic = None
     if os.path.exists(prof):
         try:
-            tp = json.load(open(prof))
+            tp = json.load(open(prof)).get("k_tc_block" if tc_dom else "k_tile", {})
             if tp.get("kernel_hash") == kernel_hash():
-                traffic = tp.get("bytes_per_launch_scaled_n30")
+                traffic = tp.get("bytes_per_launch_n30")
         except (ValueError, OSError):
             traffic = None
+    cfg = {"workload": workload_desc(args, len(gates)) + f", complex64, {mode_name(Q, kw)} plan",
+           "n": n, "state": "complex64, 8 GiB", "gates": len(gates), "passes": info["passes"],
+           "blocks": info["blocks"], "l2": "inputs larger than L2 (8 GiB state vs 129 MB); no flush",
+           "parallelism": f"replicas x{world}"}
+    cfg.update({k: v for k, v in kw.items() if k != "mode"})
+    cfg["mode"] = mode_name(Q, kw)
     line = {
         "metric": METRIC, "value": total_ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": workload_desc(args, len(gates)) + ", complex64, fused (DAG contraction + tile passes)",
-                   "n": n, "state": "complex64, 8 GiB", "gates": len(gates), "fuse_k": kml[0],
-                   "tile_qubits": kml[1], "low_qubits": kml[2], "passes": info["passes"],
-                   "blocks": info["blocks"], "l2": "inputs larger than L2 (8 GiB state vs 129 MB); no flush",
-                   "parallelism": f"replicas x{world}"},
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic,
-                     "kernel": "k_tile (tile pass)", "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
-                     "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": kern_ms},
+                     "frac": achieved / hbm_peak, "traffic": traffic, "kernel": kname,
+                     "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
+                     "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": kms},
+        "kernel_time": kern_share,
         "effective_gbps": eff_gbps, "per_gate_equivalent_gbps": pg_equiv_gbps,
-        "fused_device_ms_per_circuit": circuit_ms,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": (1 << n) * 8, "d2h_bytes_per_step": (1 << n) * 8,
                 "norm_after": e2e_norm},
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
         "norm_drift": (max(abs(x - 1) for x in norms) if norms else None),
+        "tuning_trials_c64": trials,
     }
     line.update(extra)
     if rank == 0:
@@ -379,7 +424,7 @@ def main():
 def kernel_hash() -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels_tile.cu", "cplx.cuh", "qs_internal.h"):
+    for f in ("kernels_tile.cu", "kernels_tc.cu", "cplx.cuh", "qs_internal.h"):
         h.update(open(os.path.join(ROOT, "paper_2509_04955_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 

@@ -84,7 +84,9 @@ typedef struct {
 typedef enum {
   QS_MODE_PER_GATE = 0,  /* one kernel launch per gate (Algorithms 1-4) */
   QS_MODE_FUSED = 1,     /* DAG contraction into k-qubit blocks + tile passes */
-  QS_MODE_TENSOR = 2     /* as FUSED, wide blocks on tensor cores (QS_C64 only) */
+  QS_MODE_TENSOR = 2     /* as FUSED with 6-qubit contraction; blocks carrying many gates are
+                            applied as 64x64 complex GEMMs on tensor cores (tcgen05, FP32
+                            accumulation); QS_C64 only, n >= 13 (smaller states plan as FUSED) */
 } qs_mode;
 
 /* Planner and kernel options. Zero-initialised fields take the defaults. */
@@ -99,7 +101,7 @@ typedef struct {
   int32_t fuse_parametric; /* 1 = parametric gates may join dense blocks (block matrices are then
                               rebuilt on the host at every execution; not usable batched).
                               0 = they stay separate ops resolved from theta on the device. */
-  int32_t reserved[8];
+  int32_t reserved[8];   /* reserved[0]: tensor mode, least gates per tensor-core block (0 = 10) */
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */
@@ -179,6 +181,10 @@ qs_status qs_expval_pauli_sum(qs_state_t s, const qs_pauli_term* terms, size_t n
 /* out <- sum_j c_j P_j psi (out must not alias s). */
 qs_status qs_apply_pauli_sum(qs_state_t s, const qs_pauli_term* terms, size_t nterms, qs_state_t out);
 
+/* max_i |a_i - b_i| and ||a - b||_2 in FP64 for two states of equal n (dtypes
+ * may differ: the error of a complex64 result against a complex128 run). */
+qs_status qs_state_diff(qs_state_t a, qs_state_t b, double* max_abs, double* l2);
+
 /* <a|b> in FP64: (*re, *im). */
 qs_status qs_inner(qs_state_t a, qs_state_t b, double* re, double* im);
 
@@ -232,7 +238,8 @@ qs_status qs_expval_pauli_sum_noalloc(const void* dev_state, int n, qs_dtype dty
  * the Eq. 7 ordering). In per-gate mode every op is a gate op and every pass
  * one op. */
 qs_status qs_plan_op_count(qs_plan_t p, int64_t* nops, int64_t* npasses);
-/* type: 0 = gate op, 1 = dense block, 2 = diagonal block. qubits: capacity 6.
+/* type: 0 = gate op, 1 = dense block, 2 = diagonal block, 3 = dense 6-qubit block applied on
+ * tensor cores (its own pass over 13-qubit tiles). qubits: capacity 6.
  * gate_index: the input gate of a gate op (-1 for blocks). mat (optional,
  * capacity 2 * 4096 doubles): the block's entries as (re, im) pairs. */
 qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits, int32_t* nq,
@@ -248,6 +255,10 @@ qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t
  * bracketed launches (ms) and their number, and starts a new interval. */
 qs_status qs_plan_set_timing(qs_plan_t p, int enable);
 qs_status qs_plan_timing_read(qs_plan_t p, double* total_ms, int64_t* launches);
+/* Same, split by launch kind: [0] = tile passes or per-gate kernels, [1] =
+ * tensor-core passes (arrays of 2, may be NULL). */
+qs_status qs_plan_timing_read_kinds(qs_plan_t p, double* total_ms, int64_t* launches, double* kind_ms,
+                                    int64_t* kind_launches);
 
 /* ---------------- diagnostics ---------------- */
 

@@ -86,6 +86,7 @@ _SIGS = {
     "qs_expval_pauli_sum": (C.c_int, [_VP, C.POINTER(QsPauliTerm), C.c_size_t, _DP]),
     "qs_apply_pauli_sum": (C.c_int, [_VP, C.POINTER(QsPauliTerm), C.c_size_t, _VP]),
     "qs_inner": (C.c_int, [_VP, _VP, _DP, _DP]),
+    "qs_state_diff": (C.c_int, [_VP, _VP, _DP, _DP]),
     "qs_adjoint_grad": (C.c_int, [_VP, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t, C.POINTER(QsPauliTerm),
                                   C.c_size_t, _DP, _DP]),
     "qs_plan_execute_batched": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, _DP, C.c_size_t, C.POINTER(QsPauliTerm),
@@ -95,6 +96,7 @@ _SIGS = {
     "qs_plan_pass_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I64P, _I64P]),
     "qs_plan_set_timing": (C.c_int, [_VP, C.c_int]),
     "qs_plan_timing_read": (C.c_int, [_VP, _DP, _I64P]),
+    "qs_plan_timing_read_kinds": (C.c_int, [_VP, _DP, _I64P, _DP, _I64P]),
     "qs_expval_pauli_sum_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.POINTER(QsPauliTerm), C.c_size_t,
                                               _DP]),
     "qs_last_error": (C.c_char_p, []),
@@ -171,10 +173,11 @@ def _dptr(a):
 
 
 def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0,
-              fuse_parametric=0):
+              fuse_parametric=0, tc_min_gates=0):
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
     o.paper_mode, o.tc_precision, o.fuse_parametric = paper_mode, tc_precision, fuse_parametric
+    o.reserved[0] = tc_min_gates
     return o
 
 
@@ -257,6 +260,12 @@ def qs_inner(a: int, b: int) -> complex:
     re, im = C.c_double(), C.c_double()
     _check(lib().qs_inner(a, b, C.byref(re), C.byref(im)))
     return complex(re.value, im.value)
+
+
+def qs_state_diff(a: int, b: int) -> tuple[float, float]:
+    m, l2 = C.c_double(), C.c_double()
+    _check(lib().qs_state_diff(a, b, C.byref(m), C.byref(l2)))
+    return m.value, l2.value
 
 
 def qs_expval_pauli_sum(state: int, coeff, xmask, zmask) -> float:
@@ -350,6 +359,14 @@ def qs_plan_timing_read(plan: int) -> tuple[float, int]:
     ms, n = C.c_double(), C.c_int64()
     _check(lib().qs_plan_timing_read(plan, C.byref(ms), C.byref(n)))
     return ms.value, n.value
+
+
+def qs_plan_timing_read_kinds(plan: int) -> dict:
+    ms, n = C.c_double(), C.c_int64()
+    km, kn = (C.c_double * 2)(), (C.c_int64 * 2)()
+    _check(lib().qs_plan_timing_read_kinds(plan, C.byref(ms), C.byref(n), km, kn))
+    return {"ms": ms.value, "launches": n.value, "tile_ms": km[0], "tile_launches": kn[0], "tc_ms": km[1],
+            "tc_launches": kn[1]}
 
 
 def qs_launch_count() -> int:

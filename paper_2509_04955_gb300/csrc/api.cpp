@@ -118,13 +118,23 @@ struct qs_plan_s {
   std::vector<DevOp> dops;
   std::vector<OpRec> exec_ops;     // dops in global terms (introspection)
   std::vector<std::vector<int>> pass_tiles;
+  std::vector<std::pair<int, int>> pass_ops;   // op range of each step in exec_ops
   std::vector<int64_t> block_off;  // complex offset in the block table, -1 if gate-wise
+  // tensor-core passes and the execution order of all passes
+  struct Step {
+    int kind;   // 0 = tile pass (pdesc[idx]), 1 = tensor-core pass (tcdesc[idx])
+    int idx;
+  };
+  std::vector<Step> steps;
+  std::vector<TcPassDesc> tcdesc;
+  std::vector<uint16_t> h_wimg;    // per TC pass: bf16 hi image then lo image (64 KiB)
+  int tc_prec = 3;
   int64_t btab_elems = 0;
   bool btab_parametric = false;
   std::vector<double2> h_btab;
   // device
   bool uploaded = false;
-  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab;
+  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err;
   int gtab_rows = 0;
   qs_plan_info info{};
   // batched graph cache; captured and replayed on a plan-owned stream
@@ -135,6 +145,7 @@ struct qs_plan_s {
   // measurement: events bracketing each launch of qs_plan_execute
   bool timing = false;
   std::vector<cudaEvent_t> events;
+  std::vector<int> event_kind;     // launch kind of each bracketed launch (0 tile/per-gate, 1 tensor core)
   size_t events_used = 0;
   ~qs_plan_s() {
     if (graph) cudaGraphExecDestroy(graph);
@@ -212,6 +223,12 @@ void upload(qs_plan_s& p) {
   p.d_btab.ensure(sizeof(double2) * std::max<int64_t>(1, p.btab_elems));
   if (p.btab_elems)
     CK(cudaMemcpy(p.d_btab.p, p.h_btab.data(), sizeof(double2) * p.btab_elems, cudaMemcpyHostToDevice));
+  if (!p.tcdesc.empty()) {
+    p.d_wimg.ensure(sizeof(uint16_t) * p.h_wimg.size());
+    CK(cudaMemcpy(p.d_wimg.p, p.h_wimg.data(), sizeof(uint16_t) * p.h_wimg.size(), cudaMemcpyHostToDevice));
+  }
+  p.d_err.ensure(sizeof(int) * 4);
+  CK(cudaMemset(p.d_err.p, 0, sizeof(int) * 4));
   p.uploaded = true;
 }
 
@@ -222,13 +239,22 @@ void check_state(const qs_state_s* s) { require(s != nullptr && s->d != nullptr,
 void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed = false) {
   const size_t G = std::max<size_t>(1, p.gates.size());
   const double2* gtab = p.d_gtab.as<double2>() + (size_t)row * 16 * G;
-  const size_t nl = p.mode == QS_MODE_PER_GATE ? p.gates.size() : p.pdesc.size();
+  const size_t nl = p.mode == QS_MODE_PER_GATE ? p.gates.size() : p.steps.size();
   for (size_t i = 0; i < nl; ++i) {
-    if (timed) CK(cudaEventRecord(p.next_event(), st));
-    if (p.mode == QS_MODE_PER_GATE)
+    if (timed) {
+      CK(cudaEventRecord(p.next_event(), st));
+      p.event_kind.push_back(p.mode != QS_MODE_PER_GATE && p.steps[i].kind == 1 ? 1 : 0);
+    }
+    if (p.mode == QS_MODE_PER_GATE) {
       CK(launch_gate(psi, p.n, p.dt, p.dgates[i], gtab + i * 16, false, st));
-    else
-      CK(launch_tile_pass(psi, p.n, p.dt, p.pdesc[i], p.d_ops.as<DevOp>(), gtab, p.d_btab.as<double2>(), 0, st));
+    } else if (p.steps[i].kind == 0) {
+      CK(launch_tile_pass(psi, p.n, p.dt, p.pdesc[p.steps[i].idx], p.d_ops.as<DevOp>(), gtab,
+                          p.d_btab.as<double2>(), 0, st));
+    } else {
+      const int t = p.steps[i].idx;
+      CK(launch_tc_pass(psi, p.n, p.tcdesc[t], p.d_wimg.as<uint16_t>() + (size_t)t * 32768, p.tc_prec,
+                        p.d_err.as<int>(), st));
+    }
     if (timed) CK(cudaEventRecord(p.next_event(), st));
   }
 }
@@ -254,9 +280,156 @@ void execute(qs_plan_s& p, qs_state_s& s, const double* theta, size_t ntheta) {
     CK(cudaStreamSynchronize(s.st));   // h_btab is rewritten by the next call
   }
   issue_circuit(p, s.d, 0, s.st, p.timing);
+  if (!p.tcdesc.empty()) {
+    int err = 0;
+    CK(cudaMemcpyAsync(&err, p.d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s.st));
+    CK(cudaStreamSynchronize(s.st));
+    if (err) throw Error(QS_ERR_TIMEOUT, "tensor-core pass: an MMA completion wait timed out");
+  }
 }
 
 // ---------------------------------------------------------------- plans
+
+// bf16 with round-to-nearest-even (host side, for the tensor-core W image).
+uint16_t bf16_rne(float f) {
+  uint32_t u;
+  std::memcpy(&u, &f, 4);
+  if ((u & 0x7fffffffu) > 0x7f800000u) return (uint16_t)((u >> 16) | 0x40);
+  u += 0x7fffu + ((u >> 16) & 1u);
+  return (uint16_t)(u >> 16);
+}
+
+float bf16_to_float(uint16_t h) {
+  const uint32_t u = (uint32_t)h << 16;
+  float f;
+  std::memcpy(&f, &u, 4);
+  return f;
+}
+
+// Byte offset of bf16 element (row, k) in a K-major 128-byte-swizzled operand
+// of 128 rows (two 16 KiB atoms of 64 elements along K).
+size_t sw128_offset_host(uint32_t row, uint32_t k) {
+  const uint32_t atom = k >> 6, kk = k & 63;
+  const uint32_t chunk = (kk >> 3) ^ (row & 7);
+  return (size_t)atom * 16384 + row * 128 + chunk * 16 + (kk & 7) * 2;
+}
+
+// W image of a 64x64 complex block U: element (n, k) of the N x K operand is
+// W[k][n] of the real embedding (see the tensor-core kernel), split into bf16
+// hi (first 32 KiB) and lo (second 32 KiB) parts.
+void build_w_image(const double2* U, uint16_t* img) {
+  for (uint32_t nn = 0; nn < 128; ++nn)
+    for (uint32_t k = 0; k < 128; ++k) {
+      const uint32_t co = nn >> 1, b = nn & 1, ci = k >> 1, a = k & 1;
+      const double ur = U[co * 64 + ci].x, ui = U[co * 64 + ci].y;
+      const double w = (a == 0) ? (b == 0 ? ur : ui) : (b == 0 ? -ui : ur);
+      const uint16_t hi = bf16_rne((float)w);
+      const uint16_t lo = bf16_rne((float)(w - (double)bf16_to_float(hi)));
+      const size_t off = sw128_offset_host(nn, k) / 2;
+      img[off] = hi;
+      img[16384 + off] = lo;
+    }
+}
+
+void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::vector<PassRec>& passes,
+                      const std::vector<int>& order, int low_qubits, qs_plan_info& in) {
+  const qs_dtype dt = P.dt;
+  for (const PassRec& pr : passes) {
+    PassDesc pd;
+    std::memset(&pd, 0, sizeof(pd));
+    pd.m = (int)pr.tile.size();
+    pd.L = std::min(low_qubits, pd.m);
+    pd.nhigh = pd.m - pd.L;
+    for (int j = 0; j < pd.nhigh; ++j) pd.high[j] = pr.tile[pd.L + j];
+    for (int j = 0; j < pd.L; ++j) require(pr.tile[j] == j, "internal: tile lacks low qubits");
+    auto local = [&](int q) {
+      return (int)(std::lower_bound(pr.tile.begin(), pr.tile.end(), q) - pr.tile.begin());
+    };
+    pd.op_begin = (int)P.dops.size();
+    pd.kmax = 0;
+    for (int oi = pr.op_begin; oi < pr.op_end; ++oi) {
+      const OpRec& r = ops[order[oi]];
+      DevOp d;
+      std::memset(&d, 0, sizeof(d));
+      d.type = r.type;
+      if (r.type == OP_GATE) {
+        const HGate& g = P.gates[r.gate];
+        d.form = g.form;
+        d.t0 = local(g.t[0]);
+        d.t1 = g.nt == 2 ? local(g.t[1]) : -1;
+        std::vector<int> ins;
+        if (g.form != FORM_DIAG1)
+          for (int k = 0; k < g.nt; ++k) ins.push_back(local(g.t[k]));
+        for (int k = 0; k < g.nc; ++k) {
+          ins.push_back(local(g.c[k]));
+          d.cmask |= 1u << local(g.c[k]);
+        }
+        std::sort(ins.begin(), ins.end());
+        d.nins = (int)ins.size();
+        for (int k = 0; k < d.nins; ++k) d.ins[k] = ins[k];
+        d.mat = r.gate;
+        pd.mbuf_elems = std::max(pd.mbuf_elems, 16);
+        in.flops_per_amp += 2 * gate_fma_per_amp(g);
+        in.max_block_qubits = std::max(in.max_block_qubits, __builtin_popcountll(g.qmask));
+      } else {
+        const Block& blk = P.blocks[r.block];
+        d.k = (int)blk.qubits.size();
+        for (int j = 0; j < d.k; ++j) d.ins[j] = local(blk.qubits[j]);
+        d.mat = (int32_t)P.block_off[r.block];
+        if (r.type == OP_DENSE) {
+          pd.kmax = std::max(pd.kmax, d.k);
+          pd.mbuf_elems = std::max(pd.mbuf_elems, 1 << (2 * d.k));
+          in.flops_per_amp += 8.0 * (1 << d.k);
+        } else {
+          pd.mbuf_elems = std::max(pd.mbuf_elems, 1 << d.k);
+          in.flops_per_amp += 8.0;
+        }
+        in.max_block_qubits = std::max(in.max_block_qubits, d.k);
+      }
+      P.dops.push_back(d);
+      P.exec_ops.push_back(r);
+    }
+    pd.op_end = (int)P.dops.size();
+    require(tile_smem_bytes(pd.m, pd.nhigh, pd.mbuf_elems, dt) <= 227 * 1024,
+            "tile does not fit in shared memory: lower tile_qubits");
+    P.steps.push_back({0, (int)P.pdesc.size()});
+    P.pdesc.push_back(pd);
+    P.pass_tiles.push_back(pr.tile);
+    P.pass_ops.push_back({pd.op_begin, pd.op_end});
+  }
+}
+
+void emit_tc_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
+  const Block& blk = P.blocks[r.block];
+  TcPassDesc t;
+  std::memset(&t, 0, sizeof(t));
+  for (int j = 0; j < 6; ++j) t.col[j] = blk.qubits[j];
+  int nr = 0;
+  for (int q = 0; q < P.n && nr < 7; ++q)
+    if (std::find(blk.qubits.begin(), blk.qubits.end(), q) == blk.qubits.end()) t.row[nr++] = q;
+  require(nr == 7, "internal: tensor-core tile needs 7 row qubits");
+  std::vector<int> tile(t.row, t.row + 7);
+  tile.insert(tile.end(), t.col, t.col + 6);
+  std::sort(tile.begin(), tile.end());
+  for (int j = 0; j < 13; ++j) t.tile[j] = tile[j];
+  const size_t w0 = P.h_wimg.size();
+  P.h_wimg.resize(w0 + 32768);
+  build_w_image(P.h_btab.data() + P.block_off[r.block], P.h_wimg.data() + w0);
+  DevOp d;
+  std::memset(&d, 0, sizeof(d));
+  d.type = OP_TC;
+  d.k = 6;
+  const int b = (int)P.dops.size();
+  P.dops.push_back(d);
+  P.exec_ops.push_back(r);
+  P.steps.push_back({1, (int)P.tcdesc.size()});
+  P.tcdesc.push_back(t);
+  P.pass_tiles.push_back(tile);
+  P.pass_ops.push_back({b, b + 1});
+  in.flops_per_amp += 8.0 * 64;
+  in.max_block_qubits = std::max(in.max_block_qubits, 6);
+}
+
 
 void default_opts(qs_plan_opts& o, qs_dtype dt, int n) {
   if (o.fuse_k <= 0) o.fuse_k = dt == QS_C64 ? 4 : 3;
@@ -276,7 +449,6 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   if (opts) p->opts = *opts;
   p->mode = p->opts.mode;
   require(p->mode == QS_MODE_PER_GATE || p->mode == QS_MODE_FUSED || p->mode == QS_MODE_TENSOR, "bad mode");
-  if (p->mode == QS_MODE_TENSOR) throw Error(QS_ERR_UNSUPPORTED, "tensor-core mode not built");
   resolve_gates(n, gates, ng, p->gates);
   for (size_t g = 0; g < p->gates.size(); ++g) {
     p->dgates.push_back(make_dev_gate(p->gates[g]));
@@ -301,9 +473,17 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   qs_plan_opts& o = p->opts;
   require(o.tile_qubits <= 14 && o.tile_qubits >= 0, "tile_qubits out of range (1..14)");
   require(o.low_qubits >= 0 && o.fuse_k >= 0, "negative option");
+  bool tensor = p->mode == QS_MODE_TENSOR;
+  if (tensor) {
+    if (dt != QS_C64) throw Error(QS_ERR_UNSUPPORTED, "tensor-core mode needs complex64 states");
+    require(o.tc_precision == 0 || o.tc_precision == 1 || o.tc_precision == 3, "tc_precision must be 1 or 3");
+    p->tc_prec = o.tc_precision == 0 ? 3 : o.tc_precision;
+    if (n < 13) tensor = false;   // a tensor-core tile needs 13 qubits; smaller states use CUDA-core blocks
+  }
+  const int user_k = o.fuse_k;
+  if (tensor) o.fuse_k = 0;
   default_opts(o, dt, n);
-  const int kmax_dt = 5;
-  require(o.fuse_k >= 1 && o.fuse_k <= kmax_dt, "fuse_k out of range for this dtype");
+  require(o.fuse_k >= 1 && o.fuse_k <= 5, "fuse_k out of range (1..5 on CUDA cores)");
   require(o.tile_qubits >= 1 && o.tile_qubits <= 14, "tile_qubits out of range");
   require(o.low_qubits >= 1, "low_qubits must be >= 1");
   require(o.tile_qubits - o.low_qubits >= std::min(o.fuse_k, n - o.low_qubits) || o.tile_qubits == n,
@@ -313,13 +493,32 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   require(o.low_qubits + std::max(widest, o.fuse_k) <= 14 || o.tile_qubits == n,
           "low_qubits + widest gate must fit a 14-qubit tile");
   PlanOptions po;
-  po.k = o.paper_mode ? 2 : o.fuse_k;
+  po.k = o.paper_mode ? 2 : (tensor ? (user_k == 5 ? 5 : 6) : o.fuse_k);
   po.paper = o.paper_mode != 0;
   po.amp_bytes = (int)amp_bytes(dt);
-  po.fp_weight = dt == QS_C64 ? 1.0 : 16.0;
+  // GB300: FP32 FMA 128 lanes/clk/SM, FP64 about 1/59 of that (measured),
+  // shared memory 128 B/clk/SM -> one byte costs one FP32 FMA slot.
+  po.fp_weight = dt == QS_C64 ? 1.0 : 59.0;
+  po.smem_weight = 1.0;
   po.fuse_parametric = o.fuse_parametric != 0;
   p->blocks = contract(n, p->gates, po);
-  // ops
+  if (tensor) {
+    // A block worth a tensor-core pass (one HBM sweep) carries many gates;
+    // it is padded to 6 qubits with the highest qubits it does not touch.
+    const int tc_min_gates = o.reserved[0] > 0 ? o.reserved[0] : 10;
+    for (Block& blk : p->blocks) {
+      if (!blk.parametric && (int)blk.gates.size() >= tc_min_gates) {
+        blk.rep = OP_TC;
+        blk.diag = false;
+        for (int q = n - 1; q >= 0 && blk.qubits.size() < 6; --q)
+          if (std::find(blk.qubits.begin(), blk.qubits.end(), q) == blk.qubits.end()) blk.qubits.push_back(q);
+        std::sort(blk.qubits.begin(), blk.qubits.end());
+      } else if (blk.qubits.size() > 5 || (blk.rep == OP_DENSE && (int)blk.qubits.size() > o.fuse_k)) {
+        blk.rep = OP_GATE;
+      }
+    }
+  }
+  // ops in emission order
   std::vector<OpRec> ops;
   p->block_off.assign(p->blocks.size(), -1);
   for (size_t b = 0; b < p->blocks.size(); ++b) {
@@ -338,73 +537,28 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   }
   p->h_btab.assign(std::max<int64_t>(1, p->btab_elems), make_double2(0, 0));
   compute_blocks(*p, nullptr, false);
-  std::vector<int> order;
-  std::vector<PassRec> passes = schedule_passes(n, ops, o.tile_qubits, o.low_qubits, order);
   in.blocks = 0;
   for (const Block& b : p->blocks) in.blocks += b.rep == OP_GATE ? (int64_t)b.gates.size() : 1;
   in.max_block_qubits = 0;
-  for (const PassRec& pr : passes) {
-    PassDesc pd;
-    std::memset(&pd, 0, sizeof(pd));
-    pd.m = (int)pr.tile.size();
-    pd.L = std::min(o.low_qubits, pd.m);
-    pd.nhigh = pd.m - pd.L;
-    for (int j = 0; j < pd.nhigh; ++j) pd.high[j] = pr.tile[pd.L + j];
-    for (int j = 0; j < pd.L; ++j) require(pr.tile[j] == j, "internal: tile lacks low qubits");
-    auto local = [&](int q) {
-      return (int)(std::lower_bound(pr.tile.begin(), pr.tile.end(), q) - pr.tile.begin());
-    };
-    pd.op_begin = (int)p->dops.size();
-    pd.kmax = 0;
-    for (int oi = pr.op_begin; oi < pr.op_end; ++oi) {
-      const OpRec& r = ops[order[oi]];
-      DevOp d;
-      std::memset(&d, 0, sizeof(d));
-      d.type = r.type;
-      if (r.type == OP_GATE) {
-        const HGate& g = p->gates[r.gate];
-        d.form = g.form;
-        d.t0 = local(g.t[0]);
-        d.t1 = g.nt == 2 ? local(g.t[1]) : -1;
-        std::vector<int> ins;
-        if (g.form != FORM_DIAG1)
-          for (int k = 0; k < g.nt; ++k) ins.push_back(local(g.t[k]));
-        for (int k = 0; k < g.nc; ++k) {
-          ins.push_back(local(g.c[k]));
-          d.cmask |= 1u << local(g.c[k]);
-        }
-        std::sort(ins.begin(), ins.end());
-        d.nins = (int)ins.size();
-        for (int k = 0; k < d.nins; ++k) d.ins[k] = ins[k];
-        d.mat = r.gate;
-        pd.mbuf_elems = std::max(pd.mbuf_elems, 16);
-        in.flops_per_amp += 2 * gate_fma_per_amp(g);
-        in.max_block_qubits = std::max(in.max_block_qubits, __builtin_popcountll(g.qmask));
-      } else {
-        const Block& blk = p->blocks[r.block];
-        d.k = (int)blk.qubits.size();
-        for (int j = 0; j < d.k; ++j) d.ins[j] = local(blk.qubits[j]);
-        d.mat = (int32_t)p->block_off[r.block];
-        if (r.type == OP_DENSE) {
-          pd.kmax = std::max(pd.kmax, d.k);
-          pd.mbuf_elems = std::max(pd.mbuf_elems, 1 << (2 * d.k));
-          in.flops_per_amp += 8.0 * (1 << d.k);
-        } else {
-          pd.mbuf_elems = std::max(pd.mbuf_elems, 1 << d.k);
-          in.flops_per_amp += 8.0;
-        }
-        in.max_block_qubits = std::max(in.max_block_qubits, d.k);
-      }
-      p->dops.push_back(d);
-      p->exec_ops.push_back(r);
+  // Runs of CUDA-core ops between tensor-core ops become tile passes.
+  std::vector<OpRec> seg;
+  auto flush = [&]() {
+    if (seg.empty()) return;
+    std::vector<int> order;
+    std::vector<PassRec> passes = schedule_passes(n, seg, o.tile_qubits, o.low_qubits, order);
+    emit_tile_passes(*p, seg, passes, order, o.low_qubits, in);
+    seg.clear();
+  };
+  for (const OpRec& r : ops) {
+    if (r.type != OP_TC) {
+      seg.push_back(r);
+      continue;
     }
-    pd.op_end = (int)p->dops.size();
-    require(tile_smem_bytes(pd.m, pd.nhigh, pd.mbuf_elems, dt) <= 227 * 1024,
-            "tile does not fit in shared memory: lower tile_qubits");
-    p->pdesc.push_back(pd);
-    p->pass_tiles.push_back(pr.tile);
+    flush();
+    emit_tc_pass(*p, r, in);
   }
-  in.passes = (int64_t)p->pdesc.size();
+  flush();
+  in.passes = (int64_t)p->steps.size();
   in.launches = in.passes;
   in.sweeps = (double)in.passes;
   in.tile_qubits = o.tile_qubits;
@@ -542,22 +696,35 @@ qs_status qs_plan_set_timing(qs_plan_t p, int enable) {
     require(p != nullptr, "plan is NULL");
     p->timing = enable != 0;
     p->events_used = 0;
+    p->event_kind.clear();
   });
 }
 
 qs_status qs_plan_timing_read(qs_plan_t p, double* total_ms, int64_t* launches) {
+  return qs_plan_timing_read_kinds(p, total_ms, launches, nullptr, nullptr);
+}
+
+qs_status qs_plan_timing_read_kinds(qs_plan_t p, double* total_ms, int64_t* launches, double* kind_ms,
+                                    int64_t* kind_launches) {
   return guard([&] {
     require(p != nullptr, "plan is NULL");
-    double t = 0;
+    double t = 0, km[2] = {0, 0};
+    int64_t kn[2] = {0, 0};
     for (size_t i = 0; i + 1 < p->events_used; i += 2) {
       CK(cudaEventSynchronize(p->events[i + 1]));
       float ms = 0;
       CK(cudaEventElapsedTime(&ms, p->events[i], p->events[i + 1]));
       t += ms;
+      const int k = p->event_kind[i / 2];
+      km[k] += ms;
+      kn[k] += 1;
     }
     if (total_ms) *total_ms = t;
     if (launches) *launches = (int64_t)(p->events_used / 2);
+    if (kind_ms) { kind_ms[0] = km[0]; kind_ms[1] = km[1]; }
+    if (kind_launches) { kind_launches[0] = kn[0]; kind_launches[1] = kn[1]; }
     p->events_used = 0;
+    p->event_kind.clear();
   });
 }
 
@@ -566,7 +733,7 @@ qs_status qs_plan_op_count(qs_plan_t p, int64_t* nops, int64_t* npasses) {
     require(p != nullptr, "plan is NULL");
     const bool pg = p->mode == QS_MODE_PER_GATE;
     if (nops) *nops = pg ? (int64_t)p->gates.size() : (int64_t)p->exec_ops.size();
-    if (npasses) *npasses = pg ? (int64_t)p->gates.size() : (int64_t)p->pdesc.size();
+    if (npasses) *npasses = pg ? (int64_t)p->gates.size() : (int64_t)p->steps.size();
   });
 }
 
@@ -610,13 +777,13 @@ qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t
       if (op_end) *op_end = i + 1;
       return;
     }
-    require(i >= 0 && i < (int64_t)p->pdesc.size(), "pass index out of range");
+    require(i >= 0 && i < (int64_t)p->steps.size(), "pass index out of range");
     const auto& t = p->pass_tiles[i];
     if (tile_qubits)
       for (size_t j = 0; j < t.size(); ++j) tile_qubits[j] = t[j];
     if (m) *m = (int32_t)t.size();
-    if (op_begin) *op_begin = p->pdesc[i].op_begin;
-    if (op_end) *op_end = p->pdesc[i].op_end;
+    if (op_begin) *op_begin = p->pass_ops[i].first;
+    if (op_end) *op_end = p->pass_ops[i].second;
   });
 }
 int64_t qs_launch_count(void) { return qs::launch_count(); }
@@ -787,6 +954,28 @@ qs_status qs_inner(qs_state_t a, qs_state_t b, double* re, double* im) {
     CK(cudaStreamSynchronize(a->st));
     if (re) *re = v[0];
     if (im) *im = v[1];
+  });
+}
+
+qs_status qs_state_diff(qs_state_t a, qs_state_t b, double* max_abs, double* l2) {
+  return guard([&] {
+    check_state(a);
+    check_state(b);
+    require(a->n == b->n, "states differ in n");
+    const int RB = reduce_blocks();
+    a->scratch.ensure(partial_bytes(2));
+    CK(cudaStreamSynchronize(b->st));
+    CK(launch_diff(a->d, a->dt, b->d, b->dt, a->n, a->scratch.as<double>(), a->st));
+    std::vector<double> h(2 * (size_t)RB);
+    CK(cudaMemcpyAsync(h.data(), a->scratch.p, sizeof(double) * h.size(), cudaMemcpyDeviceToHost, a->st));
+    CK(cudaStreamSynchronize(a->st));
+    double m = 0, s2 = 0;
+    for (int i = 0; i < RB; ++i) {
+      m = std::max(m, h[i]);
+      s2 += h[RB + i];
+    }
+    if (max_abs) *max_abs = m;
+    if (l2) *l2 = std::sqrt(s2);
   });
 }
 

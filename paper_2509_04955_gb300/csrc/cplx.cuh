@@ -24,6 +24,23 @@ template <typename C> __device__ __forceinline__ C cfma(C a, C b, C acc) {
 }
 template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
 
+// p*a + q*b with real p, q
+template <typename R> __device__ __forceinline__ typename V2<R>::T rmix(R p, typename V2<R>::T a, R q,
+                                                                       typename V2<R>::T b) {
+  typename V2<R>::T r;
+  r.x = fma(q, b.x, p * a.x);
+  r.y = fma(q, b.y, p * a.y);
+  return r;
+}
+// p*a + (i q)*b with real p, q
+template <typename R> __device__ __forceinline__ typename V2<R>::T ixmix(R p, typename V2<R>::T a, R q,
+                                                                        typename V2<R>::T b) {
+  typename V2<R>::T r;
+  r.x = fma(-q, b.y, p * a.x);
+  r.y = fma(q, b.x, p * a.y);
+  return r;
+}
+
 template <typename R> __device__ __forceinline__ typename V2<R>::T from_d(double2 d) {
   return mk<R>((R)d.x, (R)d.y);
 }

@@ -138,12 +138,22 @@ __global__ void __launch_bounds__(256) k_gate1(typename V2<R>::T* __restrict__ p
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += stride) {
     const uint64_t base = insert_zero_bits_u<4>(p, g.ins, g.nins) | g.cmask;
-    if (FORM == FORM_DENSE1 || FORM == FORM_ANTI1) {
+    if (FORM == FORM_DENSE1 || FORM == FORM_ANTI1 || FORM == FORM_REAL1 || FORM == FORM_RXLIKE1 ||
+        FORM == FORM_X1) {
       const C a0 = psi[base], a1 = psi[base | tb];
       C r0, r1;
       if (FORM == FORM_DENSE1) {
         r0 = cfma(u.m01, a1, cmul(u.m00, a0));
         r1 = cfma(u.m11, a1, cmul(u.m10, a0));
+      } else if (FORM == FORM_REAL1) {
+        r0 = rmix<R>(u.m00.x, a0, u.m01.x, a1);
+        r1 = rmix<R>(u.m10.x, a0, u.m11.x, a1);
+      } else if (FORM == FORM_RXLIKE1) {
+        r0 = ixmix<R>(u.m00.x, a0, u.m01.y, a1);
+        r1 = ixmix<R>(u.m11.x, a1, u.m10.y, a0);
+      } else if (FORM == FORM_X1) {
+        r0 = a1;
+        r1 = a0;
       } else {
         r0 = cmul(u.m01, a1);
         r1 = cmul(u.m10, a0);
@@ -213,6 +223,9 @@ static cudaError_t launch_gate_t(void* psi_, int n, const DevGate& g, const doub
   switch (g.form) {
     case FORM_DENSE1: k_gate1<R, FORM_DENSE1><<<gr, th, 0, st>>>(psi, count, g, mat, adjoint); break;
     case FORM_ANTI1: k_gate1<R, FORM_ANTI1><<<gr, th, 0, st>>>(psi, count, g, mat, adjoint); break;
+    case FORM_REAL1: k_gate1<R, FORM_REAL1><<<gr, th, 0, st>>>(psi, count, g, mat, adjoint); break;
+    case FORM_RXLIKE1: k_gate1<R, FORM_RXLIKE1><<<gr, th, 0, st>>>(psi, count, g, mat, adjoint); break;
+    case FORM_X1: k_gate1<R, FORM_X1><<<gr, th, 0, st>>>(psi, count, g, mat, adjoint); break;
     case FORM_PHASE1: k_gate1<R, FORM_PHASE1><<<gr, th, 0, st>>>(psi, count, g, mat, adjoint); break;
     case FORM_DIAG1: k_gate1<R, FORM_DIAG1><<<gr, th, 0, st>>>(psi, count, g, mat, adjoint); break;
     case FORM_SWAP2: k_swap2<R><<<gr, th, 0, st>>>(psi, count, g); break;

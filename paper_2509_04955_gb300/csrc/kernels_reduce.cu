@@ -125,6 +125,50 @@ cudaError_t launch_inner(const void* a, const void* b, int n, qs_dtype dt, doubl
   return launch_sum_rows(partials, 2, kRedBlocks, out2, st);
 }
 
+// ---------------------------------------------------------------- state difference
+
+// Per-CTA max |a_i - b_i| and sum |a_i - b_i|^2 (FP64) of two states of any dtypes.
+template <typename RA, typename RB>
+__global__ void __launch_bounds__(kRedThreads) k_diff(const typename V2<RA>::T* __restrict__ a,
+                                                       const typename V2<RB>::T* __restrict__ b, uint64_t dim,
+                                                       double* __restrict__ partials) {
+  double mx = 0, sq = 0;
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
+    const double dx = (double)a[i].x - (double)b[i].x, dy = (double)a[i].y - (double)b[i].y;
+    const double d2 = dx * dx + dy * dy;
+    sq += d2;
+    mx = fmax(mx, d2);
+  }
+  const double s = block_sum(sq);
+  __shared__ double wm[kRedThreads / 32];
+  for (int o = 16; o > 0; o >>= 1) mx = fmax(mx, __shfl_down_sync(0xffffffffu, mx, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = mx;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double m = 0;
+    for (int k = 0; k < kRedThreads / 32; ++k) m = fmax(m, wm[k]);
+    partials[blockIdx.x] = sqrt(m);
+    partials[kRedBlocks + blockIdx.x] = s;
+  }
+}
+
+cudaError_t launch_diff(const void* a, qs_dtype da, const void* b, qs_dtype db, int n, double* partials,
+                        cudaStream_t st) {
+  const uint64_t dim = 1ull << n;
+  if (da == QS_C64 && db == QS_C64)
+    k_diff<float, float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)a, (const float2*)b, dim, partials);
+  else if (da == QS_C64)
+    k_diff<float, double><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)a, (const double2*)b, dim, partials);
+  else if (db == QS_C64)
+    k_diff<double, float><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)a, (const float2*)b, dim, partials);
+  else
+    k_diff<double, double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)a, (const double2*)b, dim, partials);
+  note_launch();
+  return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------- Pauli expval
 
 constexpr int kMaxZ = 8;

@@ -80,29 +80,73 @@ __device__ __forceinline__ void apply_gate_op(typename V2<R>::T* tile, int m, co
     return;
   }
   const C m00 = from_d<R>(mat[0]), m01 = from_d<R>(mat[1]), m10 = from_d<R>(mat[2]), m11 = from_d<R>(mat[3]);
-  for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
-    const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
-    if (op.form == FORM_DENSE1) {
-      const C a0 = tile[b], a1 = tile[b | ta];
-      tile[b] = cfma(m01, a1, cmul(m00, a0));
-      tile[b | ta] = cfma(m11, a1, cmul(m10, a0));
-    } else if (op.form == FORM_ANTI1) {
-      const C a0 = tile[b], a1 = tile[b | ta];
-      tile[b] = cmul(m01, a1);
-      tile[b | ta] = cmul(m10, a0);
-    } else if (op.form == FORM_PHASE1) {
-      tile[b | ta] = cmul(m11, tile[b | ta]);
-    } else {  // DIAG1
-      tile[b] = cmul((b & ta) ? m11 : m00, tile[b]);
-    }
+  switch (op.form) {
+    case FORM_DENSE1:
+      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+        const C a0 = tile[b], a1 = tile[b | ta];
+        tile[b] = cfma(m01, a1, cmul(m00, a0));
+        tile[b | ta] = cfma(m11, a1, cmul(m10, a0));
+      }
+      break;
+    case FORM_REAL1:
+      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+        const C a0 = tile[b], a1 = tile[b | ta];
+        tile[b] = rmix<R>(m00.x, a0, m01.x, a1);
+        tile[b | ta] = rmix<R>(m10.x, a0, m11.x, a1);
+      }
+      break;
+    case FORM_RXLIKE1:
+      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+        const C a0 = tile[b], a1 = tile[b | ta];
+        tile[b] = ixmix<R>(m00.x, a0, m01.y, a1);
+        tile[b | ta] = ixmix<R>(m11.x, a1, m10.y, a0);
+      }
+      break;
+    case FORM_X1:
+      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+        const C a0 = tile[b], a1 = tile[b | ta];
+        tile[b] = a1;
+        tile[b | ta] = a0;
+      }
+      break;
+    case FORM_ANTI1:
+      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+        const C a0 = tile[b], a1 = tile[b | ta];
+        tile[b] = cmul(m01, a1);
+        tile[b | ta] = cmul(m10, a0);
+      }
+      break;
+    case FORM_PHASE1:
+      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+        tile[b | ta] = cmul(m11, tile[b | ta]);
+      }
+      break;
+    default:  // DIAG1
+      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
+        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
+        tile[b] = cmul((b & ta) ? m11 : m00, tile[b]);
+      }
   }
 }
+
+// Groups per thread of a dense op: each staged matrix entry is loaded once
+// and used for G groups (register budget about 64 values for the inputs).
+template <typename R, int K> struct DenseG {
+  static constexpr int v = sizeof(R) == 4 ? (K <= 3 ? 4 : K == 4 ? 2 : 1) : (K <= 2 ? 2 : 1);
+};
 
 template <typename R, int K>
 __device__ __forceinline__ void apply_dense_op(typename V2<R>::T* tile, int m, const DevOp& op,
                                                const double2* __restrict__ btab, typename V2<R>::T* mbuf) {
   using C = typename V2<R>::T;
   constexpr int D = 1 << K;
+  constexpr int G = DenseG<R, K>::v;
   for (int i = threadIdx.x; i < D * D; i += kTileThreads) mbuf[i] = from_d<R>(btab[op.mat + i]);
   __syncthreads();
   uint32_t off[D];
@@ -114,17 +158,33 @@ __device__ __forceinline__ void apply_dense_op(typename V2<R>::T* tile, int m, c
     off[j] = o;
   }
   const uint32_t groups = 1u << (m - K);
-  for (uint32_t g = threadIdx.x; g < groups; g += kTileThreads) {
-    const uint32_t i0 = ins0k<K>(g, op.ins);
-    C v[D];
+  for (uint32_t g0 = threadIdx.x; g0 < groups; g0 += kTileThreads * G) {
+    uint32_t i0[G];
+    C v[G][D];
 #pragma unroll
-    for (int j = 0; j < D; ++j) v[j] = tile[i0 | off[j]];
+    for (int i = 0; i < G; ++i) {
+      const uint32_t gi = g0 + i * kTileThreads;
+      i0[i] = ins0k<K>(gi < groups ? gi : 0, op.ins);
+#pragma unroll
+      for (int j = 0; j < D; ++j) v[i][j] = tile[i0[i] | off[j]];
+    }
 #pragma unroll
     for (int r = 0; r < D; ++r) {
-      C acc = cmul(mbuf[r * D], v[0]);
+      C acc[G];
+      {
+        const C mm = mbuf[r * D];
 #pragma unroll
-      for (int j = 1; j < D; ++j) acc = cfma(mbuf[r * D + j], v[j], acc);
-      tile[i0 | off[r]] = acc;
+        for (int i = 0; i < G; ++i) acc[i] = cmul(mm, v[i][0]);
+      }
+#pragma unroll
+      for (int j = 1; j < D; ++j) {
+        const C mm = mbuf[r * D + j];
+#pragma unroll
+        for (int i = 0; i < G; ++i) acc[i] = cfma(mm, v[i][j], acc[i]);
+      }
+#pragma unroll
+      for (int i = 0; i < G; ++i)
+        if (g0 + i * kTileThreads < groups) tile[i0[i] | off[r]] = acc[i];
     }
   }
 }

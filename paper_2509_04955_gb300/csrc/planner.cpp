@@ -113,7 +113,10 @@ void resolve_gates(int n, const qs_gate* gs, size_t ng, std::vector<HGate>& out)
     if (g.nt == 2) g.form = q.kind == QS_GATE_SWAP ? FORM_SWAP2 : FORM_DENSE2;
     else if (kind_is_phase(q.kind)) g.form = FORM_PHASE1;
     else if (kind_is_diag(q.kind)) g.form = FORM_DIAG1;
-    else if (q.kind == QS_GATE_X || q.kind == QS_GATE_Y) g.form = FORM_ANTI1;
+    else if (q.kind == QS_GATE_X) g.form = FORM_X1;
+    else if (q.kind == QS_GATE_Y) g.form = FORM_ANTI1;
+    else if (q.kind == QS_GATE_H || q.kind == QS_GATE_RY) g.form = FORM_REAL1;
+    else if (q.kind == QS_GATE_RX) g.form = FORM_RXLIKE1;
     else g.form = FORM_DENSE1;
     out.push_back(g);
   }
@@ -155,6 +158,9 @@ double gate_fma_per_amp(const HGate& g) {
   switch (g.form) {
     case FORM_DENSE1: return 8 * ctl;
     case FORM_ANTI1: return 4 * ctl;
+    case FORM_REAL1: return 4 * ctl;
+    case FORM_RXLIKE1: return 4 * ctl;
+    case FORM_X1: return 0;
     case FORM_DIAG1: return 4 * ctl;
     case FORM_PHASE1: return 2 * ctl;
     case FORM_SWAP2: return 0;
@@ -246,11 +252,17 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
     } else if (o.paper) {
       blk.rep = blk.diag ? OP_DIAG : OP_DENSE;
     } else {
+      // Cost of an op per amplitude in FP32-FMA-instruction units: arithmetic
+      // (FP64 weighted by fp_weight) and the shared-memory round trip of the
+      // amplitudes it touches (smem_weight per byte) run on different pipes,
+      // so an op costs the larger of the two.
+      auto op_cost = [&](double fma, double frac) {
+        return std::max(o.fp_weight * fma, o.smem_weight * 2.0 * o.amp_bytes * frac);
+      };
       double sep = 0;
-      for (int g : blk.gates)
-        sep += o.fp_weight * gate_fma_per_amp(gates[g]) + 2.0 * o.amp_bytes * gate_sweep_fraction(gates[g]);
-      const double dense = o.fp_weight * 4.0 * (1 << k) + 2.0 * o.amp_bytes;
-      const double dg = o.fp_weight * 4.0 + 2.0 * o.amp_bytes;
+      for (int g : blk.gates) sep += op_cost(gate_fma_per_amp(gates[g]), gate_sweep_fraction(gates[g]));
+      const double dense = op_cost(4.0 * (1 << k), 1.0);
+      const double dg = op_cost(4.0, 1.0);
       if (blk.diag) blk.rep = dg < sep ? OP_DIAG : OP_GATE;
       else blk.rep = (!o.cost_model || dense < sep) ? OP_DENSE : OP_GATE;
     }

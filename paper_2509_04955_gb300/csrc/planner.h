@@ -44,14 +44,15 @@ struct Block {
   std::vector<int> qubits;   // ascending; local bit j <-> qubits[j]
   bool diag = false;         // every member gate is diagonal
   bool parametric = false;   // some member depends on theta
-  int rep = OP_GATE;         // OP_GATE (members applied one by one), OP_DENSE or OP_DIAG
+  int rep = OP_GATE;         // OP_GATE (members applied one by one), OP_DENSE, OP_DIAG or OP_TC
 };
 
 struct PlanOptions {
   int k = 1;                 // block width
   bool paper = false;        // only the merges of Section 3.4
   bool cost_model = true;    // keep gates separate when the dense block costs more
-  double fp_weight = 1.0;    // cost of one FMA relative to one byte of shared-memory traffic
+  double fp_weight = 1.0;    // cost of one FMA of the state's precision, in FP32-FMA units
+  double smem_weight = 1.0;  // cost of one byte of shared-memory traffic, in FP32-FMA units
   int amp_bytes = 8;
   bool fuse_parametric = false;   // parametric gates may join multi-gate blocks
 };

@@ -29,7 +29,10 @@ enum GateForm : int32_t {
   FORM_DIAG1 = 2,    // 2x2 diagonal
   FORM_PHASE1 = 3,   // 2x2 diagonal with m00 == 1 for every angle (Z, S, T, P)
   FORM_SWAP2 = 4,    // two-target SWAP
-  FORM_DENSE2 = 5    // two-target 4x4 general
+  FORM_DENSE2 = 5,   // two-target 4x4 general
+  FORM_REAL1 = 6,    // 2x2 with real entries (H, RY): 4 FMA per amplitude
+  FORM_RXLIKE1 = 7,  // real diagonal, imaginary off-diagonal (RX): 4 FMA per amplitude
+  FORM_X1 = 8        // X: the pair swaps, no arithmetic
 };
 
 struct DevGate {
@@ -47,8 +50,19 @@ struct DevGate {
 enum OpType : int32_t {
   OP_GATE = 0,    // one original gate: form + tile-local positions, matrix from the gate table
   OP_DENSE = 1,   // dense k-qubit block, matrix (2^k x 2^k) in the block table
-  OP_DIAG = 2     // diagonal k-qubit block, 2^k phases in the block table
+  OP_DIAG = 2,    // diagonal k-qubit block, 2^k phases in the block table
+  OP_TC = 3       // dense 6-qubit block applied on tensor cores (its own pass, complex64)
 };
+
+// Tensor-core pass over tiles of 128 rows x 64 columns (13 qubits).
+struct TcPassDesc {
+  int32_t row[7];          // global qubits of the row bits, ascending (bit b of the row index)
+  int32_t col[6];          // block qubits, ascending (bit j of the column index = local bit j)
+  int32_t tile[13];        // row and column qubits together, ascending
+};
+cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int* err,
+                           cudaStream_t st);
+size_t tc_smem_bytes();
 
 struct DevOp {
   int32_t type;
@@ -134,6 +148,9 @@ cudaError_t launch_apply_pauli(const void* psi, void* out, int n, qs_dtype dt,
 cudaError_t launch_adjoint_step(void* phi, void* lam, int n, qs_dtype dt, const DevGate& g,
                                 const double2* mat, const double2* dmat, double* partials_row,
                                 cudaStream_t st);
+// partials[0..RB) = per-CTA max |a - b|, partials[RB..2RB) = per-CTA sum |a - b|^2
+cudaError_t launch_diff(const void* a, qs_dtype da, const void* b, qs_dtype db, int n, double* partials,
+                        cudaStream_t st);
 cudaError_t launch_sum_rows(const double* partials, int rows, int cols, double* out,
                             cudaStream_t st);
 

@@ -289,6 +289,57 @@ def test_batched_graph_matches_sequential_and_oracle(dtname):
             Q.qs_plan_free(plan)
 
 
+@pytest.mark.parametrize("n,depth,ent", [(13, 6, "cnot"), (15, 8, "cz"), (17, 5, "cnot")])
+def test_tensor_core_mode_split_bf16_matches_oracle(n, depth, ent):
+    """6-qubit blocks on tensor cores (bf16x3 products, FP32 accumulation)
+    interleaved with CUDA-core tile passes, complex64 bar 2e-5."""
+    gates = W.random_layered(n, depth, seed=n, entangler=ent)
+    psi0 = W.random_state(n, 2)
+    want = ref(n, gates, psi0=psi0.astype(np.complex64).astype(complex))
+    for tmin in (6, 10):
+        opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_precision=3)
+        opts.reserved[0] = tmin
+        plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
+        try:
+            assert any(op["type"] == 3 for op in Q.qs_plan_ops(plan))
+            h = Q.qs_state_alloc(n, Q.QS_C64)
+            try:
+                Q.qs_state_copy_from_host(h, psi0.astype(np.complex64))
+                Q.qs_plan_execute(plan, h)
+                out = np.empty(1 << n, dtype=np.complex64)
+                Q.qs_state_copy_to_host(h, out)
+            finally:
+                Q.qs_state_free(h)
+        finally:
+            Q.qs_plan_free(plan)
+        assert np.abs(out - want).max() <= 2e-5
+
+
+def test_tensor_core_plain_bf16_error_bound():
+    """Plain bf16 products (one MMA per k-step): error within the bf16
+    rounding bound, about 2^-8 of the largest amplitude per block."""
+    n = 14
+    gates = W.random_layered(n, 6, seed=5)
+    want = ref(n, gates)
+    opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_precision=1)
+    out = run(n, Q.QS_C64, gates, opts=opts)
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
+    ntc = sum(1 for op in Q.qs_plan_ops(plan) if op["type"] == 3)
+    Q.qs_plan_free(plan)
+    assert ntc >= 1
+    assert np.abs(out - want).max() <= ntc * 2.0 ** -8 * np.abs(want).max()
+
+
+def test_tensor_core_config2_shape_n20_depth40_cz():
+    """The layer structure of the 32-qubit tensor-core workload (CZ
+    entanglers, depth 40) at 20 qubits, where the oracle finishes in seconds."""
+    n = 20
+    gates = W.random_layered(n, 40, seed=0, entangler="cz")
+    want = ref(n, gates)
+    out = run(n, Q.QS_C64, gates, opts=Q.make_opts(mode=Q.QS_MODE_TENSOR))
+    assert np.abs(out - want).max() <= 2e-5
+
+
 def test_invalid_sizes_give_errors_not_faults():
     h = Q.qs_state_alloc(4, Q.QS_C64)
     try:
@@ -307,6 +358,22 @@ def test_invalid_sizes_give_errors_not_faults():
     with pytest.raises(Q.QsError) as e:
         Q.qs_state_alloc(40, Q.QS_C128)     # 16 TiB
     assert e.value.status == Q.QS_ERR_OOM
+
+
+def test_state_diff_mixed_precision():
+    n = 12
+    psi = W.random_state(n, 9)
+    a = Q.qs_state_alloc(n, Q.QS_C64)
+    b = Q.qs_state_alloc(n, Q.QS_C128)
+    try:
+        Q.qs_state_copy_from_host(a, psi.astype(np.complex64))
+        Q.qs_state_copy_from_host(b, psi)
+        m, l2 = Q.qs_state_diff(a, b)
+        d = psi.astype(np.complex64).astype(complex) - psi
+        assert abs(m - np.abs(d).max()) < 1e-15 and abs(l2 - np.linalg.norm(d)) < 1e-12
+    finally:
+        Q.qs_state_free(a)
+        Q.qs_state_free(b)
 
 
 def test_launch_counter_moves():

@@ -91,7 +91,7 @@ def plan_unitary(n, gates, plan, theta=None):
     for op in ops:
         if op["type"] == 0:
             G = O.unitary(n, [gates[op["gate"]]], theta)
-        elif op["type"] == 1:
+        elif op["type"] in (1, 3):
             G = np.stack([apply_block(c, n, op["qubits"], op["matrix"]) for c in np.eye(1 << n, dtype=complex)],
                          axis=1)
         else:
@@ -172,3 +172,36 @@ def test_per_gate_sweep_accounting():
     assert abs(info["per_gate_sweeps"] - (1 + 0.5 + 0.25 + 1 + 0.5 + 0.5)) < 1e-12
     assert info["launches"] == len(gates)
     Q.qs_plan_free(plan)
+
+
+def test_tensor_mode_plan_matches_oracle_on_a_state():
+    """Tensor-core plans (6-qubit blocks padded to 6, tile passes in between)
+    reproduce the circuit: ops applied with numpy to a random state equal the
+    oracle's gate-by-gate result."""
+    n = 14
+    gates = W.random_layered(n, 8, seed=3)
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR))
+    try:
+        ops = Q.qs_plan_ops(plan)
+        assert any(op["type"] == 3 for op in ops)
+        psi = W.random_state(n, 1)
+        cur = psi.copy()
+        for op in ops:
+            if op["type"] == 0:
+                cur = O.apply_circuit(cur, n, [gates[op["gate"]]])
+            elif op["type"] == 2:
+                cur = apply_block(cur, n, op["qubits"], np.diag(op["matrix"]))
+            else:
+                if op["type"] == 3:
+                    assert len(op["qubits"]) == 6
+                cur = apply_block(cur, n, op["qubits"], op["matrix"])
+        assert np.abs(cur - O.apply_circuit(psi, n, gates)).max() < 1e-12
+        for ps in Q.qs_plan_passes(plan):
+            b, e = ps["ops"]
+            if any(op["type"] == 3 for op in ops[b:e]):
+                assert e - b == 1 and len(ps["tile"]) == 13
+    finally:
+        Q.qs_plan_free(plan)
+    with pytest.raises(Q.QsError) as e:
+        Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR))
+    assert e.value.status == Q.QS_ERR_UNSUPPORTED
