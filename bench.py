@@ -260,8 +260,7 @@ def main():
         cands = [dict(mode=F, fuse_k=k, tile_qubits=m, low_qubits=L) for k in (1, 2, 3) for (m, L) in
                  ((12, 4), (13, 4), (13, 5))]
         if n >= 13:
-            cands += [dict(mode=T, fuse_k=k, tile_qubits=m, low_qubits=L, tc_min_gates=g) for g in (6, 10, 16)
-                      for k in (2, 3) for (m, L) in ((13, 4), (12, 4))]
+            cands += [dict(mode=T, fuse_k=2, tile_qubits=13, low_qubits=4, tc_min_gates=g) for g in (2, 3, 4, 6, 8)]
         best, trials = tune(Q, n, Q.QS_C64, gates, state, cands)
         kw = best[1]
     else:
