@@ -526,9 +526,9 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
     uint64_t qm = 0;
     for (int q : blk.qubits) qm |= 1ull << q;
     if (blk.rep == OP_GATE) {
-      for (int g : blk.gates) ops.push_back(OpRec{OP_GATE, g, -1, p->gates[g].qmask});
+      for (int g : blk.gates) ops.push_back(OpRec{OP_GATE, g, -1, p->gates[g].qmask, p->gates[g].dmask});
     } else {
-      ops.push_back(OpRec{blk.rep, -1, (int)b, qm});
+      ops.push_back(OpRec{blk.rep, -1, (int)b, qm, blk.rep == OP_TC ? 0 : blk.dmask});
       p->block_off[b] = p->btab_elems;
       const int64_t D = 1ll << blk.qubits.size();
       p->btab_elems += blk.rep == OP_DIAG ? D : D * D;
@@ -744,7 +744,7 @@ qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits,
     const bool pg = p->mode == QS_MODE_PER_GATE;
     const int64_t N = pg ? (int64_t)p->gates.size() : (int64_t)p->exec_ops.size();
     require(i >= 0 && i < N, "op index out of range");
-    OpRec r = pg ? OpRec{OP_GATE, (int)i, -1, p->gates[i].qmask} : p->exec_ops[i];
+    OpRec r = pg ? OpRec{OP_GATE, (int)i, -1, p->gates[i].qmask, p->gates[i].dmask} : p->exec_ops[i];
     if (type) *type = r.type;
     int k = 0;
     for (int b = 0; b < 64; ++b)

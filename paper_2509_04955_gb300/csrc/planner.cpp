@@ -110,6 +110,7 @@ void resolve_gates(int n, const qs_gate* gs, size_t ng, std::vector<HGate>& out)
     g.param_index = g.parametric ? q.param_index : -1;
     for (int k = 0; k < 16; ++k) g.custom[k] = cd(q.mat[2 * k], q.mat[2 * k + 1]);
     if (!g.parametric) fixed_matrix(g.kind, q.param, g.custom, g.fixed);
+    g.dmask = g.cmask | (kind_is_diag(q.kind) ? g.qmask : 0);
     if (g.nt == 2) g.form = q.kind == QS_GATE_SWAP ? FORM_SWAP2 : FORM_DENSE2;
     else if (kind_is_phase(q.kind)) g.form = FORM_PHASE1;
     else if (kind_is_diag(q.kind)) g.form = FORM_DIAG1;
@@ -189,57 +190,120 @@ static bool paper_mergeable(const HGate& a, const HGate& b, uint64_t Q) {
   return false;
 }
 
-std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOptions& o) {
+// One greedy scan from `first`: absorbs later gates that commute with every
+// gate skipped so far and keep the block within kcap qubits (and within
+// `allowed`, when given). Returns the absorbed gates in program order.
+static std::vector<int> scan_block(const std::vector<HGate>& gates, const std::vector<char>& done, int first,
+                                   int kcap, uint64_t allowed, const PlanOptions& o, uint64_t all) {
   const int G = (int)gates.size();
-  // DAG: immediate predecessors = last earlier gate on each qubit of the gate.
-  std::vector<std::vector<int>> pred(G);
-  std::vector<int> last(n, -1);
-  for (int i = 0; i < G; ++i) {
-    for (int b : mask_bits(gates[i].qmask)) {
-      if (last[b] >= 0 && std::find(pred[i].begin(), pred[i].end(), last[b]) == pred[i].end())
-        pred[i].push_back(last[b]);
-      last[b] = i;
+  std::vector<int> members{first};
+  uint64_t Q = gates[first].qmask, blk_nd = 0, blk_d = 0;
+  const bool lone = !o.fuse_parametric && gates[first].parametric;   // stays a gate op
+  for (int h = first + 1; h < G && !lone; ++h) {
+    if (done[h]) continue;
+    const HGate& gh = gates[h];
+    const uint64_t qh = gh.qmask;
+    const bool movable = (qh & blk_nd) == 0 && (qh & blk_d & ~gh.dmask) == 0;
+    bool ok = movable && popc(Q | qh) <= kcap && (qh & ~allowed) == 0;
+    if (ok && !o.fuse_parametric && gh.parametric) ok = false;
+    if (ok && o.paper) ok = paper_mergeable(gates[members[0]], gh, Q);
+    if (ok) {
+      members.push_back(h);
+      Q |= qh;
+    } else {
+      blk_nd |= qh & ~gh.dmask;
+      blk_d |= qh & gh.dmask;
     }
+    if (blk_nd == all) break;
+    if (popc(Q) >= kcap && (Q & ~blk_nd) == 0) break;
   }
+  return members;
+}
+
+// Qubit set planned from the next unemitted gates: starting from the first
+// gate's qubits, repeatedly add the qubit that makes the most gates of the
+// window fit inside the set.
+static uint64_t plan_qubits(const std::vector<HGate>& gates, const std::vector<char>& done, int first, int kcap,
+                            int n) {
+  const int G = (int)gates.size();
+  std::vector<uint64_t> win;
+  for (int h = first; h < G && (int)win.size() < 4 * n; ++h)
+    if (!done[h]) win.push_back(gates[h].qmask);
+  uint64_t Q = gates[first].qmask;
+  while (popc(Q) < kcap) {
+    int best_q = -1, best = 0;
+    for (int q = 0; q < n; ++q) {
+      if (Q & (1ull << q)) continue;
+      const uint64_t Qq = Q | (1ull << q);
+      int cnt = 0;
+      for (uint64_t m : win)
+        if ((m & (1ull << q)) && (m & ~Qq) == 0) ++cnt;
+      if (cnt > best) { best = cnt; best_q = q; }
+    }
+    if (best_q < 0) break;
+    Q |= 1ull << best_q;
+  }
+  return Q;
+}
+
+// Qubit set grown by legal scans: at each step add the qubit whose admission
+// lets the scan absorb the most gates.
+static uint64_t grow_qubits(const std::vector<HGate>& gates, const std::vector<char>& done, int first, int kcap,
+                            int n, const PlanOptions& o, uint64_t all) {
+  uint64_t Q = gates[first].qmask;
+  // candidates: qubits of the next unemitted gates
+  uint64_t cand = 0;
+  int seen = 0;
+  for (int h = first; h < (int)gates.size() && seen < 4 * n; ++h)
+    if (!done[h]) { cand |= gates[h].qmask; ++seen; }
+  while (popc(Q) < kcap) {
+    int best_q = -1;
+    size_t best = 0;
+    for (int q = 0; q < n; ++q) {
+      if ((Q & (1ull << q)) || !(cand & (1ull << q))) continue;
+      const size_t c = scan_block(gates, done, first, kcap, Q | (1ull << q), o, all).size();
+      if (c > best) { best = c; best_q = q; }
+    }
+    if (best_q < 0) break;
+    Q |= 1ull << best_q;
+  }
+  return Q;
+}
+
+std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOptions& o) {
+  // A later gate may join the block (move ahead of the gates skipped so far)
+  // when it commutes with every skipped gate: on each shared qubit both are
+  // diagonal there (Z-basis diagonal gates and controls commute). This is the
+  // dependency structure of Section 3.4's DAG with commuting diagonal gates
+  // left unordered. Growth strategies tried per block: first-fit, a qubit set
+  // planned from the next gates, and (o.search) a set grown by legal scans;
+  // the one absorbing the most gates is kept.
+  const int G = (int)gates.size();
   std::vector<char> done(G, 0);   // emitted
-  std::vector<int> owner(G, -1);  // block currently being built
   std::vector<Block> blocks;
   int first = 0;
   const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
   while (first < G) {
     while (first < G && done[first]) ++first;
     if (first >= G) break;
-    const int bid = (int)blocks.size();
     Block blk;
-    blk.gates.push_back(first);
-    owner[first] = bid;
-    uint64_t Q = gates[first].qmask, blocked = 0;
-    const int kcap = o.paper ? 2 : std::max(o.k, popc(Q));
-    const bool lone = !o.fuse_parametric && gates[first].parametric;   // stays a gate op
-    for (int h = first + 1; h < G && !lone; ++h) {
-      if (done[h]) continue;
-      const uint64_t qh = gates[h].qmask;
-      if (qh & blocked) { blocked |= qh; }
-      else {
-        bool ok = popc(Q | qh) <= kcap;
-        if (ok && !o.fuse_parametric && gates[h].parametric) ok = false;
-        if (ok && o.paper) ok = paper_mergeable(gates[blk.gates[0]], gates[h], Q);
-        if (ok)
-          for (int p : pred[h])
-            if (!done[p] && owner[p] != bid) { ok = false; break; }
-        if (ok) {
-          blk.gates.push_back(h);
-          owner[h] = bid;
-          Q |= qh;
-        } else {
-          blocked |= qh;
-        }
+    const int kcap = o.paper ? 2 : std::max(o.k, popc(gates[first].qmask));
+    std::vector<int> a = scan_block(gates, done, first, kcap, all, o, all);
+    if (!o.paper && kcap > 2 && (o.fuse_parametric || !gates[first].parametric)) {
+      std::vector<int> b = scan_block(gates, done, first, kcap, plan_qubits(gates, done, first, kcap, n), o, all);
+      if (b.size() > a.size()) a.swap(b);
+      if (o.search) {
+        std::vector<int> c = scan_block(gates, done, first, kcap, grow_qubits(gates, done, first, kcap, n, o, all), o, all);
+        if (c.size() > a.size()) a.swap(c);
       }
-      if ((blocked | Q) == all && (Q & ~blocked) == 0) break;
-      if (popc(Q) >= kcap && (Q & ~blocked) == 0) break;
     }
+    blk.gates = a;
+    uint64_t Q = 0;
+    for (int g : blk.gates) Q |= gates[g].qmask;
     for (int g : blk.gates) done[g] = 1;
     blk.qubits = mask_bits(Q);
+    blk.dmask = Q;
+    for (int g : blk.gates) blk.dmask &= gates[g].dmask | ~gates[g].qmask;
     blk.diag = true;
     for (int g : blk.gates) {
       blk.diag = blk.diag && (gates[g].form == FORM_PHASE1 || gates[g].form == FORM_DIAG1);
@@ -328,18 +392,12 @@ void block_matrix(const Block& b, const std::vector<HGate>& gates, const double*
 
 std::vector<PassRec> schedule_passes(int n, const std::vector<OpRec>& ops, int m, int L,
                                      std::vector<int>& order_out) {
+  // Same greedy as the contraction, with width m and qubits 0..L-1 always in
+  // the tile; ops move ahead of skipped ops they commute with.
   const int N = (int)ops.size();
-  std::vector<std::vector<int>> pred(N);
-  std::vector<int> last(n, -1);
-  for (int i = 0; i < N; ++i)
-    for (int b : mask_bits(ops[i].qmask)) {
-      if (last[b] >= 0 && std::find(pred[i].begin(), pred[i].end(), last[b]) == pred[i].end())
-        pred[i].push_back(last[b]);
-      last[b] = i;
-    }
   const uint64_t low = L >= 64 ? ~0ull : ((1ull << L) - 1);
+  const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
   std::vector<char> done(N, 0);
-  std::vector<int> owner(N, -1);
   std::vector<PassRec> passes;
   std::vector<int> order;   // ops reordered pass by pass
   order.reserve(N);
@@ -347,23 +405,23 @@ std::vector<PassRec> schedule_passes(int n, const std::vector<OpRec>& ops, int m
   while (true) {
     while (first < N && done[first]) ++first;
     if (first >= N) break;
-    const int pid = (int)passes.size();
     PassRec pr;
     pr.op_begin = (int)order.size();
     std::vector<int> members{first};
-    owner[first] = pid;
-    uint64_t Q = low | ops[first].qmask, blocked = 0;
+    uint64_t Q = low | ops[first].qmask, blk_nd = 0, blk_d = 0;
     for (int h = first + 1; h < N; ++h) {
       if (done[h]) continue;
-      const uint64_t qh = ops[h].qmask;
-      if (qh & blocked) { blocked |= qh; continue; }
-      bool ok = popc(Q | qh) <= m;
-      if (ok)
-        for (int p : pred[h])
-          if (!done[p] && owner[p] != pid) { ok = false; break; }
-      if (ok) { members.push_back(h); owner[h] = pid; Q |= qh; }
-      else blocked |= qh;
-      if (popc(Q) >= m && (Q & ~blocked) == 0) break;
+      const uint64_t qh = ops[h].qmask, dh = ops[h].dmask;
+      const bool movable = (qh & blk_nd) == 0 && (qh & blk_d & ~dh) == 0;
+      if (movable && popc(Q | qh) <= m) {
+        members.push_back(h);
+        Q |= qh;
+      } else {
+        blk_nd |= qh & ~dh;
+        blk_d |= qh & dh;
+      }
+      if (blk_nd == all) break;
+      if (popc(Q) >= m && (Q & ~blk_nd) == 0) break;
     }
     for (int h : members) { done[h] = 1; order.push_back(h); }
     // pad the tile to m qubits with the lowest unused qubits

@@ -17,6 +17,7 @@ struct HGate {
   int nt = 1, t[2] = {-1, -1};
   int nc = 0, c[2] = {-1, -1};
   uint64_t cmask = 0, qmask = 0;
+  uint64_t dmask = 0;        // qubits on which the gate is diagonal (controls; all qubits of a diagonal gate)
   int param_index = -1;
   double param = 0, scale = 1;
   bool parametric = false;
@@ -42,6 +43,7 @@ double gate_fma_per_amp(const HGate& g);
 struct Block {
   std::vector<int> gates;    // program order
   std::vector<int> qubits;   // ascending; local bit j <-> qubits[j]
+  uint64_t dmask = 0;        // qubits on which every member gate is diagonal
   bool diag = false;         // every member gate is diagonal
   bool parametric = false;   // some member depends on theta
   int rep = OP_GATE;         // OP_GATE (members applied one by one), OP_DENSE, OP_DIAG or OP_TC
@@ -55,6 +57,7 @@ struct PlanOptions {
   double smem_weight = 1.0;  // cost of one byte of shared-memory traffic, in FP32-FMA units
   int amp_bytes = 8;
   bool fuse_parametric = false;   // parametric gates may join multi-gate blocks
+  bool search = true;              // also grow block qubit sets by legal scans (slower planning)
 };
 
 // DAGC-k greedy contraction. Returns blocks in emission order.
@@ -65,10 +68,11 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
 void block_matrix(const Block& b, const std::vector<HGate>& gates, const double* theta, std::vector<cd>& M);
 
 struct OpRec {               // one op of the fused program (global qubit positions)
-  int type;                  // OP_GATE / OP_DENSE / OP_DIAG
+  int type;                  // OP_GATE / OP_DENSE / OP_DIAG / OP_TC
   int gate = -1;             // OP_GATE: gate index
-  int block = -1;            // OP_DENSE / OP_DIAG: block index
+  int block = -1;            // block ops: block index
   uint64_t qmask = 0;
+  uint64_t dmask = 0;        // qubits on which the op is diagonal
 };
 
 struct PassRec {
