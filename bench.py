@@ -43,6 +43,9 @@ def parse():
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi sampler (profiler runs)")
+    ap.add_argument("--no-configs", action="store_true", help="skip the per-config side measurements")
+    ap.add_argument("--full-configs", action="store_true",
+                    help="also run the complex128 n=32 reference for the tensor-core config (64 GiB, ~1 min)")
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates]")
     return ap.parse_args()
 
@@ -373,6 +376,9 @@ def main():
     Q.qs_state_free(state)
     torch.cuda.empty_cache()
 
+    if not args.no_configs:
+        extra["configs"] = run_configs(Q, torch, np, args)
+
     cpu = None
     if rank == 0 and not args.no_cpu:
         ms_cpu, desc, _ = oracle_sample(args, gates)
@@ -418,6 +424,131 @@ def main():
     if dist:
         dist.barrier()
         dist.destroy_process_group()
+
+
+def device_ms(torch, fn, reps=1):
+    st = torch.cuda.current_stream()
+    t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    t0.record(st)
+    for _ in range(reps):
+        fn()
+    t1.record(st)
+    torch.cuda.synchronize()
+    return t0.elapsed_time(t1) / reps
+
+
+def run_configs(Q, torch, np, args):
+    """Side measurements, one per benchmark configuration (timings on the
+    device with CUDA events; errors against closed forms or a complex128 run)."""
+    from paper_2509_04955_gb300 import workloads as W
+    out = {}
+    st = torch.cuda.current_stream().cuda_stream
+    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
+
+    # config 1: QFT n=28 complex128 from a seeded basis state, per-gate vs contraction k=2..5
+    n = 28
+    g = W.qft(n)
+    x = W.random_basis_index(n, 28)
+    s = Q.qs_state_alloc(n, Q.QS_C128, st)
+    idx = np.unique(np.random.default_rng(0).integers(0, 1 << n, size=4096))
+    want = np.exp(2j * np.pi * ((x * idx) % (1 << n)) / (1 << n)) / np.sqrt(1 << n)
+    c1 = {"workload": "QFT n=28 complex128, seeded basis input", "gates": len(g)}
+    for name, opts in [("per_gate", None)] + [(f"fused_k{k}", Q.make_opts(mode=F, fuse_k=k)) for k in (2, 3, 4, 5)]:
+        plan = Q.qs_plan_create(n, Q.QS_C128, g, opts)
+        Q.qs_state_set_basis(s, x)
+        Q.qs_plan_execute(plan, s)
+        Q.qs_state_set_basis(s, x)
+        ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s))
+        full = np.empty(1 << n, dtype=np.complex128)
+        Q.qs_state_copy_to_host(s, full)
+        c1[name] = {"ms": ms, "passes": Q.qs_plan_info_get(plan)["passes"],
+                    "max_abs_err_vs_closed_form": float(np.abs(full[idx] - want).max())}
+        Q.qs_plan_free(plan)
+        del full
+    Q.qs_state_free(s)
+    out["qft_n28_c128"] = c1
+
+    # config 2: random n=32 depth 40 with CZ, complex64 on tensor cores (6-qubit blocks)
+    n = 32
+    g = W.random_layered(n, 40, seed=0, entangler="cz")
+    s = Q.qs_state_alloc(n, Q.QS_C64, st)
+    c2 = {"workload": "random layered n=32 depth 40, CZ entanglers, complex64 (32 GiB)", "gates": len(g)}
+    for name, opts in (("tensor_bf16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=3)),
+                       ("tensor_bf16", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=1)),
+                       ("fused_cuda_cores_k2", Q.make_opts(mode=F, fuse_k=2, tile_qubits=13, low_qubits=4))):
+        plan = Q.qs_plan_create(n, Q.QS_C64, g, opts)
+        Q.qs_state_set_basis(s, 0)
+        ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s))
+        c2[name] = {"ms": ms, "passes": Q.qs_plan_info_get(plan)["passes"], "norm": Q.qs_norm(s)}
+        if args.full_configs and name != "fused_cuda_cores_k2":
+            c2[name]["plan"] = plan
+        else:
+            Q.qs_plan_free(plan)
+    if args.full_configs:
+        ref = Q.qs_state_alloc(n, Q.QS_C128, st)
+        pr = Q.qs_plan_create(n, Q.QS_C128, g, Q.make_opts(mode=F, fuse_k=2, tile_qubits=12, low_qubits=4))
+        Q.qs_state_set_basis(ref, 0)
+        c2["c128_fused_ms"] = device_ms(torch, lambda: Q.qs_plan_execute(pr, ref))
+        Q.qs_plan_free(pr)
+        for name in ("tensor_bf16x3", "tensor_bf16"):
+            plan = c2[name].pop("plan")
+            Q.qs_state_set_basis(s, 0)
+            Q.qs_plan_execute(plan, s)
+            m, l2 = Q.qs_state_diff(s, ref)
+            c2[name].update(max_abs_err_vs_c128_gpu=m, l2_err_vs_c128_gpu=l2)
+            Q.qs_plan_free(plan)
+        Q.qs_state_free(ref)
+    Q.qs_state_free(s)
+    out["random_n32_cz_tensor"] = c2
+
+    # config 3: UCC-style n=20 complex64, 400 Pauli exponentials, B=64 theta ~ N(0, 0.1),
+    # one CUDA graph (device-resolved angles) + <H> for a 300-term Pauli sum per state
+    n, B = 20, 64
+    g, _ = W.ucc(n, 400, seed=0)
+    th = W.thetas_normal(400, 1, sigma=0.1, batch=B)
+    H = W.random_pauli_sum(n, 300, seed=3)
+    states = [Q.qs_state_alloc(n, Q.QS_C64, st) for _ in range(B)]
+    c3 = {"workload": "UCC-style n=20 complex64, 400 terms, B=64, 300-term <H>", "gates": len(g)}
+    for name, opts in (("fused_k1", Q.make_opts(mode=F, fuse_k=1)), ("fused_k3", Q.make_opts(mode=F, fuse_k=3)),
+                       ("tensor", Q.make_opts(mode=T, tc_min_gates=2))):
+        plan = Q.qs_plan_create(n, Q.QS_C64, g, opts)
+        def go():
+            for sv in states:
+                Q.qs_state_set_basis(sv, 0)
+            return Q.qs_plan_execute_batched(plan, states, th, H)
+        go()                                   # captures the graph
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ex = go()
+        wall = (time.perf_counter() - t0) * 1e3
+        c3[name] = {"ms_per_batch": wall, "circuits_per_s": B / (wall * 1e-3),
+                    "passes_per_circuit": Q.qs_plan_info_get(plan)["passes"], "expval_b0": float(ex[0])}
+        Q.qs_plan_free(plan)
+    for sv in states:
+        Q.qs_state_free(sv)
+    out["ucc_batched_n20"] = c3
+
+    # config 4: HEA n=24, 12 layers (576 parameters), adjoint gradient of a 150-term <H>
+    n = 24
+    g, p = W.hea(n, 12)
+    th = W.thetas_uniform(p, 4)
+    H = W.random_pauli_sum(n, 150, seed=4)
+    c4 = {"workload": "HEA n=24, 576 parameters, 150-term H, adjoint gradient"}
+    grads = {}
+    for dname, dt in (("c128", Q.QS_C128), ("c64", Q.QS_C64)):
+        s = Q.qs_state_alloc(n, dt, st)
+        Q.qs_adjoint_grad(s, g, th, *H)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, gr = Q.qs_adjoint_grad(s, g, th, *H)
+        wall = (time.perf_counter() - t0) * 1e3
+        grads[dname] = gr
+        c4[dname] = {"ms": wall, "expval": e}
+        Q.qs_state_free(s)
+    c4["max_abs_grad_diff_c64_vs_c128"] = float(np.abs(grads["c64"] - grads["c128"]).max())
+    out["hea_adjoint_n24"] = c4
+    return out
 
 
 def kernel_hash() -> str:

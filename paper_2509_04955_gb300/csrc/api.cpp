@@ -142,6 +142,8 @@ struct qs_plan_s {
   std::vector<void*> graph_key;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  DevBuf d_psis;                   // state pointers of the batch
+  int64_t graph_launches = 0;      // kernel launches in one replay of the graph
   // measurement: events bracketing each launch of qs_plan_execute
   bool timing = false;
   std::vector<cudaEvent_t> events;
@@ -256,6 +258,20 @@ void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed
                         p.d_err.as<int>(), st));
     }
     if (timed) CK(cudaEventRecord(p.next_event(), st));
+  }
+}
+
+// One launch per pass for all B states (fused / tensor plans): the kernels
+// take the device array of state pointers and gate-table rows 16 G apart.
+void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_t st) {
+  const size_t G = std::max<size_t>(1, p.gates.size());
+  for (const auto& stp : p.steps) {
+    if (stp.kind == 0)
+      CK(launch_tile_pass_batched(nullptr, d_psis, B, (int64_t)(16 * G), p.n, p.dt, p.pdesc[stp.idx],
+                                  p.d_ops.as<DevOp>(), p.d_gtab.as<double2>(), p.d_btab.as<double2>(), st));
+    else
+      CK(launch_tc_pass_batched(nullptr, d_psis, B, p.n, p.tcdesc[stp.idx],
+                                p.d_wimg.as<uint16_t>() + (size_t)stp.idx * 32768, p.tc_prec, p.d_err.as<int>(), st));
   }
 }
 
@@ -1099,19 +1115,29 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     PreparedTerms P;
     double* d_part = nullptr;
     double* d_out = nullptr;
+    const bool one_launch = p->mode != QS_MODE_PER_GATE;   // batched kernels: one launch per pass
+    int64_t Z = 0;
     if (terms && nterms) {
       P = prepare_terms(p->n, terms, nterms);
+      Z = (int64_t)P.zlist.size();
       qs_state_s& s0 = *states[0];
-      s0.scratch.ensure(partial_bytes(kZPerLaunch) + sizeof(double) * P.zlist.size() * B);
+      const int cols = one_launch ? expval_batched_blocks(B) : reduce_blocks();
+      const size_t part = sizeof(double) * (size_t)cols * kZPerLaunch * (one_launch ? B : 1);
+      s0.scratch.ensure(part + sizeof(double) * P.zlist.size() * B);
       s0.scratch2.ensure(sizeof(uint64_t) * P.zlist.size());
       d_part = s0.scratch.as<double>();
-      d_out = d_part + (size_t)reduce_blocks() * kZPerLaunch;
+      d_out = (double*)((char*)s0.scratch.p + part);
     }
-    std::vector<void*> key;
-    for (int b = 0; b < B; ++b) key.push_back(states[b]->d);
+    std::vector<void*> ptrs(B);
+    for (int b = 0; b < B; ++b) ptrs[b] = states[b]->d;
+    p->d_psis.ensure(sizeof(void*) * B);
+    CK(cudaMemcpy(p->d_psis.p, ptrs.data(), sizeof(void*) * B, cudaMemcpyHostToDevice));
+    void* const* d_psis = (void* const*)p->d_psis.p;
+    std::vector<void*> key = ptrs;
     key.push_back((void*)(uintptr_t)ntheta);
     key.push_back((void*)(uintptr_t)(terms ? nterms : 0));
     key.push_back(p->d_theta.p);
+    key.push_back(p->d_psis.p);
     key.push_back(states[0]->scratch.p);
     key.push_back(states[0]->scratch2.p);
     if (!p->pgates.empty())
@@ -1119,9 +1145,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     if (terms && nterms)
       CK(cudaMemcpyAsync(states[0]->scratch2.p, P.zlist.data(), sizeof(uint64_t) * P.zlist.size(),
                          cudaMemcpyHostToDevice, st));
-    // terms contents may change between calls; they are uploaded above, the
-    // graph only depends on their count and grouping, which is part of the key
-    // through zlist ordering being rebuilt identically for identical masks.
+    // the graph depends on the grouping of the terms (x masks, z order), part of the key
     if (terms && nterms) {
       for (size_t k = 0; k < P.zlist.size(); ++k) key.push_back((void*)(uintptr_t)P.zlist[k]);
       for (auto& L : P.launches) key.push_back((void*)(uintptr_t)P.groups[L.first].x);
@@ -1129,8 +1153,8 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     if (!p->graph || p->graph_key != key) {
       if (p->graph) { cudaGraphExecDestroy(p->graph); p->graph = nullptr; }
       cudaGraph_t g = nullptr;
+      const int64_t c0 = launch_count();
       CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-      suspend_launch_count(true);
       try {
         if (!p->pgates.empty()) {
           const size_t G = std::max<size_t>(1, p->gates.size());
@@ -1138,20 +1162,31 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
                             p->d_theta.as<double>(), (int64_t)ntheta, B, p->d_gtab.as<double2>(), (int64_t)16 * G,
                             st));
         }
-        for (int b = 0; b < B; ++b) {
-          issue_circuit(*p, states[b]->d, b, st);
+        if (one_launch) {
+          issue_circuit_batched(*p, d_psis, B, st);
           if (terms && nterms)
-            issue_expval(*states[b], P, states[0]->scratch2.as<uint64_t>(), d_part,
-                         d_out + (size_t)b * P.zlist.size(), st);
+            for (size_t l = 0; l < P.launches.size(); ++l) {
+              const auto& L = P.launches[l];
+              CK(launch_expval_x_batched((const void* const*)d_psis, B, p->n, p->dt, P.groups[L.first].x,
+                                         states[0]->scratch2.as<uint64_t>() + L.second, P.counts[l], d_part,
+                                         d_out + L.second, Z, st));
+            }
+        } else {
+          for (int b = 0; b < B; ++b) {
+            issue_circuit(*p, states[b]->d, b, st);
+            if (terms && nterms)
+              issue_expval(*states[b], P, states[0]->scratch2.as<uint64_t>(), d_part, d_out + (size_t)b * Z, st);
+          }
         }
       } catch (...) {
-        suspend_launch_count(false);
         cudaStreamEndCapture(st, &g);
         if (g) cudaGraphDestroy(g);
+        note_launch(-(launch_count() - c0));
         throw;
       }
-      suspend_launch_count(false);
       CK(cudaStreamEndCapture(st, &g));
+      p->graph_launches = launch_count() - c0;   // counted at capture, executed at each replay
+      note_launch(-p->graph_launches);
       cudaGraphExec_t ex = nullptr;
       cudaError_t e = cudaGraphInstantiate(&ex, g, 0);
       cudaGraphDestroy(g);
@@ -1160,8 +1195,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
       p->graph_key = key;
     }
     CK(cudaGraphLaunch(p->graph, st));
-    note_launch((p->pgates.empty() ? 0 : 1) +
-                (int64_t)(p->info.launches + (terms && nterms ? (int64_t)P.launches.size() * 2 : 0)) * B);
+    note_launch(p->graph_launches);
     std::vector<double> vals;
     if (terms && nterms) {
       vals.resize(P.zlist.size() * B);
@@ -1169,6 +1203,12 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     }
     CK(cudaEventRecord(p->ev_out, st));
     CK(cudaStreamWaitEvent(user_st, p->ev_out, 0));
+    if (!p->tcdesc.empty()) {
+      int err = 0;
+      CK(cudaMemcpyAsync(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      if (err) throw Error(QS_ERR_TIMEOUT, "tensor-core pass: an MMA completion wait timed out");
+    }
     if (terms && nterms) {
       CK(cudaStreamSynchronize(st));
       for (int b = 0; b < B; ++b) expvals[b] = combine_expval(P, terms, vals.data() + (size_t)b * P.zlist.size());

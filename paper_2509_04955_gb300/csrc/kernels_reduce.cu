@@ -180,9 +180,15 @@ constexpr int kMaxZ = 8;
 // for odd ny (the sign and the re/im choice are folded into coef/odd below).
 // x = 0: each index once, contribution s_i |psi_i|^2.
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::T* __restrict__ psi, int n,
+__global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::T* __restrict__ psi0,
+                                                           const void* const* __restrict__ psis, int n,
                                                            uint64_t x, const uint64_t* __restrict__ zm,
                                                            int nz, double* __restrict__ partials) {
+  // gridDim.y states (batched execution): state blockIdx.y writes its own
+  // partial rows; gridDim.x CTAs per state
+  const typename V2<R>::T* __restrict__ psi =
+      psis ? (const typename V2<R>::T*)psis[blockIdx.y] : psi0;
+  partials += (int64_t)blockIdx.y * nz * gridDim.x;
   __shared__ uint64_t z_s[kMaxZ];
   __shared__ int odd_s[kMaxZ];
   if (threadIdx.x < nz) {
@@ -220,21 +226,55 @@ __global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::
   }
   for (int k = 0; k < nz; ++k) {
     const double s = block_sum(acc[k].total());
-    if (threadIdx.x == 0) partials[(int64_t)k * kRedBlocks + blockIdx.x] = s;
+    if (threadIdx.x == 0) partials[(int64_t)k * gridDim.x + blockIdx.x] = s;
   }
+}
+
+// out[b * out_stride + k] = sum_c partials[(b * nz + k) * cols + c] (one CTA per row).
+__global__ void __launch_bounds__(kRedThreads) k_sum_rows_strided(const double* __restrict__ partials, int cols,
+                                                                   int nz, int64_t out_stride,
+                                                                   double* __restrict__ out) {
+  const double* row = partials + (int64_t)blockIdx.x * cols;
+  double v = 0;
+  for (int c = threadIdx.x; c < cols; c += kRedThreads) v += row[c];
+  const double s = block_sum(v);
+  if (threadIdx.x == 0) out[(int64_t)(blockIdx.x / nz) * out_stride + blockIdx.x % nz] = s;
 }
 
 cudaError_t launch_expval_x(const void* psi, int n, qs_dtype dt, uint64_t xmask, const uint64_t* zm,
                             const double* /*coeffs*/, int nz, double* partials, double* out, cudaStream_t st) {
   if (nz > kMaxZ) return cudaErrorInvalidValue;
   if (dt == QS_C64)
-    k_expval_x<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)psi, n, xmask, zm, nz, partials);
+    k_expval_x<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)psi, nullptr, n, xmask, zm, nz, partials);
   else
-    k_expval_x<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)psi, n, xmask, zm, nz, partials);
+    k_expval_x<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)psi, nullptr, n, xmask, zm, nz, partials);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_sum_rows(partials, nz, kRedBlocks, out, st);
+}
+
+int expval_batched_blocks(int nstates) {
+  int b = kRedBlocks / nstates;
+  return b < 8 ? 8 : b;
+}
+
+cudaError_t launch_expval_x_batched(const void* const* psis, int nstates, int n, qs_dtype dt, uint64_t xmask,
+                                    const uint64_t* zm, int nz, double* partials, double* out, int64_t out_stride,
+                                    cudaStream_t st) {
+  if (nz > kMaxZ) return cudaErrorInvalidValue;
+  const int cols = expval_batched_blocks(nstates);
+  const dim3 grid(cols, nstates);
+  if (dt == QS_C64)
+    k_expval_x<float><<<grid, kRedThreads, 0, st>>>(nullptr, psis, n, xmask, zm, nz, partials);
+  else
+    k_expval_x<double><<<grid, kRedThreads, 0, st>>>(nullptr, psis, n, xmask, zm, nz, partials);
+  note_launch();
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_sum_rows_strided<<<nstates * nz, kRedThreads, 0, st>>>(partials, cols, nz, out_stride, out);
+  note_launch();
+  return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------- H |psi>

@@ -134,8 +134,10 @@ constexpr int kTc2Threads = 256;
 
 template <int PREC>
 __global__ void __launch_bounds__(kTc2Threads, 1)
-    k_tc_block(float2* __restrict__ psi, TcPassDesc p, const uint4* __restrict__ wimg, uint64_t ntiles,
-               int* __restrict__ err) {
+    k_tc_block(float2* __restrict__ psi0, void* const* __restrict__ psis, TcPassDesc p,
+               const uint4* __restrict__ wimg, int lg_tiles1, uint64_t ntiles, int* __restrict__ err) {
+  // ntiles = 2^lg_tiles1 x states; tile index t covers state t >> lg_tiles1 (batched execution)
+  const uint64_t tmask1 = (1ull << lg_tiles1) - 1;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   // A operands double-buffered: buffer b at smem + b * 2 * kTcOperandBytes (hi, then lo)
@@ -176,8 +178,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
   uint32_t phase[2] = {0, 0};
   float2 va[32], vb[32];   // two tiles in flight: register double buffer
 
+  auto state_of = [&](uint64_t t) -> float2* {
+    return psis ? (float2*)psis[t >> lg_tiles1] : psi0;
+  };
   auto load = [&](float2 (&v)[32], uint64_t t) {
-    const uint64_t rb = insert_zero_bits(t, p.tile, 13) | roff;
+    const float2* __restrict__ psi = state_of(t);
+    const uint64_t rb = insert_zero_bits(t & tmask1, p.tile, 13) | roff;
 #pragma unroll
     for (int c = 0; c < 32; ++c) v[c] = psi[rb | hcoff[c]];
   };
@@ -228,7 +234,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     if (s_abort) return false;
     {   // epilogue: TMEM lane `row`, columns 64 half .. 64 half + 63 of accumulator b
-      const uint64_t rb = insert_zero_bits(t, p.tile, 13) | roff;
+      float2* __restrict__ psi = state_of(t);
+      const uint64_t rb = insert_zero_bits(t & tmask1, p.tile, 13) | roff;
       const uint32_t taddr = tmem + b * 128 + half * 64 + ((uint32_t)((warp & 3) * 32) << 16);
 #pragma unroll
       for (int chunk = 0; chunk < 2; ++chunk) {
@@ -274,8 +281,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
 
 size_t tc_smem_bytes() { return 6 * (size_t)kTcOperandBytes + 64 * 8 + 32 + 1024; }
 
-cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int* err,
-                           cudaStream_t st) {
+cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int n, const TcPassDesc& p,
+                                   const void* wimg, int prec, int* err, cudaStream_t st) {
   const size_t smem = tc_smem_bytes();
   static bool configured[2] = {false, false};
   const int idx = prec == 3 ? 1 : 0;
@@ -288,14 +295,21 @@ cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wi
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t ntiles = 1ull << (n - 13);
+  const uint64_t ntiles1 = 1ull << (n - 13), ntiles = ntiles1 * (uint64_t)nstates;
   const uint64_t grid = ntiles < (uint64_t)sms ? ntiles : (uint64_t)sms;
   if (prec == 3)
-    k_tc_block<3><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, p, (const uint4*)wimg, ntiles, err);
+    k_tc_block<3><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, psis, p, (const uint4*)wimg, n - 13,
+                                                             ntiles, err);
   else
-    k_tc_block<1><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, p, (const uint4*)wimg, ntiles, err);
+    k_tc_block<1><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, psis, p, (const uint4*)wimg, n - 13,
+                                                             ntiles, err);
   note_launch();
   return cudaGetLastError();
+}
+
+cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int* err,
+                           cudaStream_t st) {
+  return launch_tc_pass_batched(psi, nullptr, 1, n, p, wimg, prec, err, st);
 }
 
 }  // namespace qs

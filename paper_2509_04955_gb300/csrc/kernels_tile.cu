@@ -206,10 +206,12 @@ __device__ __forceinline__ void apply_diag_op(typename V2<R>::T* tile, int m, co
 }
 
 template <typename R, int KMAX>
-__global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __restrict__ psi, PassDesc p,
-                                                        const DevOp* __restrict__ ops,
-                                                        const double2* __restrict__ gtab,
-                                                        const double2* __restrict__ btab, uint64_t ntiles) {
+__global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __restrict__ psi0,
+                                                        void* const* __restrict__ psis, int64_t gstride,
+                                                        PassDesc p, const DevOp* __restrict__ ops,
+                                                        const double2* __restrict__ gtab0,
+                                                        const double2* __restrict__ btab, int lg_tiles,
+                                                        uint64_t total) {
   using C = typename V2<R>::T;
   using C2 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;  // 16-byte vector
   constexpr int VPT = 16 / sizeof(C);                                           // amplitudes per vector
@@ -226,7 +228,12 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __rest
   }
   __syncthreads();
   const uint32_t size = 1u << m, lmask = (1u << L) - 1;
-  for (uint64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+  // `total` = 2^lg_tiles x states: with a state list (batched execution) tile
+  // index tt covers state tt >> lg_tiles, whose gate table row is gstride apart.
+  for (uint64_t tt = blockIdx.x; tt < total; tt += gridDim.x) {
+    const uint64_t sb = tt >> lg_tiles, t = tt & ((1ull << lg_tiles) - 1);
+    C* __restrict__ psi = psis ? (C*)psis[sb] : psi0;
+    const double2* __restrict__ gtab = gtab0 + sb * gstride;
     const uint64_t base = insert_zero_bits(t << L, p.high, nh);
     for (uint32_t e = threadIdx.x * VPT; e < size; e += kTileThreads * VPT) {
       const uint64_t gi = base | segoff[e >> L] | (e & lmask);
@@ -263,7 +270,8 @@ size_t tile_smem_bytes(int m, int nhigh, int mbuf_elems, qs_dtype dt) {
 }
 
 template <typename R, int KMAX>
-static cudaError_t launch_tile_t(void* psi, int n, const PassDesc& p, const DevOp* ops, const double2* gtab,
+static cudaError_t launch_tile_t(void* psi, void* const* psis, int nstates, int64_t gstride, int n,
+                                 const PassDesc& p, const DevOp* ops, const double2* gtab,
                                  const double2* btab, cudaStream_t st, size_t smem) {
   static int configured_bytes = 0;
   if ((int)smem > configured_bytes) {
@@ -278,34 +286,42 @@ static cudaError_t launch_tile_t(void* psi, int n, const PassDesc& p, const DevO
   int dev = 0, sms = 0;
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const uint64_t ntiles = 1ull << (n - p.m);
+  const uint64_t ntiles = 1ull << (n - p.m), total = ntiles * (uint64_t)nstates;
   uint64_t grid = (uint64_t)sms * per_sm;
-  if (grid > ntiles) grid = ntiles;
-  k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename V2<R>::T*)psi, p, ops, gtab, btab,
-                                                                ntiles);
+  if (grid > total) grid = total;
+  k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename V2<R>::T*)psi, psis, gstride, p, ops,
+                                                                gtab, btab, n - p.m, total);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
-                             const double2* gtab, const double2* btab, int /*threads*/, cudaStream_t st) {
+cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int n, qs_dtype dt,
+                                     const PassDesc& p, const DevOp* ops, const double2* gtab, const double2* btab,
+                                     cudaStream_t st) {
   const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.mbuf_elems, dt);
+#define QS_TILE_ARGS psi, psis, nstates, gstride, n, p, ops, gtab, btab, st, smem
   if (dt == QS_C64) {
     switch (p.kmax) {
-      case 0: case 1: case 2: return launch_tile_t<float, 2>(psi, n, p, ops, gtab, btab, st, smem);
-      case 3: return launch_tile_t<float, 3>(psi, n, p, ops, gtab, btab, st, smem);
-      case 4: return launch_tile_t<float, 4>(psi, n, p, ops, gtab, btab, st, smem);
-      case 5: return launch_tile_t<float, 5>(psi, n, p, ops, gtab, btab, st, smem);
+      case 0: case 1: case 2: return launch_tile_t<float, 2>(QS_TILE_ARGS);
+      case 3: return launch_tile_t<float, 3>(QS_TILE_ARGS);
+      case 4: return launch_tile_t<float, 4>(QS_TILE_ARGS);
+      case 5: return launch_tile_t<float, 5>(QS_TILE_ARGS);
       default: return cudaErrorInvalidValue;
     }
   }
   switch (p.kmax) {
-    case 0: case 1: case 2: return launch_tile_t<double, 2>(psi, n, p, ops, gtab, btab, st, smem);
-    case 3: return launch_tile_t<double, 3>(psi, n, p, ops, gtab, btab, st, smem);
-    case 4: return launch_tile_t<double, 4>(psi, n, p, ops, gtab, btab, st, smem);
-    case 5: return launch_tile_t<double, 5>(psi, n, p, ops, gtab, btab, st, smem);
+    case 0: case 1: case 2: return launch_tile_t<double, 2>(QS_TILE_ARGS);
+    case 3: return launch_tile_t<double, 3>(QS_TILE_ARGS);
+    case 4: return launch_tile_t<double, 4>(QS_TILE_ARGS);
+    case 5: return launch_tile_t<double, 5>(QS_TILE_ARGS);
     default: return cudaErrorInvalidValue;
   }
+#undef QS_TILE_ARGS
+}
+
+cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
+                             const double2* gtab, const double2* btab, int /*threads*/, cudaStream_t st) {
+  return launch_tile_pass_batched(psi, nullptr, 1, 0, n, dt, p, ops, gtab, btab, st);
 }
 
 }  // namespace qs

@@ -129,6 +129,17 @@ cudaError_t launch_resolve(const DevGate* gates, const int32_t* param_gates, int
                            int64_t table_stride, cudaStream_t st);
 cudaError_t launch_gate(void* psi, int n, qs_dtype dt, const DevGate& g, const double2* mat,
                         bool adjoint, cudaStream_t st);
+// Batched forms: psis = device array of nstates state pointers (psi unused);
+// gate table rows gstride apart. partials for expval: nstates * nz * cols.
+cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int n, qs_dtype dt,
+                                     const PassDesc& p, const DevOp* ops, const double2* gtab, const double2* btab,
+                                     cudaStream_t st);
+cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int n, const TcPassDesc& p,
+                                   const void* wimg, int prec, int* err, cudaStream_t st);
+int expval_batched_blocks(int nstates);
+cudaError_t launch_expval_x_batched(const void* const* psis, int nstates, int n, qs_dtype dt, uint64_t xmask,
+                                    const uint64_t* zm, int nz, double* partials, double* out, int64_t out_stride,
+                                    cudaStream_t st);
 cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
                              const double2* gate_table, const double2* block_table, int threads,
                              cudaStream_t st);

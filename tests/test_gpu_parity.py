@@ -267,11 +267,14 @@ def test_adjoint_hea_n24_full_size_against_device_parameter_shift():
 @pytest.mark.parametrize("dtname", ["c64", "c128"])
 def test_batched_graph_matches_sequential_and_oracle(dtname):
     dt = DT[dtname]
-    n, nterms, Bsz = 10, 16, 4
+    n, nterms, Bsz = 14, 16, 4
     gates, _ = W.ucc(n, nterms, 5, wmin=2, wmax=6)
     thetas = W.thetas_normal(nterms, 6, sigma=0.3, batch=Bsz)
     H = W.random_pauli_sum(n, 25, seed=8)
-    for opts in (None, Q.make_opts(fuse_k=1)):
+    modes = [None, Q.make_opts(fuse_k=1), Q.make_opts(fuse_k=3)]
+    if dt == Q.QS_C64:
+        modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2))
+    for opts in modes:
         plan = Q.qs_plan_create(n, dt, gates, opts)
         states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
         try:
@@ -338,6 +341,25 @@ def test_tensor_core_config2_shape_n20_depth40_cz():
     want = ref(n, gates)
     out = run(n, Q.QS_C64, gates, opts=Q.make_opts(mode=Q.QS_MODE_TENSOR))
     assert np.abs(out - want).max() <= 2e-5
+
+
+def test_batched_fixed_circuit_without_parameters():
+    n, Bsz = 13, 3
+    gates = W.random_layered(n, 5, seed=21)
+    want = ref(n, gates)
+    for opts in (Q.make_opts(fuse_k=2), Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2)):
+        plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
+        states = [Q.qs_state_alloc(n, Q.QS_C64) for _ in range(Bsz)]
+        try:
+            Q.qs_plan_execute_batched(plan, states)
+            for s in states:
+                out = np.empty(1 << n, dtype=np.complex64)
+                Q.qs_state_copy_to_host(s, out)
+                assert np.abs(out - want).max() <= 2e-5
+        finally:
+            for s in states:
+                Q.qs_state_free(s)
+            Q.qs_plan_free(plan)
 
 
 def test_invalid_sizes_give_errors_not_faults():
