@@ -164,31 +164,6 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def tune(Q, n, dt, gates, state, cands):
-    """Device-timed search over plan options (the autotuner): each candidate
-    is planned, run once to warm up and once timed with per-launch events."""
-    best = None
-    trials = []
-    for kw in cands:
-        try:
-            plan = Q.qs_plan_create(n, dt, gates, Q.make_opts(**kw))
-        except Q.QsError:
-            continue
-        try:
-            Q.qs_plan_execute(plan, state)
-            Q.qs_plan_set_timing(plan, True)
-            Q.qs_plan_execute(plan, state)
-            ms, _ = Q.qs_plan_timing_read(plan)
-            Q.qs_plan_set_timing(plan, False)
-            info = Q.qs_plan_info_get(plan)
-        finally:
-            Q.qs_plan_free(plan)
-        trials.append(dict(kw, ms=round(ms, 3), passes=info["passes"]))
-        if best is None or ms < best[0]:
-            best = (ms, kw, info)
-    return best, trials
-
-
 def time_steps(Q, torch, plan, state, steps, warmup, with_norm=True, per_launch=False):
     st = torch.cuda.current_stream()
     for _ in range(warmup):
@@ -260,12 +235,11 @@ def main():
     # -- plan options: a short device-timed search (autotuner), or given
     F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
     if args.tune == "auto":
-        cands = [dict(mode=F, fuse_k=k, tile_qubits=m, low_qubits=L) for k in (1, 2, 3) for (m, L) in
-                 ((12, 4), (13, 4), (13, 5))]
-        if n >= 13:
-            cands += [dict(mode=T, fuse_k=2, tile_qubits=13, low_qubits=4, tc_min_gates=g) for g in (2, 3, 4, 6, 8)]
-        best, trials = tune(Q, n, Q.QS_C64, gates, state, cands)
-        kw = best[1]
+        # the library's autotuner: device-timed search over its built-in option grid
+        t0 = time.perf_counter()
+        bopts, bms = Q.qs_plan_autotune(state, gates)
+        kw = {k: v for k, v in Q.opts_dict(bopts).items() if v or k == "mode"}
+        trials = {"chosen": Q.opts_dict(bopts), "ms": bms, "search_s": time.perf_counter() - t0}
     else:
         parts = [int(x) for x in args.tune.split(",")]
         kw = dict(mode=F, fuse_k=parts[0], tile_qubits=parts[1], low_qubits=parts[2])
@@ -339,10 +313,8 @@ def main():
     if not args.no_c128:
         s128 = Q.qs_state_alloc(n, Q.QS_C128, stream)
         if args.tune == "auto":
-            b128, t128 = tune(Q, n, Q.QS_C128, gates, s128,
-                              [dict(mode=F, fuse_k=k, tile_qubits=m, low_qubits=L) for k in (1, 2, 3)
-                               for (m, L) in ((11, 3), (12, 4))])
-            kw128 = b128[1]
+            b128, _ = Q.qs_plan_autotune(s128, gates)
+            kw128 = {k: v for k, v in Q.opts_dict(b128).items() if v or k == "mode"}
         else:
             kw128 = dict(mode=F, fuse_k=2, tile_qubits=11, low_qubits=3)
         p128 = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(**kw128))
@@ -416,7 +388,7 @@ def main():
         "clocks": clk,
         "cpu_baseline": cpu,
         "norm_drift": (max(abs(x - 1) for x in norms) if norms else None),
-        "tuning_trials_c64": trials,
+        "autotune_c64": trials,
     }
     line.update(extra)
     if rank == 0:

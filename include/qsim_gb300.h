@@ -165,6 +165,16 @@ qs_status qs_plan_free(qs_plan_t p);
  * ntheta parameters (may be NULL when the circuit has none). */
 qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta);
 
+/* Autotuner (no counterpart in the paper): plans the circuit under a built-in
+ * grid of options (per-gate; CUDA-core contraction width 1..4 with two tile
+ * shapes; for complex64 with n >= 13, tensor-core plans with three block
+ * thresholds), runs each once to warm up and once timed with CUDA events on
+ * the state's stream (the state's contents are overwritten), and writes the
+ * fastest options to *best and its time to *best_ms (may be NULL). Results
+ * are cached for the process per (n, dtype, gate list). Synchronises. */
+qs_status qs_plan_autotune(qs_state_t scratch, const qs_gate* gates, size_t ngates, const double* theta,
+                           size_t ntheta, qs_plan_opts* best, double* best_ms);
+
 /* One-shot: plan, execute, free. */
 qs_status qs_apply_circuit(qs_state_t s, const qs_gate* gates, size_t ngates,
                            const double* theta, size_t ntheta, const qs_plan_opts* opts);
@@ -244,6 +254,12 @@ qs_status qs_plan_op_count(qs_plan_t p, int64_t* nops, int64_t* npasses);
  * capacity 2 * 4096 doubles): the block's entries as (re, im) pairs. */
 qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits, int32_t* nq,
                          int32_t* gate_index, double* mat);
+/* Self-check of the blocks rebuilt on the device from theta: resolves theta,
+ * builds them on the device, copies them back and returns the largest
+ * difference to the host's FP64 ordered products (W images compared as bf16
+ * values) and the number of such blocks. Synchronises; no state is touched. */
+qs_status qs_plan_check_device_blocks(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta,
+                                      double* max_abs_diff, int64_t* nblocks);
 /* Tile qubits of pass i (ascending, capacity 14) and its op range [op_begin, op_end). */
 qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t* m,
                            int64_t* op_begin, int64_t* op_end);

@@ -81,6 +81,7 @@ _SIGS = {
     "qs_plan_info_get": (C.c_int, [_VP, C.POINTER(QsPlanInfo)]),
     "qs_plan_free": (C.c_int, [_VP]),
     "qs_plan_execute": (C.c_int, [_VP, _VP, _DP, C.c_size_t]),
+    "qs_plan_autotune": (C.c_int, [_VP, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t, C.POINTER(QsPlanOpts), _DP]),
     "qs_apply_circuit": (C.c_int, [_VP, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t, C.POINTER(QsPlanOpts)]),
     "qs_norm": (C.c_int, [_VP, _DP]),
     "qs_expval_pauli_sum": (C.c_int, [_VP, C.POINTER(QsPauliTerm), C.c_size_t, _DP]),
@@ -91,6 +92,7 @@ _SIGS = {
                                   C.c_size_t, _DP, _DP]),
     "qs_plan_execute_batched": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, _DP, C.c_size_t, C.POINTER(QsPauliTerm),
                                           C.c_size_t, _DP]),
+    "qs_plan_check_device_blocks": (C.c_int, [_VP, _VP, _DP, C.c_size_t, _DP, _I64P]),
     "qs_plan_op_count": (C.c_int, [_VP, _I64P, _I64P]),
     "qs_plan_op_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I32P, _I32P, _DP]),
     "qs_plan_pass_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I64P, _I64P]),
@@ -243,6 +245,22 @@ def qs_plan_execute(plan: int, state: int, theta=None):
     _check(lib().qs_plan_execute(plan, state, th.ctypes.data_as(_DP) if th is not None else None, nt))
 
 
+def qs_plan_autotune(state: int, gates, theta=None) -> tuple[QsPlanOpts, float]:
+    """Device-timed choice of plan options for this circuit (cached per process)."""
+    th, nt = _dptr(theta)
+    best = QsPlanOpts()
+    ms = C.c_double()
+    _check(lib().qs_plan_autotune(state, pack_gates(gates), len(gates),
+                                  th.ctypes.data_as(_DP) if th is not None else None, nt, C.byref(best),
+                                  C.byref(ms)))
+    return best, ms.value
+
+
+def opts_dict(o: QsPlanOpts) -> dict:
+    return {"mode": o.mode, "fuse_k": o.fuse_k, "tile_qubits": o.tile_qubits, "low_qubits": o.low_qubits,
+            "tc_min_gates": o.reserved[0], "tc_precision": o.tc_precision}
+
+
 def qs_apply_circuit(state: int, gates, theta=None, opts: QsPlanOpts | None = None):
     th, nt = _dptr(theta)
     _check(lib().qs_apply_circuit(state, pack_gates(gates), len(gates),
@@ -317,6 +335,14 @@ def qs_plan_execute_batched(plan: int, states: list[int], theta=None, terms=None
     _check(lib().qs_plan_execute_batched(plan, arr, B, th.ctypes.data_as(_DP) if th is not None else None, nt,
                                          tp, ntm, ex.ctypes.data_as(_DP) if terms is not None else None))
     return ex if terms is not None else None
+
+
+def qs_plan_check_device_blocks(plan: int, state: int, theta) -> tuple[float, int]:
+    th, nt = _dptr(theta)
+    d, nb = C.c_double(), C.c_int64()
+    _check(lib().qs_plan_check_device_blocks(plan, state, th.ctypes.data_as(_DP) if th is not None else None, nt,
+                                             C.byref(d), C.byref(nb)))
+    return d.value, nb.value
 
 
 def qs_plan_ops(plan: int) -> list[dict]:

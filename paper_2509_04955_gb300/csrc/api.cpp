@@ -8,6 +8,7 @@
 #include <cstring>
 #include <map>
 #include <memory>
+#include <mutex>
 #include <new>
 #include <string>
 #include <vector>
@@ -130,11 +131,15 @@ struct qs_plan_s {
   std::vector<uint16_t> h_wimg;    // per TC pass: bf16 hi image then lo image (64 KiB)
   int tc_prec = 3;
   int64_t btab_elems = 0;
-  bool btab_parametric = false;
+  // blocks whose matrices depend on theta, rebuilt on the device per batch row
+  std::vector<DevBlock> h_dblocks;
+  std::vector<DevMember> h_dmem;
+  std::vector<char> tc_param;      // per tensor-core pass: its W image is rebuilt per row
+  int btab_rows = 0, wimg_rows = 0; // rows allocated in d_btab / d_wimg
   std::vector<double2> h_btab;
   // device
   bool uploaded = false;
-  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err;
+  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err, d_dblocks, d_dmem;
   int gtab_rows = 0;
   qs_plan_info info{};
   // batched graph cache; captured and replayed on a plan-owned stream
@@ -209,6 +214,36 @@ void ensure_gtab_rows(qs_plan_s& p, int rows) {
   p.gtab_rows = rows;
 }
 
+// Block table and W images with `rows` rows (batch rows for blocks rebuilt on
+// the device); host-built entries live in row 0 and are read with stride 0.
+void ensure_block_rows(qs_plan_s& p, int rows) {
+  const bool per_row = !p.h_dblocks.empty();
+  const int want = per_row ? rows : 1;
+  if (want > p.btab_rows) {
+    p.d_btab.release();
+    p.d_btab.ensure(sizeof(double2) * std::max<int64_t>(1, p.btab_elems) * want);
+    if (p.btab_elems)
+      CK(cudaMemcpy(p.d_btab.p, p.h_btab.data(), sizeof(double2) * p.btab_elems, cudaMemcpyHostToDevice));
+    p.btab_rows = want;
+  }
+  if (!p.tcdesc.empty() && want > p.wimg_rows) {
+    p.d_wimg.release();
+    p.d_wimg.ensure(sizeof(uint16_t) * p.h_wimg.size() * want);
+    CK(cudaMemcpy(p.d_wimg.p, p.h_wimg.data(), sizeof(uint16_t) * p.h_wimg.size(), cudaMemcpyHostToDevice));
+    p.wimg_rows = want;
+  }
+}
+
+void build_device_blocks(qs_plan_s& p, int rows, cudaStream_t st) {
+  if (p.h_dblocks.empty()) return;
+  if (p.gtab_rows < rows || p.btab_rows < rows || (!p.tcdesc.empty() && p.wimg_rows < rows))
+    throw Error(QS_ERR_CUDA, "internal: block tables have fewer rows than the batch");
+  const size_t G = std::max<size_t>(1, p.gates.size());
+  CK(launch_build_blocks(p.d_dblocks.as<DevBlock>(), (int)p.h_dblocks.size(), p.d_dmem.as<DevMember>(),
+                         p.d_gtab.as<double2>(), (int64_t)(16 * G), rows, p.d_btab.as<double2>(), p.btab_elems,
+                         p.d_wimg.as<uint16_t>(), (int64_t)p.h_wimg.size(), st));
+}
+
 void upload(qs_plan_s& p) {
   if (p.uploaded) return;
   const size_t G = p.gates.size();
@@ -222,15 +257,20 @@ void upload(qs_plan_s& p) {
     p.d_ops.ensure(sizeof(DevOp) * p.dops.size());
     CK(cudaMemcpy(p.d_ops.p, p.dops.data(), sizeof(DevOp) * p.dops.size(), cudaMemcpyHostToDevice));
   }
-  p.d_btab.ensure(sizeof(double2) * std::max<int64_t>(1, p.btab_elems));
-  if (p.btab_elems)
-    CK(cudaMemcpy(p.d_btab.p, p.h_btab.data(), sizeof(double2) * p.btab_elems, cudaMemcpyHostToDevice));
-  if (!p.tcdesc.empty()) {
-    p.d_wimg.ensure(sizeof(uint16_t) * p.h_wimg.size());
-    CK(cudaMemcpy(p.d_wimg.p, p.h_wimg.data(), sizeof(uint16_t) * p.h_wimg.size(), cudaMemcpyHostToDevice));
+  ensure_block_rows(p, 1);
+  if (!p.h_dblocks.empty()) {
+    p.d_dblocks.ensure(sizeof(DevBlock) * p.h_dblocks.size());
+    CK(cudaMemcpy(p.d_dblocks.p, p.h_dblocks.data(), sizeof(DevBlock) * p.h_dblocks.size(), cudaMemcpyHostToDevice));
+    p.d_dmem.ensure(sizeof(DevMember) * std::max<size_t>(1, p.h_dmem.size()));
+    if (!p.h_dmem.empty())
+      CK(cudaMemcpy(p.d_dmem.p, p.h_dmem.data(), sizeof(DevMember) * p.h_dmem.size(), cudaMemcpyHostToDevice));
   }
   p.d_err.ensure(sizeof(int) * 4);
   CK(cudaMemset(p.d_err.p, 0, sizeof(int) * 4));
+  // kernel attributes and occupancy, here and never during a stream capture
+  for (const PassDesc& pd : p.pdesc) CK(prepare_tile_pass(pd, p.dt));
+  if (!p.tcdesc.empty()) CK(prepare_tc_pass());
+  if (!p.h_dblocks.empty()) CK(prepare_build_blocks());
   p.uploaded = true;
 }
 
@@ -265,18 +305,22 @@ void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed
 // take the device array of state pointers and gate-table rows 16 G apart.
 void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_t st) {
   const size_t G = std::max<size_t>(1, p.gates.size());
+  if (p.gtab_rows < B || (!p.h_dblocks.empty() && (p.btab_rows < B || (!p.tcdesc.empty() && p.wimg_rows < B))))
+    throw Error(QS_ERR_CUDA, "internal: tables have fewer rows than the batch");
   for (const auto& stp : p.steps) {
     if (stp.kind == 0)
-      CK(launch_tile_pass_batched(nullptr, d_psis, B, (int64_t)(16 * G), p.n, p.dt, p.pdesc[stp.idx],
+      CK(launch_tile_pass_batched(nullptr, d_psis, B, (int64_t)(16 * G), p.btab_elems, p.n, p.dt, p.pdesc[stp.idx],
                                   p.d_ops.as<DevOp>(), p.d_gtab.as<double2>(), p.d_btab.as<double2>(), st));
     else
-      CK(launch_tc_pass_batched(nullptr, d_psis, B, p.n, p.tcdesc[stp.idx],
-                                p.d_wimg.as<uint16_t>() + (size_t)stp.idx * 32768, p.tc_prec, p.d_err.as<int>(), st));
+      CK(launch_tc_pass_batched(nullptr, d_psis, B, p.tc_param[stp.idx] ? (int64_t)p.h_wimg.size() : 0, p.n,
+                                p.tcdesc[stp.idx], p.d_wimg.as<uint16_t>() + (size_t)stp.idx * 32768, p.tc_prec,
+                                p.d_err.as<int>(), st));
   }
 }
 
 void resolve_theta(qs_plan_s& p, const double* theta, size_t ntheta, int rows, cudaStream_t st) {
   if (p.pgates.empty()) return;
+  if (p.gtab_rows < rows) throw Error(QS_ERR_CUDA, "internal: gate table has fewer rows than requested");
   require(theta != nullptr, "circuit has parameters but theta is NULL");
   require((int64_t)ntheta >= p.nparams, "theta has fewer entries than the circuit's parameter indices");
   p.d_theta.ensure(sizeof(double) * ntheta * rows);
@@ -290,11 +334,7 @@ void execute(qs_plan_s& p, qs_state_s& s, const double* theta, size_t ntheta) {
   require(p.n == s.n && p.dt == s.dt, "plan and state differ in qubit count or dtype");
   upload(p);
   resolve_theta(p, theta, ntheta, 1, s.st);
-  if (p.btab_parametric) {
-    compute_blocks(p, theta, true);
-    CK(cudaMemcpyAsync(p.d_btab.p, p.h_btab.data(), sizeof(double2) * p.btab_elems, cudaMemcpyHostToDevice, s.st));
-    CK(cudaStreamSynchronize(s.st));   // h_btab is rewritten by the next call
-  }
+  build_device_blocks(p, 1, s.st);
   issue_circuit(p, s.d, 0, s.st, p.timing);
   if (!p.tcdesc.empty()) {
     int err = 0;
@@ -347,6 +387,33 @@ void build_w_image(const double2* U, uint16_t* img) {
     }
 }
 
+// Records a block whose matrix is rebuilt on the device from theta (kind: 0
+// dense, 1 diagonal, 2 tensor-core W image; out = table offset or image index).
+void register_device_block(qs_plan_s& P, const Block& blk, int kind, int64_t out) {
+  DevBlock d;
+  std::memset(&d, 0, sizeof(d));
+  d.k = (int)blk.qubits.size();
+  d.kind = kind;
+  d.out = out;
+  d.mem_begin = (int)P.h_dmem.size();
+  auto local = [&](int q) {
+    return (int)(std::lower_bound(blk.qubits.begin(), blk.qubits.end(), q) - blk.qubits.begin());
+  };
+  for (int gi : blk.gates) {
+    const HGate& g = P.gates[gi];
+    DevMember m;
+    std::memset(&m, 0, sizeof(m));
+    m.gate = gi;
+    m.nt = g.nt;
+    m.t0 = local(g.t[0]);
+    m.t1 = g.nt == 2 ? local(g.t[1]) : 0;
+    for (int k = 0; k < g.nc; ++k) m.cmask |= 1u << local(g.c[k]);
+    P.h_dmem.push_back(m);
+  }
+  d.mem_end = (int)P.h_dmem.size();
+  P.h_dblocks.push_back(d);
+}
+
 void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::vector<PassRec>& passes,
                       const std::vector<int>& order, int low_qubits, qs_plan_info& in) {
   const qs_dtype dt = P.dt;
@@ -392,6 +459,7 @@ void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::ve
         d.k = (int)blk.qubits.size();
         for (int j = 0; j < d.k; ++j) d.ins[j] = local(blk.qubits[j]);
         d.mat = (int32_t)P.block_off[r.block];
+        d.per_row = blk.parametric ? 1 : 0;
         if (r.type == OP_DENSE) {
           pd.kmax = std::max(pd.kmax, d.k);
           pd.mbuf_elems = std::max(pd.mbuf_elems, 1 << (2 * d.k));
@@ -430,7 +498,11 @@ void emit_tc_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
   for (int j = 0; j < 13; ++j) t.tile[j] = tile[j];
   const size_t w0 = P.h_wimg.size();
   P.h_wimg.resize(w0 + 32768);
-  build_w_image(P.h_btab.data() + P.block_off[r.block], P.h_wimg.data() + w0);
+  if (blk.parametric)
+    register_device_block(P, blk, 2, (int64_t)P.tcdesc.size());   // W image rebuilt per row on the device
+  else
+    build_w_image(P.h_btab.data() + P.block_off[r.block], P.h_wimg.data() + w0);
+  P.tc_param.push_back(blk.parametric ? 1 : 0);
   DevOp d;
   std::memset(&d, 0, sizeof(d));
   d.type = OP_TC;
@@ -523,7 +595,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
     // it is padded to 6 qubits with the highest qubits it does not touch.
     const int tc_min_gates = o.reserved[0] > 0 ? o.reserved[0] : 10;
     for (Block& blk : p->blocks) {
-      if (!blk.parametric && (int)blk.gates.size() >= tc_min_gates) {
+      if ((int)blk.gates.size() >= tc_min_gates) {
         blk.rep = OP_TC;
         blk.diag = false;
         for (int q = n - 1; q >= 0 && blk.qubits.size() < 6; --q)
@@ -548,7 +620,8 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
       p->block_off[b] = p->btab_elems;
       const int64_t D = 1ll << blk.qubits.size();
       p->btab_elems += blk.rep == OP_DIAG ? D : D * D;
-      if (blk.parametric) p->btab_parametric = true;
+      if (blk.parametric && blk.rep != OP_TC)
+        register_device_block(*p, blk, blk.rep == OP_DIAG ? 1 : 0, p->block_off[b]);
     }
   }
   p->h_btab.assign(std::max<int64_t>(1, p->btab_elems), make_double2(0, 0));
@@ -701,6 +774,54 @@ void upload_pauli_apply(const qs_pauli_term* t, size_t nt, DevBuf& buf, cudaStre
 
 }  // namespace
 
+// ---------------------------------------------------------------- autotuner
+
+struct TuneEntry {
+  qs_plan_opts opts;
+  double ms;
+};
+std::mutex g_tune_mu;
+std::map<std::vector<uint64_t>, TuneEntry> g_tune_cache;
+
+uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603ull) {
+  const unsigned char* p = (const unsigned char*)data;
+  for (size_t i = 0; i < bytes; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+std::vector<qs_plan_opts> tune_candidates(int n, qs_dtype dt) {
+  std::vector<qs_plan_opts> c;
+  auto add = [&](int mode, int k, int m, int L, int tcmin) {
+    qs_plan_opts o;
+    std::memset(&o, 0, sizeof(o));
+    o.mode = mode;
+    o.fuse_k = k;
+    o.tile_qubits = m;
+    o.low_qubits = L;
+    o.reserved[0] = tcmin;
+    c.push_back(o);
+  };
+  add(QS_MODE_PER_GATE, 0, 0, 0, 0);
+  const int ks[] = {1, 2, 3, 4};
+  for (int k : ks) {
+    if (dt == QS_C64) {
+      add(QS_MODE_FUSED, k, 12, 4, 0);
+      add(QS_MODE_FUSED, k, 13, 4, 0);
+    } else {
+      add(QS_MODE_FUSED, k, 11, 3, 0);
+      add(QS_MODE_FUSED, k, 12, 4, 0);
+    }
+  }
+  if (dt == QS_C64 && n >= 13) {
+    const int tm[] = {2, 4, 8};
+    for (int t : tm) add(QS_MODE_TENSOR, 2, 13, 4, t);
+  }
+  return c;
+}
+
 // =================================================================== C ABI
 
 extern "C" {
@@ -741,6 +862,58 @@ qs_status qs_plan_timing_read_kinds(qs_plan_t p, double* total_ms, int64_t* laun
     if (kind_launches) { kind_launches[0] = kn[0]; kind_launches[1] = kn[1]; }
     p->events_used = 0;
     p->event_kind.clear();
+  });
+}
+
+qs_status qs_plan_check_device_blocks(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta,
+                                      double* max_abs_diff, int64_t* nblocks) {
+  return guard([&] {
+    require(p != nullptr, "plan is NULL");
+    check_state(s);
+    require(p->n == s->n && p->dt == s->dt, "plan and state differ");
+    upload(*p);
+    resolve_theta(*p, theta, ntheta, 1, s->st);
+    build_device_blocks(*p, 1, s->st);
+    std::vector<double2> dev(std::max<int64_t>(1, p->btab_elems));
+    CK(cudaMemcpyAsync(dev.data(), p->d_btab.p, sizeof(double2) * dev.size(), cudaMemcpyDeviceToHost, s->st));
+    std::vector<uint16_t> wdev(p->h_wimg.size());
+    if (!wdev.empty())
+      CK(cudaMemcpyAsync(wdev.data(), p->d_wimg.p, sizeof(uint16_t) * wdev.size(), cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+    std::vector<double2> saved = p->h_btab;
+    compute_blocks(*p, theta, true);   // host FP64 products for the parametric blocks
+    double worst = 0;
+    int64_t cnt = 0;
+    for (size_t b = 0; b < p->blocks.size(); ++b) {
+      const Block& blk = p->blocks[b];
+      if (!blk.parametric || p->block_off[b] < 0) continue;
+      const int64_t D = 1ll << blk.qubits.size();
+      const int64_t m = blk.rep == OP_DIAG ? D : D * D;
+      for (int64_t i = 0; i < m; ++i) {
+        const double2 a = dev[p->block_off[b] + i], h = p->h_btab[p->block_off[b] + i];
+        if (blk.rep != OP_TC) worst = std::max(worst, std::hypot(a.x - h.x, a.y - h.y));
+      }
+      if (blk.rep == OP_TC) {   // compare the W image with one built on the host from the host product
+        std::vector<uint16_t> img(32768);
+        build_w_image(p->h_btab.data() + p->block_off[b], img.data());
+        for (size_t t = 0; t < p->tcdesc.size(); ++t)
+          (void)t;
+        // locate this block's tensor-core pass
+        for (size_t st = 0, ti = 0; st < p->steps.size(); ++st)
+          if (p->steps[st].kind == 1) {
+            const OpRec& r = p->exec_ops[p->pass_ops[st].first];
+            if (r.block == (int)b)
+              for (int e = 0; e < 32768; ++e)
+                worst = std::max(worst, std::fabs((double)bf16_to_float(img[e]) -
+                                                  (double)bf16_to_float(wdev[(size_t)p->steps[st].idx * 32768 + e])));
+            ++ti;
+          }
+      }
+      ++cnt;
+    }
+    p->h_btab = saved;
+    if (max_abs_diff) *max_abs_diff = worst;
+    if (nblocks) *nblocks = cnt;
   });
 }
 
@@ -923,6 +1096,67 @@ qs_status qs_plan_free(qs_plan_t p) {
   return guard([&] { delete p; });
 }
 
+qs_status qs_plan_autotune(qs_state_t s, const qs_gate* gates, size_t ngates, const double* theta, size_t ntheta,
+                           qs_plan_opts* best, double* best_ms) {
+  return guard([&] {
+    check_state(s);
+    require(best != nullptr, "best is NULL");
+    require(ngates == 0 || gates != nullptr, "gates is NULL");
+    std::vector<uint64_t> key{(uint64_t)s->n, (uint64_t)s->dt, (uint64_t)ngates,
+                              fnv1a(gates, sizeof(qs_gate) * ngates)};
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      auto it = g_tune_cache.find(key);
+      if (it != g_tune_cache.end()) {
+        *best = it->second.opts;
+        if (best_ms) *best_ms = it->second.ms;
+        return;
+      }
+    }
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    bool have = false;
+    TuneEntry top{};
+    try {
+      for (const qs_plan_opts& o : tune_candidates(s->n, s->dt)) {
+        std::unique_ptr<qs_plan_s> p;
+        try {
+          p.reset(create_plan(s->n, s->dt, gates, ngates, &o));
+        } catch (const Error& e) {
+          if (e.code == QS_ERR_ARG || e.code == QS_ERR_UNSUPPORTED) continue;   // option not valid here
+          throw;
+        }
+        execute(*p, *s, theta, ntheta);            // warm-up (uploads, attributes)
+        CK(cudaEventRecord(e0, s->st));
+        execute(*p, *s, theta, ntheta);
+        CK(cudaEventRecord(e1, s->st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (!have || ms < top.ms) {
+          top.opts = o;
+          top.ms = ms;
+          have = true;
+        }
+      }
+    } catch (...) {
+      cudaEventDestroy(e0);
+      cudaEventDestroy(e1);
+      throw;
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    require(have, "no candidate plan is valid for this circuit");
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      g_tune_cache[key] = top;
+    }
+    *best = top.opts;
+    if (best_ms) *best_ms = top.ms;
+  });
+}
+
 qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta) {
   return guard([&] {
     require(p != nullptr, "plan is NULL");
@@ -1094,7 +1328,6 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
       require(states[b]->n == p->n && states[b]->dt == p->dt, "plan and state differ in qubit count or dtype");
       require(states[b]->st == states[0]->st, "batched states must share one stream");
     }
-    require(!p->btab_parametric, "batched execution needs a plan without parametric fused blocks");
     require(terms == nullptr || expvals != nullptr, "expvals is NULL");
     cudaStream_t user_st = states[0]->st;
     if (!p->cap_stream) {
@@ -1107,6 +1340,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     CK(cudaEventRecord(p->ev_in, user_st));
     CK(cudaStreamWaitEvent(st, p->ev_in, 0));
     ensure_gtab_rows(*p, B);
+    ensure_block_rows(*p, B);
     // theta upload happens outside the graph; the graph reads p->d_theta
     if (!p->pgates.empty()) {
       require(theta != nullptr && (int64_t)ntheta >= p->nparams, "theta too short");
@@ -1138,6 +1372,9 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     key.push_back((void*)(uintptr_t)(terms ? nterms : 0));
     key.push_back(p->d_theta.p);
     key.push_back(p->d_psis.p);
+    key.push_back(p->d_btab.p);
+    key.push_back(p->d_wimg.p);
+    key.push_back(p->d_gtab.p);
     key.push_back(states[0]->scratch.p);
     key.push_back(states[0]->scratch2.p);
     if (!p->pgates.empty())
@@ -1158,10 +1395,13 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
       try {
         if (!p->pgates.empty()) {
           const size_t G = std::max<size_t>(1, p->gates.size());
+          if (p->gtab_rows < B || p->d_theta.bytes < sizeof(double) * ntheta * B)
+            throw Error(QS_ERR_CUDA, "internal: gate table or theta smaller than the batch");
           CK(launch_resolve(p->d_gates.as<DevGate>(), p->d_pg.as<int32_t>(), (int)p->pgates.size(),
                             p->d_theta.as<double>(), (int64_t)ntheta, B, p->d_gtab.as<double2>(), (int64_t)16 * G,
                             st));
         }
+        build_device_blocks(*p, B, st);
         if (one_launch) {
           issue_circuit_batched(*p, d_psis, B, st);
           if (terms && nterms)

@@ -7,8 +7,8 @@
 //   D[r][2c'+b] = sum_{c,a} A[r][2c+a] * W[2c+a][2c'+b],   K = N = 128,
 // with W[2c][2c'] = Re U[c'][c], W[2c+1][2c'] = -Im U[c'][c],
 //      W[2c][2c'+1] = Im U[c'][c], W[2c+1][2c'+1] = Re U[c'][c].
-// One persistent CTA per SM (256 threads, two per row) walks tiles of 128
-// rows: the 7 lowest qubits outside Q are the row bits (a warp's 32 rows are
+// One persistent CTA per SM (256 threads, two per row) walks a contiguous
+// range of tiles of 128 rows: the 7 lowest qubits outside Q are the row bits (a warp's 32 rows are
 // consecutive amplitudes when Q holds no low qubit, so its loads coalesce),
 // Q the column bits. Software pipeline per tile i: the loads of tile i+1 are
 // issued into registers, tile i's accumulator is read back from tensor memory
@@ -135,9 +135,16 @@ constexpr int kTc2Threads = 256;
 template <int PREC>
 __global__ void __launch_bounds__(kTc2Threads, 1)
     k_tc_block(float2* __restrict__ psi0, void* const* __restrict__ psis, TcPassDesc p,
-               const uint4* __restrict__ wimg, int lg_tiles1, uint64_t ntiles, int* __restrict__ err) {
-  // ntiles = 2^lg_tiles1 x states; tile index t covers state t >> lg_tiles1 (batched execution)
+               const uint4* __restrict__ wimg, int64_t wstride16, int lg_tiles1, uint64_t ntiles,
+               int* __restrict__ err) {
+  // ntiles = 2^lg_tiles1 x states; tile index t covers state t >> lg_tiles1 (batched execution).
+  // Each CTA takes a contiguous range of tiles; with per-state W images
+  // (wstride16 = uint4 stride, non-zero for parametric blocks) the image is
+  // reloaded when the range crosses into the next state.
   const uint64_t tmask1 = (1ull << lg_tiles1) - 1;
+  const uint64_t chunk = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t t_begin = (uint64_t)blockIdx.x * chunk;
+  const uint64_t t_end = t_begin + chunk < ntiles ? t_begin + chunk : ntiles;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   // A operands double-buffered: buffer b at smem + b * 2 * kTcOperandBytes (hi, then lo)
@@ -150,7 +157,12 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int row = (warp & 3) * 32 + lane, half = warp >> 2;
-  for (int i = tid; i < 2 * kTcOperandBytes / 16; i += kTc2Threads) ((uint4*)W_hi)[i] = wimg[i];
+  uint64_t wstate = t_begin >> lg_tiles1;   // state whose W image is resident
+  auto load_w = [&](uint64_t state) {
+    const uint4* src = wimg + (int64_t)state * wstride16;
+    for (int i = tid; i < 2 * kTcOperandBytes / 16; i += kTc2Threads) ((uint4*)W_hi)[i] = src[i];
+  };
+  load_w(wstride16 ? wstate : 0);
   if (tid < 64) {
     uint64_t o = 0;
     for (int b = 0; b < 6; ++b) o |= (uint64_t)((tid >> b) & 1) << p.col[b];
@@ -222,8 +234,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
   // one pipeline step for tile t (MMAs issued into accumulator b): `nxt`
   // holds tile t + g (in flight), `nn` receives tile t + 2g.
   auto step = [&](uint64_t t, int b, float2 (&nxt)[32], float2 (&nn)[32]) -> bool {
-    const uint64_t g = gridDim.x;
-    if (t + 2 * g < ntiles) load(nn, t + 2 * g);
+    if (t + 2 < t_end) load(nn, t + 2);
     if (tid == 0 && !mbar_wait(smem_u32(mbar + b), phase[b])) {
       atomicExch(err, 1);
       s_abort = 1;
@@ -245,29 +256,32 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
         for (int q = 0; q < 16; ++q) psi[rb | hcoff[chunk * 16 + q]] = make_float2(o[2 * q], o[2 * q + 1]);
       }
     }
-    if (t + g < ntiles) {
+    if (t + 1 < t_end) {
+      if (wstride16 && ((t + 1) >> lg_tiles1) != wstate) {   // previous MMAs are complete
+        wstate = (t + 1) >> lg_tiles1;
+        load_w(wstate);
+      }
       convert(nxt, b ^ 1);
       issue(b ^ 1);
     }
     return true;
   };
 
-  const uint64_t g = gridDim.x;
-  uint64_t t = blockIdx.x;
+  uint64_t t = t_begin;
   int b = 0;
-  if (t < ntiles) {
+  if (t < t_end) {
     load(va, t);
     convert(va, 0);
     issue(0);
-    if (t + g < ntiles) load(va, t + g);
+    if (t + 1 < t_end) load(va, t + 1);
   }
-  while (t < ntiles) {
+  while (t < t_end) {
     if (!step(t, b, va, vb)) break;
-    t += g;
+    t += 1;
     b ^= 1;
-    if (t >= ntiles) break;
+    if (t >= t_end) break;
     if (!step(t, b, vb, va)) break;
-    t += g;
+    t += 1;
     b ^= 1;
   }
   // after a timeout, give outstanding MMAs a second bounded wait before
@@ -281,35 +295,44 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
 
 size_t tc_smem_bytes() { return 6 * (size_t)kTcOperandBytes + 64 * 8 + 32 + 1024; }
 
-cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int n, const TcPassDesc& p,
-                                   const void* wimg, int prec, int* err, cudaStream_t st) {
-  const size_t smem = tc_smem_bytes();
-  static bool configured[2] = {false, false};
-  const int idx = prec == 3 ? 1 : 0;
-  if (!configured[idx]) {
-    cudaError_t e = prec == 3 ? cudaFuncSetAttribute(k_tc_block<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-                              : cudaFuncSetAttribute(k_tc_block<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured[idx] = true;
-  }
-  int dev = 0, sms = 0;
+static bool g_tc_ready = false;
+static int g_tc_sms = 0;
+
+// Host-side set-up (outside any stream capture): shared-memory attribute of
+// both precision instances and the SM count.
+cudaError_t prepare_tc_pass() {
+  if (g_tc_ready) return cudaSuccess;
+  const int smem = (int)tc_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_tc_block<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  int dev = 0;
   cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  cudaDeviceGetAttribute(&g_tc_sms, cudaDevAttrMultiProcessorCount, dev);
+  g_tc_ready = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
+                                   const TcPassDesc& p, const void* wimg, int prec, int* err, cudaStream_t st) {
+  if (!g_tc_ready) return cudaErrorInvalidConfiguration;   // not prepared
+  const size_t smem = tc_smem_bytes();
+  const int sms = g_tc_sms;
   const uint64_t ntiles1 = 1ull << (n - 13), ntiles = ntiles1 * (uint64_t)nstates;
   const uint64_t grid = ntiles < (uint64_t)sms ? ntiles : (uint64_t)sms;
   if (prec == 3)
-    k_tc_block<3><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, psis, p, (const uint4*)wimg, n - 13,
-                                                             ntiles, err);
+    k_tc_block<3><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, psis, p, (const uint4*)wimg, wstride / 8,
+                                                             n - 13, ntiles, err);
   else
-    k_tc_block<1><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, psis, p, (const uint4*)wimg, n - 13,
-                                                             ntiles, err);
+    k_tc_block<1><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, psis, p, (const uint4*)wimg, wstride / 8,
+                                                             n - 13, ntiles, err);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int* err,
                            cudaStream_t st) {
-  return launch_tc_pass_batched(psi, nullptr, 1, n, p, wimg, prec, err, st);
+  return launch_tc_pass_batched(psi, nullptr, 1, 0, n, p, wimg, prec, err, st);
 }
 
 }  // namespace qs

@@ -208,7 +208,7 @@ __device__ __forceinline__ void apply_diag_op(typename V2<R>::T* tile, int m, co
 template <typename R, int KMAX>
 __global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __restrict__ psi0,
                                                         void* const* __restrict__ psis, int64_t gstride,
-                                                        PassDesc p, const DevOp* __restrict__ ops,
+                                                        int64_t bstride, PassDesc p, const DevOp* __restrict__ ops,
                                                         const double2* __restrict__ gtab0,
                                                         const double2* __restrict__ btab, int lg_tiles,
                                                         uint64_t total) {
@@ -244,14 +244,17 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __rest
       const DevOp op = ops[o];
       if (op.type == OP_GATE) {
         apply_gate_op<R>(tile, m, op, gtab, mbuf);
-      } else if (op.type == OP_DIAG) {
-        apply_diag_op<R>(tile, m, op, btab, mbuf);
       } else {
-        if (op.k == 1) apply_dense_op<R, 1>(tile, m, op, btab, mbuf);
-        else if (op.k == 2) apply_dense_op<R, 2>(tile, m, op, btab, mbuf);
-        if constexpr (KMAX >= 3) { if (op.k == 3) apply_dense_op<R, 3>(tile, m, op, btab, mbuf); }
-        if constexpr (KMAX >= 4) { if (op.k == 4) apply_dense_op<R, 4>(tile, m, op, btab, mbuf); }
-        if constexpr (KMAX >= 5) { if (op.k == 5) apply_dense_op<R, 5>(tile, m, op, btab, mbuf); }
+        const double2* __restrict__ bt = op.per_row ? btab + sb * bstride : btab;
+        if (op.type == OP_DIAG) {
+          apply_diag_op<R>(tile, m, op, bt, mbuf);
+        } else {
+          if (op.k == 1) apply_dense_op<R, 1>(tile, m, op, bt, mbuf);
+          else if (op.k == 2) apply_dense_op<R, 2>(tile, m, op, bt, mbuf);
+          if constexpr (KMAX >= 3) { if (op.k == 3) apply_dense_op<R, 3>(tile, m, op, bt, mbuf); }
+          if constexpr (KMAX >= 4) { if (op.k == 4) apply_dense_op<R, 4>(tile, m, op, bt, mbuf); }
+          if constexpr (KMAX >= 5) { if (op.k == 5) apply_dense_op<R, 5>(tile, m, op, bt, mbuf); }
+        }
       }
       __syncthreads();
     }
@@ -269,37 +272,61 @@ size_t tile_smem_bytes(int m, int nhigh, int mbuf_elems, qs_dtype dt) {
   return (amp << m) + 8 * runs + amp * (size_t)(mbuf_elems < 16 ? 16 : mbuf_elems);
 }
 
+// Per kernel instance: the largest dynamic shared memory configured so far
+// and the resident CTAs per SM at that size. Set up by prepare_tile_pass
+// (host side, outside any stream capture) before the first launch.
 template <typename R, int KMAX>
-static cudaError_t launch_tile_t(void* psi, void* const* psis, int nstates, int64_t gstride, int n,
-                                 const PassDesc& p, const DevOp* ops, const double2* gtab,
-                                 const double2* btab, cudaStream_t st, size_t smem) {
-  static int configured_bytes = 0;
-  if ((int)smem > configured_bytes) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile<R, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    configured_bytes = (int)smem;
-  }
+struct TileCfg {
+  static int bytes, per_sm;
+};
+template <typename R, int KMAX> int TileCfg<R, KMAX>::bytes = 0;
+template <typename R, int KMAX> int TileCfg<R, KMAX>::per_sm = 0;
+
+template <typename R, int KMAX>
+static cudaError_t prepare_tile_t(size_t smem) {
+  if ((int)smem <= TileCfg<R, KMAX>::bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(k_tile<R, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   int per_sm = 0;
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<R, KMAX>, kTileThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<R, KMAX>, kTileThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  int dev = 0, sms = 0;
-  cudaGetDevice(&dev);
-  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  TileCfg<R, KMAX>::bytes = (int)smem;
+  TileCfg<R, KMAX>::per_sm = per_sm;
+  return cudaSuccess;
+}
+
+static int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  }
+  return sms;
+}
+
+template <typename R, int KMAX>
+static cudaError_t launch_tile_t(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride, int n,
+                                 const PassDesc& p, const DevOp* ops, const double2* gtab,
+                                 const double2* btab, cudaStream_t st, size_t smem) {
+  if ((int)smem > TileCfg<R, KMAX>::bytes) return cudaErrorInvalidConfiguration;   // not prepared
+  const int per_sm = TileCfg<R, KMAX>::per_sm;
+  const int sms = sm_count();
   const uint64_t ntiles = 1ull << (n - p.m), total = ntiles * (uint64_t)nstates;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > total) grid = total;
-  k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename V2<R>::T*)psi, psis, gstride, p, ops,
-                                                                gtab, btab, n - p.m, total);
+  k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename V2<R>::T*)psi, psis, gstride, bstride, p,
+                                                                ops, gtab, btab, n - p.m, total);
   note_launch();
   return cudaGetLastError();
 }
 
-cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int n, qs_dtype dt,
-                                     const PassDesc& p, const DevOp* ops, const double2* gtab, const double2* btab,
-                                     cudaStream_t st) {
+cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
+                                     int n, qs_dtype dt, const PassDesc& p, const DevOp* ops, const double2* gtab,
+                                     const double2* btab, cudaStream_t st) {
   const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.mbuf_elems, dt);
-#define QS_TILE_ARGS psi, psis, nstates, gstride, n, p, ops, gtab, btab, st, smem
+#define QS_TILE_ARGS psi, psis, nstates, gstride, bstride, n, p, ops, gtab, btab, st, smem
   if (dt == QS_C64) {
     switch (p.kmax) {
       case 0: case 1: case 2: return launch_tile_t<float, 2>(QS_TILE_ARGS);
@@ -319,9 +346,30 @@ cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, 
 #undef QS_TILE_ARGS
 }
 
+cudaError_t prepare_tile_pass(const PassDesc& p, qs_dtype dt) {
+  const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.mbuf_elems, dt);
+  sm_count();
+  if (dt == QS_C64) {
+    switch (p.kmax) {
+      case 0: case 1: case 2: return prepare_tile_t<float, 2>(smem);
+      case 3: return prepare_tile_t<float, 3>(smem);
+      case 4: return prepare_tile_t<float, 4>(smem);
+      case 5: return prepare_tile_t<float, 5>(smem);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  switch (p.kmax) {
+    case 0: case 1: case 2: return prepare_tile_t<double, 2>(smem);
+    case 3: return prepare_tile_t<double, 3>(smem);
+    case 4: return prepare_tile_t<double, 4>(smem);
+    case 5: return prepare_tile_t<double, 5>(smem);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
                              const double2* gtab, const double2* btab, int /*threads*/, cudaStream_t st) {
-  return launch_tile_pass_batched(psi, nullptr, 1, 0, n, dt, p, ops, gtab, btab, st);
+  return launch_tile_pass_batched(psi, nullptr, 1, 0, 0, n, dt, p, ops, gtab, btab, st);
 }
 
 }  // namespace qs

@@ -54,6 +54,27 @@ enum OpType : int32_t {
   OP_TC = 3       // dense 6-qubit block applied on tensor cores (its own pass, complex64)
 };
 
+// A contracted block whose matrix depends on theta: rebuilt on the device from
+// the resolved gate table (one CTA per block and batch row), FP64.
+struct DevBlock {
+  int32_t k;               // block qubits (D = 2^k <= 64)
+  int32_t kind;            // 0 dense (D*D entries), 1 diagonal (D entries), 2 tensor-core W image
+  int32_t mem_begin, mem_end;   // member gates in the DevMember array, program order
+  int64_t out;             // complex offset in the block table, or W image index
+};
+struct DevMember {
+  int32_t gate;            // row in the gate table
+  int32_t nt;              // targets: 1 or 2
+  int32_t t0, t1;          // block-local target bits
+  uint32_t cmask;          // block-local control bits
+  int32_t pad;
+};
+cudaError_t prepare_build_blocks();
+cudaError_t prepare_tc_pass();
+cudaError_t launch_build_blocks(const DevBlock* blocks, int nblocks, const DevMember* mem, const double2* gtab,
+                                int64_t gstride, int rows, double2* btab, int64_t bstride, uint16_t* wimg,
+                                int64_t wstride, cudaStream_t st);
+
 // Tensor-core pass over tiles of 128 rows x 64 columns (13 qubits).
 struct TcPassDesc {
   int32_t row[7];          // global qubits of the row bits, ascending (bit b of the row index)
@@ -73,7 +94,7 @@ struct DevOp {
   int32_t t0, t1;          // OP_GATE target positions (tile-local)
   uint32_t cmask;          // OP_GATE control mask (tile-local)
   int32_t mat;             // OP_GATE: gate index in the gate table; blocks: complex offset in block table
-  int32_t pad;
+  int32_t per_row;         // blocks: 1 = rebuilt per batch row (parametric), table rows bstride apart
 };
 
 struct PassDesc {
@@ -86,6 +107,8 @@ struct PassDesc {
   int32_t op_begin, op_end;
 };
 
+// Kernel attributes / occupancy of a pass's instance; host side, never during a capture.
+cudaError_t prepare_tile_pass(const PassDesc& p, qs_dtype dt);
 // Shared memory of one tile CTA: tile + run offsets + matrix staging buffer.
 size_t tile_smem_bytes(int m, int nhigh, int mbuf_elems, qs_dtype dt);
 
@@ -131,11 +154,12 @@ cudaError_t launch_gate(void* psi, int n, qs_dtype dt, const DevGate& g, const d
                         bool adjoint, cudaStream_t st);
 // Batched forms: psis = device array of nstates state pointers (psi unused);
 // gate table rows gstride apart. partials for expval: nstates * nz * cols.
-cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int n, qs_dtype dt,
-                                     const PassDesc& p, const DevOp* ops, const double2* gtab, const double2* btab,
-                                     cudaStream_t st);
-cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int n, const TcPassDesc& p,
-                                   const void* wimg, int prec, int* err, cudaStream_t st);
+cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
+                                     int n, qs_dtype dt, const PassDesc& p, const DevOp* ops, const double2* gtab,
+                                     const double2* btab, cudaStream_t st);
+// wstride (uint16 elements) between the W images of consecutive states; 0 = one image for all
+cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
+                                   const TcPassDesc& p, const void* wimg, int prec, int* err, cudaStream_t st);
 int expval_batched_blocks(int nstates);
 cudaError_t launch_expval_x_batched(const void* const* psis, int nstates, int n, qs_dtype dt, uint64_t xmask,
                                     const uint64_t* zm, int nz, double* partials, double* out, int64_t out_stride,

@@ -234,6 +234,28 @@ def test_parametric_circuits_both_fusion_policies(dtname):
             Q.qs_state_free(h)
 
 
+def test_parametric_tensor_core_blocks_built_on_device():
+    """Rotations folded into 6-qubit tensor-core blocks whose W images are
+    rebuilt on the device from theta at every execution."""
+    n = 14
+    gates, p = W.hea(n, 3)
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4,
+                                                            fuse_parametric=1))
+    h = Q.qs_state_alloc(n, Q.QS_C64)
+    try:
+        assert any(op["type"] == 3 for op in Q.qs_plan_ops(plan))
+        for seed in (1, 2):
+            theta = W.thetas_uniform(p, seed)
+            Q.qs_state_set_basis(h, 0)
+            Q.qs_plan_execute(plan, h, theta)
+            out = np.empty(1 << n, dtype=np.complex64)
+            Q.qs_state_copy_to_host(h, out)
+            assert np.abs(out - ref(n, gates, theta)).max() <= 2e-5
+    finally:
+        Q.qs_state_free(h)
+        Q.qs_plan_free(plan)
+
+
 def test_adjoint_hea_n24_full_size_against_device_parameter_shift():
     """Hardware-efficient ansatz at its full size (24 qubits, 12 layers, 576
     parameters, 150-term H): the adjoint gradient equals the two-term shift
@@ -271,9 +293,10 @@ def test_batched_graph_matches_sequential_and_oracle(dtname):
     gates, _ = W.ucc(n, nterms, 5, wmin=2, wmax=6)
     thetas = W.thetas_normal(nterms, 6, sigma=0.3, batch=Bsz)
     H = W.random_pauli_sum(n, 25, seed=8)
-    modes = [None, Q.make_opts(fuse_k=1), Q.make_opts(fuse_k=3)]
+    modes = [None, Q.make_opts(fuse_k=1), Q.make_opts(fuse_k=3), Q.make_opts(fuse_k=4, fuse_parametric=1)]
     if dt == Q.QS_C64:
         modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2))
+        modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
     for opts in modes:
         plan = Q.qs_plan_create(n, dt, gates, opts)
         states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
@@ -396,6 +419,24 @@ def test_state_diff_mixed_precision():
     finally:
         Q.qs_state_free(a)
         Q.qs_state_free(b)
+
+
+def test_autotuner_picks_a_valid_plan_and_caches_it():
+    n = 14
+    gates = W.random_layered(n, 6, seed=30)
+    h = Q.qs_state_alloc(n, Q.QS_C64)
+    try:
+        best, ms = Q.qs_plan_autotune(h, gates)
+        assert ms > 0
+        best2, ms2 = Q.qs_plan_autotune(h, gates)      # cached: same answer
+        assert Q.opts_dict(best) == Q.opts_dict(best2) and ms2 == ms
+        Q.qs_state_set_basis(h, 0)
+        Q.qs_apply_circuit(h, gates, None, best)
+        out = np.empty(1 << n, dtype=np.complex64)
+        Q.qs_state_copy_to_host(h, out)
+        assert np.abs(out - ref(n, gates)).max() <= 2e-5
+    finally:
+        Q.qs_state_free(h)
 
 
 def test_launch_counter_moves():
