@@ -482,8 +482,10 @@ def run_configs(Q, torch, np, args):
     H = W.random_pauli_sum(n, 300, seed=3)
     states = [Q.qs_state_alloc(n, Q.QS_C64, st) for _ in range(B)]
     c3 = {"workload": "UCC-style n=20 complex64, 400 terms, B=64, 300-term <H>", "gates": len(g)}
-    for name, opts in (("fused_k1", Q.make_opts(mode=F, fuse_k=1)), ("fused_k3", Q.make_opts(mode=F, fuse_k=3)),
-                       ("tensor", Q.make_opts(mode=T, tc_min_gates=2))):
+    for name, opts in (("fused_k1", Q.make_opts(mode=F, fuse_k=1)),
+                       ("fused_k4_device_blocks", Q.make_opts(mode=F, fuse_k=4, fuse_parametric=1)),
+                       ("tensor", Q.make_opts(mode=T, tc_min_gates=2)),
+                       ("tensor_device_blocks", Q.make_opts(mode=T, tc_min_gates=4, fuse_parametric=1))):
         plan = Q.qs_plan_create(n, Q.QS_C64, g, opts)
         def go():
             for sv in states:

@@ -132,7 +132,7 @@ __device__ __forceinline__ void issue_tile_mmas(uint32_t tmem_d, uint32_t ah, ui
 // column half h = w / 4 (complex columns 32h .. 32h + 31 = K atom h).
 constexpr int kTc2Threads = 256;
 
-template <int PREC>
+template <int PREC, bool MULTI>
 __global__ void __launch_bounds__(kTc2Threads, 1)
     k_tc_block(float2* __restrict__ psi0, void* const* __restrict__ psis, TcPassDesc p,
                const uint4* __restrict__ wimg, int64_t wstride16, int lg_tiles1, uint64_t ntiles,
@@ -142,9 +142,13 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
   // (wstride16 = uint4 stride, non-zero for parametric blocks) the image is
   // reloaded when the range crosses into the next state.
   const uint64_t tmask1 = (1ull << lg_tiles1) - 1;
+  // tile order: strided over the grid (t = blockIdx.x + i * gridDim.x) when one
+  // W image serves every tile; contiguous per CTA when W is per state
   const uint64_t chunk = (ntiles + gridDim.x - 1) / gridDim.x;
-  const uint64_t t_begin = (uint64_t)blockIdx.x * chunk;
-  const uint64_t t_end = t_begin + chunk < ntiles ? t_begin + chunk : ntiles;
+  const bool contig = MULTI && wstride16 != 0;
+  const uint64_t ts = contig ? 1 : gridDim.x;
+  const uint64_t t_begin = contig ? (uint64_t)blockIdx.x * chunk : blockIdx.x;
+  const uint64_t t_end = contig ? (t_begin + chunk < ntiles ? t_begin + chunk : ntiles) : ntiles;
   extern __shared__ __align__(1024) unsigned char tc_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tc_smem_raw + 1023) & ~(uintptr_t)1023);
   // A operands double-buffered: buffer b at smem + b * 2 * kTcOperandBytes (hi, then lo)
@@ -162,7 +166,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
     const uint4* src = wimg + (int64_t)state * wstride16;
     for (int i = tid; i < 2 * kTcOperandBytes / 16; i += kTc2Threads) ((uint4*)W_hi)[i] = src[i];
   };
-  load_w(wstride16 ? wstate : 0);
+  load_w(contig ? wstate : 0);
   if (tid < 64) {
     uint64_t o = 0;
     for (int b = 0; b < 6; ++b) o |= (uint64_t)((tid >> b) & 1) << p.col[b];
@@ -191,7 +195,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
   float2 va[32], vb[32];   // two tiles in flight: register double buffer
 
   auto state_of = [&](uint64_t t) -> float2* {
-    return psis ? (float2*)psis[t >> lg_tiles1] : psi0;
+    if constexpr (MULTI) return (float2*)psis[t >> lg_tiles1];
+    else return psi0;
   };
   auto load = [&](float2 (&v)[32], uint64_t t) {
     const float2* __restrict__ psi = state_of(t);
@@ -234,7 +239,7 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
   // one pipeline step for tile t (MMAs issued into accumulator b): `nxt`
   // holds tile t + g (in flight), `nn` receives tile t + 2g.
   auto step = [&](uint64_t t, int b, float2 (&nxt)[32], float2 (&nn)[32]) -> bool {
-    if (t + 2 < t_end) load(nn, t + 2);
+    if (t + 2 * ts < t_end) load(nn, t + 2 * ts);
     if (tid == 0 && !mbar_wait(smem_u32(mbar + b), phase[b])) {
       atomicExch(err, 1);
       s_abort = 1;
@@ -256,9 +261,9 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
         for (int q = 0; q < 16; ++q) psi[rb | hcoff[chunk * 16 + q]] = make_float2(o[2 * q], o[2 * q + 1]);
       }
     }
-    if (t + 1 < t_end) {
-      if (wstride16 && ((t + 1) >> lg_tiles1) != wstate) {   // previous MMAs are complete
-        wstate = (t + 1) >> lg_tiles1;
+    if (t + ts < t_end) {
+      if (contig && ((t + ts) >> lg_tiles1) != wstate) {   // previous MMAs are complete
+        wstate = (t + ts) >> lg_tiles1;
         load_w(wstate);
       }
       convert(nxt, b ^ 1);
@@ -273,15 +278,15 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
     load(va, t);
     convert(va, 0);
     issue(0);
-    if (t + 1 < t_end) load(va, t + 1);
+    if (t + ts < t_end) load(va, t + ts);
   }
   while (t < t_end) {
     if (!step(t, b, va, vb)) break;
-    t += 1;
+    t += ts;
     b ^= 1;
     if (t >= t_end) break;
     if (!step(t, b, vb, va)) break;
-    t += 1;
+    t += ts;
     b ^= 1;
   }
   // after a timeout, give outstanding MMAs a second bounded wait before
@@ -303,8 +308,10 @@ static int g_tc_sms = 0;
 cudaError_t prepare_tc_pass() {
   if (g_tc_ready) return cudaSuccess;
   const int smem = (int)tc_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_tc_block<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = cudaFuncSetAttribute(k_tc_block<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -320,12 +327,15 @@ cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, in
   const int sms = g_tc_sms;
   const uint64_t ntiles1 = 1ull << (n - 13), ntiles = ntiles1 * (uint64_t)nstates;
   const uint64_t grid = ntiles < (uint64_t)sms ? ntiles : (uint64_t)sms;
-  if (prec == 3)
-    k_tc_block<3><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, psis, p, (const uint4*)wimg, wstride / 8,
-                                                             n - 13, ntiles, err);
-  else
-    k_tc_block<1><<<(unsigned)grid, kTc2Threads, smem, st>>>((float2*)psi, psis, p, (const uint4*)wimg, wstride / 8,
-                                                             n - 13, ntiles, err);
+#define QS_TC_ARGS (float2*)psi, psis, p, (const uint4*)wimg, wstride / 8, n - 13, ntiles, err
+  if (psis) {
+    if (prec == 3) k_tc_block<3, true><<<(unsigned)grid, kTc2Threads, smem, st>>>(QS_TC_ARGS);
+    else k_tc_block<1, true><<<(unsigned)grid, kTc2Threads, smem, st>>>(QS_TC_ARGS);
+  } else {
+    if (prec == 3) k_tc_block<3, false><<<(unsigned)grid, kTc2Threads, smem, st>>>(QS_TC_ARGS);
+    else k_tc_block<1, false><<<(unsigned)grid, kTc2Threads, smem, st>>>(QS_TC_ARGS);
+  }
+#undef QS_TC_ARGS
   note_launch();
   return cudaGetLastError();
 }
