@@ -270,6 +270,41 @@ static uint64_t grow_qubits(const std::vector<HGate>& gates, const std::vector<c
   return Q;
 }
 
+// As grow_qubits, but each step may also add two qubits at once (a pair that
+// only pays off together, such as both ends of a two-qubit gate).
+static uint64_t grow_qubits_pairs(const std::vector<HGate>& gates, const std::vector<char>& done, int first,
+                                  int kcap, int n, const PlanOptions& o, uint64_t all) {
+  uint64_t Q = gates[first].qmask;
+  uint64_t cand = 0;
+  int seen = 0;
+  for (int h = first; h < (int)gates.size() && seen < 4 * n; ++h)
+    if (!done[h]) { cand |= gates[h].qmask; ++seen; }
+  std::vector<int> cq;
+  for (int q = 0; q < n; ++q)
+    if (cand & (1ull << q)) cq.push_back(q);
+  while (popc(Q) < kcap) {
+    uint64_t best_add = 0;
+    double best = 0;
+    for (size_t i = 0; i < cq.size(); ++i) {
+      const uint64_t a = 1ull << cq[i];
+      if (Q & a) continue;
+      const double c1 = (double)scan_block(gates, done, first, kcap, Q | a, o, all).size();
+      if (c1 > best) { best = c1; best_add = a; }
+      if (popc(Q) + 2 > kcap) continue;
+      for (size_t j = i + 1; j < cq.size(); ++j) {
+        const uint64_t b2 = 1ull << cq[j];
+        if (Q & b2) continue;
+        // a pair costs two slots: compare per added qubit, favouring progress
+        const double c2 = (double)scan_block(gates, done, first, kcap, Q | a | b2, o, all).size();
+        if (c2 - 0.5 > best) { best = c2 - 0.5; best_add = a | b2; }
+      }
+    }
+    if (!best_add) break;
+    Q |= best_add;
+  }
+  return Q;
+}
+
 std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOptions& o) {
   // A later gate may join the block (move ahead of the gates skipped so far)
   // when it commutes with every skipped gate: on each shared qubit both are
@@ -295,6 +330,11 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
       if (o.search) {
         std::vector<int> c = scan_block(gates, done, first, kcap, grow_qubits(gates, done, first, kcap, n, o, all), o, all);
         if (c.size() > a.size()) a.swap(c);
+        if (n <= 40 && gates.size() <= 4000) {
+          std::vector<int> d = scan_block(gates, done, first, kcap, grow_qubits_pairs(gates, done, first, kcap, n, o, all),
+                                          o, all);
+          if (d.size() > a.size()) a.swap(d);
+        }
       }
     }
     blk.gates = a;
