@@ -330,7 +330,7 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
       if (o.search) {
         std::vector<int> c = scan_block(gates, done, first, kcap, grow_qubits(gates, done, first, kcap, n, o, all), o, all);
         if (c.size() > a.size()) a.swap(c);
-        if (n <= 40 && gates.size() <= 4000) {
+        if (n <= 40 && gates.size() <= 40000) {
           std::vector<int> d = scan_block(gates, done, first, kcap, grow_qubits_pairs(gates, done, first, kcap, n, o, all),
                                           o, all);
           if (d.size() > a.size()) a.swap(d);
