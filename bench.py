@@ -46,7 +46,7 @@ def parse():
     ap.add_argument("--no-configs", action="store_true", help="skip the per-config side measurements")
     ap.add_argument("--full-configs", action="store_true",
                     help="also run the complex128 n=32 reference for the tensor-core config (64 GiB, ~1 min)")
-    ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates]")
+    ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
     return ap.parse_args()
 
 
@@ -245,6 +245,8 @@ def main():
         kw = dict(mode=F, fuse_k=parts[0], tile_qubits=parts[1], low_qubits=parts[2])
         if len(parts) > 3 and parts[3] > 0:
             kw.update(mode=T, tc_min_gates=parts[3])
+            if len(parts) > 4:
+                kw.update(tc_pipeline=parts[4])
         trials = None
     plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(**kw))
     info = Q.qs_plan_info_get(plan)
@@ -265,7 +267,8 @@ def main():
 
     # roofline of the kernel that dominates the timed region
     tc_dom = kern["tc_ms"] > kern["tile_ms"]
-    kname = "k_tc_block (tensor-core 6-qubit block pass)" if tc_dom else "k_tile (tile pass)"
+    tc_kernel = "k_tc_block" if kw.get("tc_pipeline", 0) == 1 else "k_tc_bulk"
+    kname = f"{tc_kernel} (tensor-core 6-qubit block pass)" if tc_dom else "k_tile (tile pass)"
     kms = (kern["tc_ms"] / max(1, kern["tc_launches"])) if tc_dom else (kern["tile_ms"] / max(1, kern["tile_launches"]))
     achieved = sweep_bytes / (kms * 1e-3) / 1e9
     eff_gbps = info["sweeps"] * sweep_bytes / (ms_step * 1e-3) / 1e9
@@ -361,7 +364,7 @@ def main():
     traffic = None
     if os.path.exists(prof):
         try:
-            tp = json.load(open(prof)).get("k_tc_block" if tc_dom else "k_tile", {})
+            tp = json.load(open(prof)).get(tc_kernel if tc_dom else "k_tile", {})
             if tp.get("kernel_hash") == kernel_hash():
                 traffic = tp.get("bytes_per_launch_n30")
         except (ValueError, OSError):

@@ -96,12 +96,16 @@ typedef struct {
   int32_t tile_qubits;   /* m: qubits staged per shared-memory tile (6..14); 0 = auto */
   int32_t low_qubits;    /* L: qubits 0..L-1 always in the tile (coalescing); 0 = auto */
   int32_t paper_mode;    /* 1 = contract only the merges of Section 3.4 (1q(x)1q, same-qubit, same-(c,t) CU) */
-  int32_t tc_precision;  /* tensor mode: 1 = bf16, 3 = bf16x3 split (default), 6 = bf16x6 split */
+  int32_t tc_precision;  /* tensor mode: 1 = bf16, 3 = bf16x3 split (default) */
   int32_t threads;       /* CUDA threads per tile CTA; 0 = auto */
-  int32_t fuse_parametric; /* 1 = parametric gates may join dense blocks (block matrices are then
-                              rebuilt on the host at every execution; not usable batched).
+  int32_t fuse_parametric; /* 1 = parametric gates may join dense blocks, whose matrices are then
+                              rebuilt from theta on the device at every execution (per batch row).
                               0 = they stay separate ops resolved from theta on the device. */
-  int32_t reserved[8];   /* reserved[0]: tensor mode, least gates per tensor-core block (0 = 10) */
+  int32_t reserved[8];   /* reserved[0]: tensor mode, least gates per tensor-core block (0 = 10).
+                            reserved[1]: tensor mode, single-state tensor-core pass pipeline:
+                            0 = tiles staged in shared memory by bulk asynchronous copies (default),
+                            1 = tiles staged in registers by the computing threads. Batched passes
+                            whose blocks depend on theta always use the register-staged kernel. */
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */

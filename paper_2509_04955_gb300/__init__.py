@@ -175,11 +175,13 @@ def _dptr(a):
 
 
 def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0,
-              fuse_parametric=0, tc_min_gates=0):
+              fuse_parametric=0, tc_min_gates=0, tc_pipeline=0):
+    """qs_plan_opts; tc_min_gates and tc_pipeline fill reserved[0] and reserved[1]."""
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
     o.paper_mode, o.tc_precision, o.fuse_parametric = paper_mode, tc_precision, fuse_parametric
     o.reserved[0] = tc_min_gates
+    o.reserved[1] = tc_pipeline
     return o
 
 
@@ -258,7 +260,7 @@ def qs_plan_autotune(state: int, gates, theta=None) -> tuple[QsPlanOpts, float]:
 
 def opts_dict(o: QsPlanOpts) -> dict:
     return {"mode": o.mode, "fuse_k": o.fuse_k, "tile_qubits": o.tile_qubits, "low_qubits": o.low_qubits,
-            "tc_min_gates": o.reserved[0], "tc_precision": o.tc_precision}
+            "tc_min_gates": o.reserved[0], "tc_precision": o.tc_precision, "tc_pipeline": o.reserved[1]}
 
 
 def qs_apply_circuit(state: int, gates, theta=None, opts: QsPlanOpts | None = None):

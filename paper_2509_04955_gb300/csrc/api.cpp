@@ -130,6 +130,7 @@ struct qs_plan_s {
   std::vector<TcPassDesc> tcdesc;
   std::vector<uint16_t> h_wimg;    // per TC pass: bf16 hi image then lo image (64 KiB)
   int tc_prec = 3;
+  int tc_pipe = 0;                 // single-state tensor-core pass: 0 bulk-copy staged, 1 register-staged
   int64_t btab_elems = 0;
   // blocks whose matrices depend on theta, rebuilt on the device per batch row
   std::vector<DevBlock> h_dblocks;
@@ -295,7 +296,7 @@ void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed
     } else {
       const int t = p.steps[i].idx;
       CK(launch_tc_pass(psi, p.n, p.tcdesc[t], p.d_wimg.as<uint16_t>() + (size_t)t * 32768, p.tc_prec,
-                        p.d_err.as<int>(), st));
+                        p.tc_pipe, p.d_err.as<int>(), st));
     }
     if (timed) CK(cudaEventRecord(p.next_event(), st));
   }
@@ -566,6 +567,8 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
     if (dt != QS_C64) throw Error(QS_ERR_UNSUPPORTED, "tensor-core mode needs complex64 states");
     require(o.tc_precision == 0 || o.tc_precision == 1 || o.tc_precision == 3, "tc_precision must be 1 or 3");
     p->tc_prec = o.tc_precision == 0 ? 3 : o.tc_precision;
+    require(o.reserved[1] == 0 || o.reserved[1] == 1, "tensor-core pipeline (reserved[1]) must be 0 or 1");
+    p->tc_pipe = o.reserved[1];
     if (n < 13) tensor = false;   // a tensor-core tile needs 13 qubits; smaller states use CUDA-core blocks
   }
   const int user_k = o.fuse_k;

@@ -298,6 +298,320 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 256;" ::"r"(tmem) : "memory");
 }
 
+// ---------------------------------------------------------------------------
+// Bulk-copy pipeline (single state). The register-staged kernel above reads
+// and writes the state with 8-byte accesses spread over the 128 rows of a
+// tile; its loads then reach about 0.8 of the copy bandwidth. Here a producer
+// warp moves each tile into shared memory with cp.async.bulk: the tile is a
+// set of 2^(13-p) runs of 2^p contiguous amplitudes (p >= 7: every qubit
+// below the 7th row qubit belongs to the tile), so every copy is at least
+// 1 KiB long and contiguous. Two landing slots of 64 KiB keep one tile in
+// flight while the previous one is converted.
+//   smem:  slot 0 | slot 1 | W hi | W lo | run/column tables | barriers
+//   TMEM:  A buffers 2 x (hi 64 + lo 64 columns), accumulators 2 x 128
+// The A operand (bf16 hi/lo of the tile, rows in lanes, K packed two per
+// column) lives in tensor memory and is written with tcgen05.st, which frees
+// the shared memory for the landing slots; W stays the smem B operand.
+// Warps 0-7 convert (slot -> TMEM A) and drain (TMEM D -> HBM), warp 8
+// issues the bulk copies, warp 9 issues the MMAs. A tile's slot is released
+// as soon as it is converted; the epilogue stores straight from registers.
+//
+// Slot reads: element (row, c) sits at tile-local index lambda = the
+// row and column bits deposited at their positions among the 13 tile qubits
+// (ascending). A warp's 32 rows read one column at a time; when block qubits
+// lie on qubits 0-3 (the low lambda bits, i.e. the shared-memory bank bits of
+// an 8-byte element) all lanes would hit the same banks, so each lane reads its
+// columns in an order XORed with phi(lane), built from lane bits whose row
+// qubits are >= 4, and restores the natural order in registers afterwards.
+
+constexpr int kTcbThreads = 320;
+constexpr int kTcbSlotBytes = 65536;
+constexpr uint32_t kTcbTmemCols = 512;
+
+__device__ __forceinline__ void mma_bf16_tmem_a(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(kIdesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
+  asm volatile(
+      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
+          taddr),
+      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
+      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
+      : "memory");
+}
+
+// Warp-uniform bounded wait: every lane polls, and the warp goes on only if
+// all lanes saw the phase complete (warp-collective tcgen05 ops follow).
+__device__ __forceinline__ bool mbar_wait_warp(uint32_t mbar, uint32_t phase) {
+  const bool ok = mbar_wait(mbar, phase);
+  return __all_sync(0xffffffffu, ok);
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
+
+// Issues the MMAs of one tile with A in tensor memory: D = A * W^T, K = 128.
+template <int PREC>
+__device__ __forceinline__ void issue_tile_mmas_ta(uint32_t tmem_d, uint32_t a_hi, uint32_t wh, uint32_t wl) {
+  const uint32_t a_lo = a_hi + 64;
+  uint32_t acc = 0;
+  if (PREC == 3) {
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks) {     // lo * hi
+      const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
+      mma_bf16_tmem_a(tmem_d, a_lo + ks * 8, smem_desc(wh + o), acc);
+      acc = 1;
+    }
+#pragma unroll
+    for (int ks = 0; ks < 8; ++ks) {     // hi * lo
+      const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
+      mma_bf16_tmem_a(tmem_d, a_hi + ks * 8, smem_desc(wl + o), 1);
+    }
+  }
+#pragma unroll
+  for (int ks = 0; ks < 8; ++ks) {       // hi * hi
+    const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
+    mma_bf16_tmem_a(tmem_d, a_hi + ks * 8, smem_desc(wh + o), acc);
+    acc = 1;
+  }
+}
+
+// Conditional swap of v[j] and v[j ^ (1 << B)] for every j with bit B clear.
+template <int B>
+__device__ __forceinline__ void xor_stage(float2 (&v)[16], bool on) {
+#pragma unroll
+  for (int j = 0; j < 16; ++j) {
+    if (j & (1 << B)) continue;
+    const float2 a = v[j], b = v[j | (1 << B)];
+    v[j] = on ? b : a;
+    v[j | (1 << B)] = on ? a : b;
+  }
+}
+
+template <int PREC>
+__global__ void __launch_bounds__(kTcbThreads, 1)
+    k_tc_bulk(float2* __restrict__ psi, TcPassDesc p, const uint4* __restrict__ wimg, uint64_t ntiles,
+              int* __restrict__ err) {
+  extern __shared__ __align__(1024) unsigned char tcb_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)tcb_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* slots = smem;                                   // 2 x 64 KiB
+  unsigned char* W_hi = smem + 2 * kTcbSlotBytes;
+  unsigned char* W_lo = W_hi + kTcOperandBytes;
+  uint64_t* runoff = (uint64_t*)(W_lo + kTcOperandBytes);       // 64: global offset of run j
+  uint64_t* coff = runoff + 64;                                  // 64: global offset of column c
+  uint32_t* lamcol = (uint32_t*)(coff + 64);                     // 64: tile-local index of column c
+  uint64_t* bar = (uint64_t*)(lamcol + 64);                      // full[2] empty[2] afull[2] mdone[2] dfree[2]
+  uint32_t* tmem_slot = (uint32_t*)(bar + 10);
+  __shared__ int s_abort;
+  __shared__ int s_p;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // tables: lambda(q) = position of qubit q among the 13 tile qubits
+  if (tid == 0) {
+    int pp = 0;
+    while (pp < 13 && p.tile[pp] == pp) ++pp;
+    s_p = pp;
+    s_abort = 0;
+    for (int i = 0; i < 10; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)),
+                   "r"((i >= 2 && i != 6 && i != 7) ? 8 : 1));   // empty/afull/dfree: 8 warps; full/mdone: 1
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  for (int i = tid; i < 2 * kTcOperandBytes / 16; i += kTcbThreads) ((uint4*)W_hi)[i] = wimg[i];
+  __syncthreads();
+  const int pr = s_p;                 // log2 of the run length in amplitudes (7..13)
+  const int nruns = 1 << (13 - pr);
+  if (tid < 64) {
+    uint64_t o = 0;
+    uint32_t lc = 0;
+    for (int b = 0; b < 6; ++b) {
+      o |= (uint64_t)((tid >> b) & 1) << p.col[b];
+      int lam = 0;
+      while (p.tile[lam] != p.col[b]) ++lam;
+      lc |= (uint32_t)((tid >> b) & 1) << lam;
+    }
+    coff[tid] = o;
+    lamcol[tid] = lc;
+    if (tid < nruns) {
+      uint64_t r = 0;
+      for (int b = 0; b < 13 - pr; ++b) r |= (uint64_t)((tid >> b) & 1) << p.tile[pr + b];
+      runoff[tid] = r;
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kTcbTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // W is read by the MMA (async proxy)
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  const uint64_t ts = gridDim.x;
+  const uint64_t my = ntiles > blockIdx.x ? (ntiles - blockIdx.x + ts - 1) / ts : 0;   // tiles of this CTA
+  uint64_t* full = bar;
+  uint64_t* empty = bar + 2;
+  uint64_t* afull = bar + 4;
+  uint64_t* mdone = bar + 6;
+  uint64_t* dfree = bar + 8;
+  auto fail = [&](int code) {
+    atomicExch(err, code);
+    *(volatile int*)&s_abort = 1;
+  };
+
+  if (warp == 8) {
+    // ---------------- producer: bulk copies of tile runs into the slots
+    const uint32_t runb = 8u << pr;
+    uint64_t i = 0;
+    for (; i < my; ++i) {
+      if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
+      const int s = (int)(i & 1);
+      if (i >= 2 && !mbar_wait_warp(smem_u32(empty + s), (uint32_t)(((i >> 1) - 1) & 1))) {
+        if (lane == 0) fail(1);
+        break;
+      }
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full + s)),
+                     "r"((uint32_t)kTcbSlotBytes)
+                     : "memory");
+      __syncwarp();
+      const uint64_t base = insert_zero_bits(blockIdx.x + i * ts, p.tile, 13);
+      for (int j = lane; j < nruns; j += 32)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(slots + s * kTcbSlotBytes + j * runb)),
+            "l"(psi + (base | runoff[j])), "r"(runb), "r"(smem_u32(full + s))
+            : "memory");
+    }
+    // after an abort, the copies already issued land before the CTA exits
+    if (*(volatile int*)&s_abort)
+      for (uint64_t k = i > 2 ? i - 2 : 0; k < i; ++k) mbar_wait(smem_u32(full + (k & 1)), (uint32_t)((k >> 1) & 1));
+  } else if (warp == 9) {
+    // ---------------- MMA issue (one thread)
+    if (lane == 0) {
+      const uint32_t wh = smem_u32(W_hi), wl = smem_u32(W_lo);
+      uint64_t i = 0;
+      for (; i < my; ++i) {
+        if (*(volatile int*)&s_abort) break;
+        const int a = (int)(i & 1);
+        if (!mbar_wait(smem_u32(afull + a), (uint32_t)((i >> 1) & 1))) { fail(1); break; }
+        if (i >= 2 && !mbar_wait(smem_u32(dfree + a), (uint32_t)(((i >> 1) - 1) & 1))) { fail(1); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        issue_tile_mmas_ta<PREC>(tmem + 256 + a * 128, tmem + a * 128, wh, wl);
+        mma_commit(smem_u32(mdone + a));
+      }
+      // MMAs still in flight after an abort complete before the memory is released
+      if (i > 0 && *(volatile int*)&s_abort) mbar_wait(smem_u32(mdone + ((i - 1) & 1)), (uint32_t)(((i - 1) >> 1) & 1));
+    }
+  } else {
+    // ---------------- warps 0-7: convert and drain; thread = (row, column half)
+    const int row = (warp & 3) * 32 + lane, half = warp >> 2;
+    uint32_t lrow = 0;
+    uint64_t roff = 0;
+    for (int b = 0; b < 7; ++b) {
+      int lam = 0;
+      while (p.tile[lam] != p.row[b]) ++lam;
+      lrow |= (uint32_t)((row >> b) & 1) << lam;
+      roff |= (uint64_t)((row >> b) & 1) << p.row[b];
+    }
+    // phi: column bits on qubits 0-3 take lane bits whose row qubits are >= 4
+    uint32_t phi = 0, xbits = 0;
+    {
+      int k = 0;
+      for (int b = 0; b < 4; ++b) {
+        if (p.col[b] > 3) break;
+        while (k < 5 && p.row[k] < 4) ++k;
+        if (k >= 5) break;
+        phi |= (uint32_t)((lane >> k) & 1) << b;
+        xbits |= 1u << b;
+        ++k;
+      }
+    }
+    const uint32_t tb = lrow | lamcol[half * 32] | lamcol[phi];
+    const uint32_t tq = (uint32_t)((warp & 3) * 32) << 16;
+    const float2* slot_f = (const float2*)slots;
+
+    auto convert = [&](uint64_t i) -> bool {
+      const int s = (int)(i & 1);
+      if (!mbar_wait_warp(smem_u32(full + s), (uint32_t)((i >> 1) & 1))) return false;
+      const float2* sl = slot_f + s * (kTcbSlotBytes / 8);
+      const uint32_t a_hi = tmem + tq + (uint32_t)(i & 1) * 128 + half * 32;
+#pragma unroll
+      for (int chunk = 0; chunk < 2; ++chunk) {
+        float2 v[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) v[j] = sl[tb ^ lamcol[chunk * 16 + j]];
+        if (xbits & 1) xor_stage<0>(v, phi & 1);
+        if (xbits & 2) xor_stage<1>(v, (phi >> 1) & 1);
+        if (xbits & 4) xor_stage<2>(v, (phi >> 2) & 1);
+        if (xbits & 8) xor_stage<3>(v, (phi >> 3) & 1);
+        uint32_t hi[16], lo[16];
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(v[j].x, v[j].y);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(v[j].x - hf.x, v[j].y - hf.y);
+          hi[j] = *(const uint32_t*)&h;
+          lo[j] = *(const uint32_t*)&l;
+        }
+        tmem_st16(a_hi + chunk * 16, hi);
+        if (PREC == 3) tmem_st16(a_hi + 64 + chunk * 16, lo);
+      }
+      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(smem_u32(empty + s));
+        mbar_arrive(smem_u32(afull + s));
+      }
+      return true;
+    };
+    auto drain = [&](uint64_t i) -> bool {
+      const int d = (int)(i & 1);
+      if (!mbar_wait_warp(smem_u32(mdone + d), (uint32_t)((i >> 1) & 1))) return false;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint64_t rb = insert_zero_bits(blockIdx.x + i * ts, p.tile, 13) | roff;
+      const uint32_t taddr = tmem + tq + 256 + d * 128 + half * 64;
+      const uint64_t* hc = coff + half * 32;
+#pragma unroll
+      for (int chunk = 0; chunk < 2; ++chunk) {
+        float o[32];
+        tmem_ld32(taddr + chunk * 32, o);
+#pragma unroll
+        for (int q = 0; q < 16; ++q) psi[rb | hc[chunk * 16 + q]] = make_float2(o[2 * q], o[2 * q + 1]);
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(dfree + d));
+      return true;
+    };
+
+    bool ok = my == 0 || convert(0);
+    for (uint64_t i = 0; ok && i < my; ++i) {
+      if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
+      if (i + 1 < my && !convert(i + 1)) { ok = false; break; }
+      if (!drain(i)) { ok = false; break; }
+    }
+    if (!ok && lane == 0) fail(1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTcbTmemCols) : "memory");
+}
+
+size_t tc_bulk_smem_bytes() {
+  return 2 * (size_t)kTcbSlotBytes + 2 * (size_t)kTcOperandBytes + 64 * 8 * 2 + 64 * 4 + 10 * 8 + 16 + 1024;
+}
+
 size_t tc_smem_bytes() { return 6 * (size_t)kTcOperandBytes + 64 * 8 + 32 + 1024; }
 
 static bool g_tc_ready = false;
@@ -312,6 +626,9 @@ cudaError_t prepare_tc_pass() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const int smem_bulk = (int)tc_bulk_smem_bytes();
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
   if (e != cudaSuccess) return e;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -340,9 +657,19 @@ cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, in
   return cudaGetLastError();
 }
 
-cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int* err,
-                           cudaStream_t st) {
-  return launch_tc_pass_batched(psi, nullptr, 1, 0, n, p, wimg, prec, err, st);
+cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int pipeline,
+                           int* err, cudaStream_t st) {
+  if (pipeline == 1) return launch_tc_pass_batched(psi, nullptr, 1, 0, n, p, wimg, prec, err, st);
+  if (!g_tc_ready) return cudaErrorInvalidConfiguration;   // not prepared
+  const uint64_t ntiles = 1ull << (n - 13);
+  const uint64_t grid = ntiles < (uint64_t)g_tc_sms ? ntiles : (uint64_t)g_tc_sms;
+  const size_t smem = tc_bulk_smem_bytes();
+  if (prec == 3)
+    k_tc_bulk<3><<<(unsigned)grid, kTcbThreads, smem, st>>>((float2*)psi, p, (const uint4*)wimg, ntiles, err);
+  else
+    k_tc_bulk<1><<<(unsigned)grid, kTcbThreads, smem, st>>>((float2*)psi, p, (const uint4*)wimg, ntiles, err);
+  note_launch();
+  return cudaGetLastError();
 }
 
 }  // namespace qs

@@ -81,9 +81,11 @@ struct TcPassDesc {
   int32_t col[6];          // block qubits, ascending (bit j of the column index = local bit j)
   int32_t tile[13];        // row and column qubits together, ascending
 };
-cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int* err,
-                           cudaStream_t st);
+// pipeline 0: bulk-copy staged kernel (k_tc_bulk); 1: register-staged kernel (k_tc_block)
+cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int pipeline,
+                           int* err, cudaStream_t st);
 size_t tc_smem_bytes();
+size_t tc_bulk_smem_bytes();
 
 struct DevOp {
   int32_t type;

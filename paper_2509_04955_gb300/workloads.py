@@ -241,6 +241,20 @@ def random_gate_mix(n: int, ngates: int, seed: int, max_controls: int = 2) -> li
     return gates
 
 
+def block_circuit(qubit_sets, gates_per_block: int, seed: int) -> list[Gate]:
+    """For each qubit set in turn, a chain of random dense two-qubit (u2)
+    gates on random pairs inside the set: a contraction to blocks of
+    len(set) qubits sees one block per set, on exactly those qubits."""
+    rng = _rng(seed)
+    gates: list[Gate] = []
+    for qs in qubit_sets:
+        qs = [int(q) for q in qs]
+        for _ in range(gates_per_block):
+            a, b = (int(x) for x in rng.choice(len(qs), size=2, replace=False))
+            gates.append(Gate("u2", (qs[a], qs[b]), matrix=tuple(random_unitary(4, rng).reshape(-1))))
+    return gates
+
+
 def inverse_circuit(gates: list[Gate], theta=None) -> list[Gate]:
     """The circuit whose product is the inverse: reversed order, each gate inverted.
 

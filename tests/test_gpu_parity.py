@@ -322,9 +322,8 @@ def test_tensor_core_mode_split_bf16_matches_oracle(n, depth, ent):
     gates = W.random_layered(n, depth, seed=n, entangler=ent)
     psi0 = W.random_state(n, 2)
     want = ref(n, gates, psi0=psi0.astype(np.complex64).astype(complex))
-    for tmin in (6, 10):
-        opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_precision=3)
-        opts.reserved[0] = tmin
+    for tmin, pipe in ((6, 0), (10, 0), (6, 1)):
+        opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_precision=3, tc_min_gates=tmin, tc_pipeline=pipe)
         plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
         try:
             assert any(op["type"] == 3 for op in Q.qs_plan_ops(plan))
@@ -339,6 +338,46 @@ def test_tensor_core_mode_split_bf16_matches_oracle(n, depth, ent):
         finally:
             Q.qs_plan_free(plan)
         assert np.abs(out - want).max() <= 2e-5
+
+
+# Block placements covering 4, 3, 2, 1 and 0 block qubits among qubits 0-3
+# (the shared-memory bank bits of the bulk-copy kernel's slot reads), plus
+# blocks entirely above the row qubits.
+BLOCK_SETS = [(0, 1, 2, 3, 4, 5), (0, 1, 2, 9, 10, 11), (1, 3, 7, 9, 11, 12), (0, 7, 8, 9, 10, 11),
+              (7, 8, 9, 10, 11, 12), (2, 4, 5, 6, 8, 12)]
+
+
+@pytest.mark.parametrize("n", [13, 14, 17])
+def test_tensor_core_pipelines_on_every_block_placement(n):
+    """Dense 6-qubit blocks on the placements above (and, for n = 17, on the
+    six highest qubits): the bulk-copy and the register-staged tensor-core
+    kernels against the oracle (complex64 bar 2e-5) and against each other.
+    Both round the same operands to bf16 and issue the same MMAs, so they
+    agree to FP32 accumulation-order level (2^-20 of the largest amplitude)."""
+    sets = list(BLOCK_SETS) + ([tuple(range(n - 6, n))] if n > 13 else [])
+    gates = W.block_circuit(sets, 12, seed=n)
+    psi0 = W.random_state(n, 4).astype(np.complex64)
+    want = ref(n, gates, psi0=psi0.astype(complex))
+    outs = []
+    for pipe in (0, 1):
+        opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=6, tc_pipeline=pipe)
+        plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
+        try:
+            tc_sets = [tuple(sorted(op["qubits"])) for op in Q.qs_plan_ops(plan) if op["type"] == 3]
+            assert len(tc_sets) == len(sets)
+            h = Q.qs_state_alloc(n, Q.QS_C64)
+            try:
+                Q.qs_state_copy_from_host(h, psi0)
+                Q.qs_plan_execute(plan, h)
+                out = np.empty(1 << n, dtype=np.complex64)
+                Q.qs_state_copy_to_host(h, out)
+            finally:
+                Q.qs_state_free(h)
+        finally:
+            Q.qs_plan_free(plan)
+        assert np.abs(out - want).max() <= 2e-5
+        outs.append(out)
+    assert np.abs(outs[0] - outs[1]).max() <= 2.0 ** -20 * np.abs(want).max()
 
 
 def test_tensor_core_plain_bf16_error_bound():
