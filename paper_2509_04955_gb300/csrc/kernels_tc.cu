@@ -312,19 +312,23 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
 // The A operand (bf16 hi/lo of the tile, rows in lanes, K packed two per
 // column) lives in tensor memory and is written with tcgen05.st, which frees
 // the shared memory for the landing slots; W stays the smem B operand.
-// Warps 0-7 convert (slot -> TMEM A) and drain (TMEM D -> HBM), warp 8
-// issues the bulk copies, warp 9 issues the MMAs. A tile's slot is released
-// as soon as it is converted; the epilogue stores straight from registers.
+// Warps 0-15 convert (slot -> TMEM A) and drain (TMEM D -> HBM), one thread
+// per (row, quarter of the columns); warp 16 issues the bulk copies, warp 17
+// the MMAs. A tile's slot is released as soon as it is converted; the
+// epilogue stores straight from registers. The global offset of a tile is
+// looked up byte by byte in tables built once per CTA.
 //
 // Slot reads: element (row, c) sits at tile-local index lambda = the
 // row and column bits deposited at their positions among the 13 tile qubits
-// (ascending). A warp's 32 rows read one column at a time; when block qubits
+// (ascending). A warp's 32 rows read one column at a time (16 columns per
+// thread: bits 0-3 of c vary inside the thread); when block qubits
 // lie on qubits 0-3 (the low lambda bits, i.e. the shared-memory bank bits of
 // an 8-byte element) all lanes would hit the same banks, so each lane reads its
 // columns in an order XORed with phi(lane), built from lane bits whose row
 // qubits are >= 4, and restores the natural order in registers afterwards.
 
-constexpr int kTcbThreads = 320;
+constexpr int kTcbComputeWarps = 16;                     // 4 per TMEM lane quadrant
+constexpr int kTcbThreads = (kTcbComputeWarps + 2) * 32;  // + producer warp + MMA warp
 constexpr int kTcbSlotBytes = 65536;
 constexpr uint32_t kTcbTmemCols = 512;
 
@@ -403,44 +407,62 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
   unsigned char* slots = smem;                                   // 2 x 64 KiB
   unsigned char* W_hi = smem + 2 * kTcbSlotBytes;
   unsigned char* W_lo = W_hi + kTcOperandBytes;
-  uint64_t* runoff = (uint64_t*)(W_lo + kTcOperandBytes);       // 64: global offset of run j
+  uint64_t* tbase = (uint64_t*)(W_lo + kTcOperandBytes);        // 4 x 256: tile number byte k -> offset
+  uint64_t* runoff = tbase + 4 * 256;                            // 64: global offset of run j
   uint64_t* coff = runoff + 64;                                  // 64: global offset of column c
   uint32_t* lamcol = (uint32_t*)(coff + 64);                     // 64: tile-local index of column c
-  uint64_t* bar = (uint64_t*)(lamcol + 64);                      // full[2] empty[2] afull[2] mdone[2] dfree[2]
+  int32_t* qpos = (int32_t*)(lamcol + 64);                       // tile[13], row[7], col[6], p, pad
+  uint64_t* bar = (uint64_t*)(qpos + 28);                        // full[2] empty[2] afull[2] mdone[2] dfree[2]
   uint32_t* tmem_slot = (uint32_t*)(bar + 10);
   __shared__ int s_abort;
-  __shared__ int s_p;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  // tables: lambda(q) = position of qubit q among the 13 tile qubits
+  int32_t* s_tile = qpos;
+  int32_t* s_row = qpos + 13;
+  int32_t* s_col = qpos + 20;
   if (tid == 0) {
+    for (int k = 0; k < 13; ++k) s_tile[k] = p.tile[k];
+    for (int k = 0; k < 7; ++k) s_row[k] = p.row[k];
+    for (int k = 0; k < 6; ++k) s_col[k] = p.col[k];
     int pp = 0;
     while (pp < 13 && p.tile[pp] == pp) ++pp;
-    s_p = pp;
+    qpos[26] = pp;
     s_abort = 0;
     for (int i = 0; i < 10; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)),
-                   "r"((i >= 2 && i != 6 && i != 7) ? 8 : 1));   // empty/afull/dfree: 8 warps; full/mdone: 1
+                   "r"((i >= 2 && i != 6 && i != 7) ? kTcbComputeWarps : 1));   // full/mdone: 1 arrival
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   for (int i = tid; i < 2 * kTcOperandBytes / 16; i += kTcbThreads) ((uint4*)W_hi)[i] = wimg[i];
   __syncthreads();
-  const int pr = s_p;                 // log2 of the run length in amplitudes (7..13)
+  const int pr = qpos[26];            // log2 of the run length in amplitudes (7..13)
   const int nruns = 1 << (13 - pr);
+  // lambda(q) = position of qubit q among the 13 tile qubits (ascending)
+  auto lam_of = [&](int q) {
+    int l = 0;
+    while (l < 12 && s_tile[l] != q) ++l;
+    return l;
+  };
+  for (int e = tid; e < 4 * 256; e += kTcbThreads) {
+    uint64_t x = (uint64_t)(e & 255) << (8 * (e >> 8));
+    for (int k = 0; k < 13; ++k) {
+      const int q = s_tile[k];
+      x = ((x >> q) << (q + 1)) | (x & ((1ull << q) - 1));
+    }
+    tbase[e] = x;
+  }
   if (tid < 64) {
     uint64_t o = 0;
     uint32_t lc = 0;
     for (int b = 0; b < 6; ++b) {
-      o |= (uint64_t)((tid >> b) & 1) << p.col[b];
-      int lam = 0;
-      while (p.tile[lam] != p.col[b]) ++lam;
-      lc |= (uint32_t)((tid >> b) & 1) << lam;
+      o |= (uint64_t)((tid >> b) & 1) << s_col[b];
+      lc |= (uint32_t)((tid >> b) & 1) << lam_of(s_col[b]);
     }
     coff[tid] = o;
     lamcol[tid] = lc;
     if (tid < nruns) {
       uint64_t r = 0;
-      for (int b = 0; b < 13 - pr; ++b) r |= (uint64_t)((tid >> b) & 1) << p.tile[pr + b];
+      for (int b = 0; b < 13 - pr; ++b) r |= (uint64_t)((tid >> b) & 1) << s_tile[pr + b];
       runoff[tid] = r;
     }
   }
@@ -466,8 +488,13 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
     atomicExch(err, code);
     *(volatile int*)&s_abort = 1;
   };
+  // global offset of tile t's amplitude with tile-local bits all zero
+  auto tile_base = [&](uint64_t t) -> uint64_t {
+    return tbase[t & 255] | tbase[256 + ((t >> 8) & 255)] | tbase[512 + ((t >> 16) & 255)] |
+           tbase[768 + ((t >> 24) & 255)];
+  };
 
-  if (warp == 8) {
+  if (warp == kTcbComputeWarps) {
     // ---------------- producer: bulk copies of tile runs into the slots
     const uint32_t runb = 8u << pr;
     uint64_t i = 0;
@@ -483,7 +510,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
                      "r"((uint32_t)kTcbSlotBytes)
                      : "memory");
       __syncwarp();
-      const uint64_t base = insert_zero_bits(blockIdx.x + i * ts, p.tile, 13);
+      const uint64_t base = tile_base(blockIdx.x + i * ts);
       for (int j = lane; j < nruns; j += 32)
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
@@ -494,7 +521,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
     // after an abort, the copies already issued land before the CTA exits
     if (*(volatile int*)&s_abort)
       for (uint64_t k = i > 2 ? i - 2 : 0; k < i; ++k) mbar_wait(smem_u32(full + (k & 1)), (uint32_t)((k >> 1) & 1));
-  } else if (warp == 9) {
+  } else if (warp == kTcbComputeWarps + 1) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
       const uint32_t wh = smem_u32(W_hi), wl = smem_u32(W_lo);
@@ -512,59 +539,55 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
       if (i > 0 && *(volatile int*)&s_abort) mbar_wait(smem_u32(mdone + ((i - 1) & 1)), (uint32_t)(((i - 1) >> 1) & 1));
     }
   } else {
-    // ---------------- warps 0-7: convert and drain; thread = (row, column half)
-    const int row = (warp & 3) * 32 + lane, half = warp >> 2;
+    // ---------------- compute warps: convert and drain; thread = (row, column quarter)
+    const int row = (warp & 3) * 32 + lane, quarter = warp >> 2;
     uint32_t lrow = 0;
     uint64_t roff = 0;
     for (int b = 0; b < 7; ++b) {
-      int lam = 0;
-      while (p.tile[lam] != p.row[b]) ++lam;
-      lrow |= (uint32_t)((row >> b) & 1) << lam;
-      roff |= (uint64_t)((row >> b) & 1) << p.row[b];
+      lrow |= (uint32_t)((row >> b) & 1) << lam_of(s_row[b]);
+      roff |= (uint64_t)((row >> b) & 1) << s_row[b];
     }
     // phi: column bits on qubits 0-3 take lane bits whose row qubits are >= 4
     uint32_t phi = 0, xbits = 0;
     {
       int k = 0;
       for (int b = 0; b < 4; ++b) {
-        if (p.col[b] > 3) break;
-        while (k < 5 && p.row[k] < 4) ++k;
+        if (s_col[b] > 3) break;
+        while (k < 5 && s_row[k] < 4) ++k;
         if (k >= 5) break;
         phi |= (uint32_t)((lane >> k) & 1) << b;
         xbits |= 1u << b;
         ++k;
       }
     }
-    const uint32_t tb = lrow | lamcol[half * 32] | lamcol[phi];
+    const uint32_t tb = lrow | lamcol[quarter * 16] | lamcol[phi];
     const uint32_t tq = (uint32_t)((warp & 3) * 32) << 16;
     const float2* slot_f = (const float2*)slots;
+    const uint64_t* qc = coff + quarter * 16;
 
     auto convert = [&](uint64_t i) -> bool {
       const int s = (int)(i & 1);
       if (!mbar_wait_warp(smem_u32(full + s), (uint32_t)((i >> 1) & 1))) return false;
       const float2* sl = slot_f + s * (kTcbSlotBytes / 8);
-      const uint32_t a_hi = tmem + tq + (uint32_t)(i & 1) * 128 + half * 32;
+      const uint32_t a_hi = tmem + tq + (uint32_t)s * 128 + quarter * 16;
+      float2 v[16];
 #pragma unroll
-      for (int chunk = 0; chunk < 2; ++chunk) {
-        float2 v[16];
+      for (int j = 0; j < 16; ++j) v[j] = sl[tb ^ lamcol[j]];
+      if (xbits & 1) xor_stage<0>(v, phi & 1);
+      if (xbits & 2) xor_stage<1>(v, (phi >> 1) & 1);
+      if (xbits & 4) xor_stage<2>(v, (phi >> 2) & 1);
+      if (xbits & 8) xor_stage<3>(v, (phi >> 3) & 1);
+      uint32_t hi[16], lo[16];
 #pragma unroll
-        for (int j = 0; j < 16; ++j) v[j] = sl[tb ^ lamcol[chunk * 16 + j]];
-        if (xbits & 1) xor_stage<0>(v, phi & 1);
-        if (xbits & 2) xor_stage<1>(v, (phi >> 1) & 1);
-        if (xbits & 4) xor_stage<2>(v, (phi >> 2) & 1);
-        if (xbits & 8) xor_stage<3>(v, (phi >> 3) & 1);
-        uint32_t hi[16], lo[16];
-#pragma unroll
-        for (int j = 0; j < 16; ++j) {
-          const __nv_bfloat162 h = __floats2bfloat162_rn(v[j].x, v[j].y);
-          const float2 hf = __bfloat1622float2(h);
-          const __nv_bfloat162 l = __floats2bfloat162_rn(v[j].x - hf.x, v[j].y - hf.y);
-          hi[j] = *(const uint32_t*)&h;
-          lo[j] = *(const uint32_t*)&l;
-        }
-        tmem_st16(a_hi + chunk * 16, hi);
-        if (PREC == 3) tmem_st16(a_hi + 64 + chunk * 16, lo);
+      for (int j = 0; j < 16; ++j) {
+        const __nv_bfloat162 h = __floats2bfloat162_rn(v[j].x, v[j].y);
+        const float2 hf = __bfloat1622float2(h);
+        const __nv_bfloat162 l = __floats2bfloat162_rn(v[j].x - hf.x, v[j].y - hf.y);
+        hi[j] = *(const uint32_t*)&h;
+        lo[j] = *(const uint32_t*)&l;
       }
+      tmem_st16(a_hi, hi);
+      if (PREC == 3) tmem_st16(a_hi + 64, lo);
       asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
@@ -578,19 +601,14 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
       const int d = (int)(i & 1);
       if (!mbar_wait_warp(smem_u32(mdone + d), (uint32_t)((i >> 1) & 1))) return false;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint64_t rb = insert_zero_bits(blockIdx.x + i * ts, p.tile, 13) | roff;
-      const uint32_t taddr = tmem + tq + 256 + d * 128 + half * 64;
-      const uint64_t* hc = coff + half * 32;
-#pragma unroll
-      for (int chunk = 0; chunk < 2; ++chunk) {
-        float o[32];
-        tmem_ld32(taddr + chunk * 32, o);
-#pragma unroll
-        for (int q = 0; q < 16; ++q) psi[rb | hc[chunk * 16 + q]] = make_float2(o[2 * q], o[2 * q + 1]);
-      }
+      float o[32];
+      tmem_ld32(tmem + tq + 256 + d * 128 + quarter * 32, o);
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(dfree + d));
+      if (lane == 0) mbar_arrive(smem_u32(dfree + d));   // accumulator read; stores follow
+      const uint64_t rb = tile_base(blockIdx.x + i * ts) | roff;
+#pragma unroll
+      for (int q = 0; q < 16; ++q) psi[rb | qc[q]] = make_float2(o[2 * q], o[2 * q + 1]);
       return true;
     };
 
@@ -609,7 +627,8 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
 }
 
 size_t tc_bulk_smem_bytes() {
-  return 2 * (size_t)kTcbSlotBytes + 2 * (size_t)kTcOperandBytes + 64 * 8 * 2 + 64 * 4 + 10 * 8 + 16 + 1024;
+  return 2 * (size_t)kTcbSlotBytes + 2 * (size_t)kTcOperandBytes + 4 * 256 * 8 + 64 * 8 * 2 + 64 * 4 + 28 * 4 +
+         10 * 8 + 16 + 1024;
 }
 
 size_t tc_smem_bytes() { return 6 * (size_t)kTcOperandBytes + 64 * 8 + 32 + 1024; }
