@@ -19,6 +19,24 @@ namespace qs {
 constexpr int kRedThreads = 256;
 constexpr int kRedBlocks = 152 * 4;
 constexpr int kRun = 32;
+constexpr int kUnroll = 4;   // independent 16-byte loads per thread per iteration (bytes in flight)
+
+// 16-byte vector of amplitudes: two complex64 or one complex128.
+template <typename R> struct Vec16;
+template <> struct Vec16<float> {
+  using T = float4;
+  static constexpr int amps = 2;
+  __device__ __forceinline__ static float2 amp(const float4& v, int k) {
+    return k == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w);
+  }
+};
+template <> struct Vec16<double> {
+  using T = double2;
+  static constexpr int amps = 1;
+  __device__ __forceinline__ static double2 amp(const double2& v, int) { return v; }
+};
+
+__device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 int reduce_blocks() { return kRedBlocks; }
 
@@ -56,14 +74,42 @@ template <> struct Acc<float> {
 
 // ---------------------------------------------------------------- norm / inner
 
+// Each thread walks its vectors in a fixed order, kUnroll loads at a time
+// (grid stride), so the result is the same on every run.
 template <typename R>
 __global__ void __launch_bounds__(kRedThreads) k_norm(const typename V2<R>::T* __restrict__ psi, uint64_t dim,
                                                        double* __restrict__ partials) {
+  using VT = typename Vec16<R>::T;
+  constexpr int A = Vec16<R>::amps;
   Acc<R> acc;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
-    const auto v = psi[i];
-    acc.add(v.x * v.x + v.y * v.y);
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (aligned16(psi) && dim % A == 0) {
+    const VT* __restrict__ pv = (const VT*)psi;
+    const uint64_t nv = dim / A;
+    for (uint64_t b = g; b < nv; b += stride * kUnroll) {
+      VT v[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint64_t idx = b + u * stride;
+        v[u] = idx < nv ? pv[idx] : VT{};
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        R s = 0;
+#pragma unroll
+        for (int k = 0; k < A; ++k) {
+          const auto a = Vec16<R>::amp(v[u], k);
+          s += a.x * a.x + a.y * a.y;
+        }
+        acc.add(s);
+      }
+    }
+  } else {
+    for (uint64_t i = g; i < dim; i += stride) {
+      const auto v = psi[i];
+      acc.add(v.x * v.x + v.y * v.y);
+    }
   }
   const double s = block_sum(acc.total());
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
@@ -73,12 +119,42 @@ template <typename R>
 __global__ void __launch_bounds__(kRedThreads) k_inner(const typename V2<R>::T* __restrict__ a,
                                                         const typename V2<R>::T* __restrict__ b, uint64_t dim,
                                                         double* __restrict__ partials) {
+  using VT = typename Vec16<R>::T;
+  constexpr int A = Vec16<R>::amps;
   Acc<R> re, im;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
-    const auto x = a[i], y = b[i];
-    re.add(x.x * y.x + x.y * y.y);   // conj(x) * y
-    im.add(x.x * y.y - x.y * y.x);
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (aligned16(a) && aligned16(b) && dim % A == 0) {
+    const VT* __restrict__ av = (const VT*)a;
+    const VT* __restrict__ bv = (const VT*)b;
+    const uint64_t nv = dim / A;
+    for (uint64_t base = g; base < nv; base += stride * kUnroll) {
+      VT va[kUnroll], vb[kUnroll];
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint64_t idx = base + u * stride;
+        va[u] = idx < nv ? av[idx] : VT{};
+        vb[u] = idx < nv ? bv[idx] : VT{};
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        R sr = 0, si = 0;
+#pragma unroll
+        for (int k = 0; k < A; ++k) {
+          const auto x = Vec16<R>::amp(va[u], k), y = Vec16<R>::amp(vb[u], k);
+          sr += x.x * y.x + x.y * y.y;   // conj(x) * y
+          si += x.x * y.y - x.y * y.x;
+        }
+        re.add(sr);
+        im.add(si);
+      }
+    }
+  } else {
+    for (uint64_t i = g; i < dim; i += stride) {
+      const auto x = a[i], y = b[i];
+      re.add(x.x * y.x + x.y * y.y);   // conj(x) * y
+      im.add(x.x * y.y - x.y * y.x);
+    }
   }
   const double sr = block_sum(re.total());
   const double si = block_sum(im.total());
@@ -198,28 +274,77 @@ __global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::
   __syncthreads();
   Acc<R> acc[kMaxZ];
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x == 0) {
+    using VT = typename Vec16<R>::T;
+    constexpr int A = Vec16<R>::amps;
     const uint64_t dim = 1ull << n;
-    for (uint64_t i = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; i < dim; i += stride) {
-      const auto a = psi[i];
-      const R p = a.x * a.x + a.y * a.y;
+    if (aligned16(psi) && dim % A == 0) {
+      const VT* __restrict__ pv = (const VT*)psi;
+      const uint64_t nv = dim / A;
+      for (uint64_t b = g; b < nv; b += stride * kUnroll) {
+        VT v[kUnroll];
 #pragma unroll
-      for (int k = 0; k < kMaxZ; ++k)
-        if (k < nz) acc[k].add((__popcll(i & z_s[k]) & 1) ? -p : p);
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint64_t idx = b + u * stride;
+          v[u] = idx < nv ? pv[idx] : VT{};
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint64_t i0 = (b + u * stride) * A;
+#pragma unroll
+          for (int k = 0; k < kMaxZ; ++k) {
+            if (k < nz) {
+              R s = 0;
+#pragma unroll
+              for (int e = 0; e < A; ++e) {
+                const auto a = Vec16<R>::amp(v[u], e);
+                const R p = a.x * a.x + a.y * a.y;
+                s += (__popcll((i0 + e) & z_s[k]) & 1) ? -p : p;
+              }
+              acc[k].add(s);
+            }
+          }
+        }
+      }
+    } else {
+      for (uint64_t i = g; i < dim; i += stride) {
+        const auto a = psi[i];
+        const R p = a.x * a.x + a.y * a.y;
+#pragma unroll
+        for (int k = 0; k < kMaxZ; ++k)
+          if (k < nz) acc[k].add((__popcll(i & z_s[k]) & 1) ? -p : p);
+      }
     }
   } else {
     const int32_t hb = 63 - __clzll((long long)x);
     const uint64_t count = 1ull << (n - 1);
-    for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += stride) {
-      const uint64_t i = ((p >> hb) << (hb + 1)) | (p & ((1ull << hb) - 1));
-      const auto a = psi[i], b = psi[i ^ x];
-      const R wr = b.x * a.x + b.y * a.y;   // Re(conj(b) a)
-      const R wi = b.x * a.y - b.y * a.x;   // Im(conj(b) a)
+    for (uint64_t p0 = g; p0 < count; p0 += stride * kUnroll) {
+      typename V2<R>::T a[kUnroll], b[kUnroll];
 #pragma unroll
-      for (int k = 0; k < kMaxZ; ++k) {
-        if (k < nz) {
-          const R v = odd_s[k] ? wi : wr;
-          acc[k].add((__popcll(i & z_s[k]) & 1) ? -v : v);
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint64_t p = p0 + u * stride;
+        const uint64_t i = ((p >> hb) << (hb + 1)) | (p & ((1ull << hb) - 1));
+        if (p < count) {
+          a[u] = psi[i];
+          b[u] = psi[i ^ x];
+        } else {
+          a[u] = mk<R>(0, 0);
+          b[u] = mk<R>(0, 0);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < kUnroll; ++u) {
+        const uint64_t p = p0 + u * stride;
+        const uint64_t i = ((p >> hb) << (hb + 1)) | (p & ((1ull << hb) - 1));
+        const R wr = b[u].x * a[u].x + b[u].y * a[u].y;   // Re(conj(b) a)
+        const R wi = b[u].x * a[u].y - b[u].y * a[u].x;   // Im(conj(b) a)
+#pragma unroll
+        for (int k = 0; k < kMaxZ; ++k) {
+          if (k < nz) {
+            const R v = odd_s[k] ? wi : wr;
+            acc[k].add((__popcll(i & z_s[k]) & 1) ? -v : v);
+          }
         }
       }
     }
