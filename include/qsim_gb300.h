@@ -102,10 +102,10 @@ typedef struct {
                               rebuilt from theta on the device at every execution (per batch row).
                               0 = they stay separate ops resolved from theta on the device. */
   int32_t reserved[8];   /* reserved[0]: tensor mode, least gates per tensor-core block (0 = 10).
-                            reserved[1]: tensor mode, single-state tensor-core pass pipeline:
-                            0 = tiles staged in shared memory by bulk asynchronous copies (default),
-                            1 = tiles staged in registers by the computing threads. Batched passes
-                            whose blocks depend on theta always use the register-staged kernel. */
+                            reserved[1]: tensor mode, tensor-core pass pipeline (single and batched
+                            executions): 0 = tiles staged in shared memory by bulk asynchronous
+                            copies (default), 1 = tiles staged in registers by the computing
+                            threads. */
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */

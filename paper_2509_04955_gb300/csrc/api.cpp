@@ -315,7 +315,7 @@ void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_
     else
       CK(launch_tc_pass_batched(nullptr, d_psis, B, p.tc_param[stp.idx] ? (int64_t)p.h_wimg.size() : 0, p.n,
                                 p.tcdesc[stp.idx], p.d_wimg.as<uint16_t>() + (size_t)stp.idx * 32768, p.tc_prec,
-                                p.d_err.as<int>(), st));
+                                p.tc_pipe, p.d_err.as<int>(), st));
   }
 }
 

@@ -6,8 +6,10 @@
 //
 // Every reduction runs on a fixed grid (reduce_blocks() CTAs) so the partial
 // sums, and therefore the FP64 result, do not depend on timing. complex64
-// states accumulate short runs in FP32 (at most kRun terms) and carry the
-// running total in FP64; complex128 states accumulate in FP64. Partials are
+// states accumulate runs of kRun terms in FP32 and add each run into an FP64
+// total; complex128 states accumulate in FP64. The runs are explicit inner
+// loops, so the FP64 add happens once per run and not, predicated, once per
+// term (GB300's FP64 pipe is about 1/60 of its FP32 rate). Partials are
 // combined in FP64 by one CTA in a fixed order.
 #include <cuda_runtime.h>
 
@@ -54,23 +56,7 @@ __device__ __forceinline__ double block_sum(double v) {
   return s;
 }
 
-// Accumulator: FP32 runs folded into FP64 for float states, FP64 for double.
-template <typename R> struct Acc;
-template <> struct Acc<double> {
-  double t = 0;
-  __device__ __forceinline__ void add(double v) { t += v; }
-  __device__ __forceinline__ double total() const { return t; }
-};
-template <> struct Acc<float> {
-  double t = 0;
-  float run = 0;
-  int cnt = 0;
-  __device__ __forceinline__ void add(float v) {
-    run += v;
-    if (++cnt == kRun) { t += (double)run; run = 0; cnt = 0; }
-  }
-  __device__ __forceinline__ double total() const { return t + (double)run; }
-};
+constexpr int kRunIters = kRun / kUnroll;   // vector iterations per FP32 run
 
 // ---------------------------------------------------------------- norm / inner
 
@@ -81,37 +67,44 @@ __global__ void __launch_bounds__(kRedThreads) k_norm(const typename V2<R>::T* _
                                                        double* __restrict__ partials) {
   using VT = typename Vec16<R>::T;
   constexpr int A = Vec16<R>::amps;
-  Acc<R> acc;
+  double tot = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (aligned16(psi) && dim % A == 0) {
     const VT* __restrict__ pv = (const VT*)psi;
     const uint64_t nv = dim / A;
-    for (uint64_t b = g; b < nv; b += stride * kUnroll) {
-      VT v[kUnroll];
+    for (uint64_t b = g; b < nv;) {
+      R run = 0;
+#pragma unroll 1
+      for (int it = 0; it < kRunIters && b < nv; ++it, b += stride * kUnroll) {
+        VT v[kUnroll];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const uint64_t idx = b + u * stride;
-        v[u] = idx < nv ? pv[idx] : VT{};
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        R s = 0;
-#pragma unroll
-        for (int k = 0; k < A; ++k) {
-          const auto a = Vec16<R>::amp(v[u], k);
-          s += a.x * a.x + a.y * a.y;
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint64_t idx = b + u * stride;
+          v[u] = idx < nv ? pv[idx] : VT{};
         }
-        acc.add(s);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+          for (int k = 0; k < A; ++k) {
+            const auto a = Vec16<R>::amp(v[u], k);
+            run += a.x * a.x + a.y * a.y;
+          }
       }
+      tot += (double)run;
     }
   } else {
-    for (uint64_t i = g; i < dim; i += stride) {
-      const auto v = psi[i];
-      acc.add(v.x * v.x + v.y * v.y);
+    for (uint64_t i = g; i < dim;) {
+      R run = 0;
+#pragma unroll 1
+      for (int it = 0; it < kRun && i < dim; ++it, i += stride) {
+        const auto v = psi[i];
+        run += v.x * v.x + v.y * v.y;
+      }
+      tot += (double)run;
     }
   }
-  const double s = block_sum(acc.total());
+  const double s = block_sum(tot);
   if (threadIdx.x == 0) partials[blockIdx.x] = s;
 }
 
@@ -121,43 +114,51 @@ __global__ void __launch_bounds__(kRedThreads) k_inner(const typename V2<R>::T* 
                                                         double* __restrict__ partials) {
   using VT = typename Vec16<R>::T;
   constexpr int A = Vec16<R>::amps;
-  Acc<R> re, im;
+  double tre = 0, tim = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (aligned16(a) && aligned16(b) && dim % A == 0) {
     const VT* __restrict__ av = (const VT*)a;
     const VT* __restrict__ bv = (const VT*)b;
     const uint64_t nv = dim / A;
-    for (uint64_t base = g; base < nv; base += stride * kUnroll) {
-      VT va[kUnroll], vb[kUnroll];
+    for (uint64_t base = g; base < nv;) {
+      R rr = 0, ri = 0;
+#pragma unroll 1
+      for (int it = 0; it < kRunIters && base < nv; ++it, base += stride * kUnroll) {
+        VT va[kUnroll], vb[kUnroll];
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const uint64_t idx = base + u * stride;
-        va[u] = idx < nv ? av[idx] : VT{};
-        vb[u] = idx < nv ? bv[idx] : VT{};
-      }
-#pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        R sr = 0, si = 0;
-#pragma unroll
-        for (int k = 0; k < A; ++k) {
-          const auto x = Vec16<R>::amp(va[u], k), y = Vec16<R>::amp(vb[u], k);
-          sr += x.x * y.x + x.y * y.y;   // conj(x) * y
-          si += x.x * y.y - x.y * y.x;
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint64_t idx = base + u * stride;
+          va[u] = idx < nv ? av[idx] : VT{};
+          vb[u] = idx < nv ? bv[idx] : VT{};
         }
-        re.add(sr);
-        im.add(si);
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+          for (int k = 0; k < A; ++k) {
+            const auto x = Vec16<R>::amp(va[u], k), y = Vec16<R>::amp(vb[u], k);
+            rr += x.x * y.x + x.y * y.y;   // conj(x) * y
+            ri += x.x * y.y - x.y * y.x;
+          }
       }
+      tre += (double)rr;
+      tim += (double)ri;
     }
   } else {
-    for (uint64_t i = g; i < dim; i += stride) {
-      const auto x = a[i], y = b[i];
-      re.add(x.x * y.x + x.y * y.y);   // conj(x) * y
-      im.add(x.x * y.y - x.y * y.x);
+    for (uint64_t i = g; i < dim;) {
+      R rr = 0, ri = 0;
+#pragma unroll 1
+      for (int it = 0; it < kRun && i < dim; ++it, i += stride) {
+        const auto x = a[i], y = b[i];
+        rr += x.x * y.x + x.y * y.y;   // conj(x) * y
+        ri += x.x * y.y - x.y * y.x;
+      }
+      tre += (double)rr;
+      tim += (double)ri;
     }
   }
-  const double sr = block_sum(re.total());
-  const double si = block_sum(im.total());
+  const double sr = block_sum(tre);
+  const double si = block_sum(tim);
   if (threadIdx.x == 0) { partials[blockIdx.x] = sr; partials[kRedBlocks + blockIdx.x] = si; }
 }
 
@@ -272,7 +273,17 @@ __global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::
     odd_s[threadIdx.x] = __popcll(x & zm[threadIdx.x]) & 1;
   }
   __syncthreads();
-  Acc<R> acc[kMaxZ];
+  double tot[kMaxZ];
+  R run[kMaxZ];
+#pragma unroll
+  for (int k = 0; k < kMaxZ; ++k) tot[k] = 0;
+  auto fold = [&]() {
+#pragma unroll
+    for (int k = 0; k < kMaxZ; ++k) {
+      if (k < nz) tot[k] += (double)run[k];
+      run[k] = 0;
+    }
+  };
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
   const uint64_t g = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (x == 0) {
@@ -282,76 +293,92 @@ __global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::
     if (aligned16(psi) && dim % A == 0) {
       const VT* __restrict__ pv = (const VT*)psi;
       const uint64_t nv = dim / A;
-      for (uint64_t b = g; b < nv; b += stride * kUnroll) {
-        VT v[kUnroll];
+      for (uint64_t b = g; b < nv;) {
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const uint64_t idx = b + u * stride;
-          v[u] = idx < nv ? pv[idx] : VT{};
-        }
+        for (int k = 0; k < kMaxZ; ++k) run[k] = 0;
+#pragma unroll 1
+        for (int it = 0; it < kRunIters && b < nv; ++it, b += stride * kUnroll) {
+          VT v[kUnroll];
 #pragma unroll
-        for (int u = 0; u < kUnroll; ++u) {
-          const uint64_t i0 = (b + u * stride) * A;
+          for (int u = 0; u < kUnroll; ++u) {
+            const uint64_t idx = b + u * stride;
+            v[u] = idx < nv ? pv[idx] : VT{};
+          }
 #pragma unroll
-          for (int k = 0; k < kMaxZ; ++k) {
-            if (k < nz) {
-              R s = 0;
+          for (int u = 0; u < kUnroll; ++u) {
+            const uint64_t i0 = (b + u * stride) * A;
 #pragma unroll
-              for (int e = 0; e < A; ++e) {
-                const auto a = Vec16<R>::amp(v[u], e);
-                const R p = a.x * a.x + a.y * a.y;
-                s += (__popcll((i0 + e) & z_s[k]) & 1) ? -p : p;
-              }
-              acc[k].add(s);
+            for (int e = 0; e < A; ++e) {
+              const auto a = Vec16<R>::amp(v[u], e);
+              const R p = a.x * a.x + a.y * a.y;
+#pragma unroll
+              for (int k = 0; k < kMaxZ; ++k)
+                if (k < nz) run[k] += (__popcll((i0 + e) & z_s[k]) & 1) ? -p : p;
             }
           }
         }
+        fold();
       }
     } else {
-      for (uint64_t i = g; i < dim; i += stride) {
-        const auto a = psi[i];
-        const R p = a.x * a.x + a.y * a.y;
+      for (uint64_t i = g; i < dim;) {
 #pragma unroll
-        for (int k = 0; k < kMaxZ; ++k)
-          if (k < nz) acc[k].add((__popcll(i & z_s[k]) & 1) ? -p : p);
+        for (int k = 0; k < kMaxZ; ++k) run[k] = 0;
+#pragma unroll 1
+        for (int it = 0; it < kRun && i < dim; ++it, i += stride) {
+          const auto a = psi[i];
+          const R p = a.x * a.x + a.y * a.y;
+#pragma unroll
+          for (int k = 0; k < kMaxZ; ++k)
+            if (k < nz) run[k] += (__popcll(i & z_s[k]) & 1) ? -p : p;
+        }
+        fold();
       }
     }
   } else {
     const int32_t hb = 63 - __clzll((long long)x);
     const uint64_t count = 1ull << (n - 1);
-    for (uint64_t p0 = g; p0 < count; p0 += stride * kUnroll) {
-      typename V2<R>::T a[kUnroll], b[kUnroll];
+    for (uint64_t p0 = g; p0 < count;) {
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const uint64_t p = p0 + u * stride;
-        const uint64_t i = ((p >> hb) << (hb + 1)) | (p & ((1ull << hb) - 1));
-        if (p < count) {
-          a[u] = psi[i];
-          b[u] = psi[i ^ x];
-        } else {
-          a[u] = mk<R>(0, 0);
-          b[u] = mk<R>(0, 0);
+      for (int k = 0; k < kMaxZ; ++k) run[k] = 0;
+#pragma unroll 1
+      for (int it = 0; it < kRunIters && p0 < count; ++it, p0 += stride * kUnroll) {
+        typename V2<R>::T a[kUnroll], b[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint64_t p = p0 + u * stride;
+          const uint64_t i = ((p >> hb) << (hb + 1)) | (p & ((1ull << hb) - 1));
+          if (p < count) {
+            a[u] = psi[i];
+            b[u] = psi[i ^ x];
+          } else {
+            a[u] = mk<R>(0, 0);
+            b[u] = mk<R>(0, 0);
+          }
         }
-      }
 #pragma unroll
-      for (int u = 0; u < kUnroll; ++u) {
-        const uint64_t p = p0 + u * stride;
-        const uint64_t i = ((p >> hb) << (hb + 1)) | (p & ((1ull << hb) - 1));
-        const R wr = b[u].x * a[u].x + b[u].y * a[u].y;   // Re(conj(b) a)
-        const R wi = b[u].x * a[u].y - b[u].y * a[u].x;   // Im(conj(b) a)
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint64_t p = p0 + u * stride;
+          const uint64_t i = ((p >> hb) << (hb + 1)) | (p & ((1ull << hb) - 1));
+          const R wr = b[u].x * a[u].x + b[u].y * a[u].y;   // Re(conj(b) a)
+          const R wi = b[u].x * a[u].y - b[u].y * a[u].x;   // Im(conj(b) a)
 #pragma unroll
-        for (int k = 0; k < kMaxZ; ++k) {
-          if (k < nz) {
-            const R v = odd_s[k] ? wi : wr;
-            acc[k].add((__popcll(i & z_s[k]) & 1) ? -v : v);
+          for (int k = 0; k < kMaxZ; ++k) {
+            if (k < nz) {
+              const R v = odd_s[k] ? wi : wr;
+              run[k] += (__popcll(i & z_s[k]) & 1) ? -v : v;
+            }
           }
         }
       }
+      fold();
     }
   }
-  for (int k = 0; k < nz; ++k) {
-    const double s = block_sum(acc[k].total());
-    if (threadIdx.x == 0) partials[(int64_t)k * gridDim.x + blockIdx.x] = s;
+#pragma unroll
+  for (int k = 0; k < kMaxZ; ++k) {
+    if (k < nz) {
+      const double s = block_sum(tot[k]);
+      if (threadIdx.x == 0) partials[(int64_t)k * gridDim.x + blockIdx.x] = s;
+    }
   }
 }
 
@@ -478,26 +505,31 @@ __global__ void __launch_bounds__(kRedThreads) k_adjoint_step(typename V2<R>::T*
   C d00 = mk<R>(0, 0), d01 = d00, d10 = d00, d11 = d00;
   if (grad) { d00 = from_d<R>(dmat[0]); d01 = from_d<R>(dmat[1]); d10 = from_d<R>(dmat[2]); d11 = from_d<R>(dmat[3]); }
   const uint64_t tb = 1ull << g.t0;
-  Acc<R> acc;
+  double tot = 0;
   const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += stride) {
-    const uint64_t i0 = insert_zero_bits_u<4>(p, g.ins, g.nins) | g.cmask, i1 = i0 | tb;
-    const C f0 = phi[i0], f1 = phi[i1];
-    const C p0 = cfma(a01, f1, cmul(a00, f0));
-    const C p1 = cfma(a11, f1, cmul(a10, f0));
-    phi[i0] = p0;
-    phi[i1] = p1;
-    const C l0 = lam[i0], l1 = lam[i1];
-    if (grad) {
-      const C m0 = cfma(d01, p1, cmul(d00, p0));
-      const C m1 = cfma(d11, p1, cmul(d10, p0));
-      acc.add(l0.x * m0.x + l0.y * m0.y + l1.x * m1.x + l1.y * m1.y);   // Re(conj(l) m)
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count;) {
+    R run = 0;
+#pragma unroll 1
+    for (int it = 0; it < kRun && p < count; ++it, p += stride) {
+      const uint64_t i0 = insert_zero_bits_u<4>(p, g.ins, g.nins) | g.cmask, i1 = i0 | tb;
+      const C f0 = phi[i0], f1 = phi[i1];
+      const C l0 = lam[i0], l1 = lam[i1];
+      const C p0 = cfma(a01, f1, cmul(a00, f0));
+      const C p1 = cfma(a11, f1, cmul(a10, f0));
+      phi[i0] = p0;
+      phi[i1] = p1;
+      if (grad) {
+        const C m0 = cfma(d01, p1, cmul(d00, p0));
+        const C m1 = cfma(d11, p1, cmul(d10, p0));
+        run += l0.x * m0.x + l0.y * m0.y + l1.x * m1.x + l1.y * m1.y;   // Re(conj(l) m)
+      }
+      lam[i0] = cfma(a01, l1, cmul(a00, l0));
+      lam[i1] = cfma(a11, l1, cmul(a10, l0));
     }
-    lam[i0] = cfma(a01, l1, cmul(a00, l0));
-    lam[i1] = cfma(a11, l1, cmul(a10, l0));
+    tot += (double)run;
   }
   if (grad) {
-    const double s = block_sum(acc.total());
+    const double s = block_sum(tot);
     if (threadIdx.x == 0) partials[blockIdx.x] = s;
   }
 }

@@ -166,7 +166,8 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
     const uint4* src = wimg + (int64_t)state * wstride16;
     for (int i = tid; i < 2 * kTcOperandBytes / 16; i += kTc2Threads) ((uint4*)W_hi)[i] = src[i];
   };
-  load_w(contig ? wstate : 0);
+  // a trailing CTA can get an empty range that starts past the last state
+  if (t_begin < t_end) load_w(contig ? wstate : 0);
   if (tid < 64) {
     uint64_t o = 0;
     for (int b = 0; b < 6; ++b) o |= (uint64_t)((tid >> b) & 1) << p.col[b];
@@ -312,16 +313,18 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
 // The A operand (bf16 hi/lo of the tile, rows in lanes, K packed two per
 // column) lives in tensor memory and is written with tcgen05.st, which frees
 // the shared memory for the landing slots; W stays the smem B operand.
-// Warps 0-15 convert (slot -> TMEM A) and drain (TMEM D -> HBM), one thread
-// per (row, quarter of the columns); warp 16 issues the bulk copies, warp 17
-// the MMAs. A tile's slot is released as soon as it is converted; the
-// epilogue stores straight from registers. The global offset of a tile is
-// looked up byte by byte in tables built once per CTA.
+// Warps 0-7 convert (slot -> TMEM A), warps 8-15 drain (TMEM D -> HBM), one
+// thread per (row, column half) in each group; warp 16 issues the bulk
+// copies, warp 17 the MMAs. Converting and draining run concurrently: a
+// tile's slot is released as soon as it is converted, its accumulator as
+// soon as it is read, and the epilogue stores straight from registers. The
+// global offset of a tile is looked up byte by byte in tables built once per
+// CTA.
 //
 // Slot reads: element (row, c) sits at tile-local index lambda = the
 // row and column bits deposited at their positions among the 13 tile qubits
-// (ascending). A warp's 32 rows read one column at a time (16 columns per
-// thread: bits 0-3 of c vary inside the thread); when block qubits
+// (ascending). A warp's 32 rows read one column at a time (16-column chunks:
+// bits 0-3 of c vary inside the thread); when block qubits
 // lie on qubits 0-3 (the low lambda bits, i.e. the shared-memory bank bits of
 // an 8-byte element) all lanes would hit the same banks, so each lane reads its
 // columns in an order XORed with phi(lane), built from lane bits whose row
@@ -398,9 +401,15 @@ __device__ __forceinline__ void xor_stage(float2 (&v)[16], bool on) {
   }
 }
 
-template <int PREC>
+// Batched execution (MULTI): tile index tt covers state tt >> lg_tiles1 of
+// `psis`; with per-state W images (wstride16 != 0, blocks rebuilt from each
+// state's theta) every CTA takes a contiguous range of tiles and the producer
+// reloads W by bulk copy when the range crosses into the next state, once the
+// MMAs of the previous tile have completed.
+template <int PREC, bool MULTI>
 __global__ void __launch_bounds__(kTcbThreads, 1)
-    k_tc_bulk(float2* __restrict__ psi, TcPassDesc p, const uint4* __restrict__ wimg, uint64_t ntiles,
+    k_tc_bulk(float2* __restrict__ psi0, void* const* __restrict__ psis, TcPassDesc p,
+              const uint4* __restrict__ wimg, int64_t wstride16, int lg_tiles1, uint64_t ntiles,
               int* __restrict__ err) {
   extern __shared__ __align__(1024) unsigned char tcb_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tcb_smem_raw + 1023) & ~(uintptr_t)1023);
@@ -412,8 +421,8 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
   uint64_t* coff = runoff + 64;                                  // 64: global offset of column c
   uint32_t* lamcol = (uint32_t*)(coff + 64);                     // 64: tile-local index of column c
   int32_t* qpos = (int32_t*)(lamcol + 64);                       // tile[13], row[7], col[6], p, pad
-  uint64_t* bar = (uint64_t*)(qpos + 28);                        // full[2] empty[2] afull[2] mdone[2] dfree[2]
-  uint32_t* tmem_slot = (uint32_t*)(bar + 10);
+  uint64_t* bar = (uint64_t*)(qpos + 28);   // full[2] empty[2] afull[2] mdone[2] dfree[2] wfull
+  uint32_t* tmem_slot = (uint32_t*)(bar + 11);
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -428,12 +437,23 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
     while (pp < 13 && p.tile[pp] == pp) ++pp;
     qpos[26] = pp;
     s_abort = 0;
-    for (int i = 0; i < 10; ++i)
+    for (int i = 0; i < 11; ++i)   // full/mdone/wfull: 1 arrival; empty/afull/dfree: one per warp of a group
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)),
-                   "r"((i >= 2 && i != 6 && i != 7) ? kTcbComputeWarps : 1));   // full/mdone: 1 arrival
+                   "r"((i >= 2 && i != 6 && i != 7 && i != 10) ? kTcbComputeWarps / 2 : 1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  for (int i = tid; i < 2 * kTcOperandBytes / 16; i += kTcbThreads) ((uint4*)W_hi)[i] = wimg[i];
+  // tile sequence of this CTA: tt = t_begin + i * tstep, i < my
+  const uint64_t tmask1 = (1ull << lg_tiles1) - 1;
+  const bool contig = MULTI && wstride16 != 0;
+  const uint64_t chunk_t = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t t_begin = contig ? (uint64_t)blockIdx.x * chunk_t : blockIdx.x;
+  const uint64_t tstep = contig ? 1 : gridDim.x;
+  const uint64_t t_end = contig ? (t_begin + chunk_t < ntiles ? t_begin + chunk_t : ntiles) : ntiles;
+  const uint64_t my = t_begin < t_end ? (t_end - t_begin + tstep - 1) / tstep : 0;
+  if (my > 0) {   // a trailing CTA can get an empty range that starts past the last state
+    const uint4* w0 = wimg + (contig ? (int64_t)(t_begin >> lg_tiles1) * wstride16 : 0);
+    for (int i = tid; i < 2 * kTcOperandBytes / 16; i += kTcbThreads) ((uint4*)W_hi)[i] = w0[i];
+  }
   __syncthreads();
   const int pr = qpos[26];            // log2 of the run length in amplitudes (7..13)
   const int nruns = 1 << (13 - pr);
@@ -477,13 +497,21 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = *tmem_slot;
-  const uint64_t ts = gridDim.x;
-  const uint64_t my = ntiles > blockIdx.x ? (ntiles - blockIdx.x + ts - 1) / ts : 0;   // tiles of this CTA
   uint64_t* full = bar;
   uint64_t* empty = bar + 2;
   uint64_t* afull = bar + 4;
   uint64_t* mdone = bar + 6;
   uint64_t* dfree = bar + 8;
+  uint64_t* wfull = bar + 10;
+  auto tile_of = [&](uint64_t i) -> uint64_t { return t_begin + i * tstep; };
+  auto state_ptr = [&](uint64_t tt) -> float2* {
+    if constexpr (MULTI) return (float2*)psis[tt >> lg_tiles1];
+    else return psi0;
+  };
+  // does tile i start a new state (W image reload)?
+  auto new_state = [&](uint64_t i) -> bool {
+    return contig && i > 0 && (tile_of(i) >> lg_tiles1) != (tile_of(i - 1) >> lg_tiles1);
+  };
   auto fail = [&](int code) {
     atomicExch(err, code);
     *(volatile int*)&s_abort = 1;
@@ -497,7 +525,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
   if (warp == kTcbComputeWarps) {
     // ---------------- producer: bulk copies of tile runs into the slots
     const uint32_t runb = 8u << pr;
-    uint64_t i = 0;
+    uint64_t i = 0, w_issued = 0;
     for (; i < my; ++i) {
       if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
       const int s = (int)(i & 1);
@@ -510,25 +538,53 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
                      "r"((uint32_t)kTcbSlotBytes)
                      : "memory");
       __syncwarp();
-      const uint64_t base = tile_base(blockIdx.x + i * ts);
+      const uint64_t tt = tile_of(i);
+      const float2* src = state_ptr(tt) + tile_base(tt & tmask1);
       for (int j = lane; j < nruns; j += 32)
         asm volatile(
             "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
                 smem_u32(slots + s * kTcbSlotBytes + j * runb)),
-            "l"(psi + (base | runoff[j])), "r"(runb), "r"(smem_u32(full + s))
+            "l"(src + runoff[j]), "r"(runb), "r"(smem_u32(full + s))
             : "memory");
+      if (new_state(i)) {
+        // W of the next state: once the MMAs of tile i - 1 (the last on the old W) are done
+        if (!mbar_wait_warp(smem_u32(mdone + ((i - 1) & 1)), (uint32_t)(((i - 1) >> 1) & 1))) {
+          if (lane == 0) fail(1);
+          ++i;   // tile i's copies are in flight
+          break;
+        }
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(wfull)),
+                       "r"((uint32_t)(2 * kTcOperandBytes))
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(W_hi)),
+              "l"(wimg + (int64_t)(tt >> lg_tiles1) * wstride16), "r"((uint32_t)(2 * kTcOperandBytes)),
+              "r"(smem_u32(wfull))
+              : "memory");
+        }
+        ++w_issued;
+        __syncwarp();
+      }
     }
     // after an abort, the copies already issued land before the CTA exits
-    if (*(volatile int*)&s_abort)
+    if (*(volatile int*)&s_abort) {
       for (uint64_t k = i > 2 ? i - 2 : 0; k < i; ++k) mbar_wait(smem_u32(full + (k & 1)), (uint32_t)((k >> 1) & 1));
+      if (w_issued > 0) mbar_wait(smem_u32(wfull), (uint32_t)((w_issued - 1) & 1));
+    }
   } else if (warp == kTcbComputeWarps + 1) {
     // ---------------- MMA issue (one thread)
     if (lane == 0) {
       const uint32_t wh = smem_u32(W_hi), wl = smem_u32(W_lo);
-      uint64_t i = 0;
+      uint64_t i = 0, w_seen = 0;
       for (; i < my; ++i) {
         if (*(volatile int*)&s_abort) break;
         const int a = (int)(i & 1);
+        if (new_state(i)) {
+          if (!mbar_wait(smem_u32(wfull), (uint32_t)(w_seen & 1))) { fail(1); break; }
+          ++w_seen;
+        }
         if (!mbar_wait(smem_u32(afull + a), (uint32_t)((i >> 1) & 1))) { fail(1); break; }
         if (i >= 2 && !mbar_wait(smem_u32(dfree + a), (uint32_t)(((i >> 1) - 1) & 1))) { fail(1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
@@ -539,84 +595,95 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
       if (i > 0 && *(volatile int*)&s_abort) mbar_wait(smem_u32(mdone + ((i - 1) & 1)), (uint32_t)(((i - 1) >> 1) & 1));
     }
   } else {
-    // ---------------- compute warps: convert and drain; thread = (row, column quarter)
-    const int row = (warp & 3) * 32 + lane, quarter = warp >> 2;
-    uint32_t lrow = 0;
-    uint64_t roff = 0;
-    for (int b = 0; b < 7; ++b) {
-      lrow |= (uint32_t)((row >> b) & 1) << lam_of(s_row[b]);
-      roff |= (uint64_t)((row >> b) & 1) << s_row[b];
-    }
-    // phi: column bits on qubits 0-3 take lane bits whose row qubits are >= 4
-    uint32_t phi = 0, xbits = 0;
-    {
-      int k = 0;
-      for (int b = 0; b < 4; ++b) {
-        if (s_col[b] > 3) break;
-        while (k < 5 && s_row[k] < 4) ++k;
-        if (k >= 5) break;
-        phi |= (uint32_t)((lane >> k) & 1) << b;
-        xbits |= 1u << b;
-        ++k;
+    // ---------------- warps 0-15: thread = (row, column half)
+    //   warps 0-7 convert (slot -> TMEM A), warps 8-15 drain (TMEM D -> HBM)
+    const bool converter = warp < kTcbComputeWarps / 2;
+    const int w8 = converter ? warp : warp - kTcbComputeWarps / 2;
+    const int row = (w8 & 3) * 32 + lane, half = w8 >> 2;
+    const uint32_t tq = (uint32_t)((w8 & 3) * 32) << 16;
+    bool ok = true;
+    if (converter) {
+      uint32_t lrow = 0;
+      for (int b = 0; b < 7; ++b) lrow |= (uint32_t)((row >> b) & 1) << lam_of(s_row[b]);
+      // phi: column bits on qubits 0-3 take lane bits whose row qubits are >= 4
+      uint32_t phi = 0, xbits = 0;
+      {
+        int k = 0;
+        for (int b = 0; b < 4; ++b) {
+          if (s_col[b] > 3) break;
+          while (k < 5 && s_row[k] < 4) ++k;
+          if (k >= 5) break;
+          phi |= (uint32_t)((lane >> k) & 1) << b;
+          xbits |= 1u << b;
+          ++k;
+        }
       }
-    }
-    const uint32_t tb = lrow | lamcol[quarter * 16] | lamcol[phi];
-    const uint32_t tq = (uint32_t)((warp & 3) * 32) << 16;
-    const float2* slot_f = (const float2*)slots;
-    const uint64_t* qc = coff + quarter * 16;
-
-    auto convert = [&](uint64_t i) -> bool {
-      const int s = (int)(i & 1);
-      if (!mbar_wait_warp(smem_u32(full + s), (uint32_t)((i >> 1) & 1))) return false;
-      const float2* sl = slot_f + s * (kTcbSlotBytes / 8);
-      const uint32_t a_hi = tmem + tq + (uint32_t)s * 128 + quarter * 16;
-      float2 v[16];
+      const float2* slot_f = (const float2*)slots;
+      for (uint64_t i = 0; i < my; ++i) {
+        if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
+        const int s = (int)(i & 1);
+        // A buffer s was last read by the MMAs of tile i - 2
+        if (i >= 2 && !mbar_wait_warp(smem_u32(mdone + s), (uint32_t)(((i >> 1) - 1) & 1))) { ok = false; break; }
+        if (!mbar_wait_warp(smem_u32(full + s), (uint32_t)((i >> 1) & 1))) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const float2* sl = slot_f + s * (kTcbSlotBytes / 8);
+#pragma unroll 1
+        for (int chunk = 0; chunk < 2; ++chunk) {
+          const int c0 = half * 32 + chunk * 16;
+          const uint32_t tb = lrow | lamcol[c0] | lamcol[phi];
+          float2 v[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) v[j] = sl[tb ^ lamcol[j]];
-      if (xbits & 1) xor_stage<0>(v, phi & 1);
-      if (xbits & 2) xor_stage<1>(v, (phi >> 1) & 1);
-      if (xbits & 4) xor_stage<2>(v, (phi >> 2) & 1);
-      if (xbits & 8) xor_stage<3>(v, (phi >> 3) & 1);
-      uint32_t hi[16], lo[16];
+          for (int j = 0; j < 16; ++j) v[j] = sl[tb ^ lamcol[j]];
+          if (xbits & 1) xor_stage<0>(v, phi & 1);
+          if (xbits & 2) xor_stage<1>(v, (phi >> 1) & 1);
+          if (xbits & 4) xor_stage<2>(v, (phi >> 2) & 1);
+          if (xbits & 8) xor_stage<3>(v, (phi >> 3) & 1);
+          uint32_t hi[16], lo[16];
 #pragma unroll
-      for (int j = 0; j < 16; ++j) {
-        const __nv_bfloat162 h = __floats2bfloat162_rn(v[j].x, v[j].y);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(v[j].x - hf.x, v[j].y - hf.y);
-        hi[j] = *(const uint32_t*)&h;
-        lo[j] = *(const uint32_t*)&l;
+          for (int j = 0; j < 16; ++j) {
+            const __nv_bfloat162 h = __floats2bfloat162_rn(v[j].x, v[j].y);
+            const float2 hf = __bfloat1622float2(h);
+            const __nv_bfloat162 l = __floats2bfloat162_rn(v[j].x - hf.x, v[j].y - hf.y);
+            hi[j] = *(const uint32_t*)&h;
+            lo[j] = *(const uint32_t*)&l;
+          }
+          const uint32_t a_hi = tmem + tq + (uint32_t)s * 128 + c0;
+          tmem_st16(a_hi, hi);
+          if (PREC == 3) tmem_st16(a_hi + 64, lo);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(smem_u32(empty + s));
+          mbar_arrive(smem_u32(afull + s));
+        }
       }
-      tmem_st16(a_hi, hi);
-      if (PREC == 3) tmem_st16(a_hi + 64, lo);
-      asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) {
-        mbar_arrive(smem_u32(empty + s));
-        mbar_arrive(smem_u32(afull + s));
-      }
-      return true;
-    };
-    auto drain = [&](uint64_t i) -> bool {
-      const int d = (int)(i & 1);
-      if (!mbar_wait_warp(smem_u32(mdone + d), (uint32_t)((i >> 1) & 1))) return false;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float o[32];
-      tmem_ld32(tmem + tq + 256 + d * 128 + quarter * 32, o);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(dfree + d));   // accumulator read; stores follow
-      const uint64_t rb = tile_base(blockIdx.x + i * ts) | roff;
+    } else {
+      uint64_t roff = 0;
+      for (int b = 0; b < 7; ++b) roff |= (uint64_t)((row >> b) & 1) << s_row[b];
+      const uint64_t* hc = coff + half * 32;
+      for (uint64_t i = 0; i < my; ++i) {
+        if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
+        const int d = (int)(i & 1);
+        if (!mbar_wait_warp(smem_u32(mdone + d), (uint32_t)((i >> 1) & 1))) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint64_t tt = tile_of(i);
+        float2* __restrict__ psi = state_ptr(tt);
+        const uint64_t rb = tile_base(tt & tmask1) | roff;
+#pragma unroll 1
+        for (int chunk = 0; chunk < 2; ++chunk) {
+          float o[32];
+          tmem_ld32(tmem + tq + 256 + d * 128 + half * 64 + chunk * 32, o);
+          if (chunk == 1) {   // accumulator read; the last stores follow
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(dfree + d));
+          }
 #pragma unroll
-      for (int q = 0; q < 16; ++q) psi[rb | qc[q]] = make_float2(o[2 * q], o[2 * q + 1]);
-      return true;
-    };
-
-    bool ok = my == 0 || convert(0);
-    for (uint64_t i = 0; ok && i < my; ++i) {
-      if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
-      if (i + 1 < my && !convert(i + 1)) { ok = false; break; }
-      if (!drain(i)) { ok = false; break; }
+          for (int q = 0; q < 16; ++q) psi[rb | hc[chunk * 16 + q]] = make_float2(o[2 * q], o[2 * q + 1]);
+        }
+      }
     }
     if (!ok && lane == 0) fail(1);
   }
@@ -628,7 +695,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
 
 size_t tc_bulk_smem_bytes() {
   return 2 * (size_t)kTcbSlotBytes + 2 * (size_t)kTcOperandBytes + 4 * 256 * 8 + 64 * 8 * 2 + 64 * 4 + 28 * 4 +
-         10 * 8 + 16 + 1024;
+         11 * 8 + 16 + 1024;
 }
 
 size_t tc_smem_bytes() { return 6 * (size_t)kTcOperandBytes + 64 * 8 + 32 + 1024; }
@@ -646,8 +713,10 @@ cudaError_t prepare_tc_pass() {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   const int smem_bulk = (int)tc_bulk_smem_bytes();
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
   if (e != cudaSuccess) return e;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -657,8 +726,25 @@ cudaError_t prepare_tc_pass() {
 }
 
 cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
-                                   const TcPassDesc& p, const void* wimg, int prec, int* err, cudaStream_t st) {
+                                   const TcPassDesc& p, const void* wimg, int prec, int pipeline, int* err,
+                                   cudaStream_t st) {
   if (!g_tc_ready) return cudaErrorInvalidConfiguration;   // not prepared
+  if (pipeline == 0) {
+    const uint64_t ntiles = (1ull << (n - 13)) * (uint64_t)nstates;
+    const uint64_t grid = ntiles < (uint64_t)g_tc_sms ? ntiles : (uint64_t)g_tc_sms;
+    const size_t smem = tc_bulk_smem_bytes();
+#define QS_TCB_ARGS (float2*)psi, psis, p, (const uint4*)wimg, wstride / 8, n - 13, ntiles, err
+    if (psis) {
+      if (prec == 3) k_tc_bulk<3, true><<<(unsigned)grid, kTcbThreads, smem, st>>>(QS_TCB_ARGS);
+      else k_tc_bulk<1, true><<<(unsigned)grid, kTcbThreads, smem, st>>>(QS_TCB_ARGS);
+    } else {
+      if (prec == 3) k_tc_bulk<3, false><<<(unsigned)grid, kTcbThreads, smem, st>>>(QS_TCB_ARGS);
+      else k_tc_bulk<1, false><<<(unsigned)grid, kTcbThreads, smem, st>>>(QS_TCB_ARGS);
+    }
+#undef QS_TCB_ARGS
+    note_launch();
+    return cudaGetLastError();
+  }
   const size_t smem = tc_smem_bytes();
   const int sms = g_tc_sms;
   const uint64_t ntiles1 = 1ull << (n - 13), ntiles = ntiles1 * (uint64_t)nstates;
@@ -678,17 +764,7 @@ cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, in
 
 cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int pipeline,
                            int* err, cudaStream_t st) {
-  if (pipeline == 1) return launch_tc_pass_batched(psi, nullptr, 1, 0, n, p, wimg, prec, err, st);
-  if (!g_tc_ready) return cudaErrorInvalidConfiguration;   // not prepared
-  const uint64_t ntiles = 1ull << (n - 13);
-  const uint64_t grid = ntiles < (uint64_t)g_tc_sms ? ntiles : (uint64_t)g_tc_sms;
-  const size_t smem = tc_bulk_smem_bytes();
-  if (prec == 3)
-    k_tc_bulk<3><<<(unsigned)grid, kTcbThreads, smem, st>>>((float2*)psi, p, (const uint4*)wimg, ntiles, err);
-  else
-    k_tc_bulk<1><<<(unsigned)grid, kTcbThreads, smem, st>>>((float2*)psi, p, (const uint4*)wimg, ntiles, err);
-  note_launch();
-  return cudaGetLastError();
+  return launch_tc_pass_batched(psi, nullptr, 1, 0, n, p, wimg, prec, pipeline, err, st);
 }
 
 }  // namespace qs

@@ -161,7 +161,8 @@ cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, 
                                      const double2* btab, cudaStream_t st);
 // wstride (uint16 elements) between the W images of consecutive states; 0 = one image for all
 cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
-                                   const TcPassDesc& p, const void* wimg, int prec, int* err, cudaStream_t st);
+                                   const TcPassDesc& p, const void* wimg, int prec, int pipeline, int* err,
+                                   cudaStream_t st);
 int expval_batched_blocks(int nstates);
 cudaError_t launch_expval_x_batched(const void* const* psis, int nstates, int n, qs_dtype dt, uint64_t xmask,
                                     const uint64_t* zm, int nz, double* partials, double* out, int64_t out_stride,

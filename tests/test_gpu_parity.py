@@ -297,6 +297,7 @@ def test_batched_graph_matches_sequential_and_oracle(dtname):
     if dt == Q.QS_C64:
         modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2))
         modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
+        modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1, tc_pipeline=1))
     for opts in modes:
         plan = Q.qs_plan_create(n, dt, gates, opts)
         states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
@@ -405,11 +406,39 @@ def test_tensor_core_config2_shape_n20_depth40_cz():
     assert np.abs(out - want).max() <= 2e-5
 
 
+@pytest.mark.parametrize("pipe", [0, 1])
+def test_batched_tensor_core_more_tiles_than_sms(pipe):
+    """77 states of 14 qubits: 154 tensor-core tiles over 152 CTAs, so the
+    contiguous per-CTA tile ranges (two tiles each) leave trailing CTAs with
+    nothing to do; blocks rebuilt per state from theta (per-state W images).
+    Sampled rows against the oracle, complex64 bar 2e-5."""
+    n, Bsz, nterms = 14, 77, 10
+    gates, _ = W.ucc(n, nterms, seed=8)
+    thetas = W.thetas_normal(nterms, 9, sigma=0.3, batch=Bsz)
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4,
+                                                            fuse_parametric=1, tc_pipeline=pipe))
+    states = [Q.qs_state_alloc(n, Q.QS_C64) for _ in range(Bsz)]
+    try:
+        assert any(op["type"] == 3 for op in Q.qs_plan_ops(plan))
+        for s in states:
+            Q.qs_state_set_basis(s, 0)
+        Q.qs_plan_execute_batched(plan, states, thetas)
+        for b in (0, 1, 38, 75, 76):
+            out = np.empty(1 << n, dtype=np.complex64)
+            Q.qs_state_copy_to_host(states[b], out)
+            assert np.abs(out - ref(n, gates, thetas[b])).max() <= 2e-5
+    finally:
+        for s in states:
+            Q.qs_state_free(s)
+        Q.qs_plan_free(plan)
+
+
 def test_batched_fixed_circuit_without_parameters():
     n, Bsz = 13, 3
     gates = W.random_layered(n, 5, seed=21)
     want = ref(n, gates)
-    for opts in (Q.make_opts(fuse_k=2), Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2)):
+    for opts in (Q.make_opts(fuse_k=2), Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2),
+                 Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2, tc_pipeline=1)):
         plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
         states = [Q.qs_state_alloc(n, Q.QS_C64) for _ in range(Bsz)]
         try:
