@@ -1354,14 +1354,30 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     double* d_out = nullptr;
     const bool one_launch = p->mode != QS_MODE_PER_GATE;   // batched kernels: one launch per pass
     int64_t Z = 0;
+    // group table for the batched expectation kernel, after the z list in scratch2:
+    // [z: Z u64][x: NL u64][z offset: NL i32][count: NL i32]
+    std::vector<unsigned char> gtab_host;
+    int NL = 0;
     if (terms && nterms) {
       P = prepare_terms(p->n, terms, nterms);
       Z = (int64_t)P.zlist.size();
+      NL = (int)P.launches.size();
       qs_state_s& s0 = *states[0];
-      const int cols = one_launch ? expval_batched_blocks(B) : reduce_blocks();
-      const size_t part = sizeof(double) * (size_t)cols * kZPerLaunch * (one_launch ? B : 1);
+      const int cols = one_launch ? expval_wave_ctas(expval_wave_states(p->n, p->dt, B)) : reduce_blocks();
+      const size_t part = one_launch ? sizeof(double) * (size_t)cols * (size_t)Z * B
+                                     : sizeof(double) * (size_t)cols * kZPerLaunch;
       s0.scratch.ensure(part + sizeof(double) * P.zlist.size() * B);
-      s0.scratch2.ensure(sizeof(uint64_t) * P.zlist.size());
+      gtab_host.resize(sizeof(uint64_t) * (Z + NL) + sizeof(int32_t) * 2 * NL);
+      std::memcpy(gtab_host.data(), P.zlist.data(), sizeof(uint64_t) * Z);
+      uint64_t* hx = (uint64_t*)(gtab_host.data() + sizeof(uint64_t) * Z);
+      int32_t* hz = (int32_t*)(hx + NL);
+      int32_t* hc = hz + NL;
+      for (int l = 0; l < NL; ++l) {
+        hx[l] = P.groups[P.launches[l].first].x;
+        hz[l] = P.launches[l].second;
+        hc[l] = P.counts[l];
+      }
+      s0.scratch2.ensure(gtab_host.size());
       d_part = s0.scratch.as<double>();
       d_out = (double*)((char*)s0.scratch.p + part);
     }
@@ -1383,8 +1399,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     if (!p->pgates.empty())
       CK(cudaMemcpyAsync(p->d_theta.p, theta, sizeof(double) * ntheta * B, cudaMemcpyHostToDevice, st));
     if (terms && nterms)
-      CK(cudaMemcpyAsync(states[0]->scratch2.p, P.zlist.data(), sizeof(uint64_t) * P.zlist.size(),
-                         cudaMemcpyHostToDevice, st));
+      CK(cudaMemcpyAsync(states[0]->scratch2.p, gtab_host.data(), gtab_host.size(), cudaMemcpyHostToDevice, st));
     // the graph depends on the grouping of the terms (x masks, z order), part of the key
     if (terms && nterms) {
       for (size_t k = 0; k < P.zlist.size(); ++k) key.push_back((void*)(uintptr_t)P.zlist[k]);
@@ -1407,13 +1422,13 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
         build_device_blocks(*p, B, st);
         if (one_launch) {
           issue_circuit_batched(*p, d_psis, B, st);
-          if (terms && nterms)
-            for (size_t l = 0; l < P.launches.size(); ++l) {
-              const auto& L = P.launches[l];
-              CK(launch_expval_x_batched((const void* const*)d_psis, B, p->n, p->dt, P.groups[L.first].x,
-                                         states[0]->scratch2.as<uint64_t>() + L.second, P.counts[l], d_part,
-                                         d_out + L.second, Z, st));
-            }
+          if (terms && nterms) {
+            const uint64_t* d_z = states[0]->scratch2.as<uint64_t>();
+            const uint64_t* d_gx = d_z + Z;
+            const int32_t* d_gz = (const int32_t*)(d_gx + NL);
+            CK(launch_expval_groups_batched((const void* const*)d_psis, B, p->n, p->dt, d_gx, d_gz, d_gz + NL, NL,
+                                            d_z, (int)Z, d_part, d_out, st));
+          }
         } else {
           for (int b = 0; b < B; ++b) {
             issue_circuit(*p, states[b]->d, b, st);

@@ -257,15 +257,9 @@ constexpr int kMaxZ = 8;
 // for odd ny (the sign and the re/im choice are folded into coef/odd below).
 // x = 0: each index once, contribution s_i |psi_i|^2.
 template <typename R>
-__global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::T* __restrict__ psi0,
-                                                           const void* const* __restrict__ psis, int n,
+__global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::T* __restrict__ psi, int n,
                                                            uint64_t x, const uint64_t* __restrict__ zm,
                                                            int nz, double* __restrict__ partials) {
-  // gridDim.y states (batched execution): state blockIdx.y writes its own
-  // partial rows; gridDim.x CTAs per state
-  const typename V2<R>::T* __restrict__ psi =
-      psis ? (const typename V2<R>::T*)psis[blockIdx.y] : psi0;
-  partials += (int64_t)blockIdx.y * nz * gridDim.x;
   __shared__ uint64_t z_s[kMaxZ];
   __shared__ int odd_s[kMaxZ];
   if (threadIdx.x < nz) {
@@ -382,51 +376,132 @@ __global__ void __launch_bounds__(kRedThreads) k_expval_x(const typename V2<R>::
   }
 }
 
-// out[b * out_stride + k] = sum_c partials[(b * nz + k) * cols + c] (one CTA per row).
-__global__ void __launch_bounds__(kRedThreads) k_sum_rows_strided(const double* __restrict__ partials, int cols,
-                                                                   int nz, int64_t out_stride,
-                                                                   double* __restrict__ out) {
-  const double* row = partials + (int64_t)blockIdx.x * cols;
-  double v = 0;
-  for (int c = threadIdx.x; c < cols; c += kRedThreads) v += row[c];
-  const double s = block_sum(v);
-  if (threadIdx.x == 0) out[(int64_t)(blockIdx.x / nz) * out_stride + blockIdx.x % nz] = s;
-}
-
 cudaError_t launch_expval_x(const void* psi, int n, qs_dtype dt, uint64_t xmask, const uint64_t* zm,
                             const double* /*coeffs*/, int nz, double* partials, double* out, cudaStream_t st) {
   if (nz > kMaxZ) return cudaErrorInvalidValue;
   if (dt == QS_C64)
-    k_expval_x<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)psi, nullptr, n, xmask, zm, nz, partials);
+    k_expval_x<float><<<kRedBlocks, kRedThreads, 0, st>>>((const float2*)psi, n, xmask, zm, nz, partials);
   else
-    k_expval_x<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)psi, nullptr, n, xmask, zm, nz, partials);
+    k_expval_x<double><<<kRedBlocks, kRedThreads, 0, st>>>((const double2*)psi, n, xmask, zm, nz, partials);
   note_launch();
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   return launch_sum_rows(partials, nz, kRedBlocks, out, st);
 }
 
-int expval_batched_blocks(int nstates) {
-  int b = kRedBlocks / nstates;
-  return b < 8 ? 8 : b;
+// ---------------------------------------------------------------- batched, L2-resident waves
+
+// All Pauli groups for the states [b0, b0 + gridDim.y) of a batch in one
+// launch. A wave's states (a few MiB each) stay resident in L2 while every
+// group sweeps them, so each state is read from HBM about once per wave
+// instead of once per group. CTA (c, s) sweeps slice c of the pair range of
+// state b0 + s for every group in turn; partials[(b Z + zi) C + c] receives
+// its FP64 sum for string zi (C = gridDim.x).
+template <typename R>
+__global__ void __launch_bounds__(kRedThreads) k_expval_groups(const void* const* __restrict__ psis, int b0, int n,
+                                                                const uint64_t* __restrict__ gx,
+                                                                const int32_t* __restrict__ gz,
+                                                                const int32_t* __restrict__ gc, int ngroups,
+                                                                const uint64_t* __restrict__ zl, int Z,
+                                                                double* __restrict__ partials) {
+  using C2 = typename V2<R>::T;
+  const int b = b0 + blockIdx.y;
+  const C2* __restrict__ psi = (const C2*)psis[b];
+  const uint64_t cta = blockIdx.x, ncta = gridDim.x;
+  for (int l = 0; l < ngroups; ++l) {
+    const uint64_t x = gx[l];
+    const int zoff = gz[l], nz = gc[l];
+    uint64_t zm[kMaxZ];
+    int odd[kMaxZ];
+#pragma unroll
+    for (int k = 0; k < kMaxZ; ++k) {
+      zm[k] = k < nz ? zl[zoff + k] : 0;
+      odd[k] = __popcll(x & zm[k]) & 1;
+    }
+    double tot[kMaxZ];
+    R run[kMaxZ];
+#pragma unroll
+    for (int k = 0; k < kMaxZ; ++k) tot[k] = 0;
+    // x = 0: every index once, s_i |psi_i|^2; else pairs (i, i xor x), i with bit hb clear
+    const uint64_t count = x == 0 ? (1ull << n) : (1ull << (n - 1));
+    const int32_t hb = x == 0 ? 0 : 63 - __clzll((long long)x);
+    const uint64_t lo = count * cta / ncta, hi = count * (cta + 1) / ncta;
+    for (uint64_t p0 = lo + threadIdx.x; p0 < hi;) {
+#pragma unroll
+      for (int k = 0; k < kMaxZ; ++k) run[k] = 0;
+#pragma unroll 1
+      for (int it = 0; it < kRunIters && p0 < hi; ++it, p0 += (uint64_t)kRedThreads * kUnroll) {
+        C2 a[kUnroll], bb[kUnroll];
+        uint64_t iu[kUnroll];
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const uint64_t pp = p0 + (uint64_t)u * kRedThreads;
+          iu[u] = x == 0 ? pp : (((pp >> hb) << (hb + 1)) | (pp & ((1ull << hb) - 1)));
+          if (pp < hi) {
+            a[u] = psi[iu[u]];
+            bb[u] = x == 0 ? a[u] : psi[iu[u] ^ x];
+          } else {
+            a[u] = mk<R>(0, 0);
+            bb[u] = a[u];
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < kUnroll; ++u) {
+          const R wr = bb[u].x * a[u].x + bb[u].y * a[u].y;   // Re(conj(b) a) (|a|^2 for x = 0)
+          const R wi = bb[u].x * a[u].y - bb[u].y * a[u].x;   // Im(conj(b) a)
+#pragma unroll
+          for (int k = 0; k < kMaxZ; ++k) {
+            if (k < nz) {
+              const R v = odd[k] ? wi : wr;
+              run[k] += (__popcll(iu[u] & zm[k]) & 1) ? -v : v;
+            }
+          }
+        }
+      }
+#pragma unroll
+      for (int k = 0; k < kMaxZ; ++k)
+        if (k < nz) tot[k] += (double)run[k];
+    }
+#pragma unroll
+    for (int k = 0; k < kMaxZ; ++k) {
+      if (k < nz) {
+        const double s = block_sum(tot[k]);
+        if (threadIdx.x == 0) partials[((int64_t)b * Z + zoff + k) * ncta + cta] = s;
+      }
+    }
+  }
 }
 
-cudaError_t launch_expval_x_batched(const void* const* psis, int nstates, int n, qs_dtype dt, uint64_t xmask,
-                                    const uint64_t* zm, int nz, double* partials, double* out, int64_t out_stride,
-                                    cudaStream_t st) {
-  if (nz > kMaxZ) return cudaErrorInvalidValue;
-  const int cols = expval_batched_blocks(nstates);
-  const dim3 grid(cols, nstates);
-  if (dt == QS_C64)
-    k_expval_x<float><<<grid, kRedThreads, 0, st>>>(nullptr, psis, n, xmask, zm, nz, partials);
-  else
-    k_expval_x<double><<<grid, kRedThreads, 0, st>>>(nullptr, psis, n, xmask, zm, nz, partials);
-  note_launch();
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  k_sum_rows_strided<<<nstates * nz, kRedThreads, 0, st>>>(partials, cols, nz, out_stride, out);
-  note_launch();
-  return cudaGetLastError();
+int expval_wave_states(int n, qs_dtype dt, int nstates) {
+  const uint64_t bytes = (1ull << n) * (dt == QS_C64 ? 8 : 16);
+  const uint64_t budget = 64ull << 20;   // about half of L2
+  uint64_t s = bytes >= budget ? 1 : budget / bytes;
+  if (s > (uint64_t)nstates) s = nstates;
+  return (int)s;
+}
+int expval_wave_ctas(int wave_states) {
+  const int c = kRedBlocks / wave_states;
+  return c < 1 ? 1 : c;
+}
+
+cudaError_t launch_expval_groups_batched(const void* const* psis, int nstates, int n, qs_dtype dt,
+                                         const uint64_t* gx, const int32_t* gz, const int32_t* gc, int ngroups,
+                                         const uint64_t* zl, int Z, double* partials, double* out,
+                                         cudaStream_t st) {
+  const int S = expval_wave_states(n, dt, nstates);
+  const int C = expval_wave_ctas(S);
+  for (int b0 = 0; b0 < nstates; b0 += S) {
+    const int nb = nstates - b0 < S ? nstates - b0 : S;
+    const dim3 grid(C, nb);
+    if (dt == QS_C64)
+      k_expval_groups<float><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, ngroups, zl, Z, partials);
+    else
+      k_expval_groups<double><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, ngroups, zl, Z, partials);
+    note_launch();
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+  }
+  return launch_sum_rows(partials, nstates * Z, C, out, st);
 }
 
 // ---------------------------------------------------------------- H |psi>

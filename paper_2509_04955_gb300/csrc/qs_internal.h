@@ -155,7 +155,7 @@ cudaError_t launch_resolve(const DevGate* gates, const int32_t* param_gates, int
 cudaError_t launch_gate(void* psi, int n, qs_dtype dt, const DevGate& g, const double2* mat,
                         bool adjoint, cudaStream_t st);
 // Batched forms: psis = device array of nstates state pointers (psi unused);
-// gate table rows gstride apart. partials for expval: nstates * nz * cols.
+// gate table rows gstride apart.
 cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
                                      int n, qs_dtype dt, const PassDesc& p, const DevOp* ops, const double2* gtab,
                                      const double2* btab, cudaStream_t st);
@@ -163,10 +163,15 @@ cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, 
 cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
                                    const TcPassDesc& p, const void* wimg, int prec, int pipeline, int* err,
                                    cudaStream_t st);
-int expval_batched_blocks(int nstates);
-cudaError_t launch_expval_x_batched(const void* const* psis, int nstates, int n, qs_dtype dt, uint64_t xmask,
-                                    const uint64_t* zm, int nz, double* partials, double* out, int64_t out_stride,
-                                    cudaStream_t st);
+// Batched <P> for every group in one launch per wave of L2-resident states:
+// out[b * Z + zi] = per-string sum of state b (string zl[zi], groups (gx, gz, gc));
+// partials hold nstates * Z * expval_wave_ctas(expval_wave_states(...)) doubles.
+int expval_wave_states(int n, qs_dtype dt, int nstates);
+int expval_wave_ctas(int wave_states);
+cudaError_t launch_expval_groups_batched(const void* const* psis, int nstates, int n, qs_dtype dt,
+                                         const uint64_t* gx, const int32_t* gz, const int32_t* gc, int ngroups,
+                                         const uint64_t* zl, int Z, double* partials, double* out,
+                                         cudaStream_t st);
 cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
                              const double2* gate_table, const double2* block_table, int threads,
                              cudaStream_t st);
