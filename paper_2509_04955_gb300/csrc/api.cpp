@@ -409,6 +409,7 @@ void register_device_block(qs_plan_s& P, const Block& blk, int kind, int64_t out
     m.t0 = local(g.t[0]);
     m.t1 = g.nt == 2 ? local(g.t[1]) : 0;
     for (int k = 0; k < g.nc; ++k) m.cmask |= 1u << local(g.c[k]);
+    m.form = g.form;
     P.h_dmem.push_back(m);
   }
   d.mem_end = (int)P.h_dmem.size();
@@ -896,20 +897,19 @@ qs_status qs_plan_check_device_blocks(qs_plan_t p, qs_state_t s, const double* t
         const double2 a = dev[p->block_off[b] + i], h = p->h_btab[p->block_off[b] + i];
         if (blk.rep != OP_TC) worst = std::max(worst, std::hypot(a.x - h.x, a.y - h.y));
       }
-      if (blk.rep == OP_TC) {   // compare the W image with one built on the host from the host product
+      if (blk.rep == OP_TC) {
+        // compare the W image with one built on the host from the host product: the
+        // value the MMAs use is hi + lo (hi and lo alone may trade one ulp at a tie)
         std::vector<uint16_t> img(32768);
         build_w_image(p->h_btab.data() + p->block_off[b], img.data());
-        for (size_t t = 0; t < p->tcdesc.size(); ++t)
-          (void)t;
-        // locate this block's tensor-core pass
-        for (size_t st = 0, ti = 0; st < p->steps.size(); ++st)
-          if (p->steps[st].kind == 1) {
-            const OpRec& r = p->exec_ops[p->pass_ops[st].first];
-            if (r.block == (int)b)
-              for (int e = 0; e < 32768; ++e)
-                worst = std::max(worst, std::fabs((double)bf16_to_float(img[e]) -
-                                                  (double)bf16_to_float(wdev[(size_t)p->steps[st].idx * 32768 + e])));
-            ++ti;
+        for (size_t st = 0; st < p->steps.size(); ++st)
+          if (p->steps[st].kind == 1 && p->exec_ops[p->pass_ops[st].first].block == (int)b) {
+            const uint16_t* dv = wdev.data() + (size_t)p->steps[st].idx * 32768;
+            for (int e = 0; e < 16384; ++e) {
+              const double wh = (double)bf16_to_float(img[e]) + (double)bf16_to_float(img[16384 + e]);
+              const double wd = (double)bf16_to_float(dv[e]) + (double)bf16_to_float(dv[16384 + e]);
+              worst = std::max(worst, std::fabs(wh - wd));
+            }
           }
       }
       ++cnt;

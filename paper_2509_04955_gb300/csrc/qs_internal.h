@@ -67,7 +67,7 @@ struct DevMember {
   int32_t nt;              // targets: 1 or 2
   int32_t t0, t1;          // block-local target bits
   uint32_t cmask;          // block-local control bits
-  int32_t pad;
+  int32_t form;            // GateForm of the target matrix (structure known for every theta)
 };
 cudaError_t prepare_build_blocks();
 cudaError_t prepare_tc_pass();

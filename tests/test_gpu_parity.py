@@ -256,6 +256,53 @@ def test_parametric_tensor_core_blocks_built_on_device():
         Q.qs_plan_free(plan)
 
 
+def _parametrized_gate_mix(n, ngates, seed):
+    """Every gate kind and form (permutations, diagonals, real, RX-like,
+    dense, SWAP, dense two-target) with each parametric gate reading theta."""
+    import dataclasses
+    gates, p = [], 0
+    for g in W.random_gate_mix(n, ngates, seed):
+        if g.kind in W.PARAMETRIC_KINDS:
+            g = dataclasses.replace(g, param_index=p, scale=1.0)
+            p += 1
+        gates.append(g)
+    return gates, p
+
+
+@pytest.mark.parametrize("mode", ["fused", "tensor"])
+def test_device_built_blocks_equal_host_products(mode):
+    """Blocks rebuilt on the device from theta (FP64 products, structured
+    forms) against the host's FP64 products of the same members: dense and
+    diagonal blocks to 1e-13; tensor-core W images compared as hi + lo (the
+    value the MMAs multiply), each side within 2^-18 |w| of w, so 2^-16."""
+    n = 13
+    gates, p = _parametrized_gate_mix(n, 160, seed=11)
+    if mode == "fused":   # the paper's merges: many 2-qubit dense blocks over every form
+        opts = Q.make_opts(paper_mode=1, fuse_parametric=1)
+        bar = 1e-13
+    else:
+        opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=3, fuse_parametric=1)
+        bar = 2.0 ** -16
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
+    h = Q.qs_state_alloc(n, Q.QS_C64)
+    try:
+        kinds = {op["type"] for op in Q.qs_plan_ops(plan)}
+        assert (3 in kinds) if mode == "tensor" else (1 in kinds)
+        for seed in (3, 4):
+            worst, nb = Q.qs_plan_check_device_blocks(plan, h, W.thetas_uniform(p, seed))
+            assert nb > 0
+            assert worst <= bar
+        theta = W.thetas_uniform(p, 5)
+        Q.qs_state_set_basis(h, 0)
+        Q.qs_plan_execute(plan, h, theta)
+        out = np.empty(1 << n, dtype=np.complex64)
+        Q.qs_state_copy_to_host(h, out)
+        assert np.abs(out - ref(n, gates, theta)).max() <= 2e-5
+    finally:
+        Q.qs_state_free(h)
+        Q.qs_plan_free(plan)
+
+
 def test_adjoint_hea_n24_full_size_against_device_parameter_shift():
     """Hardware-efficient ansatz at its full size (24 qubits, 12 layers, 576
     parameters, 150-term H): the adjoint gradient equals the two-term shift
