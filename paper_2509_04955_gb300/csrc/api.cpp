@@ -1355,9 +1355,10 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     const bool one_launch = p->mode != QS_MODE_PER_GATE;   // batched kernels: one launch per pass
     int64_t Z = 0;
     // group table for the batched expectation kernel, after the z list in scratch2:
-    // [z: Z u64][x: NL u64][z offset: NL i32][count: NL i32]
+    // [z: Z u64][x: NL u64][z offset: NL i32][count: NL i32][group order: NL i32,
+    // single-string groups first]
     std::vector<unsigned char> gtab_host;
-    int NL = 0;
+    int NL = 0, NL1 = 0;
     if (terms && nterms) {
       P = prepare_terms(p->n, terms, nterms);
       Z = (int64_t)P.zlist.size();
@@ -1367,16 +1368,20 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
       const size_t part = one_launch ? sizeof(double) * (size_t)cols * (size_t)Z * B
                                      : sizeof(double) * (size_t)cols * kZPerLaunch;
       s0.scratch.ensure(part + sizeof(double) * P.zlist.size() * B);
-      gtab_host.resize(sizeof(uint64_t) * (Z + NL) + sizeof(int32_t) * 2 * NL);
+      gtab_host.resize(sizeof(uint64_t) * (Z + NL) + sizeof(int32_t) * 3 * NL);
       std::memcpy(gtab_host.data(), P.zlist.data(), sizeof(uint64_t) * Z);
       uint64_t* hx = (uint64_t*)(gtab_host.data() + sizeof(uint64_t) * Z);
       int32_t* hz = (int32_t*)(hx + NL);
       int32_t* hc = hz + NL;
+      int32_t* ho = hc + NL;
       for (int l = 0; l < NL; ++l) {
         hx[l] = P.groups[P.launches[l].first].x;
         hz[l] = P.launches[l].second;
         hc[l] = P.counts[l];
+        if (hc[l] == 1) ho[NL1++] = l;
       }
+      for (int l = 0, r = NL1; l < NL; ++l)
+        if (hc[l] != 1) ho[r++] = l;
       s0.scratch2.ensure(gtab_host.size());
       d_part = s0.scratch.as<double>();
       d_out = (double*)((char*)s0.scratch.p + part);
@@ -1426,8 +1431,8 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
             const uint64_t* d_z = states[0]->scratch2.as<uint64_t>();
             const uint64_t* d_gx = d_z + Z;
             const int32_t* d_gz = (const int32_t*)(d_gx + NL);
-            CK(launch_expval_groups_batched((const void* const*)d_psis, B, p->n, p->dt, d_gx, d_gz, d_gz + NL, NL,
-                                            d_z, (int)Z, d_part, d_out, st));
+            CK(launch_expval_groups_batched((const void* const*)d_psis, B, p->n, p->dt, d_gx, d_gz, d_gz + NL,
+                                            d_gz + 2 * NL, NL1, NL, d_z, (int)Z, d_part, d_out, st));
           }
         } else {
           for (int b = 0; b < B; ++b) {

@@ -40,6 +40,25 @@ template <> struct Vec16<double> {
 
 __device__ __forceinline__ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
+// Amplitudes 2v and 2v + 1 (16-byte aligned state): one float4 for complex64,
+// two double2 for complex128.
+template <typename R> struct AmpPair;
+template <> struct AmpPair<float> {
+  float4 v;
+  __device__ __forceinline__ void load(const void* psi, uint64_t vi) { v = ((const float4*)psi)[vi]; }
+  __device__ __forceinline__ void zero() { v = make_float4(0, 0, 0, 0); }
+  __device__ __forceinline__ float2 a(int k) const { return k == 0 ? make_float2(v.x, v.y) : make_float2(v.z, v.w); }
+};
+template <> struct AmpPair<double> {
+  double2 v0, v1;
+  __device__ __forceinline__ void load(const void* psi, uint64_t vi) {
+    v0 = ((const double2*)psi)[2 * vi];
+    v1 = ((const double2*)psi)[2 * vi + 1];
+  }
+  __device__ __forceinline__ void zero() { v0 = v1 = make_double2(0, 0); }
+  __device__ __forceinline__ double2 a(int k) const { return k == 0 ? v0 : v1; }
+};
+
 int reduce_blocks() { return kRedBlocks; }
 
 // Sum of a per-thread double across the CTA; result valid in thread 0.
@@ -394,76 +413,99 @@ cudaError_t launch_expval_x(const void* psi, int n, qs_dtype dt, uint64_t xmask,
 // All Pauli groups for the states [b0, b0 + gridDim.y) of a batch in one
 // launch. A wave's states (a few MiB each) stay resident in L2 while every
 // group sweeps them, so each state is read from HBM about once per wave
-// instead of once per group. CTA (c, s) sweeps slice c of the pair range of
-// state b0 + s for every group in turn; partials[(b Z + zi) C + c] receives
-// its FP64 sum for string zi (C = gridDim.x).
-template <typename R>
+// instead of once per group. CTA (c, s) sweeps slice c of state b0 + s for
+// every group in turn; partials[(b Z + zi) C + c] receives its FP64 sum for
+// string zi (C = gridDim.x). Loads take amplitude pairs (2v, 2v + 1): for x
+// with its highest bit hb >= 1, pairs 2q and 2q + 1 start at consecutive even
+// indices i, i + 1 and their partners i ^ x, (i + 1) ^ x form one aligned
+// pair (swapped when x is odd); x = 1 pairs the two halves of an item; x = 0
+// takes two diagonal terms per item. NZ bounds the strings of a group.
+template <typename R, int NZ>
 __global__ void __launch_bounds__(kRedThreads) k_expval_groups(const void* const* __restrict__ psis, int b0, int n,
                                                                 const uint64_t* __restrict__ gx,
                                                                 const int32_t* __restrict__ gz,
-                                                                const int32_t* __restrict__ gc, int ngroups,
+                                                                const int32_t* __restrict__ gc,
+                                                                const int32_t* __restrict__ glist, int ngroups,
                                                                 const uint64_t* __restrict__ zl, int Z,
                                                                 double* __restrict__ partials) {
   using C2 = typename V2<R>::T;
   const int b = b0 + blockIdx.y;
-  const C2* __restrict__ psi = (const C2*)psis[b];
+  const void* __restrict__ psi = psis[b];
   const uint64_t cta = blockIdx.x, ncta = gridDim.x;
-  for (int l = 0; l < ngroups; ++l) {
+  for (int li = 0; li < ngroups; ++li) {
+    const int l = glist[li];
     const uint64_t x = gx[l];
     const int zoff = gz[l], nz = gc[l];
-    uint64_t zm[kMaxZ];
-    int odd[kMaxZ];
+    uint64_t zm[NZ];
+    int odd[NZ];
 #pragma unroll
-    for (int k = 0; k < kMaxZ; ++k) {
+    for (int k = 0; k < NZ; ++k) {
       zm[k] = k < nz ? zl[zoff + k] : 0;
       odd[k] = __popcll(x & zm[k]) & 1;
     }
-    double tot[kMaxZ];
-    R run[kMaxZ];
+    double tot[NZ];
+    R run[NZ];
 #pragma unroll
-    for (int k = 0; k < kMaxZ; ++k) tot[k] = 0;
-    // x = 0: every index once, s_i |psi_i|^2; else pairs (i, i xor x), i with bit hb clear
-    const uint64_t count = x == 0 ? (1ull << n) : (1ull << (n - 1));
-    const int32_t hb = x == 0 ? 0 : 63 - __clzll((long long)x);
-    const uint64_t lo = count * cta / ncta, hi = count * (cta + 1) / ncta;
-    for (uint64_t p0 = lo + threadIdx.x; p0 < hi;) {
+    for (int k = 0; k < NZ; ++k) tot[k] = 0;
+    const int32_t hb = x == 0 ? -1 : 63 - __clzll((long long)x);
+    // vector items: x = 0 -> 2^(n-1) vectors of two amplitudes; x = 1 -> 2^(n-1) vectors
+    // (one pair each); hb >= 1 -> 2^(n-2) pairs of pairs
+    const uint64_t items = hb >= 1 ? (1ull << (n - 2)) : (1ull << (n - 1));
+    const uint64_t lo = items * cta / ncta, hi = items * (cta + 1) / ncta;
+    auto accum = [&](const C2& a0, const C2& bb0, uint64_t i0) {
+      const R wr = bb0.x * a0.x + bb0.y * a0.y;   // Re(conj(b) a) (|a|^2 for x = 0)
+      const R wi = bb0.x * a0.y - bb0.y * a0.x;   // Im(conj(b) a)
 #pragma unroll
-      for (int k = 0; k < kMaxZ; ++k) run[k] = 0;
+      for (int k = 0; k < NZ; ++k) {
+        if (k < nz) {
+          const R v = odd[k] ? wi : wr;
+          run[k] += (__popcll(i0 & zm[k]) & 1) ? -v : v;
+        }
+      }
+    };
+    for (uint64_t q0 = lo + threadIdx.x; q0 < hi;) {
+#pragma unroll
+      for (int k = 0; k < NZ; ++k) run[k] = 0;
 #pragma unroll 1
-      for (int it = 0; it < kRunIters && p0 < hi; ++it, p0 += (uint64_t)kRedThreads * kUnroll) {
-        C2 a[kUnroll], bb[kUnroll];
+      for (int it = 0; it < kRunIters && q0 < hi; ++it, q0 += (uint64_t)kRedThreads * kUnroll) {
+        AmpPair<R> va[kUnroll], vb[kUnroll];
         uint64_t iu[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-          const uint64_t pp = p0 + (uint64_t)u * kRedThreads;
-          iu[u] = x == 0 ? pp : (((pp >> hb) << (hb + 1)) | (pp & ((1ull << hb) - 1)));
-          if (pp < hi) {
-            a[u] = psi[iu[u]];
-            bb[u] = x == 0 ? a[u] : psi[iu[u] ^ x];
+          const uint64_t q = q0 + (uint64_t)u * kRedThreads;
+          // first amplitude index of the item
+          iu[u] = hb >= 1 ? ((((2 * q) >> hb) << (hb + 1)) | ((2 * q) & ((1ull << hb) - 1))) : 2 * q;
+          if (q < hi) {
+            va[u].load(psi, iu[u] >> 1);
+            if (hb >= 1) vb[u].load(psi, (iu[u] ^ x) >> 1);
+            else vb[u] = va[u];
           } else {
-            a[u] = mk<R>(0, 0);
-            bb[u] = a[u];
+            va[u].zero();
+            vb[u].zero();
           }
         }
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-          const R wr = bb[u].x * a[u].x + bb[u].y * a[u].y;   // Re(conj(b) a) (|a|^2 for x = 0)
-          const R wi = bb[u].x * a[u].y - bb[u].y * a[u].x;   // Im(conj(b) a)
-#pragma unroll
-          for (int k = 0; k < kMaxZ; ++k) {
-            if (k < nz) {
-              const R v = odd[k] ? wi : wr;
-              run[k] += (__popcll(iu[u] & zm[k]) & 1) ? -v : v;
-            }
+          const C2 a0 = va[u].a(0), a1 = va[u].a(1);
+          if (hb < 0) {            // diagonal: two indices per item
+            accum(a0, a0, iu[u]);
+            accum(a1, a1, iu[u] + 1);
+          } else if (hb == 0) {    // x = 1: the item holds the pair
+            accum(a0, a1, iu[u]);
+          } else {
+            const C2 p0 = vb[u].a(0), p1 = vb[u].a(1);
+            const bool sw = (x & 1) != 0;
+            accum(a0, sw ? p1 : p0, iu[u]);
+            accum(a1, sw ? p0 : p1, iu[u] + 1);
           }
         }
       }
 #pragma unroll
-      for (int k = 0; k < kMaxZ; ++k)
+      for (int k = 0; k < NZ; ++k)
         if (k < nz) tot[k] += (double)run[k];
     }
 #pragma unroll
-    for (int k = 0; k < kMaxZ; ++k) {
+    for (int k = 0; k < NZ; ++k) {
       if (k < nz) {
         const double s = block_sum(tot[k]);
         if (threadIdx.x == 0) partials[((int64_t)b * Z + zoff + k) * ncta + cta] = s;
@@ -485,19 +527,32 @@ int expval_wave_ctas(int wave_states) {
 }
 
 cudaError_t launch_expval_groups_batched(const void* const* psis, int nstates, int n, qs_dtype dt,
-                                         const uint64_t* gx, const int32_t* gz, const int32_t* gc, int ngroups,
-                                         const uint64_t* zl, int Z, double* partials, double* out,
-                                         cudaStream_t st) {
+                                         const uint64_t* gx, const int32_t* gz, const int32_t* gc,
+                                         const int32_t* glist, int ngroups1, int ngroups, const uint64_t* zl, int Z,
+                                         double* partials, double* out, cudaStream_t st) {
+  // glist[0, ngroups1): groups with one string; glist[ngroups1, ngroups): the rest
   const int S = expval_wave_states(n, dt, nstates);
   const int C = expval_wave_ctas(S);
   for (int b0 = 0; b0 < nstates; b0 += S) {
     const int nb = nstates - b0 < S ? nstates - b0 : S;
     const dim3 grid(C, nb);
-    if (dt == QS_C64)
-      k_expval_groups<float><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, ngroups, zl, Z, partials);
-    else
-      k_expval_groups<double><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, ngroups, zl, Z, partials);
-    note_launch();
+    const int nrest = ngroups - ngroups1;
+    if (dt == QS_C64) {
+      if (ngroups1)
+        k_expval_groups<float, 1><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist, ngroups1, zl, Z,
+                                                                partials);
+      if (nrest)
+        k_expval_groups<float, kMaxZ><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist + ngroups1,
+                                                                    nrest, zl, Z, partials);
+    } else {
+      if (ngroups1)
+        k_expval_groups<double, 1><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist, ngroups1, zl, Z,
+                                                                 partials);
+      if (nrest)
+        k_expval_groups<double, kMaxZ><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist + ngroups1,
+                                                                     nrest, zl, Z, partials);
+    }
+    note_launch((ngroups1 ? 1 : 0) + (nrest ? 1 : 0));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }

@@ -168,10 +168,11 @@ cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, in
 // partials hold nstates * Z * expval_wave_ctas(expval_wave_states(...)) doubles.
 int expval_wave_states(int n, qs_dtype dt, int nstates);
 int expval_wave_ctas(int wave_states);
+// glist orders the groups: [0, ngroups1) hold one string each, the rest up to 8.
 cudaError_t launch_expval_groups_batched(const void* const* psis, int nstates, int n, qs_dtype dt,
-                                         const uint64_t* gx, const int32_t* gz, const int32_t* gc, int ngroups,
-                                         const uint64_t* zl, int Z, double* partials, double* out,
-                                         cudaStream_t st);
+                                         const uint64_t* gx, const int32_t* gz, const int32_t* gc,
+                                         const int32_t* glist, int ngroups1, int ngroups, const uint64_t* zl, int Z,
+                                         double* partials, double* out, cudaStream_t st);
 cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
                              const double2* gate_table, const double2* block_table, int threads,
                              cudaStream_t st);

@@ -453,6 +453,48 @@ def test_tensor_core_config2_shape_n20_depth40_cz():
     assert np.abs(out - want).max() <= 2e-5
 
 
+def _structured_pauli_sum(n, seed):
+    """Every x-mask case of the batched expectation kernel: x = 0 (Z
+    strings), x = 1, odd and even x with a high bit, and 11 strings sharing one
+    x (more than one launch group of 8), plus random strings."""
+    rng = np.random.default_rng(seed)
+    xs, zs = [], []
+    for x in (0, 0, 1, 3, (1 << (n - 1)) | 1, 2, 6, 1 << (n - 1)):
+        xs.append(x & ((1 << n) - 1))
+        zs.append(int(rng.integers(0, 1 << n)))
+    shared = int(rng.integers(1, 1 << n))
+    for _ in range(11):
+        xs.append(shared)
+        zs.append(int(rng.integers(0, 1 << n)))
+    c, xr, zr = W.random_pauli_sum(n, 12, seed)
+    coeff = np.concatenate([rng.standard_normal(len(xs)), c])
+    return coeff, np.array(xs + list(xr), dtype=np.uint64), np.array(zs + list(zr), dtype=np.uint64)
+
+
+@pytest.mark.parametrize("n", [2, 13])
+def test_batched_expectation_every_mask_case(n):
+    """Batched <H> (one launch per wave of states, 16-byte pair loads) on a
+    sum that hits every x-mask case, against the oracle per state: bar 2e-5
+    times the coefficient sum (complex64)."""
+    Bsz = 5
+    gates = W.random_layered(n, 3, seed=n)
+    H = _structured_pauli_sum(n, seed=7)
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(fuse_k=2, tile_qubits=min(n, 8), low_qubits=1))
+    states = [Q.qs_state_alloc(n, Q.QS_C64) for _ in range(Bsz)]
+    try:
+        for b, s in enumerate(states):
+            Q.qs_state_set_basis(s, (b * 2654435761) % (1 << n))
+        ex = Q.qs_plan_execute_batched(plan, states, None, H)
+        for b in range(Bsz):
+            psi = O.apply_circuit(O.basis(n, (b * 2654435761) % (1 << n)), n, gates, None)
+            want = O.expval(psi, n, *H).real
+            assert abs(ex[b] - want) <= 2e-5 * np.abs(H[0]).sum()
+    finally:
+        for s in states:
+            Q.qs_state_free(s)
+        Q.qs_plan_free(plan)
+
+
 @pytest.mark.parametrize("pipe", [0, 1])
 def test_batched_tensor_core_more_tiles_than_sms(pipe):
     """77 states of 14 qubits: 154 tensor-core tiles over 152 CTAs, so the
