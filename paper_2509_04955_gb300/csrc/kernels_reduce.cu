@@ -419,8 +419,10 @@ cudaError_t launch_expval_x(const void* psi, int n, qs_dtype dt, uint64_t xmask,
 // with its highest bit hb >= 1, pairs 2q and 2q + 1 start at consecutive even
 // indices i, i + 1 and their partners i ^ x, (i + 1) ^ x form one aligned
 // pair (swapped when x is odd); x = 1 pairs the two halves of an item; x = 0
-// takes two diagonal terms per item. NZ bounds the strings of a group.
-template <typename R, int NZ>
+// takes two diagonal terms per item. NZ bounds the strings of a group; I is
+// the index type (32-bit while 2^n fits). i is even, so the sign parity of
+// i + 1 is that of i xor bit 0 of z: one popcount per item and string.
+template <typename R, int NZ, typename I>
 __global__ void __launch_bounds__(kRedThreads) k_expval_groups(const void* const* __restrict__ psis, int b0, int n,
                                                                 const uint64_t* __restrict__ gx,
                                                                 const int32_t* __restrict__ gz,
@@ -436,13 +438,15 @@ __global__ void __launch_bounds__(kRedThreads) k_expval_groups(const void* const
     const int l = glist[li];
     const uint64_t x = gx[l];
     const int zoff = gz[l], nz = gc[l];
-    uint64_t zm[NZ];
+    I zm[NZ];
     int odd[NZ];
 #pragma unroll
     for (int k = 0; k < NZ; ++k) {
-      zm[k] = k < nz ? zl[zoff + k] : 0;
-      odd[k] = __popcll(x & zm[k]) & 1;
+      const uint64_t z = k < nz ? zl[zoff + k] : 0;
+      zm[k] = (I)z;
+      odd[k] = __popcll(x & z) & 1;
     }
+    const I xi = (I)x;
     double tot[NZ];
     R run[NZ];
 #pragma unroll
@@ -450,34 +454,41 @@ __global__ void __launch_bounds__(kRedThreads) k_expval_groups(const void* const
     const int32_t hb = x == 0 ? -1 : 63 - __clzll((long long)x);
     // vector items: x = 0 -> 2^(n-1) vectors of two amplitudes; x = 1 -> 2^(n-1) vectors
     // (one pair each); hb >= 1 -> 2^(n-2) pairs of pairs
-    const uint64_t items = hb >= 1 ? (1ull << (n - 2)) : (1ull << (n - 1));
-    const uint64_t lo = items * cta / ncta, hi = items * (cta + 1) / ncta;
-    auto accum = [&](const C2& a0, const C2& bb0, uint64_t i0) {
-      const R wr = bb0.x * a0.x + bb0.y * a0.y;   // Re(conj(b) a) (|a|^2 for x = 0)
-      const R wi = bb0.x * a0.y - bb0.y * a0.x;   // Im(conj(b) a)
+    const I items = hb >= 1 ? ((I)1 << (n - 2)) : ((I)1 << (n - 1));
+    const I lo = (I)((uint64_t)items * cta / ncta), hi = (I)((uint64_t)items * (cta + 1) / ncta);
+    const I hmask = hb >= 1 ? (((I)1 << hb) - 1) : 0;
+    // the two terms of an item: amplitudes i (even) and i + 1 against partners b0, b1
+    auto accum2 = [&](const C2& a0, const C2& p0, const C2& a1, const C2& p1, I i0, bool two) {
+      const R wr0 = p0.x * a0.x + p0.y * a0.y, wi0 = p0.x * a0.y - p0.y * a0.x;   // conj(b) a
+      const R wr1 = p1.x * a1.x + p1.y * a1.y, wi1 = p1.x * a1.y - p1.y * a1.x;
 #pragma unroll
       for (int k = 0; k < NZ; ++k) {
         if (k < nz) {
-          const R v = odd[k] ? wi : wr;
-          run[k] += (__popcll(i0 & zm[k]) & 1) ? -v : v;
+          const int par = __popc((uint32_t)(i0 & zm[k])) + (sizeof(I) > 4 ? __popc((uint32_t)((uint64_t)(i0 & zm[k]) >> 32)) : 0);
+          const R v0 = odd[k] ? wi0 : wr0;
+          run[k] += (par & 1) ? -v0 : v0;
+          if (two) {
+            const R v1 = odd[k] ? wi1 : wr1;
+            run[k] += ((par ^ (int)zm[k]) & 1) ? -v1 : v1;
+          }
         }
       }
     };
-    for (uint64_t q0 = lo + threadIdx.x; q0 < hi;) {
+    for (I q0 = lo + threadIdx.x; q0 < hi;) {
 #pragma unroll
       for (int k = 0; k < NZ; ++k) run[k] = 0;
 #pragma unroll 1
-      for (int it = 0; it < kRunIters && q0 < hi; ++it, q0 += (uint64_t)kRedThreads * kUnroll) {
+      for (int it = 0; it < kRunIters && q0 < hi; ++it, q0 += (I)(kRedThreads * kUnroll)) {
         AmpPair<R> va[kUnroll], vb[kUnroll];
-        uint64_t iu[kUnroll];
+        I iu[kUnroll];
 #pragma unroll
         for (int u = 0; u < kUnroll; ++u) {
-          const uint64_t q = q0 + (uint64_t)u * kRedThreads;
+          const I q2 = 2 * (q0 + (I)(u * kRedThreads));
           // first amplitude index of the item
-          iu[u] = hb >= 1 ? ((((2 * q) >> hb) << (hb + 1)) | ((2 * q) & ((1ull << hb) - 1))) : 2 * q;
-          if (q < hi) {
+          iu[u] = hb >= 1 ? (((q2 >> hb) << (hb + 1)) | (q2 & hmask)) : q2;
+          if (q0 + (I)(u * kRedThreads) < hi) {
             va[u].load(psi, iu[u] >> 1);
-            if (hb >= 1) vb[u].load(psi, (iu[u] ^ x) >> 1);
+            if (hb >= 1) vb[u].load(psi, (iu[u] ^ xi) >> 1);
             else vb[u] = va[u];
           } else {
             va[u].zero();
@@ -488,15 +499,13 @@ __global__ void __launch_bounds__(kRedThreads) k_expval_groups(const void* const
         for (int u = 0; u < kUnroll; ++u) {
           const C2 a0 = va[u].a(0), a1 = va[u].a(1);
           if (hb < 0) {            // diagonal: two indices per item
-            accum(a0, a0, iu[u]);
-            accum(a1, a1, iu[u] + 1);
+            accum2(a0, a0, a1, a1, iu[u], true);
           } else if (hb == 0) {    // x = 1: the item holds the pair
-            accum(a0, a1, iu[u]);
+            accum2(a0, a1, a0, a1, iu[u], false);
           } else {
             const C2 p0 = vb[u].a(0), p1 = vb[u].a(1);
             const bool sw = (x & 1) != 0;
-            accum(a0, sw ? p1 : p0, iu[u]);
-            accum(a1, sw ? p0 : p1, iu[u] + 1);
+            accum2(a0, sw ? p1 : p0, a1, sw ? p0 : p1, iu[u], true);
           }
         }
       }
@@ -526,6 +535,18 @@ int expval_wave_ctas(int wave_states) {
   return c < 1 ? 1 : c;
 }
 
+template <typename R, typename I>
+static void expval_groups_wave(dim3 grid, cudaStream_t st, const void* const* psis, int b0, int n, const uint64_t* gx,
+                               const int32_t* gz, const int32_t* gc, const int32_t* glist, int ngroups1,
+                               int ngroups, const uint64_t* zl, int Z, double* partials) {
+  if (ngroups1)
+    k_expval_groups<R, 1, I><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist, ngroups1, zl, Z,
+                                                           partials);
+  if (ngroups > ngroups1)
+    k_expval_groups<R, kMaxZ, I><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist + ngroups1,
+                                                               ngroups - ngroups1, zl, Z, partials);
+}
+
 cudaError_t launch_expval_groups_batched(const void* const* psis, int nstates, int n, qs_dtype dt,
                                          const uint64_t* gx, const int32_t* gz, const int32_t* gc,
                                          const int32_t* glist, int ngroups1, int ngroups, const uint64_t* zl, int Z,
@@ -533,26 +554,18 @@ cudaError_t launch_expval_groups_batched(const void* const* psis, int nstates, i
   // glist[0, ngroups1): groups with one string; glist[ngroups1, ngroups): the rest
   const int S = expval_wave_states(n, dt, nstates);
   const int C = expval_wave_ctas(S);
+  const bool i32 = n <= 31;
   for (int b0 = 0; b0 < nstates; b0 += S) {
     const int nb = nstates - b0 < S ? nstates - b0 : S;
     const dim3 grid(C, nb);
-    const int nrest = ngroups - ngroups1;
     if (dt == QS_C64) {
-      if (ngroups1)
-        k_expval_groups<float, 1><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist, ngroups1, zl, Z,
-                                                                partials);
-      if (nrest)
-        k_expval_groups<float, kMaxZ><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist + ngroups1,
-                                                                    nrest, zl, Z, partials);
+      if (i32) expval_groups_wave<float, uint32_t>(grid, st, psis, b0, n, gx, gz, gc, glist, ngroups1, ngroups, zl, Z, partials);
+      else expval_groups_wave<float, uint64_t>(grid, st, psis, b0, n, gx, gz, gc, glist, ngroups1, ngroups, zl, Z, partials);
     } else {
-      if (ngroups1)
-        k_expval_groups<double, 1><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist, ngroups1, zl, Z,
-                                                                 partials);
-      if (nrest)
-        k_expval_groups<double, kMaxZ><<<grid, kRedThreads, 0, st>>>(psis, b0, n, gx, gz, gc, glist + ngroups1,
-                                                                     nrest, zl, Z, partials);
+      if (i32) expval_groups_wave<double, uint32_t>(grid, st, psis, b0, n, gx, gz, gc, glist, ngroups1, ngroups, zl, Z, partials);
+      else expval_groups_wave<double, uint64_t>(grid, st, psis, b0, n, gx, gz, gc, glist, ngroups1, ngroups, zl, Z, partials);
     }
-    note_launch((ngroups1 ? 1 : 0) + (nrest ? 1 : 0));
+    note_launch((ngroups1 ? 1 : 0) + (ngroups > ngroups1 ? 1 : 0));
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
   }
