@@ -47,6 +47,9 @@ def parse():
     ap.add_argument("--full-configs", action="store_true",
                     help="also run the complex128 n=32 reference for the tensor-core config (64 GiB, ~1 min)")
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
+    ap.add_argument("--only-config", default=None,
+                    choices=["qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20", "hea_adjoint_n24"],
+                    help="run one configuration workload alone (no headline) and print its JSON")
     return ap.parse_args()
 
 
@@ -218,6 +221,10 @@ def main():
     import paper_2509_04955_gb300 as Q
     import numpy as np
 
+    if args.only_config:
+        print(json.dumps({"only_config": args.only_config, **run_configs(Q, torch, np, args)}))
+        return
+
     peaks = {}
     pk = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pk):
@@ -370,8 +377,10 @@ def main():
         except (ValueError, OSError):
             traffic = None
     cfg = {"workload": workload_desc(args, len(gates)) + f", complex64, {mode_name(Q, kw)} plan",
-           "n": n, "state": "complex64, 8 GiB", "gates": len(gates), "passes": info["passes"],
-           "blocks": info["blocks"], "l2": "inputs larger than L2 (8 GiB state vs 129 MB); no flush",
+           "n": n, "state": f"complex64, {(1 << n) * 8 / 2**30:g} GiB", "gates": len(gates), "passes": info["passes"],
+           "blocks": info["blocks"],
+           "l2": (f"inputs larger than L2 ({(1 << n) * 8 / 2**30:g} GiB state vs 129 MB); no flush"
+                  if (1 << n) * 8 > 129e6 else "state fits L2: timed passes may hit L2"),
            "parallelism": f"replicas x{world}"}
     cfg.update({k: v for k, v in kw.items() if k != "mode"})
     cfg["mode"] = mode_name(Q, kw)
@@ -421,7 +430,24 @@ def run_configs(Q, torch, np, args):
     st = torch.cuda.current_stream().cuda_stream
     F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
 
+    def want(name):
+        return args.only_config in (None, name)
+
     # config 1: QFT n=28 complex128 from a seeded basis state, per-gate vs contraction k=2..5
+    if want("qft_n28_c128"):
+        out["qft_n28_c128"] = config_qft(Q, torch, np, st, args)
+    if want("random_n32_cz_tensor"):
+        out["random_n32_cz_tensor"] = config_n32(Q, torch, np, st, args)
+    if want("ucc_batched_n20"):
+        out["ucc_batched_n20"] = config_ucc(Q, torch, np, st, args)
+    if want("hea_adjoint_n24"):
+        out["hea_adjoint_n24"] = config_hea(Q, torch, np, st, args)
+    return out
+
+
+def config_qft(Q, torch, np, st, args):
+    from paper_2509_04955_gb300 import workloads as W
+    F = Q.QS_MODE_FUSED
     n = 28
     g = W.qft(n)
     x = W.random_basis_index(n, 28)
@@ -442,9 +468,13 @@ def run_configs(Q, torch, np, args):
         Q.qs_plan_free(plan)
         del full
     Q.qs_state_free(s)
-    out["qft_n28_c128"] = c1
+    return c1
 
+
+def config_n32(Q, torch, np, st, args):
     # config 2: random n=32 depth 40 with CZ, complex64 on tensor cores (6-qubit blocks)
+    from paper_2509_04955_gb300 import workloads as W
+    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
     n = 32
     g = W.random_layered(n, 40, seed=0, entangler="cz")
     s = Q.qs_state_alloc(n, Q.QS_C64, st)
@@ -475,10 +505,14 @@ def run_configs(Q, torch, np, args):
             Q.qs_plan_free(plan)
         Q.qs_state_free(ref)
     Q.qs_state_free(s)
-    out["random_n32_cz_tensor"] = c2
+    return c2
 
+
+def config_ucc(Q, torch, np, st, args):
     # config 3: UCC-style n=20 complex64, 400 Pauli exponentials, B=64 theta ~ N(0, 0.1),
     # one CUDA graph (device-resolved angles) + <H> for a 300-term Pauli sum per state
+    from paper_2509_04955_gb300 import workloads as W
+    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
     n, B = 20, 64
     g, _ = W.ucc(n, 400, seed=0)
     th = W.thetas_normal(400, 1, sigma=0.1, batch=B)
@@ -504,9 +538,12 @@ def run_configs(Q, torch, np, args):
         Q.qs_plan_free(plan)
     for sv in states:
         Q.qs_state_free(sv)
-    out["ucc_batched_n20"] = c3
+    return c3
 
+
+def config_hea(Q, torch, np, st, args):
     # config 4: HEA n=24, 12 layers (576 parameters), adjoint gradient of a 150-term <H>
+    from paper_2509_04955_gb300 import workloads as W
     n = 24
     g, p = W.hea(n, 12)
     th = W.thetas_uniform(p, 4)
@@ -524,8 +561,7 @@ def run_configs(Q, torch, np, args):
         c4[dname] = {"ms": wall, "expval": e}
         Q.qs_state_free(s)
     c4["max_abs_grad_diff_c64_vs_c128"] = float(np.abs(grads["c64"] - grads["c128"]).max())
-    out["hea_adjoint_n24"] = c4
-    return out
+    return c4
 
 
 def kernel_hash() -> str:
