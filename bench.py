@@ -285,11 +285,11 @@ def main():
     extra = {}
     if tc_dom:
         alg_tflops = 512.0 * (1 << n) / (kms * 1e-3) / 1e12     # 8 * 2^6 real flops per amplitude
-        mult = 3 if kw.get("tc_precision", 3) in (0, 3) else 1
-        extra["tensor_pipe"] = {"algorithmic_tflops": alg_tflops, "executed_bf16_tflops": alg_tflops * 2 * mult,
+        mult = 3 if kw.get("tc_precision", 4) in (0, 3, 4) else 1
+        extra["tensor_pipe"] = {"algorithmic_tflops": alg_tflops, "executed_f16_tflops": alg_tflops * 2 * mult,
                                 "bf16_peak_tflops": bf16_peak, "executed_frac": alg_tflops * 2 * mult / bf16_peak,
-                                "note": "complex 64x64 block as a real 128x128 GEMM: 2x the complex flops; "
-                                        "bf16x3 runs 3 MMAs"}
+                                "note": "complex 64x64 block as a real 128x128 GEMM: 2x the complex flops; the "
+                                        "fp16 / bf16 hi-lo split runs 3 MMAs (fp16 and bf16 share the MMA rate)"}
 
     # -- per-gate comparator (same circuit, same state)
     if not args.no_per_gate:
@@ -479,7 +479,8 @@ def config_n32(Q, torch, np, st, args):
     g = W.random_layered(n, 40, seed=0, entangler="cz")
     s = Q.qs_state_alloc(n, Q.QS_C64, st)
     c2 = {"workload": "random layered n=32 depth 40, CZ entanglers, complex64 (32 GiB)", "gates": len(g)}
-    for name, opts in (("tensor_bf16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=3)),
+    for name, opts in (("tensor_fp16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=4)),
+                       ("tensor_bf16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=3)),
                        ("tensor_bf16", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=1)),
                        ("fused_cuda_cores_k2", Q.make_opts(mode=F, fuse_k=2, tile_qubits=13, low_qubits=4))):
         plan = Q.qs_plan_create(n, Q.QS_C64, g, opts)
@@ -496,7 +497,7 @@ def config_n32(Q, torch, np, st, args):
         Q.qs_state_set_basis(ref, 0)
         c2["c128_fused_ms"] = device_ms(torch, lambda: Q.qs_plan_execute(pr, ref))
         Q.qs_plan_free(pr)
-        for name in ("tensor_bf16x3", "tensor_bf16"):
+        for name in ("tensor_fp16x3", "tensor_bf16x3", "tensor_bf16"):
             plan = c2[name].pop("plan")
             Q.qs_state_set_basis(s, 0)
             Q.qs_plan_execute(plan, s)

@@ -96,7 +96,9 @@ typedef struct {
   int32_t tile_qubits;   /* m: qubits staged per shared-memory tile (6..14); 0 = auto */
   int32_t low_qubits;    /* L: qubits 0..L-1 always in the tile (coalescing); 0 = auto */
   int32_t paper_mode;    /* 1 = contract only the merges of Section 3.4 (1q(x)1q, same-qubit, same-(c,t) CU) */
-  int32_t tc_precision;  /* tensor mode: 1 = bf16, 3 = bf16x3 split (default) */
+  int32_t tc_precision;  /* tensor mode: 4 = fp16 hi/lo split with three products and a power-of-two
+                            pre-scale of the amplitudes (default; about 2^-22 relative per pass),
+                            3 = bf16 hi/lo split, three products (about 2^-16), 1 = bf16, one product */
   int32_t threads;       /* CUDA threads per tile CTA; 0 = auto */
   int32_t fuse_parametric; /* 1 = parametric gates may join dense blocks, whose matrices are then
                               rebuilt from theta on the device at every execution (per batch row).

@@ -242,7 +242,7 @@ void build_device_blocks(qs_plan_s& p, int rows, cudaStream_t st) {
   const size_t G = std::max<size_t>(1, p.gates.size());
   CK(launch_build_blocks(p.d_dblocks.as<DevBlock>(), (int)p.h_dblocks.size(), p.d_dmem.as<DevMember>(),
                          p.d_gtab.as<double2>(), (int64_t)(16 * G), rows, p.d_btab.as<double2>(), p.btab_elems,
-                         p.d_wimg.as<uint16_t>(), (int64_t)p.h_wimg.size(), st));
+                         p.d_wimg.as<uint16_t>(), (int64_t)p.h_wimg.size(), p.tc_prec == 4 ? 1 : 0, st));
 }
 
 void upload(qs_plan_s& p) {
@@ -363,7 +363,35 @@ float bf16_to_float(uint16_t h) {
   return f;
 }
 
-// Byte offset of bf16 element (row, k) in a K-major 128-byte-swizzled operand
+// fp16 with round-to-nearest-even (host side, for the tensor-core W image);
+// subnormals kept, |f| >= 65520 rounds to infinity.
+uint16_t f16_rne(float f) {
+  uint32_t x;
+  std::memcpy(&x, &f, 4);
+  const uint16_t sign = (uint16_t)((x >> 16) & 0x8000u);
+  const uint32_t ax = x & 0x7fffffffu;
+  if (ax > 0x7f800000u) return (uint16_t)(sign | 0x7e00u);
+  if (ax >= 0x477ff000u) return (uint16_t)(sign | 0x7c00u);
+  if (ax < 0x38800000u) {   // below 2^-14: a multiple of 2^-24 (the scaling is exact)
+    const float q = std::fabs(f) * 16777216.0f;
+    return (uint16_t)(sign | (uint16_t)std::nearbyint(q));   // 1024 encodes the smallest normal
+  }
+  uint32_t h = ((ax >> 23) - 112u) << 10 | ((ax >> 13) & 0x3ffu);
+  const uint32_t rem = ax & 0x1fffu;
+  if (rem > 0x1000u || (rem == 0x1000u && (h & 1u))) ++h;
+  return (uint16_t)(sign | h);
+}
+
+float f16_to_float(uint16_t h) {
+  const uint32_t e = (h >> 10) & 0x1fu, m = h & 0x3ffu;
+  float v;
+  if (e == 0) v = std::ldexp((float)m, -24);
+  else if (e == 31) v = m ? NAN : INFINITY;
+  else v = std::ldexp((float)(m | 0x400u), (int)e - 25);
+  return (h & 0x8000u) ? -v : v;
+}
+
+// Byte offset of a 16-bit element (row, k) in a K-major 128-byte-swizzled operand
 // of 128 rows (two 16 KiB atoms of 64 elements along K).
 size_t sw128_offset_host(uint32_t row, uint32_t k) {
   const uint32_t atom = k >> 6, kk = k & 63;
@@ -372,21 +400,30 @@ size_t sw128_offset_host(uint32_t row, uint32_t k) {
 }
 
 // W image of a 64x64 complex block U: element (n, k) of the N x K operand is
-// W[k][n] of the real embedding (see the tensor-core kernel), split into bf16
-// hi (first 32 KiB) and lo (second 32 KiB) parts.
-void build_w_image(const double2* U, uint16_t* img) {
+// W[k][n] of the real embedding (see the tensor-core kernel), rounded to FP32
+// and split into hi (first 32 KiB) and lo (second 32 KiB) parts: fp16 for
+// tensor-core precision 4, bf16 otherwise (the same steps as the device builder).
+void build_w_image(const double2* U, uint16_t* img, bool half) {
   for (uint32_t nn = 0; nn < 128; ++nn)
     for (uint32_t k = 0; k < 128; ++k) {
       const uint32_t co = nn >> 1, b = nn & 1, ci = k >> 1, a = k & 1;
-      const double ur = U[co * 64 + ci].x, ui = U[co * 64 + ci].y;
-      const double w = (a == 0) ? (b == 0 ? ur : ui) : (b == 0 ? -ui : ur);
-      const uint16_t hi = bf16_rne((float)w);
-      const uint16_t lo = bf16_rne((float)(w - (double)bf16_to_float(hi)));
+      const float ur = (float)U[co * 64 + ci].x, ui = (float)U[co * 64 + ci].y;
+      const float w = (a == 0) ? (b == 0 ? ur : ui) : (b == 0 ? -ui : ur);
+      uint16_t hi, lo;
+      if (half) {
+        hi = f16_rne(w);
+        lo = f16_rne(w - f16_to_float(hi));
+      } else {
+        hi = bf16_rne(w);
+        lo = bf16_rne(w - bf16_to_float(hi));
+      }
       const size_t off = sw128_offset_host(nn, k) / 2;
       img[off] = hi;
       img[16384 + off] = lo;
     }
 }
+
+float w_to_float(uint16_t v, bool half) { return half ? f16_to_float(v) : bf16_to_float(v); }
 
 // Records a block whose matrix is rebuilt on the device from theta (kind: 0
 // dense, 1 diagonal, 2 tensor-core W image; out = table offset or image index).
@@ -503,7 +540,7 @@ void emit_tc_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
   if (blk.parametric)
     register_device_block(P, blk, 2, (int64_t)P.tcdesc.size());   // W image rebuilt per row on the device
   else
-    build_w_image(P.h_btab.data() + P.block_off[r.block], P.h_wimg.data() + w0);
+    build_w_image(P.h_btab.data() + P.block_off[r.block], P.h_wimg.data() + w0, P.tc_prec == 4);
   P.tc_param.push_back(blk.parametric ? 1 : 0);
   DevOp d;
   std::memset(&d, 0, sizeof(d));
@@ -566,8 +603,9 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   bool tensor = p->mode == QS_MODE_TENSOR;
   if (tensor) {
     if (dt != QS_C64) throw Error(QS_ERR_UNSUPPORTED, "tensor-core mode needs complex64 states");
-    require(o.tc_precision == 0 || o.tc_precision == 1 || o.tc_precision == 3, "tc_precision must be 1 or 3");
-    p->tc_prec = o.tc_precision == 0 ? 3 : o.tc_precision;
+    require(o.tc_precision == 0 || o.tc_precision == 1 || o.tc_precision == 3 || o.tc_precision == 4,
+            "tc_precision must be 1, 3 or 4");
+    p->tc_prec = o.tc_precision == 0 ? 4 : o.tc_precision;
     require(o.reserved[1] == 0 || o.reserved[1] == 1, "tensor-core pipeline (reserved[1]) must be 0 or 1");
     p->tc_pipe = o.reserved[1];
     if (n < 13) tensor = false;   // a tensor-core tile needs 13 qubits; smaller states use CUDA-core blocks
@@ -901,13 +939,14 @@ qs_status qs_plan_check_device_blocks(qs_plan_t p, qs_state_t s, const double* t
         // compare the W image with one built on the host from the host product: the
         // value the MMAs use is hi + lo (hi and lo alone may trade one ulp at a tie)
         std::vector<uint16_t> img(32768);
-        build_w_image(p->h_btab.data() + p->block_off[b], img.data());
+        build_w_image(p->h_btab.data() + p->block_off[b], img.data(), p->tc_prec == 4);
         for (size_t st = 0; st < p->steps.size(); ++st)
           if (p->steps[st].kind == 1 && p->exec_ops[p->pass_ops[st].first].block == (int)b) {
             const uint16_t* dv = wdev.data() + (size_t)p->steps[st].idx * 32768;
             for (int e = 0; e < 16384; ++e) {
-              const double wh = (double)bf16_to_float(img[e]) + (double)bf16_to_float(img[16384 + e]);
-              const double wd = (double)bf16_to_float(dv[e]) + (double)bf16_to_float(dv[16384 + e]);
+              const bool hf = p->tc_prec == 4;
+              const double wh = (double)w_to_float(img[e], hf) + (double)w_to_float(img[16384 + e], hf);
+              const double wd = (double)w_to_float(dv[e], hf) + (double)w_to_float(dv[16384 + e], hf);
               worst = std::max(worst, std::fabs(wh - wd));
             }
           }

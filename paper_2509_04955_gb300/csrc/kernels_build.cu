@@ -10,6 +10,7 @@
 // bf16 hi / lo W image in the K-major 128-byte-swizzled layout the
 // tensor-core pass loads (real embedding W[2c+a][2c'+b] of U[c'][c]).
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "qs_internal.h"
@@ -39,7 +40,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_blocks(const DevBlock* 
                                                                  const DevMember* __restrict__ mem,
                                                                  const double2* __restrict__ gtab, int64_t gstride,
                                                                  double2* __restrict__ btab, int64_t bstride,
-                                                                 uint16_t* __restrict__ wimg, int64_t wstride) {
+                                                                 uint16_t* __restrict__ wimg, int64_t wstride,
+                                                                 int whalf) {
   extern __shared__ double2 M[];   // D x D, row-major: M[r * D + c]
   const DevBlock blk = blocks[blockIdx.x];
   const int row = blockIdx.y;
@@ -112,7 +114,8 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_blocks(const DevBlock* 
     for (int i = threadIdx.x; i < D; i += kBuildThreads) out[i] = M[i * D + i];
   } else {
     // W image: 16-byte chunks of 8 consecutive k (4 input columns) of output row nn,
-    // K atom `atom`, 128-byte swizzle; bf16 hi / lo split in FP32 (the product is FP64)
+    // K atom `atom`, 128-byte swizzle; hi / lo split in FP32 (the product is FP64),
+    // fp16 parts when `whalf` (the pass splits the state into fp16), else bf16
     uint16_t* img = wimg + (int64_t)row * wstride + blk.out * 32768;
     for (int e = threadIdx.x; e < 2048; e += kBuildThreads) {
       const int atom = e >> 10, nn = (e >> 3) & 127, ch = e & 7;
@@ -123,11 +126,19 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_blocks(const DevBlock* 
         const double2 uv = M[co * 64 + ci0 + q];
         const float ur = (float)uv.x, ui = (float)uv.y;
         const float w0 = b == 0 ? ur : ui, w1 = b == 0 ? -ui : ur;   // W[nn][2 ci], W[nn][2 ci + 1]
-        const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
-        hi[q] = *(const uint32_t*)&h;
-        lo[q] = *(const uint32_t*)&l;
+        if (whalf) {
+          const __half2 h = __floats2half2_rn(w0, w1);
+          const float2 hf = __half22float2(h);
+          const __half2 l = __floats2half2_rn(w0 - hf.x, w1 - hf.y);
+          hi[q] = *(const uint32_t*)&h;
+          lo[q] = *(const uint32_t*)&l;
+        } else {
+          const __nv_bfloat162 h = __floats2bfloat162_rn(w0, w1);
+          const float2 hf = __bfloat1622float2(h);
+          const __nv_bfloat162 l = __floats2bfloat162_rn(w0 - hf.x, w1 - hf.y);
+          hi[q] = *(const uint32_t*)&h;
+          lo[q] = *(const uint32_t*)&l;
+        }
       }
       const int off = (atom * 16384 + nn * 128 + ((ch ^ (nn & 7)) << 4)) >> 1;   // uint16 units
       *(uint4*)(img + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
@@ -150,12 +161,12 @@ cudaError_t prepare_build_blocks() {
 
 cudaError_t launch_build_blocks(const DevBlock* blocks, int nblocks, const DevMember* mem, const double2* gtab,
                                 int64_t gstride, int rows, double2* btab, int64_t bstride, uint16_t* wimg,
-                                int64_t wstride, cudaStream_t st) {
+                                int64_t wstride, int whalf, cudaStream_t st) {
   if (nblocks == 0 || rows == 0) return cudaSuccess;
   if (!g_build_ready) return cudaErrorInvalidConfiguration;   // not prepared
   const int smem = 64 * 64 * (int)sizeof(double2);
   k_build_blocks<<<dim3(nblocks, rows), kBuildThreads, smem, st>>>(blocks, mem, gtab, gstride, btab, bstride, wimg,
-                                                                   wstride);
+                                                                   wstride, whalf);
   note_launch();
   return cudaGetLastError();
 }

@@ -15,15 +15,21 @@
 // and stored, then tile i+1 is converted into the other A buffer and its MMAs
 // are issued into the other accumulator (A operands and accumulators are
 // double-buffered, 256 TMEM columns).
-// Precision: A and W are split into bf16 hi + lo parts; bf16x3 accumulates
-// lo*hi + hi*lo + hi*hi (about 16 significant bits per product), bf16 takes
-// hi*hi only. Operands sit in shared memory in the K-major 128-byte-swizzled
+// Precision (PREC): A and W are split into hi + lo parts and the MMAs
+// accumulate lo*hi + hi*lo + hi*hi. PREC 4 (default) splits into fp16: 11 + 11
+// significant bits, about 2^-22 relative per product; the amplitudes are first
+// multiplied by 2^s, s = min(floor(n / 2), 15) (exact), so that typical
+// amplitudes of a 2^n state (about 2^(-n/2)) are not fp16 subnormals while the
+// largest possible one (1) stays far below the fp16 maximum, and the outputs
+// are multiplied by 2^-s. PREC 3 splits into bf16 (8 + 8 bits, about 2^-16),
+// PREC 1 takes bf16 hi*hi only. Operands sit in shared memory in the K-major 128-byte-swizzled
 // layout; the W image (hi and lo, 64 KiB) is prepared on the host and stays
 // resident in shared memory for all tiles of the CTA.
 //
 // Every wait on an mbarrier is bounded: on timeout the kernel sets *err,
 // stops taking tiles, frees its tensor memory and returns.
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include "qs_internal.h"
@@ -50,15 +56,40 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
   return d;
 }
 
-// Instruction descriptor: kind::f16 with BF16 A/B, FP32 D, both K-major, M = 128, N = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// Instruction descriptor: kind::f16, FP32 D, both operands K-major, M = 128,
+// N = 128; A and B both BF16 (PREC 1, 3) or both FP16 (PREC 4).
+template <int PREC>
+constexpr uint32_t idesc_for() {
+  return (1u << 4) | (PREC == 4 ? 0u : ((1u << 7) | (1u << 10))) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+}
 
+template <int PREC>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem),
-      "l"(a), "l"(b), "r"(kIdesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc_for<PREC>()), "r"(acc));
+}
+
+// hi / lo split of one complex amplitude (scaled by `scale` first for PREC 4),
+// packed as two 16-bit values (re low, im high) each.
+template <int PREC>
+__device__ __forceinline__ void split_amp(float2 a, float scale, uint32_t& hi, uint32_t& lo) {
+  if constexpr (PREC == 4) {
+    const float x = a.x * scale, y = a.y * scale;
+    const __half2 h = __floats2half2_rn(x, y);
+    const float2 hf = __half22float2(h);
+    const __half2 l = __floats2half2_rn(x - hf.x, y - hf.y);
+    hi = *(const uint32_t*)&h;
+    lo = *(const uint32_t*)&l;
+  } else {
+    const __nv_bfloat162 h = __floats2bfloat162_rn(a.x, a.y);
+    const float2 hf = __bfloat1622float2(h);
+    const __nv_bfloat162 l = __floats2bfloat162_rn(a.x - hf.x, a.y - hf.y);
+    hi = *(const uint32_t*)&h;
+    lo = *(const uint32_t*)&l;
+  }
 }
 
 __device__ __forceinline__ void mma_commit(uint32_t mbar) {
@@ -107,23 +138,23 @@ __device__ __forceinline__ uint32_t sw128_offset(uint32_t row, uint32_t k) {
 template <int PREC>
 __device__ __forceinline__ void issue_tile_mmas(uint32_t tmem_d, uint32_t ah, uint32_t al, uint32_t wh, uint32_t wl) {
   uint32_t acc = 0;
-  if (PREC == 3) {
+  if (PREC >= 3) {
 #pragma unroll
     for (int ks = 0; ks < 8; ++ks) {     // lo * hi
       const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
-      mma_bf16(tmem_d, smem_desc(al + o), smem_desc(wh + o), acc);
+      mma_bf16<PREC>(tmem_d, smem_desc(al + o), smem_desc(wh + o), acc);
       acc = 1;
     }
 #pragma unroll
     for (int ks = 0; ks < 8; ++ks) {     // hi * lo
       const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
-      mma_bf16(tmem_d, smem_desc(ah + o), smem_desc(wl + o), 1);
+      mma_bf16<PREC>(tmem_d, smem_desc(ah + o), smem_desc(wl + o), 1);
     }
   }
 #pragma unroll
   for (int ks = 0; ks < 8; ++ks) {       // hi * hi
     const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
-    mma_bf16(tmem_d, smem_desc(ah + o), smem_desc(wh + o), acc);
+    mma_bf16<PREC>(tmem_d, smem_desc(ah + o), smem_desc(wh + o), acc);
     acc = 1;
   }
 }
@@ -136,7 +167,8 @@ template <int PREC, bool MULTI>
 __global__ void __launch_bounds__(kTc2Threads, 1)
     k_tc_block(float2* __restrict__ psi0, void* const* __restrict__ psis, TcPassDesc p,
                const uint4* __restrict__ wimg, int64_t wstride16, int lg_tiles1, uint64_t ntiles,
-               int* __restrict__ err) {
+               float ascale, int* __restrict__ err) {
+  // ascale: factor applied to the amplitudes before the fp16 split (PREC 4), undone on output
   // ntiles = 2^lg_tiles1 x states; tile index t covers state t >> lg_tiles1 (batched execution).
   // Each CTA takes a contiguous range of tiles; with per-state W images
   // (wstride16 = uint4 stride, non-zero for parametric blocks) the image is
@@ -213,17 +245,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
     for (int j = 0; j < 8; ++j) {
       uint32_t hi[4], lo[4];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const float2 a = v[4 * j + q];
-        const __nv_bfloat162 h = __floats2bfloat162_rn(a.x, a.y);
-        const float2 hf = __bfloat1622float2(h);
-        const __nv_bfloat162 l = __floats2bfloat162_rn(a.x - hf.x, a.y - hf.y);
-        hi[q] = *(const uint32_t*)&h;
-        lo[q] = *(const uint32_t*)&l;
-      }
+      for (int q = 0; q < 4; ++q) split_amp<PREC>(v[4 * j + q], ascale, hi[q], lo[q]);
       const uint32_t off = row * 128 + ((j ^ (row & 7)) << 4);
       *(uint4*)(a_hi + off) = make_uint4(hi[0], hi[1], hi[2], hi[3]);
-      if (PREC == 3) *(uint4*)(a_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
+      if (PREC >= 3) *(uint4*)(a_lo + off) = make_uint4(lo[0], lo[1], lo[2], lo[3]);
     }
   };
   auto issue = [&](int b) {
@@ -258,8 +283,10 @@ __global__ void __launch_bounds__(kTc2Threads, 1)
       for (int chunk = 0; chunk < 2; ++chunk) {
         float o[32];
         tmem_ld32(taddr + chunk * 32, o);
+        const float inv = 1.0f / ascale;   // a power of two: exact
 #pragma unroll
-        for (int q = 0; q < 16; ++q) psi[rb | hcoff[chunk * 16 + q]] = make_float2(o[2 * q], o[2 * q + 1]);
+        for (int q = 0; q < 16; ++q)
+          psi[rb | hcoff[chunk * 16 + q]] = make_float2(o[2 * q] * inv, o[2 * q + 1] * inv);
       }
     }
     if (t + ts < t_end) {
@@ -335,12 +362,13 @@ constexpr int kTcbThreads = (kTcbComputeWarps + 2) * 32;  // + producer warp + M
 constexpr int kTcbSlotBytes = 65536;
 constexpr uint32_t kTcbTmemCols = 512;
 
+template <int PREC>
 __device__ __forceinline__ void mma_bf16_tmem_a(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(b), "r"(kIdesc), "r"(acc));
+      "r"(tmem_a), "l"(b), "r"(idesc_for<PREC>()), "r"(acc));
 }
 
 __device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
@@ -368,23 +396,23 @@ template <int PREC>
 __device__ __forceinline__ void issue_tile_mmas_ta(uint32_t tmem_d, uint32_t a_hi, uint32_t wh, uint32_t wl) {
   const uint32_t a_lo = a_hi + 64;
   uint32_t acc = 0;
-  if (PREC == 3) {
+  if (PREC >= 3) {
 #pragma unroll
     for (int ks = 0; ks < 8; ++ks) {     // lo * hi
       const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
-      mma_bf16_tmem_a(tmem_d, a_lo + ks * 8, smem_desc(wh + o), acc);
+      mma_bf16_tmem_a<PREC>(tmem_d, a_lo + ks * 8, smem_desc(wh + o), acc);
       acc = 1;
     }
 #pragma unroll
     for (int ks = 0; ks < 8; ++ks) {     // hi * lo
       const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
-      mma_bf16_tmem_a(tmem_d, a_hi + ks * 8, smem_desc(wl + o), 1);
+      mma_bf16_tmem_a<PREC>(tmem_d, a_hi + ks * 8, smem_desc(wl + o), 1);
     }
   }
 #pragma unroll
   for (int ks = 0; ks < 8; ++ks) {       // hi * hi
     const uint32_t o = (ks >> 2) * kTcAtomBytes + (ks & 3) * 32;
-    mma_bf16_tmem_a(tmem_d, a_hi + ks * 8, smem_desc(wh + o), acc);
+    mma_bf16_tmem_a<PREC>(tmem_d, a_hi + ks * 8, smem_desc(wh + o), acc);
     acc = 1;
   }
 }
@@ -406,11 +434,30 @@ __device__ __forceinline__ void xor_stage(float2 (&v)[16], bool on) {
 // state's theta) every CTA takes a contiguous range of tiles and the producer
 // reloads W by bulk copy when the range crosses into the next state, once the
 // MMAs of the previous tile have completed.
+// Exchange of in-thread bit J (slot index) with lane bit M: the lane with
+// bit M clear keeps its slots with bit J clear and receives, into the slots
+// with bit J set, its partner's slots with bit J clear; the partner the reverse.
+template <int J, int M>
+__device__ __forceinline__ void xchg_stage(float2 (&v)[16], bool up) {
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    if (q & (1 << J)) continue;
+    const int q1 = q | (1 << J);
+    const float2 send = up ? v[q] : v[q1];
+    float2 recv;
+    recv.x = __shfl_xor_sync(0xffffffffu, send.x, 1 << M);
+    recv.y = __shfl_xor_sync(0xffffffffu, send.y, 1 << M);
+    if (up) v[q] = recv;
+    else v[q1] = recv;
+  }
+}
+
 template <int PREC, bool MULTI>
 __global__ void __launch_bounds__(kTcbThreads, 1)
     k_tc_bulk(float2* __restrict__ psi0, void* const* __restrict__ psis, TcPassDesc p,
               const uint4* __restrict__ wimg, int64_t wstride16, int lg_tiles1, uint64_t ntiles,
-              int* __restrict__ err) {
+              float ascale, int* __restrict__ err) {
+  // ascale: factor applied to the amplitudes before the fp16 split (PREC 4), undone on output
   extern __shared__ __align__(1024) unsigned char tcb_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tcb_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* slots = smem;                                   // 2 x 64 KiB
@@ -421,8 +468,8 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
   uint64_t* coff = runoff + 64;                                  // 64: global offset of column c
   uint32_t* lamcol = (uint32_t*)(coff + 64);                     // 64: tile-local index of column c
   int32_t* qpos = (int32_t*)(lamcol + 64);                       // tile[13], row[7], col[6], p, pad
-  uint64_t* bar = (uint64_t*)(qpos + 28);   // full[2] empty[2] afull[2] mdone[2] dfree[2] wfull
-  uint32_t* tmem_slot = (uint32_t*)(bar + 11);
+  uint64_t* bar = (uint64_t*)(qpos + 28);   // full[2] empty[2] afull[2] mdone[2] dfree[2] wfull wfree
+  uint32_t* tmem_slot = (uint32_t*)(bar + 12);
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -437,9 +484,9 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
     while (pp < 13 && p.tile[pp] == pp) ++pp;
     qpos[26] = pp;
     s_abort = 0;
-    for (int i = 0; i < 11; ++i)   // full/mdone/wfull: 1 arrival; empty/afull/dfree: one per warp of a group
+    for (int i = 0; i < 12; ++i)   // full/mdone/wfull/wfree: 1 arrival; empty/afull/dfree: one per warp of a group
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)),
-                   "r"((i >= 2 && i != 6 && i != 7 && i != 10) ? kTcbComputeWarps / 2 : 1));
+                   "r"((i >= 2 && i != 6 && i != 7 && i < 10) ? kTcbComputeWarps / 2 : 1));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   // tile sequence of this CTA: tt = t_begin + i * tstep, i < my
@@ -503,6 +550,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
   uint64_t* mdone = bar + 6;
   uint64_t* dfree = bar + 8;
   uint64_t* wfull = bar + 10;
+  uint64_t* wfree = bar + 11;   // completes when the MMAs on a state's W image are done
   auto tile_of = [&](uint64_t i) -> uint64_t { return t_begin + i * tstep; };
   auto state_ptr = [&](uint64_t tt) -> float2* {
     if constexpr (MULTI) return (float2*)psis[tt >> lg_tiles1];
@@ -547,8 +595,13 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
             "l"(src + runoff[j]), "r"(runb), "r"(smem_u32(full + s))
             : "memory");
       if (new_state(i)) {
-        // W of the next state: once the MMAs of tile i - 1 (the last on the old W) are done
-        if (!mbar_wait_warp(smem_u32(mdone + ((i - 1) & 1)), (uint32_t)(((i - 1) >> 1) & 1))) {
+        // W of the next state, once the MMAs of tile i - 1 (the last on the old W) are
+        // done: the MMA thread commits `wfree` after them. (The accumulator barriers
+        // cannot tell: the producer may be up to three tiles ahead of the MMAs, and a
+        // parity wait is exact only within one phase.) wfree completes once per state
+        // boundary and its next completion needs this reload, so phase w_issued is
+        // the one to wait for.
+        if (!mbar_wait_warp(smem_u32(wfree), (uint32_t)(w_issued & 1))) {
           if (lane == 0) fail(1);
           ++i;   // tile i's copies are in flight
           break;
@@ -590,6 +643,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         issue_tile_mmas_ta<PREC>(tmem + 256 + a * 128, tmem + a * 128, wh, wl);
         mma_commit(smem_u32(mdone + a));
+        if (i + 1 < my && new_state(i + 1)) mma_commit(smem_u32(wfree));   // last tile on this W
       }
       // MMAs still in flight after an abort complete before the memory is released
       if (i > 0 && *(volatile int*)&s_abort) mbar_wait(smem_u32(mdone + ((i - 1) & 1)), (uint32_t)(((i - 1) >> 1) & 1));
@@ -640,16 +694,10 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
           if (xbits & 8) xor_stage<3>(v, (phi >> 3) & 1);
           uint32_t hi[16], lo[16];
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const __nv_bfloat162 h = __floats2bfloat162_rn(v[j].x, v[j].y);
-            const float2 hf = __bfloat1622float2(h);
-            const __nv_bfloat162 l = __floats2bfloat162_rn(v[j].x - hf.x, v[j].y - hf.y);
-            hi[j] = *(const uint32_t*)&h;
-            lo[j] = *(const uint32_t*)&l;
-          }
+          for (int j = 0; j < 16; ++j) split_amp<PREC>(v[j], ascale, hi[j], lo[j]);
           const uint32_t a_hi = tmem + tq + (uint32_t)s * 128 + c0;
           tmem_st16(a_hi, hi);
-          if (PREC == 3) tmem_st16(a_hi + 64, lo);
+          if (PREC >= 3) tmem_st16(a_hi + 64, lo);
         }
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -660,9 +708,21 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
         }
       }
     } else {
+      // Store coalescing: a 32-byte sector is 4 amplitudes (qubits 0 and 1). When
+      // column bit 0 (and bit 1) of the block sit on qubits 0 / 1, they are
+      // exchanged with lane bits 4 (and 3), whose row qubits are >= 3, through
+      // shuffles, so every warp store covers whole sectors. Slot q of lane l
+      // then holds (row: l with bit 4 := q bit 0 [bit 3 := q bit 1],
+      // column: q with bit 0 := l bit 4 [bit 1 := l bit 3]).
+      const bool s0 = s_col[0] <= 1, s1 = s_col[0] == 0 && s_col[1] == 1;
+      const bool l4 = (lane >> 4) & 1, l3 = (lane >> 3) & 1;
+      const uint64_t rbit4 = 1ull << s_row[4], rbit3 = 1ull << s_row[3];
       uint64_t roff = 0;
       for (int b = 0; b < 7; ++b) roff |= (uint64_t)((row >> b) & 1) << s_row[b];
+      if (s0) roff &= ~rbit4;
+      if (s1) roff &= ~rbit3;
       const uint64_t* hc = coff + half * 32;
+      const float inv = 1.0f / ascale;   // a power of two: exact
       for (uint64_t i = 0; i < my; ++i) {
         if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
         const int d = (int)(i & 1);
@@ -680,8 +740,25 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
             __syncwarp();
             if (lane == 0) mbar_arrive(smem_u32(dfree + d));
           }
+          float2 v[16];
 #pragma unroll
-          for (int q = 0; q < 16; ++q) psi[rb | hc[chunk * 16 + q]] = make_float2(o[2 * q], o[2 * q + 1]);
+          for (int q = 0; q < 16; ++q) v[q] = make_float2(o[2 * q] * inv, o[2 * q + 1] * inv);
+          if (s0) xchg_stage<0, 4>(v, l4);
+          if (s1) xchg_stage<1, 3>(v, l3);
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            uint64_t a = rb;
+            int qq = q;
+            if (s0) {
+              if (q & 1) a |= rbit4;
+              qq = (qq & ~1) | (int)l4;
+            }
+            if (s1) {
+              if (q & 2) a |= rbit3;
+              qq = (qq & ~2) | ((int)l3 << 1);
+            }
+            psi[a | hc[chunk * 16 + qq]] = v[q];
+          }
         }
       }
     }
@@ -695,7 +772,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
 
 size_t tc_bulk_smem_bytes() {
   return 2 * (size_t)kTcbSlotBytes + 2 * (size_t)kTcOperandBytes + 4 * 256 * 8 + 64 * 8 * 2 + 64 * 4 + 28 * 4 +
-         11 * 8 + 16 + 1024;
+         12 * 8 + 16 + 1024;
 }
 
 size_t tc_smem_bytes() { return 6 * (size_t)kTcOperandBytes + 64 * 8 + 32 + 1024; }
@@ -704,19 +781,24 @@ static bool g_tc_ready = false;
 static int g_tc_sms = 0;
 
 // Host-side set-up (outside any stream capture): shared-memory attribute of
-// both precision instances and the SM count.
+// every instance and the SM count.
+template <int PREC>
+static cudaError_t set_tc_attributes(int smem, int smem_bulk) {
+  cudaError_t e = cudaFuncSetAttribute(k_tc_block<PREC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<PREC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_bulk<PREC, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_tc_bulk<PREC, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
+  return e;
+}
+
 cudaError_t prepare_tc_pass() {
   if (g_tc_ready) return cudaSuccess;
-  const int smem = (int)tc_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_tc_block<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_block<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  const int smem_bulk = (int)tc_bulk_smem_bytes();
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<3, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<1, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<3, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc_bulk<1, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem_bulk);
+  const int smem = (int)tc_smem_bytes(), smem_bulk = (int)tc_bulk_smem_bytes();
+  cudaError_t e = set_tc_attributes<1>(smem, smem_bulk);
+  if (e == cudaSuccess) e = set_tc_attributes<3>(smem, smem_bulk);
+  if (e == cudaSuccess) e = set_tc_attributes<4>(smem, smem_bulk);
   if (e != cudaSuccess) return e;
   int dev = 0;
   cudaGetDevice(&dev);
@@ -725,39 +807,44 @@ cudaError_t prepare_tc_pass() {
   return cudaSuccess;
 }
 
+// 2^s with s = min(floor(n / 2), 15): the fp16 pre-scale of PREC 4 (|amp| <= 1,
+// so scaled values stay <= 32768 < 65504, the largest fp16).
+float tc_amp_scale(int n, int prec) {
+  if (prec != 4) return 1.0f;
+  const int s = n / 2 < 15 ? n / 2 : 15;
+  return (float)(1u << s);
+}
+
+template <int PREC>
+static void launch_tc_instance(int pipeline, bool multi, unsigned grid, size_t smem, cudaStream_t st, float2* psi,
+                               void* const* psis, const TcPassDesc& p, const uint4* w, int64_t ws16, int lg,
+                               uint64_t ntiles, float sc, int* err) {
+  if (pipeline == 0) {
+    if (multi) k_tc_bulk<PREC, true><<<grid, kTcbThreads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err);
+    else k_tc_bulk<PREC, false><<<grid, kTcbThreads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err);
+  } else {
+    if (multi) k_tc_block<PREC, true><<<grid, kTc2Threads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err);
+    else k_tc_block<PREC, false><<<grid, kTc2Threads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err);
+  }
+}
+
 cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
                                    const TcPassDesc& p, const void* wimg, int prec, int pipeline, int* err,
                                    cudaStream_t st) {
   if (!g_tc_ready) return cudaErrorInvalidConfiguration;   // not prepared
-  if (pipeline == 0) {
-    const uint64_t ntiles = (1ull << (n - 13)) * (uint64_t)nstates;
-    const uint64_t grid = ntiles < (uint64_t)g_tc_sms ? ntiles : (uint64_t)g_tc_sms;
-    const size_t smem = tc_bulk_smem_bytes();
-#define QS_TCB_ARGS (float2*)psi, psis, p, (const uint4*)wimg, wstride / 8, n - 13, ntiles, err
-    if (psis) {
-      if (prec == 3) k_tc_bulk<3, true><<<(unsigned)grid, kTcbThreads, smem, st>>>(QS_TCB_ARGS);
-      else k_tc_bulk<1, true><<<(unsigned)grid, kTcbThreads, smem, st>>>(QS_TCB_ARGS);
-    } else {
-      if (prec == 3) k_tc_bulk<3, false><<<(unsigned)grid, kTcbThreads, smem, st>>>(QS_TCB_ARGS);
-      else k_tc_bulk<1, false><<<(unsigned)grid, kTcbThreads, smem, st>>>(QS_TCB_ARGS);
-    }
-#undef QS_TCB_ARGS
-    note_launch();
-    return cudaGetLastError();
-  }
-  const size_t smem = tc_smem_bytes();
-  const int sms = g_tc_sms;
-  const uint64_t ntiles1 = 1ull << (n - 13), ntiles = ntiles1 * (uint64_t)nstates;
-  const uint64_t grid = ntiles < (uint64_t)sms ? ntiles : (uint64_t)sms;
-#define QS_TC_ARGS (float2*)psi, psis, p, (const uint4*)wimg, wstride / 8, n - 13, ntiles, err
-  if (psis) {
-    if (prec == 3) k_tc_block<3, true><<<(unsigned)grid, kTc2Threads, smem, st>>>(QS_TC_ARGS);
-    else k_tc_block<1, true><<<(unsigned)grid, kTc2Threads, smem, st>>>(QS_TC_ARGS);
-  } else {
-    if (prec == 3) k_tc_block<3, false><<<(unsigned)grid, kTc2Threads, smem, st>>>(QS_TC_ARGS);
-    else k_tc_block<1, false><<<(unsigned)grid, kTc2Threads, smem, st>>>(QS_TC_ARGS);
-  }
-#undef QS_TC_ARGS
+  if (prec != 1 && prec != 3 && prec != 4) return cudaErrorInvalidValue;
+  const uint64_t ntiles = (1ull << (n - 13)) * (uint64_t)nstates;
+  const unsigned grid = (unsigned)(ntiles < (uint64_t)g_tc_sms ? ntiles : (uint64_t)g_tc_sms);
+  const size_t smem = pipeline == 0 ? tc_bulk_smem_bytes() : tc_smem_bytes();
+  const float sc = tc_amp_scale(n, prec);
+  const bool multi = psis != nullptr;
+  const uint4* w = (const uint4*)wimg;
+  if (prec == 4)
+    launch_tc_instance<4>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err);
+  else if (prec == 3)
+    launch_tc_instance<3>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err);
+  else
+    launch_tc_instance<1>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err);
   note_launch();
   return cudaGetLastError();
 }

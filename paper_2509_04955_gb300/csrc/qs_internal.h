@@ -71,9 +71,10 @@ struct DevMember {
 };
 cudaError_t prepare_build_blocks();
 cudaError_t prepare_tc_pass();
+// whalf: tensor-core W images in fp16 hi / lo (precision 4), else bf16
 cudaError_t launch_build_blocks(const DevBlock* blocks, int nblocks, const DevMember* mem, const double2* gtab,
                                 int64_t gstride, int rows, double2* btab, int64_t bstride, uint16_t* wimg,
-                                int64_t wstride, cudaStream_t st);
+                                int64_t wstride, int whalf, cudaStream_t st);
 
 // Tensor-core pass over tiles of 128 rows x 64 columns (13 qubits).
 struct TcPassDesc {

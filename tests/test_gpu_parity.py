@@ -364,14 +364,15 @@ def test_batched_graph_matches_sequential_and_oracle(dtname):
 
 
 @pytest.mark.parametrize("n,depth,ent", [(13, 6, "cnot"), (15, 8, "cz"), (17, 5, "cnot")])
-def test_tensor_core_mode_split_bf16_matches_oracle(n, depth, ent):
-    """6-qubit blocks on tensor cores (bf16x3 products, FP32 accumulation)
-    interleaved with CUDA-core tile passes, complex64 bar 2e-5."""
+def test_tensor_core_mode_split_products_match_oracle(n, depth, ent):
+    """6-qubit blocks on tensor cores (fp16 and bf16 hi/lo split products,
+    FP32 accumulation) interleaved with CUDA-core tile passes, complex64 bar
+    2e-5, both pipelines."""
     gates = W.random_layered(n, depth, seed=n, entangler=ent)
     psi0 = W.random_state(n, 2)
     want = ref(n, gates, psi0=psi0.astype(np.complex64).astype(complex))
-    for tmin, pipe in ((6, 0), (10, 0), (6, 1)):
-        opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_precision=3, tc_min_gates=tmin, tc_pipeline=pipe)
+    for tmin, pipe, prec in ((6, 0, 4), (10, 0, 4), (6, 1, 4), (6, 0, 3), (6, 1, 3)):
+        opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_precision=prec, tc_min_gates=tmin, tc_pipeline=pipe)
         plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
         try:
             assert any(op["type"] == 3 for op in Q.qs_plan_ops(plan))
@@ -489,6 +490,37 @@ def test_batched_expectation_every_mask_case(n):
             psi = O.apply_circuit(O.basis(n, (b * 2654435761) % (1 << n)), n, gates, None)
             want = O.expval(psi, n, *H).real
             assert abs(ex[b] - want) <= 2e-5 * np.abs(H[0]).sum()
+    finally:
+        for s in states:
+            Q.qs_state_free(s)
+        Q.qs_plan_free(plan)
+
+
+@pytest.mark.parametrize("n,Bsz", [(15, 77), (16, 40)])
+@pytest.mark.parametrize("pipe", [0, 1])
+def test_batched_tensor_core_ranges_cross_states(n, Bsz, pipe):
+    """Per-CTA tile ranges of 3 tiles over states of 4 (n = 15) or 8 (n = 16)
+    tiles: most CTAs cross a state boundary mid-range and reload that state's
+    W image (rebuilt from its own theta) while earlier tiles are in flight.
+    States of every row against the oracle, complex64 bar 2e-5 (the states
+    keep most weight on |0..0>, amplitude about 0.76: the default fp16 split
+    holds the bar there, the bf16 split, about 2^-16 per pass, does not)."""
+    nterms = 8
+    gates, _ = W.ucc(n, nterms, seed=n)
+    thetas = W.thetas_normal(nterms, 10 + n, sigma=0.5, batch=Bsz)
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4,
+                                                            fuse_parametric=1, tc_pipeline=pipe))
+    states = [Q.qs_state_alloc(n, Q.QS_C64) for _ in range(Bsz)]
+    try:
+        assert any(op["type"] == 3 for op in Q.qs_plan_ops(plan))
+        for rep_ in range(2):            # capture, then graph replay
+            for s in states:
+                Q.qs_state_set_basis(s, 0)
+            Q.qs_plan_execute_batched(plan, states, thetas)
+        for b in range(Bsz):
+            out = np.empty(1 << n, dtype=np.complex64)
+            Q.qs_state_copy_to_host(states[b], out)
+            assert np.abs(out - ref(n, gates, thetas[b])).max() <= 2e-5, b
     finally:
         for s in states:
             Q.qs_state_free(s)
