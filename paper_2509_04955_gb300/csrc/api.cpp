@@ -566,7 +566,9 @@ void default_opts(qs_plan_opts& o, qs_dtype dt, int n) {
   if (o.low_qubits > o.tile_qubits) o.low_qubits = o.tile_qubits;
 }
 
-qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, const qs_plan_opts* opts) {
+// no_merge: every gate stays its own op (the reverse sweep of the adjoint gradient).
+qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, const qs_plan_opts* opts,
+                       bool no_merge = false) {
   require(n >= 1 && n <= kMaxQubits, "n out of range");
   require(dt == QS_C64 || dt == QS_C128, "bad dtype");
   require(ng == 0 || gates != nullptr, "gates is NULL");
@@ -631,6 +633,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   po.fp_weight = dt == QS_C64 ? 1.0 : 59.0;
   po.smem_weight = 1.0;
   po.fuse_parametric = o.fuse_parametric != 0;
+  po.no_merge = no_merge;
   p->blocks = contract(n, p->gates, po);
   if (tensor) {
     // A block worth a tensor-core pass (one HBM sweep) carries many gates;
@@ -1302,17 +1305,28 @@ qs_status qs_adjoint_grad(qs_state_t s, const qs_gate* gates, size_t ngates, con
     check_state(s);
     require(grad_out != nullptr || ntheta == 0, "grad_out is NULL");
     require(nterms == 0 || terms != nullptr, "terms is NULL");
-    std::unique_ptr<qs_plan_s> p(create_plan(s->n, s->dt, gates, ngates, nullptr));
+    // forward: phi = U psi with a fused plan (tile passes, CUDA cores)
+    qs_plan_opts fo;
+    std::memset(&fo, 0, sizeof(fo));
+    fo.mode = QS_MODE_FUSED;
+    std::unique_ptr<qs_plan_s> p(create_plan(s->n, s->dt, gates, ngates, &fo));
+    // reverse sweep: the reversed circuit, one op per gate, grouped into tile passes
+    std::vector<qs_gate> rev(gates, gates + ngates);
+    std::reverse(rev.begin(), rev.end());
+    qs_plan_opts ro;
+    std::memset(&ro, 0, sizeof(ro));
+    ro.mode = QS_MODE_FUSED;
+    ro.fuse_k = 1;
+    std::unique_ptr<qs_plan_s> rp(create_plan(s->n, s->dt, rev.data(), rev.size(), &ro, /*no_merge=*/true));
     upload(*p);
+    upload(*rp);
     const size_t bytes = s->bytes();
-    DevBuf phi, lam, part, aux;
+    DevBuf phi, lam, part, aux, gadj, grow_d;
     phi.ensure(bytes);
     lam.ensure(bytes);
     CK(cudaMemcpyAsync(phi.p, s->d, bytes, cudaMemcpyDeviceToDevice, s->st));
-    qs_state_s sphi;   // borrowed views (not owning)
+    qs_state_s sphi;   // borrowed view (not owning)
     sphi.n = s->n; sphi.dt = s->dt; sphi.d = phi.p; sphi.st = s->st;
-    qs_state_s slam;
-    slam.n = s->n; slam.dt = s->dt; slam.d = lam.p; slam.st = s->st;
     execute(*p, sphi, theta, ntheta);
     // lam = H phi
     group_terms(s->n, terms, nterms);
@@ -1321,31 +1335,36 @@ qs_status qs_adjoint_grad(qs_state_t s, const qs_gate* gates, size_t ngates, con
     std::vector<unsigned char> host;
     upload_pauli_apply(terms, nterms, aux, s->st, &dx, &dz, &dph, host);
     CK(launch_apply_pauli(phi.p, lam.p, s->n, s->dt, dx, dz, (const double*)dph, (int)nterms, s->st));
-    // rows: one per parametric gate occurrence, plus 2 for <phi|lam>
-    const int rows = (int)p->pgates.size();
+    // rows: one per parametric gate of the reversed circuit, plus 2 for <phi|lam>
+    const int G = (int)rp->gates.size();
+    std::vector<int32_t> grow(std::max(1, G), -1);
+    std::vector<int> row_gate;
+    for (int j = 0; j < G; ++j)
+      if (rp->gates[j].parametric) {
+        grow[j] = (int32_t)row_gate.size();
+        row_gate.push_back(j);
+      }
+    const int rows = (int)row_gate.size();
     const int RB = reduce_blocks();
     part.ensure(partial_bytes(rows + 2) + sizeof(double) * (rows + 2));
     double* d_part = part.as<double>();
     double* d_sum = d_part + (size_t)RB * (rows + 2);
+    CK(cudaMemsetAsync(d_part, 0, partial_bytes(rows), s->st));
     CK(launch_inner(phi.p, lam.p, s->n, s->dt, d_part + (size_t)RB * rows, d_sum + rows, s->st));
-    const double2* gtab = p->d_gtab.as<double2>();
-    int row = rows;
-    for (int k = (int)p->gates.size() - 1; k >= 0; --k) {
-      const HGate& g = p->gates[k];
-      if (g.nt == 1) {
-        const DevGate dg = make_dev_gate(g, true);
-        double* prow = nullptr;
-        const double2* dm = nullptr;
-        if (g.parametric) {
-          --row;
-          prow = d_part + (size_t)RB * row;
-          dm = gtab + (size_t)k * 16 + 4;
-        }
-        CK(launch_adjoint_step(phi.p, lam.p, s->n, s->dt, dg, gtab + (size_t)k * 16, dm, prow, s->st));
-      } else {
-        CK(launch_gate(phi.p, s->n, s->dt, p->dgates[k], gtab + (size_t)k * 16, true, s->st));
-        CK(launch_gate(lam.p, s->n, s->dt, p->dgates[k], gtab + (size_t)k * 16, true, s->st));
+    if (G > 0) {
+      // G^dagger and dG for every gate of the reversed circuit (theta resolved on the device)
+      resolve_theta(*rp, theta, ntheta, 1, s->st);
+      gadj.ensure(sizeof(double2) * 16 * (size_t)G);
+      CK(launch_adjoint_table(rp->d_gates.as<DevGate>(), G, rp->d_gtab.as<double2>(), gadj.as<double2>(), s->st));
+      grow_d.ensure(sizeof(int32_t) * grow.size());
+      CK(cudaMemcpyAsync(grow_d.p, grow.data(), sizeof(int32_t) * grow.size(), cudaMemcpyHostToDevice, s->st));
+      for (const PassDesc& pd : rp->pdesc) {
+        require(adjoint_tile_smem_bytes(pd, s->dt) <= 227 * 1024, "adjoint tile pass does not fit shared memory");
+        CK(prepare_adjoint_tile(pd, s->dt));
       }
+      for (const auto& stp : rp->steps)
+        CK(launch_adjoint_tile(phi.p, lam.p, s->n, s->dt, rp->pdesc[stp.idx], rp->d_ops.as<DevOp>(),
+                               gadj.as<double2>(), grow_d.as<int32_t>(), d_part, RB, s->st));
     }
     CK(launch_sum_rows(d_part, rows, RB, d_sum, s->st));
     std::vector<double> sums(rows + 2);
@@ -1353,7 +1372,7 @@ qs_status qs_adjoint_grad(qs_state_t s, const qs_gate* gates, size_t ngates, con
     CK(cudaStreamSynchronize(s->st));
     for (size_t j = 0; j < ntheta; ++j) grad_out[j] = 0;
     for (int r = 0; r < rows; ++r) {
-      const HGate& g = p->gates[p->pgates[r]];
+      const HGate& g = rp->gates[row_gate[r]];
       require((size_t)g.param_index < ntheta, "theta shorter than the parameter indices");
       grad_out[g.param_index] += 2.0 * g.scale * sums[r];
     }

@@ -1,8 +1,7 @@
 // Reductions and Pauli-sum kernels (not in the paper; textbook definitions).
 //
 // Norm sum_i |psi_i|^2, inner product <a|b>, expectation of Pauli strings
-// P|i> = i^{#Y} (-1)^{popcount(i & z)} |i xor x>, H|psi>, and the fused step of
-// the adjoint gradient (Jones and Gacon, arXiv:2009.02823).
+// P|i> = i^{#Y} (-1)^{popcount(i & z)} |i xor x>, and H|psi>.
 //
 // Every reduction runs on a fixed grid (reduce_blocks() CTAs) so the partial
 // sums, and therefore the FP64 result, do not depend on timing. complex64
@@ -626,68 +625,6 @@ cudaError_t launch_apply_pauli(const void* psi, void* out, int n, qs_dtype dt, c
     if (off + kMaxTermsPerLaunch >= nt) break;
   }
   return cudaSuccess;
-}
-
-// ---------------------------------------------------------------- adjoint step
-
-// Reverse-sweep step for one single-target gate G with controls (Jones and
-// Gacon, Alg. 1): phi <- G^dagger phi; if dmat != NULL accumulate
-// Re<lam| dG phi> over the controlled pairs (dG is zero elsewhere);
-// lam <- G^dagger lam. One read and one write of each state.
-template <typename R>
-__global__ void __launch_bounds__(kRedThreads) k_adjoint_step(typename V2<R>::T* __restrict__ phi,
-                                                               typename V2<R>::T* __restrict__ lam, uint64_t count,
-                                                               DevGate g, const double2* __restrict__ mat,
-                                                               const double2* __restrict__ dmat,
-                                                               double* __restrict__ partials) {
-  using C = typename V2<R>::T;
-  // adjoint of the 2x2 target matrix
-  const C a00 = cconj(from_d<R>(mat[0])), a01 = cconj(from_d<R>(mat[2]));
-  const C a10 = cconj(from_d<R>(mat[1])), a11 = cconj(from_d<R>(mat[3]));
-  const bool grad = dmat != nullptr;
-  C d00 = mk<R>(0, 0), d01 = d00, d10 = d00, d11 = d00;
-  if (grad) { d00 = from_d<R>(dmat[0]); d01 = from_d<R>(dmat[1]); d10 = from_d<R>(dmat[2]); d11 = from_d<R>(dmat[3]); }
-  const uint64_t tb = 1ull << g.t0;
-  double tot = 0;
-  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
-  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count;) {
-    R run = 0;
-#pragma unroll 1
-    for (int it = 0; it < kRun && p < count; ++it, p += stride) {
-      const uint64_t i0 = insert_zero_bits_u<4>(p, g.ins, g.nins) | g.cmask, i1 = i0 | tb;
-      const C f0 = phi[i0], f1 = phi[i1];
-      const C l0 = lam[i0], l1 = lam[i1];
-      const C p0 = cfma(a01, f1, cmul(a00, f0));
-      const C p1 = cfma(a11, f1, cmul(a10, f0));
-      phi[i0] = p0;
-      phi[i1] = p1;
-      if (grad) {
-        const C m0 = cfma(d01, p1, cmul(d00, p0));
-        const C m1 = cfma(d11, p1, cmul(d10, p0));
-        run += l0.x * m0.x + l0.y * m0.y + l1.x * m1.x + l1.y * m1.y;   // Re(conj(l) m)
-      }
-      lam[i0] = cfma(a01, l1, cmul(a00, l0));
-      lam[i1] = cfma(a11, l1, cmul(a10, l0));
-    }
-    tot += (double)run;
-  }
-  if (grad) {
-    const double s = block_sum(tot);
-    if (threadIdx.x == 0) partials[blockIdx.x] = s;
-  }
-}
-
-cudaError_t launch_adjoint_step(void* phi, void* lam, int n, qs_dtype dt, const DevGate& g, const double2* mat,
-                                const double2* dmat, double* partials_row, cudaStream_t st) {
-  const uint64_t count = 1ull << (n - g.nins);
-  if (dt == QS_C64)
-    k_adjoint_step<float><<<kRedBlocks, kRedThreads, 0, st>>>((float2*)phi, (float2*)lam, count, g, mat, dmat,
-                                                               partials_row);
-  else
-    k_adjoint_step<double><<<kRedBlocks, kRedThreads, 0, st>>>((double2*)phi, (double2*)lam, count, g, mat, dmat,
-                                                                partials_row);
-  note_launch();
-  return cudaGetLastError();
 }
 
 }  // namespace qs

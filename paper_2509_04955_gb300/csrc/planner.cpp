@@ -323,8 +323,8 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
     if (first >= G) break;
     Block blk;
     const int kcap = o.paper ? 2 : std::max(o.k, popc(gates[first].qmask));
-    std::vector<int> a = scan_block(gates, done, first, kcap, all, o, all);
-    if (!o.paper && kcap > 2 && (o.fuse_parametric || !gates[first].parametric)) {
+    std::vector<int> a = o.no_merge ? std::vector<int>{first} : scan_block(gates, done, first, kcap, all, o, all);
+    if (!o.no_merge && !o.paper && kcap > 2 && (o.fuse_parametric || !gates[first].parametric)) {
       std::vector<int> b = scan_block(gates, done, first, kcap, plan_qubits(gates, done, first, kcap, n), o, all);
       if (b.size() > a.size()) a.swap(b);
       if (o.search) {

@@ -58,6 +58,7 @@ struct PlanOptions {
   int amp_bytes = 8;
   bool fuse_parametric = false;   // parametric gates may join multi-gate blocks
   bool search = true;              // also grow block qubit sets by legal scans (slower planning)
+  bool no_merge = false;           // every gate its own block (the adjoint reverse sweep keeps gates apart)
 };
 
 // DAGC-k greedy contraction. Returns blocks in emission order.

@@ -178,6 +178,17 @@ cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, c
                              const double2* gate_table, const double2* block_table, int threads,
                              cudaStream_t st);
 
+// Adjoint gradient, tiled reverse sweep: G^dagger table (with the angle
+// derivatives), then one launch per tile pass of the reversed circuit over phi
+// and lam; partials[row * pcols + CTA] for the parametric gates (rows via grow).
+cudaError_t launch_adjoint_table(const DevGate* gates, int ngates, const double2* gtab, double2* gadj,
+                                 cudaStream_t st);
+cudaError_t prepare_adjoint_tile(const PassDesc& p, qs_dtype dt);
+size_t adjoint_tile_smem_bytes(const PassDesc& p, qs_dtype dt);
+cudaError_t launch_adjoint_tile(void* phi, void* lam, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
+                                const double2* gadj, const int32_t* grow, double* partials, int pcols,
+                                cudaStream_t st);
+
 // Reductions write FP64 partials into `partials` (capacity >= reduce_blocks()).
 int reduce_blocks();
 cudaError_t launch_norm(const void* psi, int n, qs_dtype dt, double* partials, double* out,
@@ -190,9 +201,6 @@ cudaError_t launch_expval_x(const void* psi, int n, qs_dtype dt, uint64_t xmask,
 cudaError_t launch_apply_pauli(const void* psi, void* out, int n, qs_dtype dt,
                                const uint64_t* xm, const uint64_t* zm, const double* coeff, int nt,
                                cudaStream_t st);
-cudaError_t launch_adjoint_step(void* phi, void* lam, int n, qs_dtype dt, const DevGate& g,
-                                const double2* mat, const double2* dmat, double* partials_row,
-                                cudaStream_t st);
 // partials[0..RB) = per-CTA max |a - b|, partials[RB..2RB) = per-CTA sum |a - b|^2
 cudaError_t launch_diff(const void* a, qs_dtype da, const void* b, qs_dtype db, int n, double* partials,
                         cudaStream_t st);

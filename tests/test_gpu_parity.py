@@ -208,6 +208,33 @@ def test_adjoint_gradient_matches_oracle(dtname, maker):
 
 
 @pytest.mark.parametrize("dtname", ["c128", "c64"])
+@pytest.mark.parametrize("maker", ["mix", "hea"])
+def test_adjoint_gradient_over_many_tiles(dtname, maker):
+    """15 qubits: the reverse sweep runs as several tile passes of 2^12
+    (complex64) or 2^11 (complex128) amplitudes over 8 or 16 tiles, with
+    gradient parts summed over tiles and CTAs; every gate form, controlled
+    rotations and two-target gates (mix), or the hardware-efficient ansatz."""
+    dt = DT[dtname]
+    n = 15
+    if maker == "mix":
+        gates, p = _parametrized_gate_mix(n, 140, seed=21)
+        theta = W.thetas_uniform(p, 22)
+    else:
+        gates, p = W.hea(n, 4)
+        theta = W.thetas_uniform(p, 23)
+    H = W.random_pauli_sum(n, 25, seed=24)
+    h = Q.qs_state_alloc(n, dt)
+    try:
+        e, g = Q.qs_adjoint_grad(h, gates, theta, *H)
+    finally:
+        Q.qs_state_free(h)
+    e_ref, g_ref = O.adjoint_grad(O.basis(n, 0), n, gates, theta, *H)
+    scale = np.abs(H[0]).sum()
+    assert abs(e - e_ref) <= TOL[dt] * scale * 10
+    assert np.abs(g - g_ref).max() <= TOL[dt] * scale * 10
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
 def test_parametric_circuits_both_fusion_policies(dtname):
     """Parametric rotations resolved on the device (default) or folded into
     dense blocks rebuilt on the host at each execution (fuse_parametric=1)."""
