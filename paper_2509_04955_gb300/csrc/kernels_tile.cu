@@ -28,6 +28,33 @@ namespace qs {
 
 constexpr int kTileThreads = 256;
 
+// HBM <-> shared-memory transfer of one tile: 16-byte vectors, BATCH
+// independent loads issued before their shared-memory stores (and the reverse
+// on the way out), so a CTA keeps kTileThreads x BATCH x 16 bytes in flight.
+template <typename C, typename C2, int VPT, bool LOAD, int BATCH = (VPT == 2 ? 8 : 4)>
+__device__ __forceinline__ void tile_io(C* __restrict__ psi, C* tile, uint64_t base, const uint64_t* segoff,
+                                        uint32_t size, int L, uint32_t lmask) {
+  for (uint32_t e0 = threadIdx.x * VPT; e0 < size; e0 += kTileThreads * VPT * BATCH) {
+    C2 buf[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const uint32_t e = e0 + (uint32_t)u * kTileThreads * VPT;
+      if (e < size) {
+        if (LOAD) buf[u] = *(const C2*)(psi + (base | segoff[e >> L] | (e & lmask)));
+        else buf[u] = *(const C2*)(tile + e);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const uint32_t e = e0 + (uint32_t)u * kTileThreads * VPT;
+      if (e < size) {
+        if (LOAD) *(C2*)(tile + e) = buf[u];
+        else *(C2*)(psi + (base | segoff[e >> L] | (e & lmask))) = buf[u];
+      }
+    }
+  }
+}
+
 __device__ __forceinline__ uint32_t ins0(uint32_t x, const int32_t* pos, int npos) {
   return insert_zero_bits_u<4, uint32_t>(x, pos, npos);
 }
@@ -205,8 +232,10 @@ __device__ __forceinline__ void apply_diag_op(typename V2<R>::T* tile, int m, co
   }
 }
 
+// Gate-only passes (KMAX <= 2) keep two CTAs per SM (load of one tile overlaps
+// the ops of the other); wider dense ops need more registers.
 template <typename R, int KMAX>
-__global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __restrict__ psi0,
+__global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typename V2<R>::T* __restrict__ psi0,
                                                         void* const* __restrict__ psis, int64_t gstride,
                                                         int64_t bstride, PassDesc p, const DevOp* __restrict__ ops,
                                                         const double2* __restrict__ gtab0,
@@ -235,10 +264,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __rest
     C* __restrict__ psi = psis ? (C*)psis[sb] : psi0;
     const double2* __restrict__ gtab = gtab0 + sb * gstride;
     const uint64_t base = insert_zero_bits(t << L, p.high, nh);
-    for (uint32_t e = threadIdx.x * VPT; e < size; e += kTileThreads * VPT) {
-      const uint64_t gi = base | segoff[e >> L] | (e & lmask);
-      *(C2*)(tile + e) = *(const C2*)(psi + gi);
-    }
+    tile_io<C, C2, VPT, true>(psi, tile, base, segoff, size, L, lmask);
     __syncthreads();
     for (int o = p.op_begin; o < p.op_end; ++o) {
       const DevOp op = ops[o];
@@ -258,10 +284,7 @@ __global__ void __launch_bounds__(kTileThreads) k_tile(typename V2<R>::T* __rest
       }
       __syncthreads();
     }
-    for (uint32_t e = threadIdx.x * VPT; e < size; e += kTileThreads * VPT) {
-      const uint64_t gi = base | segoff[e >> L] | (e & lmask);
-      *(C2*)(psi + gi) = *(const C2*)(tile + e);
-    }
+    tile_io<C, C2, VPT, false>(psi, tile, base, segoff, size, L, lmask);
     __syncthreads();
   }
 }
@@ -438,6 +461,7 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint_tile(typename V2<R>::T
   using C = typename V2<R>::T;
   using C2 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;   // 16-byte vector
   constexpr int VPT = 16 / sizeof(C);
+  constexpr int kAdjIo = 1;   // compute-bound: registers go to occupancy (up to 3 CTAs per SM), not transfers
   constexpr int kWarps = kTileThreads / 32;
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = p.m, L = p.L, nh = p.nhigh;
@@ -458,11 +482,8 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint_tile(typename V2<R>::T
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (uint64_t t = blockIdx.x; t < (1ull << lg_tiles); t += gridDim.x) {
     const uint64_t base = insert_zero_bits(t << L, p.high, nh);
-    for (uint32_t e = threadIdx.x * VPT; e < size; e += kTileThreads * VPT) {
-      const uint64_t gi = base | segoff[e >> L] | (e & lmask);
-      *(C2*)(tphi + e) = *(const C2*)(phi + gi);
-      *(C2*)(tlam + e) = *(const C2*)(lam + gi);
-    }
+    tile_io<C, C2, VPT, true, kAdjIo>(phi, tphi, base, segoff, size, L, lmask);
+    tile_io<C, C2, VPT, true, kAdjIo>(lam, tlam, base, segoff, size, L, lmask);
     __syncthreads();
     for (int o = p.op_begin; o < p.op_end; ++o) {
       const DevOp op = ops[o];
@@ -477,11 +498,8 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint_tile(typename V2<R>::T
       apply_gate_op<R>(tlam, m, op, gadj, mbuf);
       __syncthreads();
     }
-    for (uint32_t e = threadIdx.x * VPT; e < size; e += kTileThreads * VPT) {
-      const uint64_t gi = base | segoff[e >> L] | (e & lmask);
-      *(C2*)(phi + gi) = *(const C2*)(tphi + e);
-      *(C2*)(lam + gi) = *(const C2*)(tlam + e);
-    }
+    tile_io<C, C2, VPT, false, kAdjIo>(phi, tphi, base, segoff, size, L, lmask);
+    tile_io<C, C2, VPT, false, kAdjIo>(lam, tlam, base, segoff, size, L, lmask);
     __syncthreads();
   }
   for (int i = threadIdx.x; i < nops; i += kTileThreads) {
