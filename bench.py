@@ -48,7 +48,8 @@ def parse():
                     help="also run the complex128 n=32 reference for the tensor-core config (64 GiB, ~1 min)")
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
     ap.add_argument("--only-config", default=None,
-                    choices=["qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20", "hea_adjoint_n24"],
+                    choices=["qft_n30_m2", "qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20",
+                             "hea_adjoint_n24"],
                     help="run one configuration workload alone (no headline) and print its JSON")
     return ap.parse_args()
 
@@ -434,6 +435,8 @@ def run_configs(Q, torch, np, args):
         return args.only_config in (None, name)
 
     # config 1: QFT n=28 complex128 from a seeded basis state, per-gate vs contraction k=2..5
+    if want("qft_n30_m2"):
+        out["qft_n30_m2"] = config_qft30(Q, torch, np, st, args)
     if want("qft_n28_c128"):
         out["qft_n28_c128"] = config_qft(Q, torch, np, st, args)
     if want("random_n32_cz_tensor"):
@@ -442,6 +445,42 @@ def run_configs(Q, torch, np, args):
         out["ucc_batched_n20"] = config_ucc(Q, torch, np, st, args)
     if want("hea_adjoint_n24"):
         out["hea_adjoint_n24"] = config_hea(Q, torch, np, st, args)
+    return out
+
+
+def config_qft30(Q, torch, np, st, args):
+    """Second n=30 workload of the headline metric: QFT from a seeded basis state,
+    complex64 and complex128, per-gate vs fused; sampled amplitudes against the
+    closed form psi_y = 2^{-n/2} exp(2 pi i x y / 2^n)."""
+    from paper_2509_04955_gb300 import workloads as W
+    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
+    n = 30
+    g = W.qft(n)
+    x = W.random_basis_index(n, 30)
+    idx = np.unique(np.random.default_rng(0).integers(0, 1 << n, size=4096)).astype(np.uint64)
+    want = np.exp(2j * np.pi * ((x * idx.astype(object)) % (1 << n)).astype(np.float64) / (1 << n)) / np.sqrt(1 << n)
+    out = {"workload": "QFT n=30, seeded basis input (H, controlled phases, final swaps)", "gates": len(g)}
+    variants = {"c64": [("per_gate", None), ("fused_k4", Q.make_opts(mode=F, fuse_k=4)),
+                        ("tensor", Q.make_opts(mode=T, tc_min_gates=2))],
+                "c128": [("per_gate", None), ("fused_k5", Q.make_opts(mode=F, fuse_k=5))]}
+    for dname, dt in (("c64", Q.QS_C64), ("c128", Q.QS_C128)):
+        s = Q.qs_state_alloc(n, dt, st)
+        res = {}
+        amp = 8 if dt == Q.QS_C64 else 16
+        for name, opts in variants[dname]:
+            plan = Q.qs_plan_create(n, dt, g, opts)
+            Q.qs_state_set_basis(s, x)
+            Q.qs_plan_execute(plan, s)
+            Q.qs_state_set_basis(s, x)
+            ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s))
+            info = Q.qs_plan_info_get(plan)
+            got = Q.qs_state_get_amplitudes(s, idx, dt)
+            res[name] = {"ms": ms, "passes": info["passes"],
+                         "effective_gbps": info["sweeps"] * 2 * (1 << n) * amp / (ms * 1e-3) / 1e9,
+                         "max_abs_err_vs_closed_form": float(np.abs(got - want).max())}
+            Q.qs_plan_free(plan)
+        out[dname] = res
+        Q.qs_state_free(s)
     return out
 
 

@@ -154,6 +154,14 @@ qs_status qs_state_copy_to_host(qs_state_t s, void* host, size_t bytes);
 /* dst <- src (same n and dtype), device to device. */
 qs_status qs_state_copy(qs_state_t dst, qs_state_t src);
 
+/* Reads `count` amplitudes psi[idx[k]] (idx host array, each < 2^n) into
+ * host memory `out` (count complex values of the state's dtype, interleaved
+ * re/im), gathered on the device: sampling a state without copying all 2^n
+ * amplitudes (Eq. 1 indexing: qubit q is bit q of the index). An index >= 2^n
+ * gives QS_ERR_ARG before any device work. Synchronises the state's stream.
+ * (An access helper with no counterpart in the paper.) */
+qs_status qs_state_get_amplitudes(qs_state_t s, const uint64_t* idx, size_t count, void* out);
+
 /* ---------------- circuits ---------------- */
 
 /* Plans a circuit for n qubits: resolves gate matrices (FP64), builds the gate

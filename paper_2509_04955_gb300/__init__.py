@@ -76,6 +76,7 @@ _SIGS = {
     "qs_state_copy_from_host": (C.c_int, [_VP, _VP, C.c_size_t]),
     "qs_state_copy_to_host": (C.c_int, [_VP, _VP, C.c_size_t]),
     "qs_state_copy": (C.c_int, [_VP, _VP]),
+    "qs_state_get_amplitudes": (C.c_int, [_VP, C.POINTER(C.c_uint64), C.c_size_t, _VP]),
     "qs_plan_create": (C.c_int, [C.c_int, C.c_int, C.POINTER(QsGate), C.c_size_t, C.POINTER(QsPlanOpts),
                                  C.POINTER(_VP)]),
     "qs_plan_info_get": (C.c_int, [_VP, C.POINTER(QsPlanInfo)]),
@@ -223,6 +224,14 @@ def qs_state_copy_to_host(h: int, out: np.ndarray):
 
 def qs_state_copy(dst: int, src: int):
     _check(lib().qs_state_copy(dst, src))
+
+
+def qs_state_get_amplitudes(h: int, idx, dtype: int) -> np.ndarray:
+    """psi[idx] gathered on the device (dtype: the state's QS_C64 / QS_C128)."""
+    ix = np.ascontiguousarray(idx, dtype=np.uint64)
+    out = np.empty(len(ix), dtype=NP_DTYPE[dtype])
+    _check(lib().qs_state_get_amplitudes(h, ix.ctypes.data_as(C.POINTER(C.c_uint64)), len(ix), out.ctypes.data))
+    return out
 
 
 def qs_plan_create(n: int, dtype: int, gates, opts: QsPlanOpts | None = None) -> int:
@@ -448,6 +457,10 @@ class State:
 
     def norm(self) -> float:
         return qs_norm(self.handle)
+
+    def amplitudes(self, idx) -> np.ndarray:
+        """psi[idx] for a list of basis indices, gathered on the device."""
+        return qs_state_get_amplitudes(self.handle, idx, self.dtype)
 
     def expval(self, coeff, xmask, zmask) -> float:
         return qs_expval_pauli_sum(self.handle, coeff, xmask, zmask)

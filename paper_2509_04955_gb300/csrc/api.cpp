@@ -1113,6 +1113,24 @@ qs_status qs_state_copy_to_host(qs_state_t s, void* host, size_t bytes) {
   });
 }
 
+qs_status qs_state_get_amplitudes(qs_state_t s, const uint64_t* idx, size_t count, void* out) {
+  return guard([&] {
+    check_state(s);
+    if (count == 0) return;
+    require(idx != nullptr && out != nullptr, "NULL argument");
+    const uint64_t dim = 1ull << s->n;
+    for (size_t k = 0; k < count; ++k) require(idx[k] < dim, "amplitude index >= 2^n");
+    const size_t ab = amp_bytes(s->dt);
+    DevBuf didx, dout;
+    didx.ensure(sizeof(uint64_t) * count);
+    dout.ensure(ab * count);
+    CK(cudaMemcpyAsync(didx.p, idx, sizeof(uint64_t) * count, cudaMemcpyHostToDevice, s->st));
+    CK(launch_gather(s->d, s->dt, didx.as<uint64_t>(), count, dout.p, s->st));
+    CK(cudaMemcpyAsync(out, dout.p, ab * count, cudaMemcpyDeviceToHost, s->st));
+    CK(cudaStreamSynchronize(s->st));
+  });
+}
+
 qs_status qs_state_copy(qs_state_t dst, qs_state_t src) {
   return guard([&] {
     check_state(dst);

@@ -49,6 +49,23 @@ __global__ void k_set_basis(C* __restrict__ psi, uint64_t dim, uint64_t x) {
   }
 }
 
+template <typename C>
+__global__ void k_gather(const C* __restrict__ psi, const uint64_t* __restrict__ idx, uint64_t count,
+                         C* __restrict__ out) {
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t k = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; k < count; k += stride) out[k] = psi[idx[k]];
+}
+
+cudaError_t launch_gather(const void* psi, qs_dtype dt, const uint64_t* idx, uint64_t count, void* out,
+                          cudaStream_t st) {
+  if (count == 0) return cudaSuccess;
+  const int th = 256, gr = grid_for(count, th);
+  if (dt == QS_C64) k_gather<float2><<<gr, th, 0, st>>>((const float2*)psi, idx, count, (float2*)out);
+  else k_gather<double2><<<gr, th, 0, st>>>((const double2*)psi, idx, count, (double2*)out);
+  note_launch();
+  return cudaGetLastError();
+}
+
 cudaError_t launch_set_basis(void* psi, int n, qs_dtype dt, uint64_t x, cudaStream_t st) {
   const uint64_t dim = 1ull << n;
   const int th = 256, gr = grid_for(dim, th);

@@ -150,6 +150,9 @@ template <> struct Cplx<float> { using T = float2; };
 template <> struct Cplx<double> { using T = double2; };
 
 cudaError_t launch_set_basis(void* psi, int n, qs_dtype dt, uint64_t x, cudaStream_t st);
+// out[k] = psi[idx[k]] (device arrays)
+cudaError_t launch_gather(const void* psi, qs_dtype dt, const uint64_t* idx, uint64_t count, void* out,
+                          cudaStream_t st);
 cudaError_t launch_resolve(const DevGate* gates, const int32_t* param_gates, int nparam_gates,
                            const double* theta, int64_t ntheta, int batch, double2* table,
                            int64_t table_stride, cudaStream_t st);

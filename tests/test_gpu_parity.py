@@ -601,6 +601,26 @@ def test_batched_fixed_circuit_without_parameters():
             Q.qs_plan_free(plan)
 
 
+@pytest.mark.parametrize("dtname", ["c64", "c128"])
+def test_gathered_amplitudes_equal_the_full_copy(dtname):
+    dt = DT[dtname]
+    n = 13
+    gates = W.random_layered(n, 4, seed=3)
+    h = Q.qs_state_alloc(n, dt)
+    try:
+        Q.qs_apply_circuit(h, gates)
+        full = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+        Q.qs_state_copy_to_host(h, full)
+        idx = np.array([0, 1, 7, (1 << n) - 1, 4096, 17, 17], dtype=np.uint64)
+        got = Q.qs_state_get_amplitudes(h, idx, dt)
+        assert np.array_equal(got, full[idx.astype(np.int64)])
+        assert len(Q.qs_state_get_amplitudes(h, [], dt)) == 0
+        with pytest.raises(Q.QsError):
+            Q.qs_state_get_amplitudes(h, [1 << n], dt)
+    finally:
+        Q.qs_state_free(h)
+
+
 def test_invalid_sizes_give_errors_not_faults():
     h = Q.qs_state_alloc(4, Q.QS_C64)
     try:
