@@ -189,6 +189,48 @@ def pauli_string_masks(n: int, support: list[int], letters: str) -> tuple[int, i
     return x, z
 
 
+def random_regular_graph(n: int, degree: int, seed: int) -> list[tuple[int, int]]:
+    """Edges (u < v) of a random simple d-regular graph on n vertices: the
+    configuration model (n*d stubs paired at random), redrawn until the pairing
+    has no loop and no repeated edge."""
+    if (n * degree) % 2 or degree >= n:
+        raise ValueError("no simple d-regular graph with these sizes")
+    rng = _rng(seed)
+    for _ in range(10000):
+        stubs = np.repeat(np.arange(n), degree)
+        rng.shuffle(stubs)
+        pairs = stubs.reshape(-1, 2)
+        edges = {(int(min(a, b)), int(max(a, b))) for a, b in pairs}
+        if len(edges) == len(pairs) and all(a != b for a, b in edges):
+            return sorted(edges)
+    raise RuntimeError("no simple pairing found")
+
+
+def qaoa(n: int, layers: int, edges) -> tuple[list[Gate], int]:
+    """QAOA circuit for MaxCut: H on every qubit, then per layer l the cost
+    unitary prod_edges exp(-i gamma_l Z_u Z_v) (CNOT(u -> v), RZ_v(2 gamma_l),
+    CNOT(u -> v)) and the mixer prod_q exp(-i beta_l X_q) = RX_q(2 beta_l).
+    Parameters: theta[2 l] = gamma_l, theta[2 l + 1] = beta_l."""
+    gates = [Gate("h", (q,)) for q in range(n)]
+    for layer in range(layers):
+        for u, v in edges:
+            gates.append(Gate("x", (v,), (u,)))
+            gates.append(Gate("rz", (v,), param_index=2 * layer, scale=2.0))
+            gates.append(Gate("x", (v,), (u,)))
+        for q in range(n):
+            gates.append(Gate("rx", (q,), param_index=2 * layer + 1, scale=2.0))
+    return gates, 2 * layers
+
+
+def maxcut_hamiltonian(edges):
+    """C = sum_edges (1 - Z_u Z_v) / 2 as (coeff, xmask, zmask): the number of
+    cut edges of a computational basis state."""
+    coeff = [0.5 * len(edges)] + [-0.5] * len(edges)
+    xm = [0] * (len(edges) + 1)
+    zm = [0] + [(1 << u) | (1 << v) for u, v in edges]
+    return np.array(coeff), np.array(xm, dtype=np.uint64), np.array(zm, dtype=np.uint64)
+
+
 def random_basis_index(n: int, seed: int) -> int:
     return int(_rng(seed).integers(0, 1 << n)) if n < 63 else int(_rng(seed).integers(0, 1 << 62))
 

@@ -194,6 +194,37 @@ def test_circuit_times_inverse_is_identity_and_norm(maker):
     assert np.abs(back - psi).max() < 1e-13
 
 
+def test_qaoa_circuit_equals_matrix_exponentials():
+    """The QAOA gate list applied by the oracle equals the textbook unitary
+    prod_l exp(-i beta_l B) exp(-i gamma_l C_ZZ) H^n |0>, with C_ZZ = sum_edges
+    Z_u Z_v and B = sum_q X_q built as explicit 2^n x 2^n matrices."""
+    n, layers = 6, 2
+    edges = W.random_regular_graph(n, 3, seed=5)
+    assert len(edges) == 9 and all(sum(1 for e in edges if q in e) == 3 for q in range(n))
+    gates, p = W.qaoa(n, layers, edges)
+    theta = np.array([0.37, -0.81, 1.13, 0.29])
+    psi = O.apply_circuit(O.basis(n, 0), n, gates, theta)
+    I2, X, Z = np.eye(2), np.array([[0, 1], [1, 0]]), np.diag([1.0, -1.0])
+
+    def on(q, m):   # qubit q = bit q of the index: the rightmost Kronecker factor is qubit 0
+        out = np.eye(1)
+        for k in reversed(range(n)):
+            out = np.kron(out, m if k == q else I2)
+        return out
+    czz = sum(on(u, Z) @ on(v, Z) for u, v in edges)
+    bx = sum(on(q, X) for q in range(n))
+    want = np.full(1 << n, 2 ** (-n / 2), dtype=complex)
+    for layer in range(layers):
+        want = scipy.linalg.expm(-1j * theta[2 * layer] * czz) @ want
+        want = scipy.linalg.expm(-1j * theta[2 * layer + 1] * bx) @ want
+    assert np.abs(psi - want).max() < 1e-12
+    # MaxCut value of a basis state = number of cut edges
+    H = W.maxcut_hamiltonian(edges)
+    for x in (0, 5, 42, 63):
+        cut = sum(((x >> u) & 1) != ((x >> v) & 1) for u, v in edges)
+        assert abs(O.expval(O.basis(n, x), n, *H).real - cut) < 1e-12
+
+
 def test_pauli_exponential_closed_form():
     """exp(-i t P) psi = cos t psi - i sin t P psi for every letter mix."""
     n = 6
