@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
     ap.add_argument("--only-config", default=None,
                     choices=["qft_n30_m2", "qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20",
-                             "hea_adjoint_n24"],
+                             "hea_adjoint_n24", "qaoa_n30"],
                     help="run one configuration workload alone (no headline) and print its JSON")
     return ap.parse_args()
 
@@ -445,6 +445,79 @@ def run_configs(Q, torch, np, args):
         out["ucc_batched_n20"] = config_ucc(Q, torch, np, st, args)
     if want("hea_adjoint_n24"):
         out["hea_adjoint_n24"] = config_hea(Q, torch, np, st, args)
+    if want("qaoa_n30"):
+        out["qaoa_n30"] = config_qaoa30(Q, torch, np, st, args)
+    return out
+
+
+def config_qaoa30(Q, torch, np, st, args):
+    """QAOA for MaxCut (Section 4.1's third circuit class) at n=30 on a seeded
+    random 3-regular graph, depth p=4 (690 gates): per-gate vs contraction with
+    and without diagonal phase passes (one sweep per cost layer); <C> of every
+    variant against the complex128 contraction; the phase kernel timed alone on
+    one cost layer; depth 1 against the published p=1 closed form; the paper-mode
+    contraction's gate-count compression (Fig. 16's ratio)."""
+    sys.path.insert(0, os.path.join(os.path.dirname(os.path.abspath(__file__)), "tests"))
+    from closed_forms import qaoa_p1_maxcut
+    from paper_2509_04955_gb300 import workloads as W
+    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
+    n, p = 30, 4
+    edges = W.random_regular_graph(n, 3, seed=0)
+    g, npar = W.qaoa(n, p, edges)
+    H = W.maxcut_hamiltonian(edges)
+    th = W.thetas_uniform(npar, 1)
+    out = {"workload": f"QAOA MaxCut n=30, random 3-regular graph ({len(edges)} edges), p={p}, seeded angles",
+           "gates": len(g)}
+    pl = Q.qs_plan_create(n, Q.QS_C128, g, Q.make_opts(paper_mode=1))
+    info = Q.qs_plan_info_get(pl)
+    out["paper_mode_compression"] = (info["gates"] - info["blocks"]) / info["gates"]
+    Q.qs_plan_free(pl)
+    variants = {"c64": [("per_gate", None), ("fused_no_phase", Q.make_opts(mode=F, phase_min_gates=-1)),
+                        ("fused", Q.make_opts(mode=F)),
+                        ("fused_m14", Q.make_opts(mode=F, tile_qubits=14, low_qubits=4)),
+                        ("tensor", Q.make_opts(mode=T, tc_min_gates=4, fuse_parametric=1))],
+                "c128": [("per_gate", None), ("fused_no_phase", Q.make_opts(mode=F, phase_min_gates=-1)),
+                         ("fused", Q.make_opts(mode=F)),
+                         ("fused_m13", Q.make_opts(mode=F, tile_qubits=13, low_qubits=3))]}
+    ref_e = None
+    for dname, dt in (("c128", Q.QS_C128), ("c64", Q.QS_C64)):
+        s = Q.qs_state_alloc(n, dt, st)
+        amp = 8 if dt == Q.QS_C64 else 16
+        res = {}
+        for name, opts in variants[dname]:
+            plan = Q.qs_plan_create(n, dt, g, opts)
+            Q.qs_state_set_basis(s, 0)
+            Q.qs_plan_execute(plan, s, th)
+            Q.qs_state_set_basis(s, 0)
+            ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s, th))
+            e = Q.qs_expval_pauli_sum(s, *H)
+            if ref_e is None:
+                ref_e = e
+            info = Q.qs_plan_info_get(plan)
+            ops = Q.qs_plan_ops(plan)
+            res[name] = {"ms": ms, "passes": info["passes"],
+                         "phase_passes": sum(op["type"] == 4 for op in ops),
+                         "effective_gbps": info["sweeps"] * 2 * (1 << n) * amp / (ms * 1e-3) / 1e9,
+                         "expected_cut": e, "abs_diff_vs_c128_fused": abs(e - ref_e)}
+            Q.qs_plan_free(plan)
+        # one cost layer alone: a single phase pass
+        layer = g[n:n + 3 * len(edges)]
+        plan = Q.qs_plan_create(n, dt, layer, Q.make_opts(mode=F))
+        assert [op["type"] for op in Q.qs_plan_ops(plan)] == [4]
+        Q.qs_plan_execute(plan, s, th)
+        ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s, th), reps=5)
+        res["phase_pass_alone"] = {"ms": ms, "gbps": 2 * (1 << n) * amp / (ms * 1e-3) / 1e9,
+                                   "terms": len(Q.qs_plan_ops(plan)[0]["terms"])}
+        Q.qs_plan_free(plan)
+        # depth 1 against the closed form
+        g1, _ = W.qaoa(n, 1, edges)
+        plan = Q.qs_plan_create(n, dt, g1, Q.make_opts(mode=F))
+        Q.qs_state_set_basis(s, 0)
+        Q.qs_plan_execute(plan, s, th[:2])
+        res["p1_abs_err_vs_closed_form"] = abs(Q.qs_expval_pauli_sum(s, *H) - qaoa_p1_maxcut(n, edges, *th[:2]))
+        Q.qs_plan_free(plan)
+        out[dname] = res
+        Q.qs_state_free(s)
     return out
 
 

@@ -107,7 +107,14 @@ typedef struct {
                             reserved[1]: tensor mode, tensor-core pass pipeline (single and batched
                             executions): 0 = tiles staged in shared memory by bulk asynchronous
                             copies (default), 1 = tiles staged in registers by the computing
-                            threads. */
+                            threads.
+                            reserved[2]: fused and tensor modes, n >= 12: least gates in a
+                            diagonal phase run (0 = max(16, 2n), < 0 = no phase runs). A phase
+                            run is a contiguous stretch of CNOTs, SWAPs and diagonal gates
+                            (Z, S, T, RZ, P and their one-control forms) whose permutation of
+                            the basis composes to the identity, such as a QAOA cost layer; it
+                            runs as one sweep multiplying amplitude x by
+                            prod_j exp(i alpha_j (-1)^popcount(mask_j & x)) (qs_plan_phase_terms). */
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */
@@ -263,9 +270,11 @@ qs_status qs_expval_pauli_sum_noalloc(const void* dev_state, int n, qs_dtype dty
  * one op. */
 qs_status qs_plan_op_count(qs_plan_t p, int64_t* nops, int64_t* npasses);
 /* type: 0 = gate op, 1 = dense block, 2 = diagonal block, 3 = dense 6-qubit block applied on
- * tensor cores (its own pass over 13-qubit tiles). qubits: capacity 6.
+ * tensor cores (its own pass over 13-qubit tiles), 4 = diagonal phase run (its own pass; its
+ * terms via qs_plan_phase_terms). qubits: capacity 6, or n for a phase run.
  * gate_index: the input gate of a gate op (-1 for blocks). mat (optional,
- * capacity 2 * 4096 doubles): the block's entries as (re, im) pairs. */
+ * capacity 2 * 4096 doubles): the block's entries as (re, im) pairs; not
+ * written for a phase run. */
 qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits, int32_t* nq,
                          int32_t* gate_index, double* mat);
 /* Self-check of the blocks rebuilt on the device from theta: resolves theta,
@@ -274,9 +283,19 @@ qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits,
  * values) and the number of such blocks. Synchronises; no state is touched. */
 qs_status qs_plan_check_device_blocks(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta,
                                       double* max_abs_diff, int64_t* nblocks);
-/* Tile qubits of pass i (ascending, capacity 14) and its op range [op_begin, op_end). */
+/* Tile qubits of pass i (ascending, capacity 14; a phase pass lists the qubits
+ * of its run, capacity n) and its op range [op_begin, op_end). */
 qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t* m,
                            int64_t* op_begin, int64_t* op_end);
+/* Terms of phase-run op i (type 4): the run multiplies amplitude x by
+ * prod_j exp(i alpha_j (-1)^popcount(masks[j] & x)), alpha_j = alpha0[j] +
+ * coef[j] * theta[param_index[j]] (param_index[j] >= 0) or alpha0[j]. The
+ * phase polynomial of the run's gates: with b_q the bit of qubit q,
+ * RZ(a) = exp(-i a/2 (-1)^b), P(a) = exp(i a b) and a CNOT adds the control's
+ * parity to the target's. Writes min(cap, count) terms; *nterms = count.
+ * QS_ERR_ARG when op i is not a phase run. */
+qs_status qs_plan_phase_terms(qs_plan_t p, int64_t i, uint64_t* masks, int32_t* param_index, double* alpha0,
+                              double* coef, int64_t cap, int64_t* nterms);
 
 /* ---------------- measurement ----------------
  * With timing enabled, every kernel launch issued by qs_plan_execute is

@@ -97,6 +97,7 @@ _SIGS = {
     "qs_plan_op_count": (C.c_int, [_VP, _I64P, _I64P]),
     "qs_plan_op_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I32P, _I32P, _DP]),
     "qs_plan_pass_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I64P, _I64P]),
+    "qs_plan_phase_terms": (C.c_int, [_VP, C.c_int64, C.POINTER(C.c_uint64), _I32P, _DP, _DP, C.c_int64, _I64P]),
     "qs_plan_set_timing": (C.c_int, [_VP, C.c_int]),
     "qs_plan_timing_read": (C.c_int, [_VP, _DP, _I64P]),
     "qs_plan_timing_read_kinds": (C.c_int, [_VP, _DP, _I64P, _DP, _I64P]),
@@ -176,13 +177,14 @@ def _dptr(a):
 
 
 def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0,
-              fuse_parametric=0, tc_min_gates=0, tc_pipeline=0):
-    """qs_plan_opts; tc_min_gates and tc_pipeline fill reserved[0] and reserved[1]."""
+              fuse_parametric=0, tc_min_gates=0, tc_pipeline=0, phase_min_gates=0):
+    """qs_plan_opts; tc_min_gates, tc_pipeline and phase_min_gates fill reserved[0..2]."""
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
     o.paper_mode, o.tc_precision, o.fuse_parametric = paper_mode, tc_precision, fuse_parametric
     o.reserved[0] = tc_min_gates
     o.reserved[1] = tc_pipeline
+    o.reserved[2] = phase_min_gates
     return o
 
 
@@ -269,7 +271,8 @@ def qs_plan_autotune(state: int, gates, theta=None) -> tuple[QsPlanOpts, float]:
 
 def opts_dict(o: QsPlanOpts) -> dict:
     return {"mode": o.mode, "fuse_k": o.fuse_k, "tile_qubits": o.tile_qubits, "low_qubits": o.low_qubits,
-            "tc_min_gates": o.reserved[0], "tc_precision": o.tc_precision, "tc_pipeline": o.reserved[1]}
+            "tc_min_gates": o.reserved[0], "tc_precision": o.tc_precision, "tc_pipeline": o.reserved[1],
+            "phase_min_gates": o.reserved[2]}
 
 
 def qs_apply_circuit(state: int, gates, theta=None, opts: QsPlanOpts | None = None):
@@ -364,10 +367,12 @@ def qs_plan_ops(plan: int) -> list[dict]:
     mat = np.zeros(2 * 4096)
     for i in range(n_ops.value):
         t, nq, gi = C.c_int32(), C.c_int32(), C.c_int32()
-        qs = (C.c_int32 * 6)()
+        qs = (C.c_int32 * 64)()
         _check(lib().qs_plan_op_get(plan, i, C.byref(t), qs, C.byref(nq), C.byref(gi), mat.ctypes.data_as(_DP)))
         d = {"type": t.value, "qubits": tuple(qs[j] for j in range(nq.value)), "gate": gi.value}
-        if t.value != 0:
+        if t.value == 4:
+            d["terms"] = qs_plan_phase_terms(plan, i)
+        elif t.value != 0:
             cnt = (1 << nq.value) if t.value == 2 else (1 << (2 * nq.value))
             v = mat[: 2 * cnt].view(np.complex128).copy()
             d["matrix"] = v if t.value == 2 else v.reshape(1 << nq.value, 1 << nq.value)
@@ -380,12 +385,26 @@ def qs_plan_passes(plan: int) -> list[dict]:
     _check(lib().qs_plan_op_count(plan, C.byref(n_ops), C.byref(n_pass)))
     out = []
     for i in range(n_pass.value):
-        tq = (C.c_int32 * 14)()
+        tq = (C.c_int32 * 64)()
         m = C.c_int32()
         b, e = C.c_int64(), C.c_int64()
         _check(lib().qs_plan_pass_get(plan, i, tq, C.byref(m), C.byref(b), C.byref(e)))
         out.append({"tile": tuple(tq[j] for j in range(m.value)), "ops": (b.value, e.value)})
     return out
+
+
+def qs_plan_phase_terms(plan: int, i: int) -> list[tuple[int, int, float, float]]:
+    """Terms (mask, param_index, alpha0, coef) of phase-run op i."""
+    cnt = C.c_int64()
+    _check(lib().qs_plan_phase_terms(plan, i, None, None, None, None, 0, C.byref(cnt)))
+    k = cnt.value
+    m = (C.c_uint64 * max(1, k))()
+    pi = (C.c_int32 * max(1, k))()
+    a0 = np.zeros(max(1, k))
+    cf = np.zeros(max(1, k))
+    _check(lib().qs_plan_phase_terms(plan, i, m, pi, a0.ctypes.data_as(_DP), cf.ctypes.data_as(_DP), k,
+                                     C.byref(cnt)))
+    return [(int(m[j]), int(pi[j]), float(a0[j]), float(cf[j])) for j in range(k)]
 
 
 def qs_plan_set_timing(plan: int, enable: bool):

@@ -123,9 +123,15 @@ struct qs_plan_s {
   std::vector<int64_t> block_off;  // complex offset in the block table, -1 if gate-wise
   // tensor-core passes and the execution order of all passes
   struct Step {
-    int kind;   // 0 = tile pass (pdesc[idx]), 1 = tensor-core pass (tcdesc[idx])
+    int kind;   // 0 = tile pass (pdesc[idx]), 1 = tensor-core pass (tcdesc[idx]), 2 = phase pass (phdesc[idx])
     int idx;
   };
+  // diagonal phase runs (their own passes)
+  std::vector<PhaseRun> runs;
+  std::vector<PhasePassDesc> phdesc;
+  std::vector<DevPhaseTerm> h_pterms;
+  int64_t theta_stride = 0;        // entries per theta row of the last resolve
+  bool theta_needed = false;       // some phase term depends on theta
   std::vector<Step> steps;
   std::vector<TcPassDesc> tcdesc;
   std::vector<uint16_t> h_wimg;    // per TC pass: bf16 hi image then lo image (64 KiB)
@@ -140,7 +146,7 @@ struct qs_plan_s {
   std::vector<double2> h_btab;
   // device
   bool uploaded = false;
-  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err, d_dblocks, d_dmem;
+  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err, d_dblocks, d_dmem, d_pterms;
   int gtab_rows = 0;
   qs_plan_info info{};
   // batched graph cache; captured and replayed on a plan-owned stream
@@ -266,6 +272,11 @@ void upload(qs_plan_s& p) {
     if (!p.h_dmem.empty())
       CK(cudaMemcpy(p.d_dmem.p, p.h_dmem.data(), sizeof(DevMember) * p.h_dmem.size(), cudaMemcpyHostToDevice));
   }
+  if (!p.h_pterms.empty()) {
+    p.d_pterms.ensure(sizeof(DevPhaseTerm) * p.h_pterms.size());
+    CK(cudaMemcpy(p.d_pterms.p, p.h_pterms.data(), sizeof(DevPhaseTerm) * p.h_pterms.size(), cudaMemcpyHostToDevice));
+  }
+  for (PhasePassDesc& d : p.phdesc) CK(prepare_phase_pass(d, p.dt));
   p.d_err.ensure(sizeof(int) * 4);
   CK(cudaMemset(p.d_err.p, 0, sizeof(int) * 4));
   // kernel attributes and occupancy, here and never during a stream capture
@@ -293,6 +304,10 @@ void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed
     } else if (p.steps[i].kind == 0) {
       CK(launch_tile_pass(psi, p.n, p.dt, p.pdesc[p.steps[i].idx], p.d_ops.as<DevOp>(), gtab,
                           p.d_btab.as<double2>(), 0, st));
+    } else if (p.steps[i].kind == 2) {
+      const double* th = p.theta_needed ? p.d_theta.as<double>() + (size_t)row * p.theta_stride : nullptr;
+      CK(launch_phase_pass(psi, nullptr, 1, p.n, p.dt, p.d_pterms.as<DevPhaseTerm>(), p.phdesc[p.steps[i].idx], th,
+                           p.theta_stride, st));
     } else {
       const int t = p.steps[i].idx;
       CK(launch_tc_pass(psi, p.n, p.tcdesc[t], p.d_wimg.as<uint16_t>() + (size_t)t * 32768, p.tc_prec,
@@ -309,7 +324,10 @@ void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_
   if (p.gtab_rows < B || (!p.h_dblocks.empty() && (p.btab_rows < B || (!p.tcdesc.empty() && p.wimg_rows < B))))
     throw Error(QS_ERR_CUDA, "internal: tables have fewer rows than the batch");
   for (const auto& stp : p.steps) {
-    if (stp.kind == 0)
+    if (stp.kind == 2)
+      CK(launch_phase_pass(nullptr, d_psis, B, p.n, p.dt, p.d_pterms.as<DevPhaseTerm>(), p.phdesc[stp.idx],
+                           p.theta_needed ? p.d_theta.as<double>() : nullptr, p.theta_stride, st));
+    else if (stp.kind == 0)
       CK(launch_tile_pass_batched(nullptr, d_psis, B, (int64_t)(16 * G), p.btab_elems, p.n, p.dt, p.pdesc[stp.idx],
                                   p.d_ops.as<DevOp>(), p.d_gtab.as<double2>(), p.d_btab.as<double2>(), st));
     else
@@ -326,6 +344,7 @@ void resolve_theta(qs_plan_s& p, const double* theta, size_t ntheta, int rows, c
   require((int64_t)ntheta >= p.nparams, "theta has fewer entries than the circuit's parameter indices");
   p.d_theta.ensure(sizeof(double) * ntheta * rows);
   CK(cudaMemcpyAsync(p.d_theta.p, theta, sizeof(double) * ntheta * rows, cudaMemcpyHostToDevice, st));
+  p.theta_stride = (int64_t)ntheta;
   const size_t G = std::max<size_t>(1, p.gates.size());
   CK(launch_resolve(p.d_gates.as<DevGate>(), p.d_pg.as<int32_t>(), (int)p.pgates.size(), p.d_theta.as<double>(),
                     (int64_t)ntheta, rows, p.d_gtab.as<double2>(), (int64_t)16 * G, st));
@@ -522,6 +541,71 @@ void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::ve
   }
 }
 
+// Terms of a phase run sorted into the classes the phase kernel expects
+// (repeated (mask, parameter) pairs merged), appended to the plan's array.
+void emit_phase_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
+  const PhaseRun& run = P.runs[r.block];
+  const uint64_t low = (1ull << kPhaseChunkBits) - 1;
+  std::map<std::pair<uint64_t, int>, PhaseTerm> merged;
+  for (const PhaseTerm& t : run.terms) {
+    PhaseTerm& m = merged[{t.mask, t.pidx}];
+    m.mask = t.mask;
+    m.pidx = t.pidx;
+    m.alpha0 += t.alpha0;
+    m.coef += t.coef;
+  }
+  auto cls = [&](uint64_t m) {   // 0 LOW, 1 + u LIN, 13 HIGH, 14 MIXED
+    const int nlo = __builtin_popcountll(m & low);
+    if (nlo == 0) return kPhaseChunkBits + 1;
+    if (nlo == 1) return 1 + __builtin_ctzll(m & low);
+    return (m & ~low) ? kPhaseChunkBits + 2 : 0;
+  };
+  std::vector<PhaseTerm> ts;
+  for (auto& kv : merged) ts.push_back(kv.second);
+  std::stable_sort(ts.begin(), ts.end(), [&](const PhaseTerm& a, const PhaseTerm& b) { return cls(a.mask) < cls(b.mask); });
+  PhasePassDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.term_off = (int32_t)P.h_pterms.size();
+  d.nterms = (int32_t)ts.size();
+  int k = 0;
+  auto skip_class = [&](int c) { while (k < (int)ts.size() && cls(ts[k].mask) == c) ++k; };
+  skip_class(0);
+  d.nlow = k;
+  for (int u = 0; u < kPhaseChunkBits; ++u) {
+    d.lin_off[u] = k;
+    skip_class(1 + u);
+  }
+  d.lin_off[kPhaseChunkBits] = k;
+  d.high_begin = k;
+  skip_class(kPhaseChunkBits + 1);
+  d.mixed_begin = k;
+  require(d.nterms <= kPhaseMaxTerms && d.nterms - d.mixed_begin <= kPhaseMaxMixed, "internal: phase run too large");
+  for (const PhaseTerm& t : ts) {
+    DevPhaseTerm dt;
+    std::memset(&dt, 0, sizeof(dt));
+    dt.mask = t.mask;
+    dt.pidx = t.pidx;
+    dt.alpha0 = t.alpha0;
+    dt.coef = t.coef;
+    P.h_pterms.push_back(dt);
+    if (t.pidx >= 0 && t.coef != 0) P.theta_needed = true;
+  }
+  DevOp op;
+  std::memset(&op, 0, sizeof(op));
+  op.type = OP_PHASE;
+  const int b = (int)P.dops.size();
+  P.dops.push_back(op);
+  P.exec_ops.push_back(r);
+  P.steps.push_back({2, (int)P.phdesc.size()});
+  P.phdesc.push_back(d);
+  std::vector<int> qs;
+  for (int q = 0; q < P.n; ++q)
+    if (run.qmask & (1ull << q)) qs.push_back(q);
+  P.pass_tiles.push_back(qs);
+  P.pass_ops.push_back({b, b + 1});
+  in.flops_per_amp += 18.0;   // three complex products per amplitude
+}
+
 void emit_tc_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
   const Block& blk = P.blocks[r.block];
   TcPassDesc t;
@@ -634,7 +718,31 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   po.smem_weight = 1.0;
   po.fuse_parametric = o.fuse_parametric != 0;
   po.no_merge = no_merge;
-  p->blocks = contract(n, p->gates, po);
+  // Diagonal phase runs (reserved[2]: least gates per run, 0 = 2n, < 0 = none)
+  // become their own passes; the gates between them are contracted segment by
+  // segment, so no block moves across a run.
+  const int phase_min = o.reserved[2] == 0 ? std::max(16, 2 * n) : o.reserved[2];
+  if (!no_merge && !po.paper && phase_min > 0 && n >= kPhaseChunkBits)
+    p->runs = find_phase_runs(n, p->gates, phase_min, kPhaseMaxTerms, kPhaseMaxMixed, kPhaseChunkBits);
+  std::vector<std::pair<int, int>> items;   // (0, block) or (1, run) in program order
+  {
+    int pos = 0;
+    auto contract_range = [&](int b, int e) {
+      if (b >= e) return;
+      std::vector<HGate> sub(p->gates.begin() + b, p->gates.begin() + e);
+      for (Block& blk : contract(n, sub, po)) {
+        for (int& g : blk.gates) g += b;
+        items.push_back({0, (int)p->blocks.size()});
+        p->blocks.push_back(std::move(blk));
+      }
+    };
+    for (size_t r = 0; r < p->runs.size(); ++r) {
+      contract_range(pos, p->runs[r].begin);
+      items.push_back({1, (int)r});
+      pos = p->runs[r].end;
+    }
+    contract_range(pos, (int)p->gates.size());
+  }
   if (tensor) {
     // A block worth a tensor-core pass (one HBM sweep) carries many gates;
     // it is padded to 6 qubits with the highest qubits it does not touch.
@@ -654,7 +762,13 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   // ops in emission order
   std::vector<OpRec> ops;
   p->block_off.assign(p->blocks.size(), -1);
-  for (size_t b = 0; b < p->blocks.size(); ++b) {
+  for (const auto& it : items) {
+    if (it.first == 1) {
+      const PhaseRun& run = p->runs[it.second];
+      ops.push_back(OpRec{OP_PHASE, -1, it.second, run.qmask, run.qmask});
+      continue;
+    }
+    const size_t b = (size_t)it.second;
     const Block& blk = p->blocks[b];
     uint64_t qm = 0;
     for (int q : blk.qubits) qm |= 1ull << q;
@@ -673,6 +787,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   compute_blocks(*p, nullptr, false);
   in.blocks = 0;
   for (const Block& b : p->blocks) in.blocks += b.rep == OP_GATE ? (int64_t)b.gates.size() : 1;
+  in.blocks += (int64_t)p->runs.size();
   in.max_block_qubits = 0;
   // Runs of CUDA-core ops between tensor-core ops become tile passes.
   std::vector<OpRec> seg;
@@ -684,12 +799,15 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
     seg.clear();
   };
   for (const OpRec& r : ops) {
-    if (r.type != OP_TC) {
+    if (r.type != OP_TC && r.type != OP_PHASE) {
       seg.push_back(r);
       continue;
     }
     flush();
-    emit_tc_pass(*p, r, in);
+    if (r.type == OP_TC)
+      emit_tc_pass(*p, r, in);
+    else
+      emit_phase_pass(*p, r, in);
   }
   flush();
   in.passes = (int64_t)p->steps.size();
@@ -988,7 +1106,7 @@ qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits,
       }
     if (nq) *nq = k;
     if (gate_index) *gate_index = r.gate;
-    if (mat && r.type != OP_GATE) {
+    if (mat && r.type != OP_GATE && r.type != OP_PHASE) {
       const int64_t off = p->block_off[r.block];
       const int64_t D = 1ll << k;
       const int64_t cnt = r.type == OP_DIAG ? D : D * D;
@@ -996,6 +1114,29 @@ qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits,
         mat[2 * j] = p->h_btab[off + j].x;
         mat[2 * j + 1] = p->h_btab[off + j].y;
       }
+    }
+  });
+}
+
+qs_status qs_plan_phase_terms(qs_plan_t p, int64_t i, uint64_t* masks, int32_t* param_index, double* alpha0,
+                              double* coef, int64_t cap, int64_t* nterms) {
+  return guard([&] {
+    require(p != nullptr, "plan is NULL");
+    require(p->mode != QS_MODE_PER_GATE && i >= 0 && i < (int64_t)p->exec_ops.size(), "op index out of range");
+    const OpRec& r = p->exec_ops[i];
+    require(r.type == OP_PHASE, "op is not a phase pass");
+    int64_t step = -1;
+    for (size_t s = 0; s < p->steps.size(); ++s)
+      if (p->steps[s].kind == 2 && p->pass_ops[s].first == i) step = (int64_t)s;
+    require(step >= 0, "internal: phase op without a pass");
+    const PhasePassDesc& d = p->phdesc[p->steps[step].idx];
+    if (nterms) *nterms = d.nterms;
+    for (int64_t j = 0; j < d.nterms && j < cap; ++j) {
+      const DevPhaseTerm& t = p->h_pterms[d.term_off + j];
+      if (masks) masks[j] = t.mask;
+      if (param_index) param_index[j] = t.pidx;
+      if (alpha0) alpha0[j] = t.alpha0;
+      if (coef) coef[j] = t.coef;
     }
   });
 }
@@ -1424,6 +1565,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     if (!p->pgates.empty()) {
       require(theta != nullptr && (int64_t)ntheta >= p->nparams, "theta too short");
       p->d_theta.ensure(sizeof(double) * ntheta * B);
+      p->theta_stride = (int64_t)ntheta;   // phase passes read row b at b * ntheta (ntheta is in the graph key)
     }
     PreparedTerms P;
     double* d_part = nullptr;

@@ -428,6 +428,109 @@ void block_matrix(const Block& b, const std::vector<HGate>& gates, const double*
   }
 }
 
+// ---------------------------------------------------------------- phase runs
+
+// Phase-polynomial tracking: rows[q] is the parity mask, over the bits of the
+// index at the start of the run, that bit q holds now. A CNOT (c -> t) sets
+// rows[t] ^= rows[c]; a SWAP exchanges two rows; a diagonal gate on bit q
+// contributes terms in rows[q] (and rows[c] for a control). Where every row is
+// its own unit vector again, the run so far is diagonal in the original index.
+static bool phase_terms_of(const HGate& g, const std::vector<uint64_t>& rows, std::vector<PhaseTerm>& out) {
+  // angle a of the gate: RZ(a) = exp(-i a/2 Z), P(a) = diag(1, e^{ia})
+  double a0 = 0, ascale = 0;
+  int pidx = -1;
+  bool rz = false;
+  switch (g.kind) {
+    case QS_GATE_Z: a0 = M_PI; break;
+    case QS_GATE_S: a0 = M_PI / 2; break;
+    case QS_GATE_SDG: a0 = -M_PI / 2; break;
+    case QS_GATE_T: a0 = M_PI / 4; break;
+    case QS_GATE_TDG: a0 = -M_PI / 4; break;
+    case QS_GATE_RZ: rz = true; [[fallthrough]];
+    case QS_GATE_P:
+      a0 = g.param;
+      if (g.parametric) { ascale = g.scale; pidx = g.param_index; }
+      break;
+    default: return false;
+  }
+  if (g.nt != 1 || g.nc > 1) return false;
+  auto add = [&](uint64_t mask, double c) { out.push_back(PhaseTerm{mask, pidx, c * a0, c * ascale}); };
+  const uint64_t mt = rows[g.t[0]];
+  if (g.nc == 0) {
+    // RZ(a): e^{-i a/2 s}; P(a) = e^{i a b}, b = (1 - s)/2
+    add(mt, -0.5);
+    if (!rz) add(0, 0.5);
+  } else {
+    // controlled on b_c = (1 - s_c)/2: RZ gives e^{-i a/4 s_t} e^{+i a/4 s_c s_t};
+    // P gives e^{i a b_c b_t} = e^{i a/4 (1 - s_c - s_t + s_c s_t)}
+    const uint64_t mc = rows[g.c[0]];
+    add(mt, -0.25);
+    add(mc ^ mt, 0.25);
+    if (!rz) {
+      add(mc, -0.25);
+      add(0, 0.25);
+    }
+  }
+  return true;
+}
+
+std::vector<PhaseRun> find_phase_runs(int n, const std::vector<HGate>& gates, int min_gates, int max_terms,
+                                      int max_mixed, int low_bits) {
+  std::vector<PhaseRun> runs;
+  const int G = (int)gates.size();
+  const uint64_t low = low_bits >= 64 ? ~0ull : ((1ull << low_bits) - 1);
+  auto mixed = [&](uint64_t m) { return popc(m & low) >= 2 && (m & ~low) != 0; };
+  std::vector<uint64_t> rows(n);
+  std::vector<PhaseTerm> terms;
+  int i = 0;
+  while (i < G) {
+    for (int q = 0; q < n; ++q) rows[q] = 1ull << q;
+    terms.clear();
+    int off = 0, nmixed = 0;        // rows not equal to their unit vector; mixed terms so far
+    int best_end = -1;
+    size_t best_terms = 0;
+    uint64_t qm = 0, best_qm = 0;
+    auto set_row = [&](int q, uint64_t v) {
+      off -= rows[q] != (1ull << q);
+      rows[q] = v;
+      off += rows[q] != (1ull << q);
+    };
+    for (int h = i; h < G && h - i < 8192; ++h) {
+      const HGate& g = gates[h];
+      const size_t t0 = terms.size();
+      if (g.kind == QS_GATE_X && g.nt == 1 && g.nc == 1) {
+        set_row(g.t[0], rows[g.t[0]] ^ rows[g.c[0]]);
+      } else if (g.kind == QS_GATE_SWAP && g.nc == 0) {
+        const uint64_t a = rows[g.t[0]], b = rows[g.t[1]];
+        set_row(g.t[0], b);
+        set_row(g.t[1], a);
+      } else if (!phase_terms_of(g, rows, terms)) {
+        break;
+      }
+      for (size_t k = t0; k < terms.size(); ++k) nmixed += mixed(terms[k].mask);
+      if ((int)terms.size() > max_terms || nmixed > max_mixed) break;
+      qm |= g.qmask;
+      if (off == 0) {
+        best_end = h + 1;
+        best_terms = terms.size();
+        best_qm = qm;
+      }
+    }
+    if (best_end - i >= min_gates) {
+      PhaseRun r;
+      r.begin = i;
+      r.end = best_end;
+      r.qmask = best_qm;
+      r.terms.assign(terms.begin(), terms.begin() + best_terms);
+      runs.push_back(std::move(r));
+      i = best_end;
+    } else {
+      ++i;
+    }
+  }
+  return runs;
+}
+
 // ---------------------------------------------------------------- passes
 
 std::vector<PassRec> schedule_passes(int n, const std::vector<OpRec>& ops, int m, int L,

@@ -68,10 +68,33 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
 // product of the member gates (Eq. 7 for distinct qubits, M2 M1 on one qubit).
 void block_matrix(const Block& b, const std::vector<HGate>& gates, const double* theta, std::vector<cd>& M);
 
+// Phase polynomial of a diagonal run: the run multiplies amplitude x by
+// prod_j exp(i alpha_j s_j(x)), s_j(x) = (-1)^popcount(mask_j & x), with
+// alpha_j = alpha0 + coef * theta[pidx] (pidx >= 0) or alpha0 (pidx < 0).
+struct PhaseTerm {
+  uint64_t mask = 0;
+  int pidx = -1;
+  double alpha0 = 0, coef = 0;
+};
+// A contiguous run of program gates [begin, end) made of CNOTs, SWAPs and
+// diagonal gates (at most one control) whose GF(2) permutation of the basis
+// composes to the identity: the run is then a diagonal operator on the whole
+// register, exp(i sum_j alpha_j s_j(x)) (the cost layer of QAOA, Section 4.1's
+// third circuit class, is one such run per layer).
+struct PhaseRun {
+  int begin = 0, end = 0;
+  uint64_t qmask = 0;
+  std::vector<PhaseTerm> terms;
+};
+// Runs of at least min_gates gates, at most max_terms terms of which at most
+// max_mixed have >= 2 mask bits below low_bits together with a bit above.
+std::vector<PhaseRun> find_phase_runs(int n, const std::vector<HGate>& gates, int min_gates, int max_terms,
+                                      int max_mixed, int low_bits);
+
 struct OpRec {               // one op of the fused program (global qubit positions)
-  int type;                  // OP_GATE / OP_DENSE / OP_DIAG / OP_TC
+  int type;                  // OP_GATE / OP_DENSE / OP_DIAG / OP_TC / OP_PHASE
   int gate = -1;             // OP_GATE: gate index
-  int block = -1;            // block ops: block index
+  int block = -1;            // block ops: block index; OP_PHASE: run index
   uint64_t qmask = 0;
   uint64_t dmask = 0;        // qubits on which the op is diagonal
 };

@@ -51,7 +51,8 @@ enum OpType : int32_t {
   OP_GATE = 0,    // one original gate: form + tile-local positions, matrix from the gate table
   OP_DENSE = 1,   // dense k-qubit block, matrix (2^k x 2^k) in the block table
   OP_DIAG = 2,    // diagonal k-qubit block, 2^k phases in the block table
-  OP_TC = 3       // dense 6-qubit block applied on tensor cores (its own pass, complex64)
+  OP_TC = 3,      // dense 6-qubit block applied on tensor cores (its own pass, complex64)
+  OP_PHASE = 4    // diagonal phase polynomial of a gate run over the whole register (its own pass)
 };
 
 // A contracted block whose matrix depends on theta: rebuilt on the device from
@@ -87,6 +88,37 @@ cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wi
                            int* err, cudaStream_t st);
 size_t tc_smem_bytes();
 size_t tc_bulk_smem_bytes();
+
+// Diagonal phase pass: amplitude x times prod_j exp(i alpha_j s_j(x)),
+// s_j(x) = (-1)^popcount(mask_j & x), alpha_j = alpha0 + coef * theta[pidx]
+// (pidx >= 0) or alpha0.
+struct DevPhaseTerm {
+  uint64_t mask;
+  int32_t pidx;
+  int32_t pad;
+  double alpha0, coef;
+};
+constexpr int kPhaseChunkBits = 12;   // amplitudes per warp chunk: 2^12 (lo = bits 0..11)
+constexpr int kPhaseMaxTerms = 1024;
+constexpr int kPhaseMaxMixed = 16;
+// A pass's terms, in class order (relative to term_off): LOW [0, nlow) (only
+// bits below 12, at least two), LIN [lin_off[u], lin_off[u + 1]) for the one
+// bit u < 12 they have (lin_off[0] = nlow, lin_off[12] = high_begin), HIGH
+// [high_begin, mixed_begin) (no bit below 12), MIXED [mixed_begin, nterms).
+struct PhasePassDesc {
+  int32_t term_off, nterms;
+  int32_t nlow;
+  int32_t lin_off[kPhaseChunkBits + 1];
+  int32_t high_begin, mixed_begin;
+  int32_t occ;             // resident CTAs per SM, set by prepare_phase_pass
+};
+size_t phase_smem_bytes(int nterms, qs_dtype dt);
+cudaError_t prepare_phase_pass(PhasePassDesc& d, qs_dtype dt);
+// psis: device array of nstates state pointers (psi unused), else psi alone;
+// theta rows ntheta apart, one per state (may be null when no term has pidx >= 0)
+cudaError_t launch_phase_pass(void* psi, void* const* psis, int nstates, int n, qs_dtype dt,
+                              const DevPhaseTerm* terms, const PhasePassDesc& d, const double* theta,
+                              int64_t ntheta, cudaStream_t st);
 
 struct DevOp {
   int32_t type;

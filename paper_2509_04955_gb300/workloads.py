@@ -222,6 +222,47 @@ def qaoa(n: int, layers: int, edges) -> tuple[list[Gate], int]:
     return gates, 2 * layers
 
 
+def phase_run_circuit(n: int, layers: int, per_layer: int, seed: int, max_weight: int = 4):
+    """Layers of H on every qubit, each followed by a stretch of gates that is
+    diagonal as a whole: Z-string exponentials (a CNOT ladder, RZ, the ladder
+    undone; weight 2..max_weight), one-control phase gates (CP, CRZ, CZ, CS,
+    CT), one-qubit diagonal gates (Z, S, T, Sdg, Tdg, RZ, P) and SWAP
+    sandwiches (SWAP, a diagonal gate on one of the two qubits, SWAP). Angles
+    are parametric (one parameter each) or fixed uniform in [-pi, pi].
+    Returns (gates, number of parameters)."""
+    rng = _rng(seed)
+    gates: list[Gate] = []
+    npar = 0
+
+    def angle_gate(kind, q, controls=()):
+        nonlocal npar
+        if rng.integers(0, 2):
+            npar += 1
+            return Gate(kind, (q,), controls, param_index=npar - 1, scale=float(rng.choice([1.0, -2.0, 0.5])))
+        return Gate(kind, (q,), controls, angle=float(rng.uniform(-math.pi, math.pi)))
+
+    for _ in range(layers):
+        gates += [Gate("h", (q,)) for q in range(n)]
+        for _ in range(per_layer):
+            c = int(rng.integers(0, 4))
+            if c == 0:
+                sup = [int(q) for q in rng.choice(n, int(rng.integers(2, max_weight + 1)), replace=False)]
+                ladder = [Gate("x", (sup[i + 1],), (sup[i],)) for i in range(len(sup) - 1)]
+                gates += ladder + [angle_gate("rz", sup[-1])] + ladder[::-1]
+            elif c == 1:
+                a, b = (int(q) for q in rng.choice(n, 2, replace=False))
+                kind = ("p", "rz", "z", "s", "t")[int(rng.integers(0, 5))]
+                gates.append(angle_gate(kind, b, (a,)) if kind in ("p", "rz") else Gate(kind, (b,), (a,)))
+            elif c == 2:
+                q = int(rng.integers(0, n))
+                kind = ("z", "s", "t", "sdg", "tdg", "rz", "p")[int(rng.integers(0, 7))]
+                gates.append(angle_gate(kind, q) if kind in ("rz", "p") else Gate(kind, (q,)))
+            else:
+                a, b = (int(q) for q in rng.choice(n, 2, replace=False))
+                gates += [Gate("swap", (a, b)), angle_gate("p", a), Gate("swap", (a, b))]
+    return gates, npar
+
+
 def maxcut_hamiltonian(edges):
     """C = sum_edges (1 - Z_u Z_v) / 2 as (coeff, xmask, zmask): the number of
     cut edges of a computational basis state."""

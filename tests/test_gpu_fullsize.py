@@ -16,7 +16,10 @@ these add like a random walk, so the test requires
 after a round trip sits on the amplitude of size 1, unlike the forward
 results checked against 2e-5 elsewhere);
 * the batched UCC workload (20 qubits, 400 terms, 64 parameter vectors, one
-  CUDA graph): sampled states' <H> against the oracle.
+  CUDA graph): sampled states' <H> against the oracle;
+* QAOA at 30 qubits (8 GiB complex64, 16 GiB complex128): depth 1 gives the
+  expected cut of the published p = 1 closed form (pinned against the oracle
+  on small graphs); depth 4 times its inverse returns |0..0>.
 """
 import numpy as np
 import pytest
@@ -81,6 +84,43 @@ def test_n32_cz_circuit_tensor_plan_times_inverse(prec):
                                                                   tc_precision=prec))
     assert abs(mid - 1) < 1e-4 and abs(end - 1) < 1e-4
     assert max_abs <= bar and l2 <= bar, (max_abs, l2, bar)
+
+
+@pytest.mark.parametrize("dtname,mode", [("c64", Q.QS_MODE_FUSED), ("c64", Q.QS_MODE_TENSOR),
+                                         ("c128", Q.QS_MODE_FUSED)])
+def test_qaoa_n30_p1_expected_cut_closed_form(dtname, mode):
+    from closed_forms import qaoa_p1_maxcut
+    dt = {"c64": Q.QS_C64, "c128": Q.QS_C128}[dtname]
+    n = 30
+    edges = W.random_regular_graph(n, 3, seed=0)
+    gates, p = W.qaoa(n, 1, edges)
+    H = W.maxcut_hamiltonian(edges)
+    th = np.array([0.37, -0.81])
+    opts = Q.make_opts(mode=mode, tc_min_gates=4, fuse_parametric=1)
+    plan = Q.qs_plan_create(n, dt, gates, opts)
+    h = Q.qs_state_alloc(n, dt)
+    try:
+        assert sum(op["type"] == 4 for op in Q.qs_plan_ops(plan)) == 1
+        Q.qs_plan_execute(plan, h, th)
+        e = Q.qs_expval_pauli_sum(h, *H)
+        assert abs(Q.qs_norm(h) - 1) < (1e-12 if dt == Q.QS_C128 else 1e-5)
+        bar = (1e-10 if dt == Q.QS_C128 else 2e-5) * np.abs(H[0]).sum()
+        assert abs(e - qaoa_p1_maxcut(n, edges, *th)) <= bar, (e, qaoa_p1_maxcut(n, edges, *th))
+    finally:
+        Q.qs_state_free(h)
+        Q.qs_plan_free(plan)
+
+
+def test_qaoa_n30_p4_times_inverse():
+    n = 30
+    edges = W.random_regular_graph(n, 3, seed=0)
+    gates, p = W.qaoa(n, 4, edges)
+    th = W.thetas_uniform(p, 1)
+    fixed = W.inverse_circuit(W.inverse_circuit(gates, th))     # the same circuit with resolved angles
+    mid, end, max_abs, l2, bar = roundtrip(n, fixed, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4))
+    assert abs(mid - 1) < 1e-4 and abs(end - 1) < 1e-4
+    # phase passes and tile passes are FP32 products: about 1e-6 per pass
+    assert max_abs <= 2e-4 and l2 <= 2e-4, (max_abs, l2)
 
 
 def test_ucc_batched_n20_b64_sampled_against_oracle():

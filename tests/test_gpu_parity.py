@@ -679,3 +679,69 @@ def test_launch_counter_moves():
     before = Q.qs_launch_count()
     run(8, Q.QS_C64, W.random_layered(8, 2, 0))
     assert Q.qs_launch_count() > before
+
+
+def _phase_workload(maker, n):
+    if maker == "qaoa":
+        return W.qaoa(n, 3, W.random_regular_graph(n, 3, seed=n))
+    return W.phase_run_circuit(n, 3, 30, seed=n)
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+@pytest.mark.parametrize("maker,n", [("qaoa", 16), ("zoo", 15), ("qaoa", 12), ("zoo", 13), ("zoo", 18)])
+def test_phase_pass_matches_oracle(dtname, maker, n):
+    """Diagonal phase runs (QAOA cost layers; Z-string exponentials, one-control
+    phases and SWAP sandwiches) as one sweep each, from a random state, element
+    by element against the oracle. n = 12 is a single 4096-amplitude chunk;
+    n = 18 spans more chunks than the grid has warps."""
+    dt = DT[dtname]
+    gates, p = _phase_workload(maker, n)
+    theta = W.thetas_uniform(max(p, 1), 7)
+    psi0 = W.random_state(n, 8)
+    want = ref(n, gates, theta, psi0=psi0)
+    modes = [Q.make_opts(), Q.make_opts(fuse_k=2, phase_min_gates=4)]
+    if dt == Q.QS_C64 and n >= 13:
+        modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
+    for opts in modes:
+        plan = Q.qs_plan_create(n, dt, gates, opts)
+        try:
+            assert sum(op["type"] == 4 for op in Q.qs_plan_ops(plan)) >= 3
+        finally:
+            Q.qs_plan_free(plan)
+        got = run(n, dt, gates, theta, psi0=psi0, opts=opts)
+        assert np.abs(got - want).max() <= TOL[dt], (opts, np.abs(got - want).max())
+
+
+@pytest.mark.parametrize("dtname", ["c64", "c128"])
+def test_phase_pass_batched_rows_use_their_own_parameters(dtname):
+    """A QAOA plan executed for several parameter rows in one CUDA graph: the
+    phase pass reads each row's angles; every row's state and <C> against the
+    oracle, on capture and on replay with the rows reversed."""
+    dt = DT[dtname]
+    n, Bsz = 14, 5
+    edges = W.random_regular_graph(n, 3, seed=3)
+    gates, p = W.qaoa(n, 2, edges)
+    H = W.maxcut_hamiltonian(edges)
+    thetas = np.stack([W.thetas_uniform(p, 20 + b) for b in range(Bsz)])
+    modes = [Q.make_opts(), Q.make_opts(fuse_k=4, fuse_parametric=1)]
+    if dt == Q.QS_C64:
+        modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
+    for opts in modes:
+        plan = Q.qs_plan_create(n, dt, gates, opts)
+        states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
+        try:
+            for rep in range(2):
+                for s in states:
+                    Q.qs_state_set_basis(s, 0)
+                th = thetas if rep == 0 else thetas[::-1].copy()
+                ex = Q.qs_plan_execute_batched(plan, states, th, H)
+                for b in range(Bsz):
+                    psi = O.apply_circuit(O.basis(n, 0), n, gates, th[b])
+                    out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+                    Q.qs_state_copy_to_host(states[b], out)
+                    assert np.abs(out - psi).max() <= TOL[dt]
+                    assert abs(ex[b] - O.expval(psi, n, *H).real) <= TOL[dt] * np.abs(H[0]).sum() * 10
+        finally:
+            for s in states:
+                Q.qs_state_free(s)
+            Q.qs_plan_free(plan)

@@ -162,6 +162,70 @@ def test_paper_mode_compression_on_hea():
     Q.qs_plan_free(plan)
 
 
+def phase_diagonal(n, terms, theta):
+    """prod_j exp(i alpha_j (-1)^popcount(mask_j & x)) over all x."""
+    x = np.arange(1 << n, dtype=np.int64)
+    ang = np.zeros(1 << n)
+    for mask, pidx, a0, coef in terms:
+        a = a0 + (coef * theta[pidx] if pidx >= 0 else 0.0)
+        par = np.zeros(1 << n, dtype=np.int64)
+        for q in range(n):
+            if (mask >> q) & 1:
+                par ^= (x >> q) & 1
+        ang += a * (1 - 2 * par)
+    return np.exp(1j * ang)
+
+
+def apply_plan_ops(psi, n, gates, plan, theta):
+    cur = psi.copy()
+    for op in Q.qs_plan_ops(plan):
+        if op["type"] == 0:
+            cur = O.apply_circuit(cur, n, [gates[op["gate"]]], theta)
+        elif op["type"] == 2:
+            cur = apply_block(cur, n, op["qubits"], np.diag(op["matrix"]))
+        elif op["type"] == 4:
+            cur = cur * phase_diagonal(n, op["terms"], theta)
+        else:
+            cur = apply_block(cur, n, op["qubits"], op["matrix"])
+    return cur
+
+
+@pytest.mark.parametrize("maker", ["qaoa", "zoo"])
+def test_phase_runs_equal_their_gates(maker):
+    """Runs of CNOTs, SWAPs and diagonal gates whose basis permutation is the
+    identity become one diagonal phase op; its phase polynomial applied with
+    numpy, with the other ops, reproduces the oracle's gate-by-gate state for
+    random parameters. n = 14 > 12 puts masks on both sides of the kernel's
+    lo / hi split (every term class occurs in the zoo)."""
+    n = 14
+    if maker == "qaoa":
+        gates, p = W.qaoa(n, 3, W.random_regular_graph(n, 3, seed=1))
+    else:
+        gates, p = W.phase_run_circuit(n, 3, 30, seed=2)
+    theta = W.thetas_uniform(max(p, 1), 3)
+    psi = W.random_state(n, 4)
+    want = O.apply_circuit(psi, n, gates, theta)
+    for opts in (Q.make_opts(), Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4),
+                 Q.make_opts(phase_min_gates=4)):
+        plan = Q.qs_plan_create(n, Q.QS_C128, gates, opts) if opts.mode != Q.QS_MODE_TENSOR else \
+            Q.qs_plan_create(n, Q.QS_C64, gates, opts)
+        try:
+            ops = Q.qs_plan_ops(plan)
+            runs = [op for op in ops if op["type"] == 4]
+            assert len(runs) >= 3
+            assert np.abs(apply_plan_ops(psi, n, gates, plan, theta) - want).max() < 1e-12
+            if maker == "zoo":
+                low = (1 << 12) - 1
+                classes = {("low" if m & ~low == 0 else "mixed") if bin(m & low).count("1") >= 2 else
+                           ("lin" if m & low else "high") for op in runs for m, *_ in op["terms"]}
+                assert {"low", "lin", "high", "mixed"} <= classes, classes
+        finally:
+            Q.qs_plan_free(plan)
+    plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(phase_min_gates=-1))
+    assert not any(op["type"] == 4 for op in Q.qs_plan_ops(plan))
+    Q.qs_plan_free(plan)
+
+
 def test_per_gate_sweep_accounting():
     n = 8
     gates = [W.Gate("h", (0,)), W.Gate("x", (1,), controls=(0,)), W.Gate("z", (2,), controls=(1,)),

@@ -225,6 +225,24 @@ def test_qaoa_circuit_equals_matrix_exponentials():
         assert abs(O.expval(O.basis(n, x), n, *H).real - cut) < 1e-12
 
 
+def test_qaoa_p1_expected_cut_closed_form():
+    """Depth-1 QAOA on random 3- and 4-regular graphs (some with triangles):
+    the oracle's <C> equals the published p = 1 formula for every edge sum.
+    This pins the formula the full-size GPU test relies on."""
+    from closed_forms import qaoa_p1_maxcut
+    triangles = 0
+    for n, d, seed in ((8, 3, 0), (8, 3, 1), (10, 3, 4), (9, 4, 2), (10, 4, 5)):
+        edges = W.random_regular_graph(n, d, seed)
+        nb = [{v for e in edges for v in e if q in e and v != q} for q in range(n)]
+        triangles += sum(len(nb[u] & nb[v]) for u, v in edges)
+        gates, p = W.qaoa(n, 1, edges)
+        H = W.maxcut_hamiltonian(edges)
+        for th in ([0.37, -0.81], [1.1, 0.3], [-0.6, 1.4]):
+            psi = O.apply_circuit(O.basis(n, 0), n, gates, np.array(th))
+            assert abs(O.expval(psi, n, *H).real - qaoa_p1_maxcut(n, edges, *th)) < 1e-12
+    assert triangles > 0
+
+
 def test_pauli_exponential_closed_form():
     """exp(-i t P) psi = cos t psi - i sin t P psi for every letter mix."""
     n = 6
