@@ -49,7 +49,7 @@ def parse():
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
     ap.add_argument("--only-config", default=None,
                     choices=["qft_n30_m2", "qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20",
-                             "hea_adjoint_n24", "qaoa_n30"],
+                             "hea_adjoint_n24", "qaoa_n30", "smgp_ablation"],
                     help="run one configuration workload alone (no headline) and print its JSON")
     return ap.parse_args()
 
@@ -447,6 +447,49 @@ def run_configs(Q, torch, np, args):
         out["hea_adjoint_n24"] = config_hea(Q, torch, np, st, args)
     if want("qaoa_n30"):
         out["qaoa_n30"] = config_qaoa30(Q, torch, np, st, args)
+    if want("smgp_ablation"):
+        out["smgp_ablation"] = config_smgp(Q, torch, np, st, args)
+    return out
+
+
+def config_smgp(Q, torch, np, st, args):
+    """The ablation of Fig. 14 / 15 on GB300: QAOA (3-regular, p = 4) and VQE-HEA
+    (5 layers of RX, RY, RZ + staggered CNOTs) at 20-30 qubits, one gate per launch
+    (Algorithms 1-4) vs staggered multi-gate groups (Section 3.3) vs tile passes
+    (several gates per HBM sweep); time per circuit and average memory throughput
+    (the bytes each variant moves / its time)."""
+    from paper_2509_04955_gb300 import workloads as W
+    out = {"note": "throughput = sweeps x 2 x 2^n x amplitude bytes / time, the bytes each variant moves"}
+    for circ in ("qaoa", "hea"):
+        res = {}
+        for n in (20, 24, 28, 30):
+            if circ == "qaoa":
+                g, npar = W.qaoa(n, 4, W.random_regular_graph(n, 3, seed=0))
+            else:
+                g, npar = W.hea_staggered(n, 5)
+            th = W.thetas_uniform(npar, 2)
+            row = {"gates": len(g)}
+            for dname, dt in (("c128", Q.QS_C128), ("c64", Q.QS_C64)):
+                s = Q.qs_state_alloc(n, dt, st)
+                amp = 8 if dt == Q.QS_C64 else 16
+                r = {}
+                for name, opts in (("per_gate", None), ("smgp", Q.make_opts(mode=Q.QS_MODE_SMGP)),
+                                   ("tile_passes", Q.make_opts(mode=Q.QS_MODE_FUSED, phase_min_gates=-1))):
+                    plan = Q.qs_plan_create(n, dt, g, opts)
+                    Q.qs_state_set_basis(s, 0)
+                    Q.qs_plan_execute(plan, s, th)
+                    reps = 3 if n <= 24 else 1
+                    ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s, th), reps=reps)
+                    info = Q.qs_plan_info_get(plan)
+                    r[name] = {"ms": ms, "launches": info["launches"],
+                               "gbps": info["sweeps"] * 2 * (1 << n) * amp / (ms * 1e-3) / 1e9}
+                    Q.qs_plan_free(plan)
+                r["speedup_smgp_vs_per_gate"] = r["per_gate"]["ms"] / r["smgp"]["ms"]
+                r["speedup_tile_vs_per_gate"] = r["per_gate"]["ms"] / r["tile_passes"]["ms"]
+                row[dname] = r
+                Q.qs_state_free(s)
+            res[f"n{n}"] = row
+        out[circ] = res
     return out
 
 

@@ -84,9 +84,16 @@ typedef struct {
 typedef enum {
   QS_MODE_PER_GATE = 0,  /* one kernel launch per gate (Algorithms 1-4) */
   QS_MODE_FUSED = 1,     /* DAG contraction into k-qubit blocks + tile passes */
-  QS_MODE_TENSOR = 2     /* as FUSED with 6-qubit contraction; blocks carrying many gates are
+  QS_MODE_TENSOR = 2,    /* as FUSED with 6-qubit contraction; blocks carrying many gates are
                             applied as 64x64 complex GEMMs on tensor cores (tcgen05, FP32
                             accumulation); QS_C64 only, n >= 13 (smaller states plan as FUSED) */
+  QS_MODE_SMGP = 3       /* staggered multi-gate parallelism (Section 3.3, Tab. 3): runs of 2, 4 or 8
+                            consecutive uncontrolled one-target gates on distinct qubits become a
+                            group; the state is cut into S segments by qubits no member targets,
+                            and S launches of a two-dimensional block (x = amplitude pairs, y =
+                            member) let member j update segment (T + j) mod S at step T; other
+                            gates run one launch each as in QS_MODE_PER_GATE. Introspection and
+                            batched execution treat the plan as a per-gate plan. */
 } qs_mode;
 
 /* Planner and kernel options. Zero-initialised fields take the defaults. */

@@ -24,7 +24,7 @@ LIB_PATH = os.path.join(_HERE, "libqsgb300.so")
 
 QS_OK, QS_ERR_ARG, QS_ERR_OOM, QS_ERR_CUDA, QS_ERR_TIMEOUT, QS_ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5
 QS_C64, QS_C128 = 0, 1
-QS_MODE_PER_GATE, QS_MODE_FUSED, QS_MODE_TENSOR = 0, 1, 2
+QS_MODE_PER_GATE, QS_MODE_FUSED, QS_MODE_TENSOR, QS_MODE_SMGP = 0, 1, 2, 3
 KIND = {"h": 1, "x": 2, "y": 3, "z": 4, "s": 5, "sdg": 6, "t": 7, "tdg": 8, "rx": 9, "ry": 10,
         "rz": 11, "p": 12, "u1": 13, "swap": 14, "u2": 15}
 DTYPES = {"c64": QS_C64, "c128": QS_C128, "complex64": QS_C64, "complex128": QS_C128}

@@ -126,6 +126,11 @@ struct qs_plan_s {
     int kind;   // 0 = tile pass (pdesc[idx]), 1 = tensor-core pass (tcdesc[idx]), 2 = phase pass (phdesc[idx])
     int idx;
   };
+  // staggered multi-gate groups (per-gate plans built with QS_MODE_SMGP):
+  // steps in program order, (group, -1) or (-1, gate)
+  bool smgp = false;
+  std::vector<SmgpDesc> smgp_groups;
+  std::vector<std::pair<int, int>> smgp_steps;
   // diagonal phase runs (their own passes)
   std::vector<PhaseRun> runs;
   std::vector<PhasePassDesc> phdesc;
@@ -146,7 +151,7 @@ struct qs_plan_s {
   std::vector<double2> h_btab;
   // device
   bool uploaded = false;
-  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err, d_dblocks, d_dmem, d_pterms;
+  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err, d_dblocks, d_dmem, d_pterms, d_smgp;
   int gtab_rows = 0;
   qs_plan_info info{};
   // batched graph cache; captured and replayed on a plan-owned stream
@@ -277,6 +282,11 @@ void upload(qs_plan_s& p) {
     CK(cudaMemcpy(p.d_pterms.p, p.h_pterms.data(), sizeof(DevPhaseTerm) * p.h_pterms.size(), cudaMemcpyHostToDevice));
   }
   for (PhasePassDesc& d : p.phdesc) CK(prepare_phase_pass(d, p.dt));
+  if (!p.smgp_groups.empty()) {
+    p.d_smgp.ensure(sizeof(SmgpDesc) * p.smgp_groups.size());
+    CK(cudaMemcpy(p.d_smgp.p, p.smgp_groups.data(), sizeof(SmgpDesc) * p.smgp_groups.size(),
+                  cudaMemcpyHostToDevice));
+  }
   p.d_err.ensure(sizeof(int) * 4);
   CK(cudaMemset(p.d_err.p, 0, sizeof(int) * 4));
   // kernel attributes and occupancy, here and never during a stream capture
@@ -293,6 +303,23 @@ void check_state(const qs_state_s* s) { require(s != nullptr && s->d != nullptr,
 void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed = false) {
   const size_t G = std::max<size_t>(1, p.gates.size());
   const double2* gtab = p.d_gtab.as<double2>() + (size_t)row * 16 * G;
+  if (p.smgp) {
+    for (const auto& s : p.smgp_steps) {
+      if (timed) {
+        CK(cudaEventRecord(p.next_event(), st));
+        p.event_kind.push_back(0);
+      }
+      if (s.first < 0) {
+        CK(launch_gate(psi, p.n, p.dt, p.dgates[s.second], gtab + (size_t)s.second * 16, false, st));
+      } else {
+        const SmgpDesc& d = p.smgp_groups[s.first];
+        for (int T = 0; T < d.S; ++T)
+          CK(launch_smgp_step(psi, p.n, p.dt, p.d_smgp.as<SmgpDesc>() + s.first, d, T, gtab, st));
+      }
+      if (timed) CK(cudaEventRecord(p.next_event(), st));
+    }
+    return;
+  }
   const size_t nl = p.mode == QS_MODE_PER_GATE ? p.gates.size() : p.steps.size();
   for (size_t i = 0; i < nl; ++i) {
     if (timed) {
@@ -650,6 +677,71 @@ void default_opts(qs_plan_opts& o, qs_dtype dt, int n) {
   if (o.low_qubits > o.tile_qubits) o.low_qubits = o.tile_qubits;
 }
 
+// Staggered multi-gate groups (Section 3.3): runs of consecutive uncontrolled
+// one-target gates on distinct qubits, S = the largest power of two <= 8 that
+// the run and the register allow (S targets plus lg S segment qubits); the
+// segment qubits are the highest qubits no member targets.
+void plan_smgp(qs_plan_s& p) {
+  const int G = (int)p.gates.size(), n = p.n;
+  qs_plan_info& in = p.info;
+  in.launches = 0;
+  in.sweeps = 0;
+  int i = 0;
+  while (i < G) {
+    uint64_t used = 0;
+    int cnt = 0;
+    while (i + cnt < G && cnt < kSmgpMax) {
+      const HGate& g = p.gates[i + cnt];
+      if (g.nt != 1 || g.nc != 0 || (used & g.qmask)) break;
+      used |= g.qmask;
+      ++cnt;
+    }
+    int S = 1, lgS = 0;
+    while (2 * S <= cnt && 2 * S + lgS + 1 <= n) {
+      S *= 2;
+      ++lgS;
+    }
+    if (S < 2) {
+      p.smgp_steps.push_back({-1, i});
+      in.launches += 1;
+      in.sweeps += gate_sweep_fraction(p.gates[i]);
+      ++i;
+      continue;
+    }
+    SmgpDesc d;
+    std::memset(&d, 0, sizeof(d));
+    d.S = S;
+    d.lgS = lgS;
+    uint64_t targets = 0;
+    for (int j = 0; j < S; ++j) targets |= p.gates[i + j].qmask;
+    std::vector<int> seg;
+    for (int q = n - 1; q >= 0 && (int)seg.size() < lgS; --q)
+      if (!(targets & (1ull << q))) seg.push_back(q);
+    std::sort(seg.begin(), seg.end());
+    for (int s = 0; s < S; ++s) {
+      uint64_t o = 0;
+      for (int b = 0; b < lgS; ++b) o |= (uint64_t)((s >> b) & 1) << seg[b];
+      d.seg_or[s] = o;
+    }
+    for (int j = 0; j < S; ++j) {
+      const HGate& g = p.gates[i + j];
+      d.gate[j] = i + j;
+      d.form[j] = g.form;
+      d.t[j] = g.t[0];
+      std::vector<int> pos(seg);
+      pos.push_back(g.t[0]);
+      std::sort(pos.begin(), pos.end());
+      for (int k = 0; k < 4; ++k) d.pos[j][k] = k < (int)pos.size() ? pos[k] : 63;
+    }
+    p.smgp_steps.push_back({(int)p.smgp_groups.size(), -1});
+    p.smgp_groups.push_back(d);
+    in.launches += S;
+    in.sweeps += S;
+    i += S;
+  }
+  in.passes = in.launches;
+}
+
 // no_merge: every gate stays its own op (the reverse sweep of the adjoint gradient).
 qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, const qs_plan_opts* opts,
                        bool no_merge = false) {
@@ -661,7 +753,12 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   p->dt = dt;
   if (opts) p->opts = *opts;
   p->mode = p->opts.mode;
-  require(p->mode == QS_MODE_PER_GATE || p->mode == QS_MODE_FUSED || p->mode == QS_MODE_TENSOR, "bad mode");
+  require(p->mode == QS_MODE_PER_GATE || p->mode == QS_MODE_FUSED || p->mode == QS_MODE_TENSOR ||
+          p->mode == QS_MODE_SMGP, "bad mode");
+  if (p->mode == QS_MODE_SMGP) {   // a per-gate plan whose independent gate runs are staggered
+    p->smgp = true;
+    p->mode = QS_MODE_PER_GATE;
+  }
   resolve_gates(n, gates, ng, p->gates);
   for (size_t g = 0; g < p->gates.size(); ++g) {
     p->dgates.push_back(make_dev_gate(p->gates[g]));
@@ -678,6 +775,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
     in.passes = (int64_t)ng;
     in.launches = (int64_t)ng;
     in.sweeps = in.per_gate_sweeps;
+    if (p->smgp) plan_smgp(*p);
     for (const HGate& g : p->gates) in.flops_per_amp += 2 * gate_fma_per_amp(g);
     in.max_block_qubits = 0;
     for (const HGate& g : p->gates) in.max_block_qubits = std::max(in.max_block_qubits, __builtin_popcountll(g.qmask));

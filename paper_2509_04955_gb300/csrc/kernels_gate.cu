@@ -259,4 +259,78 @@ cudaError_t launch_gate(void* psi, int n, qs_dtype dt, const DevGate& g, const d
                       : launch_gate_t<double>(psi, n, g, mat, adjoint, st);
 }
 
+// ---------------------------------------------------------------- staggered multi-gate parallelism
+
+// Section 3.3's two-dimensional block: threadIdx.y selects the member gate,
+// threadIdx.x the amplitude pair, and at time step T member j works on
+// segment (T + j) mod S (the cyclic timeline of Tab. 3), so the S gates of a
+// launch never touch the same amplitudes. S launches apply every member to
+// every segment; the members act on distinct qubits and commute, so the
+// order in which a segment meets them does not matter. Each launch is one
+// sweep of the state (S segments, one gate each).
+template <typename R>
+__global__ void __launch_bounds__(256) k_smgp_step(typename V2<R>::T* __restrict__ psi, uint64_t count,
+                                                   const SmgpDesc* __restrict__ d, int T,
+                                                   const double2* __restrict__ gtab) {
+  using C = typename V2<R>::T;
+  const int j = threadIdx.y;
+  const int S = d->S, lg1 = d->lgS + 1;
+  const int s = (T + j) & (S - 1);
+  const Mat2<R> u = load_mat2<R>(gtab + (int64_t)d->gate[j] * 16, false);
+  const int form = d->form[j];
+  const uint64_t tb = 1ull << d->t[j], so = d->seg_or[s];
+  int32_t pos[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) pos[k] = d->pos[j][k];
+  const uint64_t stride = (uint64_t)gridDim.x * blockDim.x;
+  for (uint64_t p = (uint64_t)blockIdx.x * blockDim.x + threadIdx.x; p < count; p += stride) {
+    const uint64_t base = insert_zero_bits_u<4>(p, pos, lg1) | so;
+    const C a0 = psi[base], a1 = psi[base | tb];
+    C r0, r1;
+    switch (form) {   // uniform per warp: blockDim.x >= 32
+      case FORM_REAL1:
+        r0 = rmix<R>(u.m00.x, a0, u.m01.x, a1);
+        r1 = rmix<R>(u.m10.x, a0, u.m11.x, a1);
+        break;
+      case FORM_RXLIKE1:
+        r0 = ixmix<R>(u.m00.x, a0, u.m01.y, a1);
+        r1 = ixmix<R>(u.m11.x, a1, u.m10.y, a0);
+        break;
+      case FORM_X1:
+        r0 = a1;
+        r1 = a0;
+        break;
+      case FORM_ANTI1:
+        r0 = cmul(u.m01, a1);
+        r1 = cmul(u.m10, a0);
+        break;
+      case FORM_PHASE1:
+        r0 = a0;
+        r1 = cmul(u.m11, a1);
+        break;
+      case FORM_DIAG1:
+        r0 = cmul(u.m00, a0);
+        r1 = cmul(u.m11, a1);
+        break;
+      default:
+        r0 = cfma(u.m01, a1, cmul(u.m00, a0));
+        r1 = cfma(u.m11, a1, cmul(u.m10, a0));
+    }
+    psi[base] = r0;
+    psi[base | tb] = r1;
+  }
+}
+
+cudaError_t launch_smgp_step(void* psi, int n, qs_dtype dt, const SmgpDesc* d_desc, const SmgpDesc& h, int T,
+                             const double2* gtab, cudaStream_t st) {
+  if (h.S < 2 || h.S > kSmgpMax || (1 << h.lgS) != h.S || n < h.S + h.lgS) return cudaErrorInvalidValue;
+  const uint64_t count = 1ull << (n - h.lgS - 1);   // pairs per segment
+  const dim3 block(256 / h.S, h.S);
+  const int gr = grid_for(count, 256 / h.S);
+  if (dt == QS_C64) k_smgp_step<float><<<gr, block, 0, st>>>((float2*)psi, count, d_desc, T, gtab);
+  else k_smgp_step<double><<<gr, block, 0, st>>>((double2*)psi, count, d_desc, T, gtab);
+  note_launch();
+  return cudaGetLastError();
+}
+
 }  // namespace qs

@@ -190,6 +190,21 @@ cudaError_t launch_resolve(const DevGate* gates, const int32_t* param_gates, int
                            int64_t table_stride, cudaStream_t st);
 cudaError_t launch_gate(void* psi, int n, qs_dtype dt, const DevGate& g, const double2* mat,
                         bool adjoint, cudaStream_t st);
+// Staggered multi-gate group (Section 3.3, Tab. 3): S = 2^lgS one-target
+// gates on distinct qubits; the state is cut into S segments by lgS qubits no
+// member targets; at time step T gate j updates segment (T + j) mod S.
+constexpr int kSmgpMax = 8;
+struct SmgpDesc {
+  int32_t S, lgS;
+  int32_t gate[kSmgpMax];     // gate-table rows
+  int32_t form[kSmgpMax];     // GateForm of the target matrix (diagonal forms applied as 2x2)
+  int32_t t[kSmgpMax];        // target qubits
+  int32_t pos[kSmgpMax][4];   // ascending: the segment qubits and t[j] (lgS + 1 entries)
+  uint64_t seg_or[kSmgpMax];  // segment s -> its bits on the segment qubits
+};
+// One time step of group d (device descriptor), a 2-D block: x = amplitude pairs, y = member gate.
+cudaError_t launch_smgp_step(void* psi, int n, qs_dtype dt, const SmgpDesc* d_desc, const SmgpDesc& h_desc, int T,
+                             const double2* gtab, cudaStream_t st);
 // Batched forms: psis = device array of nstates state pointers (psi unused);
 // gate table rows gstride apart.
 cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,

@@ -189,6 +189,22 @@ def pauli_string_masks(n: int, support: list[int], letters: str) -> tuple[int, i
     return x, z
 
 
+def hea_staggered(n: int, layers: int) -> tuple[list[Gate], int]:
+    """The VQE-HEA circuit class of Section 4.1: per layer RX, RY, RZ on every
+    qubit (one parameter each), then CNOT(q -> q + 1) for q = layer mod 2,
+    layer mod 2 + 2, ... (staggered). Returns (gates, number of parameters)."""
+    gates: list[Gate] = []
+    k = 0
+    for layer in range(layers):
+        for kind in ("rx", "ry", "rz"):
+            for q in range(n):
+                gates.append(Gate(kind, (q,), param_index=k))
+                k += 1
+        for q in range(layer % 2, n - 1, 2):
+            gates.append(Gate("x", (q + 1,), (q,)))
+    return gates, k
+
+
 def random_regular_graph(n: int, degree: int, seed: int) -> list[tuple[int, int]]:
     """Edges (u < v) of a random simple d-regular graph on n vertices: the
     configuration model (n*d stubs paired at random), redrawn until the pairing

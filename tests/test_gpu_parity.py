@@ -745,3 +745,36 @@ def test_phase_pass_batched_rows_use_their_own_parameters(dtname):
             for s in states:
                 Q.qs_state_free(s)
             Q.qs_plan_free(plan)
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+@pytest.mark.parametrize("maker,n", [("hea", 12), ("qaoa", 14), ("layered", 11), ("mix", 7), ("hea", 5)])
+def test_smgp_staggered_groups_match_oracle(dtname, maker, n):
+    """Staggered multi-gate plans (groups of 8, 4 and 2 one-target gates, one
+    two-dimensional launch per time step) element by element against the
+    oracle, from a random state; every one-target form inside groups."""
+    dt = DT[dtname]
+    theta = None
+    if maker == "hea":
+        gates, p = W.hea_staggered(n, 3)
+        theta = W.thetas_uniform(p, 5)
+    elif maker == "qaoa":
+        gates, p = W.qaoa(n, 2, W.random_regular_graph(n, 3, seed=2))
+        theta = W.thetas_uniform(p, 6)
+    elif maker == "layered":
+        gates = W.random_layered(n, 6, seed=4)
+    else:
+        kinds = ("h", "x", "y", "z", "s", "sdg", "t", "tdg", "rx", "ry", "rz", "p")
+        rng = np.random.default_rng(9)
+        gates = [W.Gate(kinds[int(rng.integers(0, len(kinds)))], (q,), angle=float(rng.uniform(-3, 3)))
+                 for _ in range(4) for q in rng.permutation(n)]
+    psi0 = W.random_state(n, 10)
+    plan = Q.qs_plan_create(n, dt, gates, Q.make_opts(mode=Q.QS_MODE_SMGP))
+    try:
+        info = Q.qs_plan_info_get(plan)
+        assert info["launches"] == len(gates)   # S launches per group of S gates
+    finally:
+        Q.qs_plan_free(plan)
+    got = run(n, dt, gates, theta, psi0=psi0, opts=Q.make_opts(mode=Q.QS_MODE_SMGP))
+    want = ref(n, gates, theta, psi0=psi0)
+    assert np.abs(got - want).max() <= TOL[dt]

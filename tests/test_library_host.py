@@ -226,6 +226,25 @@ def test_phase_runs_equal_their_gates(maker):
     Q.qs_plan_free(plan)
 
 
+def test_smgp_groups_and_launch_accounting():
+    """Staggered multi-gate plans (Section 3.3): runs of uncontrolled one-target
+    gates on distinct qubits become groups of S = 8, 4 or 2 (S targets plus
+    lg S segment qubits must fit the register); each group costs S launches,
+    the other gates one each."""
+    n = 12
+    gates = [W.Gate("h", (q,)) for q in range(n)] + [W.Gate("x", (1,), (0,))] + \
+        [W.Gate("rz", (q,), angle=0.1) for q in (3, 4, 3)]
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(mode=Q.QS_MODE_SMGP))
+    info = Q.qs_plan_info_get(plan)
+    # 12 H -> groups of 8 and 4; CNOT single; RZ(3), RZ(4) -> group of 2; RZ(3) single
+    assert info["launches"] == 8 + 4 + 1 + 2 + 1
+    assert len(Q.qs_plan_ops(plan)) == len(gates)     # introspection as a per-gate plan
+    Q.qs_plan_free(plan)
+    small = Q.qs_plan_create(5, Q.QS_C64, [W.Gate("h", (q,)) for q in range(5)], Q.make_opts(mode=Q.QS_MODE_SMGP))
+    assert Q.qs_plan_info_get(small)["launches"] == 2 + 2 + 1    # S + lg S <= 5 caps groups at 2
+    Q.qs_plan_free(small)
+
+
 def test_per_gate_sweep_accounting():
     n = 8
     gates = [W.Gate("h", (0,)), W.Gate("x", (1,), controls=(0,)), W.Gate("z", (2,), controls=(1,)),
