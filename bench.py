@@ -46,6 +46,7 @@ def parse():
     ap.add_argument("--no-configs", action="store_true", help="skip the per-config side measurements")
     ap.add_argument("--full-configs", action="store_true",
                     help="also run the complex128 n=32 reference for the tensor-core config (64 GiB, ~1 min)")
+    ap.add_argument("--qaoa-n", type=int, default=30, help="register size of the qaoa_n30 configuration")
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
     ap.add_argument("--only-config", default=None,
                     choices=["qft_n30_m2", "qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20",
@@ -504,12 +505,12 @@ def config_qaoa30(Q, torch, np, st, args):
     from closed_forms import qaoa_p1_maxcut
     from paper_2509_04955_gb300 import workloads as W
     F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
-    n, p = 30, 4
+    n, p = args.qaoa_n, 4
     edges = W.random_regular_graph(n, 3, seed=0)
     g, npar = W.qaoa(n, p, edges)
     H = W.maxcut_hamiltonian(edges)
     th = W.thetas_uniform(npar, 1)
-    out = {"workload": f"QAOA MaxCut n=30, random 3-regular graph ({len(edges)} edges), p={p}, seeded angles",
+    out = {"workload": f"QAOA MaxCut n={n}, random 3-regular graph ({len(edges)} edges), p={p}, seeded angles",
            "gates": len(g)}
     pl = Q.qs_plan_create(n, Q.QS_C128, g, Q.make_opts(paper_mode=1))
     info = Q.qs_plan_info_get(pl)
