@@ -339,6 +339,24 @@ def main():
         Q.qs_state_set_basis(s128, 0)
         Q.qs_plan_execute(p128, s128)
         Q.qs_plan_free(p128)
+        # the same complex128 circuit with tile passes computed in FP32 pairs, against the FP64 run
+        kwp = dict(kw128, c128_pairs=1)
+        if kwp.get("mode") != F:
+            kwp = dict(mode=F, fuse_k=2, tile_qubits=11, low_qubits=3, c128_pairs=1)
+        s2 = Q.qs_state_alloc(n, Q.QS_C128, stream)
+        pp2 = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(**kwp))
+        ip2 = Q.qs_plan_info_get(pp2)
+        Q.qs_state_set_basis(s2, 0)
+        fp_ms, _, fpk, _ = time_steps(Q, torch, pp2, s2, 1, 1, per_launch=True)
+        Q.qs_state_set_basis(s2, 0)
+        Q.qs_plan_execute(pp2, s2)
+        m2, l2 = Q.qs_state_diff(s2, s128)
+        extra["c128_fused_fp32_pairs"] = dict(kwp, ms=fp_ms, passes=ip2["passes"],
+                                              pass_gbps=ip2["passes"] * sb128 / (fpk["ms"] * 1e-3) / 1e9,
+                                              max_abs_vs_fp64=m2, l2_vs_fp64=l2,
+                                              arithmetic="tile passes in FP32 pairs (about 2^-46 per operation)")
+        Q.qs_plan_free(pp2)
+        Q.qs_state_free(s2)
         prec = {}
         Q.qs_state_set_basis(state, 0)
         Q.qs_plan_execute(plan, state)

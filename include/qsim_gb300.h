@@ -121,7 +121,14 @@ typedef struct {
                             (Z, S, T, RZ, P and their one-control forms) whose permutation of
                             the basis composes to the identity, such as a QAOA cost layer; it
                             runs as one sweep multiplying amplitude x by
-                            prod_j exp(i alpha_j (-1)^popcount(mask_j & x)) (qs_plan_phase_terms). */
+                            prod_j exp(i alpha_j (-1)^popcount(mask_j & x)) (qs_plan_phase_terms).
+                            reserved[3]: QS_C128 fused plans: 0 = tile passes compute in FP64
+                            (default), 1 = in FP32 pairs ("double-float": each real held as h + l
+                            with two floats, error-free sum and product transformations, about
+                            46 significant bits, relative error near 2^-46 per operation); the
+                            state stays complex128 in memory, split into pairs when a tile is
+                            loaded and joined when it is stored. GB300's FP32 rate is about 64x
+                            its FP64 rate. */
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */

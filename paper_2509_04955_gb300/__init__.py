@@ -177,14 +177,15 @@ def _dptr(a):
 
 
 def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0,
-              fuse_parametric=0, tc_min_gates=0, tc_pipeline=0, phase_min_gates=0):
-    """qs_plan_opts; tc_min_gates, tc_pipeline and phase_min_gates fill reserved[0..2]."""
+              fuse_parametric=0, tc_min_gates=0, tc_pipeline=0, phase_min_gates=0, c128_pairs=0):
+    """qs_plan_opts; tc_min_gates, tc_pipeline, phase_min_gates and c128_pairs fill reserved[0..3]."""
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
     o.paper_mode, o.tc_precision, o.fuse_parametric = paper_mode, tc_precision, fuse_parametric
     o.reserved[0] = tc_min_gates
     o.reserved[1] = tc_pipeline
     o.reserved[2] = phase_min_gates
+    o.reserved[3] = c128_pairs
     return o
 
 
@@ -272,7 +273,7 @@ def qs_plan_autotune(state: int, gates, theta=None) -> tuple[QsPlanOpts, float]:
 def opts_dict(o: QsPlanOpts) -> dict:
     return {"mode": o.mode, "fuse_k": o.fuse_k, "tile_qubits": o.tile_qubits, "low_qubits": o.low_qubits,
             "tc_min_gates": o.reserved[0], "tc_precision": o.tc_precision, "tc_pipeline": o.reserved[1],
-            "phase_min_gates": o.reserved[2]}
+            "phase_min_gates": o.reserved[2], "c128_pairs": o.reserved[3]}
 
 
 def qs_apply_circuit(state: int, gates, theta=None, opts: QsPlanOpts | None = None):

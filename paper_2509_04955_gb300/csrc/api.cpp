@@ -142,6 +142,7 @@ struct qs_plan_s {
   std::vector<uint16_t> h_wimg;    // per TC pass: bf16 hi image then lo image (64 KiB)
   int tc_prec = 3;
   int tc_pipe = 0;                 // single-state tensor-core pass: 0 bulk-copy staged, 1 register-staged
+  bool df = false;                 // complex128 tile passes computed in FP32 pairs
   int64_t btab_elems = 0;
   // blocks whose matrices depend on theta, rebuilt on the device per batch row
   std::vector<DevBlock> h_dblocks;
@@ -505,6 +506,7 @@ void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::ve
   for (const PassRec& pr : passes) {
     PassDesc pd;
     std::memset(&pd, 0, sizeof(pd));
+    pd.df = P.df ? 1 : 0;
     pd.m = (int)pr.tile.size();
     pd.L = std::min(low_qubits, pd.m);
     pd.nhigh = pd.m - pd.L;
@@ -812,7 +814,11 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   po.amp_bytes = (int)amp_bytes(dt);
   // GB300: FP32 FMA 128 lanes/clk/SM, FP64 about 1/59 of that (measured),
   // shared memory 128 B/clk/SM -> one byte costs one FP32 FMA slot.
-  po.fp_weight = dt == QS_C64 ? 1.0 : 59.0;
+  // reserved[3] = 1: complex128 tile passes in FP32 pairs, about 15 FP32
+  // instructions per FMA (a pair product and a pair sum)
+  require(o.reserved[3] == 0 || o.reserved[3] == 1, "complex128 arithmetic (reserved[3]) must be 0 or 1");
+  p->df = dt == QS_C128 && o.reserved[3] == 1;
+  po.fp_weight = dt == QS_C64 ? 1.0 : (p->df ? 15.0 : 59.0);
   po.smem_weight = 1.0;
   po.fuse_parametric = o.fuse_parametric != 0;
   po.no_merge = no_merge;

@@ -21,12 +21,46 @@
 //   OP_DIAG  diagonal block, 2^k phases.
 #include <cuda_runtime.h>
 
+#include <type_traits>
+
 #include "cplx.cuh"
+#include "dfloat.cuh"
 #include "qs_internal.h"
 
 namespace qs {
 
 constexpr int kTileThreads = 256;
+
+// Amplitude type in HBM for each arithmetic type of the tile (complex128 tiles
+// computed in FP32 pairs keep complex128 in HBM).
+template <typename R> struct GAmp { using T = typename V2<R>::T; };
+template <> struct GAmp<dfl> { using T = double2; };
+
+// The same transfer for FP32-pair tiles: one complex128 amplitude per 16-byte
+// access, split into (h, l) pairs on the way in and joined on the way out.
+template <bool LOAD, int BATCH = 4>
+__device__ __forceinline__ void tile_io_df(double2* __restrict__ psi, dfc* tile, uint64_t base, const uint64_t* segoff,
+                                           uint32_t size, int L, uint32_t lmask) {
+  for (uint32_t e0 = threadIdx.x; e0 < size; e0 += kTileThreads * BATCH) {
+    double2 buf[BATCH];
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const uint32_t e = e0 + (uint32_t)u * kTileThreads;
+      if (e < size) {
+        if (LOAD) buf[u] = psi[base | segoff[e >> L] | (e & lmask)];
+        else buf[u] = from_dfc(tile[e]);
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < BATCH; ++u) {
+      const uint32_t e = e0 + (uint32_t)u * kTileThreads;
+      if (e < size) {
+        if (LOAD) tile[e] = to_dfc(buf[u]);
+        else psi[base | segoff[e >> L] | (e & lmask)] = buf[u];
+      }
+    }
+  }
+}
 
 // HBM <-> shared-memory transfer of one tile: 16-byte vectors, BATCH
 // independent loads issued before their shared-memory stores (and the reverse
@@ -235,15 +269,17 @@ __device__ __forceinline__ void apply_diag_op(typename V2<R>::T* tile, int m, co
 // Gate-only passes (KMAX <= 2) keep two CTAs per SM (load of one tile overlaps
 // the ops of the other); wider dense ops need more registers.
 template <typename R, int KMAX>
-__global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typename V2<R>::T* __restrict__ psi0,
+__global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typename GAmp<R>::T* __restrict__ psi0,
                                                         void* const* __restrict__ psis, int64_t gstride,
                                                         int64_t bstride, PassDesc p, const DevOp* __restrict__ ops,
                                                         const double2* __restrict__ gtab0,
                                                         const double2* __restrict__ btab, int lg_tiles,
                                                         uint64_t total) {
   using C = typename V2<R>::T;
+  using G = typename GAmp<R>::T;
   using C2 = typename std::conditional<sizeof(R) == 4, float4, double2>::type;  // 16-byte vector
   constexpr int VPT = 16 / sizeof(C);                                           // amplitudes per vector
+  constexpr bool kDF = std::is_same<R, dfl>::value;
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = p.m, L = p.L, nh = p.nhigh;
   C* tile = (C*)smem;
@@ -261,10 +297,11 @@ __global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typena
   // index tt covers state tt >> lg_tiles, whose gate table row is gstride apart.
   for (uint64_t tt = blockIdx.x; tt < total; tt += gridDim.x) {
     const uint64_t sb = tt >> lg_tiles, t = tt & ((1ull << lg_tiles) - 1);
-    C* __restrict__ psi = psis ? (C*)psis[sb] : psi0;
+    G* __restrict__ psi = psis ? (G*)psis[sb] : psi0;
     const double2* __restrict__ gtab = gtab0 + sb * gstride;
     const uint64_t base = insert_zero_bits(t << L, p.high, nh);
-    tile_io<C, C2, VPT, true>(psi, tile, base, segoff, size, L, lmask);
+    if constexpr (kDF) tile_io_df<true>(psi, tile, base, segoff, size, L, lmask);
+    else tile_io<C, C2, VPT, true>(psi, tile, base, segoff, size, L, lmask);
     __syncthreads();
     for (int o = p.op_begin; o < p.op_end; ++o) {
       const DevOp op = ops[o];
@@ -284,7 +321,8 @@ __global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typena
       }
       __syncthreads();
     }
-    tile_io<C, C2, VPT, false>(psi, tile, base, segoff, size, L, lmask);
+    if constexpr (kDF) tile_io_df<false>(psi, tile, base, segoff, size, L, lmask);
+    else tile_io<C, C2, VPT, false>(psi, tile, base, segoff, size, L, lmask);
     __syncthreads();
   }
 }
@@ -339,7 +377,7 @@ static cudaError_t launch_tile_t(void* psi, void* const* psis, int nstates, int6
   const uint64_t ntiles = 1ull << (n - p.m), total = ntiles * (uint64_t)nstates;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > total) grid = total;
-  k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename V2<R>::T*)psi, psis, gstride, bstride, p,
+  k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename GAmp<R>::T*)psi, psis, gstride, bstride, p,
                                                                 ops, gtab, btab, n - p.m, total);
   note_launch();
   return cudaGetLastError();
@@ -356,6 +394,15 @@ cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, 
       case 3: return launch_tile_t<float, 3>(QS_TILE_ARGS);
       case 4: return launch_tile_t<float, 4>(QS_TILE_ARGS);
       case 5: return launch_tile_t<float, 5>(QS_TILE_ARGS);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (p.df) {
+    switch (p.kmax) {
+      case 0: case 1: case 2: return launch_tile_t<dfl, 2>(QS_TILE_ARGS);
+      case 3: return launch_tile_t<dfl, 3>(QS_TILE_ARGS);
+      case 4: return launch_tile_t<dfl, 4>(QS_TILE_ARGS);
+      case 5: return launch_tile_t<dfl, 5>(QS_TILE_ARGS);
       default: return cudaErrorInvalidValue;
     }
   }
@@ -378,6 +425,15 @@ cudaError_t prepare_tile_pass(const PassDesc& p, qs_dtype dt) {
       case 3: return prepare_tile_t<float, 3>(smem);
       case 4: return prepare_tile_t<float, 4>(smem);
       case 5: return prepare_tile_t<float, 5>(smem);
+      default: return cudaErrorInvalidValue;
+    }
+  }
+  if (p.df) {
+    switch (p.kmax) {
+      case 0: case 1: case 2: return prepare_tile_t<dfl, 2>(smem);
+      case 3: return prepare_tile_t<dfl, 3>(smem);
+      case 4: return prepare_tile_t<dfl, 4>(smem);
+      case 5: return prepare_tile_t<dfl, 5>(smem);
       default: return cudaErrorInvalidValue;
     }
   }

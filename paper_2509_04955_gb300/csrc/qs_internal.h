@@ -140,6 +140,7 @@ struct PassDesc {
   int32_t kmax;            // widest dense block op in the pass (selects the kernel instance)
   int32_t mbuf_elems;      // matrix staging entries the pass needs (max over its ops)
   int32_t op_begin, op_end;
+  int32_t df;              // complex128 tile computed in FP32 pairs (double-float), else FP64
 };
 
 // Kernel attributes / occupancy of a pass's instance; host side, never during a capture.

@@ -778,3 +778,39 @@ def test_smgp_staggered_groups_match_oracle(dtname, maker, n):
     got = run(n, dt, gates, theta, psi0=psi0, opts=Q.make_opts(mode=Q.QS_MODE_SMGP))
     want = ref(n, gates, theta, psi0=psi0)
     assert np.abs(got - want).max() <= TOL[dt]
+
+
+PAIRS = [Q.make_opts(fuse_k=1, c128_pairs=1), Q.make_opts(fuse_k=3, c128_pairs=1),
+         Q.make_opts(fuse_k=5, tile_qubits=11, low_qubits=3, c128_pairs=1),
+         Q.make_opts(fuse_k=2, tile_qubits=6, low_qubits=2, c128_pairs=1),
+         Q.make_opts(paper_mode=1, c128_pairs=1)]
+
+
+@pytest.mark.parametrize("oi", range(len(PAIRS)))
+def test_c128_fp32_pair_tile_passes_match_oracle(oi):
+    """complex128 tile passes computed in FP32 pairs (every gate kind and form,
+    dense blocks k = 1..5, diagonal blocks) hold the complex128 bar against the
+    oracle, and sit within 1e-13 of the FP64 tile passes."""
+    n = 9
+    gates = W.random_gate_mix(n, 120, seed=30 + oi) + W.random_layered(n, 3, seed=oi)
+    psi0 = W.random_state(n, 4)
+    want = ref(n, gates, psi0=psi0)
+    got = run(n, Q.QS_C128, gates, psi0=psi0, opts=PAIRS[oi])
+    assert np.abs(got - want).max() <= 1e-12
+    fp64 = run(n, Q.QS_C128, gates, psi0=psi0, opts=Q.make_opts(fuse_k=3))
+    assert np.abs(got - fp64).max() <= 1e-13
+
+
+def test_c128_fp32_pairs_many_tiles_and_parameters():
+    """n = 18 random layers over many tiles, and a parametric HEA (device-resolved
+    angles, blocks rebuilt from theta) in FP32 pairs, against the oracle."""
+    n = 18
+    gates = W.random_layered(n, 6, seed=4)
+    got = run(n, Q.QS_C128, gates, opts=Q.make_opts(fuse_k=4, c128_pairs=1))
+    assert np.abs(got - ref(n, gates)).max() <= 1e-12
+    n = 12
+    gates, p = W.hea_staggered(n, 3)
+    theta = W.thetas_uniform(p, 3)
+    for opts in (Q.make_opts(c128_pairs=1), Q.make_opts(fuse_k=3, fuse_parametric=1, c128_pairs=1)):
+        got = run(n, Q.QS_C128, gates, theta, opts=opts)
+        assert np.abs(got - ref(n, gates, theta)).max() <= 1e-12
