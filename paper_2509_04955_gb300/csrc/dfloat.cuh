@@ -105,7 +105,8 @@ __device__ __forceinline__ double widen(float f) {
   const uint32_t u = __float_as_uint(f);
   const unsigned long long s = (unsigned long long)(u & 0x80000000u) << 32;
   if ((u & 0x7f800000u) == 0) return __longlong_as_double((long long)s);
-  return __longlong_as_double((long long)(s | ((unsigned long long)((u & 0x7fffffffu) + (896u << 23)) << 29)));
+  // exponent rebias 127 -> 1023 (+896) in 64-bit arithmetic: 896 << 23 does not fit 32 bits
+  return __longlong_as_double((long long)(s | (((unsigned long long)(u & 0x7fffffffu) + (896ull << 23)) << 29)));
 }
 
 __device__ __forceinline__ dfl::operator double() const { return widen(h) + widen(l); }

@@ -47,26 +47,35 @@ def df_fma(a, b, c):
     return fast_two_sum(s, t)
 
 
+M32, M64 = 0xFFFFFFFF, 0xFFFFFFFFFFFFFFFF
+
+
+def u32(x):
+    """A uint32 intermediate of the C code: wraps like the hardware."""
+    return x & M32
+
+
 def split(d):
     b = int(np.array([d], dtype=np.float64).view(np.uint64)[0])
-    hi, lo = b >> 32, b & 0xFFFFFFFF
+    hi, lo = b >> 32, b & M32
     ex, sign = (hi >> 20) & 0x7FF, hi & 0x80000000
-    u2f = lambda u: np.array([u], dtype=np.uint32).view(np.float32)[0]   # noqa: E731
+    u2f = lambda u: np.array([u32(u)], dtype=np.uint32).view(np.float32)[0]   # noqa: E731
     if ex <= 896:
         return f32(0), f32(0)
-    h = u2f(sign | ((ex - 896) << 23) | ((hi & 0xFFFFF) << 3) | (lo >> 29))
+    h = u2f(sign | u32(u32(ex - 896) << 23) | u32((hi & 0xFFFFF) << 3) | (lo >> 29))
     if ex < 920:
         return h, f32(0)
-    eb = (ex - 919) << 23
+    eb = u32(u32(ex - 919) << 23)
     return h, f32(u2f(sign | eb | ((lo & 0x1FFFFFFF) >> 6)) - u2f(sign | eb))
 
 
 def widen(f):
     u = int(np.array([f], dtype=np.float32).view(np.uint32)[0])
-    s = (u & 0x80000000) << 32
+    s = ((u & 0x80000000) << 32) & M64
     if (u & 0x7F800000) == 0:
         return np.array([s], dtype=np.uint64).view(np.float64)[0]
-    return np.array([s | (((u & 0x7FFFFFFF) + (896 << 23)) << 29)], dtype=np.uint64).view(np.float64)[0]
+    # 64-bit intermediate, as in the C code (896 << 23 needs 34 bits)
+    return np.array([s | ((((u & 0x7FFFFFFF) + (896 << 23)) << 29) & M64)], dtype=np.uint64).view(np.float64)[0]
 
 
 def join(p):
