@@ -103,6 +103,36 @@ __device__ __forceinline__ uint32_t ins0k(uint32_t x, const int32_t* pos) {
   return x;
 }
 
+// One-target gate over the tile: each thread takes kPairBatch independent
+// pairs per iteration (all loads, then the arithmetic, then the stores), so
+// the dependent chains of one pair overlap with the others'. A slot past the
+// end recomputes the iteration's first pair and does not store.
+constexpr int kPairBatch = 4;
+
+template <typename C, typename F>
+__device__ __forceinline__ void pairs_apply(C* tile, uint32_t count, const int32_t* ins, int nins, uint32_t cmask,
+                                            uint32_t ta, F f) {
+  for (uint32_t p0 = threadIdx.x; p0 < count; p0 += kTileThreads * kPairBatch) {
+    uint32_t idx[kPairBatch];
+    C a0[kPairBatch], a1[kPairBatch];
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u) {
+      const uint32_t p = p0 + (uint32_t)u * kTileThreads;
+      idx[u] = ins0(p < count ? p : p0, ins, nins) | cmask;
+      a0[u] = tile[idx[u]];
+      a1[u] = tile[idx[u] | ta];
+    }
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u) f(a0[u], a1[u]);
+#pragma unroll
+    for (int u = 0; u < kPairBatch; ++u)
+      if (p0 + (uint32_t)u * kTileThreads < count) {
+        tile[idx[u]] = a0[u];
+        tile[idx[u] | ta] = a1[u];
+      }
+  }
+}
+
 template <typename R>
 __device__ __forceinline__ void apply_gate_op(typename V2<R>::T* tile, int m, const DevOp& op,
                                               const double2* __restrict__ gtab, typename V2<R>::T* mbuf) {
@@ -143,44 +173,39 @@ __device__ __forceinline__ void apply_gate_op(typename V2<R>::T* tile, int m, co
   const C m00 = from_d<R>(mat[0]), m01 = from_d<R>(mat[1]), m10 = from_d<R>(mat[2]), m11 = from_d<R>(mat[3]);
   switch (op.form) {
     case FORM_DENSE1:
-      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
-        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
-        const C a0 = tile[b], a1 = tile[b | ta];
-        tile[b] = cfma(m01, a1, cmul(m00, a0));
-        tile[b | ta] = cfma(m11, a1, cmul(m10, a0));
-      }
+      pairs_apply(tile, count, op.ins, op.nins, op.cmask, ta, [&](C& a0, C& a1) {
+        const C r0 = cfma(m01, a1, cmul(m00, a0));
+        a1 = cfma(m11, a1, cmul(m10, a0));
+        a0 = r0;
+      });
       break;
     case FORM_REAL1:
-      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
-        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
-        const C a0 = tile[b], a1 = tile[b | ta];
-        tile[b] = rmix<R>(m00.x, a0, m01.x, a1);
-        tile[b | ta] = rmix<R>(m10.x, a0, m11.x, a1);
-      }
+      pairs_apply(tile, count, op.ins, op.nins, op.cmask, ta, [&](C& a0, C& a1) {
+        const C r0 = rmix<R>(m00.x, a0, m01.x, a1);
+        a1 = rmix<R>(m10.x, a0, m11.x, a1);
+        a0 = r0;
+      });
       break;
     case FORM_RXLIKE1:
-      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
-        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
-        const C a0 = tile[b], a1 = tile[b | ta];
-        tile[b] = ixmix<R>(m00.x, a0, m01.y, a1);
-        tile[b | ta] = ixmix<R>(m11.x, a1, m10.y, a0);
-      }
+      pairs_apply(tile, count, op.ins, op.nins, op.cmask, ta, [&](C& a0, C& a1) {
+        const C r0 = ixmix<R>(m00.x, a0, m01.y, a1);
+        a1 = ixmix<R>(m11.x, a1, m10.y, a0);
+        a0 = r0;
+      });
       break;
     case FORM_X1:
-      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
-        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
-        const C a0 = tile[b], a1 = tile[b | ta];
-        tile[b] = a1;
-        tile[b | ta] = a0;
-      }
+      pairs_apply(tile, count, op.ins, op.nins, op.cmask, ta, [&](C& a0, C& a1) {
+        const C r0 = a1;
+        a1 = a0;
+        a0 = r0;
+      });
       break;
     case FORM_ANTI1:
-      for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
-        const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
-        const C a0 = tile[b], a1 = tile[b | ta];
-        tile[b] = cmul(m01, a1);
-        tile[b | ta] = cmul(m10, a0);
-      }
+      pairs_apply(tile, count, op.ins, op.nins, op.cmask, ta, [&](C& a0, C& a1) {
+        const C r0 = cmul(m01, a1);
+        a1 = cmul(m10, a0);
+        a0 = r0;
+      });
       break;
     case FORM_PHASE1:
       for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
