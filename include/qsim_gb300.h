@@ -311,6 +311,45 @@ qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t
 qs_status qs_plan_phase_terms(qs_plan_t p, int64_t i, uint64_t* masks, int32_t* param_index, double* alpha0,
                               double* coef, int64_t cap, int64_t* nterms);
 
+/* ---------------- host-resident states (Section 3.2, batched processing) ----------------
+ * A state larger than device memory stays in host memory (on Grace, the CPU's
+ * memory reached over NVLink-C2C). The high n - batch_qubits qubits index
+ * batches of 2^batch_qubits contiguous amplitudes (Section 3.2: the batch
+ * index is the high qubits). The circuit is cut into streamed passes, each
+ * touching at most pass_qubits batch-index qubits: the tile-pass scheduler with
+ * the batch_qubits low qubits always present, so gates move ahead of gates they
+ * commute with (disjoint qubits, or diagonal on the shared ones). For each pass, every group of 2^(qubits it selects) batches is copied into
+ * one of three device buffers, the pass's gates run there as a plan over
+ * batch_qubits + selected qubits (planned with opts, so tile, tensor-core and
+ * phase passes all apply), and the group is copied back; copies in, compute
+ * and copies out run on three streams, so one group loads while another is
+ * computed and a third is stored (the multi-buffering of Tab. 2). */
+typedef struct {
+  int64_t passes;        /* streamed passes: the state crosses the host link twice per pass */
+  int64_t groups;        /* buffer loads over all passes */
+  int64_t copies;        /* host <-> device copies issued */
+  double bytes_h2d, bytes_d2h;
+  double device_bytes;   /* device memory held by the three buffers */
+  int64_t reserved[4];
+} qs_stream_info;
+
+/* Applies the circuit to host_psi (2^n amplitudes of dtype, interleaved (re, im);
+ * page-locked memory for overlapped copies, e.g. cudaHostAlloc or a pinned
+ * torch tensor), in place. 1 <= batch_qubits <= n, 0 <= pass_qubits <= n -
+ * batch_qubits, batch_qubits + pass_qubits <= 40; every gate may touch at
+ * most pass_qubits qubits >= batch_qubits (QS_ERR_ARG otherwise). Device
+ * memory: 3 x 2^(batch_qubits + pass_qubits) amplitudes. Blocks until the
+ * state is back in host memory. info may be NULL. */
+qs_status qs_stream_apply(void* host_psi, int n, qs_dtype dtype, const qs_gate* gates, size_t ngates,
+                          const double* theta, size_t ntheta, const qs_plan_opts* opts, int batch_qubits,
+                          int pass_qubits, qs_stream_info* info);
+/* Host only: the streamed passes qs_stream_apply would run. high_masks[i] = the
+ * batch-index qubits pass i touches, pass_end[i] = the end of its gates in
+ * order (both capacity cap, may be NULL); order (capacity ngates, may be NULL)
+ * = the gate indices in execution order. */
+qs_status qs_stream_plan(int n, const qs_gate* gates, size_t ngates, int batch_qubits, int pass_qubits,
+                         int64_t* npasses, uint64_t* high_masks, int64_t* pass_end, int64_t cap, int32_t* order);
+
 /* ---------------- measurement ----------------
  * With timing enabled, every kernel launch issued by qs_plan_execute is
  * bracketed by two CUDA events on the state's stream. qs_plan_timing_read

@@ -63,6 +63,14 @@ class QsPlanInfo(C.Structure):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
 
 
+class QsStreamInfo(C.Structure):
+    _fields_ = [("passes", C.c_int64), ("groups", C.c_int64), ("copies", C.c_int64), ("bytes_h2d", C.c_double),
+                ("bytes_d2h", C.c_double), ("device_bytes", C.c_double), ("reserved", C.c_int64 * 4)]
+
+    def as_dict(self) -> dict:
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
 _VP, _I64P, _I32P, _DP = C.c_void_p, C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.POINTER(C.c_double)
 
 # name -> (restype, argtypes)
@@ -97,6 +105,10 @@ _SIGS = {
     "qs_plan_op_count": (C.c_int, [_VP, _I64P, _I64P]),
     "qs_plan_op_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I32P, _I32P, _DP]),
     "qs_plan_pass_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I64P, _I64P]),
+    "qs_stream_apply": (C.c_int, [_VP, C.c_int, C.c_int, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t,
+                                  C.POINTER(QsPlanOpts), C.c_int, C.c_int, C.POINTER(QsStreamInfo)]),
+    "qs_stream_plan": (C.c_int, [C.c_int, C.POINTER(QsGate), C.c_size_t, C.c_int, C.c_int, _I64P,
+                                 C.POINTER(C.c_uint64), _I64P, C.c_int64, _I32P]),
     "qs_plan_phase_terms": (C.c_int, [_VP, C.c_int64, C.POINTER(C.c_uint64), _I32P, _DP, _DP, C.c_int64, _I64P]),
     "qs_plan_set_timing": (C.c_int, [_VP, C.c_int]),
     "qs_plan_timing_read": (C.c_int, [_VP, _DP, _I64P]),
@@ -281,6 +293,44 @@ def qs_apply_circuit(state: int, gates, theta=None, opts: QsPlanOpts | None = No
     _check(lib().qs_apply_circuit(state, pack_gates(gates), len(gates),
                                   th.ctypes.data_as(_DP) if th is not None else None, nt,
                                   C.byref(opts) if opts is not None else None))
+
+
+def _host_ptr(a) -> int:
+    """Address of a host buffer: a numpy array or a (pinned) CPU torch tensor."""
+    if hasattr(a, "data_ptr"):
+        assert not a.is_cuda and a.is_contiguous()
+        return a.data_ptr()
+    assert a.flags["C_CONTIGUOUS"] and a.flags["WRITEABLE"]
+    return a.ctypes.data
+
+
+def qs_stream_apply(host_psi, n: int, dtype: int, gates, theta=None, opts: QsPlanOpts | None = None,
+                    batch_qubits: int = 0, pass_qubits: int = 2) -> dict:
+    """Applies the circuit to a host-resident state in place, streaming it through
+    three device buffers (qs_stream_apply); returns the stream statistics."""
+    th, nt = _dptr(theta)
+    info = QsStreamInfo()
+    _check(lib().qs_stream_apply(_host_ptr(host_psi), n, dtype, pack_gates(gates), len(gates),
+                                 th.ctypes.data_as(_DP) if th is not None else None, nt,
+                                 C.byref(opts) if opts is not None else None, batch_qubits, pass_qubits,
+                                 C.byref(info)))
+    return info.as_dict()
+
+
+def qs_stream_plan(n: int, gates, batch_qubits: int, pass_qubits: int) -> list[tuple[int, list[int]]]:
+    """Streamed passes (host only): (batch-index qubit mask, gate indices in execution order)."""
+    cnt = C.c_int64()
+    pg = pack_gates(gates)
+    _check(lib().qs_stream_plan(n, pg, len(gates), batch_qubits, pass_qubits, C.byref(cnt), None, None, 0, None))
+    k = max(1, cnt.value)
+    m, e = (C.c_uint64 * k)(), (C.c_int64 * k)()
+    order = (C.c_int32 * max(1, len(gates)))()
+    _check(lib().qs_stream_plan(n, pg, len(gates), batch_qubits, pass_qubits, C.byref(cnt), m, e, cnt.value, order))
+    out, b = [], 0
+    for i in range(cnt.value):
+        out.append((int(m[i]), [int(order[j]) for j in range(b, e[i])]))
+        b = e[i]
+    return out
 
 
 def qs_norm(state: int) -> float:

@@ -814,3 +814,35 @@ def test_c128_fp32_pairs_many_tiles_and_parameters():
     for opts in (Q.make_opts(c128_pairs=1), Q.make_opts(fuse_k=3, fuse_parametric=1, c128_pairs=1)):
         got = run(n, Q.QS_C128, gates, theta, opts=opts)
         assert np.abs(got - ref(n, gates, theta)).max() <= 1e-12
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+@pytest.mark.parametrize("maker", ["layered", "qaoa", "mix"])
+def test_stream_apply_host_resident_state(dtname, maker):
+    """A state held in host memory and streamed through three device buffers
+    (Section 3.2's batches, high qubits = batch index) equals the oracle, with
+    per-gate, fused and (complex64, 13-qubit buffers) tensor-core sub-plans,
+    from pageable numpy memory and from pinned torch memory."""
+    import torch
+    dt = DT[dtname]
+    n, theta = 16, None
+    if maker == "layered":
+        gates = W.random_layered(n, 5, seed=3)
+    elif maker == "qaoa":
+        gates, p = W.qaoa(n, 2, W.random_regular_graph(n, 3, seed=4))
+        theta = W.thetas_uniform(p, 2)
+    else:
+        gates = [g for g in W.random_gate_mix(n, 80, seed=5) if sum(q >= 11 for q in g.qubits) <= 2]
+    psi0 = W.random_state(n, 6)
+    want = ref(n, gates, theta, psi0=psi0)
+    cases = [(None, 10, 2), (Q.make_opts(), 10, 2), (Q.make_opts(fuse_k=3), 11, 3)]
+    if dt == Q.QS_C64:
+        cases.append((Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2), 11, 2))
+    for opts, l, h in cases:
+        host = np.ascontiguousarray(psi0, dtype=Q.NP_DTYPE[dt])
+        info = Q.qs_stream_apply(host, n, dt, gates, theta, opts, batch_qubits=l, pass_qubits=h)
+        assert info["passes"] == len(Q.qs_stream_plan(n, gates, l, h)) >= 2
+        assert np.abs(host - want).max() <= TOL[dt], (opts, l, h)
+    pinned = torch.from_numpy(np.ascontiguousarray(psi0, dtype=Q.NP_DTYPE[dt])).pin_memory()
+    Q.qs_stream_apply(pinned, n, dt, gates, theta, Q.make_opts(), batch_qubits=10, pass_qubits=2)
+    assert np.abs(pinned.numpy() - want).max() <= TOL[dt]

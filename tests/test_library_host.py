@@ -245,6 +245,31 @@ def test_smgp_groups_and_launch_accounting():
     Q.qs_plan_free(small)
 
 
+@pytest.mark.parametrize("l,h", [(8, 2), (9, 1), (6, 3)])
+def test_stream_passes_reorder_only_commuting_gates(l, h):
+    """Host-resident execution (Section 3.2): streamed passes come from the
+    tile-pass scheduler with the l low qubits always present and at most h
+    batch-index qubits per pass. Every gate appears once; applying the passes'
+    gates in their order reproduces the circuit (oracle, n = 11); random layers
+    at depth 6 need several passes, and a gate needing more than h batch qubits
+    is an argument error."""
+    n = 11
+    gates = W.random_layered(n, 6, seed=l) + W.random_gate_mix(n, 40, seed=h)
+    gates = [g for g in gates if sum(q >= l for q in g.qubits) <= h]
+    passes = Q.qs_stream_plan(n, gates, l, h)
+    order = [g for _, gs in passes for g in gs]
+    assert sorted(order) == list(range(len(gates)))
+    assert all(bin(m).count("1") <= h and m & ((1 << l) - 1) == 0 for m, _ in passes)
+    psi = W.random_state(n, 5)
+    want = O.apply_circuit(psi, n, gates)
+    got = O.apply_circuit(psi, n, [gates[i] for i in order])
+    assert np.abs(got - want).max() < 1e-12
+    assert len(passes) > 1
+    with pytest.raises(Q.QsError):
+        Q.qs_stream_plan(n, [W.Gate("x", (10,), (8, 9))], 8, 2)
+    assert len(Q.qs_stream_plan(n, gates, l, n - l)) == 1
+
+
 def test_per_gate_sweep_accounting():
     n = 8
     gates = [W.Gate("h", (0,)), W.Gate("x", (1,), controls=(0,)), W.Gate("z", (2,), controls=(1,)),
