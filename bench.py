@@ -47,10 +47,11 @@ def parse():
     ap.add_argument("--full-configs", action="store_true",
                     help="also run the complex128 n=32 reference for the tensor-core config (64 GiB, ~1 min)")
     ap.add_argument("--qaoa-n", type=int, default=30, help="register size of the qaoa_n30 configuration")
+    ap.add_argument("--stream-n", type=int, default=31, help="register size of the host-resident configuration")
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
     ap.add_argument("--only-config", default=None,
                     choices=["qft_n30_m2", "qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20",
-                             "hea_adjoint_n24", "qaoa_n30", "smgp_ablation"],
+                             "hea_adjoint_n24", "qaoa_n30", "smgp_ablation", "stream_host_state"],
                     help="run one configuration workload alone (no headline) and print its JSON")
     return ap.parse_args()
 
@@ -468,6 +469,70 @@ def run_configs(Q, torch, np, args):
         out["qaoa_n30"] = config_qaoa30(Q, torch, np, st, args)
     if want("smgp_ablation"):
         out["smgp_ablation"] = config_smgp(Q, torch, np, st, args)
+    if want("stream_host_state"):
+        out["stream_host_state"] = config_stream(Q, torch, np, st, args)
+    return out
+
+
+def config_stream(Q, torch, np, st, args):
+    """Section 3.2's batched processing on one GB300: a complex64 state kept in
+    pinned host memory, streamed through three device buffers of 2^(l + 2)
+    amplitudes (batches of 2^l, the 4 high qubits as batch index, at most 2 of
+    them per pass). Reported against the host link's own duplex copy rate (the
+    roofline of a streamed pass: the state crosses the link once each way) and
+    against the same circuit run with the state resident in HBM."""
+    from paper_2509_04955_gb300 import workloads as W
+    n = args.stream_n
+    l, h = n - 4, 2
+    gates = W.random_layered(n, 4, seed=0)
+    nb = (1 << n) * 8
+    out = {"workload": f"random layered n={n} depth 4, complex64 state in pinned host memory "
+                       f"({nb / 2**30:.0f} GiB), batches of 2^{l}, 2 batch qubits per pass", "gates": len(gates)}
+    host = torch.zeros(1 << n, dtype=torch.complex64, pin_memory=True)
+    host[0] = 1
+    # duplex copy rate of the link: the whole state in batch-sized chunks each way at once
+    dev = torch.empty(2 << l, dtype=torch.complex64, device="cuda")
+    s1, s2 = torch.cuda.Stream(), torch.cuda.Stream()
+    chunk = 1 << l
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for c in range(1 << (n - l)):
+        with torch.cuda.stream(s1):
+            dev[:chunk].copy_(host[c * chunk:(c + 1) * chunk], non_blocking=True)
+        with torch.cuda.stream(s2):
+            host[c * chunk:(c + 1) * chunk].copy_(dev[chunk:], non_blocking=True)
+    torch.cuda.synchronize()
+    dt_copy = time.perf_counter() - t0
+    del dev
+    host.zero_()
+    host[0] = 1
+    out["link_duplex_gbps_each_way"] = nb / dt_copy / 1e9
+    opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2)
+    Q.qs_stream_apply(host, n, Q.QS_C64, gates[:2], None, opts, batch_qubits=l, pass_qubits=h)   # warm-up
+    host.zero_()
+    host[0] = 1
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    info = Q.qs_stream_apply(host, n, Q.QS_C64, gates, None, opts, batch_qubits=l, pass_qubits=h)
+    ms = (time.perf_counter() - t0) * 1e3
+    out.update(info)
+    out["ms"] = ms
+    out["link_gbps_each_way"] = info["passes"] * nb / (ms * 1e-3) / 1e9
+    out["frac_of_link_duplex"] = out["link_gbps_each_way"] / out["link_duplex_gbps_each_way"]
+    # the same circuit with the state resident in HBM, and the two results compared
+    s = Q.qs_state_alloc(n, Q.QS_C64, st)
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
+    Q.qs_state_set_basis(s, 0)
+    out["in_hbm_ms"] = device_ms(torch, lambda: Q.qs_plan_execute(plan, s))
+    Q.qs_state_set_basis(s, 0)
+    Q.qs_plan_execute(plan, s)
+    s2 = Q.qs_state_alloc(n, Q.QS_C64, st)
+    Q.lib().qs_state_copy_from_host(s2, host.data_ptr(), nb)
+    out["max_abs_diff_vs_in_hbm"], out["l2_diff_vs_in_hbm"] = Q.qs_state_diff(s2, s)
+    Q.qs_plan_free(plan)
+    Q.qs_state_free(s)
+    Q.qs_state_free(s2)
+    del host
     return out
 
 
