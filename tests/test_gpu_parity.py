@@ -832,7 +832,7 @@ def test_stream_apply_host_resident_state(dtname, maker):
         gates, p = W.qaoa(n, 2, W.random_regular_graph(n, 3, seed=4))
         theta = W.thetas_uniform(p, 2)
     else:
-        gates = [g for g in W.random_gate_mix(n, 80, seed=5) if sum(q >= 11 for q in g.qubits) <= 2]
+        gates = [g for g in W.random_gate_mix(n, 80, seed=5) if sum(q >= 10 for q in g.qubits) <= 2]
     psi0 = W.random_state(n, 6)
     want = ref(n, gates, theta, psi0=psi0)
     cases = [(None, 10, 2), (Q.make_opts(), 10, 2), (Q.make_opts(fuse_k=3), 11, 3)]
