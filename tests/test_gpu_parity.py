@@ -839,10 +839,10 @@ def test_stream_apply_host_resident_state(dtname, maker):
     if dt == Q.QS_C64:
         cases.append((Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2), 11, 2))
     for opts, l, h in cases:
-        host = np.ascontiguousarray(psi0, dtype=Q.NP_DTYPE[dt])
+        host = np.array(psi0, dtype=Q.NP_DTYPE[dt], copy=True)   # streamed in place
         info = Q.qs_stream_apply(host, n, dt, gates, theta, opts, batch_qubits=l, pass_qubits=h)
         assert info["passes"] == len(Q.qs_stream_plan(n, gates, l, h)) >= 2
         assert np.abs(host - want).max() <= TOL[dt], (opts, l, h)
-    pinned = torch.from_numpy(np.ascontiguousarray(psi0, dtype=Q.NP_DTYPE[dt])).pin_memory()
+    pinned = torch.from_numpy(np.array(psi0, dtype=Q.NP_DTYPE[dt], copy=True)).pin_memory()
     Q.qs_stream_apply(pinned, n, dt, gates, theta, Q.make_opts(), batch_qubits=10, pass_qubits=2)
     assert np.abs(pinned.numpy() - want).max() <= TOL[dt]
