@@ -393,7 +393,7 @@ def main():
     if os.path.exists(prof):
         try:
             tp = json.load(open(prof)).get(tc_kernel if tc_dom else "k_tile", {})
-            if tp.get("kernel_hash") == kernel_hash():
+            if tp.get("kernel_hash") == kernel_hash(tc_kernel if tc_dom else "k_tile"):
                 traffic = tp.get("bytes_per_launch_n30")
         except (ValueError, OSError):
             traffic = None
@@ -804,10 +804,15 @@ def config_hea(Q, torch, np, st, args):
     return c4
 
 
-def kernel_hash() -> str:
+# The sources each kernel is compiled from (its traffic record is void once they change).
+KERNEL_SOURCES = {"k_tc_bulk": ("kernels_tc.cu", "cplx.cuh"), "k_tc_block": ("kernels_tc.cu", "cplx.cuh"),
+                  "k_tile": ("kernels_tile.cu", "cplx.cuh", "dfloat.cuh", "qs_internal.h")}
+
+
+def kernel_hash(kernel: str) -> str:
     import hashlib
     h = hashlib.sha256()
-    for f in ("kernels_tile.cu", "kernels_tc.cu", "cplx.cuh", "qs_internal.h"):
+    for f in KERNEL_SOURCES[kernel]:
         h.update(open(os.path.join(ROOT, "paper_2509_04955_gb300", "csrc", f), "rb").read())
     return h.hexdigest()[:16]
 
