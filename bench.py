@@ -605,7 +605,8 @@ def config_qaoa30(Q, torch, np, st, args):
                         ("tensor", Q.make_opts(mode=T, tc_min_gates=4, fuse_parametric=1))],
                 "c128": [("per_gate", None), ("fused_no_phase", Q.make_opts(mode=F, phase_min_gates=-1)),
                          ("fused", Q.make_opts(mode=F)),
-                         ("fused_m13", Q.make_opts(mode=F, tile_qubits=13, low_qubits=3))]}
+                         ("fused_m13", Q.make_opts(mode=F, tile_qubits=13, low_qubits=3)),
+                         ("fused_fp32_pairs", Q.make_opts(mode=F, tile_qubits=12, low_qubits=4, c128_pairs=1))]}
     ref_e = None
     for dname, dt in (("c128", Q.QS_C128), ("c64", Q.QS_C64)):
         s = Q.qs_state_alloc(n, dt, st)

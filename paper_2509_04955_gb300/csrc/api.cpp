@@ -601,6 +601,7 @@ void emit_phase_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
   std::memset(&d, 0, sizeof(d));
   d.term_off = (int32_t)P.h_pterms.size();
   d.nterms = (int32_t)ts.size();
+  d.df = P.df ? 1 : 0;
   int k = 0;
   auto skip_class = [&](int c) { while (k < (int)ts.size() && cls(ts[k].mask) == c) ++k; };
   skip_class(0);

@@ -18,12 +18,15 @@
 // 64 values of each half of lo in its own shared memory, then streams the
 // chunk with 16-byte loads: D(x) = E[lo] B[lo >> 6] A[lo & 63] (x MIXED).
 // Three complex products per amplitude: HBM-bound for complex64 (FP32),
-// bound by GB300's FP64 pipe for complex128.
+// bound by GB300's FP64 pipe for complex128, unless the plan computes
+// complex128 in FP32 pairs (dfloat.cuh): the amplitudes are then split into
+// pairs as they are loaded and joined as they are stored.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 
 #include "cplx.cuh"
+#include "dfloat.cuh"
 #include "qs_internal.h"
 
 namespace qs {
@@ -39,11 +42,32 @@ template <typename C> __device__ __forceinline__ C conj_if(C z, int flip) {
   return z;
 }
 
+__device__ __forceinline__ float shfl_r(float v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ double shfl_r(double v, int src) { return __shfl_sync(0xffffffffu, v, src); }
+__device__ __forceinline__ dfl shfl_r(dfl v, int src) {
+  return dfl(__shfl_sync(0xffffffffu, v.h, src), __shfl_sync(0xffffffffu, v.l, src));
+}
+__device__ __forceinline__ float shfl_xor_r(float v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ double shfl_xor_r(double v, int m) { return __shfl_xor_sync(0xffffffffu, v, m); }
+__device__ __forceinline__ dfl shfl_xor_r(dfl v, int m) {
+  return dfl(__shfl_xor_sync(0xffffffffu, v.h, m), __shfl_xor_sync(0xffffffffu, v.l, m));
+}
+
 template <typename C> __device__ __forceinline__ C shfl_c(C v, int src) {
-  v.x = __shfl_sync(0xffffffffu, v.x, src);
-  v.y = __shfl_sync(0xffffffffu, v.y, src);
+  v.x = shfl_r(v.x, src);
+  v.y = shfl_r(v.y, src);
   return v;
 }
+
+// amplitude type in HBM; complex128 computed in FP32 pairs keeps complex128 there
+template <typename R> struct PhaseG { using T = typename V2<R>::T; };
+template <> struct PhaseG<dfl> { using T = double2; };
+__device__ __forceinline__ double2 to_calc(double2 a, double) { return a; }
+__device__ __forceinline__ dfc to_calc(double2 a, dfl) { return to_dfc(a); }
+__device__ __forceinline__ double2 to_mem(double2 a) { return a; }
+__device__ __forceinline__ double2 to_mem(dfc a) { return from_dfc(a); }
+
+template <typename R> __device__ __forceinline__ typename V2<R>::T c_one() { return mk<R>(R(1.0), R(0.0)); }
 
 // z_j and mask_j arrays are sized for an even count, which keeps the per-warp
 // tables after them 16-byte aligned
@@ -62,6 +86,7 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase_pass(void* psi0, void* 
                                                               PhasePassDesc d, const double* __restrict__ theta,
                                                               int64_t ntheta) {
   using C = typename V2<R>::T;
+  using G = typename PhaseG<R>::T;
   extern __shared__ __align__(16) unsigned char smem[];
   C* E = reinterpret_cast<C*>(smem);
   C* Z = E + kPhaseChunk;
@@ -72,7 +97,7 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase_pass(void* psi0, void* 
   C* mx = ab + 128;
 
   const int row = blockIdx.y;
-  C* psi = reinterpret_cast<C*>(psis ? psis[row] : psi0);
+  G* psi = reinterpret_cast<G*>(psis ? psis[row] : psi0);
   const DevPhaseTerm* T = terms + d.term_off;
 
   // z_j = exp(i alpha_j): angles in FP64 from theta, rounded to the state's precision
@@ -82,12 +107,12 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase_pass(void* psi0, void* 
     if (t.pidx >= 0) a += t.coef * theta[(int64_t)row * ntheta + t.pidx];
     double s, c;
     sincos(a, &s, &c);
-    Z[j] = mk<R>((R)c, (R)s);
+    Z[j] = mk<R>(R(c), R(s));
     M[j] = t.mask;
   }
   __syncthreads();
   for (int lo = threadIdx.x; lo < kPhaseChunk; lo += kPhaseThreads) {
-    C e = mk<R>(1, 0);
+    C e = c_one<R>();
     for (int j = 0; j < d.nlow; ++j) e = cmul(e, conj_if(Z[j], parity64(M[j] & (uint64_t)lo)));
     E[lo] = e;
   }
@@ -106,18 +131,18 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase_pass(void* psi0, void* 
        ch += (uint64_t)gridDim.x * kPhaseWarps) {
     const uint64_t base = ch << kPhaseChunkBits;
     // C = product of the HIGH terms (spread over the lanes, then a butterfly product)
-    C cst = mk<R>(1, 0);
+    C cst = c_one<R>();
     for (int j = d.high_begin + lane; j < d.mixed_begin; j += 32)
       cst = cmul(cst, conj_if(Z[j], parity64(M[j] & base)));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
       C other;
-      other.x = __shfl_xor_sync(0xffffffffu, cst.x, o);
-      other.y = __shfl_xor_sync(0xffffffffu, cst.y, o);
+      other.x = shfl_xor_r(cst.x, o);
+      other.y = shfl_xor_r(cst.y, o);
       cst = cmul(cst, other);
     }
     // lane u < 12: w_u = product of its LIN terms with their hi signs
-    C wv = mk<R>(1, 0);
+    C wv = c_one<R>();
     for (int j = u_lo; j < u_hi; ++j) wv = cmul(wv, conj_if(Z[j], parity64(M[j] & base)));
     C w[kPhaseChunkBits];
 #pragma unroll
@@ -125,7 +150,7 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase_pass(void* psi0, void* 
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int e = lane + 32 * h;
-      C a = cst, b = mk<R>(1, 0);
+      C a = cst, b = c_one<R>();
 #pragma unroll
       for (int u = 0; u < 6; ++u) {
         a = cmul(a, conj_if(w[u], (e >> u) & 1));
@@ -170,11 +195,11 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase_pass(void* psi0, void* 
       }
     } else {
       // lane l holds amplitude l + 32 i: lo & 63 = l + 32 (i & 1), lo >> 6 = i >> 1
-      C* p = psi + base;
+      G* p = psi + base;
       const C a0 = ab[lane], a1 = ab[lane + 32];
 #pragma unroll 1
       for (int i0 = 0; i0 < 128; i0 += 4) {
-        C v[4];
+        G v[4];
 #pragma unroll
         for (int k = 0; k < 4; ++k) v[k] = p[lane + 32 * (i0 + k)];
 #pragma unroll
@@ -185,7 +210,7 @@ __global__ void __launch_bounds__(kPhaseThreads) k_phase_pass(void* psi0, void* 
             const uint64_t lo = (uint64_t)(lane + 32 * i);
             for (int j = 0; j < nmixed; ++j) f = cmul(f, conj_if(mx[j], parity64(M[d.mixed_begin + j] & lo)));
           }
-          v[k] = cmul(v[k], f);
+          v[k] = to_mem(cmul(to_calc(v[k], R()), f));
         }
 #pragma unroll
         for (int k = 0; k < 4; ++k) p[lane + 32 * (i0 + k)] = v[k];
@@ -210,7 +235,8 @@ static int phase_sm_count() {
 cudaError_t prepare_phase_pass(PhasePassDesc& d, qs_dtype dt) {
   if (d.nterms > kPhaseMaxTerms || d.nterms - d.mixed_begin > kPhaseMaxMixed) return cudaErrorInvalidValue;
   const size_t smem = phase_smem_bytes(d.nterms, dt);
-  const void* fn = dt == QS_C64 ? (const void*)k_phase_pass<float> : (const void*)k_phase_pass<double>;
+  const void* fn = dt == QS_C64 ? (const void*)k_phase_pass<float>
+                   : d.df ? (const void*)k_phase_pass<dfl> : (const void*)k_phase_pass<double>;
   cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)phase_smem_bytes(kPhaseMaxTerms, dt));
   if (e != cudaSuccess) return e;
@@ -235,6 +261,8 @@ cudaError_t launch_phase_pass(void* psi, void* const* psis, int nstates, int n, 
   const size_t smem = phase_smem_bytes(d.nterms, dt);
   if (dt == QS_C64)
     k_phase_pass<float><<<dim3(gx, nstates), kPhaseThreads, smem, st>>>(psi, psis, n, terms, d, theta, ntheta);
+  else if (d.df)
+    k_phase_pass<dfl><<<dim3(gx, nstates), kPhaseThreads, smem, st>>>(psi, psis, n, terms, d, theta, ntheta);
   else
     k_phase_pass<double><<<dim3(gx, nstates), kPhaseThreads, smem, st>>>(psi, psis, n, terms, d, theta, ntheta);
   note_launch();

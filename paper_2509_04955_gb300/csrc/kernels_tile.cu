@@ -109,16 +109,21 @@ __device__ __forceinline__ uint32_t ins0k(uint32_t x, const int32_t* pos) {
 // end recomputes the iteration's first pair and does not store.
 constexpr int kPairBatch = 4;
 
-template <typename C, typename F>
-__device__ __forceinline__ void pairs_apply(C* tile, uint32_t count, const int32_t* ins, int nins, uint32_t cmask,
-                                            uint32_t ta, F f) {
+// ONE: the op inserts a single zero bit (an uncontrolled one-target gate), so
+// the pair index is ((p & ~lo) << 1) | (p & lo) with lo the bits below it.
+template <bool ONE, typename C, typename F>
+__device__ __forceinline__ void pairs_apply_t(C* tile, uint32_t count, const int32_t* ins, int nins, uint32_t cmask,
+                                              uint32_t ta, F f) {
+  const uint32_t lo = (1u << ins[0]) - 1;
   for (uint32_t p0 = threadIdx.x; p0 < count; p0 += kTileThreads * kPairBatch) {
     uint32_t idx[kPairBatch];
     C a0[kPairBatch], a1[kPairBatch];
 #pragma unroll
     for (int u = 0; u < kPairBatch; ++u) {
       const uint32_t p = p0 + (uint32_t)u * kTileThreads;
-      idx[u] = ins0(p < count ? p : p0, ins, nins) | cmask;
+      const uint32_t q = p < count ? p : p0;
+      if constexpr (ONE) idx[u] = ((q & ~lo) << 1) | (q & lo);
+      else idx[u] = ins0(q, ins, nins) | cmask;
       a0[u] = tile[idx[u]];
       a1[u] = tile[idx[u] | ta];
     }
@@ -131,6 +136,13 @@ __device__ __forceinline__ void pairs_apply(C* tile, uint32_t count, const int32
         tile[idx[u] | ta] = a1[u];
       }
   }
+}
+
+template <typename C, typename F>
+__device__ __forceinline__ void pairs_apply(C* tile, uint32_t count, const int32_t* ins, int nins, uint32_t cmask,
+                                            uint32_t ta, F f) {
+  if (nins == 1 && cmask == 0) pairs_apply_t<true>(tile, count, ins, nins, cmask, ta, f);
+  else pairs_apply_t<false>(tile, count, ins, nins, cmask, ta, f);
 }
 
 template <typename R>

@@ -111,6 +111,7 @@ struct PhasePassDesc {
   int32_t lin_off[kPhaseChunkBits + 1];
   int32_t high_begin, mixed_begin;
   int32_t occ;             // resident CTAs per SM, set by prepare_phase_pass
+  int32_t df;              // complex128 computed in FP32 pairs
 };
 size_t phase_smem_bytes(int nterms, qs_dtype dt);
 cudaError_t prepare_phase_pass(PhasePassDesc& d, qs_dtype dt);

@@ -702,6 +702,8 @@ def test_phase_pass_matches_oracle(dtname, maker, n):
     modes = [Q.make_opts(), Q.make_opts(fuse_k=2, phase_min_gates=4)]
     if dt == Q.QS_C64 and n >= 13:
         modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
+    if dt == Q.QS_C128:   # phase and tile passes in FP32 pairs
+        modes.append(Q.make_opts(c128_pairs=1))
     for opts in modes:
         plan = Q.qs_plan_create(n, dt, gates, opts)
         try:
