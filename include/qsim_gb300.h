@@ -200,6 +200,20 @@ qs_status qs_plan_free(qs_plan_t p);
  * ntheta parameters (may be NULL when the circuit has none). */
 qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta);
 
+/* Runs the plan on `count` independent states held in host memory (page-locked
+ * for overlap): host_in[i] (2^n amplitudes, read) -> host_out[i] (written; the
+ * pointer arrays may repeat a buffer, and host_out may be NULL to keep only
+ * the norms), norms[i] = ||psi_i||^2 after the circuit (may be NULL). The
+ * states pass through the nwork >= 1 device states in `work` (same n and
+ * dtype as the plan) round robin: the copy of input i+1 into one work state
+ * and the copy of result i-1 out of another run on their own streams while
+ * input i is computed, so with nwork >= 2 the host link is hidden behind the
+ * circuit. theta as for qs_plan_execute, shared by all inputs. Blocks until
+ * every result is in host memory. */
+qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const void* const* host_in,
+                               void* const* host_out, int count, const double* theta, size_t ntheta,
+                               double* norms);
+
 /* Autotuner (no counterpart in the paper): plans the circuit under a built-in
  * grid of options (per-gate; CUDA-core contraction width 1..4 with two tile
  * shapes; for complex64 with n >= 13, tensor-core plans with three block

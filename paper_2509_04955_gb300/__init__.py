@@ -105,6 +105,8 @@ _SIGS = {
     "qs_plan_op_count": (C.c_int, [_VP, _I64P, _I64P]),
     "qs_plan_op_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I32P, _I32P, _DP]),
     "qs_plan_pass_get": (C.c_int, [_VP, C.c_int64, _I32P, _I32P, _I64P, _I64P]),
+    "qs_plan_execute_host": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, C.POINTER(_VP), C.POINTER(_VP), C.c_int, _DP,
+                                       C.c_size_t, _DP]),
     "qs_stream_apply": (C.c_int, [_VP, C.c_int, C.c_int, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t,
                                   C.POINTER(QsPlanOpts), C.c_int, C.c_int, C.POINTER(QsStreamInfo)]),
     "qs_stream_plan": (C.c_int, [C.c_int, C.POINTER(QsGate), C.c_size_t, C.c_int, C.c_int, _I64P,
@@ -296,11 +298,11 @@ def qs_apply_circuit(state: int, gates, theta=None, opts: QsPlanOpts | None = No
 
 
 def _host_ptr(a) -> int:
-    """Address of a host buffer: a numpy array or a (pinned) CPU torch tensor."""
+    """Address of a host buffer: a contiguous numpy array or a (pinned) CPU torch tensor."""
     if hasattr(a, "data_ptr"):
         assert not a.is_cuda and a.is_contiguous()
         return a.data_ptr()
-    assert a.flags["C_CONTIGUOUS"] and a.flags["WRITEABLE"]
+    assert a.flags["C_CONTIGUOUS"]
     return a.ctypes.data
 
 
@@ -315,6 +317,25 @@ def qs_stream_apply(host_psi, n: int, dtype: int, gates, theta=None, opts: QsPla
                                  C.byref(opts) if opts is not None else None, batch_qubits, pass_qubits,
                                  C.byref(info)))
     return info.as_dict()
+
+
+def qs_plan_execute_host(plan: int, work: list[int], host_in: list, host_out: list | None = None, theta=None,
+                         want_norms: bool = True):
+    """Runs the plan on len(host_in) host-resident states through the device states
+    `work`, overlapping the copies with the circuit (qs_plan_execute_host); returns
+    the norms (or None)."""
+    th, nt = _dptr(theta)
+    cnt = len(host_in)
+    w = (_VP * len(work))(*work)
+    hin = (_VP * max(1, cnt))(*[_host_ptr(a) for a in host_in])
+    hout = None
+    if host_out is not None:
+        hout = (_VP * max(1, cnt))(*[_host_ptr(a) if a is not None else None for a in host_out])
+    norms = np.zeros(max(1, cnt)) if want_norms else None
+    _check(lib().qs_plan_execute_host(plan, w, len(work), hin, hout, cnt,
+                                      th.ctypes.data_as(_DP) if th is not None else None, nt,
+                                      norms.ctypes.data_as(_DP) if norms is not None else None))
+    return norms[:cnt] if want_norms else None
 
 
 def qs_stream_plan(n: int, gates, batch_qubits: int, pass_qubits: int) -> list[tuple[int, list[int]]]:

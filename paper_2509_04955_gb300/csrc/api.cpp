@@ -1506,6 +1506,82 @@ qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t
   });
 }
 
+qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const void* const* host_in,
+                               void* const* host_out, int count, const double* theta, size_t ntheta,
+                               double* norms) {
+  return guard([&] {
+    require(p != nullptr && work != nullptr && nwork >= 1 && count >= 0, "bad arguments");
+    require(count == 0 || host_in != nullptr, "host_in is NULL");
+    for (int b = 0; b < nwork; ++b) {
+      check_state(work[b]);
+      require(work[b]->n == p->n && work[b]->dt == p->dt, "work state and plan differ in qubit count or dtype");
+      for (int c = 0; c < b; ++c) require(work[c] != work[b], "work states must be distinct");
+    }
+    for (int i = 0; i < count; ++i) require(host_in[i] != nullptr, "host_in has a NULL entry");
+    const size_t bytes = amp_bytes(p->dt) << p->n;
+    upload(*p);
+    cudaStream_t si = nullptr, sc = nullptr, so = nullptr;
+    std::vector<cudaEvent_t> loaded(nwork, nullptr), computed(nwork, nullptr), stored(nwork, nullptr);
+    auto cleanup = [&]() {
+      for (int b = 0; b < nwork; ++b) {
+        if (loaded[b]) cudaEventDestroy(loaded[b]);
+        if (computed[b]) cudaEventDestroy(computed[b]);
+        if (stored[b]) cudaEventDestroy(stored[b]);
+      }
+      if (si) cudaStreamDestroy(si);
+      if (sc) cudaStreamDestroy(sc);
+      if (so) cudaStreamDestroy(so);
+    };
+    try {
+      CK(cudaStreamCreateWithFlags(&si, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithFlags(&sc, cudaStreamNonBlocking));
+      CK(cudaStreamCreateWithFlags(&so, cudaStreamNonBlocking));
+      for (int b = 0; b < nwork; ++b) {
+        CK(cudaEventCreateWithFlags(&loaded[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&computed[b], cudaEventDisableTiming));
+        CK(cudaEventCreateWithFlags(&stored[b], cudaEventDisableTiming));
+        // earlier work queued on the work states' own streams comes first
+        CK(cudaEventRecord(stored[b], work[b]->st));
+        work[b]->scratch.ensure(partial_bytes(1) + sizeof(double));
+      }
+      resolve_theta(*p, theta, ntheta, 1, sc);
+      build_device_blocks(*p, 1, sc);
+      for (int i = 0; i < count; ++i) {
+        const int b = i % nwork;
+        qs_state_s& w = *work[b];
+        CK(cudaStreamWaitEvent(si, stored[b], 0));
+        CK(cudaMemcpyAsync(w.d, host_in[i], bytes, cudaMemcpyHostToDevice, si));
+        CK(cudaEventRecord(loaded[b], si));
+        CK(cudaStreamWaitEvent(sc, loaded[b], 0));
+        issue_circuit(*p, w.d, 0, sc);
+        double* d_part = w.scratch.as<double>();
+        if (norms) CK(launch_norm(w.d, w.n, w.dt, d_part, d_part + reduce_blocks(), sc));
+        CK(cudaEventRecord(computed[b], sc));
+        CK(cudaStreamWaitEvent(so, computed[b], 0));
+        if (host_out && host_out[i]) CK(cudaMemcpyAsync(host_out[i], w.d, bytes, cudaMemcpyDeviceToHost, so));
+        if (norms) CK(cudaMemcpyAsync(&norms[i], d_part + reduce_blocks(), sizeof(double), cudaMemcpyDeviceToHost, so));
+        CK(cudaEventRecord(stored[b], so));
+      }
+      CK(cudaStreamSynchronize(so));
+      CK(cudaStreamSynchronize(sc));
+      CK(cudaStreamSynchronize(si));
+      for (int b = 0; b < nwork; ++b) CK(cudaStreamWaitEvent(work[b]->st, stored[b], 0));
+      if (!p->tcdesc.empty()) {
+        int err = 0;
+        CK(cudaMemcpy(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
+        if (err) throw Error(QS_ERR_TIMEOUT, "tensor-core pass: an MMA completion wait timed out");
+      }
+    } catch (...) {
+      if (si) cudaStreamSynchronize(si);
+      if (sc) cudaStreamSynchronize(sc);
+      if (so) cudaStreamSynchronize(so);
+      cleanup();
+      throw;
+    }
+    cleanup();
+  });
+}
+
 qs_status qs_apply_circuit(qs_state_t s, const qs_gate* gates, size_t ngates, const double* theta, size_t ntheta,
                            const qs_plan_opts* opts) {
   return guard([&] {

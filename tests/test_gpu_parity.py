@@ -848,3 +848,35 @@ def test_stream_apply_host_resident_state(dtname, maker):
     pinned = torch.from_numpy(np.array(psi0, dtype=Q.NP_DTYPE[dt], copy=True)).pin_memory()
     Q.qs_stream_apply(pinned, n, dt, gates, theta, Q.make_opts(), batch_qubits=10, pass_qubits=2)
     assert np.abs(pinned.numpy() - want).max() <= TOL[dt]
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+@pytest.mark.parametrize("nwork", [1, 2, 3])
+def test_execute_host_pipeline_matches_oracle(dtname, nwork):
+    """qs_plan_execute_host: five different host-resident input states through
+    1-3 device work states (copies in and out overlapped with the circuit);
+    every output and its norm against the oracle, including a parametric
+    circuit resolved once for all inputs and a host_out of NULL (norms only)."""
+    import torch
+    dt = DT[dtname]
+    n = 14
+    gates, p = W.hea_staggered(n, 2)
+    theta = W.thetas_uniform(p, 4)
+    ins = [np.array(W.random_state(n, 40 + i), dtype=Q.NP_DTYPE[dt]) for i in range(5)]
+    outs = [torch.empty(1 << n, dtype=torch.complex128 if dt == Q.QS_C128 else torch.complex64).pin_memory()
+            for _ in range(5)]
+    opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2, fuse_parametric=1) if dt == Q.QS_C64 else Q.make_opts()
+    plan = Q.qs_plan_create(n, dt, gates, opts)
+    work = [Q.qs_state_alloc(n, dt) for _ in range(nwork)]
+    try:
+        norms = Q.qs_plan_execute_host(plan, work, ins, outs, theta)
+        for i in range(5):
+            want = ref(n, gates, theta, psi0=ins[i].astype(np.complex128))
+            assert np.abs(outs[i].numpy() - want).max() <= TOL[dt]
+            assert abs(norms[i] - 1) <= 10 * TOL[dt]
+        norms2 = Q.qs_plan_execute_host(plan, work, ins[:2], None, theta)
+        assert np.abs(norms2 - norms[:2]).max() <= 1e-12
+    finally:
+        for w in work:
+            Q.qs_state_free(w)
+        Q.qs_plan_free(plan)
