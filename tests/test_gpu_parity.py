@@ -880,3 +880,29 @@ def test_execute_host_pipeline_matches_oracle(dtname, nwork):
         for w in work:
             Q.qs_state_free(w)
         Q.qs_plan_free(plan)
+
+
+def test_stream_and_pipeline_edge_cases():
+    """Streaming with every batch alone (pass_qubits 0: only gates below the batch
+    qubits), with one batch holding the whole state (batch_qubits = n), and the
+    host pipeline with no inputs."""
+    n = 13
+    dt = Q.QS_C128
+    psi0 = W.random_state(n, 12)
+    low_gates = [g for g in W.random_layered(n, 4, seed=6) if max(g.qubits) < 9]
+    host = np.array(psi0, copy=True)
+    info = Q.qs_stream_apply(host, n, dt, low_gates, None, Q.make_opts(), batch_qubits=9, pass_qubits=0)
+    assert info["passes"] == 1 and info["groups"] == 16
+    assert np.abs(host - ref(n, low_gates, psi0=psi0)).max() <= TOL[dt]
+    gates = W.random_layered(n, 4, seed=7)
+    host = np.array(psi0, copy=True)
+    info = Q.qs_stream_apply(host, n, dt, gates, None, None, batch_qubits=n, pass_qubits=0)
+    assert info["passes"] == 1 and info["groups"] == 1
+    assert np.abs(host - ref(n, gates, psi0=psi0)).max() <= TOL[dt]
+    plan = Q.qs_plan_create(n, dt, gates, Q.make_opts())
+    w = Q.qs_state_alloc(n, dt)
+    try:
+        assert len(Q.qs_plan_execute_host(plan, [w], [], [])) == 0
+    finally:
+        Q.qs_state_free(w)
+        Q.qs_plan_free(plan)

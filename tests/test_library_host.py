@@ -268,6 +268,9 @@ def test_stream_passes_reorder_only_commuting_gates(l, h):
     with pytest.raises(Q.QsError):
         Q.qs_stream_plan(n, [W.Gate("x", (10,), (8, 9))], 8, 2)
     assert len(Q.qs_stream_plan(n, gates, l, n - l)) == 1
+    assert len(Q.qs_stream_plan(n, gates, n, 0)) == 1          # one batch: the whole state
+    with pytest.raises(Q.QsError):
+        Q.qs_stream_plan(n, gates, 0, 2)                       # batches of at least one qubit
 
 
 def test_per_gate_sweep_accounting():
