@@ -48,6 +48,7 @@ def parse():
                     help="also run the complex128 n=32 reference for the tensor-core config (64 GiB, ~1 min)")
     ap.add_argument("--qaoa-n", type=int, default=30, help="register size of the qaoa_n30 configuration")
     ap.add_argument("--stream-n", type=int, default=31, help="register size of the host-resident configuration")
+    ap.add_argument("--smgp-ns", default="20,24,28,30", help="register sizes of the SMGP ablation (comma list)")
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
     ap.add_argument("--only-config", default=None,
                     choices=["qft_n30_m2", "qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20",
@@ -558,7 +559,7 @@ def config_smgp(Q, torch, np, st, args):
     out = {"note": "throughput = sweeps x 2 x 2^n x amplitude bytes / time, the bytes each variant moves"}
     for circ in ("qaoa", "hea"):
         res = {}
-        for n in (20, 24, 28, 30):
+        for n in (int(x) for x in args.smgp_ns.split(",")):
             if circ == "qaoa":
                 g, npar = W.qaoa(n, 4, W.random_regular_graph(n, 3, seed=0))
             else:
