@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <functional>
 #include <map>
 #include <memory>
 #include <mutex>
@@ -352,21 +353,45 @@ void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed
 
 // One launch per pass for all B states (fused / tensor plans): the kernels
 // take the device array of state pointers and gate-table rows 16 G apart.
-void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_t st) {
+// States per wave of the batched schedule: when at least two states fit in
+// about half of the L2 (64 MiB), every pass runs on one wave before the next
+// wave starts, so after the first pass a wave's states are read from L2
+// rather than HBM; otherwise (or with reserved[4] = 1) each pass covers the
+// whole batch.
+int batched_wave(const qs_plan_s& p, int B) {
+  if (p.opts.reserved[4] == 1) return B;
+  const int w = expval_wave_states(p.n, p.dt, B);
+  return w >= 2 ? w : B;
+}
+
+// after_wave(w0, nb) runs once per wave, after its passes (the expectation values,
+// while the wave is still in L2).
+void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_t st,
+                           const std::function<void(int, int)>& after_wave = nullptr) {
   const size_t G = std::max<size_t>(1, p.gates.size());
   if (p.gtab_rows < B || (!p.h_dblocks.empty() && (p.btab_rows < B || (!p.tcdesc.empty() && p.wimg_rows < B))))
     throw Error(QS_ERR_CUDA, "internal: tables have fewer rows than the batch");
-  for (const auto& stp : p.steps) {
-    if (stp.kind == 2)
-      CK(launch_phase_pass(nullptr, d_psis, B, p.n, p.dt, p.d_pterms.as<DevPhaseTerm>(), p.phdesc[stp.idx],
-                           p.theta_needed ? p.d_theta.as<double>() : nullptr, p.theta_stride, st));
-    else if (stp.kind == 0)
-      CK(launch_tile_pass_batched(nullptr, d_psis, B, (int64_t)(16 * G), p.btab_elems, p.n, p.dt, p.pdesc[stp.idx],
-                                  p.d_ops.as<DevOp>(), p.d_gtab.as<double2>(), p.d_btab.as<double2>(), st));
-    else
-      CK(launch_tc_pass_batched(nullptr, d_psis, B, p.tc_param[stp.idx] ? (int64_t)p.h_wimg.size() : 0, p.n,
-                                p.tcdesc[stp.idx], p.d_wimg.as<uint16_t>() + (size_t)stp.idx * 32768, p.tc_prec,
-                                p.tc_pipe, p.d_err.as<int>(), st));
+  const int wave = batched_wave(p, B);
+  for (int w0 = 0; w0 < B; w0 += wave) {
+    const int nb = std::min(wave, B - w0);
+    void* const* ps = d_psis + w0;
+    for (const auto& stp : p.steps) {
+      if (stp.kind == 2) {
+        CK(launch_phase_pass(nullptr, ps, nb, p.n, p.dt, p.d_pterms.as<DevPhaseTerm>(), p.phdesc[stp.idx],
+                             p.theta_needed ? p.d_theta.as<double>() + (size_t)w0 * p.theta_stride : nullptr,
+                             p.theta_stride, st));
+      } else if (stp.kind == 0) {
+        CK(launch_tile_pass_batched(nullptr, ps, nb, (int64_t)(16 * G), p.btab_elems, w0, p.n, p.dt, p.pdesc[stp.idx],
+                                    p.d_ops.as<DevOp>(), p.d_gtab.as<double2>() + (size_t)w0 * 16 * G,
+                                    p.d_btab.as<double2>(), st));
+      } else {
+        const int64_t wstride = p.tc_param[stp.idx] ? (int64_t)p.h_wimg.size() : 0;
+        CK(launch_tc_pass_batched(nullptr, ps, nb, wstride, p.n, p.tcdesc[stp.idx],
+                                  p.d_wimg.as<uint16_t>() + (size_t)stp.idx * 32768 + (size_t)w0 * wstride, p.tc_prec,
+                                  p.tc_pipe, p.d_err.as<int>(), st));
+      }
+    }
+    if (after_wave) after_wave(w0, nb);
   }
 }
 
@@ -1952,7 +1977,10 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
       NL = (int)P.launches.size();
       qs_state_s& s0 = *states[0];
       const int cols = one_launch ? expval_wave_ctas(expval_wave_states(p->n, p->dt, B)) : reduce_blocks();
-      const size_t part = one_launch ? sizeof(double) * (size_t)cols * (size_t)Z * B
+      // one launch per wave reuses the partials from offset 0 (each launch reduces
+      // its own before the next starts): wave x Z x C(wave) <= Z x reduce_blocks()
+      const size_t part = one_launch ? sizeof(double) * (size_t)Z *
+                                           std::max<size_t>((size_t)cols * B, (size_t)reduce_blocks())
                                      : sizeof(double) * (size_t)cols * kZPerLaunch;
       s0.scratch.ensure(part + sizeof(double) * P.zlist.size() * B);
       gtab_host.resize(sizeof(uint64_t) * (Z + NL) + sizeof(int32_t) * 3 * NL);
@@ -2013,14 +2041,18 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
         }
         build_device_blocks(*p, B, st);
         if (one_launch) {
-          issue_circuit_batched(*p, d_psis, B, st);
-          if (terms && nterms) {
-            const uint64_t* d_z = states[0]->scratch2.as<uint64_t>();
-            const uint64_t* d_gx = d_z + Z;
-            const int32_t* d_gz = (const int32_t*)(d_gx + NL);
-            CK(launch_expval_groups_batched((const void* const*)d_psis, B, p->n, p->dt, d_gx, d_gz, d_gz + NL,
-                                            d_gz + 2 * NL, NL1, NL, d_z, (int)Z, d_part, d_out, st));
-          }
+          // expectation values of each wave right after its passes (the wave is in L2);
+          // the partials are reused from offset 0 by every launch
+          std::function<void(int, int)> ev;
+          if (terms && nterms)
+            ev = [&](int w0, int nb) {
+              const uint64_t* d_z = states[0]->scratch2.as<uint64_t>();
+              const uint64_t* d_gx = d_z + Z;
+              const int32_t* d_gz = (const int32_t*)(d_gx + NL);
+              CK(launch_expval_groups_batched((const void* const*)(d_psis + w0), nb, p->n, p->dt, d_gx, d_gz, d_gz + NL,
+                                              d_gz + 2 * NL, NL1, NL, d_z, (int)Z, d_part, d_out + (size_t)w0 * Z, st));
+            };
+          issue_circuit_batched(*p, d_psis, B, st, ev);
         } else {
           for (int b = 0; b < B; ++b) {
             issue_circuit(*p, states[b]->d, b, st);

@@ -310,7 +310,7 @@ __global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typena
                                                         void* const* __restrict__ psis, int64_t gstride,
                                                         int64_t bstride, PassDesc p, const DevOp* __restrict__ ops,
                                                         const double2* __restrict__ gtab0,
-                                                        const double2* __restrict__ btab, int lg_tiles,
+                                                        const double2* __restrict__ btab, int64_t brow0, int lg_tiles,
                                                         uint64_t total) {
   using C = typename V2<R>::T;
   using G = typename GAmp<R>::T;
@@ -345,7 +345,7 @@ __global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typena
       if (op.type == OP_GATE) {
         apply_gate_op<R>(tile, m, op, gtab, mbuf);
       } else {
-        const double2* __restrict__ bt = op.per_row ? btab + sb * bstride : btab;
+        const double2* __restrict__ bt = op.per_row ? btab + (brow0 + (int64_t)sb) * bstride : btab;
         if (op.type == OP_DIAG) {
           apply_diag_op<R>(tile, m, op, bt, mbuf);
         } else {
@@ -405,8 +405,8 @@ static int sm_count() {
 }
 
 template <typename R, int KMAX>
-static cudaError_t launch_tile_t(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride, int n,
-                                 const PassDesc& p, const DevOp* ops, const double2* gtab,
+static cudaError_t launch_tile_t(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
+                                 int64_t brow0, int n, const PassDesc& p, const DevOp* ops, const double2* gtab,
                                  const double2* btab, cudaStream_t st, size_t smem) {
   if ((int)smem > TileCfg<R, KMAX>::bytes) return cudaErrorInvalidConfiguration;   // not prepared
   const int per_sm = TileCfg<R, KMAX>::per_sm;
@@ -415,16 +415,16 @@ static cudaError_t launch_tile_t(void* psi, void* const* psis, int nstates, int6
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > total) grid = total;
   k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename GAmp<R>::T*)psi, psis, gstride, bstride, p,
-                                                                ops, gtab, btab, n - p.m, total);
+                                                                ops, gtab, btab, brow0, n - p.m, total);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
-                                     int n, qs_dtype dt, const PassDesc& p, const DevOp* ops, const double2* gtab,
-                                     const double2* btab, cudaStream_t st) {
+                                     int64_t brow0, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
+                                     const double2* gtab, const double2* btab, cudaStream_t st) {
   const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.mbuf_elems, dt);
-#define QS_TILE_ARGS psi, psis, nstates, gstride, bstride, n, p, ops, gtab, btab, st, smem
+#define QS_TILE_ARGS psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem
   if (dt == QS_C64) {
     switch (p.kmax) {
       case 0: case 1: case 2: return launch_tile_t<float, 2>(QS_TILE_ARGS);
@@ -485,7 +485,7 @@ cudaError_t prepare_tile_pass(const PassDesc& p, qs_dtype dt) {
 
 cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
                              const double2* gtab, const double2* btab, int /*threads*/, cudaStream_t st) {
-  return launch_tile_pass_batched(psi, nullptr, 1, 0, 0, n, dt, p, ops, gtab, btab, st);
+  return launch_tile_pass_batched(psi, nullptr, 1, 0, 0, 0, n, dt, p, ops, gtab, btab, st);
 }
 
 // ---------------------------------------------------------------- adjoint gradient, tiled reverse sweep

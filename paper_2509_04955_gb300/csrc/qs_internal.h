@@ -208,10 +208,12 @@ struct SmgpDesc {
 cudaError_t launch_smgp_step(void* psi, int n, qs_dtype dt, const SmgpDesc* d_desc, const SmgpDesc& h_desc, int T,
                              const double2* gtab, cudaStream_t st);
 // Batched forms: psis = device array of nstates state pointers (psi unused);
-// gate table rows gstride apart.
+// gate table rows gstride apart (gtab points at the first state's row);
+// blocks rebuilt per row are read from block-table row brow0 + state, bstride
+// apart (fixed blocks from row 0).
 cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
-                                     int n, qs_dtype dt, const PassDesc& p, const DevOp* ops, const double2* gtab,
-                                     const double2* btab, cudaStream_t st);
+                                     int64_t brow0, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
+                                     const double2* gtab, const double2* btab, cudaStream_t st);
 // wstride (uint16 elements) between the W images of consecutive states; 0 = one image for all
 cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
                                    const TcPassDesc& p, const void* wimg, int prec, int pipeline, int* err,

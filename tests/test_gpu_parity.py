@@ -906,3 +906,46 @@ def test_stream_and_pipeline_edge_cases():
     finally:
         Q.qs_state_free(w)
         Q.qs_plan_free(plan)
+
+
+@pytest.mark.parametrize("dtname", ["c64", "c128"])
+def test_batched_l2_waves_ragged(dtname):
+    """Batched execution in L2-sized waves (two 32 MiB states per wave, the last
+    wave holding one): every row's state and <H> equal the pass-major schedule
+    and the oracle, for CUDA-core plans with parametric blocks rebuilt per row
+    and (complex64) tensor-core plans with per-row W images."""
+    dt = DT[dtname]
+    n = 22 if dt == Q.QS_C64 else 21
+    Bsz = 5
+    gates, _ = W.ucc(n, 10, seed=3, wmin=2, wmax=5)
+    th = W.thetas_normal(10, 4, sigma=0.3, batch=Bsz)
+    H = W.random_pauli_sum(n, 12, seed=5)
+    modes = [Q.make_opts(fuse_k=4, fuse_parametric=1)]
+    if dt == Q.QS_C64:
+        modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
+    want2 = O.apply_circuit(O.basis(n, 0), n, gates, th[2])
+    want_e = [O.expval(O.apply_circuit(O.basis(n, 0), n, gates, th[b]), n, *H).real for b in range(Bsz)]
+    for base in modes:
+        results = []
+        for pass_major in (0, 1):
+            o = Q.make_opts(mode=base.mode, fuse_k=base.fuse_k, fuse_parametric=1, tc_min_gates=base.reserved[0],
+                            batch_pass_major=pass_major)
+            plan = Q.qs_plan_create(n, dt, gates, o)
+            states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
+            try:
+                for s in states:
+                    Q.qs_state_set_basis(s, 0)
+                ex = Q.qs_plan_execute_batched(plan, states, th, H)
+                out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+                Q.qs_state_copy_to_host(states[2], out)
+                results.append((ex, out))
+            finally:
+                for s in states:
+                    Q.qs_state_free(s)
+                Q.qs_plan_free(plan)
+        (ex0, out0), (ex1, out1) = results
+        assert np.abs(out0 - want2).max() <= TOL[dt]
+        assert np.abs(out0 - out1).max() <= TOL[dt]
+        for b in range(Bsz):
+            assert abs(ex0[b] - want_e[b]) <= TOL[dt] * np.abs(H[0]).sum() * 10
+            assert abs(ex0[b] - ex1[b]) <= TOL[dt] * np.abs(H[0]).sum() * 10
