@@ -129,10 +129,10 @@ typedef struct {
                             state stays complex128 in memory, split into pairs when a tile is
                             loaded and joined when it is stored. GB300's FP32 rate is about 64x
                             its FP64 rate.
-                            reserved[4]: qs_plan_execute_batched schedule: 0 = when at least two
-                            states fit in 64 MiB (about half the L2), every pass runs on one wave
-                            of such states before the next wave (passes then read L2, not HBM),
-                            1 = every pass covers the whole batch. */
+                            reserved[4]: qs_plan_execute_batched schedule: 0 = every pass covers
+                            the whole batch (default), 1 = when at least two states fit in 64 MiB
+                            (about half the L2), every pass runs on one wave of such states
+                            before the next wave (passes then read L2, not HBM; more launches). */
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */

@@ -192,8 +192,8 @@ def _dptr(a):
 
 def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0,
               fuse_parametric=0, tc_min_gates=0, tc_pipeline=0, phase_min_gates=0, c128_pairs=0,
-              batch_pass_major=0):
-    """qs_plan_opts; tc_min_gates, tc_pipeline, phase_min_gates, c128_pairs and batch_pass_major fill
+              batch_l2_waves=0):
+    """qs_plan_opts; tc_min_gates, tc_pipeline, phase_min_gates, c128_pairs and batch_l2_waves fill
     reserved[0..4]."""
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
@@ -202,7 +202,7 @@ def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_m
     o.reserved[1] = tc_pipeline
     o.reserved[2] = phase_min_gates
     o.reserved[3] = c128_pairs
-    o.reserved[4] = batch_pass_major
+    o.reserved[4] = batch_l2_waves
     return o
 
 

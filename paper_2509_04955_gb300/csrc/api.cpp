@@ -353,13 +353,14 @@ void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed
 
 // One launch per pass for all B states (fused / tensor plans): the kernels
 // take the device array of state pointers and gate-table rows 16 G apart.
-// States per wave of the batched schedule: when at least two states fit in
-// about half of the L2 (64 MiB), every pass runs on one wave before the next
-// wave starts, so after the first pass a wave's states are read from L2
-// rather than HBM; otherwise (or with reserved[4] = 1) each pass covers the
-// whole batch.
+// States per wave of the batched schedule. Default: each pass covers the whole
+// batch (one launch per pass). With reserved[4] = 1, when at least two states
+// fit in about half of the L2 (64 MiB), every pass runs on one wave before the
+// next wave starts, so after the first pass a wave's states come from L2; on
+// GB300 the extra launches cost more than that saves (UCC n = 20, B = 64:
+// 131 ms per batch in 8 waves against 106 ms pass by pass).
 int batched_wave(const qs_plan_s& p, int B) {
-  if (p.opts.reserved[4] == 1) return B;
+  if (p.opts.reserved[4] != 1) return B;
   const int w = expval_wave_states(p.n, p.dt, B);
   return w >= 2 ? w : B;
 }

@@ -910,9 +910,9 @@ def test_stream_and_pipeline_edge_cases():
 
 @pytest.mark.parametrize("dtname", ["c64", "c128"])
 def test_batched_l2_waves_ragged(dtname):
-    """Batched execution in L2-sized waves (two 32 MiB states per wave, the last
-    wave holding one): every row's state and <H> equal the pass-major schedule
-    and the oracle, for CUDA-core plans with parametric blocks rebuilt per row
+    """Batched execution in L2-sized waves (batch_l2_waves: two 32 MiB states per
+    wave, the last wave holding one): every row's state and <H> equal the
+    default pass-by-pass schedule and the oracle, for CUDA-core plans with parametric blocks rebuilt per row
     and (complex64) tensor-core plans with per-row W images."""
     dt = DT[dtname]
     n = 22 if dt == Q.QS_C64 else 21
@@ -927,9 +927,9 @@ def test_batched_l2_waves_ragged(dtname):
     want_e = [O.expval(O.apply_circuit(O.basis(n, 0), n, gates, th[b]), n, *H).real for b in range(Bsz)]
     for base in modes:
         results = []
-        for pass_major in (0, 1):
+        for waves in (1, 0):
             o = Q.make_opts(mode=base.mode, fuse_k=base.fuse_k, fuse_parametric=1, tc_min_gates=base.reserved[0],
-                            batch_pass_major=pass_major)
+                            batch_l2_waves=waves)
             plan = Q.qs_plan_create(n, dt, gates, o)
             states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
             try:
