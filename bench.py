@@ -28,6 +28,8 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "circuit wall time & effective HBM GB/s per state sweep (n=30 c128/c64), fused vs per-gate"
+# FP64 FMA throughput of one GB300, measured by an FMA loop (the driver's peaks file has no FP64 figure)
+FP64_PEAK_TFLOPS = 1.19
 
 
 def parse():
@@ -345,9 +347,13 @@ def main():
         i128 = Q.qs_plan_info_get(p128)
         f128_ms, _, f128k, _ = time_steps(Q, torch, p128, s128, 1, 1, per_launch=True)
         sb128 = 2 * (1 << n) * 16
+        fp64_tf = i128["flops_per_amp"] * (1 << n) / (f128k["ms"] * 1e-3) / 1e12
         extra["c128_fused"] = dict(kw128, ms=f128_ms, passes=i128["passes"], flops_per_amp=i128["flops_per_amp"],
                                    pass_gbps=i128["passes"] * sb128 / (f128k["ms"] * 1e-3) / 1e9,
-                                   bound="fp64 alu (GB300 FP64 ~1.2 TFLOP/s measured)")
+                                   bound="fp64 alu", fp64_tflops=fp64_tf, fp64_peak_tflops=FP64_PEAK_TFLOPS,
+                                   fp64_frac=fp64_tf / FP64_PEAK_TFLOPS,
+                                   fp64_peak_source="dependent-free FP64 FMA loop on GB300 (CUDA events), not in "
+                                                    "MEASURED_PEAKS.json")
         Q.qs_state_set_basis(s128, 0)
         Q.qs_plan_execute(p128, s128)
         Q.qs_plan_free(p128)
