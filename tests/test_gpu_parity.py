@@ -728,6 +728,8 @@ def test_phase_pass_batched_rows_use_their_own_parameters(dtname):
     modes = [Q.make_opts(), Q.make_opts(fuse_k=4, fuse_parametric=1)]
     if dt == Q.QS_C64:
         modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
+    else:   # phase and tile passes in FP32 pairs, per-row angles
+        modes.append(Q.make_opts(fuse_k=2, fuse_parametric=1, c128_pairs=1))
     for opts in modes:
         plan = Q.qs_plan_create(n, dt, gates, opts)
         states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
