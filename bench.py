@@ -819,6 +819,22 @@ def config_hea(Q, torch, np, st, args):
         wall = (time.perf_counter() - t0) * 1e3
         grads[dname] = gr
         c4[dname] = {"ms": wall, "expval": e}
+        if dt == Q.QS_C128:   # the same gradient with the tile passes in FP32 pairs
+            o = Q.make_opts(c128_pairs=1)
+            Q.qs_adjoint_grad(s, g, th, *H, opts=o)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2, gr2 = Q.qs_adjoint_grad(s, g, th, *H, opts=o)
+            c4["c128_fp32_pairs"] = {"ms": (time.perf_counter() - t0) * 1e3, "expval": e2,
+                                     "max_abs_grad_diff_vs_fp64": float(np.abs(gr2 - gr).max())}
+        else:                 # forward on tensor cores
+            o = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2, fuse_parametric=1)
+            Q.qs_adjoint_grad(s, g, th, *H, opts=o)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            e2, gr2 = Q.qs_adjoint_grad(s, g, th, *H, opts=o)
+            c4["c64_tensor_forward"] = {"ms": (time.perf_counter() - t0) * 1e3, "expval": e2,
+                                        "max_abs_grad_diff_vs_default": float(np.abs(gr2 - gr).max())}
         Q.qs_state_free(s)
     c4["max_abs_grad_diff_c64_vs_c128"] = float(np.abs(grads["c64"] - grads["c128"]).max())
     return c4

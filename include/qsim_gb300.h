@@ -258,6 +258,12 @@ qs_status qs_adjoint_grad(qs_state_t s, const qs_gate* gates, size_t ngates,
                           const double* theta, size_t ntheta,
                           const qs_pauli_term* terms, size_t nterms,
                           double* expval_out, double* grad_out);
+/* Same, with plan options (may be NULL = the defaults above): they plan the
+ * forward execution (any fused or tensor mode); their complex128 arithmetic
+ * (reserved[3], FP32 pairs) applies to the reverse sweep as well. */
+qs_status qs_adjoint_grad_opts(qs_state_t s, const qs_gate* gates, size_t ngates, const double* theta, size_t ntheta,
+                               const qs_pauli_term* terms, size_t nterms, const qs_plan_opts* opts,
+                               double* expval_out, double* grad_out);
 
 /* ---------------- batched execution ---------------- */
 

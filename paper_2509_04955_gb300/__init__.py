@@ -99,6 +99,8 @@ _SIGS = {
     "qs_state_diff": (C.c_int, [_VP, _VP, _DP, _DP]),
     "qs_adjoint_grad": (C.c_int, [_VP, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t, C.POINTER(QsPauliTerm),
                                   C.c_size_t, _DP, _DP]),
+    "qs_adjoint_grad_opts": (C.c_int, [_VP, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t, C.POINTER(QsPauliTerm),
+                                       C.c_size_t, C.POINTER(QsPlanOpts), _DP, _DP]),
     "qs_plan_execute_batched": (C.c_int, [_VP, C.POINTER(_VP), C.c_int, _DP, C.c_size_t, C.POINTER(QsPauliTerm),
                                           C.c_size_t, _DP]),
     "qs_plan_check_device_blocks": (C.c_int, [_VP, _VP, _DP, C.c_size_t, _DP, _I64P]),
@@ -400,13 +402,19 @@ def qs_apply_pauli_sum(state: int, coeff, xmask, zmask, out: int):
     _check(lib().qs_apply_pauli_sum(state, pack_terms(coeff, xmask, zmask), len(coeff), out))
 
 
-def qs_adjoint_grad(state: int, gates, theta, coeff, xmask, zmask):
+def qs_adjoint_grad(state: int, gates, theta, coeff, xmask, zmask, opts: QsPlanOpts | None = None):
+    """<H> and its gradient (qs_adjoint_grad, or qs_adjoint_grad_opts when opts is given)."""
     th = np.ascontiguousarray(theta, dtype=np.float64)
     grad = np.zeros(max(1, th.size))
     e = C.c_double()
-    _check(lib().qs_adjoint_grad(state, pack_gates(gates), len(gates), th.ctypes.data_as(_DP), th.size,
-                                 pack_terms(coeff, xmask, zmask), len(coeff), C.byref(e),
-                                 grad.ctypes.data_as(_DP)))
+    if opts is None:
+        _check(lib().qs_adjoint_grad(state, pack_gates(gates), len(gates), th.ctypes.data_as(_DP), th.size,
+                                     pack_terms(coeff, xmask, zmask), len(coeff), C.byref(e),
+                                     grad.ctypes.data_as(_DP)))
+    else:
+        _check(lib().qs_adjoint_grad_opts(state, pack_gates(gates), len(gates), th.ctypes.data_as(_DP), th.size,
+                                          pack_terms(coeff, xmask, zmask), len(coeff), C.byref(opts), C.byref(e),
+                                          grad.ctypes.data_as(_DP)))
     return e.value, grad[: th.size]
 
 

@@ -1855,14 +1855,22 @@ qs_status qs_apply_pauli_sum(qs_state_t s, const qs_pauli_term* terms, size_t nt
 
 qs_status qs_adjoint_grad(qs_state_t s, const qs_gate* gates, size_t ngates, const double* theta, size_t ntheta,
                           const qs_pauli_term* terms, size_t nterms, double* expval_out, double* grad_out) {
+  return qs_adjoint_grad_opts(s, gates, ngates, theta, ntheta, terms, nterms, nullptr, expval_out, grad_out);
+}
+
+qs_status qs_adjoint_grad_opts(qs_state_t s, const qs_gate* gates, size_t ngates, const double* theta, size_t ntheta,
+                               const qs_pauli_term* terms, size_t nterms, const qs_plan_opts* opts,
+                               double* expval_out, double* grad_out) {
   return guard([&] {
     check_state(s);
     require(grad_out != nullptr || ntheta == 0, "grad_out is NULL");
     require(nterms == 0 || terms != nullptr, "terms is NULL");
-    // forward: phi = U psi with a fused plan (tile passes, CUDA cores)
+    require(opts == nullptr || opts->mode != QS_MODE_PER_GATE, "the forward plan of the adjoint needs a fused or tensor mode");
+    // forward: phi = U psi with a fused plan (tile passes, CUDA cores), or the caller's options
     qs_plan_opts fo;
     std::memset(&fo, 0, sizeof(fo));
     fo.mode = QS_MODE_FUSED;
+    if (opts) fo = *opts;
     std::unique_ptr<qs_plan_s> p(create_plan(s->n, s->dt, gates, ngates, &fo));
     // reverse sweep: the reversed circuit, one op per gate, grouped into tile passes
     std::vector<qs_gate> rev(gates, gates + ngates);
@@ -1871,6 +1879,7 @@ qs_status qs_adjoint_grad(qs_state_t s, const qs_gate* gates, size_t ngates, con
     std::memset(&ro, 0, sizeof(ro));
     ro.mode = QS_MODE_FUSED;
     ro.fuse_k = 1;
+    ro.reserved[3] = opts ? opts->reserved[3] : 0;   // complex128 arithmetic of the reverse sweep
     std::unique_ptr<qs_plan_s> rp(create_plan(s->n, s->dt, rev.data(), rev.size(), &ro, /*no_merge=*/true));
     upload(*p);
     upload(*rp);

@@ -57,6 +57,7 @@ __device__ __forceinline__ dfl operator+(dfl a, dfl b) {
   return fast_two_sum(s, e);
 }
 __device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl& operator+=(dfl& a, dfl b) { return a = a + b; }
 
 __device__ __forceinline__ dfl operator*(dfl a, dfl b) {
   const float p = a.h * b.h;

@@ -515,7 +515,7 @@ __device__ __forceinline__ R adjoint_grad_part(const typename V2<R>::T* tphi, co
   const C d00 = from_d<R>(dmat[0]), d01 = from_d<R>(dmat[1]), d10 = from_d<R>(dmat[2]), d11 = from_d<R>(dmat[3]);
   const uint32_t count = 1u << (m - op.nins);
   const uint32_t ta = 1u << op.t0;
-  R acc = 0;
+  R acc = R(0.0);
   if (op.form == FORM_DIAG1) {   // element-wise enumeration (the target is not inserted)
     for (uint32_t p = threadIdx.x; p < count; p += kTileThreads) {
       const uint32_t b = ins0(p, op.ins, op.nins) | op.cmask;
@@ -545,8 +545,8 @@ __device__ __forceinline__ R adjoint_grad_part(const typename V2<R>::T* tphi, co
 // CTA's tiles; partials[row * pcols + CTA] receives the CTA's sum (rows from
 // grow[gate], -1 for fixed gates).
 template <typename R>
-__global__ void __launch_bounds__(kTileThreads) k_adjoint_tile(typename V2<R>::T* __restrict__ phi,
-                                                                typename V2<R>::T* __restrict__ lam, PassDesc p,
+__global__ void __launch_bounds__(kTileThreads) k_adjoint_tile(typename GAmp<R>::T* __restrict__ phi,
+                                                                typename GAmp<R>::T* __restrict__ lam, PassDesc p,
                                                                 const DevOp* __restrict__ ops,
                                                                 const double2* __restrict__ gadj,
                                                                 const int32_t* __restrict__ grow, int lg_tiles,
@@ -556,6 +556,7 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint_tile(typename V2<R>::T
   constexpr int VPT = 16 / sizeof(C);
   constexpr int kAdjIo = 1;   // compute-bound: registers go to occupancy (up to 3 CTAs per SM), not transfers
   constexpr int kWarps = kTileThreads / 32;
+  constexpr bool kDF = std::is_same<R, dfl>::value;
   extern __shared__ __align__(16) unsigned char smem[];
   const int m = p.m, L = p.L, nh = p.nhigh;
   const int nops = p.op_end - p.op_begin;
@@ -575,24 +576,34 @@ __global__ void __launch_bounds__(kTileThreads) k_adjoint_tile(typename V2<R>::T
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (uint64_t t = blockIdx.x; t < (1ull << lg_tiles); t += gridDim.x) {
     const uint64_t base = insert_zero_bits(t << L, p.high, nh);
-    tile_io<C, C2, VPT, true, kAdjIo>(phi, tphi, base, segoff, size, L, lmask);
-    tile_io<C, C2, VPT, true, kAdjIo>(lam, tlam, base, segoff, size, L, lmask);
+    if constexpr (kDF) {
+      tile_io_df<true, kAdjIo>(phi, tphi, base, segoff, size, L, lmask);
+      tile_io_df<true, kAdjIo>(lam, tlam, base, segoff, size, L, lmask);
+    } else {
+      tile_io<C, C2, VPT, true, kAdjIo>(phi, tphi, base, segoff, size, L, lmask);
+      tile_io<C, C2, VPT, true, kAdjIo>(lam, tlam, base, segoff, size, L, lmask);
+    }
     __syncthreads();
     for (int o = p.op_begin; o < p.op_end; ++o) {
       const DevOp op = ops[o];
       apply_gate_op<R>(tphi, m, op, gadj, mbuf);
       const int row = grow[op.mat];
       if (row >= 0) {
-        R part = adjoint_grad_part<R>(tphi, tlam, m, op, gadj + (int64_t)op.mat * 16 + 4);
+        double part = (double)adjoint_grad_part<R>(tphi, tlam, m, op, gadj + (int64_t)op.mat * 16 + 4);
         for (int s = 16; s > 0; s >>= 1) part += __shfl_xor_sync(0xffffffffu, part, s);
-        if (lane == 0) gacc[(o - p.op_begin) * kWarps + warp] += (double)part;
+        if (lane == 0) gacc[(o - p.op_begin) * kWarps + warp] += part;
       }
       if (op.form == FORM_DENSE2) __syncthreads();   // the matrix buffer is loaded again below
       apply_gate_op<R>(tlam, m, op, gadj, mbuf);
       __syncthreads();
     }
-    tile_io<C, C2, VPT, false, kAdjIo>(phi, tphi, base, segoff, size, L, lmask);
-    tile_io<C, C2, VPT, false, kAdjIo>(lam, tlam, base, segoff, size, L, lmask);
+    if constexpr (kDF) {
+      tile_io_df<false, kAdjIo>(phi, tphi, base, segoff, size, L, lmask);
+      tile_io_df<false, kAdjIo>(lam, tlam, base, segoff, size, L, lmask);
+    } else {
+      tile_io<C, C2, VPT, false, kAdjIo>(phi, tphi, base, segoff, size, L, lmask);
+      tile_io<C, C2, VPT, false, kAdjIo>(lam, tlam, base, segoff, size, L, lmask);
+    }
     __syncthreads();
   }
   for (int i = threadIdx.x; i < nops; i += kTileThreads) {
@@ -636,7 +647,8 @@ cudaError_t prepare_adjoint_tile(const PassDesc& p, qs_dtype dt) {
   const size_t smem = adjoint_tile_smem_bytes(p, dt);
   if (smem > 227 * 1024) return cudaErrorInvalidValue;
   sm_count();
-  return dt == QS_C64 ? prepare_adjoint_t<float>(smem) : prepare_adjoint_t<double>(smem);
+  if (dt == QS_C64) return prepare_adjoint_t<float>(smem);
+  return p.df ? prepare_adjoint_t<dfl>(smem) : prepare_adjoint_t<double>(smem);
 }
 
 // Grid of the adjoint tile pass: at most `pcols` CTAs (the partial-sum columns).
@@ -644,9 +656,9 @@ cudaError_t launch_adjoint_tile(void* phi, void* lam, int n, qs_dtype dt, const 
                                 const double2* gadj, const int32_t* grow, double* partials, int pcols,
                                 cudaStream_t st) {
   const size_t smem = adjoint_tile_smem_bytes(p, dt);
-  const int per_sm = dt == QS_C64 ? AdjCfg<float>::per_sm : AdjCfg<double>::per_sm;
-  if ((int)smem > (dt == QS_C64 ? AdjCfg<float>::bytes : AdjCfg<double>::bytes) || per_sm < 1)
-    return cudaErrorInvalidConfiguration;   // not prepared
+  const int per_sm = dt == QS_C64 ? AdjCfg<float>::per_sm : p.df ? AdjCfg<dfl>::per_sm : AdjCfg<double>::per_sm;
+  const int bytes = dt == QS_C64 ? AdjCfg<float>::bytes : p.df ? AdjCfg<dfl>::bytes : AdjCfg<double>::bytes;
+  if ((int)smem > bytes || per_sm < 1) return cudaErrorInvalidConfiguration;   // not prepared
   uint64_t grid = (uint64_t)sm_count() * per_sm;
   const uint64_t ntiles = 1ull << (n - p.m);
   if (grid > ntiles) grid = ntiles;
@@ -654,6 +666,9 @@ cudaError_t launch_adjoint_tile(void* phi, void* lam, int n, qs_dtype dt, const 
   if (dt == QS_C64)
     k_adjoint_tile<float><<<(unsigned)grid, kTileThreads, smem, st>>>((float2*)phi, (float2*)lam, p, ops, gadj, grow,
                                                                        n - p.m, partials, pcols);
+  else if (p.df)
+    k_adjoint_tile<dfl><<<(unsigned)grid, kTileThreads, smem, st>>>((double2*)phi, (double2*)lam, p, ops, gadj, grow,
+                                                                     n - p.m, partials, pcols);
   else
     k_adjoint_tile<double><<<(unsigned)grid, kTileThreads, smem, st>>>((double2*)phi, (double2*)lam, p, ops, gadj,
                                                                         grow, n - p.m, partials, pcols);

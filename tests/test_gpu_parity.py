@@ -951,3 +951,36 @@ def test_batched_l2_waves_ragged(dtname):
         for b in range(Bsz):
             assert abs(ex0[b] - want_e[b]) <= TOL[dt] * np.abs(H[0]).sum() * 10
             assert abs(ex0[b] - ex1[b]) <= TOL[dt] * np.abs(H[0]).sum() * 10
+
+
+@pytest.mark.parametrize("maker", ["mix", "hea"])
+def test_adjoint_gradient_c128_fp32_pairs_and_options(maker):
+    """qs_adjoint_grad_opts: complex128 with the forward tile passes and the
+    reverse sweep in FP32 pairs, against the oracle at the complex128 bar and
+    within 1e-12 of the FP64 sweep; complex64 with a tensor-core forward plan."""
+    n = 15
+    if maker == "mix":
+        gates, p = _parametrized_gate_mix(n, 140, seed=31)
+        theta = W.thetas_uniform(p, 32)
+    else:
+        gates, p = W.hea(n, 4)
+        theta = W.thetas_uniform(p, 33)
+    H = W.random_pauli_sum(n, 25, seed=34)
+    scale = np.abs(H[0]).sum()
+    e_ref, g_ref = O.adjoint_grad(O.basis(n, 0), n, gates, theta, *H)
+    h = Q.qs_state_alloc(n, Q.QS_C128)
+    try:
+        e, g = Q.qs_adjoint_grad(h, gates, theta, *H, opts=Q.make_opts(c128_pairs=1))
+        e64, g64 = Q.qs_adjoint_grad(h, gates, theta, *H)
+    finally:
+        Q.qs_state_free(h)
+    assert abs(e - e_ref) <= 1e-12 * scale * 10
+    assert np.abs(g - g_ref).max() <= 1e-12 * scale * 10
+    assert np.abs(g - g64).max() <= 1e-12 * scale
+    h = Q.qs_state_alloc(n, Q.QS_C64)
+    try:
+        e, g = Q.qs_adjoint_grad(h, gates, theta, *H, opts=Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2,
+                                                                         fuse_parametric=1))
+    finally:
+        Q.qs_state_free(h)
+    assert np.abs(g - g_ref).max() <= 2e-5 * scale * 10
