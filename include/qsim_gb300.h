@@ -132,11 +132,7 @@ typedef struct {
                             reserved[4]: qs_plan_execute_batched schedule: 0 = every pass covers
                             the whole batch (default), 1 = when at least two states fit in 64 MiB
                             (about half the L2), every pass runs on one wave of such states
-                            before the next wave (passes then read L2, not HBM; more launches).
-                            reserved[5]: 0 = consecutive one-target gates of a tile pass whose
-                            non-diagonal targets share at most 4 tile bits (3 for complex128)
-                            run in registers with one shared-memory round trip (default),
-                            1 = one round trip per gate. */
+                            before the next wave (passes then read L2, not HBM; more launches). */
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */

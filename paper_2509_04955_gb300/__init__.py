@@ -194,9 +194,9 @@ def _dptr(a):
 
 def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0,
               fuse_parametric=0, tc_min_gates=0, tc_pipeline=0, phase_min_gates=0, c128_pairs=0,
-              batch_l2_waves=0, no_gate_runs=0):
-    """qs_plan_opts; tc_min_gates, tc_pipeline, phase_min_gates, c128_pairs, batch_l2_waves and
-    no_gate_runs fill reserved[0..5]."""
+              batch_l2_waves=0):
+    """qs_plan_opts; tc_min_gates, tc_pipeline, phase_min_gates, c128_pairs and batch_l2_waves fill
+    reserved[0..4]."""
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
     o.paper_mode, o.tc_precision, o.fuse_parametric = paper_mode, tc_precision, fuse_parametric
@@ -205,7 +205,6 @@ def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_m
     o.reserved[2] = phase_min_gates
     o.reserved[3] = c128_pairs
     o.reserved[4] = batch_l2_waves
-    o.reserved[5] = no_gate_runs
     return o
 
 

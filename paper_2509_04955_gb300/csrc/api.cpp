@@ -149,8 +149,6 @@ struct qs_plan_s {
   int tc_prec = 3;
   int tc_pipe = 0;                 // single-state tensor-core pass: 0 bulk-copy staged, 1 register-staged
   bool df = false;                 // complex128 tile passes computed in FP32 pairs
-  bool gate_by_gate = false;       // keep one op per gate (the adjoint's reverse sweep)
-  std::vector<DevRunMember> h_runmem;   // members of the gate runs (OP_GRUN)
   int64_t btab_elems = 0;
   // blocks whose matrices depend on theta, rebuilt on the device per batch row
   std::vector<DevBlock> h_dblocks;
@@ -160,7 +158,7 @@ struct qs_plan_s {
   std::vector<double2> h_btab;
   // device
   bool uploaded = false;
-  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err, d_dblocks, d_dmem, d_pterms, d_smgp, d_runmem;
+  DevBuf d_gates, d_pg, d_gtab, d_theta, d_ops, d_btab, d_wimg, d_err, d_dblocks, d_dmem, d_pterms, d_smgp;
   int gtab_rows = 0;
   qs_plan_info info{};
   // batched graph cache; captured and replayed on a plan-owned stream
@@ -286,10 +284,6 @@ void upload(qs_plan_s& p) {
     if (!p.h_dmem.empty())
       CK(cudaMemcpy(p.d_dmem.p, p.h_dmem.data(), sizeof(DevMember) * p.h_dmem.size(), cudaMemcpyHostToDevice));
   }
-  if (!p.h_runmem.empty()) {
-    p.d_runmem.ensure(sizeof(DevRunMember) * p.h_runmem.size());
-    CK(cudaMemcpy(p.d_runmem.p, p.h_runmem.data(), sizeof(DevRunMember) * p.h_runmem.size(), cudaMemcpyHostToDevice));
-  }
   if (!p.h_pterms.empty()) {
     p.d_pterms.ensure(sizeof(DevPhaseTerm) * p.h_pterms.size());
     CK(cudaMemcpy(p.d_pterms.p, p.h_pterms.data(), sizeof(DevPhaseTerm) * p.h_pterms.size(), cudaMemcpyHostToDevice));
@@ -303,7 +297,6 @@ void upload(qs_plan_s& p) {
   p.d_err.ensure(sizeof(int) * 4);
   CK(cudaMemset(p.d_err.p, 0, sizeof(int) * 4));
   // kernel attributes and occupancy, here and never during a stream capture
-  for (PassDesc& pd : p.pdesc) pd.runmem = p.d_runmem.p;
   for (const PassDesc& pd : p.pdesc) CK(prepare_tile_pass(pd, p.dt));
   if (!p.tcdesc.empty()) CK(prepare_tc_pass());
   if (!p.h_dblocks.empty()) CK(prepare_build_blocks());
@@ -538,73 +531,6 @@ void register_device_block(qs_plan_s& P, const Block& blk, int kind, int64_t out
   P.h_dblocks.push_back(d);
 }
 
-// Gate runs: consecutive one-target gate ops of a tile pass whose non-diagonal
-// targets lie on at most kRunMaxBits tile bits, all at positions >= 5, become
-// one OP_GRUN. Each thread then holds the 2^r amplitudes spanning those bits
-// in registers and applies every gate of the run before storing them back:
-// one shared-memory round trip for the run instead of one per gate. Diagonal
-// gates (any target) and controls (any bits) join freely. Targets at positions
-// >= 5 keep the 32 lanes of a warp on consecutive amplitudes (conflict-free
-// shared-memory banks). The ops of pass pd are rewritten in place.
-void form_gate_runs(qs_plan_s& P, PassDesc& pd) {
-  std::vector<DevOp> in(P.dops.begin() + pd.op_begin, P.dops.end());
-  std::vector<DevOp> out;
-  size_t i = 0;
-  auto mergeable = [](const DevOp& d) {
-    return d.type == OP_GATE && d.t1 < 0 && d.form != FORM_SWAP2 && d.form != FORM_DENSE2;
-  };
-  auto diag = [](const DevOp& d) { return d.form == FORM_PHASE1 || d.form == FORM_DIAG1; };
-  // register bits per run: 16 complex64 amplitudes per thread where the pass's
-  // kernel instance runs one CTA per SM (kmax >= 3), else 8 (registers for two CTAs)
-  const int max_bits = P.dt == QS_C64 && pd.kmax >= 3 ? kRunMaxBits : kRunMaxBits - 1;
-  while (i < in.size()) {
-    uint32_t R = 0;
-    size_t j = i;
-    while (j < in.size() && j - i < (size_t)kRunMaxMembers && mergeable(in[j])) {
-      if (!diag(in[j])) {
-        const uint32_t t = 1u << in[j].t0;
-        if (in[j].t0 < 5 || (!(R & t) && __builtin_popcount(R) >= max_bits)) break;
-        R |= t;
-      }
-      ++j;
-    }
-    if (j - i < 2) {
-      out.push_back(in[i]);
-      ++i;
-      continue;
-    }
-    DevOp run;
-    std::memset(&run, 0, sizeof(run));
-    run.type = OP_GRUN;
-    int pos[kRunMaxBits];
-    run.k = 0;
-    for (int b = 0; b < 32; ++b)
-      if (R & (1u << b)) pos[run.k] = b, run.ins[run.k++] = b;
-    run.mat = (int32_t)P.h_runmem.size();
-    run.nins = (int32_t)(j - i);
-    for (size_t k = i; k < j; ++k) {
-      const DevOp& d = in[k];
-      DevRunMember mb;
-      std::memset(&mb, 0, sizeof(mb));
-      mb.gate = d.mat;
-      mb.form = d.form;
-      mb.j = -1;
-      mb.tbit = d.t0;
-      for (int b = 0; b < run.k; ++b) {
-        if (pos[b] == d.t0) mb.j = b;
-        if (d.cmask & (1u << pos[b])) mb.cm_reg |= 1u << b;
-      }
-      mb.cm_tile = d.cmask & ~R;
-      P.h_runmem.push_back(mb);
-    }
-    pd.mbuf_elems = std::max(pd.mbuf_elems, 4 * run.nins);
-    out.push_back(run);
-    i = j;
-  }
-  P.dops.resize(pd.op_begin);
-  P.dops.insert(P.dops.end(), out.begin(), out.end());
-}
-
 void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::vector<PassRec>& passes,
                       const std::vector<int>& order, int low_qubits, qs_plan_info& in) {
   const qs_dtype dt = P.dt;
@@ -621,7 +547,6 @@ void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::ve
       return (int)(std::lower_bound(pr.tile.begin(), pr.tile.end(), q) - pr.tile.begin());
     };
     pd.op_begin = (int)P.dops.size();
-    const int exec_begin = (int)P.exec_ops.size();
     pd.kmax = 0;
     for (int oi = pr.op_begin; oi < pr.op_end; ++oi) {
       const OpRec& r = ops[order[oi]];
@@ -666,14 +591,13 @@ void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::ve
       P.dops.push_back(d);
       P.exec_ops.push_back(r);
     }
-    if (!P.gate_by_gate) form_gate_runs(P, pd);
     pd.op_end = (int)P.dops.size();
     require(tile_smem_bytes(pd.m, pd.nhigh, pd.mbuf_elems, dt) <= 227 * 1024,
             "tile does not fit in shared memory: lower tile_qubits");
     P.steps.push_back({0, (int)P.pdesc.size()});
     P.pdesc.push_back(pd);
     P.pass_tiles.push_back(pr.tile);
-    P.pass_ops.push_back({exec_begin, (int)P.exec_ops.size()});
+    P.pass_ops.push_back({pd.op_begin, pd.op_end});
   }
 }
 
@@ -730,7 +654,7 @@ void emit_phase_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
   DevOp op;
   std::memset(&op, 0, sizeof(op));
   op.type = OP_PHASE;
-  const int b = (int)P.exec_ops.size();
+  const int b = (int)P.dops.size();
   P.dops.push_back(op);
   P.exec_ops.push_back(r);
   P.steps.push_back({2, (int)P.phdesc.size()});
@@ -767,7 +691,7 @@ void emit_tc_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
   std::memset(&d, 0, sizeof(d));
   d.type = OP_TC;
   d.k = 6;
-  const int b = (int)P.exec_ops.size();
+  const int b = (int)P.dops.size();
   P.dops.push_back(d);
   P.exec_ops.push_back(r);
   P.steps.push_back({1, (int)P.tcdesc.size()});
@@ -930,7 +854,6 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   po.smem_weight = 1.0;
   po.fuse_parametric = o.fuse_parametric != 0;
   po.no_merge = no_merge;
-  p->gate_by_gate = no_merge || o.reserved[5] == 1;   // reserved[5] = 1: no gate runs
   // Diagonal phase runs (reserved[2]: least gates per run, 0 = 2n, < 0 = none)
   // become their own passes; the gates between them are contracted segment by
   // segment, so no block moves across a run.

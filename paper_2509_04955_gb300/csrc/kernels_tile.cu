@@ -233,89 +233,6 @@ __device__ __forceinline__ void apply_gate_op(typename V2<R>::T* tile, int m, co
   }
 }
 
-// One member of a gate run applied to the 2^RB amplitudes a thread holds:
-// pairs (v, v | 2^J) over the register index v, controls on register bits
-// checked per v (the loop over v is unrolled, so J and v are compile-time).
-template <typename R, int RB, int J>
-__device__ __forceinline__ void run_member(typename V2<R>::T* a, int form, uint32_t cm, typename V2<R>::T m00,
-                                           typename V2<R>::T m01, typename V2<R>::T m10, typename V2<R>::T m11) {
-  using C = typename V2<R>::T;
-  constexpr int V = 1 << RB;
-#pragma unroll
-  for (int v = 0; v < V; ++v) {
-    if (v & (1 << J)) continue;
-    if (((uint32_t)v & cm) != cm) continue;
-    C& x0 = a[v];
-    C& x1 = a[v | (1 << J)];
-    C r0, r1;
-    switch (form) {
-      case FORM_REAL1: r0 = rmix<R>(m00.x, x0, m01.x, x1); r1 = rmix<R>(m10.x, x0, m11.x, x1); break;
-      case FORM_RXLIKE1: r0 = ixmix<R>(m00.x, x0, m01.y, x1); r1 = ixmix<R>(m11.x, x1, m10.y, x0); break;
-      case FORM_X1: r0 = x1; r1 = x0; break;
-      case FORM_ANTI1: r0 = cmul(m01, x1); r1 = cmul(m10, x0); break;
-      case FORM_PHASE1: r0 = x0; r1 = cmul(m11, x1); break;
-      case FORM_DIAG1: r0 = cmul(m00, x0); r1 = cmul(m11, x1); break;
-      default: r0 = cfma(m01, x1, cmul(m00, x0)); r1 = cfma(m11, x1, cmul(m10, x0));
-    }
-    x0 = r0;
-    x1 = r1;
-  }
-}
-
-// A gate run (OP_GRUN): each thread loads the 2^RB amplitudes that differ in
-// the run's register bits, applies the members in program order in
-// registers, and stores them back.
-template <typename R, int RB>
-__device__ __forceinline__ void apply_grun(typename V2<R>::T* tile, int m, const DevOp& op,
-                                           const DevRunMember* __restrict__ rm, const double2* __restrict__ gtab,
-                                           typename V2<R>::T* mbuf) {
-  using C = typename V2<R>::T;
-  constexpr int V = 1 << RB;
-  const int nm = op.nins;
-  const DevRunMember* mem = rm + op.mat;
-  for (int i = threadIdx.x; i < 4 * nm; i += kTileThreads)
-    mbuf[i] = from_d<R>(gtab[(int64_t)mem[i >> 2].gate * 16 + (i & 3)]);
-  __syncthreads();
-  uint32_t bit[RB > 0 ? RB : 1];
-#pragma unroll
-  for (int b = 0; b < RB; ++b) bit[b] = 1u << op.ins[b];
-  // offset of register index v: the register bits set in v (v is a compile-time index)
-  auto off = [&](int v) {
-    uint32_t o = 0;
-#pragma unroll
-    for (int b = 0; b < RB; ++b)
-      if (v & (1 << b)) o |= bit[b];
-    return o;
-  };
-  const uint32_t groups = 1u << (m - RB);
-  for (uint32_t g = threadIdx.x; g < groups; g += kTileThreads) {
-    const uint32_t base = ins0k<RB>(g, op.ins);
-    C a[V];
-#pragma unroll
-    for (int v = 0; v < V; ++v) a[v] = tile[base | off(v)];
-    for (int k = 0; k < nm; ++k) {
-      const DevRunMember mb = mem[k];
-      if ((base & mb.cm_tile) != mb.cm_tile) continue;
-      const C m00 = mbuf[4 * k], m01 = mbuf[4 * k + 1], m10 = mbuf[4 * k + 2], m11 = mbuf[4 * k + 3];
-      if (mb.j < 0) {   // diagonal, target bit outside the register bits: one factor for all v
-        const bool one = (base >> mb.tbit) & 1u;
-        if (mb.form == FORM_PHASE1 && !one) continue;
-        const C f = one ? m11 : m00;
-#pragma unroll
-        for (int v = 0; v < V; ++v)
-          if (((uint32_t)v & mb.cm_reg) == mb.cm_reg) a[v] = cmul(f, a[v]);
-        continue;
-      }
-      if constexpr (RB >= 1) { if (mb.j == 0) run_member<R, RB, 0>(a, mb.form, mb.cm_reg, m00, m01, m10, m11); }
-      if constexpr (RB >= 2) { if (mb.j == 1) run_member<R, RB, 1>(a, mb.form, mb.cm_reg, m00, m01, m10, m11); }
-      if constexpr (RB >= 3) { if (mb.j == 2) run_member<R, RB, 2>(a, mb.form, mb.cm_reg, m00, m01, m10, m11); }
-      if constexpr (RB >= 4) { if (mb.j == 3) run_member<R, RB, 3>(a, mb.form, mb.cm_reg, m00, m01, m10, m11); }
-    }
-#pragma unroll
-    for (int v = 0; v < V; ++v) tile[base | off(v)] = a[v];
-  }
-}
-
 // Groups per thread of a dense op: each staged matrix entry is loaded once
 // and used for G groups (register budget about 64 values for the inputs).
 template <typename R, int K> struct DenseG {
@@ -427,17 +344,6 @@ __global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typena
       const DevOp op = ops[o];
       if (op.type == OP_GATE) {
         apply_gate_op<R>(tile, m, op, gtab, mbuf);
-      } else if (op.type == OP_GRUN) {
-        const DevRunMember* rm = (const DevRunMember*)p.runmem;
-        switch (op.k) {   // the planner caps k at kRunMaxBits (complex64) or kRunMaxBits - 1
-          case 0: apply_grun<R, 0>(tile, m, op, rm, gtab, mbuf); break;
-          case 1: apply_grun<R, 1>(tile, m, op, rm, gtab, mbuf); break;
-          case 2: apply_grun<R, 2>(tile, m, op, rm, gtab, mbuf); break;
-          case 3: apply_grun<R, 3>(tile, m, op, rm, gtab, mbuf); break;
-          default:   // 16 amplitudes per thread: complex64 in the one-CTA-per-SM instances only
-            if constexpr (sizeof(R) == 4 && KMAX >= 3) apply_grun<R, 4>(tile, m, op, rm, gtab, mbuf);
-            break;
-        }
       } else {
         const double2* __restrict__ bt = op.per_row ? btab + (brow0 + (int64_t)sb) * bstride : btab;
         if (op.type == OP_DIAG) {

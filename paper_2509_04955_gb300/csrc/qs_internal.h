@@ -52,20 +52,7 @@ enum OpType : int32_t {
   OP_DENSE = 1,   // dense k-qubit block, matrix (2^k x 2^k) in the block table
   OP_DIAG = 2,    // diagonal k-qubit block, 2^k phases in the block table
   OP_TC = 3,      // dense 6-qubit block applied on tensor cores (its own pass, complex64)
-  OP_PHASE = 4,   // diagonal phase polynomial of a gate run over the whole register (its own pass)
-  OP_GRUN = 5     // consecutive one-target gates applied in registers over k tile bits (ins[0..k)),
-                  // members [mat, mat + nins) of the run-member table
-};
-
-constexpr int kRunMaxBits = 4;
-constexpr int kRunMaxMembers = 32;
-struct DevRunMember {
-  int32_t gate;            // row in the gate table
-  int32_t form;            // GateForm of the one-target matrix
-  int32_t j;               // register index of the target bit, -1: a diagonal gate whose target is outside
-  int32_t tbit;            // tile-local target bit
-  uint32_t cm_reg;         // control bits among the register bits (mask over the register index)
-  uint32_t cm_tile;        // control bits outside the register bits (tile-local mask)
+  OP_PHASE = 4    // diagonal phase polynomial of a gate run over the whole register (its own pass)
 };
 
 // A contracted block whose matrix depends on theta: rebuilt on the device from
@@ -155,7 +142,6 @@ struct PassDesc {
   int32_t mbuf_elems;      // matrix staging entries the pass needs (max over its ops)
   int32_t op_begin, op_end;
   int32_t df;              // complex128 tile computed in FP32 pairs (double-float), else FP64
-  const void* runmem;      // device table of gate-run members (DevRunMember), set when the plan is uploaded
 };
 
 // Kernel attributes / occupancy of a pass's instance; host side, never during a capture.

@@ -984,29 +984,3 @@ def test_adjoint_gradient_c128_fp32_pairs_and_options(maker):
     finally:
         Q.qs_state_free(h)
     assert np.abs(g - g_ref).max() <= 2e-5 * scale * 10
-
-
-@pytest.mark.parametrize("dtname", ["c128", "c64"])
-@pytest.mark.parametrize("m,L", [(12, 4), (13, 3), (10, 2)])
-def test_gate_runs_equal_gate_by_gate(dtname, m, L):
-    """Tile passes with gate runs (one-target gates applied in registers over up
-    to 4 tile bits, diagonal gates and controls anywhere) against one round
-    trip per gate and the oracle: random layers, every one-target form with
-    controls, parametric rotations; FP32 pairs for complex128 as well."""
-    dt = DT[dtname]
-    n = 16
-    gates = W.random_layered(n, 5, seed=m) + W.random_gate_mix(n, 120, seed=L)
-    hg, p = W.hea_staggered(n, 2)
-    theta = W.thetas_uniform(p, 9)
-    psi0 = W.random_state(n, 11)
-    for circ, th in ((gates, None), (hg, theta)):
-        want = ref(n, circ, th, psi0=psi0)
-        variants = [Q.make_opts(fuse_k=1, tile_qubits=m, low_qubits=L),
-                    Q.make_opts(fuse_k=3, tile_qubits=m, low_qubits=L),
-                    Q.make_opts(fuse_k=1, tile_qubits=m, low_qubits=L, no_gate_runs=1)]
-        if dt == Q.QS_C128:
-            variants.append(Q.make_opts(fuse_k=1, tile_qubits=m, low_qubits=L, c128_pairs=1))
-        outs = [run(n, dt, circ, th, psi0=psi0, opts=o) for o in variants]
-        for o in outs:
-            assert np.abs(o - want).max() <= TOL[dt]
-        assert np.abs(outs[0] - outs[2]).max() <= TOL[dt] / 10
