@@ -131,7 +131,7 @@ def test_qft_n28_c128_full_size_sampled_closed_form():
     gates = W.qft(n)
     rng = np.random.default_rng(0)
     idx = np.unique(rng.integers(0, 1 << n, size=1 << 16))
-    for opts in (Q.make_opts(fuse_k=4), None):
+    for opts in (Q.make_opts(fuse_k=4), None, Q.make_opts(fuse_k=2, c128_pairs=1)):
         h = Q.qs_state_alloc(n, Q.QS_C128)
         try:
             Q.qs_state_set_basis(h, x)
@@ -984,3 +984,23 @@ def test_adjoint_gradient_c128_fp32_pairs_and_options(maker):
     finally:
         Q.qs_state_free(h)
     assert np.abs(g - g_ref).max() <= 2e-5 * scale * 10
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+def test_phase_pass_complete_graph_many_terms(dtname):
+    """QAOA on the complete graph of 14 qubits: 91 ZZ terms in one phase run
+    (66 inside the 12 low bits, 24 with one low bit, 1 above), so the per-bit
+    factor lists hold several terms each; against the oracle."""
+    dt = DT[dtname]
+    n = 14
+    edges = [(u, v) for u in range(n) for v in range(u + 1, n)]
+    gates, p = W.qaoa(n, 2, edges)
+    theta = np.array([0.23, -0.41, 0.17, 0.62])
+    plan = Q.qs_plan_create(n, dt, gates, Q.make_opts())
+    try:
+        runs = [op for op in Q.qs_plan_ops(plan) if op["type"] == 4]
+        assert len(runs) == 2 and len(runs[0]["terms"]) >= 91
+    finally:
+        Q.qs_plan_free(plan)
+    got = run(n, dt, gates, theta, opts=Q.make_opts())
+    assert np.abs(got - ref(n, gates, theta)).max() <= TOL[dt]
