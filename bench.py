@@ -150,6 +150,22 @@ def oracle_sample(args, gates, budget_s: float = 15.0):
 
 # ----------------------------------------------------------------- main paths
 
+def max_over_ranks(value: float, dist, device: str) -> float:
+    """The largest value over the ranks (the job's step time is the slowest rank's);
+    `dist` is torch.distributed with an initialised group, or None for one process."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_ms_per_circuit(ms_step_max: float, world: int) -> float:
+    """Job time per circuit: each of the `world` replicas runs one circuit per step."""
+    return ms_step_max / world
+
+
 def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -274,10 +290,7 @@ def main():
         clocks.start()
     ms_step, launches, kern, norms = time_steps(Q, torch, plan, state, args.steps, args.warmup, per_launch=True)
     clk = clocks.stop() if clocks else None
-    if dist:
-        t = torch.tensor([ms_step], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms_step = float(t.item())
+    ms_step = max_over_ranks(ms_step, dist, "cuda")
 
     # roofline of the kernel that dominates the timed region
     tc_dom = kern["tc_ms"] > kern["tile_ms"]
@@ -404,7 +417,7 @@ def main():
         ms_cpu, desc, _ = oracle_sample(args, gates)
         cpu = {"value": ms_cpu, "unit": "ms", "cores": 1, "kind": "oracle", "sample": desc}
 
-    total_ms = ms_step / world       # job time per circuit with `world` replicas
+    total_ms = job_ms_per_circuit(ms_step, world)
     prof = os.path.join(ROOT, "profiles", "traffic.json")
     traffic = None
     if os.path.exists(prof):
