@@ -211,9 +211,11 @@ qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t
  * states pass through the nwork >= 1 device states in `work` (same n and
  * dtype as the plan) round robin: the copy of input i+1 into one work state
  * and the copy of result i-1 out of another run on their own streams while
- * input i is computed, so with nwork >= 2 the host link is hidden behind the
- * circuit. theta as for qs_plan_execute, shared by all inputs. Blocks until
- * every result is in host memory. */
+ * input i is computed. With nwork >= 2 the copies overlap CUDA-core passes
+ * completely; measured on GB300, they do not overlap tensor-core passes.
+ * theta as for qs_plan_execute, shared by all inputs. Blocks until every
+ * result is in host memory. QS_ERR_ARG for a NULL input, work states of
+ * another n or dtype, or a work state listed twice. */
 qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const void* const* host_in,
                                void* const* host_out, int count, const double* theta, size_t ntheta,
                                double* norms);
