@@ -446,7 +446,7 @@ def main():
         "kernel_time": kern_share,
         "effective_gbps": eff_gbps, "per_gate_equivalent_gbps": pg_equiv_gbps,
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": (1 << n) * 8, "d2h_bytes_per_step": (1 << n) * 8 + 8,
-                     "steps": e2e_steps, "api": "qs_plan_execute_host (2 device work states, copies overlapped)",
+                     "steps": e2e_steps, "api": "qs_plan_execute_host (2 device work states, copies on their own streams)",
                      "sequential_ms": e2e_seq_ms, "device_norm_last": float(e2e_norms[-1]),
                 "norm_after": e2e_norm},
         "gpu_launches": launches,
