@@ -227,6 +227,10 @@ qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const v
       }
       resolve_theta(*p, theta, ntheta, 1, sc);
       build_device_blocks(*p, 1, sc);
+      // norms land in a device array read once at the end: a per-step copy into the
+      // caller's (pageable) array would block this loop until that step's circuit ends
+      DevBuf dnorm;
+      if (norms) dnorm.ensure(sizeof(double) * std::max(1, count));
       for (int i = 0; i < count; ++i) {
         const int b = i % nwork;
         qs_state_s& w = *work[b];
@@ -235,17 +239,16 @@ qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const v
         CK(cudaEventRecord(loaded[b], si));
         CK(cudaStreamWaitEvent(sc, loaded[b], 0));
         issue_circuit(*p, w.d, 0, sc);
-        double* d_part = w.scratch.as<double>();
-        if (norms) CK(launch_norm(w.d, w.n, w.dt, d_part, d_part + reduce_blocks(), sc));
+        if (norms) CK(launch_norm(w.d, w.n, w.dt, w.scratch.as<double>(), dnorm.as<double>() + i, sc));
         CK(cudaEventRecord(computed[b], sc));
         CK(cudaStreamWaitEvent(so, computed[b], 0));
         if (host_out && host_out[i]) CK(cudaMemcpyAsync(host_out[i], w.d, bytes, cudaMemcpyDeviceToHost, so));
-        if (norms) CK(cudaMemcpyAsync(&norms[i], d_part + reduce_blocks(), sizeof(double), cudaMemcpyDeviceToHost, so));
         CK(cudaEventRecord(stored[b], so));
       }
       CK(cudaStreamSynchronize(so));
       CK(cudaStreamSynchronize(sc));
       CK(cudaStreamSynchronize(si));
+      if (norms && count > 0) CK(cudaMemcpy(norms, dnorm.p, sizeof(double) * count, cudaMemcpyDeviceToHost));
       for (int b = 0; b < nwork; ++b) CK(cudaStreamWaitEvent(work[b]->st, stored[b], 0));
       if (!p->tcdesc.empty()) {
         int err = 0;
