@@ -211,8 +211,8 @@ qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t
  * states pass through the nwork >= 1 device states in `work` (same n and
  * dtype as the plan) round robin: the copy of input i+1 into one work state
  * and the copy of result i-1 out of another run on their own streams while
- * input i is computed. With nwork >= 2 the copies overlap CUDA-core passes
- * completely; measured on GB300, they do not overlap tensor-core passes.
+ * input i is computed, so with nwork >= 2 the host link hides behind the
+ * circuit (norms are gathered on the device and read once at the end).
  * theta as for qs_plan_execute, shared by all inputs. Blocks until every
  * result is in host memory. QS_ERR_ARG for a NULL input, work states of
  * another n or dtype, or a work state listed twice. */
