@@ -609,16 +609,16 @@ def _make_expval_function():
         adjoint gradient computed by the library (``qs_adjoint_grad``)."""
 
         @staticmethod
-        def forward(ctx, theta, psi0: State, gates, terms):
+        def forward(ctx, theta, psi0: State, gates, terms, opts=None):
             th = theta.detach().to("cpu", torch.float64).numpy()
-            e, g = qs_adjoint_grad(psi0.handle, gates, th, *terms)
+            e, g = qs_adjoint_grad(psi0.handle, gates, th, *terms, opts=opts)
             ctx.save_for_backward(torch.as_tensor(g, dtype=theta.dtype))
             return theta.new_tensor(e)
 
         @staticmethod
         def backward(ctx, grad_out):
             (g,) = ctx.saved_tensors
-            return grad_out * g.to(grad_out.device), None, None, None
+            return grad_out * g.to(grad_out.device), None, None, None, None
 
     return Expval
 
@@ -626,9 +626,11 @@ def _make_expval_function():
 _Expval = None
 
 
-def expval(theta, psi0: State, gates, terms):
-    """Differentiable <H>: ``expval(theta, psi0, gates, (coeff, xmask, zmask))``."""
+def expval(theta, psi0: State, gates, terms, opts: QsPlanOpts | None = None):
+    """Differentiable <H>: ``expval(theta, psi0, gates, (coeff, xmask, zmask))``; ``opts``
+    (optional) plans the forward execution and sets the complex128 arithmetic of the
+    adjoint sweep (``qs_adjoint_grad_opts``)."""
     global _Expval
     if _Expval is None:
         _Expval = _make_expval_function()
-    return _Expval.apply(theta, psi0, gates, terms)
+    return _Expval.apply(theta, psi0, gates, terms, opts)

@@ -1004,3 +1004,26 @@ def test_phase_pass_complete_graph_many_terms(dtname):
         Q.qs_plan_free(plan)
     got = run(n, dt, gates, theta, opts=Q.make_opts())
     assert np.abs(got - ref(n, gates, theta)).max() <= TOL[dt]
+
+
+def test_torch_autograd_expval_with_options():
+    """Q.expval through torch.autograd: the value and theta.grad equal the
+    oracle's adjoint gradient, with the default plan and with complex128 FP32
+    pairs passed as plan options."""
+    import torch
+    n = 10
+    gates, p = W.hea(n, 3)
+    th0 = W.thetas_uniform(p, 41)
+    H = W.random_pauli_sum(n, 12, seed=42)
+    e_ref, g_ref = O.adjoint_grad(O.basis(n, 0), n, gates, th0, *H)
+    scale = np.abs(H[0]).sum()
+    psi0 = Q.State(n, "c128")
+    try:
+        for opts in (None, Q.make_opts(c128_pairs=1)):
+            theta = torch.tensor(th0, requires_grad=True)
+            e = Q.expval(theta, psi0, gates, H, opts)
+            e.backward()
+            assert abs(float(e) - e_ref) <= 1e-12 * scale * 10
+            assert np.abs(theta.grad.numpy() - g_ref).max() <= 1e-12 * scale * 10
+    finally:
+        psi0.free()
