@@ -203,6 +203,7 @@ qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const v
     upload(*p);
     cudaStream_t si = nullptr, sc = nullptr, so = nullptr;
     std::vector<cudaEvent_t> loaded(nwork, nullptr), computed(nwork, nullptr), stored(nwork, nullptr);
+    DevBuf dnorm;   // outlives the streams' work (freed after the synchronisations below)
     auto cleanup = [&]() {
       for (int b = 0; b < nwork; ++b) {
         if (loaded[b]) cudaEventDestroy(loaded[b]);
@@ -229,7 +230,6 @@ qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const v
       build_device_blocks(*p, 1, sc);
       // norms land in a device array read once at the end: a per-step copy into the
       // caller's (pageable) array would block this loop until that step's circuit ends
-      DevBuf dnorm;
       if (norms) dnorm.ensure(sizeof(double) * std::max(1, count));
       for (int i = 0; i < count; ++i) {
         const int b = i % nwork;
