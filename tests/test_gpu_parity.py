@@ -1023,7 +1023,7 @@ def test_torch_autograd_expval_with_options():
             theta = torch.tensor(th0, requires_grad=True)
             e = Q.expval(theta, psi0, gates, H, opts)
             e.backward()
-            assert abs(float(e) - e_ref) <= 1e-12 * scale * 10
+            assert abs(float(e.detach()) - e_ref) <= 1e-12 * scale * 10
             assert np.abs(theta.grad.numpy() - g_ref).max() <= 1e-12 * scale * 10
     finally:
         psi0.free()
