@@ -696,7 +696,8 @@ def config_qft30(Q, torch, np, st, args):
     out = {"workload": "QFT n=30, seeded basis input (H, controlled phases, final swaps)", "gates": len(g)}
     variants = {"c64": [("per_gate", None), ("fused_k4", Q.make_opts(mode=F, fuse_k=4)),
                         ("tensor", Q.make_opts(mode=T, tc_min_gates=2))],
-                "c128": [("per_gate", None), ("fused_k5", Q.make_opts(mode=F, fuse_k=5))]}
+                "c128": [("per_gate", None), ("fused_k5", Q.make_opts(mode=F, fuse_k=5)),
+                         ("fused_fp32_pairs", Q.make_opts(mode=F, fuse_k=2, c128_pairs=1))]}
     for dname, dt in (("c64", Q.QS_C64), ("c128", Q.QS_C128)):
         s = Q.qs_state_alloc(n, dt, st)
         res = {}
