@@ -39,6 +39,27 @@ def test_every_declared_symbol_is_exported_and_bound():
     assert "sm_103a" in Q.qs_version()
 
 
+def test_header_is_plain_c_and_links_from_c(tmp_path):
+    """The boundary is a C ABI: include/qsim_gb300.h compiles as strict C99
+    (no C++ types in any signature), and a C program links against the library
+    and calls an entry point that needs no device."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    src = tmp_path / "use_abi.c"
+    src.write_text('#include <stdio.h>\n#include "qsim_gb300.h"\n'
+                   "int main(void) { qs_plan_opts o = {0}; qs_stream_info si = {0}; (void)o; (void)si;\n"
+                   '  printf("%s\\n", qs_version()); return 0; }\n')
+    lib = Q.lib()._name
+    exe = tmp_path / "use_abi"
+    subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror", "-I", os.path.join(ROOT, "include"),
+                    str(src), lib, "-o", str(exe), "-Wl,-rpath," + os.path.dirname(lib)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout
+    assert "sm_103a" in out
+
+
 def test_no_gpu_means_an_error_not_a_fallback():
     import torch
     if torch.cuda.is_available():
