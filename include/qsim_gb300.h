@@ -20,7 +20,9 @@
  *   - Outputs are written only when the call returns QS_OK.
  *   - Device work is ordered on the state's stream. Calls that return host
  *     values (norm, expectation, gradient, copies to host) synchronise that
- *     stream before returning.
+ *     stream before returning. A call on two states whose streams differ
+ *     orders them with events: its work waits for what was queued on both,
+ *     and a state written by the call is ready on its own stream afterwards.
  *   - Errors: a negative qs_status; qs_last_error() returns a message for the
  *     calling thread. Invalid arguments (qubit >= n, repeated qubit in a gate,
  *     unknown kind, size mismatch) give QS_ERR_ARG before any device work.

@@ -350,7 +350,9 @@ qs_status qs_state_copy(qs_state_t dst, qs_state_t src) {
     check_state(dst);
     check_state(src);
     require(dst->n == src->n && dst->dt == src->dt, "states differ in n or dtype");
+    stream_after(dst->st, src->st);
     CK(cudaMemcpyAsync(dst->d, src->d, src->bytes(), cudaMemcpyDeviceToDevice, dst->st));
+    stream_after(src->st, dst->st);   // later writes of src wait for the copy
   });
 }
 
@@ -473,6 +475,7 @@ qs_status qs_inner(qs_state_t a, qs_state_t b, double* re, double* im) {
     check_state(b);
     require(a->n == b->n && a->dt == b->dt, "states differ in n or dtype");
     a->scratch.ensure(partial_bytes(2) + 2 * sizeof(double));
+    stream_after(a->st, b->st);
     double* d_part = a->scratch.as<double>();
     double* d_out = d_part + 2 * reduce_blocks();
     CK(launch_inner(a->d, b->d, a->n, a->dt, d_part, d_out, a->st));
@@ -526,6 +529,7 @@ qs_status qs_apply_pauli_sum(qs_state_t s, const qs_pauli_term* terms, size_t nt
     double2* dph;
     std::vector<unsigned char> host;
     upload_pauli_apply(terms, nterms, s->scratch2, s->st, &dx, &dz, &dph, host);
+    stream_after(s->st, out->st);
     CK(launch_apply_pauli(s->d, out->d, s->n, s->dt, dx, dz, (const double*)dph, (int)nterms, s->st));
     CK(cudaStreamSynchronize(s->st));
   });
@@ -611,12 +615,13 @@ qs_status qs_adjoint_grad_opts(qs_state_t s, const qs_gate* gates, size_t ngates
     std::vector<double> sums(rows + 2);
     CK(cudaMemcpyAsync(sums.data(), d_sum, sizeof(double) * (rows + 2), cudaMemcpyDeviceToHost, s->st));
     CK(cudaStreamSynchronize(s->st));
-    for (size_t j = 0; j < ntheta; ++j) grad_out[j] = 0;
+    std::vector<double> grad(ntheta, 0.0);   // outputs are written only on success
     for (int r = 0; r < rows; ++r) {
       const HGate& g = rp->gates[row_gate[r]];
       require((size_t)g.param_index < ntheta, "theta shorter than the parameter indices");
-      grad_out[g.param_index] += 2.0 * g.scale * sums[r];
+      grad[g.param_index] += 2.0 * g.scale * sums[r];
     }
+    std::copy(grad.begin(), grad.end(), grad_out);
     if (expval_out) *expval_out = sums[rows];
   });
 }
@@ -692,7 +697,8 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     std::vector<void*> ptrs(B);
     for (int b = 0; b < B; ++b) ptrs[b] = states[b]->d;
     p->d_psis.ensure(sizeof(void*) * B);
-    CK(cudaMemcpy(p->d_psis.p, ptrs.data(), sizeof(void*) * B, cudaMemcpyHostToDevice));
+    // ordered on the plan's stream: a replay still running there reads the previous table
+    CK(cudaMemcpyAsync(p->d_psis.p, ptrs.data(), sizeof(void*) * B, cudaMemcpyHostToDevice, st));
     void* const* d_psis = (void* const*)p->d_psis.p;
     std::vector<void*> key = ptrs;
     key.push_back((void*)(uintptr_t)ntheta);

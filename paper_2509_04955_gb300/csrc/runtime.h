@@ -90,6 +90,18 @@ struct DevBuf {
 
 inline size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
 
+// Makes later work on `waiter` wait for everything queued on `producer` so far
+// (two states on different streams); nothing to do when they are one stream.
+inline void stream_after(cudaStream_t waiter, cudaStream_t producer) {
+  if (waiter == producer) return;
+  cudaEvent_t e;
+  CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+  cudaError_t r = cudaEventRecord(e, producer);
+  if (r == cudaSuccess) r = cudaStreamWaitEvent(waiter, e, 0);
+  cudaEventDestroy(e);   // released once the wait has been satisfied
+  CK(r);
+}
+
 }  // namespace rt
 }  // namespace qs
 

@@ -1027,3 +1027,46 @@ def test_torch_autograd_expval_with_options():
             assert np.abs(theta.grad.numpy() - g_ref).max() <= 1e-12 * scale * 10
     finally:
         psi0.free()
+
+
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+def test_two_states_on_two_streams(dtname):
+    """Copy, inner product and Pauli apply between states on different non-blocking
+    streams: the circuit queued on the source's stream (no host wait) must be
+    complete when the other stream reads it."""
+    import torch
+    dt = DT[dtname]
+    n = 18
+    gates = W.random_layered(n, 30, seed=3)
+    theta = None
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    a = Q.qs_state_alloc(n, dt, C_stream(sa))
+    b = Q.qs_state_alloc(n, dt, C_stream(sb))
+    c = Q.qs_state_alloc(n, dt, C_stream(sb))
+    plan = Q.qs_plan_create(n, dt, gates, Q.make_opts(mode=Q.QS_MODE_PER_GATE))
+    try:
+        want = ref(n, gates, theta)
+        Q.qs_plan_execute(plan, a, theta)          # queued on stream a only
+        Q.qs_state_copy(b, a)                      # ordered on stream b
+        out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+        Q.qs_state_copy_to_host(b, out)
+        assert np.abs(out - want).max() <= TOL[dt]
+        Q.qs_state_set_basis(a, 0)
+        Q.qs_plan_execute(plan, a, theta)          # a again holds C|0>, queued on stream a
+        ip = Q.qs_inner(b, a)                      # runs on stream b
+        assert abs(ip - 1.0) <= (1e-10 if dt == Q.QS_C128 else 1e-4)
+        coeff, xm, zm = np.array([1.0]), np.array([1], dtype=np.uint64), np.array([0], dtype=np.uint64)
+        Q.qs_state_set_basis(a, 0)
+        Q.qs_plan_execute(plan, a, theta)
+        Q.qs_apply_pauli_sum(a, coeff, xm, zm, c)  # output c on stream b, written on stream a
+        Q.qs_state_copy_to_host(c, out)
+        assert np.abs(out - O.apply_pauli_sum(want, n, coeff, xm, zm)).max() <= TOL[dt]
+    finally:
+        Q.qs_plan_free(plan)
+        for h in (a, b, c):
+            Q.qs_state_free(h)
+
+
+def C_stream(s):
+    import ctypes
+    return ctypes.c_void_p(s.cuda_stream)
