@@ -646,6 +646,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     upload(*p);
     CK(cudaEventRecord(p->ev_in, user_st));
     CK(cudaStreamWaitEvent(st, p->ev_in, 0));
+    plan_wait(*p, st);
     ensure_gtab_rows(*p, B);
     ensure_block_rows(*p, B);
     // theta upload happens outside the graph; the graph reads p->d_theta
@@ -779,6 +780,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     }
     CK(cudaEventRecord(p->ev_out, st));
     CK(cudaStreamWaitEvent(user_st, p->ev_out, 0));
+    plan_done(*p, st);
     if (!p->tcdesc.empty()) {
       int err = 0;
       CK(cudaMemcpyAsync(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));

@@ -118,6 +118,17 @@ void upload(qs_plan_s& p) {
 
 void check_state(const qs_state_s* s) { require(s != nullptr && s->d != nullptr, "null state"); }
 
+// An event (not the previous stream itself, which the caller may have destroyed
+// since) orders executions of one plan on different streams.
+void plan_wait(qs_plan_s& p, cudaStream_t st) {
+  if (p.ev_done) CK(cudaStreamWaitEvent(st, p.ev_done, 0));
+}
+
+void plan_done(qs_plan_s& p, cudaStream_t st) {
+  if (!p.ev_done) CK(cudaEventCreateWithFlags(&p.ev_done, cudaEventDisableTiming));
+  CK(cudaEventRecord(p.ev_done, st));
+}
+
 // Issues the kernels of one circuit execution on `st` for batch row `row` of
 // the gate table (theta already resolved into it).
 void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed) {
@@ -225,9 +236,11 @@ void resolve_theta(qs_plan_s& p, const double* theta, size_t ntheta, int rows, c
 void execute(qs_plan_s& p, qs_state_s& s, const double* theta, size_t ntheta) {
   require(p.n == s.n && p.dt == s.dt, "plan and state differ in qubit count or dtype");
   upload(p);
+  plan_wait(p, s.st);
   resolve_theta(p, theta, ntheta, 1, s.st);
   build_device_blocks(p, 1, s.st);
   issue_circuit(p, s.d, 0, s.st, p.timing);
+  plan_done(p, s.st);
   if (!p.tcdesc.empty()) {
     int err = 0;
     CK(cudaMemcpyAsync(&err, p.d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s.st));

@@ -180,6 +180,9 @@ struct qs_plan_s {
   std::vector<void*> graph_key;
   cudaStream_t cap_stream = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  // recorded after each execution's last use of the device tables; the next
+  // execution, on whatever stream, waits for it before it rewrites them
+  cudaEvent_t ev_done = nullptr;
   DevBuf d_psis;                   // state pointers of the batch
   int64_t graph_launches = 0;      // kernel launches in one replay of the graph
   // measurement: events bracketing each launch of qs_plan_execute
@@ -192,6 +195,7 @@ struct qs_plan_s {
     for (cudaEvent_t e : events) cudaEventDestroy(e);
     if (ev_in) cudaEventDestroy(ev_in);
     if (ev_out) cudaEventDestroy(ev_out);
+    if (ev_done) cudaEventDestroy(ev_done);
     if (cap_stream) cudaStreamDestroy(cap_stream);
   }
   cudaEvent_t next_event() {
@@ -230,6 +234,8 @@ void ensure_block_rows(qs_plan_s& p, int rows);
 void build_device_blocks(qs_plan_s& p, int rows, cudaStream_t st);
 void upload(qs_plan_s& p);
 void check_state(const qs_state_s* s);
+void plan_wait(qs_plan_s& p, cudaStream_t st);   // st waits for the plan's previous execution
+void plan_done(qs_plan_s& p, cudaStream_t st);   // marks the end of this execution on st
 void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed = false);
 int batched_wave(const qs_plan_s& p, int B);
 void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_t st,

@@ -226,6 +226,7 @@ qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const v
         CK(cudaEventRecord(stored[b], work[b]->st));
         work[b]->scratch.ensure(partial_bytes(1) + sizeof(double));
       }
+      plan_wait(*p, sc);
       resolve_theta(*p, theta, ntheta, 1, sc);
       build_device_blocks(*p, 1, sc);
       // norms land in a device array read once at the end: a per-step copy into the

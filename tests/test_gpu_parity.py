@@ -1067,6 +1067,33 @@ def test_two_states_on_two_streams(dtname):
             Q.qs_state_free(h)
 
 
+@pytest.mark.parametrize("dtname", ["c128", "c64"])
+def test_one_plan_executed_on_two_streams(dtname):
+    """One parametric plan run back to back on states with different streams and
+    different parameters: the second execution rewrites the plan's gate table and
+    theta rows only after the first has used them."""
+    import torch
+    dt = DT[dtname]
+    n = 17
+    gates, p = W.hea(n, 6)
+    t1, t2 = W.thetas_uniform(p, 1), W.thetas_uniform(p, 2)
+    sa, sb = torch.cuda.Stream(), torch.cuda.Stream()
+    a = Q.qs_state_alloc(n, dt, C_stream(sa))
+    b = Q.qs_state_alloc(n, dt, C_stream(sb))
+    plan = Q.qs_plan_create(n, dt, gates, Q.make_opts(fuse_k=2))
+    try:
+        Q.qs_plan_execute(plan, a, t1)
+        Q.qs_plan_execute(plan, b, t2)
+        for h, th in ((a, t1), (b, t2)):
+            out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+            Q.qs_state_copy_to_host(h, out)
+            assert np.abs(out - ref(n, gates, th)).max() <= TOL[dt]
+    finally:
+        Q.qs_plan_free(plan)
+        Q.qs_state_free(a)
+        Q.qs_state_free(b)
+
+
 def C_stream(s):
     import ctypes
     return ctypes.c_void_p(s.cuda_stream)
