@@ -119,12 +119,15 @@ void upload(qs_plan_s& p) {
 void check_state(const qs_state_s* s) { require(s != nullptr && s->d != nullptr, "null state"); }
 
 // An event (not the previous stream itself, which the caller may have destroyed
-// since) orders executions of one plan on different streams.
+// since) orders executions of one plan on different streams. Inside a caller's
+// stream capture the event is left alone (see capturing()).
+
 void plan_wait(qs_plan_s& p, cudaStream_t st) {
-  if (p.ev_done) CK(cudaStreamWaitEvent(st, p.ev_done, 0));
+  if (p.ev_done && !capturing(st)) CK(cudaStreamWaitEvent(st, p.ev_done, 0));
 }
 
 void plan_done(qs_plan_s& p, cudaStream_t st) {
+  if (capturing(st)) return;
   if (!p.ev_done) CK(cudaEventCreateWithFlags(&p.ev_done, cudaEventDisableTiming));
   CK(cudaEventRecord(p.ev_done, st));
 }

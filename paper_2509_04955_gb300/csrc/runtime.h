@@ -90,10 +90,23 @@ struct DevBuf {
 
 inline size_t amp_bytes(qs_dtype dt) { return dt == QS_C64 ? 8 : 16; }
 
+// True while `st` is being captured into a CUDA graph by the caller. The
+// library's cross-stream events stay out of such captures: a captured wait on
+// an event recorded outside the capture is not allowed, and the graph orders
+// its own launches.
+inline bool capturing(cudaStream_t st) {
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cs) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return cs != cudaStreamCaptureStatusNone;
+}
+
 // Makes later work on `waiter` wait for everything queued on `producer` so far
 // (two states on different streams); nothing to do when they are one stream.
 inline void stream_after(cudaStream_t waiter, cudaStream_t producer) {
-  if (waiter == producer) return;
+  if (waiter == producer || capturing(waiter) || capturing(producer)) return;
   cudaEvent_t e;
   CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
   cudaError_t r = cudaEventRecord(e, producer);
