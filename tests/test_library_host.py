@@ -177,10 +177,15 @@ def test_paper_mode_compression_on_hea():
     info = Q.qs_plan_info_get(plan)
     ratio = (info["gates"] - info["blocks"]) / info["gates"]
     assert 0.3 < ratio < 0.95
-    U, _ = plan_unitary(6, gates[:40] if False else [g for g in gates if max(g.qubits) < 6], Q.qs_plan_create(
-        6, Q.QS_C128, [g for g in gates if max(g.qubits) < 6], Q.make_opts(paper_mode=1, tile_qubits=6, low_qubits=1)))
-    assert np.abs(U - O.unitary(6, [g for g in gates if max(g.qubits) < 6])).max() < 1e-12
     Q.qs_plan_free(plan)
+    # the same merges on the circuit's first six qubits reproduce its unitary
+    small = [g for g in gates if max(g.qubits) < 6]
+    plan = Q.qs_plan_create(6, Q.QS_C128, small, Q.make_opts(paper_mode=1, tile_qubits=6, low_qubits=1))
+    try:
+        U, _ = plan_unitary(6, small, plan)
+        assert np.abs(U - O.unitary(6, small)).max() < 1e-12
+    finally:
+        Q.qs_plan_free(plan)
 
 
 def phase_diagonal(n, terms, theta):
@@ -337,3 +342,59 @@ def test_tensor_mode_plan_matches_oracle_on_a_state():
     with pytest.raises(Q.QsError) as e:
         Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR))
     assert e.value.status == Q.QS_ERR_UNSUPPORTED
+
+
+def test_planner_fuzz_ops_reproduce_the_circuit():
+    """Seeded sweep over circuits (random mixes with controls, layers, QFT, QAOA,
+    diagonal runs, HEA with parameters) and plan options (contraction width,
+    tile width, low qubits, paper mode, phase runs on or off, SMGP): in every
+    plan each gate is applied exactly once and the ops applied with numpy, in
+    plan order, reproduce the oracle's gate-by-gate state."""
+    rng = np.random.default_rng(2509)
+    seen = set()
+    for case in range(48):
+        kind = ("mix", "layered", "qft", "qaoa", "phase", "hea")[case % 6]
+        # phase runs need a 4096-amplitude chunk (n >= 12)
+        n = 12 + case % 2 if kind in ("qaoa", "phase") else int(rng.integers(3, 10))
+        theta = None
+        if kind == "mix":
+            gates = W.random_gate_mix(n, 40, seed=case)
+        elif kind == "layered":
+            gates = W.random_layered(n, 4, seed=case, entangler=("cnot", "cz")[case % 2])
+        elif kind == "qft":
+            gates = W.qft(n)
+        elif kind == "qaoa":
+            gates, p = W.qaoa(n, 2, [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < 0.4])
+            theta = W.thetas_uniform(max(p, 1), case)
+        elif kind == "phase":
+            gates, p = W.phase_run_circuit(n, 2, 12, seed=case, max_weight=min(4, n))
+            theta = W.thetas_uniform(max(p, 1), case)
+        else:
+            gates, p = W.hea(n, 2)
+            theta = W.thetas_uniform(p, case)
+        L = int(rng.integers(1, min(3, n - 1) + 1))
+        k = int(rng.integers(1, min(5, n - L) + 1))
+        m = int(rng.integers(L + k, n + 1))          # a tile holds the low qubits plus a block
+        pick = (case // 6) % 4                    # every circuit kind meets every option set
+        dt = (Q.QS_C64, Q.QS_C128)[case % 2]       # the cost rule differs: more dense blocks in complex64
+        if pick == 0:
+            opts = Q.make_opts(fuse_k=k, tile_qubits=m, low_qubits=L, phase_min_gates=4)
+        elif pick == 1:
+            opts = Q.make_opts(fuse_k=k, tile_qubits=m, low_qubits=L, phase_min_gates=-1)
+        elif pick == 2:
+            opts = Q.make_opts(paper_mode=1, fuse_k=k, tile_qubits=m, low_qubits=L)
+        else:
+            opts = Q.make_opts(mode=Q.QS_MODE_SMGP)
+        plan = Q.qs_plan_create(n, dt, gates, opts)
+        try:
+            ops = Q.qs_plan_ops(plan)
+            seen.update(op["type"] for op in ops)
+            per_gate = [op["gate"] for op in ops if op["type"] == 0]
+            assert len(per_gate) == len(set(per_gate)), (case, kind)
+            psi = W.random_state(n, case)
+            got = apply_plan_ops(psi, n, gates, plan, theta)
+            want = O.apply_circuit(psi, n, gates, theta)
+            assert np.abs(got - want).max() < 1e-12, (case, kind, n, pick)
+        finally:
+            Q.qs_plan_free(plan)
+    assert seen == {0, 1, 2, 4}, seen     # per-gate, dense block, diagonal block, phase run
