@@ -193,10 +193,12 @@ static bool paper_mergeable(const HGate& a, const HGate& b, uint64_t Q) {
 // One greedy scan from `first`: absorbs later gates that commute with every
 // gate skipped so far and keep the block within kcap qubits (and within
 // `allowed`, when given). Returns the absorbed gates in program order.
-static std::vector<int> scan_block(const std::vector<HGate>& gates, const std::vector<char>& done, int first,
-                                   int kcap, uint64_t allowed, const PlanOptions& o, uint64_t all) {
+// With `members` NULL only the count is returned (the growth searches).
+static int scan_block(const std::vector<HGate>& gates, const std::vector<char>& done, int first, int kcap,
+                      uint64_t allowed, const PlanOptions& o, uint64_t all, std::vector<int>* members) {
   const int G = (int)gates.size();
-  std::vector<int> members{first};
+  if (members) members->assign(1, first);
+  int count = 1;
   uint64_t Q = gates[first].qmask, blk_nd = 0, blk_d = 0;
   const bool lone = !o.fuse_parametric && gates[first].parametric;   // stays a gate op
   for (int h = first + 1; h < G && !lone; ++h) {
@@ -206,18 +208,28 @@ static std::vector<int> scan_block(const std::vector<HGate>& gates, const std::v
     const bool movable = (qh & blk_nd) == 0 && (qh & blk_d & ~gh.dmask) == 0;
     bool ok = movable && popc(Q | qh) <= kcap && (qh & ~allowed) == 0;
     if (ok && !o.fuse_parametric && gh.parametric) ok = false;
-    if (ok && o.paper) ok = paper_mergeable(gates[members[0]], gh, Q);
+    if (ok && o.paper) ok = paper_mergeable(gates[first], gh, Q);
     if (ok) {
-      members.push_back(h);
+      if (members) members->push_back(h);
+      ++count;
       Q |= qh;
     } else {
       blk_nd |= qh & ~gh.dmask;
       blk_d |= qh & gh.dmask;
     }
-    if (blk_nd == all) break;
+    // no later gate can join once every admissible qubit is blocked by a skipped
+    // gate that is not diagonal there, or the block is full and all of it blocked
+    if ((allowed & all & ~blk_nd) == 0) break;
     if (popc(Q) >= kcap && (Q & ~blk_nd) == 0) break;
   }
-  return members;
+  return count;
+}
+
+static std::vector<int> scan_members(const std::vector<HGate>& gates, const std::vector<char>& done, int first,
+                                     int kcap, uint64_t allowed, const PlanOptions& o, uint64_t all) {
+  std::vector<int> m;
+  scan_block(gates, done, first, kcap, allowed, o, all, &m);
+  return m;
 }
 
 // Qubit set planned from the next unemitted gates: starting from the first
@@ -261,7 +273,7 @@ static uint64_t grow_qubits(const std::vector<HGate>& gates, const std::vector<c
     size_t best = 0;
     for (int q = 0; q < n; ++q) {
       if ((Q & (1ull << q)) || !(cand & (1ull << q))) continue;
-      const size_t c = scan_block(gates, done, first, kcap, Q | (1ull << q), o, all).size();
+      const size_t c = (size_t)scan_block(gates, done, first, kcap, Q | (1ull << q), o, all, nullptr);
       if (c > best) { best = c; best_q = q; }
     }
     if (best_q < 0) break;
@@ -288,14 +300,14 @@ static uint64_t grow_qubits_pairs(const std::vector<HGate>& gates, const std::ve
     for (size_t i = 0; i < cq.size(); ++i) {
       const uint64_t a = 1ull << cq[i];
       if (Q & a) continue;
-      const double c1 = (double)scan_block(gates, done, first, kcap, Q | a, o, all).size();
+      const double c1 = (double)scan_block(gates, done, first, kcap, Q | a, o, all, nullptr);
       if (c1 > best) { best = c1; best_add = a; }
       if (popc(Q) + 2 > kcap) continue;
       for (size_t j = i + 1; j < cq.size(); ++j) {
         const uint64_t b2 = 1ull << cq[j];
         if (Q & b2) continue;
         // a pair costs two slots: compare per added qubit, favouring progress
-        const double c2 = (double)scan_block(gates, done, first, kcap, Q | a | b2, o, all).size();
+        const double c2 = (double)scan_block(gates, done, first, kcap, Q | a | b2, o, all, nullptr);
         if (c2 - 0.5 > best) { best = c2 - 0.5; best_add = a | b2; }
       }
     }
@@ -323,16 +335,16 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
     if (first >= G) break;
     Block blk;
     const int kcap = o.paper ? 2 : std::max(o.k, popc(gates[first].qmask));
-    std::vector<int> a = o.no_merge ? std::vector<int>{first} : scan_block(gates, done, first, kcap, all, o, all);
+    std::vector<int> a = o.no_merge ? std::vector<int>{first} : scan_members(gates, done, first, kcap, all, o, all);
     if (!o.no_merge && !o.paper && kcap > 2 && (o.fuse_parametric || !gates[first].parametric)) {
-      std::vector<int> b = scan_block(gates, done, first, kcap, plan_qubits(gates, done, first, kcap, n), o, all);
+      std::vector<int> b = scan_members(gates, done, first, kcap, plan_qubits(gates, done, first, kcap, n), o, all);
       if (b.size() > a.size()) a.swap(b);
       if (o.search) {
-        std::vector<int> c = scan_block(gates, done, first, kcap, grow_qubits(gates, done, first, kcap, n, o, all), o, all);
+        std::vector<int> c = scan_members(gates, done, first, kcap, grow_qubits(gates, done, first, kcap, n, o, all), o, all);
         if (c.size() > a.size()) a.swap(c);
         if (n <= 40 && gates.size() <= 40000) {
-          std::vector<int> d = scan_block(gates, done, first, kcap, grow_qubits_pairs(gates, done, first, kcap, n, o, all),
-                                          o, all);
+          std::vector<int> d = scan_members(gates, done, first, kcap,
+                                            grow_qubits_pairs(gates, done, first, kcap, n, o, all), o, all);
           if (d.size() > a.size()) a.swap(d);
         }
       }
@@ -411,19 +423,27 @@ void block_matrix(const Block& b, const std::vector<HGate>& gates, const double*
       if (b.qubits[j] == q) return j;
     throw Error(QS_ERR_ARG, "internal: qubit not in block");
   };
+  // each member's matrix and block-local positions, once
+  struct Local {
+    cd m[16];
+    int lt[2];
+    uint64_t lc;
+  };
+  std::vector<Local> loc(b.gates.size());
+  for (size_t i = 0; i < b.gates.size(); ++i) {
+    const HGate& g = gates[b.gates[i]];
+    target_matrix(g, theta, loc[i].m);
+    loc[i].lt[0] = local(g.t[0]);
+    loc[i].lt[1] = g.nt == 2 ? local(g.t[1]) : 0;
+    loc[i].lc = 0;
+    for (int j = 0; j < g.nc; ++j) loc[i].lc |= 1ull << local(g.c[j]);
+  }
   std::vector<cd> col(D);
   for (uint64_t c = 0; c < D; ++c) {
     std::fill(col.begin(), col.end(), cd(0));
     col[c] = 1;
-    for (int gi : b.gates) {
-      const HGate& g = gates[gi];
-      cd m[16];
-      target_matrix(g, theta, m);
-      int lt[2] = {local(g.t[0]), g.nt == 2 ? local(g.t[1]) : 0};
-      uint64_t lc = 0;
-      for (int j = 0; j < g.nc; ++j) lc |= 1ull << local(g.c[j]);
-      apply_local(g, lt, lc, m, col.data(), k);
-    }
+    for (size_t i = 0; i < b.gates.size(); ++i)
+      apply_local(gates[b.gates[i]], loc[i].lt, loc[i].lc, loc[i].m, col.data(), k);
     for (uint64_t r = 0; r < D; ++r) M[r * D + c] = col[r];
   }
 }
