@@ -425,7 +425,8 @@ def main():
         try:
             tp = json.load(open(prof)).get(tc_kernel if tc_dom else "k_tile", {})
             if tp.get("kernel_hash") == kernel_hash(tc_kernel if tc_dom else "k_tile"):
-                traffic = tp.get("bytes_per_launch_n30")
+                # per launch at this n: traffic is proportional to the amplitudes swept
+                traffic = tp.get("bytes_per_launch_n30") * 2.0 ** (n - 30)
         except (ValueError, OSError):
             traffic = None
     cfg = {"workload": workload_desc(args, len(gates)) + f", complex64, {mode_name(Q, kw)} plan",
