@@ -23,6 +23,10 @@
  *     stream before returning. A call on two states whose streams differ
  *     orders them with events: its work waits for what was queued on both,
  *     and a state written by the call is ready on its own stream afterwards.
+ *   - A plan holds device tables (gate matrices, parameter rows, a CUDA graph)
+ *     that each execution rewrites: one thread at a time may use a plan.
+ *     Executions of one plan on states with different streams are ordered by
+ *     the plan itself (each waits for the previous one's device work).
  *   - Errors: a negative qs_status; qs_last_error() returns a message for the
  *     calling thread. Invalid arguments (qubit >= n, repeated qubit in a gate,
  *     unknown kind, size mismatch) give QS_ERR_ARG before any device work.
