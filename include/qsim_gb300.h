@@ -284,6 +284,16 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B,
                                   const double* theta, size_t ntheta,
                                   const qs_pauli_term* terms, size_t nterms, double* expvals);
 
+/* One-shot batched apply: plans the circuit for the states' n and dtype with
+ * opts (NULL = per-gate mode, as for qs_plan_create), applies it to the B
+ * states with row b of theta (B x ntheta, row-major; NULL when the circuit
+ * has no parameters) driving state b, synchronises the states' stream and
+ * frees the plan. The states must share n, dtype and stream (QS_ERR_ARG
+ * otherwise). For repeated batches keep a plan and call
+ * qs_plan_execute_batched, which replays its captured graph. */
+qs_status qs_apply_circuit_batched(qs_state_t* states, int B, const qs_gate* gates, size_t ngates,
+                                   const double* theta, size_t ntheta, const qs_plan_opts* opts);
+
 /* ---------------- allocation-free expectation value ----------------
  * The paper has no counterpart: this is a deployment variant of
  * qs_expval_pauli_sum for callers that cannot allocate device memory while

@@ -119,6 +119,8 @@ _SIGS = {
     "qs_plan_timing_read_kinds": (C.c_int, [_VP, _DP, _I64P, _DP, _I64P]),
     "qs_expval_pauli_sum_noalloc": (C.c_int, [_VP, C.c_int, C.c_int, _VP, C.POINTER(QsPauliTerm), C.c_size_t,
                                               _DP]),
+    "qs_apply_circuit_batched": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t,
+                                           C.POINTER(QsPlanOpts)]),
     "qs_last_error": (C.c_char_p, []),
     "qs_launch_count": (C.c_int64, []),
     "qs_version": (C.c_char_p, []),
@@ -432,6 +434,19 @@ def qs_plan_execute_batched(plan: int, states: list[int], theta=None, terms=None
     _check(lib().qs_plan_execute_batched(plan, arr, B, th.ctypes.data_as(_DP) if th is not None else None, nt,
                                          tp, ntm, ex.ctypes.data_as(_DP) if terms is not None else None))
     return ex if terms is not None else None
+
+
+def qs_apply_circuit_batched(states: list[int], gates, theta=None, opts: QsPlanOpts | None = None):
+    """One-shot: plan, apply to every state with its own theta row, free."""
+    B = len(states)
+    arr = (_VP * B)(*states)
+    th, nt = (None, 0)
+    if theta is not None:
+        th = np.ascontiguousarray(theta, dtype=np.float64).reshape(B, -1)
+        nt = th.shape[1]
+    _check(lib().qs_apply_circuit_batched(arr, B, pack_gates(gates), len(gates),
+                                          th.ctypes.data_as(_DP) if th is not None else None, nt,
+                                          C.byref(opts) if opts is not None else None))
 
 
 def qs_plan_check_device_blocks(plan: int, state: int, theta) -> tuple[float, int]:

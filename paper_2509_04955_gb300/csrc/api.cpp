@@ -794,4 +794,16 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
   });
 }
 
+qs_status qs_apply_circuit_batched(qs_state_t* states, int B, const qs_gate* gates, size_t ngates,
+                                   const double* theta, size_t ntheta, const qs_plan_opts* opts) {
+  return guard([&] {
+    require(states != nullptr && B >= 1, "bad arguments");
+    check_state(states[0]);
+    std::unique_ptr<qs_plan_s> p(create_plan(states[0]->n, states[0]->dt, gates, ngates, opts));
+    const qs_status st = qs_plan_execute_batched(p.get(), states, B, theta, ntheta, nullptr, 0, nullptr);
+    if (st != QS_OK) throw Error(st, g_err);
+    CK(cudaStreamSynchronize(states[0]->st));   // the plan's device tables are freed on return
+  });
+}
+
 }  // extern "C"

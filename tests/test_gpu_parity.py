@@ -1094,6 +1094,31 @@ def test_one_plan_executed_on_two_streams(dtname):
         Q.qs_state_free(b)
 
 
+@pytest.mark.parametrize("dtname,n,opts", [("c128", 11, None), ("c64", 11, None),
+                                            ("c128", 11, Q.make_opts(fuse_k=2)),
+                                            ("c64", 13, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4,
+                                                                    fuse_parametric=1))])
+def test_one_shot_batched_apply(dtname, n, opts):
+    """qs_apply_circuit_batched: plan, B states each with its own parameter row,
+    free; every state equals the oracle with that row."""
+    dt = DT[dtname]
+    gates, p = W.hea(n, 3)
+    B = 3
+    theta = np.stack([W.thetas_uniform(p, 10 + b) for b in range(B)])
+    hs = [Q.qs_state_alloc(n, dt) for _ in range(B)]
+    try:
+        for b, h in enumerate(hs):
+            Q.qs_state_set_basis(h, b)
+        Q.qs_apply_circuit_batched(hs, gates, theta, opts)
+        for b, h in enumerate(hs):
+            out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+            Q.qs_state_copy_to_host(h, out)
+            assert np.abs(out - ref(n, gates, theta[b], basis=b)).max() <= TOL[dt]
+    finally:
+        for h in hs:
+            Q.qs_state_free(h)
+
+
 def C_stream(s):
     import ctypes
     return ctypes.c_void_p(s.cuda_stream)
