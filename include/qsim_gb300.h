@@ -200,7 +200,8 @@ qs_status qs_state_get_amplitudes(qs_state_t s, const uint64_t* idx, size_t coun
  * included), contracts it greedily into blocks of <= fuse_k qubits whose
  * unitary is the ordered product (Eq. 7 for distinct qubits, M2 M1 for the
  * same qubit), and groups blocks into tile passes. opts NULL = per-gate mode.
- * Parametric gates are resolved at execution time from theta. */
+ * Parametric gates are resolved at execution time from theta. More than 2^30
+ * gates give QS_ERR_ARG. */
 qs_status qs_plan_create(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates,
                          const qs_plan_opts* opts, qs_plan_t* out);
 qs_status qs_plan_info_get(qs_plan_t p, qs_plan_info* info);

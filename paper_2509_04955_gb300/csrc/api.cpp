@@ -381,6 +381,7 @@ qs_status qs_plan_autotune(qs_state_t s, const qs_gate* gates, size_t ngates, co
     check_state(s);
     require(best != nullptr, "best is NULL");
     require(ngates == 0 || gates != nullptr, "gates is NULL");
+    require(ngates <= kMaxGates, "too many gates (at most 2^30 per circuit)");
     std::vector<uint64_t> key{(uint64_t)s->n, (uint64_t)s->dt, (uint64_t)ngates,
                               fnv1a(gates, sizeof(qs_gate) * ngates)};
     {

@@ -80,6 +80,7 @@ void target_matrix(const HGate& g, const double* theta, cd* m) {
 }
 
 void resolve_gates(int n, const qs_gate* gs, size_t ng, std::vector<HGate>& out) {
+  if (ng > kMaxGates) throw Error(QS_ERR_ARG, "too many gates (at most 2^30 per circuit)");
   out.clear();
   out.reserve(ng);
   for (size_t i = 0; i < ng; ++i) {

@@ -27,6 +27,9 @@ struct HGate {
 };
 
 // Validates and resolves the caller's gates. Throws qs::Error on bad input.
+// Gates of one circuit are indexed with 32-bit integers: longer lists are an
+// argument error.
+constexpr size_t kMaxGates = size_t(1) << 30;
 void resolve_gates(int n, const qs_gate* g, size_t ng, std::vector<HGate>& out);
 // Target matrix (2x2 or 4x4 row-major) for given theta (may be null when not parametric).
 void target_matrix(const HGate& g, const double* theta, cd* m);

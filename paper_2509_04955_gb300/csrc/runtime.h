@@ -13,6 +13,7 @@
 #include <memory>
 #include <mutex>
 #include <new>
+#include <stdexcept>
 #include <string>
 #include <vector>
 
@@ -48,6 +49,9 @@ qs_status guard(F&& f) {
     return e.code;
   } catch (const std::bad_alloc&) {
     g_err = "host allocation failed";
+    return QS_ERR_OOM;
+  } catch (const std::length_error& e) {   // a host container asked for more than it can hold
+    g_err = std::string("host allocation too large: ") + e.what();
     return QS_ERR_OOM;
   } catch (const std::exception& e) {
     g_err = e.what();

@@ -88,6 +88,22 @@ def test_theta_bounds_and_options_are_validated():
         Q.qs_plan_create(10, Q.QS_C64, W.qft(10), Q.make_opts(tile_qubits=15))
 
 
+def test_gate_count_limit_is_checked_before_the_list_is_read():
+    """A gate count above 2^30 (the planner's 32-bit gate indices) is an argument
+    error raised before any gate is read: the one-gate array passed here is never
+    read past its end."""
+    import ctypes
+    one = Q.pack_gates([W.Gate("h", (0,))])
+    h = ctypes.c_void_p()
+    for create in ("plan", "stream"):
+        if create == "plan":
+            st = Q.lib().qs_plan_create(4, Q.QS_C64, one, (1 << 30) + 1, None, ctypes.byref(h))
+        else:
+            st = Q.lib().qs_stream_plan(4, one, (1 << 30) + 1, 2, 1, None, None, None, 0, None)
+        assert st == Q.QS_ERR_ARG
+        assert "too many gates" in Q.lib().qs_last_error().decode()
+
+
 # ------------------------------------------------------------- planner algebra
 
 def apply_block(psi, n, qubits, M):
