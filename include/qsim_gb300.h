@@ -233,9 +233,33 @@ qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const v
  * thresholds), runs each once to warm up and once timed with CUDA events on
  * the state's stream (the state's contents are overwritten), and writes the
  * fastest options to *best and its time to *best_ms (may be NULL). Results
- * are cached for the process per (n, dtype, gate list). Synchronises. */
+ * are cached per (n, dtype, gate list): a cached circuit is not timed again,
+ * and the cache can be saved to and loaded from a file (below). Synchronises. */
 qs_status qs_plan_autotune(qs_state_t scratch, const qs_gate* gates, size_t ngates, const double* theta,
                            size_t ntheta, qs_plan_opts* best, double* best_ms);
+
+/* The autotuner's cache, kept across processes (no counterpart in the paper).
+ * Entries are keyed by (n, dtype, gate count, a hash of the fields each gate
+ * uses: targets up to nq, controls up to nctrl, the angle and parameter
+ * binding of rotations, the matrix of U1/U2), so unused fields do not matter.
+ *   qs_tune_cache_lookup: host only; *found = 1 and *best / *best_ms (each may
+ *     be NULL) when the circuit has an entry, else *found = 0.
+ *   qs_tune_cache_put: records options for a circuit (a deployment's known
+ *     choice); they must plan it (else the qs_plan_create error); ms >= 0.
+ *   qs_tune_cache_save: writes every entry as text (path: a file name;
+ *     *entries may be NULL); QS_ERR_ARG when the file cannot be written.
+ *   qs_tune_cache_load: merges a saved file into the cache (its entries
+ *     replace equal keys); a malformed file or out-of-range value gives
+ *     QS_ERR_ARG and leaves the cache unchanged.
+ *   qs_tune_cache_clear: empties the cache.
+ * All are thread-safe. */
+qs_status qs_tune_cache_lookup(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates, qs_plan_opts* best,
+                               double* best_ms, int* found);
+qs_status qs_tune_cache_put(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates, const qs_plan_opts* opts,
+                            double ms);
+qs_status qs_tune_cache_save(const char* path, int64_t* entries);
+qs_status qs_tune_cache_load(const char* path, int64_t* entries);
+qs_status qs_tune_cache_clear(void);
 
 /* One-shot: plan, execute, free. */
 qs_status qs_apply_circuit(qs_state_t s, const qs_gate* gates, size_t ngates,

@@ -121,6 +121,13 @@ _SIGS = {
                                               _DP]),
     "qs_apply_circuit_batched": (C.c_int, [C.POINTER(_VP), C.c_int, C.POINTER(QsGate), C.c_size_t, _DP, C.c_size_t,
                                            C.POINTER(QsPlanOpts)]),
+    "qs_tune_cache_lookup": (C.c_int, [C.c_int, C.c_int, C.POINTER(QsGate), C.c_size_t, C.POINTER(QsPlanOpts), _DP,
+                                       C.POINTER(C.c_int)]),
+    "qs_tune_cache_put": (C.c_int, [C.c_int, C.c_int, C.POINTER(QsGate), C.c_size_t, C.POINTER(QsPlanOpts),
+                                    C.c_double]),
+    "qs_tune_cache_save": (C.c_int, [C.c_char_p, _I64P]),
+    "qs_tune_cache_load": (C.c_int, [C.c_char_p, _I64P]),
+    "qs_tune_cache_clear": (C.c_int, []),
     "qs_last_error": (C.c_char_p, []),
     "qs_launch_count": (C.c_int64, []),
     "qs_version": (C.c_char_p, []),
@@ -289,6 +296,34 @@ def qs_plan_autotune(state: int, gates, theta=None) -> tuple[QsPlanOpts, float]:
                                   th.ctypes.data_as(_DP) if th is not None else None, nt, C.byref(best),
                                   C.byref(ms)))
     return best, ms.value
+
+
+def qs_tune_cache_lookup(n: int, dtype: int, gates):
+    """(options, ms) cached for this circuit, or None."""
+    o, ms, found = QsPlanOpts(), C.c_double(), C.c_int()
+    _check(lib().qs_tune_cache_lookup(n, dtype, pack_gates(gates), len(gates), C.byref(o), C.byref(ms),
+                                      C.byref(found)))
+    return (o, ms.value) if found.value else None
+
+
+def qs_tune_cache_put(n: int, dtype: int, gates, opts: QsPlanOpts, ms: float):
+    _check(lib().qs_tune_cache_put(n, dtype, pack_gates(gates), len(gates), C.byref(opts), ms))
+
+
+def qs_tune_cache_save(path: str) -> int:
+    cnt = C.c_int64()
+    _check(lib().qs_tune_cache_save(os.fsencode(path), C.byref(cnt)))
+    return cnt.value
+
+
+def qs_tune_cache_load(path: str) -> int:
+    cnt = C.c_int64()
+    _check(lib().qs_tune_cache_load(os.fsencode(path), C.byref(cnt)))
+    return cnt.value
+
+
+def qs_tune_cache_clear():
+    _check(lib().qs_tune_cache_clear())
 
 
 def opts_dict(o: QsPlanOpts) -> dict:

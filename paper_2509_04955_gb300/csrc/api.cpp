@@ -3,6 +3,8 @@
 // state runs in the CUDA kernels of kernels_*.cu.
 #include "runtime.h"
 
+#include <cstdio>
+
 namespace qs {
 namespace rt {
 thread_local std::string g_err;
@@ -26,6 +28,45 @@ uint64_t fnv1a(const void* data, size_t bytes, uint64_t h = 1469598103934665603u
     h *= 1099511628211ull;
   }
   return h;
+}
+
+// Key of a gate list for the tuning cache: only the fields a gate's kind uses
+// (targets up to nq, controls up to nctrl, the angle of rotations, the
+// parameter binding, the matrix of U1/U2), so unused fields left unset by a
+// caller do not split one circuit into several keys.
+uint64_t gate_list_key(const qs_gate* gates, size_t ng) {
+  uint64_t h = fnv1a(&ng, sizeof(ng));
+  auto mix = [&](const void* d, size_t b) { h = fnv1a(d, b, h); };
+  for (size_t i = 0; i < ng; ++i) {
+    const qs_gate& g = gates[i];
+    mix(&g.kind, sizeof(g.kind));
+    const int nq = std::max(0, std::min(g.nq, 2)), nc = std::max(0, std::min(g.nctrl, 2));
+    mix(&nq, sizeof(nq));
+    mix(g.q, sizeof(int32_t) * nq);
+    mix(&nc, sizeof(nc));
+    mix(g.ctrl, sizeof(int32_t) * nc);
+    const bool angle = g.kind == QS_GATE_RX || g.kind == QS_GATE_RY || g.kind == QS_GATE_RZ || g.kind == QS_GATE_P;
+    if (angle) {
+      const int32_t pi = g.param_index >= 0 ? g.param_index : -1;
+      mix(&pi, sizeof(pi));
+      mix(&g.param, sizeof(g.param));
+      if (pi >= 0) mix(&g.scale, sizeof(g.scale));
+    }
+    if (g.kind == QS_GATE_U1) mix(g.mat, sizeof(double) * 8);
+    if (g.kind == QS_GATE_U2) mix(g.mat, sizeof(double) * 32);
+  }
+  return h;
+}
+
+std::vector<uint64_t> tune_key(int n, qs_dtype dt, const qs_gate* gates, size_t ng) {
+  return {(uint64_t)n, (uint64_t)dt, (uint64_t)ng, gate_list_key(gates, ng)};
+}
+
+void check_tune_args(int n, qs_dtype dt, const qs_gate* gates, size_t ng) {
+  require(n >= 1 && n <= kMaxQubits, "n out of range");
+  require(dt == QS_C64 || dt == QS_C128, "bad dtype");
+  require(ng == 0 || gates != nullptr, "gates is NULL");
+  require(ng <= kMaxGates, "too many gates (at most 2^30 per circuit)");
 }
 
 std::vector<qs_plan_opts> tune_candidates(int n, qs_dtype dt) {
@@ -380,10 +421,8 @@ qs_status qs_plan_autotune(qs_state_t s, const qs_gate* gates, size_t ngates, co
   return guard([&] {
     check_state(s);
     require(best != nullptr, "best is NULL");
-    require(ngates == 0 || gates != nullptr, "gates is NULL");
-    require(ngates <= kMaxGates, "too many gates (at most 2^30 per circuit)");
-    std::vector<uint64_t> key{(uint64_t)s->n, (uint64_t)s->dt, (uint64_t)ngates,
-                              fnv1a(gates, sizeof(qs_gate) * ngates)};
+    check_tune_args(s->n, s->dt, gates, ngates);
+    const std::vector<uint64_t> key = tune_key(s->n, s->dt, gates, ngates);
     {
       std::lock_guard<std::mutex> lock(g_tune_mu);
       auto it = g_tune_cache.find(key);
@@ -434,6 +473,125 @@ qs_status qs_plan_autotune(qs_state_t s, const qs_gate* gates, size_t ngates, co
     }
     *best = top.opts;
     if (best_ms) *best_ms = top.ms;
+  });
+}
+
+qs_status qs_tune_cache_lookup(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates, qs_plan_opts* best,
+                               double* best_ms, int* found) {
+  return guard([&] {
+    check_tune_args(n, dtype, gates, ngates);
+    require(found != nullptr, "found is NULL");
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto it = g_tune_cache.find(tune_key(n, dtype, gates, ngates));
+    *found = it != g_tune_cache.end();
+    if (*found) {
+      if (best) *best = it->second.opts;
+      if (best_ms) *best_ms = it->second.ms;
+    }
+  });
+}
+
+qs_status qs_tune_cache_put(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates, const qs_plan_opts* opts,
+                            double ms) {
+  return guard([&] {
+    check_tune_args(n, dtype, gates, ngates);
+    require(opts != nullptr, "opts is NULL");
+    require(std::isfinite(ms) && ms >= 0, "ms must be finite and >= 0");
+    std::unique_ptr<qs_plan_s> p(create_plan(n, dtype, gates, ngates, opts));   // the options must plan this circuit
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache[tune_key(n, dtype, gates, ngates)] = TuneEntry{*opts, ms};
+  });
+}
+
+qs_status qs_tune_cache_clear(void) {
+  return guard([&] {
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    g_tune_cache.clear();
+  });
+}
+
+// Text format: a first line "qsgb300-tune 1", then one entry per line:
+// n dtype ngates key(hex) ms mode fuse_k tile_qubits low_qubits paper_mode
+// tc_precision threads fuse_parametric reserved[0..7]
+qs_status qs_tune_cache_save(const char* path, int64_t* entries) {
+  return guard([&] {
+    require(path != nullptr, "path is NULL");
+    std::string out = "qsgb300-tune 1\n";
+    int64_t cnt = 0;
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      for (const auto& kv : g_tune_cache) {
+        const qs_plan_opts& o = kv.second.opts;
+        char line[512];
+        std::snprintf(line, sizeof(line), "%llu %llu %llu %016llx %.17g %d %d %d %d %d %d %d %d",
+                      (unsigned long long)kv.first[0], (unsigned long long)kv.first[1],
+                      (unsigned long long)kv.first[2], (unsigned long long)kv.first[3], kv.second.ms, o.mode,
+                      o.fuse_k, o.tile_qubits, o.low_qubits, o.paper_mode, o.tc_precision, o.threads,
+                      o.fuse_parametric);
+        out += line;
+        for (int r = 0; r < 8; ++r) out += " " + std::to_string(o.reserved[r]);
+        out += "\n";
+        ++cnt;
+      }
+    }
+    FILE* f = std::fopen(path, "w");
+    require(f != nullptr, "cannot open the cache file for writing");
+    const bool ok = std::fwrite(out.data(), 1, out.size(), f) == out.size();
+    const bool closed = std::fclose(f) == 0;
+    require(ok && closed, "cannot write the cache file");
+    if (entries) *entries = cnt;
+  });
+}
+
+qs_status qs_tune_cache_load(const char* path, int64_t* entries) {
+  return guard([&] {
+    require(path != nullptr, "path is NULL");
+    FILE* f = std::fopen(path, "r");
+    require(f != nullptr, "cannot open the cache file");
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof(buf), f)) > 0) text.append(buf, got);
+    std::fclose(f);
+    // parse everything first: a malformed file leaves the cache unchanged
+    std::vector<std::pair<std::vector<uint64_t>, TuneEntry>> parsed;
+    size_t pos = 0;
+    int line_no = 0;
+    while (pos < text.size()) {
+      size_t end = text.find('\n', pos);
+      if (end == std::string::npos) end = text.size();
+      const std::string line = text.substr(pos, end - pos);
+      pos = end + 1;
+      ++line_no;
+      if (line_no == 1) {
+        require(line == "qsgb300-tune 1", "not a tuning cache file (bad first line)");
+        continue;
+      }
+      if (line.empty()) continue;
+      unsigned long long n, dt, ng, key;
+      double ms;
+      qs_plan_opts o;
+      std::memset(&o, 0, sizeof(o));
+      int used = 0;
+      const int k = std::sscanf(line.c_str(), "%llu %llu %llu %llx %lg %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d %d%n",
+                                &n, &dt, &ng, &key, &ms, &o.mode, &o.fuse_k, &o.tile_qubits, &o.low_qubits,
+                                &o.paper_mode, &o.tc_precision, &o.threads, &o.fuse_parametric, &o.reserved[0],
+                                &o.reserved[1], &o.reserved[2], &o.reserved[3], &o.reserved[4], &o.reserved[5],
+                                &o.reserved[6], &o.reserved[7], &used);
+      const std::string where = "cache file line " + std::to_string(line_no);
+      if (k != 21 || line.find_first_not_of(" \t\r", (size_t)used) != std::string::npos)
+        throw Error(QS_ERR_ARG, where + ": malformed entry");
+      if (n < 1 || n > (unsigned long long)kMaxQubits || (dt != QS_C64 && dt != QS_C128) || ng > kMaxGates ||
+          !std::isfinite(ms) || ms < 0 || o.mode < QS_MODE_PER_GATE || o.mode > QS_MODE_SMGP)
+        throw Error(QS_ERR_ARG, where + ": value out of range");
+      parsed.push_back({{n, dt, ng, key}, TuneEntry{o, ms}});
+    }
+    require(line_no >= 1, "not a tuning cache file (empty)");
+    {
+      std::lock_guard<std::mutex> lock(g_tune_mu);
+      for (auto& e : parsed) g_tune_cache[e.first] = e.second;
+    }
+    if (entries) *entries = (int64_t)parsed.size();
   });
 }
 

@@ -414,3 +414,53 @@ def test_planner_fuzz_ops_reproduce_the_circuit():
         finally:
             Q.qs_plan_free(plan)
     assert seen == {0, 1, 2, 4}, seen     # per-gate, dense block, diagonal block, phase run
+
+
+def test_tuning_cache_put_lookup_save_load(tmp_path):
+    """The autotuner's cache across processes: an entry put for a circuit is
+    found again, survives a save / clear / load round trip with its options and
+    time, ignores fields a gate's kind does not use, and a malformed file is
+    refused without touching the cache."""
+    import dataclasses
+    n = 12
+    gates, p = W.hea(n, 2)
+    Q.qs_tune_cache_clear()
+    assert Q.qs_tune_cache_lookup(n, Q.QS_C64, gates) is None
+    opts = Q.make_opts(fuse_k=3, tile_qubits=11, low_qubits=4, phase_min_gates=-1)
+    Q.qs_tune_cache_put(n, Q.QS_C64, gates, opts, 1.25)
+    hit = Q.qs_tune_cache_lookup(n, Q.QS_C64, gates)
+    assert hit is not None and Q.opts_dict(hit[0]) == Q.opts_dict(opts) and hit[1] == 1.25
+    assert Q.qs_tune_cache_lookup(n, Q.QS_C128, gates) is None              # the dtype is part of the key
+    assert Q.qs_tune_cache_lookup(n, Q.QS_C64, gates[:-1]) is None          # and the gate list
+    moved = [dataclasses.replace(gates[0], angle=gates[0].angle + 0.5)] + gates[1:]
+    assert Q.qs_tune_cache_lookup(n, Q.QS_C64, moved) is None               # and a rotation's angle
+    # unused fields (a second target slot, the matrix of a non-matrix gate) do not change the key
+    arr = Q.pack_gates(gates)
+    for k in range(len(gates)):
+        if arr[k].nq == 1:
+            arr[k].q[1] = 7
+        arr[k].mat[0] = 3.0
+    import ctypes
+    found = ctypes.c_int()
+    assert Q.lib().qs_tune_cache_lookup(n, Q.QS_C64, arr, len(gates), None, None, ctypes.byref(found)) == Q.QS_OK
+    assert found.value == 1
+    path = str(tmp_path / "tune.txt")
+    assert Q.qs_tune_cache_save(path) == 1
+    Q.qs_tune_cache_clear()
+    assert Q.qs_tune_cache_lookup(n, Q.QS_C64, gates) is None
+    assert Q.qs_tune_cache_load(path) == 1
+    hit = Q.qs_tune_cache_lookup(n, Q.QS_C64, gates)
+    assert hit is not None and Q.opts_dict(hit[0]) == Q.opts_dict(opts) and hit[1] == 1.25
+    text = open(path).read().splitlines()
+    assert text[0] == "qsgb300-tune 1" and len(text) == 2
+    for bad in (["qsgb300-tune 1", text[1] + " 9"], ["qsgb300-tune 1", "12 0 1"], ["not a cache", text[1]],
+                ["qsgb300-tune 1", text[1].replace("12 0 ", "99 0 ", 1)]):
+        (tmp_path / "bad.txt").write_text("\n".join(bad) + "\n")
+        Q.qs_tune_cache_clear()
+        with pytest.raises(Q.QsError) as e:
+            Q.qs_tune_cache_load(str(tmp_path / "bad.txt"))
+        assert e.value.status == Q.QS_ERR_ARG
+        assert Q.qs_tune_cache_lookup(n, Q.QS_C64, gates) is None
+    with pytest.raises(Q.QsError):      # options that cannot plan the circuit are refused
+        Q.qs_tune_cache_put(n, Q.QS_C64, gates, Q.make_opts(fuse_k=6), 1.0)
+    Q.qs_tune_cache_clear()
