@@ -858,7 +858,7 @@ def config_hea(Q, torch, np, st, args):
 
 # The sources each kernel is compiled from (its traffic record is void once they change).
 KERNEL_SOURCES = {"k_tc_bulk": ("kernels_tc.cu", "cplx.cuh"), "k_tc_block": ("kernels_tc.cu", "cplx.cuh"),
-                  "k_tile": ("kernels_tile.cu", "cplx.cuh", "dfloat.cuh", "qs_internal.h")}
+                  "k_tile": ("kernels_tile.cuh", "cplx.cuh", "dfloat.cuh", "qs_internal.h")}
 
 
 def kernel_hash(kernel: str) -> str:

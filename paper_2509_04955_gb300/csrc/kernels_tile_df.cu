@@ -1,0 +1,20 @@
+// Tile-pass kernels for complex128 computed in FP32 pairs, blocks of up to 4 qubits
+// (5-qubit blocks: kernels_tile_df5.cu): instances of kernels_tile.cuh (the
+// dispatcher is in kernels_tile.cu).
+#include "kernels_tile.cuh"
+
+namespace qs {
+
+cudaError_t launch_tile_df(int kmax, void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
+                          int64_t brow0, int n, const PassDesc& p, const DevOp* ops, const double2* gtab,
+                          const double2* btab, cudaStream_t st, size_t smem) {
+  if (kmax == 5) return launch_tile_df5(kmax, psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem);
+  return launch_tile_range<dfl, 2, 4>(kmax, psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem);
+}
+
+cudaError_t prepare_tile_df(int kmax, size_t smem) {
+  if (kmax == 5) return prepare_tile_df5(kmax, smem);
+  return prepare_tile_range<dfl, 2, 4>(kmax, smem);
+}
+
+}  // namespace qs
