@@ -191,25 +191,39 @@ static bool paper_mergeable(const HGate& a, const HGate& b, uint64_t Q) {
   return false;
 }
 
+// The fields the scans read, packed (an HGate carries two 4x4 complex
+// matrices, so scanning HGates would touch a cache line per gate field).
+struct GateLite {
+  uint64_t qmask, dmask;
+  bool parametric;
+};
+
+static std::vector<GateLite> lite_of(const std::vector<HGate>& gates) {
+  std::vector<GateLite> v(gates.size());
+  for (size_t i = 0; i < gates.size(); ++i) v[i] = GateLite{gates[i].qmask, gates[i].dmask, gates[i].parametric};
+  return v;
+}
+
 // One greedy scan from `first`: absorbs later gates that commute with every
 // gate skipped so far and keep the block within kcap qubits (and within
 // `allowed`, when given). Returns the absorbed gates in program order.
 // With `members` NULL only the count is returned (the growth searches).
-static int scan_block(const std::vector<HGate>& gates, const std::vector<char>& done, int first, int kcap,
-                      uint64_t allowed, const PlanOptions& o, uint64_t all, std::vector<int>* members) {
+static int scan_block(const std::vector<HGate>& gates, const std::vector<GateLite>& lite,
+                      const std::vector<char>& done, int first, int kcap, uint64_t allowed, const PlanOptions& o,
+                      uint64_t all, std::vector<int>* members) {
   const int G = (int)gates.size();
   if (members) members->assign(1, first);
   int count = 1;
-  uint64_t Q = gates[first].qmask, blk_nd = 0, blk_d = 0;
-  const bool lone = !o.fuse_parametric && gates[first].parametric;   // stays a gate op
+  uint64_t Q = lite[first].qmask, blk_nd = 0, blk_d = 0;
+  const bool lone = !o.fuse_parametric && lite[first].parametric;   // stays a gate op
   for (int h = first + 1; h < G && !lone; ++h) {
     if (done[h]) continue;
-    const HGate& gh = gates[h];
+    const GateLite& gh = lite[h];
     const uint64_t qh = gh.qmask;
     const bool movable = (qh & blk_nd) == 0 && (qh & blk_d & ~gh.dmask) == 0;
     bool ok = movable && popc(Q | qh) <= kcap && (qh & ~allowed) == 0;
     if (ok && !o.fuse_parametric && gh.parametric) ok = false;
-    if (ok && o.paper) ok = paper_mergeable(gates[first], gh, Q);
+    if (ok && o.paper) ok = paper_mergeable(gates[first], gates[h], Q);
     if (ok) {
       if (members) members->push_back(h);
       ++count;
@@ -226,10 +240,11 @@ static int scan_block(const std::vector<HGate>& gates, const std::vector<char>& 
   return count;
 }
 
-static std::vector<int> scan_members(const std::vector<HGate>& gates, const std::vector<char>& done, int first,
-                                     int kcap, uint64_t allowed, const PlanOptions& o, uint64_t all) {
+static std::vector<int> scan_members(const std::vector<HGate>& gates, const std::vector<GateLite>& lite,
+                                     const std::vector<char>& done, int first, int kcap, uint64_t allowed,
+                                     const PlanOptions& o, uint64_t all) {
   std::vector<int> m;
-  scan_block(gates, done, first, kcap, allowed, o, all, &m);
+  scan_block(gates, lite, done, first, kcap, allowed, o, all, &m);
   return m;
 }
 
@@ -261,8 +276,9 @@ static uint64_t plan_qubits(const std::vector<HGate>& gates, const std::vector<c
 
 // Qubit set grown by legal scans: at each step add the qubit whose admission
 // lets the scan absorb the most gates.
-static uint64_t grow_qubits(const std::vector<HGate>& gates, const std::vector<char>& done, int first, int kcap,
-                            int n, const PlanOptions& o, uint64_t all) {
+static uint64_t grow_qubits(const std::vector<HGate>& gates, const std::vector<GateLite>& lite,
+                            const std::vector<char>& done, int first, int kcap, int n, const PlanOptions& o,
+                            uint64_t all) {
   uint64_t Q = gates[first].qmask;
   // candidates: qubits of the next unemitted gates
   uint64_t cand = 0;
@@ -274,7 +290,7 @@ static uint64_t grow_qubits(const std::vector<HGate>& gates, const std::vector<c
     size_t best = 0;
     for (int q = 0; q < n; ++q) {
       if ((Q & (1ull << q)) || !(cand & (1ull << q))) continue;
-      const size_t c = (size_t)scan_block(gates, done, first, kcap, Q | (1ull << q), o, all, nullptr);
+      const size_t c = (size_t)scan_block(gates, lite, done, first, kcap, Q | (1ull << q), o, all, nullptr);
       if (c > best) { best = c; best_q = q; }
     }
     if (best_q < 0) break;
@@ -285,8 +301,9 @@ static uint64_t grow_qubits(const std::vector<HGate>& gates, const std::vector<c
 
 // As grow_qubits, but each step may also add two qubits at once (a pair that
 // only pays off together, such as both ends of a two-qubit gate).
-static uint64_t grow_qubits_pairs(const std::vector<HGate>& gates, const std::vector<char>& done, int first,
-                                  int kcap, int n, const PlanOptions& o, uint64_t all) {
+static uint64_t grow_qubits_pairs(const std::vector<HGate>& gates, const std::vector<GateLite>& lite,
+                                  const std::vector<char>& done, int first, int kcap, int n, const PlanOptions& o,
+                                  uint64_t all) {
   uint64_t Q = gates[first].qmask;
   uint64_t cand = 0;
   int seen = 0;
@@ -301,14 +318,14 @@ static uint64_t grow_qubits_pairs(const std::vector<HGate>& gates, const std::ve
     for (size_t i = 0; i < cq.size(); ++i) {
       const uint64_t a = 1ull << cq[i];
       if (Q & a) continue;
-      const double c1 = (double)scan_block(gates, done, first, kcap, Q | a, o, all, nullptr);
+      const double c1 = (double)scan_block(gates, lite, done, first, kcap, Q | a, o, all, nullptr);
       if (c1 > best) { best = c1; best_add = a; }
       if (popc(Q) + 2 > kcap) continue;
       for (size_t j = i + 1; j < cq.size(); ++j) {
         const uint64_t b2 = 1ull << cq[j];
         if (Q & b2) continue;
         // a pair costs two slots: compare per added qubit, favouring progress
-        const double c2 = (double)scan_block(gates, done, first, kcap, Q | a | b2, o, all, nullptr);
+        const double c2 = (double)scan_block(gates, lite, done, first, kcap, Q | a | b2, o, all, nullptr);
         if (c2 - 0.5 > best) { best = c2 - 0.5; best_add = a | b2; }
       }
     }
@@ -328,6 +345,7 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
   // the one absorbing the most gates is kept.
   const int G = (int)gates.size();
   std::vector<char> done(G, 0);   // emitted
+  const std::vector<GateLite> lite = lite_of(gates);
   std::vector<Block> blocks;
   int first = 0;
   const uint64_t all = n >= 64 ? ~0ull : ((1ull << n) - 1);
@@ -336,16 +354,17 @@ std::vector<Block> contract(int n, const std::vector<HGate>& gates, const PlanOp
     if (first >= G) break;
     Block blk;
     const int kcap = o.paper ? 2 : std::max(o.k, popc(gates[first].qmask));
-    std::vector<int> a = o.no_merge ? std::vector<int>{first} : scan_members(gates, done, first, kcap, all, o, all);
+    std::vector<int> a = o.no_merge ? std::vector<int>{first} : scan_members(gates, lite, done, first, kcap, all, o, all);
     if (!o.no_merge && !o.paper && kcap > 2 && (o.fuse_parametric || !gates[first].parametric)) {
-      std::vector<int> b = scan_members(gates, done, first, kcap, plan_qubits(gates, done, first, kcap, n), o, all);
+      std::vector<int> b = scan_members(gates, lite, done, first, kcap, plan_qubits(gates, done, first, kcap, n), o, all);
       if (b.size() > a.size()) a.swap(b);
       if (o.search) {
-        std::vector<int> c = scan_members(gates, done, first, kcap, grow_qubits(gates, done, first, kcap, n, o, all), o, all);
+        std::vector<int> c = scan_members(gates, lite, done, first, kcap,
+                                          grow_qubits(gates, lite, done, first, kcap, n, o, all), o, all);
         if (c.size() > a.size()) a.swap(c);
         if (n <= 40 && gates.size() <= 40000) {
-          std::vector<int> d = scan_members(gates, done, first, kcap,
-                                            grow_qubits_pairs(gates, done, first, kcap, n, o, all), o, all);
+          std::vector<int> d = scan_members(gates, lite, done, first, kcap,
+                                            grow_qubits_pairs(gates, lite, done, first, kcap, n, o, all), o, all);
           if (d.size() > a.size()) a.swap(d);
         }
       }
