@@ -439,6 +439,11 @@ def test_tuning_cache_put_lookup_save_load(tmp_path):
     for k in range(len(gates)):
         if arr[k].nq == 1:
             arr[k].q[1] = 7
+        arr[k].ctrl[1] = 5 if arr[k].nctrl < 2 else arr[k].ctrl[1]
+        if arr[k].nctrl == 0:
+            arr[k].ctrl[0] = 4
+        if arr[k].kind not in (Q.KIND["rx"], Q.KIND["ry"], Q.KIND["rz"], Q.KIND["p"]):
+            arr[k].param, arr[k].param_index, arr[k].scale = 9.0, 3, 2.0
         arr[k].mat[0] = 3.0
     import ctypes
     found = ctypes.c_int()
