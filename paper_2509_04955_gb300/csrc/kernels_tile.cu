@@ -1,6 +1,6 @@
 // Tile passes: the dispatcher over the per-type instances (kernels_tile_f32.cu,
-// kernels_tile_f64.cu, kernels_tile_df.cu; kernel code in kernels_tile.cuh)
-// and the adjoint gradient's tiled reverse sweep.
+// kernels_tile_f64.cu, kernels_tile_df.cu and kernels_tile_df5.cu; kernel code
+// in kernels_tile.cuh) and the adjoint gradient's tiled reverse sweep.
 #include "kernels_tile.cuh"
 
 namespace qs {
