@@ -469,3 +469,27 @@ def test_tuning_cache_put_lookup_save_load(tmp_path):
     with pytest.raises(Q.QsError):      # options that cannot plan the circuit are refused
         Q.qs_tune_cache_put(n, Q.QS_C64, gates, Q.make_opts(fuse_k=6), 1.0)
     Q.qs_tune_cache_clear()
+
+
+def test_product_and_oracle_share_no_code():
+    """The CUDA library and its binding never import, include or link the oracle,
+    and the oracle uses nothing of the library: only the seeded input generators
+    (workloads.py, no simulator arithmetic) serve both sides."""
+    import glob
+    import os
+    import re
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    pkg = os.path.join(root, "paper_2509_04955_gb300")
+    product = glob.glob(os.path.join(pkg, "*.py")) + glob.glob(os.path.join(pkg, "csrc", "*"))
+    for f in product:
+        if f.endswith("workloads.py") or os.path.isdir(f) or f.endswith((".o", ".so")):
+            continue
+        text = open(f, errors="replace").read()
+        assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
+        assert not re.search(r'#include\s+[<"][^>"]*oracle', text), f
+    for f in glob.glob(os.path.join(root, "oracle", "*")):
+        if os.path.isdir(f) or f.endswith((".o", ".so")):
+            continue
+        text = open(f, errors="replace").read()
+        assert "qsim_gb300" not in text and "csrc" not in text, f
+        assert not re.search(r"^\s*(import|from)\s+paper_2509_04955_gb300(?!\.workloads)", text, re.M), f
