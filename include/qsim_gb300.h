@@ -168,21 +168,23 @@ typedef struct qs_plan_s* qs_plan_t;
 qs_status qs_state_alloc(int n, qs_dtype dtype, void* stream, qs_state_t* out);
 
 /* Wraps caller-owned device memory of 2^n amplitudes (not initialised, not
- * freed by qs_state_free). dev_ptr must be 16-byte aligned. */
+ * freed by qs_state_free). dev_ptr must be 16-byte aligned. (The state
+ * vector of Eq. 1.) */
 qs_status qs_state_wrap(void* dev_ptr, int n, qs_dtype dtype, void* stream, qs_state_t* out);
 
 qs_status qs_state_free(qs_state_t s);
 qs_status qs_state_info(qs_state_t s, int* n, qs_dtype* dtype, void** dev_ptr);
 qs_status qs_state_set_stream(qs_state_t s, void* stream);
 
-/* Sets the computational basis state |x> (x < 2^n). */
+/* Sets the computational basis state |x> (x < 2^n). (|x> of Eq. 1: qubit q is bit q of x.) */
 qs_status qs_state_set_basis(qs_state_t s, uint64_t x);
 
 /* Copies 2^n amplitudes (bytes = 2^n * amp size) between host and device;
- * host memory may be pageable or pinned. */
+ * host memory may be pageable or pinned. (Data movement: no counterpart in
+ * the paper.) */
 qs_status qs_state_copy_from_host(qs_state_t s, const void* host, size_t bytes);
 qs_status qs_state_copy_to_host(qs_state_t s, void* host, size_t bytes);
-/* dst <- src (same n and dtype), device to device. */
+/* dst <- src (same n and dtype), device to device. (No counterpart in the paper.) */
 qs_status qs_state_copy(qs_state_t dst, qs_state_t src);
 
 /* Reads `count` amplitudes psi[idx[k]] (idx host array, each < 2^n) into
@@ -208,7 +210,9 @@ qs_status qs_plan_info_get(qs_plan_t p, qs_plan_info* info);
 qs_status qs_plan_free(qs_plan_t p);
 
 /* Applies a plan to a state in place: psi <- G_N ... G_1 psi. theta holds
- * ntheta parameters (may be NULL when the circuit has none). */
+ * ntheta parameters (may be NULL when the circuit has none). Per gate the
+ * update of Eq. 3-4 (Algorithms 1-4); fused blocks apply their product
+ * matrix (Eq. 6-7, Section 3.4). */
 qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta);
 
 /* Runs the plan on `count` independent states held in host memory (page-locked
@@ -222,7 +226,8 @@ qs_status qs_plan_execute(qs_plan_t p, qs_state_t s, const double* theta, size_t
  * circuit (norms are gathered on the device and read once at the end).
  * theta as for qs_plan_execute, shared by all inputs. Blocks until every
  * result is in host memory. QS_ERR_ARG for a NULL input, work states of
- * another n or dtype, or a work state listed twice. */
+ * another n or dtype, or a work state listed twice. The overlap of copies
+ * with compute follows Section 3.2's multi-buffering (Tab. 2). */
 qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const void* const* host_in,
                                void* const* host_out, int count, const double* theta, size_t ntheta,
                                double* norms);
@@ -255,33 +260,35 @@ qs_status qs_plan_autotune(qs_state_t scratch, const qs_gate* gates, size_t ngat
  * All are thread-safe. */
 qs_status qs_tune_cache_lookup(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates, qs_plan_opts* best,
                                double* best_ms, int* found);
-qs_status qs_tune_cache_put(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates, const qs_plan_opts* opts,
-                            double ms);
+qs_status qs_tune_cache_put(int n, qs_dtype dtype, const qs_gate* gates, size_t ngates,
+                            const qs_plan_opts* opts, double ms);
 qs_status qs_tune_cache_save(const char* path, int64_t* entries);
 qs_status qs_tune_cache_load(const char* path, int64_t* entries);
 qs_status qs_tune_cache_clear(void);
 
-/* One-shot: plan, execute, free. */
+/* One-shot: plan, execute, free. (Eq. 3-4 per gate, as qs_plan_execute.) */
 qs_status qs_apply_circuit(qs_state_t s, const qs_gate* gates, size_t ngates,
                            const double* theta, size_t ntheta, const qs_plan_opts* opts);
 
 /* ---------------- observables ---------------- */
 
-/* *out = sum_i |psi_i|^2, accumulated in FP64. */
+/* *out = sum_i |psi_i|^2, accumulated in FP64. (No counterpart in the paper.) */
 qs_status qs_norm(qs_state_t s, double* out);
 
 /* *out = sum_j c_j <psi|P_j|psi> with P|i> = i^{#Y} (-1)^{popcount(i & z)} |i xor x>,
- * accumulated in FP64 (terms with equal xmask share one sweep). */
+ * accumulated in FP64 (terms with equal xmask share one sweep). (No
+ * counterpart in the paper: the textbook expectation value of a Pauli sum.) */
 qs_status qs_expval_pauli_sum(qs_state_t s, const qs_pauli_term* terms, size_t nterms, double* out);
 
-/* out <- sum_j c_j P_j psi (out must not alias s). */
+/* out <- sum_j c_j P_j psi (out must not alias s). (No counterpart in the paper.) */
 qs_status qs_apply_pauli_sum(qs_state_t s, const qs_pauli_term* terms, size_t nterms, qs_state_t out);
 
 /* max_i |a_i - b_i| and ||a - b||_2 in FP64 for two states of equal n (dtypes
- * may differ: the error of a complex64 result against a complex128 run). */
+ * may differ: the error of a complex64 result against a complex128 run).
+ * (No counterpart in the paper.) */
 qs_status qs_state_diff(qs_state_t a, qs_state_t b, double* max_abs, double* l2);
 
-/* <a|b> in FP64: (*re, *im). */
+/* <a|b> in FP64: (*re, *im). (No counterpart in the paper.) */
 qs_status qs_inner(qs_state_t a, qs_state_t b, double* re, double* im);
 
 /* Adjoint-method gradient (Jones and Gacon, arXiv:2009.02823) of
@@ -293,10 +300,11 @@ qs_status qs_adjoint_grad(qs_state_t s, const qs_gate* gates, size_t ngates,
                           double* expval_out, double* grad_out);
 /* Same, with plan options (may be NULL = the defaults above): they plan the
  * forward execution (any fused or tensor mode); their complex128 arithmetic
- * (reserved[3], FP32 pairs) applies to the reverse sweep as well. */
-qs_status qs_adjoint_grad_opts(qs_state_t s, const qs_gate* gates, size_t ngates, const double* theta, size_t ntheta,
-                               const qs_pauli_term* terms, size_t nterms, const qs_plan_opts* opts,
-                               double* expval_out, double* grad_out);
+ * (reserved[3], FP32 pairs) applies to the reverse sweep as well.
+ * (Jones and Gacon, as qs_adjoint_grad.) */
+qs_status qs_adjoint_grad_opts(qs_state_t s, const qs_gate* gates, size_t ngates, const double* theta,
+                               size_t ntheta, const qs_pauli_term* terms, size_t nterms,
+                               const qs_plan_opts* opts, double* expval_out, double* grad_out);
 
 /* ---------------- batched execution ---------------- */
 
@@ -304,7 +312,9 @@ qs_status qs_adjoint_grad_opts(qs_state_t s, const qs_gate* gates, size_t ngates
  * theta, B x ntheta row-major, drives state b) and, when terms != NULL,
  * writes <H> of each final state to expvals[b]. All states must share n,
  * dtype and stream. The launch sequence is captured once into a CUDA graph
- * and replayed. */
+ * and replayed.
+ * (No counterpart in the paper: the many parameter vectors of one circuit
+ * that a variational loop evaluates.) */
 qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B,
                                   const double* theta, size_t ntheta,
                                   const qs_pauli_term* terms, size_t nterms, double* expvals);
@@ -315,7 +325,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B,
  * has no parameters) driving state b, synchronises the states' stream and
  * frees the plan. The states must share n, dtype and stream (QS_ERR_ARG
  * otherwise). For repeated batches keep a plan and call
- * qs_plan_execute_batched, which replays its captured graph. */
+ * qs_plan_execute_batched, which replays its captured graph. (No counterpart in the paper.) */
 qs_status qs_apply_circuit_batched(qs_state_t* states, int B, const qs_gate* gates, size_t ngates,
                                    const double* theta, size_t ntheta, const qs_plan_opts* opts);
 
@@ -355,17 +365,20 @@ qs_status qs_plan_op_count(qs_plan_t p, int64_t* nops, int64_t* npasses);
  * terms via qs_plan_phase_terms). qubits: capacity 6, or n for a phase run.
  * gate_index: the input gate of a gate op (-1 for blocks). mat (optional,
  * capacity 2 * 4096 doubles): the block's entries as (re, im) pairs; not
- * written for a phase run. */
+ * written for a phase run.
+ * (Introspection: no counterpart in the paper.) */
 qs_status qs_plan_op_get(qs_plan_t p, int64_t i, int32_t* type, int32_t* qubits, int32_t* nq,
                          int32_t* gate_index, double* mat);
 /* Self-check of the blocks rebuilt on the device from theta: resolves theta,
  * builds them on the device, copies them back and returns the largest
  * difference to the host's FP64 ordered products (W images compared as bf16
- * values) and the number of such blocks. Synchronises; no state is touched. */
+ * values) and the number of such blocks. Synchronises; no state is touched.
+ * (Self-check: no counterpart in the paper.) */
 qs_status qs_plan_check_device_blocks(qs_plan_t p, qs_state_t s, const double* theta, size_t ntheta,
                                       double* max_abs_diff, int64_t* nblocks);
 /* Tile qubits of pass i (ascending, capacity 14; a phase pass lists the qubits
- * of its run, capacity n) and its op range [op_begin, op_end). */
+ * of its run, capacity n) and its op range [op_begin, op_end).
+ * (Introspection: no counterpart in the paper.) */
 qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t* m,
                            int64_t* op_begin, int64_t* op_end);
 /* Terms of phase-run op i (type 4): the run multiplies amplitude x by
@@ -374,7 +387,8 @@ qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t
  * phase polynomial of the run's gates: with b_q the bit of qubit q,
  * RZ(a) = exp(-i a/2 (-1)^b), P(a) = exp(i a b) and a CNOT adds the control's
  * parity to the target's. Writes min(cap, count) terms; *nterms = count.
- * QS_ERR_ARG when op i is not a phase run. */
+ * QS_ERR_ARG when op i is not a phase run.
+ * (The phase polynomial of a diagonal run: no counterpart in the paper.) */
 qs_status qs_plan_phase_terms(qs_plan_t p, int64_t i, uint64_t* masks, int32_t* param_index, double* alpha0,
                               double* coef, int64_t cap, int64_t* nterms);
 
@@ -385,7 +399,8 @@ qs_status qs_plan_phase_terms(qs_plan_t p, int64_t i, uint64_t* masks, int32_t* 
  * index is the high qubits). The circuit is cut into streamed passes, each
  * touching at most pass_qubits batch-index qubits: the tile-pass scheduler with
  * the batch_qubits low qubits always present, so gates move ahead of gates they
- * commute with (disjoint qubits, or diagonal on the shared ones). For each pass, every group of 2^(qubits it selects) batches is copied into
+ * commute with (disjoint qubits, or diagonal on the shared ones). For each
+ * pass, every group of 2^(qubits it selects) batches is copied into
  * one of three device buffers, the pass's gates run there as a plan over
  * batch_qubits + selected qubits (planned with opts, so tile, tensor-core and
  * phase passes all apply), and the group is copied back; copies in, compute
@@ -406,18 +421,22 @@ typedef struct {
  * batch_qubits, batch_qubits + pass_qubits <= 40; every gate may touch at
  * most pass_qubits qubits >= batch_qubits (QS_ERR_ARG otherwise). Device
  * memory: 3 x 2^(batch_qubits + pass_qubits) amplitudes. Blocks until the
- * state is back in host memory. info may be NULL. */
+ * state is back in host memory. info may be NULL.
+ * Section 3.2: batches of 2^batch_qubits contiguous amplitudes, the high
+ * qubits as batch index, multi-buffered copies (Tab. 2). */
 qs_status qs_stream_apply(void* host_psi, int n, qs_dtype dtype, const qs_gate* gates, size_t ngates,
                           const double* theta, size_t ntheta, const qs_plan_opts* opts, int batch_qubits,
                           int pass_qubits, qs_stream_info* info);
 /* Host only: the streamed passes qs_stream_apply would run. high_masks[i] = the
  * batch-index qubits pass i touches, pass_end[i] = the end of its gates in
  * order (both capacity cap, may be NULL); order (capacity ngates, may be NULL)
- * = the gate indices in execution order. */
+ * = the gate indices in execution order.
+ * (Section 3.2's batch passes, planned on the host.) */
 qs_status qs_stream_plan(int n, const qs_gate* gates, size_t ngates, int batch_qubits, int pass_qubits,
-                         int64_t* npasses, uint64_t* high_masks, int64_t* pass_end, int64_t cap, int32_t* order);
+                         int64_t* npasses, uint64_t* high_masks, int64_t* pass_end, int64_t cap,
+                         int32_t* order);
 
-/* ---------------- measurement ----------------
+/* ---------------- measurement (no counterpart in the paper) ----------------
  * With timing enabled, every kernel launch issued by qs_plan_execute is
  * bracketed by two CUDA events on the state's stream. qs_plan_timing_read
  * waits for the recorded events, returns the summed device time of the
@@ -425,14 +444,16 @@ qs_status qs_stream_plan(int n, const qs_gate* gates, size_t ngates, int batch_q
 qs_status qs_plan_set_timing(qs_plan_t p, int enable);
 qs_status qs_plan_timing_read(qs_plan_t p, double* total_ms, int64_t* launches);
 /* Same, split by launch kind: [0] = tile passes or per-gate kernels, [1] =
- * tensor-core passes (arrays of 2, may be NULL). */
+ * tensor-core passes (arrays of 2, may be NULL).
+ * (Measurement: no counterpart in the paper.) */
 qs_status qs_plan_timing_read_kinds(qs_plan_t p, double* total_ms, int64_t* launches, double* kind_ms,
                                     int64_t* kind_launches);
 
-/* ---------------- diagnostics ---------------- */
+/* ---------------- diagnostics (no counterpart in the paper) ---------------- */
 
 const char* qs_last_error(void);
-/* Number of library kernel launches issued by this process so far. */
+/* Number of library kernel launches issued by this process so far.
+ * (Diagnostics: no counterpart in the paper.) */
 int64_t qs_launch_count(void);
 const char* qs_version(void);
 
