@@ -344,9 +344,11 @@ qs_status qs_apply_circuit_batched(qs_state_t* states, int B, const qs_gate* gat
  *              legacy default stream); terms: host array of nterms <= 1024
  *              Pauli strings (more gives QS_ERR_ARG before any device work);
  *   *out: the FP64 expectation value; the call synchronises `stream`.
- * The first call on a device looks up the array's device address on that
- * device (make that device current); make this first call before any stream
- * capture. All calls share the one array: calls whose device work overlaps
+ * Every call looks up the array's device address in the current CUDA context
+ * (make the state's device current), so the address stays right after a
+ * device reset or a switch of context; the first call on a device loads the
+ * library's device code there, so make it before any stream capture. All
+ * calls share the one array: calls whose device work overlaps
  * (other threads, other streams) race on it and must be serialised by the
  * caller. Every slot a call reads is written earlier in the same call, so no
  * clearing is needed between calls. */
@@ -455,6 +457,10 @@ const char* qs_last_error(void);
 /* Number of library kernel launches issued by this process so far.
  * (Diagnostics: no counterpart in the paper.) */
 int64_t qs_launch_count(void);
+/* Number of device allocations (cudaMalloc) the library has made in this
+ * process so far: states, plan tables, scratch buffers. A call that should not
+ * allocate leaves it unchanged. (Diagnostics: no counterpart in the paper.) */
+int64_t qs_device_alloc_count(void);
 const char* qs_version(void);
 
 #ifdef __cplusplus

@@ -130,6 +130,7 @@ _SIGS = {
     "qs_tune_cache_clear": (C.c_int, []),
     "qs_last_error": (C.c_char_p, []),
     "qs_launch_count": (C.c_int64, []),
+    "qs_device_alloc_count": (C.c_int64, []),
     "qs_version": (C.c_char_p, []),
 }
 
@@ -560,6 +561,11 @@ def qs_plan_timing_read_kinds(plan: int) -> dict:
 
 def qs_launch_count() -> int:
     return lib().qs_launch_count()
+
+
+def qs_device_alloc_count() -> int:
+    """Device allocations (cudaMalloc) the library has made in this process."""
+    return lib().qs_device_alloc_count()
 
 
 def qs_version() -> str:

@@ -276,6 +276,7 @@ qs_status qs_plan_pass_get(qs_plan_t p, int64_t i, int32_t* tile_qubits, int32_t
   });
 }
 int64_t qs_launch_count(void) { return qs::launch_count(); }
+int64_t qs_device_alloc_count(void) { return qs::device_alloc_count(); }
 const char* qs_version(void) { return "gb300-statevec 0.1 (sm_103a)"; }
 
 qs_status qs_state_alloc(int n, qs_dtype dtype, void* stream, qs_state_t* out) {
@@ -293,6 +294,7 @@ qs_status qs_state_alloc(int n, qs_dtype dtype, void* stream, qs_state_t* out) {
       cudaGetLastError();
       throw Error(QS_ERR_OOM, "cannot allocate " + std::to_string(s->bytes()) + " bytes for the state");
     }
+    note_device_alloc();
     s->owned = true;
     CK(launch_set_basis(s->d, n, dtype, 0, s->st));
     *out = s.release();

@@ -28,11 +28,28 @@ void note_launch(int64_t k) {
 }
 void suspend_launch_count(bool on) { g_count_suspended = on; }
 int64_t launch_count() { return g_launches.load(); }
+static std::atomic<int64_t> g_allocs{0};
+void note_device_alloc() { ++g_allocs; }
+int64_t device_alloc_count() { return g_allocs.load(); }
+
+int device_sm_count() {
+  static std::atomic<int> sms{0};
+  int v = sms.load();
+  if (v > 0) return v;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+      v <= 0) {
+    cudaGetLastError();
+    return 152;   // not cached: asked again on the next call
+  }
+  sms.store(v);
+  return v;
+}
 
 static int grid_for(uint64_t work, int threads) {
-  // Enough CTAs to fill 152 SMs several times over; the kernels stride.
+  // Enough CTAs to fill every SM several times over; the kernels stride.
   uint64_t want = (work + threads - 1) / threads;
-  const uint64_t cap = 152ull * 16;
+  const uint64_t cap = (uint64_t)device_sm_count() * 16;
   if (want > cap) want = cap;
   if (want < 1) want = 1;
   return (int)want;

@@ -18,7 +18,12 @@
 namespace qs {
 
 constexpr int kRedThreads = 256;
-constexpr int kRedBlocks = 152 * 4;
+// The reduction grid is a fixed constant, deliberately not the device's SM
+// count: the CTA partition of the index range, hence every partial sum and the
+// order in which they are combined, is the same on every device and every
+// run, so the FP64 results are bit-for-bit reproducible. 608 CTAs = four per
+// SM on a 152-SM GB300.
+constexpr int kRedBlocks = 608;
 constexpr int kRun = 32;
 constexpr int kUnroll = 4;   // independent 16-byte loads per thread per iteration (bytes in flight)
 
@@ -266,7 +271,7 @@ cudaError_t launch_diff(const void* a, qs_dtype da, const void* b, qs_dtype db, 
 
 // ---------------------------------------------------------------- Pauli expval
 
-constexpr int kMaxZ = 8;
+constexpr int kMaxZ = kExpvalMaxZ;
 
 // One sweep for all strings sharing xmask x. Pairs (i, j = i xor x) are
 // visited once (i has the highest bit of x clear). For w = conj(psi_j) psi_i:
@@ -611,7 +616,8 @@ cudaError_t launch_apply_pauli(const void* psi, void* out, int n, qs_dtype dt, c
   for (int off = 0; off < nt || first; off += kMaxTermsPerLaunch) {
     const int cnt = nt - off < kMaxTermsPerLaunch ? nt - off : kMaxTermsPerLaunch;
     uint64_t g = (dim + kRedThreads - 1) / kRedThreads;
-    if (g > 152ull * 16) g = 152ull * 16;
+    const uint64_t cap = (uint64_t)device_sm_count() * 16;
+    if (g > cap) g = cap;
     if (dt == QS_C64)
       k_apply_pauli<float><<<(unsigned)g, kRedThreads, 0, st>>>((const float2*)psi, (float2*)out, dim, xm + off,
                                                                  zm + off, (const double2*)ph + off, cnt, !first);

@@ -14,7 +14,6 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <mutex>
 #include <string>   // error messages only
 
 #include "qs_internal.h"
@@ -29,47 +28,32 @@ using namespace qs;
 namespace {
 
 constexpr int kNoAllocMaxTerms = 1024;      // largest Pauli sum accepted
-constexpr int kNoAllocZPerLaunch = 8;       // strings per expectation launch (the kernel's limit)
-constexpr int kNoAllocPartialRows = 8;      // rows of per-CTA partial sums per launch
+constexpr int kNoAllocZPerLaunch = kExpvalMaxZ;   // strings per expectation launch (the kernel's limit)
+constexpr int kNoAllocPartialRows = kNoAllocZPerLaunch;   // rows of per-CTA partial sums per launch
 constexpr int kNoAllocPartialCols = 1024;   // >= the reduction grid
+static_assert(kNoAllocZPerLaunch == 8, "scratch layout sized for 8 strings per expectation launch");
 constexpr size_t kPartialBytes = sizeof(double) * kNoAllocPartialRows * kNoAllocPartialCols;
 constexpr size_t kOutBytes = sizeof(double) * kNoAllocMaxTerms;
 constexpr size_t kZBytes = sizeof(uint64_t) * kNoAllocMaxTerms;
 constexpr size_t NOALLOC_SCRATCH_BYTES = kPartialBytes + kOutBytes + kZBytes;
-constexpr int kMaxDevices = 64;
 
 // Layout: [partials: 8 x 1024 doubles][per-string results: 1024 doubles][z masks: 1024 uint64].
 // Every launch writes each slot it later reads, so nothing needs clearing
 // between calls; stale contents from an earlier call are never read.
 static __device__ __align__(256) unsigned char g_noalloc_scratch[NOALLOC_SCRATCH_BYTES];
 
-std::mutex g_setup_mu;
-void* g_scratch_addr[kMaxDevices] = {nullptr};
-
-// Device address of the scratch array on the current device, looked up once
-// per device (with that device current) and cached.
+// Device address of the scratch array in the current CUDA context. In host
+// code g_noalloc_scratch names a host-side stand-in, never the device array,
+// so the address is asked for on every call: the module holding the array is
+// loaded per context, and a cached address would go stale after
+// cudaDeviceReset or when the caller makes another context current. The
+// lookup is cheap once the module is loaded in that context.
 cudaError_t scratch_address(void** out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
+  void* p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
   if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_setup_mu);
-  if (!g_scratch_addr[dev]) {
-    void* p = nullptr;
-    e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = p;
-  }
-  *out = g_scratch_addr[dev];
+  *out = p;
   return cudaSuccess;
-}
-
-// Factor turning the kernel's per-string sum into <P> (see k_expval_x).
-double string_factor(uint64_t x, uint64_t z) {
-  if (x == 0) return 1.0;
-  const int ny = __builtin_popcountll(x & z);
-  if ((ny & 1) == 0) return ((ny / 2) & 1) ? -2.0 : 2.0;
-  return (((ny + 1) / 2) & 1) ? -2.0 : 2.0;
 }
 
 qs_status fail(qs_status code, const std::string& msg) {
@@ -132,7 +116,7 @@ extern "C" qs_status qs_expval_pauli_sum_noalloc(const void* dev_state, int n, q
   double total = 0;
   for (size_t k = 0; k < nterms; ++k) {
     const qs_pauli_term& t = terms[order[k]];
-    total += t.coeff * string_factor(t.xmask, t.zmask) * vals[k];
+    total += t.coeff * rt::term_factor(t) * vals[k];
   }
   *out = total;
   return QS_OK;

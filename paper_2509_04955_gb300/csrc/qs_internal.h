@@ -264,5 +264,20 @@ cudaError_t launch_sum_rows(const double* partials, int rows, int cols, double* 
 void note_launch(int64_t k = 1);
 // While suspended (graph capture), launches are not counted; replays are.
 void suspend_launch_count(bool on);
+// Device allocations (cudaMalloc) made by the library so far (diagnostics).
+void note_device_alloc();
+int64_t device_alloc_count();
+// SM count of the current device (queried once per process; grids of
+// streaming kernels are sized from it).
+int device_sm_count();
+
+// Pauli strings one expectation launch (k_expval_x) handles: callers split
+// longer groups of equal x mask into launches of at most this many strings.
+constexpr int kExpvalMaxZ = 8;
+
+namespace rt {
+// Sign and factor turning k_expval_x's per-string sum into <P> (runtime.cpp).
+double term_factor(const qs_pauli_term& t);
+}  // namespace rt
 
 }  // namespace qs

@@ -87,6 +87,7 @@ struct DevBuf {
     if (b <= bytes) return;
     release();
     CK(cudaMalloc(&p, b));
+    note_device_alloc();
     bytes = b;
   }
   template <class T> T* as() const { return (T*)p; }
@@ -241,7 +242,7 @@ struct PreparedTerms {
   std::vector<int> counts;
 };
 
-constexpr int kZPerLaunch = 8;
+constexpr int kZPerLaunch = kExpvalMaxZ;
 
 // ---- device tables of a plan, upload and execution (runtime.cpp)
 void fill_fixed_table(const qs_plan_s& p, std::vector<double2>& tab);
