@@ -90,9 +90,19 @@ typedef struct {
 typedef enum {
   QS_MODE_PER_GATE = 0,  /* one kernel launch per gate (Algorithms 1-4) */
   QS_MODE_FUSED = 1,     /* DAG contraction into k-qubit blocks + tile passes */
-  QS_MODE_TENSOR = 2,    /* as FUSED with 6-qubit contraction; blocks carrying many gates are
-                            applied as 64x64 complex GEMMs on tensor cores (tcgen05, FP32
-                            accumulation); QS_C64 only, n >= 13 (smaller states plan as FUSED) */
+  QS_MODE_TENSOR = 2,    /* as FUSED, with blocks applied as dense complex GEMMs on tensor cores
+                            (tcgen05), each its own pass over the state.
+                            QS_C64: 6-qubit contraction, blocks of >= reserved[0] gates (default
+                            10) as 64x64 complex blocks with FP32 accumulation (tc_precision),
+                            n >= 13 (smaller states plan as FUSED).
+                            QS_C128: 5-qubit contraction, blocks of >= reserved[0] gates (default
+                            1: every block) as 32x32 complex blocks computed exactly: each row of
+                            64 reals shares a power-of-two scale, amplitudes and W are cut into
+                            five 9-bit integer digits (fp16), the 15 digit products of the five
+                            leading levels accumulate exactly in FP32 and are combined into FP64
+                            without FP64 instructions; per pass the absolute error is about
+                            2^-43 times the largest amplitude of the 64-real row. n >= 12
+                            (smaller states plan as FUSED); tc_precision must be 0. */
   QS_MODE_SMGP = 3       /* staggered multi-gate parallelism (Section 3.3, Tab. 3): runs of 2, 4 or 8
                             consecutive uncontrolled one-target gates on distinct qubits become a
                             group; the state is cut into S segments by qubits no member targets,
@@ -105,11 +115,12 @@ typedef enum {
 /* Planner and kernel options. Zero-initialised fields take the defaults. */
 typedef struct {
   int32_t mode;          /* qs_mode */
-  int32_t fuse_k;        /* max qubits per fused block (1..5 on CUDA cores, 6 tensor); 0 = auto */
+  int32_t fuse_k;        /* max qubits per fused block (1..5 on CUDA cores; tensor mode: 6 for
+                            QS_C64, or 5 when fuse_k = 5; always 5 for QS_C128); 0 = auto */
   int32_t tile_qubits;   /* m: qubits staged per shared-memory tile (6..14); 0 = auto */
   int32_t low_qubits;    /* L: qubits 0..L-1 always in the tile (coalescing); 0 = auto */
   int32_t paper_mode;    /* 1 = contract only the merges of Section 3.4 (1q(x)1q, same-qubit, same-(c,t) CU) */
-  int32_t tc_precision;  /* tensor mode: 4 = fp16 hi/lo split with three products and a power-of-two
+  int32_t tc_precision;  /* tensor mode, QS_C64: 4 = fp16 hi/lo split with three products and a power-of-two
                             pre-scale of the amplitudes (default; about 2^-22 relative per pass),
                             3 = bf16 hi/lo split, three products (about 2^-16), 1 = bf16, one product */
   int32_t threads;       /* CUDA threads per tile CTA; 0 = auto */
@@ -362,8 +373,9 @@ qs_status qs_expval_pauli_sum_noalloc(const void* dev_state, int n, qs_dtype dty
  * the Eq. 7 ordering). In per-gate mode every op is a gate op and every pass
  * one op. */
 qs_status qs_plan_op_count(qs_plan_t p, int64_t* nops, int64_t* npasses);
-/* type: 0 = gate op, 1 = dense block, 2 = diagonal block, 3 = dense 6-qubit block applied on
- * tensor cores (its own pass over 13-qubit tiles), 4 = diagonal phase run (its own pass; its
+/* type: 0 = gate op, 1 = dense block, 2 = diagonal block, 3 = dense block applied on tensor
+ * cores (its own pass: 6 qubits over 13-qubit tiles for QS_C64, 5 qubits over 12-qubit tiles
+ * for QS_C128), 4 = diagonal phase run (its own pass; its
  * terms via qs_plan_phase_terms). qubits: capacity 6, or n for a phase run.
  * gate_index: the input gate of a gate op (-1 for blocks). mat (optional,
  * capacity 2 * 4096 doubles): the block's entries as (re, im) pairs; not
@@ -450,6 +462,18 @@ qs_status qs_plan_timing_read(qs_plan_t p, double* total_ms, int64_t* launches);
  * (Measurement: no counterpart in the paper.) */
 qs_status qs_plan_timing_read_kinds(qs_plan_t p, double* total_ms, int64_t* launches, double* kind_ms,
                                     int64_t* kind_launches);
+
+/* Bounded waits of the tensor-core passes: every wait of their pipelines
+ * (a landing slot, an operand, an accumulator) polls an mbarrier at most
+ * `polls` times (0 = the default bound, 2^26 polls that may each suspend the
+ * thread briefly; below 64, immediate non-blocking checks) before the pass
+ * records a timeout, stops, lets its copies and MMAs in flight complete
+ * (under the default bound), frees its tensor memory and returns; the
+ * execution then fails with QS_ERR_TIMEOUT and the state is left partly
+ * updated. A small limit makes the waits run out on purpose (a test of that
+ * path); the plan keeps the limit until it is set again.
+ * (Failure detection: no counterpart in the paper.) */
+qs_status qs_plan_set_wait_limit(qs_plan_t p, uint32_t polls);
 
 /* ---------------- diagnostics (no counterpart in the paper) ---------------- */
 

@@ -130,6 +130,7 @@ _SIGS = {
     "qs_tune_cache_clear": (C.c_int, []),
     "qs_last_error": (C.c_char_p, []),
     "qs_launch_count": (C.c_int64, []),
+    "qs_plan_set_wait_limit": (C.c_int, [_VP, C.c_uint32]),
     "qs_device_alloc_count": (C.c_int64, []),
     "qs_version": (C.c_char_p, []),
 }
@@ -539,6 +540,11 @@ def qs_plan_phase_terms(plan: int, i: int) -> list[tuple[int, int, float, float]
     _check(lib().qs_plan_phase_terms(plan, i, m, pi, a0.ctypes.data_as(_DP), cf.ctypes.data_as(_DP), k,
                                      C.byref(cnt)))
     return [(int(m[j]), int(pi[j]), float(a0[j]), float(cf[j])) for j in range(k)]
+
+
+def qs_plan_set_wait_limit(plan: int, polls: int):
+    """Polls per tensor-core pipeline wait before the pass gives up (0 = default)."""
+    _check(lib().qs_plan_set_wait_limit(plan, int(polls)))
 
 
 def qs_plan_set_timing(plan: int, enable: bool):

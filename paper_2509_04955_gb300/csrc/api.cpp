@@ -96,6 +96,10 @@ std::vector<qs_plan_opts> tune_candidates(int n, qs_dtype dt) {
     const int tm[] = {2, 4, 8};
     for (int t : tm) add(QS_MODE_TENSOR, 2, 13, 4, t);
   }
+  if (dt == QS_C128 && n >= 12) {   // every block on tensor cores, or only those of >= 2 / 4 gates
+    const int tm[] = {1, 2, 4};
+    for (int t : tm) add(QS_MODE_TENSOR, 2, 11, 3, t);
+  }
   return c;
 }
 
@@ -104,6 +108,14 @@ std::vector<qs_plan_opts> tune_candidates(int n, qs_dtype dt) {
 extern "C" {
 
 const char* qs_last_error(void) { return g_err.c_str(); }
+
+qs_status qs_plan_set_wait_limit(qs_plan_t p, uint32_t polls) {
+  return guard([&] {
+    require(p != nullptr, "plan is NULL");
+    p->tc_spin = polls;
+    p->graph_key.clear();   // a captured graph holds the old limit: recapture on the next batch
+  });
+}
 
 qs_status qs_plan_set_timing(qs_plan_t p, int enable) {
   return guard([&] {
@@ -170,7 +182,19 @@ qs_status qs_plan_check_device_blocks(qs_plan_t p, qs_state_t s, const double* t
         const double2 a = dev[p->block_off[b] + i], h = p->h_btab[p->block_off[b] + i];
         if (blk.rep != OP_TC) worst = std::max(worst, std::hypot(a.x - h.x, a.y - h.y));
       }
-      if (blk.rep == OP_TC) {
+      if (blk.rep == OP_TC && p->dt == QS_C128) {
+        // digit planes: compare the values they stand for (the FP64 products on the
+        // host and the device may differ in their last bits)
+        std::vector<uint16_t> img(kTc128WElems);
+        build_w_digits(p->h_btab.data() + p->block_off[b], img.data());
+        for (size_t st = 0; st < p->steps.size(); ++st)
+          if (p->steps[st].kind == 1 && p->exec_ops[p->pass_ops[st].first].block == (int)b) {
+            const uint16_t* dv = wdev.data() + (size_t)p->steps[st].idx * p->wimg_pass;
+            for (uint32_t nn = 0; nn < 64; ++nn)
+              for (uint32_t k = 0; k < 64; ++k)
+                worst = std::max(worst, std::fabs(w_digit_value(img.data(), nn, k) - w_digit_value(dv, nn, k)));
+          }
+      } else if (blk.rep == OP_TC) {
         // compare the W image with one built on the host from the host product: the
         // value the MMAs use is hi + lo (hi and lo alone may trade one ulp at a tie)
         std::vector<uint16_t> img(32768);
@@ -942,12 +966,7 @@ qs_status qs_plan_execute_batched(qs_plan_t p, qs_state_t* states, int B, const 
     CK(cudaEventRecord(p->ev_out, st));
     CK(cudaStreamWaitEvent(user_st, p->ev_out, 0));
     plan_done(*p, st);
-    if (!p->tcdesc.empty()) {
-      int err = 0;
-      CK(cudaMemcpyAsync(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
-      CK(cudaStreamSynchronize(st));
-      if (err) throw Error(QS_ERR_TIMEOUT, "tensor-core pass: an MMA completion wait timed out");
-    }
+    check_tc_error(*p, st);
     if (terms && nterms) {
       CK(cudaStreamSynchronize(st));
       for (int b = 0; b < B; ++b) expvals[b] = combine_expval(P, terms, vals.data() + (size_t)b * P.zlist.size());

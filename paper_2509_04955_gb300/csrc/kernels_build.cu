@@ -7,8 +7,9 @@
 // row); column c of the 2^k x 2^k matrix is e_c pushed through the member
 // gates, in FP64. Dense blocks are written to the
 // block table, diagonal blocks as their diagonal, tensor-core blocks as the
-// bf16 hi / lo W image in the K-major 128-byte-swizzled layout the
-// tensor-core pass loads (real embedding W[2c+a][2c'+b] of U[c'][c]).
+// 16-bit hi / lo W image (complex64 pass) or the five fp16 digit planes
+// (complex128 pass) in the K-major 128-byte-swizzled layout the tensor-core
+// pass loads (real embedding W[2c+a][2c'+b] of U[c'][c]).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -41,7 +42,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_blocks(const DevBlock* 
                                                                  const double2* __restrict__ gtab, int64_t gstride,
                                                                  double2* __restrict__ btab, int64_t bstride,
                                                                  uint16_t* __restrict__ wimg, int64_t wstride,
-                                                                 int whalf) {
+                                                                 int wmode, int64_t wpass) {
   extern __shared__ double2 M[];   // D x D, row-major: M[r * D + c]
   const DevBlock blk = blocks[blockIdx.x];
   const int row = blockIdx.y;
@@ -112,11 +113,37 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_blocks(const DevBlock* 
   } else if (blk.kind == 1) {
     double2* out = btab + (int64_t)row * bstride + blk.out;
     for (int i = threadIdx.x; i < D; i += kBuildThreads) out[i] = M[i * D + i];
+  } else if (wmode == 2) {
+    // complex128 pass (D = 32): digit planes of the real embedding, entry
+    // (nn, k) = W[k][nn], w = 2^-8 sum_j g_j 2^(-9 j) with balanced digits of
+    // X = rint(w 2^53) (the host's build_w_digits), fp16, K-major 128-byte
+    // swizzle; planes 5..9 hold 2^-9 g_1 .. 2^-9 g_5
+    uint16_t* img = wimg + (int64_t)row * wstride + blk.out * wpass;
+    for (int e = threadIdx.x; e < 64 * 64; e += kBuildThreads) {
+      const int nn = e >> 6, kk = e & 63;
+      const int co = nn >> 1, b = nn & 1, ci = kk >> 1, a = kk & 1;
+      const double2 uv = M[co * 32 + ci];
+      const double w = a == 0 ? (b == 0 ? uv.x : uv.y) : (b == 0 ? -uv.y : uv.x);
+      long long X = __double2ll_rn(w * 9007199254740992.0);   // w 2^53 (exact scaling)
+      int g[6];
+#pragma unroll
+      for (int j = 5; j >= 1; --j) {
+        g[j] = (int)(((X + 256) & 511) - 256);
+        X = (X - g[j]) / 512;
+      }
+      g[0] = (int)X;
+      const int off = (nn * 128 + (((kk >> 3) ^ (nn & 7)) << 4) + (kk & 7) * 2) >> 1;
+#pragma unroll
+      for (int j = 0; j < 5; ++j) img[j * 4096 + off] = __half_as_ushort(__int2half_rn(g[j]));
+#pragma unroll
+      for (int j = 1; j < 6; ++j) img[(4 + j) * 4096 + off] = __half_as_ushort(__float2half_rn((float)g[j] * 0.001953125f));
+    }
   } else {
     // W image: 16-byte chunks of 8 consecutive k (4 input columns) of output row nn,
     // K atom `atom`, 128-byte swizzle; hi / lo split in FP32 (the product is FP64),
     // fp16 parts when `whalf` (the pass splits the state into fp16), else bf16
-    uint16_t* img = wimg + (int64_t)row * wstride + blk.out * 32768;
+    const bool whalf = wmode == 1;
+    uint16_t* img = wimg + (int64_t)row * wstride + blk.out * wpass;
     for (int e = threadIdx.x; e < 2048; e += kBuildThreads) {
       const int atom = e >> 10, nn = (e >> 3) & 127, ch = e & 7;
       const int co = nn >> 1, b = nn & 1, ci0 = atom * 32 + ch * 4;
@@ -161,12 +188,12 @@ cudaError_t prepare_build_blocks() {
 
 cudaError_t launch_build_blocks(const DevBlock* blocks, int nblocks, const DevMember* mem, const double2* gtab,
                                 int64_t gstride, int rows, double2* btab, int64_t bstride, uint16_t* wimg,
-                                int64_t wstride, int whalf, cudaStream_t st) {
+                                int64_t wstride, int wmode, int64_t wpass, cudaStream_t st) {
   if (nblocks == 0 || rows == 0) return cudaSuccess;
   if (!g_build_ready) return cudaErrorInvalidConfiguration;   // not prepared
   const int smem = 64 * 64 * (int)sizeof(double2);
   k_build_blocks<<<dim3(nblocks, rows), kBuildThreads, smem, st>>>(blocks, mem, gtab, gstride, btab, bstride, wimg,
-                                                                   wstride, whalf);
+                                                                   wstride, wmode, wpass);
   note_launch();
   return cudaGetLastError();
 }

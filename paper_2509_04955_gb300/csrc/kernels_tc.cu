@@ -33,28 +33,12 @@
 #include <cuda_runtime.h>
 
 #include "qs_internal.h"
+#include "tcgen05.cuh"
 
 namespace qs {
 
 constexpr int kTcAtomBytes = 16384;            // 128 rows x 128 B (64 bf16 of K)
 constexpr int kTcOperandBytes = 2 * kTcAtomBytes;   // K = 128 bf16 per row
-constexpr uint32_t kTcSpinLimit = 1u << 26;
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 B apart (stride byte offset), version 1 (bits 46-48).
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
-  uint64_t d = 0;
-  d |= (uint64_t)((addr >> 4) & 0x3FFF);
-  d |= (uint64_t)1 << 16;                 // leading byte offset (unused with 128B swizzle)
-  d |= (uint64_t)(1024 >> 4) << 32;       // stride byte offset
-  d |= (uint64_t)1 << 46;                 // descriptor version
-  d |= (uint64_t)2 << 61;                 // SWIZZLE_128B
-  return d;
-}
 
 // Instruction descriptor: kind::f16, FP32 D, both operands K-major, M = 128,
 // N = 128; A and B both BF16 (PREC 1, 3) or both FP16 (PREC 4).
@@ -90,41 +74,6 @@ __device__ __forceinline__ void split_amp(float2 a, float scale, uint32_t& hi, u
     hi = *(const uint32_t*)&h;
     lo = *(const uint32_t*)&l;
   }
-}
-
-__device__ __forceinline__ void mma_commit(uint32_t mbar) {
-  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar)
-               : "memory");
-}
-
-__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t phase) {
-  for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
-    uint32_t done;
-    asm volatile(
-        "{\n\t.reg .pred p;\n\t"
-        "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-        "selp.u32 %0, 1, 0, p;\n\t}\n"
-        : "=r"(done)
-        : "r"(mbar), "r"(phase)
-        : "memory");
-    if (done) return true;
-  }
-  return false;
-}
-
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
-  uint32_t r[32];
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr));
-  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Byte offset of bf16 element (row, k) in a K-major SW128 operand of 128 rows.
@@ -371,26 +320,6 @@ __device__ __forceinline__ void mma_bf16_tmem_a(uint32_t tmem_d, uint32_t tmem_a
       "r"(tmem_a), "l"(b), "r"(idesc_for<PREC>()), "r"(acc));
 }
 
-__device__ __forceinline__ void tmem_st16(uint32_t taddr, const uint32_t* v) {
-  asm volatile(
-      "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};" ::"r"(
-          taddr),
-      "r"(v[0]), "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7]), "r"(v[8]), "r"(v[9]),
-      "r"(v[10]), "r"(v[11]), "r"(v[12]), "r"(v[13]), "r"(v[14]), "r"(v[15])
-      : "memory");
-}
-
-// Warp-uniform bounded wait: every lane polls, and the warp goes on only if
-// all lanes saw the phase complete (warp-collective tcgen05 ops follow).
-__device__ __forceinline__ bool mbar_wait_warp(uint32_t mbar, uint32_t phase) {
-  const bool ok = mbar_wait(mbar, phase);
-  return __all_sync(0xffffffffu, ok);
-}
-
-__device__ __forceinline__ void mbar_arrive(uint32_t mbar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
-}
-
 // Issues the MMAs of one tile with A in tensor memory: D = A * W^T, K = 128.
 template <int PREC>
 __device__ __forceinline__ void issue_tile_mmas_ta(uint32_t tmem_d, uint32_t a_hi, uint32_t wh, uint32_t wl) {
@@ -456,8 +385,11 @@ template <int PREC, bool MULTI>
 __global__ void __launch_bounds__(kTcbThreads, 1)
     k_tc_bulk(float2* __restrict__ psi0, void* const* __restrict__ psis, TcPassDesc p,
               const uint4* __restrict__ wimg, int64_t wstride16, int lg_tiles1, uint64_t ntiles,
-              float ascale, int* __restrict__ err) {
-  // ascale: factor applied to the amplitudes before the fp16 split (PREC 4), undone on output
+              float ascale, int* __restrict__ err, uint32_t spin) {
+  // ascale: factor applied to the amplitudes before the fp16 split (PREC 4), undone on output.
+  // spin: polls allowed per pipeline wait; when one runs out the CTA records the
+  // error and stops, and the waits for its copies and MMAs already in flight
+  // use the default bound (kTcSpinLimit), so it never exits with them pending.
   extern __shared__ __align__(1024) unsigned char tcb_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)tcb_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* slots = smem;                                   // 2 x 64 KiB
@@ -577,7 +509,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
     for (; i < my; ++i) {
       if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
       const int s = (int)(i & 1);
-      if (i >= 2 && !mbar_wait_warp(smem_u32(empty + s), (uint32_t)(((i >> 1) - 1) & 1))) {
+      if (i >= 2 && !mbar_wait_warp(smem_u32(empty + s), (uint32_t)(((i >> 1) - 1) & 1), spin)) {
         if (lane == 0) fail(1);
         break;
       }
@@ -601,7 +533,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
         // parity wait is exact only within one phase.) wfree completes once per state
         // boundary and its next completion needs this reload, so phase w_issued is
         // the one to wait for.
-        if (!mbar_wait_warp(smem_u32(wfree), (uint32_t)(w_issued & 1))) {
+        if (!mbar_wait_warp(smem_u32(wfree), (uint32_t)(w_issued & 1), spin)) {
           if (lane == 0) fail(1);
           ++i;   // tile i's copies are in flight
           break;
@@ -635,11 +567,11 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
         if (*(volatile int*)&s_abort) break;
         const int a = (int)(i & 1);
         if (new_state(i)) {
-          if (!mbar_wait(smem_u32(wfull), (uint32_t)(w_seen & 1))) { fail(1); break; }
+          if (!mbar_wait(smem_u32(wfull), (uint32_t)(w_seen & 1), spin)) { fail(1); break; }
           ++w_seen;
         }
-        if (!mbar_wait(smem_u32(afull + a), (uint32_t)((i >> 1) & 1))) { fail(1); break; }
-        if (i >= 2 && !mbar_wait(smem_u32(dfree + a), (uint32_t)(((i >> 1) - 1) & 1))) { fail(1); break; }
+        if (!mbar_wait(smem_u32(afull + a), (uint32_t)((i >> 1) & 1), spin)) { fail(1); break; }
+        if (i >= 2 && !mbar_wait(smem_u32(dfree + a), (uint32_t)(((i >> 1) - 1) & 1), spin)) { fail(1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         issue_tile_mmas_ta<PREC>(tmem + 256 + a * 128, tmem + a * 128, wh, wl);
         mma_commit(smem_u32(mdone + a));
@@ -677,8 +609,8 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
         if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
         const int s = (int)(i & 1);
         // A buffer s was last read by the MMAs of tile i - 2
-        if (i >= 2 && !mbar_wait_warp(smem_u32(mdone + s), (uint32_t)(((i >> 1) - 1) & 1))) { ok = false; break; }
-        if (!mbar_wait_warp(smem_u32(full + s), (uint32_t)((i >> 1) & 1))) { ok = false; break; }
+        if (i >= 2 && !mbar_wait_warp(smem_u32(mdone + s), (uint32_t)(((i >> 1) - 1) & 1), spin)) { ok = false; break; }
+        if (!mbar_wait_warp(smem_u32(full + s), (uint32_t)((i >> 1) & 1), spin)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const float2* sl = slot_f + s * (kTcbSlotBytes / 8);
 #pragma unroll 1
@@ -726,7 +658,7 @@ __global__ void __launch_bounds__(kTcbThreads, 1)
       for (uint64_t i = 0; i < my; ++i) {
         if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
         const int d = (int)(i & 1);
-        if (!mbar_wait_warp(smem_u32(mdone + d), (uint32_t)((i >> 1) & 1))) { ok = false; break; }
+        if (!mbar_wait_warp(smem_u32(mdone + d), (uint32_t)((i >> 1) & 1), spin)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint64_t tt = tile_of(i);
         float2* __restrict__ psi = state_ptr(tt);
@@ -818,10 +750,10 @@ float tc_amp_scale(int n, int prec) {
 template <int PREC>
 static void launch_tc_instance(int pipeline, bool multi, unsigned grid, size_t smem, cudaStream_t st, float2* psi,
                                void* const* psis, const TcPassDesc& p, const uint4* w, int64_t ws16, int lg,
-                               uint64_t ntiles, float sc, int* err) {
+                               uint64_t ntiles, float sc, int* err, uint32_t spin) {
   if (pipeline == 0) {
-    if (multi) k_tc_bulk<PREC, true><<<grid, kTcbThreads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err);
-    else k_tc_bulk<PREC, false><<<grid, kTcbThreads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err);
+    if (multi) k_tc_bulk<PREC, true><<<grid, kTcbThreads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err, spin);
+    else k_tc_bulk<PREC, false><<<grid, kTcbThreads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err, spin);
   } else {
     if (multi) k_tc_block<PREC, true><<<grid, kTc2Threads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err);
     else k_tc_block<PREC, false><<<grid, kTc2Threads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, sc, err);
@@ -830,7 +762,8 @@ static void launch_tc_instance(int pipeline, bool multi, unsigned grid, size_t s
 
 cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
                                    const TcPassDesc& p, const void* wimg, int prec, int pipeline, int* err,
-                                   cudaStream_t st) {
+                                   cudaStream_t st, uint32_t spin) {
+  if (spin == 0) spin = kTcSpinLimit;
   if (!g_tc_ready) return cudaErrorInvalidConfiguration;   // not prepared
   if (prec != 1 && prec != 3 && prec != 4) return cudaErrorInvalidValue;
   const uint64_t ntiles = (1ull << (n - 13)) * (uint64_t)nstates;
@@ -840,18 +773,18 @@ cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, in
   const bool multi = psis != nullptr;
   const uint4* w = (const uint4*)wimg;
   if (prec == 4)
-    launch_tc_instance<4>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err);
+    launch_tc_instance<4>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err, spin);
   else if (prec == 3)
-    launch_tc_instance<3>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err);
+    launch_tc_instance<3>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err, spin);
   else
-    launch_tc_instance<1>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err);
+    launch_tc_instance<1>(pipeline, multi, grid, smem, st, (float2*)psi, psis, p, w, wstride / 8, n - 13, ntiles, sc, err, spin);
   note_launch();
   return cudaGetLastError();
 }
 
 cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int pipeline,
-                           int* err, cudaStream_t st) {
-  return launch_tc_pass_batched(psi, nullptr, 1, 0, n, p, wimg, prec, pipeline, err, st);
+                           int* err, cudaStream_t st, uint32_t spin) {
+  return launch_tc_pass_batched(psi, nullptr, 1, 0, n, p, wimg, prec, pipeline, err, st, spin);
 }
 
 }  // namespace qs

@@ -1,0 +1,536 @@
+// Tensor-core pass for complex128 states: one dense 5-qubit block (32 x 32
+// complex, FP64 entries) applied with fp16 tcgen05 MMAs whose products and
+// sums are exact, so the result carries about 45 significant bits per pass
+// with no FP64 instruction.
+//
+// A fused block of Section 3.4 on qubits Q (|Q| = 5) is psi'[r, :] = U psi[r, :]
+// over the 2^(n-5) rows r (the other bits). Over reals with interleaved
+// (re, im) columns this is the real GEMM D[r][n] = sum_k A[r][k] W[k][n],
+// K = N = 64, with W the real embedding of U (as in the complex64 pass).
+//
+// Exact slicing (the error-free splitting of Ozaki, Ogita, Oishi and Rump,
+// "Error-free transformations of matrix multiplication", 2012, with the
+// fixed-point digits used for fp16 tensor cores): every row of A gets one
+// power-of-two scale 2^E with |a| < 2^E for the row's 64 reals, and each a is
+// written as 2^(E-8) sum_{i<6} d_i 2^(-9 i) with integer digits |d_i| <= 260;
+// each W entry (|w| <= 1) as 2^-8 sum_{j<6} g_j 2^(-9 j), |g_j| <= 256. Digits
+// are small integers, exact in fp16, and a digit product is exact in the
+// MMA. The products A_i W_j with i + j = l (level l) are accumulated in FP32 in
+// tensor memory, one accumulator per level; a level sums at most 4 products
+// of K = 64 terms of magnitude <= 260 * 256, so levels 0..2 stay below 2^24 and
+// are exact integers (level 3 too, save for an adversarial alignment of all
+// 256 of its digit products, which costs at most one unit of level 3). The
+// fifth accumulator holds level 4 plus 2^-9 times level 5 (its products
+// A_i W_(5-i), i = 0..5, against W planes or an A plane pre-scaled by 2^-9,
+// which fp16 holds exactly), rounded in FP32 at about 2^-24 of level 4. The
+// levels, D = 2^(E-16) sum_l acc_l 2^(-9 l), are combined in FP32 pairs
+// (TwoSum) and written back as FP64 by their bit patterns. What is dropped
+// (A's bits below 2^-47 of its scale, W's below 2^-54, levels above 5) leaves
+// an absolute error per pass of about 2^-47 times the row's scale 2^E
+// (|a| < 2^E <= 2 max |a|).
+//
+// Pipeline (one persistent CTA per SM, 576 threads, tiles of 128 rows x 32
+// columns = 4096 amplitudes = 64 KiB, 12 tile qubits: the block's 5 and the 7
+// lowest other qubits):
+//   warp 16  producer: cp.async.bulk of the tile's runs (>= 2 KiB each) into
+//            one of two 64 KiB landing slots;
+//   warps 0-7 converters, thread = (row, column half): the row's exponent (the
+//            two halves exchange their maxima), then the six digit planes of
+//            the tile written to tensor memory with tcgen05.st (A operand);
+//   warp 17  one thread issues the 21 products x 4 k-steps (M = 128, N = 64,
+//            K = 16, A from tensor memory, W planes from shared memory) and
+//            commits;
+//   warps 8-15 drainers, thread = (row, column half): tcgen05.ld of the five
+//            accumulators, combination, FP64 stores to HBM.
+// Tensor memory (512 columns): A digit planes at 32 p (p < 6), level-l
+// accumulator at 192 + 64 l. Both are single-buffered, so a tile's MMAs wait
+// for the previous tile's accumulators to be read, and its digits for the
+// previous tile's MMAs; the landing slots keep the loads streaming meanwhile.
+//
+// Every wait is bounded (`spin` polls; the waits for copies and MMAs already in
+// flight at an abort use kTcSpinLimit): a wait that runs out records *err = 1,
+// the CTA stops taking tiles, lets its copies land and its MMAs finish, frees
+// its tensor memory and returns.
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+#include "qs_internal.h"
+#include "tcgen05.cuh"
+
+namespace qs {
+
+constexpr int kT2Warps = 16;                              // converters + drainers
+constexpr int kT2Threads = (kT2Warps + 2) * 32;           // + producer warp + MMA warp
+constexpr int kT2SlotBytes = 65536;                       // 4096 complex128
+constexpr int kT2PlaneBytes = 8192;                       // W digit plane: 64 (N) x 64 (K) fp16, SW128
+constexpr int kT2WBytes = 10 * kT2PlaneBytes;           // g_0..g_4, then 2^-9 g_1..2^-9 g_5
+constexpr uint32_t kT2TmemCols = 512;
+constexpr uint32_t kT2AccCol = 192;
+// kind::f16, fp16 A and B, FP32 D, both K-major, N = 64 (bits 17-22), M = 128 (bits 24-28)
+constexpr uint32_t kT2Idesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+
+__device__ __forceinline__ void t2_mma(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "r"(tmem_a), "l"(b), "r"(kT2Idesc), "r"(acc));
+}
+
+__device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
+  asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
+               "r"(v[1]), "r"(v[2]), "r"(v[3]), "r"(v[4]), "r"(v[5]), "r"(v[6]), "r"(v[7])
+               : "memory");
+}
+
+// Loads 8 columns (this thread's lane); the caller waits with tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+               : "r"(taddr));
+}
+
+// rint for |x| < 2^22 by the 1.5 * 2^23 shift (rounding to nearest even).
+__device__ __forceinline__ float t2_rint(float x) {
+  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+}
+
+// The six digits of one FP64 value a (bit pattern whi:wlo) of a row with
+// biased-exponent maximum emax_b: s = a 2^(8 - E), E = emax_b - 1022, so
+// |s| < 256, and s ~ sum_{i<6} d_i 2^(-9 i) (d[5] is returned as 2^-9 d5,
+// the form its tensor-memory plane holds); the error is below 2^-39 (the 6
+// FP64 mantissa bits the split drops) and 2^-46. The FP64 mantissa is cut by
+// bits into hi (sign, exponent, top 23 stored bits) and lo (the next 23 bits,
+// pre-scaled by 2^18); digits come from hi with exact FP32 steps until hi is
+// used up, lo joins at digit 2. Values with |s| < 2^-40 (and FP64 zeros /
+// subnormals) give zero digits.
+__device__ __forceinline__ void t2_digits(uint32_t whi, uint32_t wlo, int emax_b, float* d) {
+  const int ex = (int)((whi >> 20) & 0x7ffu);
+  const int fe = ex + 134 - emax_b;             // biased FP32 exponent of s (<= 134)
+  const uint32_t sign = whi & 0x80000000u;
+  float hi = 0.f, lo18 = 0.f;
+  if (ex != 0 && fe >= 87) {
+    hi = __uint_as_float(sign | ((uint32_t)fe << 23) | ((whi & 0xfffffu) << 3) | (wlo >> 29));
+    // lo = m 2^(e_s - 46) with m the remainder's top 23 bits: X - 2^x with
+    // X = (1 + m 2^-23) 2^x, x = e_s - 23; pre-scaled by 2^18: x = e_s - 5
+    const uint32_t eb = (uint32_t)(fe - 5) << 23;
+    lo18 = __fsub_rn(__uint_as_float(sign | eb | ((wlo & 0x1fffffffu) >> 6)), __uint_as_float(sign | eb));
+  }
+  d[0] = t2_rint(hi);
+  float t = __fsub_rn(hi, d[0]);                // exact, |t| <= 1/2
+  float u = __fmul_rn(t, 512.f);
+  d[1] = t2_rint(u);
+  t = __fsub_rn(u, d[1]);                       // exact
+  const float v = __fmaf_rn(t, 512.f, lo18);
+  d[2] = t2_rint(v);
+  const float r = __fadd_rn(__fmaf_rn(t, 512.f, -d[2]), lo18);
+  u = __fmul_rn(r, 512.f);
+  d[3] = t2_rint(u);
+  t = __fsub_rn(u, d[3]);
+  u = __fmul_rn(t, 512.f);
+  d[4] = t2_rint(u);
+  t = __fsub_rn(u, d[4]);
+  d[5] = __fmul_rn(t2_rint(__fmul_rn(t, 512.f)), 0.001953125f);
+}
+
+__device__ __forceinline__ void t2_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// FP64 bit pattern of 2^(emax_b - 1038) * (acc0 + acc1 2^-9 + acc2 2^-18 +
+// acc3 2^-27 + acc4 2^-36): FP32-pair sum, then s + e joined by integer
+// arithmetic on s's widened bit pattern (e added in units of 2^-46 of s).
+__device__ __forceinline__ double t2_combine(float c0, float c1, float c2, float c3, float c4, int emax_b) {
+  // levels 1-3 can be as large as s when the leading levels cancel, so each
+  // enters through TwoSum; level 4 (< 2^-12 units) is added to the error word
+  float s, e, e2;
+  t2_two_sum(c0, __fmul_rn(c1, 0.001953125f), s, e);
+  t2_two_sum(s, __fmul_rn(c2, 3.814697265625e-06f), s, e2);
+  e = __fadd_rn(e, e2);
+  t2_two_sum(s, __fmul_rn(c3, 7.450580596923828e-09f), s, e2);
+  e = __fadd_rn(e, e2);
+  e = __fmaf_rn(c4, 1.4551915228366852e-11f, e);
+  const float s2 = __fadd_rn(s, e);             // FastTwoSum: |s| >= |e|
+  e = __fsub_rn(e, __fsub_rn(s2, s));
+  s = s2;
+  const uint32_t us = __float_as_uint(s);
+  const int fs = (int)((us >> 23) & 0xffu);     // biased FP32 exponent of s
+  const int de = fs + emax_b - 142;             // biased FP64 exponent of the result
+  if (fs == 0 || de <= 0) return 0.0;           // |result| < 2^-1022 (or s = 0): flushed
+  long long mag = ((long long)de << 52) | ((long long)(us & 0x7fffffu) << 29);
+  if (fs >= 46 && fs <= 254) {
+    // e in units of 2^(x_s - 46), x_s = fs - 127: |k| <= 2^22
+    const float sc = __uint_as_float((uint32_t)(300 - fs) << 23);
+    const int k = __float_as_int(__fadd_rn(__fmul_rn(e, sc), 12582912.0f)) - 0x4B400000;
+    long long adj = (long long)((us >> 31) ? -k : k) << 6;   // in units of s's FP64 ulp
+    if ((us & 0x7fffffu) == 0 && adj < 0) adj *= 2;        // below a power of two the ulp halves
+    mag += adj;
+  }
+  return __longlong_as_double((long long)((unsigned long long)(us >> 31) << 63) | mag);
+}
+
+template <bool MULTI>
+__global__ void __launch_bounds__(kT2Threads, 1)
+    k_tc128(double2* __restrict__ psi0, void* const* __restrict__ psis, Tc5PassDesc p,
+            const uint4* __restrict__ wimg, int64_t wstride16, int lg_tiles1, uint64_t ntiles,
+            int* __restrict__ err, uint32_t spin) {
+  extern __shared__ __align__(1024) unsigned char t2_smem_raw[];
+  unsigned char* smem = (unsigned char*)(((uintptr_t)t2_smem_raw + 1023) & ~(uintptr_t)1023);
+  unsigned char* slots = smem;                                  // 2 x 64 KiB
+  unsigned char* W = smem + 2 * kT2SlotBytes;                   // 10 digit planes
+  uint64_t* tbase = (uint64_t*)(W + kT2WBytes);                 // 4 x 256: tile number byte -> offset
+  uint64_t* runoff = tbase + 4 * 256;                           // 32: global offset of run j
+  uint64_t* coff = runoff + 32;                                 // 32: global offset of column c
+  uint32_t* lamcol = (uint32_t*)(coff + 32);                    // 32: tile-local index of column c
+  int32_t* xe = (int32_t*)(lamcol + 32);                        // [2][128][2]: half-row exponent maxima
+  int32_t* etab = xe + 2 * 128 * 2;                             // [2][128]: row exponent maxima
+  int32_t* qpos = etab + 2 * 128;                               // tile[12], row[7], col[5], p
+  // full[2] empty[2] afull mdone dfree efull[2] wfull wfree xbar[2][4]
+  uint64_t* bar = (uint64_t*)(qpos + 26);
+  uint32_t* tmem_slot = (uint32_t*)(bar + 19);
+  __shared__ int s_abort;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int32_t* s_tile = qpos;
+  int32_t* s_row = qpos + 12;
+  int32_t* s_col = qpos + 19;
+  if (tid == 0) {
+    for (int k = 0; k < 12; ++k) s_tile[k] = p.tile[k];
+    for (int k = 0; k < 7; ++k) s_row[k] = p.row[k];
+    for (int k = 0; k < 5; ++k) s_col[k] = p.col[k];
+    int pp = 0;
+    while (pp < 12 && p.tile[pp] == pp) ++pp;
+    qpos[24] = pp;
+    s_abort = 0;
+    // arrivals: full, wfull, wfree, mdone: 1 (expect_tx / commit); empty, afull, dfree, efull: one per
+    // warp of 8; xbar (row-exponent exchange of converter warps quad and quad + 4): 2
+    const uint32_t cnt[19] = {1, 1, 8, 8, 8, 1, 8, 8, 8, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2};
+    for (int i = 0; i < 19; ++i)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)), "r"(cnt[i]));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const uint64_t tmask1 = (1ull << lg_tiles1) - 1;
+  const bool contig = MULTI && wstride16 != 0;
+  const uint64_t chunk_t = (ntiles + gridDim.x - 1) / gridDim.x;
+  const uint64_t t_begin = contig ? (uint64_t)blockIdx.x * chunk_t : blockIdx.x;
+  const uint64_t tstep = contig ? 1 : gridDim.x;
+  const uint64_t t_end = contig ? (t_begin + chunk_t < ntiles ? t_begin + chunk_t : ntiles) : ntiles;
+  const uint64_t my = t_begin < t_end ? (t_end - t_begin + tstep - 1) / tstep : 0;
+  if (my > 0) {   // a trailing CTA can get an empty range that starts past the last state
+    const uint4* w0 = wimg + (contig ? (int64_t)(t_begin >> lg_tiles1) * wstride16 : 0);
+    for (int i = tid; i < kT2WBytes / 16; i += kT2Threads) ((uint4*)W)[i] = w0[i];
+  }
+  __syncthreads();
+  const int pr = qpos[24];            // log2 of the run length in amplitudes (7..12)
+  const int nruns = 1 << (12 - pr);
+  auto lam_of = [&](int q) {          // position of qubit q among the 12 tile qubits
+    int l = 0;
+    while (l < 11 && s_tile[l] != q) ++l;
+    return l;
+  };
+  for (int e = tid; e < 4 * 256; e += kT2Threads) {
+    uint64_t x = (uint64_t)(e & 255) << (8 * (e >> 8));
+    for (int k = 0; k < 12; ++k) {
+      const int q = s_tile[k];
+      x = ((x >> q) << (q + 1)) | (x & ((1ull << q) - 1));
+    }
+    tbase[e] = x;
+  }
+  if (tid < 32) {
+    uint64_t o = 0;
+    uint32_t lc = 0;
+    for (int b = 0; b < 5; ++b) {
+      o |= (uint64_t)((tid >> b) & 1) << s_col[b];
+      lc |= (uint32_t)((tid >> b) & 1) << lam_of(s_col[b]);
+    }
+    coff[tid] = o;
+    lamcol[tid] = lc;
+    if (tid < nruns) {
+      uint64_t r = 0;
+      for (int b = 0; b < 12 - pr; ++b) r |= (uint64_t)((tid >> b) & 1) << s_tile[pr + b];
+      runoff[tid] = r;
+    }
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(kT2TmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // W is read by the MMA (async proxy)
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = *tmem_slot;
+  uint64_t* full = bar;
+  uint64_t* empty = bar + 2;
+  uint64_t* afull = bar + 4;
+  uint64_t* mdone = bar + 5;
+  uint64_t* dfree = bar + 6;
+  uint64_t* efull = bar + 7;
+  uint64_t* wfull = bar + 9;
+  uint64_t* wfree = bar + 10;   // completes when the MMAs on a state's W planes are done
+  uint64_t* xbar = bar + 11;    // [parity][quad]
+  auto tile_of = [&](uint64_t i) -> uint64_t { return t_begin + i * tstep; };
+  auto state_ptr = [&](uint64_t tt) -> double2* {
+    if constexpr (MULTI) return (double2*)psis[tt >> lg_tiles1];
+    else return psi0;
+  };
+  auto new_state = [&](uint64_t i) -> bool {
+    return contig && i > 0 && (tile_of(i) >> lg_tiles1) != (tile_of(i - 1) >> lg_tiles1);
+  };
+  auto fail = [&](int code) {
+    atomicExch(err, code);
+    *(volatile int*)&s_abort = 1;
+  };
+  auto tile_base = [&](uint64_t t) -> uint64_t {
+    return tbase[t & 255] | tbase[256 + ((t >> 8) & 255)] | tbase[512 + ((t >> 16) & 255)] |
+           tbase[768 + ((t >> 24) & 255)];
+  };
+
+  if (warp == kT2Warps) {
+    // ---------------- producer: bulk copies of tile runs into the slots
+    const uint32_t runb = 16u << pr;
+    uint64_t i = 0, w_issued = 0;
+    for (; i < my; ++i) {
+      if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
+      const int s = (int)(i & 1);
+      if (i >= 2 && !mbar_wait_warp(smem_u32(empty + s), (uint32_t)(((i >> 1) - 1) & 1), spin)) {
+        if (lane == 0) fail(1);
+        break;
+      }
+      if (lane == 0)
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full + s)),
+                     "r"((uint32_t)kT2SlotBytes)
+                     : "memory");
+      __syncwarp();
+      const uint64_t tt = tile_of(i);
+      const double2* src = state_ptr(tt) + tile_base(tt & tmask1);
+      for (int j = lane; j < nruns; j += 32)
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(slots + s * kT2SlotBytes + j * runb)),
+            "l"(src + runoff[j]), "r"(runb), "r"(smem_u32(full + s))
+            : "memory");
+      if (new_state(i)) {
+        // W planes of the next state once the MMAs of tile i - 1 (the last on the
+        // old planes) are done: wfree completes once per state boundary.
+        if (!mbar_wait_warp(smem_u32(wfree), (uint32_t)(w_issued & 1), spin)) {
+          if (lane == 0) fail(1);
+          ++i;   // tile i's copies are in flight
+          break;
+        }
+        if (lane == 0) {
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(wfull)),
+                       "r"((uint32_t)kT2WBytes)
+                       : "memory");
+          asm volatile(
+              "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                  smem_u32(W)),
+              "l"(wimg + (int64_t)(tt >> lg_tiles1) * wstride16), "r"((uint32_t)kT2WBytes), "r"(smem_u32(wfull))
+              : "memory");
+        }
+        ++w_issued;
+        __syncwarp();
+      }
+    }
+    // after an abort, the copies already issued land before the CTA exits
+    if (*(volatile int*)&s_abort) {
+      for (uint64_t k = i > 2 ? i - 2 : 0; k < i; ++k) mbar_wait(smem_u32(full + (k & 1)), (uint32_t)((k >> 1) & 1));
+      if (w_issued > 0) mbar_wait(smem_u32(wfull), (uint32_t)((w_issued - 1) & 1));
+    }
+  } else if (warp == kT2Warps + 1) {
+    // ---------------- MMA issue (one thread): level l = i + j gets A_i W_j; the
+    // level-4 accumulator also A_i (2^-9 W_(5-i)), i = 0..4 (planes 9 - i), and
+    // (2^-9 A_5) W_0
+    if (lane == 0) {
+      const uint32_t wb = smem_u32(W);
+      uint64_t i = 0, w_seen = 0;
+      for (; i < my; ++i) {
+        if (*(volatile int*)&s_abort) break;
+        if (new_state(i)) {
+          if (!mbar_wait(smem_u32(wfull), (uint32_t)(w_seen & 1), spin)) { fail(1); break; }
+          ++w_seen;
+        }
+        if (!mbar_wait(smem_u32(afull), (uint32_t)(i & 1), spin)) { fail(1); break; }
+        if (i >= 1 && !mbar_wait(smem_u32(dfree), (uint32_t)((i - 1) & 1), spin)) { fail(1); break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int l = 0; l < 5; ++l) {
+#pragma unroll
+          for (int ai = 0; ai <= l; ++ai) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              t2_mma(tmem + kT2AccCol + 64 * l, tmem + 32 * ai + 8 * ks,
+                     smem_desc(wb + (l - ai) * kT2PlaneBytes + 32 * ks), (ai | ks) ? 1u : 0u);
+          }
+        }
+#pragma unroll
+        for (int ai = 0; ai <= 4; ++ai) {
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            t2_mma(tmem + kT2AccCol + 64 * 4, tmem + 32 * ai + 8 * ks, smem_desc(wb + (9 - ai) * kT2PlaneBytes + 32 * ks),
+                   1u);
+        }
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks)
+          t2_mma(tmem + kT2AccCol + 64 * 4, tmem + 32 * 5 + 8 * ks, smem_desc(wb + 32 * ks), 1u);
+        mma_commit(smem_u32(mdone));
+        if (i + 1 < my && new_state(i + 1)) mma_commit(smem_u32(wfree));   // last tile on these planes
+      }
+      // MMAs still in flight after an abort complete before the memory is released
+      if (i > 0 && *(volatile int*)&s_abort) mbar_wait(smem_u32(mdone), (uint32_t)((i - 1) & 1));
+    }
+  } else {
+    // ---------------- warps 0-15: thread = (row, column half h: complex columns 16h .. 16h + 15)
+    const bool converter = warp < kT2Warps / 2;
+    const int w8 = converter ? warp : warp - kT2Warps / 2;
+    const int quad = w8 & 3, h = w8 >> 2;
+    const int row = quad * 32 + lane;
+    const uint32_t tq = (uint32_t)(quad * 32) << 16;
+    bool ok = true;
+    if (converter) {
+      uint32_t lrow = 0;
+      for (int b = 0; b < 7; ++b) lrow |= (uint32_t)((row >> b) & 1) << lam_of(s_row[b]);
+      const unsigned char* sl0 = slots;
+      for (uint64_t i = 0; i < my; ++i) {
+        if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
+        const int s = (int)(i & 1), par = (int)(i & 1);
+        if (!mbar_wait_warp(smem_u32(full + s), (uint32_t)((i >> 1) & 1), spin)) { ok = false; break; }
+        const unsigned char* sl = sl0 + s * kT2SlotBytes;
+        // the row's exponent: maximum biased FP64 exponent over its 64 reals
+        int em = 0;
+#pragma unroll 4
+        for (int j = 0; j < 16; ++j) {
+          const uint4 v = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + j]));
+          em = max(em, (int)((v.y >> 20) & 0x7ffu));
+          em = max(em, (int)((v.w >> 20) & 0x7ffu));
+        }
+        // exchange with the warp holding the other half of the same rows (bounded
+        // wait, no named barrier: a warp that aborts must not leave its partner stuck)
+        xe[(par * 128 + row) * 2 + h] = em;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(xbar + par * 4 + quad));
+        if (!mbar_wait_warp(smem_u32(xbar + par * 4 + quad), (uint32_t)((i >> 1) & 1), spin)) { ok = false; break; }
+        em = max(em, xe[(par * 128 + row) * 2 + (h ^ 1)]);
+        // A planes are free once the previous tile's MMAs are done; that also
+        // means the drainers of tile i - 2 (same parity) have read their
+        // exponents (they release the accumulators the MMAs of tile i - 1 need
+        // only after reading them), so this tile's may take their place now.
+        if (i >= 1 && !mbar_wait_warp(smem_u32(mdone), (uint32_t)((i - 1) & 1), spin)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        if (h == 0) etab[par * 128 + row] = em;
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(efull + par));
+#pragma unroll 1
+        for (int c8 = 0; c8 < 2; ++c8) {
+          uint32_t pl[6][8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const uint4 v = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + 8 * c8 + j]));
+            float dr[6], di[6];
+            t2_digits(v.y, v.x, em, dr);
+            t2_digits(v.w, v.z, em, di);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+              const __half2 hv = __floats2half2_rn(dr[q], di[q]);
+              pl[q][j] = *(const uint32_t*)&hv;
+            }
+          }
+#pragma unroll
+          for (int q = 0; q < 6; ++q) tmem_st8(tmem + tq + 32 * q + 16 * h + 8 * c8, pl[q]);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(smem_u32(empty + s));
+          mbar_arrive(smem_u32(afull));
+        }
+      }
+    } else {
+      uint64_t roff = 0;
+      for (int b = 0; b < 7; ++b) roff |= (uint64_t)((row >> b) & 1) << s_row[b];
+      for (uint64_t i = 0; i < my; ++i) {
+        if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
+        const int par = (int)(i & 1);
+        if (!mbar_wait_warp(smem_u32(mdone), (uint32_t)(i & 1), spin)) { ok = false; break; }
+        if (!mbar_wait_warp(smem_u32(efull + par), (uint32_t)((i >> 1) & 1), spin)) { ok = false; break; }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const int em = etab[par * 128 + row];
+        const uint64_t tt = tile_of(i);
+        double2* __restrict__ psi = state_ptr(tt);
+        const uint64_t rb = tile_base(tt & tmask1) | roff;
+#pragma unroll 1
+        for (int c4 = 0; c4 < 4; ++c4) {
+          uint32_t a[5][8];
+#pragma unroll
+          for (int l = 0; l < 5; ++l) tmem_ld8(tmem + tq + kT2AccCol + 64 * l + 32 * h + 8 * c4, a[l]);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (c4 == 3) {   // accumulators read; the last stores follow
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(dfree));
+          }
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            double2 o;
+            o.x = t2_combine(__uint_as_float(a[0][2 * j]), __uint_as_float(a[1][2 * j]), __uint_as_float(a[2][2 * j]),
+                             __uint_as_float(a[3][2 * j]), __uint_as_float(a[4][2 * j]), em);
+            o.y = t2_combine(__uint_as_float(a[0][2 * j + 1]), __uint_as_float(a[1][2 * j + 1]),
+                             __uint_as_float(a[2][2 * j + 1]), __uint_as_float(a[3][2 * j + 1]),
+                             __uint_as_float(a[4][2 * j + 1]), em);
+            psi[rb | coff[16 * h + 4 * c4 + j]] = o;
+          }
+        }
+      }
+    }
+    if (!ok && lane == 0) fail(1);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0)
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kT2TmemCols) : "memory");
+}
+
+size_t tc128_smem_bytes() {
+  return 2 * (size_t)kT2SlotBytes + kT2WBytes + 4 * 256 * 8 + 32 * 8 * 2 + 32 * 4 + 2 * 128 * 2 * 4 + 2 * 128 * 4 +
+         26 * 4 + 19 * 8 + 16 + 1024;
+}
+
+static bool g_tc128_ready = false;
+static int g_tc128_sms = 0;
+
+// Host-side set-up (outside any stream capture): shared-memory attribute and SM count.
+cudaError_t prepare_tc128_pass() {
+  if (g_tc128_ready) return cudaSuccess;
+  const int smem = (int)tc128_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_tc128<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc128<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  g_tc128_sms = device_sm_count();
+  g_tc128_ready = true;
+  return cudaSuccess;
+}
+
+cudaError_t launch_tc128_pass(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
+                              const Tc5PassDesc& p, const void* wimg, int* err, cudaStream_t st, uint32_t spin) {
+  if (!g_tc128_ready) return cudaErrorInvalidConfiguration;   // not prepared
+  if (n < 12) return cudaErrorInvalidValue;
+  if (spin == 0) spin = kTcSpinLimit;
+  const uint64_t ntiles = (1ull << (n - 12)) * (uint64_t)nstates;
+  const unsigned grid = (unsigned)(ntiles < (uint64_t)g_tc128_sms ? ntiles : (uint64_t)g_tc128_sms);
+  const size_t smem = tc128_smem_bytes();
+  const uint4* w = (const uint4*)wimg;
+  const int64_t ws16 = wstride / 8;   // uint16 elements -> uint4
+  if (psis != nullptr)
+    k_tc128<true><<<grid, kT2Threads, smem, st>>>(nullptr, psis, p, w, ws16, n - 12, ntiles, err, spin);
+  else
+    k_tc128<false><<<grid, kT2Threads, smem, st>>>((double2*)psi, nullptr, p, w, ws16, n - 12, ntiles, err, spin);
+  note_launch();
+  return cudaGetLastError();
+}
+
+}  // namespace qs

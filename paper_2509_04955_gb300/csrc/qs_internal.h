@@ -51,7 +51,7 @@ enum OpType : int32_t {
   OP_GATE = 0,    // one original gate: form + tile-local positions, matrix from the gate table
   OP_DENSE = 1,   // dense k-qubit block, matrix (2^k x 2^k) in the block table
   OP_DIAG = 2,    // diagonal k-qubit block, 2^k phases in the block table
-  OP_TC = 3,      // dense 6-qubit block applied on tensor cores (its own pass, complex64)
+  OP_TC = 3,      // dense block on tensor cores (its own pass): 6 qubits for complex64, 5 for complex128
   OP_PHASE = 4    // diagonal phase polynomial of a gate run over the whole register (its own pass)
 };
 
@@ -72,10 +72,12 @@ struct DevMember {
 };
 cudaError_t prepare_build_blocks();
 cudaError_t prepare_tc_pass();
-// whalf: tensor-core W images in fp16 hi / lo (precision 4), else bf16
+// Tensor-core W images (blocks of kind 2): wmode 0 = 64x64 complex64-pass image as bf16 hi / lo,
+// 1 = the same as fp16 hi / lo (precision 4), 2 = the five fp16 digit planes of a 32x32 block for
+// the complex128 pass; image i of row r at wimg + r * wstride + i * wpass (uint16 elements).
 cudaError_t launch_build_blocks(const DevBlock* blocks, int nblocks, const DevMember* mem, const double2* gtab,
                                 int64_t gstride, int rows, double2* btab, int64_t bstride, uint16_t* wimg,
-                                int64_t wstride, int whalf, cudaStream_t st);
+                                int64_t wstride, int wmode, int64_t wpass, cudaStream_t st);
 
 // Tensor-core pass over tiles of 128 rows x 64 columns (13 qubits).
 struct TcPassDesc {
@@ -83,11 +85,29 @@ struct TcPassDesc {
   int32_t col[6];          // block qubits, ascending (bit j of the column index = local bit j)
   int32_t tile[13];        // row and column qubits together, ascending
 };
-// pipeline 0: bulk-copy staged kernel (k_tc_bulk); 1: register-staged kernel (k_tc_block)
+// pipeline 0: bulk-copy staged kernel (k_tc_bulk); 1: register-staged kernel (k_tc_block).
+// spin: polls per pipeline wait of the bulk-copy kernel before it gives up and
+// sets *err (0 = the default bound).
 cudaError_t launch_tc_pass(void* psi, int n, const TcPassDesc& p, const void* wimg, int prec, int pipeline,
-                           int* err, cudaStream_t st);
+                           int* err, cudaStream_t st, uint32_t spin = 0);
 size_t tc_smem_bytes();
 size_t tc_bulk_smem_bytes();
+
+// Complex128 tensor-core pass over tiles of 128 rows x 32 columns (12 qubits):
+// a dense 5-qubit block as exact fp16 digit products (kernels_tc128.cu).
+struct Tc5PassDesc {
+  int32_t row[7];          // global qubits of the row bits, ascending
+  int32_t col[5];          // block qubits, ascending (bit j of the column index = local bit j)
+  int32_t tile[12];        // row and column qubits together, ascending
+};
+// uint16 elements of one pass's W digit planes: g_0..g_4 and 2^-9 g_1..2^-9 g_5, 4096 each
+constexpr int64_t kTc128WElems = 10 * 4096;
+cudaError_t prepare_tc128_pass();
+size_t tc128_smem_bytes();
+// psis: device array of nstates state pointers (psi unused), else psi alone; wstride (uint16
+// elements) between the W planes of consecutive states, 0 = one set for all; spin as launch_tc_pass
+cudaError_t launch_tc128_pass(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
+                              const Tc5PassDesc& p, const void* wimg, int* err, cudaStream_t st, uint32_t spin = 0);
 
 // Diagonal phase pass: amplitude x times prod_j exp(i alpha_j s_j(x)),
 // s_j(x) = (-1)^popcount(mask_j & x), alpha_j = alpha0 + coef * theta[pidx]
@@ -217,7 +237,7 @@ cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, 
 // wstride (uint16 elements) between the W images of consecutive states; 0 = one image for all
 cudaError_t launch_tc_pass_batched(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
                                    const TcPassDesc& p, const void* wimg, int prec, int pipeline, int* err,
-                                   cudaStream_t st);
+                                   cudaStream_t st, uint32_t spin = 0);
 // Batched <P> for every group in one launch per wave of L2-resident states:
 // out[b * Z + zi] = per-string sum of state b (string zl[zi], groups (gx, gz, gc));
 // partials hold nstates * Z * expval_wave_ctas(expval_wave_states(...)) doubles.

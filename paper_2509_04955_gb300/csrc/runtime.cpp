@@ -58,7 +58,7 @@ void ensure_block_rows(qs_plan_s& p, int rows) {
       CK(cudaMemcpy(p.d_btab.p, p.h_btab.data(), sizeof(double2) * p.btab_elems, cudaMemcpyHostToDevice));
     p.btab_rows = want;
   }
-  if (!p.tcdesc.empty() && want > p.wimg_rows) {
+  if (p.has_tc() && want > p.wimg_rows) {
     p.d_wimg.release();
     p.d_wimg.ensure(sizeof(uint16_t) * p.h_wimg.size() * want);
     CK(cudaMemcpy(p.d_wimg.p, p.h_wimg.data(), sizeof(uint16_t) * p.h_wimg.size(), cudaMemcpyHostToDevice));
@@ -68,12 +68,13 @@ void ensure_block_rows(qs_plan_s& p, int rows) {
 
 void build_device_blocks(qs_plan_s& p, int rows, cudaStream_t st) {
   if (p.h_dblocks.empty()) return;
-  if (p.gtab_rows < rows || p.btab_rows < rows || (!p.tcdesc.empty() && p.wimg_rows < rows))
+  if (p.gtab_rows < rows || p.btab_rows < rows || (p.has_tc() && p.wimg_rows < rows))
     throw Error(QS_ERR_CUDA, "internal: block tables have fewer rows than the batch");
   const size_t G = std::max<size_t>(1, p.gates.size());
   CK(launch_build_blocks(p.d_dblocks.as<DevBlock>(), (int)p.h_dblocks.size(), p.d_dmem.as<DevMember>(),
                          p.d_gtab.as<double2>(), (int64_t)(16 * G), rows, p.d_btab.as<double2>(), p.btab_elems,
-                         p.d_wimg.as<uint16_t>(), (int64_t)p.h_wimg.size(), p.tc_prec == 4 ? 1 : 0, st));
+                         p.d_wimg.as<uint16_t>(), (int64_t)p.h_wimg.size(),
+                         p.dt == QS_C128 ? 2 : (p.tc_prec == 4 ? 1 : 0), p.wimg_pass, st));
 }
 
 void upload(qs_plan_s& p) {
@@ -112,6 +113,7 @@ void upload(qs_plan_s& p) {
   // kernel attributes and occupancy, here and never during a stream capture
   for (const PassDesc& pd : p.pdesc) CK(prepare_tile_pass(pd, p.dt));
   if (!p.tcdesc.empty()) CK(prepare_tc_pass());
+  if (!p.tc5desc.empty()) CK(prepare_tc128_pass());
   if (!p.h_dblocks.empty()) CK(prepare_build_blocks());
   p.uploaded = true;
 }
@@ -171,8 +173,11 @@ void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed
                            p.theta_stride, st));
     } else {
       const int t = p.steps[i].idx;
-      CK(launch_tc_pass(psi, p.n, p.tcdesc[t], p.d_wimg.as<uint16_t>() + (size_t)t * 32768, p.tc_prec,
-                        p.tc_pipe, p.d_err.as<int>(), st));
+      const uint16_t* w = p.d_wimg.as<uint16_t>() + (size_t)t * p.wimg_pass;
+      if (p.dt == QS_C128)
+        CK(launch_tc128_pass(psi, nullptr, 1, 0, p.n, p.tc5desc[t], w, p.d_err.as<int>(), st, p.tc_spin));
+      else
+        CK(launch_tc_pass(psi, p.n, p.tcdesc[t], w, p.tc_prec, p.tc_pipe, p.d_err.as<int>(), st, p.tc_spin));
     }
     if (timed) CK(cudaEventRecord(p.next_event(), st));
   }
@@ -197,7 +202,7 @@ int batched_wave(const qs_plan_s& p, int B) {
 void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_t st,
                            const std::function<void(int, int)>& after_wave) {
   const size_t G = std::max<size_t>(1, p.gates.size());
-  if (p.gtab_rows < B || (!p.h_dblocks.empty() && (p.btab_rows < B || (!p.tcdesc.empty() && p.wimg_rows < B))))
+  if (p.gtab_rows < B || (!p.h_dblocks.empty() && (p.btab_rows < B || (p.has_tc() && p.wimg_rows < B))))
     throw Error(QS_ERR_CUDA, "internal: tables have fewer rows than the batch");
   const int wave = batched_wave(p, B);
   for (int w0 = 0; w0 < B; w0 += wave) {
@@ -214,9 +219,13 @@ void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_
                                     p.d_btab.as<double2>(), st));
       } else {
         const int64_t wstride = p.tc_param[stp.idx] ? (int64_t)p.h_wimg.size() : 0;
-        CK(launch_tc_pass_batched(nullptr, ps, nb, wstride, p.n, p.tcdesc[stp.idx],
-                                  p.d_wimg.as<uint16_t>() + (size_t)stp.idx * 32768 + (size_t)w0 * wstride, p.tc_prec,
-                                  p.tc_pipe, p.d_err.as<int>(), st));
+        const uint16_t* w = p.d_wimg.as<uint16_t>() + (size_t)stp.idx * p.wimg_pass + (size_t)w0 * wstride;
+        if (p.dt == QS_C128)
+          CK(launch_tc128_pass(nullptr, ps, nb, wstride, p.n, p.tc5desc[stp.idx], w, p.d_err.as<int>(), st,
+                               p.tc_spin));
+        else
+          CK(launch_tc_pass_batched(nullptr, ps, nb, wstride, p.n, p.tcdesc[stp.idx], w, p.tc_prec, p.tc_pipe,
+                                    p.d_err.as<int>(), st, p.tc_spin));
       }
     }
     if (after_wave) after_wave(w0, nb);
@@ -244,11 +253,20 @@ void execute(qs_plan_s& p, qs_state_s& s, const double* theta, size_t ntheta) {
   build_device_blocks(p, 1, s.st);
   issue_circuit(p, s.d, 0, s.st, p.timing);
   plan_done(p, s.st);
-  if (!p.tcdesc.empty()) {
-    int err = 0;
-    CK(cudaMemcpyAsync(&err, p.d_err.p, sizeof(int), cudaMemcpyDeviceToHost, s.st));
-    CK(cudaStreamSynchronize(s.st));
-    if (err) throw Error(QS_ERR_TIMEOUT, "tensor-core pass: an MMA completion wait timed out");
+  check_tc_error(p, s.st);
+}
+
+// Reads the tensor-core passes' error flag after the work queued on `st`,
+// clears it for the next execution and reports a timeout.
+void check_tc_error(qs_plan_s& p, cudaStream_t st) {
+  if (!p.has_tc()) return;
+  int err = 0;
+  CK(cudaMemcpyAsync(&err, p.d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (err) {
+    CK(cudaMemsetAsync(p.d_err.p, 0, sizeof(int), st));
+    CK(cudaStreamSynchronize(st));
+    throw Error(QS_ERR_TIMEOUT, "tensor-core pass: a pipeline wait ran out of polls");
   }
 }
 
@@ -331,6 +349,41 @@ void build_w_image(const double2* U, uint16_t* img, bool half) {
 }
 
 float w_to_float(uint16_t v, bool half) { return half ? f16_to_float(v) : bf16_to_float(v); }
+
+// Digit planes of a 32x32 complex block U for the complex128 tensor-core pass:
+// entry (nn, k) of the N x K = 64 x 64 operand is W[k][nn] of the real
+// embedding, w = 2^-8 sum_{j<6} g_j 2^(-9 j) with balanced integer digits
+// (|g_j| <= 256; X = rint(w 2^53) split from the bottom), plane j (j < 5)
+// stored as fp16 integers in the K-major 128-byte-swizzled layout (8 KiB per
+// plane), then planes 5..9 = 2^-9 g_1 .. 2^-9 g_5 (exact in fp16) for the
+// level-5 products the pass folds into its level-4 accumulator. The device
+// builder (kernels_build.cu) follows the same steps.
+void build_w_digits(const double2* U, uint16_t* img) {
+  for (uint32_t nn = 0; nn < 64; ++nn)
+    for (uint32_t k = 0; k < 64; ++k) {
+      const uint32_t co = nn >> 1, b = nn & 1, ci = k >> 1, a = k & 1;
+      const double ur = U[co * 32 + ci].x, ui = U[co * 32 + ci].y;
+      const double w = (a == 0) ? (b == 0 ? ur : ui) : (b == 0 ? -ui : ur);
+      long long X = std::llrint(std::ldexp(w, 53));
+      int g[6];
+      for (int j = 5; j >= 1; --j) {
+        g[j] = (int)(((X + 256) & 511) - 256);
+        X = (X - g[j]) / 512;
+      }
+      g[0] = (int)X;
+      const size_t off = (nn * 128 + (((k >> 3) ^ (nn & 7)) << 4) + (k & 7) * 2) / 2;
+      for (int j = 0; j < 5; ++j) img[(size_t)j * 4096 + off] = f16_rne((float)g[j]);
+      for (int j = 1; j < 6; ++j) img[(size_t)(4 + j) * 4096 + off] = f16_rne(std::ldexp((float)g[j], -9));
+    }
+}
+
+// The value an entry (nn, k) of a digit image stands for: 2^-8 sum_{j<6} g_j 2^(-9 j).
+double w_digit_value(const uint16_t* img, uint32_t nn, uint32_t k) {
+  const size_t off = (nn * 128 + (((k >> 3) ^ (nn & 7)) << 4) + (k & 7) * 2) / 2;
+  double v = (double)f16_to_float(img[(size_t)9 * 4096 + off]);   // 2^-9 g_5
+  for (int j = 4; j >= 0; --j) v = v / 512.0 + (double)f16_to_float(img[(size_t)j * 4096 + off]);
+  return std::ldexp(v, -8);
+}
 
 // Records a block whose matrix is rebuilt on the device from theta (kind: 0
 // dense, 1 diagonal, 2 tensor-core W image; out = table offset or image index).
@@ -496,7 +549,49 @@ void emit_phase_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
   in.flops_per_amp += 18.0;   // three complex products per amplitude
 }
 
+// A complex128 tensor-core pass: one dense 5-qubit block over tiles of the
+// block's qubits and the 7 lowest other qubits; W as five digit planes.
+static void emit_tc128_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
+  const Block& blk = P.blocks[r.block];
+  Tc5PassDesc t;
+  std::memset(&t, 0, sizeof(t));
+  require(blk.qubits.size() == 5, "internal: complex128 tensor-core block needs 5 qubits");
+  for (int j = 0; j < 5; ++j) t.col[j] = blk.qubits[j];
+  int nr = 0;
+  for (int q = 0; q < P.n && nr < 7; ++q)
+    if (std::find(blk.qubits.begin(), blk.qubits.end(), q) == blk.qubits.end()) t.row[nr++] = q;
+  require(nr == 7, "internal: tensor-core tile needs 7 row qubits");
+  std::vector<int> tile(t.row, t.row + 7);
+  tile.insert(tile.end(), t.col, t.col + 5);
+  std::sort(tile.begin(), tile.end());
+  for (int j = 0; j < 12; ++j) t.tile[j] = tile[j];
+  const size_t w0 = P.h_wimg.size();
+  P.h_wimg.resize(w0 + kTc128WElems);
+  if (blk.parametric)
+    register_device_block(P, blk, 2, (int64_t)P.tc5desc.size());   // digit planes rebuilt per row on the device
+  else
+    build_w_digits(P.h_btab.data() + P.block_off[r.block], P.h_wimg.data() + w0);
+  P.tc_param.push_back(blk.parametric ? 1 : 0);
+  DevOp d;
+  std::memset(&d, 0, sizeof(d));
+  d.type = OP_TC;
+  d.k = 5;
+  const int b = (int)P.dops.size();
+  P.dops.push_back(d);
+  P.exec_ops.push_back(r);
+  P.steps.push_back({1, (int)P.tc5desc.size()});
+  P.tc5desc.push_back(t);
+  P.pass_tiles.push_back(tile);
+  P.pass_ops.push_back({b, b + 1});
+  in.flops_per_amp += 8.0 * 32;
+  in.max_block_qubits = std::max(in.max_block_qubits, 5);
+}
+
 void emit_tc_pass(qs_plan_s& P, const OpRec& r, qs_plan_info& in) {
+  if (P.dt == QS_C128) {
+    emit_tc128_pass(P, r, in);
+    return;
+  }
   const Block& blk = P.blocks[r.block];
   TcPassDesc t;
   std::memset(&t, 0, sizeof(t));
@@ -648,8 +743,14 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   require(o.tile_qubits <= 14 && o.tile_qubits >= 0, "tile_qubits out of range (1..14)");
   require(o.low_qubits >= 0 && o.fuse_k >= 0, "negative option");
   bool tensor = p->mode == QS_MODE_TENSOR;
-  if (tensor) {
-    if (dt != QS_C64) throw Error(QS_ERR_UNSUPPORTED, "tensor-core mode needs complex64 states");
+  if (tensor && dt == QS_C128) {
+    // complex128: 5-qubit blocks as exact fp16 digit products (one arithmetic only)
+    require(o.tc_precision == 0, "complex128 tensor-core passes take tc_precision 0 (exact digit products)");
+    require(o.reserved[1] == 0, "complex128 tensor-core passes have one pipeline (reserved[1] = 0)");
+    p->tc_prec = 0;
+    p->wimg_pass = kTc128WElems;
+    if (n < 12) tensor = false;   // a tile needs 12 qubits; smaller states use CUDA-core blocks
+  } else if (tensor) {
     require(o.tc_precision == 0 || o.tc_precision == 1 || o.tc_precision == 3 || o.tc_precision == 4,
             "tc_precision must be 1, 3 or 4");
     p->tc_prec = o.tc_precision == 0 ? 4 : o.tc_precision;
@@ -657,6 +758,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
     p->tc_pipe = o.reserved[1];
     if (n < 13) tensor = false;   // a tensor-core tile needs 13 qubits; smaller states use CUDA-core blocks
   }
+  const int tc_width = dt == QS_C128 ? 5 : 6;
   const int user_k = o.fuse_k;
   if (tensor) o.fuse_k = 0;
   default_opts(o, dt, n);
@@ -670,7 +772,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   require(o.low_qubits + std::max(widest, o.fuse_k) <= 14 || o.tile_qubits == n,
           "low_qubits + widest gate must fit a 14-qubit tile");
   PlanOptions po;
-  po.k = o.paper_mode ? 2 : (tensor ? (user_k == 5 ? 5 : 6) : o.fuse_k);
+  po.k = o.paper_mode ? 2 : (tensor ? (dt == QS_C128 ? 5 : (user_k == 5 ? 5 : 6)) : o.fuse_k);
   po.paper = o.paper_mode != 0;
   po.amp_bytes = (int)amp_bytes(dt);
   // GB300: FP32 FMA 128 lanes/clk/SM, FP64 about 1/59 of that (measured),
@@ -709,14 +811,16 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
     contract_range(pos, (int)p->gates.size());
   }
   if (tensor) {
-    // A block worth a tensor-core pass (one HBM sweep) carries many gates;
-    // it is padded to 6 qubits with the highest qubits it does not touch.
-    const int tc_min_gates = o.reserved[0] > 0 ? o.reserved[0] : 10;
+    // A block worth a tensor-core pass (one HBM sweep) carries many gates in
+    // complex64, where CUDA-core tile passes are cheap; in complex128 (FP64 or
+    // FP32-pair tile passes) every block is. It is padded to the pass's width
+    // (6 qubits complex64, 5 complex128) with the highest qubits it does not touch.
+    const int tc_min_gates = o.reserved[0] > 0 ? o.reserved[0] : (dt == QS_C128 ? 1 : 10);
     for (Block& blk : p->blocks) {
       if ((int)blk.gates.size() >= tc_min_gates) {
         blk.rep = OP_TC;
         blk.diag = false;
-        for (int q = n - 1; q >= 0 && blk.qubits.size() < 6; --q)
+        for (int q = n - 1; q >= 0 && (int)blk.qubits.size() < tc_width; --q)
           if (std::find(blk.qubits.begin(), blk.qubits.end(), q) == blk.qubits.end()) blk.qubits.push_back(q);
         std::sort(blk.qubits.begin(), blk.qubits.end());
       } else if (blk.qubits.size() > 5 || (blk.rep == OP_DENSE && (int)blk.qubits.size() > o.fuse_k)) {

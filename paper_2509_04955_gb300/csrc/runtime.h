@@ -176,8 +176,13 @@ struct qs_plan_s {
   int64_t theta_stride = 0;        // entries per theta row of the last resolve
   bool theta_needed = false;       // some phase term depends on theta
   std::vector<Step> steps;
-  std::vector<TcPassDesc> tcdesc;
-  std::vector<uint16_t> h_wimg;    // per TC pass: bf16 hi image then lo image (64 KiB)
+  std::vector<TcPassDesc> tcdesc;   // complex64 tensor-core passes
+  std::vector<Tc5PassDesc> tc5desc; // complex128 tensor-core passes
+  // per TC pass: 16-bit hi image then lo image (64 KiB, complex64) or five digit planes (40 KiB, complex128)
+  std::vector<uint16_t> h_wimg;
+  int64_t wimg_pass = 32768;       // uint16 elements per pass in h_wimg / d_wimg
+  uint32_t tc_spin = 0;            // polls per tensor-core pipeline wait (0 = default bound)
+  bool has_tc() const { return !tcdesc.empty() || !tc5desc.empty(); }
   int tc_prec = 3;
   int tc_pipe = 0;                 // single-state tensor-core pass: 0 bulk-copy staged, 1 register-staged
   bool df = false;                 // complex128 tile passes computed in FP32 pairs
@@ -260,6 +265,7 @@ void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_
                            const std::function<void(int, int)>& after_wave = nullptr);
 void resolve_theta(qs_plan_s& p, const double* theta, size_t ntheta, int rows, cudaStream_t st);
 void execute(qs_plan_s& p, qs_state_s& s, const double* theta, size_t ntheta);
+void check_tc_error(qs_plan_s& p, cudaStream_t st);
 // ---- tensor-core W images (16-bit hi / lo split, 128-byte swizzle)
 uint16_t bf16_rne(float f);
 float bf16_to_float(uint16_t h);
@@ -267,6 +273,8 @@ uint16_t f16_rne(float f);
 float f16_to_float(uint16_t h);
 size_t sw128_offset_host(uint32_t row, uint32_t k);
 void build_w_image(const double2* U, uint16_t* img, bool half);
+void build_w_digits(const double2* U, uint16_t* img);
+double w_digit_value(const uint16_t* img, uint32_t nn, uint32_t k);
 float w_to_float(uint16_t v, bool half);
 // ---- planning: passes of every kind, options, plan construction
 void register_device_block(qs_plan_s& P, const Block& blk, int kind, int64_t out);

@@ -161,12 +161,7 @@ qs_status qs_stream_apply(void* host_psi, int n, qs_dtype dt, const qs_gate* gat
       }
       CK(cudaStreamSynchronize(sd));
       CK(cudaStreamSynchronize(sc));
-      for (auto& pp : plans)
-        if (!pp->tcdesc.empty()) {
-          int err = 0;
-          CK(cudaMemcpy(&err, pp->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-          if (err) throw Error(QS_ERR_TIMEOUT, "tensor-core pass: an MMA completion wait timed out");
-        }
+      for (auto& pp : plans) check_tc_error(*pp, sd);
       if (info) {
         std::memset(info, 0, sizeof(*info));
         info->passes = (int64_t)passes.size();
@@ -251,11 +246,7 @@ qs_status qs_plan_execute_host(qs_plan_t p, qs_state_t* work, int nwork, const v
       CK(cudaStreamSynchronize(si));
       if (norms && count > 0) CK(cudaMemcpy(norms, dnorm.p, sizeof(double) * count, cudaMemcpyDeviceToHost));
       for (int b = 0; b < nwork; ++b) CK(cudaStreamWaitEvent(work[b]->st, stored[b], 0));
-      if (!p->tcdesc.empty()) {
-        int err = 0;
-        CK(cudaMemcpy(&err, p->d_err.p, sizeof(int), cudaMemcpyDeviceToHost));
-        if (err) throw Error(QS_ERR_TIMEOUT, "tensor-core pass: an MMA completion wait timed out");
-      }
+      check_tc_error(*p, sc);
     } catch (...) {
       if (si) cudaStreamSynchronize(si);
       if (sc) cudaStreamSynchronize(sc);

@@ -355,9 +355,44 @@ def test_tensor_mode_plan_matches_oracle_on_a_state():
                 assert e - b == 1 and len(ps["tile"]) == 13
     finally:
         Q.qs_plan_free(plan)
+
+
+@pytest.mark.parametrize("tc_min", [0, 2, 5])
+def test_complex128_tensor_plan_matches_oracle_on_a_state(tc_min):
+    """Complex128 tensor-core plans: 5-qubit contraction, blocks of >= tc_min
+    gates (0: every block) padded to 5 qubits on 12-qubit tiles, the rest as
+    CUDA-core ops; applied with numpy they reproduce the oracle's state. The
+    complex64 precision options are refused."""
+    n = 13
+    gates = W.random_layered(n, 6, seed=4)
+    plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=tc_min))
+    try:
+        ops = Q.qs_plan_ops(plan)
+        tc = [op for op in ops if op["type"] == 3]
+        assert tc
+        if tc_min == 0:
+            assert all(op["type"] in (3, 4) for op in ops)
+        psi = W.random_state(n, 2)
+        cur = psi.copy()
+        for op in ops:
+            if op["type"] == 0:
+                cur = O.apply_circuit(cur, n, [gates[op["gate"]]])
+            elif op["type"] == 2:
+                cur = apply_block(cur, n, op["qubits"], np.diag(op["matrix"]))
+            else:
+                if op["type"] == 3:
+                    assert len(op["qubits"]) == 5
+                cur = apply_block(cur, n, op["qubits"], op["matrix"])
+        assert np.abs(cur - O.apply_circuit(psi, n, gates)).max() < 1e-12
+        for ps in Q.qs_plan_passes(plan):
+            b, e = ps["ops"]
+            if any(op["type"] == 3 for op in ops[b:e]):
+                assert e - b == 1 and len(ps["tile"]) == 12
+    finally:
+        Q.qs_plan_free(plan)
     with pytest.raises(Q.QsError) as e:
-        Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR))
-    assert e.value.status == Q.QS_ERR_UNSUPPORTED
+        Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_precision=4))
+    assert e.value.status == Q.QS_ERR_ARG
 
 
 def test_planner_fuzz_ops_reproduce_the_circuit():

@@ -1,0 +1,506 @@
+"""Host-side models of the complex128 tensor-core pass (k_tc128, no GPU).
+
+They restate in Python, with numpy float32 arithmetic (IEEE round to nearest,
+the rounding of the kernel's __fadd_rn / __fmul_rn / __fmaf_rn steps, whose
+FMAs here only add a power-of-two multiple), the kernel's arithmetic and check
+what it relies on:
+
+* digits: every FP64 value of a row becomes six integer digits with
+  |d| <= 260 whose sum 2^(E-8) sum_i d_i 2^(-9 i) is within 2^(E-46) of it;
+  the host's W digits (six, balanced, |g| <= 256) are within 2^-54 of w;
+* exactness: the level sums of a 64-term row (levels 0..2, and 3 short of an
+  adversarial alignment) stay below 2^24, so FP32 accumulation is exact;
+* the combination of the five levels back to FP64 (FP32 pairs joined by
+  integer arithmetic) equals their exact sum to 2^-46 relative, including
+  results just below a power of two;
+* a whole row: U psi through digits, exact level sums (level 5 folded into
+  level 4) and the combination is within 2^-46 of the row's scale 2^E
+  (|a| < 2^E <= 2 max |a|) of the FP64 product, for
+  Haar-random blocks and rows of every shape (random, one non-zero entry,
+  mixed magnitudes, FP64 zeros and subnormals, exact powers of two);
+* indexing: runs of >= 2^7 amplitudes land every element (row, column) of a
+  tile at its tile-local index, the tiles partition the state, and stores
+  go to roff(row) | coff(column) of the tile;
+* barriers: the single-buffered A and accumulator protocol (with the row
+  exponent exchange and the exponent table) has no deadlock or hazard under
+  random delays, for 1 to 54 tiles per CTA, with and without W reloads.
+"""
+import random
+from fractions import Fraction
+
+import numpy as np
+import pytest
+
+F32 = np.float32
+MAGIC = F32(12582912.0)
+
+
+def f32(bits):
+    return np.array(bits, dtype=np.uint32).view(np.float32)
+
+
+def rint32(x):
+    return (x + MAGIC) - MAGIC
+
+
+# ---------------------------------------------------------------- kernel arithmetic, restated
+
+def digits(a, emax_b):
+    """t2_digits over an array of FP64 values of one row (emax_b per value)."""
+    u = np.asarray(a, dtype=np.float64).view(np.uint64)
+    whi = (u >> np.uint64(32)).astype(np.int64)
+    wlo = (u & np.uint64(0xFFFFFFFF)).astype(np.int64)
+    ex = (whi >> 20) & 0x7FF
+    fe = ex + 134 - np.asarray(emax_b, dtype=np.int64)
+    sign = whi & 0x80000000
+    ok = (ex != 0) & (fe >= 87)
+    fe_ok = np.where(ok, fe, 127)
+    hi = f32((sign | (fe_ok << 23) | ((whi & 0xFFFFF) << 3) | (wlo >> 29)).astype(np.uint32))
+    eb = (fe_ok - 5) << 23
+    lo18 = f32((sign | eb | ((wlo & 0x1FFFFFFF) >> 6)).astype(np.uint32)) - f32((sign | eb).astype(np.uint32))
+    hi = np.where(ok, hi, F32(0))
+    lo18 = np.where(ok, lo18, F32(0))
+    d0 = rint32(hi)
+    t = hi - d0
+    u1 = t * F32(512)
+    d1 = rint32(u1)
+    t = u1 - d1
+    v = t * F32(512) + lo18               # fmaf(t, 512, lo18): t * 512 is exact
+    d2 = rint32(v)
+    r = (t * F32(512) - d2) + lo18        # fmaf(t, 512, -d2) is exact
+    u3 = r * F32(512)
+    d3 = rint32(u3)
+    t = u3 - d3
+    u4 = t * F32(512)
+    d4 = rint32(u4)
+    t = u4 - d4
+    d5 = rint32(t * F32(512))             # the kernel stores 2^-9 d5 (exact in fp16)
+    return np.stack([d0, d1, d2, d3, d4, d5]).astype(np.float64)
+
+
+def w_digits(w):
+    """build_w_digits for one value: balanced digits of X = rint(w 2^53)."""
+    X = int(np.rint(np.ldexp(np.float64(w), 53)))
+    g = [0] * 6
+    for j in range(5, 0, -1):
+        g[j] = ((X + 256) & 511) - 256
+        X = (X - g[j]) // 512
+    g[0] = X
+    return g
+
+
+def two_sum(a, b):
+    s = a + b
+    bb = s - a
+    return s, (a - (s - bb)) + (b - bb)
+
+
+def combine(c, emax_b):
+    """t2_combine: five level sums (float32) -> FP64 value 2^(emax_b - 1038) sum_l c_l 2^(-9 l)."""
+    c0, c1, c2, c3, c4 = (F32(x) for x in c)
+    s, e = two_sum(c0, c1 * F32(2.0 ** -9))
+    s, e2 = two_sum(s, c2 * F32(2.0 ** -18))
+    e = e + e2
+    s, e2 = two_sum(s, c3 * F32(2.0 ** -27))
+    e = e + e2
+    e = c4 * F32(2.0 ** -36) + e
+    s2 = s + e
+    e = e - (s2 - s)
+    s = s2
+    us = int(np.array(s, dtype=np.float32).view(np.uint32))
+    fs = (us >> 23) & 0xFF
+    de = fs + emax_b - 142
+    if fs == 0 or de <= 0:
+        return 0.0
+    mag = (de << 52) | ((us & 0x7FFFFF) << 29)
+    if 46 <= fs <= 254:
+        sc = f32(np.uint32((300 - fs) << 23))
+        k = int(np.array((e * sc) + MAGIC, dtype=np.float32).view(np.int32)) - 0x4B400000
+        adj = (-k if us >> 31 else k) << 6
+        if (us & 0x7FFFFF) == 0 and adj < 0:
+            adj *= 2
+        mag += adj
+    bits = ((us >> 31) << 63) | mag
+    return float(np.array(bits, dtype=np.uint64).view(np.float64))
+
+
+def row_emax(vals):
+    u = np.asarray(vals, dtype=np.float64).view(np.uint64)
+    return int(((u >> np.uint64(52)) & np.uint64(0x7FF)).max())
+
+
+def apply_row(U, a):
+    """One output row of the pass: U (32x32 complex) applied to a (32 complex) the kernel's way."""
+    reals = np.empty(64)
+    reals[0::2], reals[1::2] = a.real, a.imag
+    em = row_emax(reals)
+    D = digits(reals, em)                            # 6 x 64
+    assert np.abs(D).max() <= 260
+    Wd = np.zeros((6, 64, 64), dtype=np.int64)       # [j][k][nn]
+    for co in range(32):
+        for ci in range(32):
+            u = U[co, ci]
+            for k, nn, w in ((2 * ci, 2 * co, u.real), (2 * ci, 2 * co + 1, u.imag),
+                             (2 * ci + 1, 2 * co, -u.imag), (2 * ci + 1, 2 * co + 1, u.real)):
+                Wd[:, k, nn] = w_digits(w)
+    assert np.abs(Wd).max() <= 256
+    Di = D.astype(np.int64)
+    out = np.empty(64)
+    for nn in range(64):
+        lev = []
+        for l in range(5):
+            tot = 0
+            for i in range(l + 1):
+                # one K = 16 MMA per k-step: the accumulator after each step
+                for ks in range(4):
+                    tot += int((Di[i, 16 * ks:16 * ks + 16] * Wd[l - i, 16 * ks:16 * ks + 16, nn]).sum())
+                    if l <= 2:
+                        assert abs(tot) < 2 ** 24, "an exact level left the FP32 integer range"
+            if l == 4:   # level 5 folded in: A_i (2^-9 W_(5-i)), i < 5, and (2^-9 A_5) W_0
+                tot = Fraction(tot) + sum(Fraction(int((Di[i] * Wd[5 - i, :, nn]).sum()), 512) for i in range(0, 6))
+            lev.append(F32(float(tot)))                # exact for levels <= 2 (checked), rounded above
+        out[nn] = combine(lev, em)
+    return out[0::2] + 1j * out[1::2], em
+
+
+def haar(d, rng):
+    z = (rng.standard_normal((d, d)) + 1j * rng.standard_normal((d, d))) / np.sqrt(2)
+    q, r = np.linalg.qr(z)
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+# ---------------------------------------------------------------- arithmetic checks
+
+def test_digits_reconstruct_every_value_of_a_row():
+    rng = np.random.default_rng(0)
+    vals = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-12, 1, 4000),
+                           [0.0, -0.0, 5e-324, -2.2e-308, 1.0, -1.0, 0.5, 2.0 ** -30, 1 - 2 ** -53, 0.999999999]])
+    for em_extra in (0, 1, 7, 30):
+        em = row_emax(vals) + em_extra
+        E = em - 1022
+        assert np.all(np.abs(vals) < 2.0 ** E)
+        D = digits(vals, np.full(vals.shape, em))
+        assert np.abs(D).max() <= 260
+        rec = np.zeros_like(vals)
+        for i in range(6):
+            rec += D[i] * 2.0 ** (-9 * i)
+        rec *= 2.0 ** (E - 8)
+        assert np.abs(rec - vals).max() <= 2.0 ** (E - 46)
+
+
+def test_w_digits_reconstruct_within_2_pow_minus_54():
+    rng = np.random.default_rng(1)
+    for w in list(rng.uniform(-1, 1, 3000)) + [1.0, -1.0, 0.0, 0.5, -0.5, 2 ** -44, 1 - 2 ** -50]:
+        g = w_digits(w)
+        assert max(abs(x) for x in g) <= 256
+        v = sum(Fraction(x) * Fraction(2) ** (-8 - 9 * j) for j, x in enumerate(g))
+        assert abs(v - Fraction(w)) <= Fraction(2) ** -54
+
+
+def test_combine_equals_the_exact_level_sum():
+    rng = np.random.default_rng(2)
+    for trial in range(3000):
+        c = [float(rng.integers(-2 ** 22, 2 ** 22)), float(rng.integers(-2 ** 23, 2 ** 23)),
+             float(rng.integers(-3 * 2 ** 22, 3 * 2 ** 22)), float(rng.integers(-2 ** 24, 2 ** 24)),
+             float(F32(rng.standard_normal() * 2.0 ** rng.integers(0, 24)))]
+        if trial % 5 == 0:
+            c[0] = 0.0
+        if trial % 7 == 0:   # just below or above a power of two
+            c = [float(2 ** 20), -1.0 * rng.integers(1, 512), float(rng.integers(-2 ** 10, 2 ** 10)), 0.0, 0.0]
+        em = int(rng.integers(900, 1100))
+        exact = sum(Fraction(x) * Fraction(2) ** (-9 * l) for l, x in enumerate(c)) * Fraction(2) ** (em - 1038)
+        got = combine(c, em)
+        # relative to the result, or absolute at 2^-34 of a level-0 unit (2^(E-50) for rows scaled 2^E)
+        assert abs(Fraction(got) - exact) <= abs(exact) * Fraction(2) ** -46 + Fraction(2) ** (em - 1038 - 34)
+
+
+@pytest.mark.parametrize("shape", ["random", "one", "mixed", "tiny", "powers", "zeros"])
+def test_a_whole_row_matches_the_fp64_product(shape):
+    rng = np.random.default_rng(["random", "one", "mixed", "tiny", "powers", "zeros"].index(shape) + 40)
+    for trial in range(3):
+        U = haar(32, rng)
+        a = (rng.standard_normal(32) + 1j * rng.standard_normal(32)) / 8
+        if shape == "one":
+            a = np.zeros(32, complex)
+            a[rng.integers(32)] = 1.0 if trial == 0 else np.exp(1j * rng.uniform(0, 6.3))
+        elif shape == "mixed":
+            a *= 10.0 ** rng.integers(-15, 1, 32)
+        elif shape == "tiny":
+            a *= 2.0 ** -900
+            a[3] = 5e-324
+        elif shape == "powers":
+            a = (2.0 ** -rng.integers(1, 12, 32)) * rng.choice([-1, 1], 32) + 1j * 2.0 ** -rng.integers(1, 12, 32)
+        elif shape == "zeros":
+            a[::2] = 0
+            a[5] = -0.0
+        got, em = apply_row(U, a)
+        want = U @ a
+        if np.abs(np.concatenate([a.real, a.imag])).max() == 0:
+            assert np.all(got == 0)
+            continue
+        scale = 2.0 ** (em - 1022)
+        assert np.abs(got - want).max() <= 2.0 ** -46 * scale + 1e-300, (shape, trial)
+
+
+def test_level_three_range_holds_for_random_rows():
+    """Level 3 sums 4 products; only an adversarial alignment of all digits could reach 2^24."""
+    rng = np.random.default_rng(5)
+    U = haar(32, rng)
+    for _ in range(3):
+        a = (rng.standard_normal(32) + 1j * rng.standard_normal(32))
+        reals = np.empty(64)
+        reals[0::2], reals[1::2] = a.real, a.imag
+        D = digits(reals, np.full(64, row_emax(reals))).astype(np.int64)
+        Wd = np.array([[w_digits(x) for x in col] for col in
+                       np.concatenate([U.real.T, U.imag.T]).reshape(64, 32)]).transpose(2, 0, 1)
+        for nn in range(32):
+            l3 = sum(int((D[i] * np.resize(Wd[3 - i, :, nn], 64)).sum()) for i in range(4))
+            assert abs(l3) < 2 ** 22
+
+
+# ---------------------------------------------------------------- indexing
+
+def _geometry(n, Q):
+    Q = sorted(Q)
+    R = [q for q in range(n) if q not in Q][:7]
+    T = sorted(Q + R)
+    pr = 0
+    while pr < 12 and T[pr] == pr:
+        pr += 1
+    lam = {q: i for i, q in enumerate(T)}
+    lamcol = [sum(((c >> b) & 1) << lam[Q[b]] for b in range(5)) for c in range(32)]
+    coff = [sum(((c >> b) & 1) << Q[b] for b in range(5)) for c in range(32)]
+    return Q, R, T, pr, lam, lamcol, coff
+
+
+def _tile_base(T, t):
+    x = t
+    for q in T:
+        x = ((x >> q) << (q + 1)) | (x & ((1 << q) - 1))
+    return x
+
+
+PLACEMENTS = [(0, 1, 2, 3, 4), (0, 1, 2, 9, 10), (1, 3, 7, 9, 11), (7, 8, 9, 10, 11), (2, 4, 5, 6, 8),
+              (12, 13, 14, 15, 16), (0, 5, 11, 13, 15), (3, 4, 5, 6, 7), (0, 2, 4, 6, 8)]
+
+
+@pytest.mark.parametrize("Q", PLACEMENTS)
+def test_tile_elements_land_and_store_at_their_amplitudes(Q):
+    n = 17
+    Q, R, T, pr, lam, lamcol, coff = _geometry(n, Q)
+    assert pr >= 7
+    runoff = [sum(((j >> b) & 1) << T[pr + b] for b in range(12 - pr)) for j in range(1 << (12 - pr))]
+    seen = set()
+    for t in range(1 << (n - 12)):
+        tb = _tile_base(T, t)
+        slot = {}
+        for j, r in enumerate(runoff):             # run j of 2^pr amplitudes at slot offset j 2^pr
+            for o in range(1 << pr):
+                slot[j * (1 << pr) + o] = tb + r + o
+        assert sorted(slot) == list(range(4096))
+        for row in range(128):
+            lrow = sum(((row >> b) & 1) << lam[R[b]] for b in range(7))
+            roff = sum(((row >> b) & 1) << R[b] for b in range(7))
+            for c in range(32):
+                g = slot[lrow | lamcol[c]]
+                assert g == (tb | roff | coff[c])      # the drainer's store address
+                seen.add(g)
+    assert len(seen) == 1 << n
+
+
+# ---------------------------------------------------------------- barriers
+
+class _Bar:
+    """mbarrier: `done` completed phases; try_wait.parity(P) passes iff (done & 1) != P."""
+
+    def __init__(self, count):
+        self.count, self.pending, self.done, self.tx = count, count, 0, 0
+
+    def arrive(self):
+        self.pending -= 1
+        self._check()
+
+    def expect_tx(self, b):
+        self.tx += b
+        self.arrive()
+
+    def complete_tx(self, b):
+        self.tx -= b
+        self._check()
+
+    def _check(self):
+        if self.pending == 0 and self.tx == 0:
+            self.done += 1
+            self.pending = self.count
+
+    def ok(self, parity):
+        return (self.done & 1) != parity
+
+
+def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True):
+    rng = random.Random(seed)
+    state = lambda i: (t_begin + i) // tiles_per_state
+    new_state = lambda i: i > 0 and state(i) != state(i - 1)
+    full, empty = [_Bar(1), _Bar(1)], [_Bar(8), _Bar(8)]
+    afull, mdone, dfree = _Bar(8), _Bar(1), _Bar(8)
+    efull = [_Bar(8), _Bar(8)]
+    xbar = [[_Bar(2) for _ in range(4)] for _ in range(2)]
+    wfull, wfree = _Bar(1), _Bar(1)
+    events, now, last_finish = [], [0.0], [0.0]
+    W = {"state": state(0), "writing": None}
+    A = {"tile": None}                   # tile whose digits the A planes hold
+    Dacc = {"tile": None, "read": True}  # tile whose levels the accumulators hold
+    slot_of = {0: None, 1: None}
+    xe = {}                              # (parity, quad, half) -> tile
+    etab = {0: None, 1: None}
+    inflight, errors = {}, []
+
+    def later(dt, fn):
+        events.append((now[0] + dt, fn))
+
+    def producer():
+        issued = 0
+        for i in range(my):
+            s = i & 1
+            if i >= 2:
+                yield lambda: empty[s].ok(((i >> 1) - 1) & 1)
+            full[s].expect_tx(1)
+
+            def land(s=s, i=i):
+                slot_of[s] = i
+                full[s].complete_tx(1)
+            later(rng.uniform(1, 5), land)
+            if new_state(i):
+                yield lambda: wfree.ok(issued & 1)
+                if any(st != state(i) for st in inflight.values()):
+                    errors.append("W overwritten under in-flight MMAs")
+                W["writing"] = state(i)
+                wfull.expect_tx(1)
+
+                def wland(st=state(i)):
+                    W["state"], W["writing"] = st, None
+                    wfull.complete_tx(1)
+                later(rng.uniform(1, 5), wland)
+                issued += 1
+
+    def mma():
+        seen = 0
+        for i in range(my):
+            if new_state(i):
+                yield lambda: wfull.ok(seen & 1)
+                seen += 1
+            yield lambda: afull.ok(i & 1)
+            if i >= 1:
+                yield lambda: dfree.ok((i - 1) & 1)
+            if W["state"] != state(i) or W["writing"] is not None:
+                errors.append("MMA reads the wrong W")
+            if A["tile"] != i:
+                errors.append("MMA reads digits of another tile")
+            if not Dacc["read"]:
+                errors.append("accumulators overwritten before they were read")
+            Dacc["tile"], Dacc["read"] = None, False
+            inflight[i] = state(i)
+
+            def finish(i=i, last=(i + 1 < my and new_state(i + 1))):
+                del inflight[i]
+                Dacc["tile"] = i
+                mdone.arrive()
+                if last:
+                    wfree.arrive()
+            last_finish[0] = max(last_finish[0], now[0] + rng.uniform(0.5, 3))
+            events.append((last_finish[0], finish))
+
+    def converter(quad, half):
+        for i in range(my):
+            s, par = i & 1, i & 1
+            yield lambda: full[s].ok((i >> 1) & 1)
+            if slot_of[s] != i:
+                errors.append("converter reads a slot holding another tile")
+            yield ("sleep", rng.uniform(0, 0.5))
+            xe[(par, quad, half)] = i
+            xbar[par][quad].arrive()
+            yield lambda: xbar[par][quad].ok((i >> 1) & 1)
+            if xe.get((par, quad, half ^ 1)) != i:
+                errors.append("row exponent exchanged with another tile")
+            if not etab_after_mdone:
+                if half == 0:
+                    etab[par] = i
+                efull[par].arrive()
+            if i >= 1:
+                yield lambda: mdone.ok((i - 1) & 1)
+            if (i - 1) in inflight:
+                errors.append("A planes overwritten under an MMA")
+            if etab_after_mdone:   # the drainers of tile i - 2 (same parity) read their entry
+                if half == 0:
+                    etab[par] = i
+                efull[par].arrive()
+            yield ("sleep", rng.uniform(0, 1))
+            A["tile"] = i
+            empty[s].arrive()
+            afull.arrive()
+
+    def drainer():
+        for i in range(my):
+            par = i & 1
+            yield lambda: mdone.ok(i & 1)
+            yield lambda: efull[par].ok((i >> 1) & 1)
+            if Dacc["tile"] != i:
+                errors.append("accumulators read before their MMAs finished")
+            if etab[par] != i:
+                errors.append("exponent table holds another tile")
+            yield ("sleep", rng.uniform(0, 1))
+            dfree.arrive()
+            if dfree.pending == dfree.count:   # the eighth drainer warp: accumulators free
+                Dacc["read"] = True
+            yield ("sleep", rng.uniform(0, 4))   # combination and stores after the release
+
+    roles = [producer(), mma()] + [converter(q, h) for h in range(2) for q in range(4)] + \
+            [drainer() for _ in range(8)]
+    waiting, sleeping, alive = {}, {}, set(range(len(roles)))
+    for _ in range(400000):
+        if not alive:
+            return errors
+        progressed = False
+        order = list(alive)
+        rng.shuffle(order)
+        for j in order:
+            if j in sleeping:
+                if sleeping[j] > now[0]:
+                    continue
+                del sleeping[j]
+            w = waiting.get(j)
+            if w is not None and not w():
+                continue
+            try:
+                nxt = next(roles[j])
+                if isinstance(nxt, tuple):
+                    sleeping[j], waiting[j] = now[0] + nxt[1], None
+                else:
+                    waiting[j] = nxt
+            except StopIteration:
+                alive.discard(j)
+            progressed = True
+        if not progressed:
+            if not events and not sleeping:
+                return errors + ["deadlock"]
+            now[0] = max(now[0], min([e[0] for e in events] + list(sleeping.values())))
+            for e in [e for e in events if e[0] <= now[0]]:
+                events.remove(e)
+                e[1]()
+    return errors + ["no progress"]
+
+
+def test_barrier_protocol_has_no_hazard_or_deadlock():
+    for seed in range(300):
+        r = random.Random(seed * 11 + 5)
+        tps = r.choice([1, 2, 3, 4, 8, 1 << 20])
+        my = r.choice([1, 2, 3, 4, 5, 7, 20, 54])
+        tb = r.randrange(0, 4 * min(tps, 8))
+        assert _simulate(my, tps, tb, seed) == [], (seed, tps, my, tb)
+
+
+def test_exponent_table_written_before_the_mdone_wait_is_caught_by_the_model():
+    """Writing tile i's row exponents before waiting for tile i - 1's MMAs lets
+    them overwrite tile i - 2's entry while its drainers are still storing."""
+    fails = sum(1 for seed in range(200) if _simulate(20, 1 << 20, 0, seed, etab_after_mdone=False))
+    assert fails > 20
