@@ -40,12 +40,15 @@
 //   warp 17  one thread issues the 21 products x 4 k-steps (M = 128, N = 64,
 //            K = 16, A from tensor memory, W planes from shared memory) and
 //            commits;
-//   warps 8-15 drainers, thread = (row, column half): tcgen05.ld of the five
-//            accumulators, combination, FP64 stores to HBM.
+//   warps 8-15 drainers, thread = (row, column half): per 8 columns, tcgen05.ld
+//            of the five accumulators, the levels folded into an FP32 pair
+//            written back over levels 0-1 (releasing levels 2-4), then the
+//            pairs read back, joined to FP64 and stored to HBM.
 // Tensor memory (512 columns): A digit planes at 32 p (p < 6), level-l
-// accumulator at 192 + 64 l. Both are single-buffered, so a tile's MMAs wait
-// for the previous tile's accumulators to be read, and its digits for the
-// previous tile's MMAs; the landing slots keep the loads streaming meanwhile.
+// accumulator at 192 + 64 l. Both are single-buffered: a tile's digits wait
+// for the previous tile's MMAs (the first 8 columns are computed before the
+// wait), its level 2-4 products for the previous tile's fold and its level
+// 0-1 products for the read-back; the landing slots keep the loads streaming.
 //
 // Every wait is bounded (`spin` polls; the waits for copies and MMAs already in
 // flight at an abort use kTcSpinLimit): a wait that runs out records *err = 1,
@@ -90,69 +93,88 @@ __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t* r) {
                : "r"(taddr));
 }
 
-// rint for |x| < 2^22 by the 1.5 * 2^23 shift (rounding to nearest even).
-__device__ __forceinline__ float t2_rint(float x) {
-  return __fsub_rn(__fadd_rn(x, 12582912.0f), 12582912.0f);
+constexpr float kT2Magic = 12582912.0f;   // 1.5 * 2^23: x + it rounds x to an integer (|x| < 2^22)
+
+// Loads 16 columns (this thread's lane); the caller waits with tcgen05.wait::ld.
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+        "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
 }
 
-// The six digits of one FP64 value a (bit pattern whi:wlo) of a row with
-// biased-exponent maximum emax_b: s = a 2^(8 - E), E = emax_b - 1022, so
-// |s| < 256, and s ~ sum_{i<6} d_i 2^(-9 i) (d[5] is returned as 2^-9 d5,
-// the form its tensor-memory plane holds); the error is below 2^-39 (the 6
-// FP64 mantissa bits the split drops) and 2^-46. The FP64 mantissa is cut by
-// bits into hi (sign, exponent, top 23 stored bits) and lo (the next 23 bits,
-// pre-scaled by 2^18); digits come from hi with exact FP32 steps until hi is
-// used up, lo joins at digit 2. Values with |s| < 2^-40 (and FP64 zeros /
+// The six digits of one FP64 value a (bit pattern whi:wlo) of a row whose
+// biased-exponent maximum is emax_b (fe_off = 134 - emax_b): s = a 2^(8 - E),
+// E = emax_b - 1022, so |s| < 256, and s ~ sum_{i<6} d_i 2^(-9 i) (d[5] is
+// returned as 2^-9 d5, the form its tensor-memory plane holds); the error is
+// below 2^-39 (the 6 FP64 mantissa bits the split drops) and 2^-46. The FP64
+// mantissa is cut by bits into hi (sign, exponent, top 23 stored bits) and lo
+// (the next 23 bits, pre-scaled by 2^18); digits come from hi with exact FP32
+// steps (x + 1.5 2^23 rounds to an integer, fma(t, 512, -d) is exact) until hi
+// is used up, lo joins at digit 2. Values with |s| < 2^-40 (and FP64 zeros /
 // subnormals) give zero digits.
-__device__ __forceinline__ void t2_digits(uint32_t whi, uint32_t wlo, int emax_b, float* d) {
-  const int ex = (int)((whi >> 20) & 0x7ffu);
-  const int fe = ex + 134 - emax_b;             // biased FP32 exponent of s (<= 134)
-  const uint32_t sign = whi & 0x80000000u;
-  float hi = 0.f, lo18 = 0.f;
-  if (ex != 0 && fe >= 87) {
-    hi = __uint_as_float(sign | ((uint32_t)fe << 23) | ((whi & 0xfffffu) << 3) | (wlo >> 29));
-    // lo = m 2^(e_s - 46) with m the remainder's top 23 bits: X - 2^x with
-    // X = (1 + m 2^-23) 2^x, x = e_s - 23; pre-scaled by 2^18: x = e_s - 5
-    const uint32_t eb = (uint32_t)(fe - 5) << 23;
-    lo18 = __fsub_rn(__uint_as_float(sign | eb | ((wlo & 0x1fffffffu) >> 6)), __uint_as_float(sign | eb));
-  }
-  d[0] = t2_rint(hi);
+__device__ __forceinline__ void t2_digits(uint32_t whi, uint32_t wlo, int fe_off, float* d) {
+  const uint32_t ex = (whi >> 20) & 0x7ffu;
+  const int fe = (int)ex + fe_off;              // biased FP32 exponent of s (<= 134)
+  const uint32_t se = (whi & 0x80000000u) | ((uint32_t)fe << 23);
+  float hi = __uint_as_float(se | (__funnelshift_l(wlo, whi, 3) & 0x7fffffu));
+  // lo = m 2^(e_s - 46) with m the remainder's top 23 bits: X - 2^x with
+  // X = (1 + m 2^-23) 2^x, x = e_s - 23; pre-scaled by 2^18: x = e_s - 5
+  const uint32_t eb = se - (5u << 23);
+  float lo18 = __fsub_rn(__uint_as_float(eb | ((wlo & 0x1fffffffu) >> 6)), __uint_as_float(eb));
+  const bool ok = ex != 0 && fe >= 87;
+  hi = ok ? hi : 0.f;
+  lo18 = ok ? lo18 : 0.f;
+  d[0] = __fsub_rn(__fadd_rn(hi, kT2Magic), kT2Magic);
   float t = __fsub_rn(hi, d[0]);                // exact, |t| <= 1/2
-  float u = __fmul_rn(t, 512.f);
-  d[1] = t2_rint(u);
-  t = __fsub_rn(u, d[1]);                       // exact
-  const float v = __fmaf_rn(t, 512.f, lo18);
-  d[2] = t2_rint(v);
-  const float r = __fadd_rn(__fmaf_rn(t, 512.f, -d[2]), lo18);
-  u = __fmul_rn(r, 512.f);
-  d[3] = t2_rint(u);
-  t = __fsub_rn(u, d[3]);
-  u = __fmul_rn(t, 512.f);
-  d[4] = t2_rint(u);
-  t = __fsub_rn(u, d[4]);
-  d[5] = __fmul_rn(t2_rint(__fmul_rn(t, 512.f)), 0.001953125f);
+  d[1] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
+  t = __fmaf_rn(t, 512.f, -d[1]);               // exact
+  d[2] = __fsub_rn(__fadd_rn(__fmaf_rn(t, 512.f, lo18), kT2Magic), kT2Magic);
+  t = __fadd_rn(__fmaf_rn(t, 512.f, -d[2]), lo18);
+  d[3] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
+  t = __fmaf_rn(t, 512.f, -d[3]);
+  d[4] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
+  t = __fmaf_rn(t, 512.f, -d[4]);
+  d[5] = __fmaf_rn(__fmaf_rn(t, 512.f, kT2Magic), 0.001953125f, -kT2Magic * 0.001953125f);
 }
 
-__device__ __forceinline__ void t2_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
+// The same six digits from an FP32 pair s + e (|e| <= ulp(s) / 2) of a row
+// with scale 2^E: hi = s 2^(8-E) and lo = e 2^(26-E) (sc8 = 2^(8-E),
+// sc26 = 2^(26-E), exact power-of-two scalings; tiny values flush to zero).
+__device__ __forceinline__ void t2_digits_pair(float s, float e, float sc8, float sc26, float* d) {
+  const float hi = __fmul_rn(s, sc8);
+  const float lo18 = __fmul_rn(e, sc26);
+  d[0] = __fsub_rn(__fadd_rn(hi, kT2Magic), kT2Magic);
+  float t = __fsub_rn(hi, d[0]);
+  d[1] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
+  t = __fmaf_rn(t, 512.f, -d[1]);
+  d[2] = __fsub_rn(__fadd_rn(__fmaf_rn(t, 512.f, lo18), kT2Magic), kT2Magic);
+  t = __fadd_rn(__fmaf_rn(t, 512.f, -d[2]), lo18);
+  d[3] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
+  t = __fmaf_rn(t, 512.f, -d[3]);
+  d[4] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
+  t = __fmaf_rn(t, 512.f, -d[4]);
+  d[5] = __fmaf_rn(__fmaf_rn(t, 512.f, kT2Magic), 0.001953125f, -kT2Magic * 0.001953125f);
+}
+
+// 2^k as a float (-126 <= k <= 127)
+__device__ __forceinline__ float t2_pow2(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
+
+// (s, e) += c 2^-k with TwoSum (s + e = a + b exactly, b = c 2^-k scaled inside the FMAs)
+__device__ __forceinline__ void t2_absorb(float& s, float& e, float c, float sc) {
+  const float a = s;
+  s = __fmaf_rn(c, sc, a);
   const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+  e = __fadd_rn(e, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fmaf_rn(c, sc, -bb)));
 }
 
-// FP64 bit pattern of 2^(emax_b - 1038) * (acc0 + acc1 2^-9 + acc2 2^-18 +
-// acc3 2^-27 + acc4 2^-36): FP32-pair sum, then s + e joined by integer
-// arithmetic on s's widened bit pattern (e added in units of 2^-46 of s).
-__device__ __forceinline__ double t2_combine(float c0, float c1, float c2, float c3, float c4, int emax_b) {
-  // levels 1-3 can be as large as s when the leading levels cancel, so each
-  // enters through TwoSum; level 4 (< 2^-12 units) is added to the error word
-  float s, e, e2;
-  t2_two_sum(c0, __fmul_rn(c1, 0.001953125f), s, e);
-  t2_two_sum(s, __fmul_rn(c2, 3.814697265625e-06f), s, e2);
-  e = __fadd_rn(e, e2);
-  t2_two_sum(s, __fmul_rn(c3, 7.450580596923828e-09f), s, e2);
-  e = __fadd_rn(e, e2);
-  e = __fmaf_rn(c4, 1.4551915228366852e-11f, e);
-  const float s2 = __fadd_rn(s, e);             // FastTwoSum: |s| >= |e|
+// FP64 value 2^(E - 16) (s + e) of an FP32 pair, normalised first with a
+// FastTwoSum, built by integer arithmetic on s's widened bit pattern with e
+// added in units of 2^-46 of s; below 2^-1022 it flushes to zero.
+__device__ __forceinline__ double t2_join(float s, float e, int E) {
+  const int emax_b = E + 1022;
+  const float s2 = __fadd_rn(s, e);             // FastTwoSum: |s| >= |e| after the level sums
   e = __fsub_rn(e, __fsub_rn(s2, s));
   s = s2;
   const uint32_t us = __float_as_uint(s);
@@ -163,7 +185,7 @@ __device__ __forceinline__ double t2_combine(float c0, float c1, float c2, float
   if (fs >= 46 && fs <= 254) {
     // e in units of 2^(x_s - 46), x_s = fs - 127: |k| <= 2^22
     const float sc = __uint_as_float((uint32_t)(300 - fs) << 23);
-    const int k = __float_as_int(__fadd_rn(__fmul_rn(e, sc), 12582912.0f)) - 0x4B400000;
+    const int k = __float_as_int(__fmaf_rn(e, sc, kT2Magic)) - 0x4B400000;
     long long adj = (long long)((us >> 31) ? -k : k) << 6;   // in units of s's FP64 ulp
     if ((us & 0x7fffffu) == 0 && adj < 0) adj *= 2;        // below a power of two the ulp halves
     mag += adj;
@@ -171,7 +193,10 @@ __device__ __forceinline__ double t2_combine(float c0, float c1, float c2, float
   return __longlong_as_double((long long)((unsigned long long)(us >> 31) << 63) | mag);
 }
 
-template <bool MULTI>
+// PIN / POUT: the pass reads / writes the state as FP32 pairs (the form kept
+// between consecutive tensor-core passes: per amplitude the floats
+// re.s, im.s, re.e, im.e with value s + e, |e| <= ulp(s) / 2), else as FP64.
+template <bool MULTI, bool PIN, bool POUT>
 __global__ void __launch_bounds__(kT2Threads, 1)
     k_tc128(double2* __restrict__ psi0, void* const* __restrict__ psis, Tc5PassDesc p,
             const uint4* __restrict__ wimg, int64_t wstride16, int lg_tiles1, uint64_t ntiles,
@@ -185,11 +210,11 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   uint64_t* coff = runoff + 32;                                 // 32: global offset of column c
   uint32_t* lamcol = (uint32_t*)(coff + 32);                    // 32: tile-local index of column c
   int32_t* xe = (int32_t*)(lamcol + 32);                        // [2][128][2]: half-row exponent maxima
-  int32_t* etab = xe + 2 * 128 * 2;                             // [2][128]: row exponent maxima
+  int32_t* etab = xe + 2 * 128 * 2;                             // [2][128]: row scale exponents E
   int32_t* qpos = etab + 2 * 128;                               // tile[12], row[7], col[5], p
-  // full[2] empty[2] afull mdone dfree efull[2] wfull wfree xbar[2][4]
+  // full[2] empty[2] afull mdone dfree efull[2] wfull wfree xbar[2][4] dfree01
   uint64_t* bar = (uint64_t*)(qpos + 26);
-  uint32_t* tmem_slot = (uint32_t*)(bar + 19);
+  uint32_t* tmem_slot = (uint32_t*)(bar + 20);
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -204,10 +229,10 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     while (pp < 12 && p.tile[pp] == pp) ++pp;
     qpos[24] = pp;
     s_abort = 0;
-    // arrivals: full, wfull, wfree, mdone: 1 (expect_tx / commit); empty, afull, dfree, efull: one per
-    // warp of 8; xbar (row-exponent exchange of converter warps quad and quad + 4): 2
-    const uint32_t cnt[19] = {1, 1, 8, 8, 8, 1, 8, 8, 8, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2};
-    for (int i = 0; i < 19; ++i)
+    // arrivals: full, wfull, wfree, mdone: 1 (expect_tx / commit); empty, afull, dfree, efull, dfree01:
+    // one per warp of 8; xbar (row-exponent exchange of converter warps quad and quad + 4): 2
+    const uint32_t cnt[20] = {1, 1, 8, 8, 8, 1, 8, 8, 8, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 8};
+    for (int i = 0; i < 20; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)), "r"(cnt[i]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -268,11 +293,12 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   uint64_t* empty = bar + 2;
   uint64_t* afull = bar + 4;
   uint64_t* mdone = bar + 5;
-  uint64_t* dfree = bar + 6;
+  uint64_t* dfree = bar + 6;      // levels 2-4 of the accumulators read (folded into levels 0-1)
   uint64_t* efull = bar + 7;
   uint64_t* wfull = bar + 9;
-  uint64_t* wfree = bar + 10;   // completes when the MMAs on a state's W planes are done
-  uint64_t* xbar = bar + 11;    // [parity][quad]
+  uint64_t* wfree = bar + 10;     // completes when the MMAs on a state's W planes are done
+  uint64_t* xbar = bar + 11;      // [parity][quad]
+  uint64_t* dfree01 = bar + 19;   // levels 0-1 (the folded FP32 pairs) read
   auto tile_of = [&](uint64_t i) -> uint64_t { return t_begin + i * tstep; };
   auto state_ptr = [&](uint64_t tt) -> double2* {
     if constexpr (MULTI) return (double2*)psis[tt >> lg_tiles1];
@@ -355,10 +381,13 @@ __global__ void __launch_bounds__(kT2Threads, 1)
           ++w_seen;
         }
         if (!mbar_wait(smem_u32(afull), (uint32_t)(i & 1), spin)) { fail(1); break; }
+        // levels 2-4 (18 of the 21 products) as soon as the drainers have folded
+        // the previous tile's levels into levels 0-1, then levels 0-1 once they
+        // have read those back
         if (i >= 1 && !mbar_wait(smem_u32(dfree), (uint32_t)((i - 1) & 1), spin)) { fail(1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int l = 0; l < 5; ++l) {
+        for (int l = 2; l < 5; ++l) {
 #pragma unroll
           for (int ai = 0; ai <= l; ++ai) {
 #pragma unroll
@@ -377,6 +406,23 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 #pragma unroll
         for (int ks = 0; ks < 4; ++ks)
           t2_mma(tmem + kT2AccCol + 64 * 4, tmem + 32 * 5 + 8 * ks, smem_desc(wb + 32 * ks), 1u);
+        if (i >= 1 && !mbar_wait(smem_u32(dfree01), (uint32_t)((i - 1) & 1), spin)) {
+          mma_commit(smem_u32(mdone));   // the issued MMAs complete before the abort drain below
+          ++i;
+          fail(1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int l = 0; l < 2; ++l) {
+#pragma unroll
+          for (int ai = 0; ai <= l; ++ai) {
+#pragma unroll
+            for (int ks = 0; ks < 4; ++ks)
+              t2_mma(tmem + kT2AccCol + 64 * l, tmem + 32 * ai + 8 * ks,
+                     smem_desc(wb + (l - ai) * kT2PlaneBytes + 32 * ks), (ai | ks) ? 1u : 0u);
+          }
+        }
         mma_commit(smem_u32(mdone));
         if (i + 1 < my && new_state(i + 1)) mma_commit(smem_u32(wfree));   // last tile on these planes
       }
@@ -400,13 +446,19 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         const int s = (int)(i & 1), par = (int)(i & 1);
         if (!mbar_wait_warp(smem_u32(full + s), (uint32_t)((i >> 1) & 1), spin)) { ok = false; break; }
         const unsigned char* sl = sl0 + s * kT2SlotBytes;
-        // the row's exponent: maximum biased FP64 exponent over its 64 reals
+        // the row's exponent: maximum biased exponent over its 64 reals (of the
+        // FP64 values, or of the pairs' leading floats)
         int em = 0;
 #pragma unroll 4
         for (int j = 0; j < 16; ++j) {
           const uint4 v = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + j]));
-          em = max(em, (int)((v.y >> 20) & 0x7ffu));
-          em = max(em, (int)((v.w >> 20) & 0x7ffu));
+          if constexpr (PIN) {
+            em = max(em, (int)((v.x >> 23) & 0xffu));
+            em = max(em, (int)((v.y >> 23) & 0xffu));
+          } else {
+            em = max(em, (int)((v.y >> 20) & 0x7ffu));
+            em = max(em, (int)((v.w >> 20) & 0x7ffu));
+          }
         }
         // exchange with the warp holding the other half of the same rows (bounded
         // wait, no named barrier: a warp that aborts must not leave its partner stuck)
@@ -415,33 +467,47 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         if (lane == 0) mbar_arrive(smem_u32(xbar + par * 4 + quad));
         if (!mbar_wait_warp(smem_u32(xbar + par * 4 + quad), (uint32_t)((i >> 1) & 1), spin)) { ok = false; break; }
         em = max(em, xe[(par * 128 + row) * 2 + (h ^ 1)]);
-        // A planes are free once the previous tile's MMAs are done; that also
-        // means the drainers of tile i - 2 (same parity) have read their
-        // exponents (they release the accumulators the MMAs of tile i - 1 need
-        // only after reading them), so this tile's may take their place now.
-        if (i >= 1 && !mbar_wait_warp(smem_u32(mdone), (uint32_t)((i - 1) & 1), spin)) { ok = false; break; }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        if (h == 0) etab[par * 128 + row] = em;
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(efull + par));
+        // row scale 2^E, |a| < 2^E; E >= -101 keeps every scale below a float
+        const int E = max(PIN ? em - 126 : em - 1022, -101);
+        const int fe_off = -888 - E;                    // FP64 input: biased exponent offset of s
+        const float sc8 = t2_pow2(8 - E), sc26 = t2_pow2(26 - E);   // pair input
 #pragma unroll 1
         for (int c8 = 0; c8 < 2; ++c8) {
+          // digits of 8 columns; the first 8 while the previous tile's MMAs may
+          // still read the A planes
           uint32_t pl[6][8];
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const uint4 v = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + 8 * c8 + j]));
             float dr[6], di[6];
-            t2_digits(v.y, v.x, em, dr);
-            t2_digits(v.w, v.z, em, di);
+            if constexpr (PIN) {
+              t2_digits_pair(__uint_as_float(v.x), __uint_as_float(v.z), sc8, sc26, dr);
+              t2_digits_pair(__uint_as_float(v.y), __uint_as_float(v.w), sc8, sc26, di);
+            } else {
+              t2_digits(v.y, v.x, fe_off, dr);
+              t2_digits(v.w, v.z, fe_off, di);
+            }
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
               const __half2 hv = __floats2half2_rn(dr[q], di[q]);
               pl[q][j] = *(const uint32_t*)&hv;
             }
           }
+          if (c8 == 0) {
+            // A planes are free once the previous tile's MMAs are done; that also
+            // means the drainers of tile i - 2 (same parity) have read their
+            // exponents (they release the accumulators the MMAs of tile i - 1
+            // need only after reading them), so this tile's may take their place.
+            if (i >= 1 && !mbar_wait_warp(smem_u32(mdone), (uint32_t)((i - 1) & 1), spin)) { ok = false; break; }
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            if (h == 0) etab[par * 128 + row] = E;
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(efull + par));
+          }
 #pragma unroll
           for (int q = 0; q < 6; ++q) tmem_st8(tmem + tq + 32 * q + 16 * h + 8 * c8, pl[q]);
         }
+        if (!ok) break;
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
@@ -459,30 +525,68 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         if (!mbar_wait_warp(smem_u32(mdone), (uint32_t)(i & 1), spin)) { ok = false; break; }
         if (!mbar_wait_warp(smem_u32(efull + par), (uint32_t)((i >> 1) & 1), spin)) { ok = false; break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const int em = etab[par * 128 + row];
+        const int E = etab[par * 128 + row];
+        const float osc = t2_pow2(E - 16);   // pair output scale
         const uint64_t tt = tile_of(i);
         double2* __restrict__ psi = state_ptr(tt);
         const uint64_t rb = tile_base(tt & tmask1) | roff;
+        // fold: per 8 columns, the five levels into an FP32 pair (s, e) written
+        // back over levels 0 and 1, which releases levels 2-4 to the next MMAs
+        const uint32_t col0 = tmem + tq + kT2AccCol + 32 * h;
 #pragma unroll 1
         for (int c4 = 0; c4 < 4; ++c4) {
+          const uint32_t col = col0 + 8 * c4;
           uint32_t a[5][8];
 #pragma unroll
-          for (int l = 0; l < 5; ++l) tmem_ld8(tmem + tq + kT2AccCol + 64 * l + 32 * h + 8 * c4, a[l]);
+          for (int l = 0; l < 5; ++l) tmem_ld8(col + 64 * l, a[l]);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (c4 == 3) {   // accumulators read; the last stores follow
+          uint32_t ps[8], pe[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) {
+            float sk = __uint_as_float(a[0][k]), ek = 0.f;
+            t2_absorb(sk, ek, __uint_as_float(a[1][k]), 0.001953125f);
+            t2_absorb(sk, ek, __uint_as_float(a[2][k]), 3.814697265625e-06f);
+            t2_absorb(sk, ek, __uint_as_float(a[3][k]), 7.450580596923828e-09f);
+            ek = __fmaf_rn(__uint_as_float(a[4][k]), 1.4551915228366852e-11f, ek);
+            ps[k] = __float_as_uint(sk);
+            pe[k] = __float_as_uint(ek);
+          }
+          tmem_st8(col, ps);
+          tmem_st8(col + 64, pe);
+        }
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(dfree));
+        // the pairs back, joined to FP64 and stored
+#pragma unroll 1
+        for (int c4 = 0; c4 < 4; ++c4) {
+          const uint32_t col = col0 + 8 * c4;
+          uint32_t ps[8], pe[8];
+          tmem_ld8(col, ps);
+          tmem_ld8(col + 64, pe);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (c4 == 3) {   // levels 0-1 read; the last stores follow
             asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
             __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(dfree));
+            if (lane == 0) mbar_arrive(smem_u32(dfree01));
           }
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
-            double2 o;
-            o.x = t2_combine(__uint_as_float(a[0][2 * j]), __uint_as_float(a[1][2 * j]), __uint_as_float(a[2][2 * j]),
-                             __uint_as_float(a[3][2 * j]), __uint_as_float(a[4][2 * j]), em);
-            o.y = t2_combine(__uint_as_float(a[0][2 * j + 1]), __uint_as_float(a[1][2 * j + 1]),
-                             __uint_as_float(a[2][2 * j + 1]), __uint_as_float(a[3][2 * j + 1]),
-                             __uint_as_float(a[4][2 * j + 1]), em);
-            psi[rb | coff[16 * h + 4 * c4 + j]] = o;
+            if constexpr (POUT) {
+              float sr = __uint_as_float(ps[2 * j]), er = __uint_as_float(pe[2 * j]);
+              float si = __uint_as_float(ps[2 * j + 1]), ei = __uint_as_float(pe[2 * j + 1]);
+              const float tr = __fadd_rn(sr, er), ti = __fadd_rn(si, ei);   // FastTwoSum
+              er = __fsub_rn(er, __fsub_rn(tr, sr));
+              ei = __fsub_rn(ei, __fsub_rn(ti, si));
+              *(float4*)(psi + (rb | coff[16 * h + 4 * c4 + j])) =
+                  make_float4(__fmul_rn(tr, osc), __fmul_rn(ti, osc), __fmul_rn(er, osc), __fmul_rn(ei, osc));
+            } else {
+              double2 o;
+              o.x = t2_join(__uint_as_float(ps[2 * j]), __uint_as_float(pe[2 * j]), E);
+              o.y = t2_join(__uint_as_float(ps[2 * j + 1]), __uint_as_float(pe[2 * j + 1]), E);
+              psi[rb | coff[16 * h + 4 * c4 + j]] = o;
+            }
           }
         }
       }
@@ -497,22 +601,40 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 
 size_t tc128_smem_bytes() {
   return 2 * (size_t)kT2SlotBytes + kT2WBytes + 4 * 256 * 8 + 32 * 8 * 2 + 32 * 4 + 2 * 128 * 2 * 4 + 2 * 128 * 4 +
-         26 * 4 + 19 * 8 + 16 + 1024;
+         26 * 4 + 20 * 8 + 16 + 1024;
 }
 
 static bool g_tc128_ready = false;
 static int g_tc128_sms = 0;
 
 // Host-side set-up (outside any stream capture): shared-memory attribute and SM count.
+template <bool MULTI, bool PIN, bool POUT>
+static cudaError_t set_tc128_attribute(int smem) {
+  return cudaFuncSetAttribute(k_tc128<MULTI, PIN, POUT>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+}
+
 cudaError_t prepare_tc128_pass() {
   if (g_tc128_ready) return cudaSuccess;
   const int smem = (int)tc128_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_tc128<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_tc128<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e = set_tc128_attribute<false, false, false>(smem);
+  if (e == cudaSuccess) e = set_tc128_attribute<false, false, true>(smem);
+  if (e == cudaSuccess) e = set_tc128_attribute<false, true, false>(smem);
+  if (e == cudaSuccess) e = set_tc128_attribute<false, true, true>(smem);
+  if (e == cudaSuccess) e = set_tc128_attribute<true, false, false>(smem);
+  if (e == cudaSuccess) e = set_tc128_attribute<true, false, true>(smem);
+  if (e == cudaSuccess) e = set_tc128_attribute<true, true, false>(smem);
+  if (e == cudaSuccess) e = set_tc128_attribute<true, true, true>(smem);
   if (e != cudaSuccess) return e;
   g_tc128_sms = device_sm_count();
   g_tc128_ready = true;
   return cudaSuccess;
+}
+
+template <bool MULTI, bool PIN, bool POUT>
+static void launch_tc128_instance(unsigned grid, size_t smem, cudaStream_t st, double2* psi, void* const* psis,
+                                  const Tc5PassDesc& p, const uint4* w, int64_t ws16, int lg, uint64_t ntiles, int* err,
+                                  uint32_t spin) {
+  k_tc128<MULTI, PIN, POUT><<<grid, kT2Threads, smem, st>>>(psi, psis, p, w, ws16, lg, ntiles, err, spin);
 }
 
 cudaError_t launch_tc128_pass(void* psi, void* const* psis, int nstates, int64_t wstride, int n,
@@ -525,10 +647,20 @@ cudaError_t launch_tc128_pass(void* psi, void* const* psis, int nstates, int64_t
   const size_t smem = tc128_smem_bytes();
   const uint4* w = (const uint4*)wimg;
   const int64_t ws16 = wstride / 8;   // uint16 elements -> uint4
-  if (psis != nullptr)
-    k_tc128<true><<<grid, kT2Threads, smem, st>>>(nullptr, psis, p, w, ws16, n - 12, ntiles, err, spin);
-  else
-    k_tc128<false><<<grid, kT2Threads, smem, st>>>((double2*)psi, nullptr, p, w, ws16, n - 12, ntiles, err, spin);
+  double2* ps = (double2*)psi;
+  const int lg = n - 12;
+  const int fmt = (p.in_pairs ? 1 : 0) | (p.out_pairs ? 2 : 0);
+  if (psis != nullptr) {
+    if (fmt == 0) launch_tc128_instance<true, false, false>(grid, smem, st, nullptr, psis, p, w, ws16, lg, ntiles, err, spin);
+    else if (fmt == 1) launch_tc128_instance<true, true, false>(grid, smem, st, nullptr, psis, p, w, ws16, lg, ntiles, err, spin);
+    else if (fmt == 2) launch_tc128_instance<true, false, true>(grid, smem, st, nullptr, psis, p, w, ws16, lg, ntiles, err, spin);
+    else launch_tc128_instance<true, true, true>(grid, smem, st, nullptr, psis, p, w, ws16, lg, ntiles, err, spin);
+  } else {
+    if (fmt == 0) launch_tc128_instance<false, false, false>(grid, smem, st, ps, nullptr, p, w, ws16, lg, ntiles, err, spin);
+    else if (fmt == 1) launch_tc128_instance<false, true, false>(grid, smem, st, ps, nullptr, p, w, ws16, lg, ntiles, err, spin);
+    else if (fmt == 2) launch_tc128_instance<false, false, true>(grid, smem, st, ps, nullptr, p, w, ws16, lg, ntiles, err, spin);
+    else launch_tc128_instance<false, true, true>(grid, smem, st, ps, nullptr, p, w, ws16, lg, ntiles, err, spin);
+  }
   note_launch();
   return cudaGetLastError();
 }

@@ -99,6 +99,10 @@ struct Tc5PassDesc {
   int32_t row[7];          // global qubits of the row bits, ascending
   int32_t col[5];          // block qubits, ascending (bit j of the column index = local bit j)
   int32_t tile[12];        // row and column qubits together, ascending
+  // 1 = the pass reads / writes the state as FP32 pairs (between consecutive
+  // complex128 tensor-core passes; per amplitude the floats re.s, im.s, re.e,
+  // im.e, value s + e), 0 = as complex128
+  int32_t in_pairs, out_pairs;
 };
 // uint16 elements of one pass's W digit planes: g_0..g_4 and 2^-9 g_1..2^-9 g_5, 4096 each
 constexpr int64_t kTc128WElems = 10 * 4096;

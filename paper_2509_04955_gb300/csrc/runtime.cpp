@@ -879,6 +879,16 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
       emit_phase_pass(*p, r, in);
   }
   flush();
+  // Consecutive complex128 tensor-core passes hand the state over as FP32
+  // pairs (about 48 significant bits, the same 16 bytes per amplitude): only
+  // the first of a run reads complex128 and only the last writes it.
+  if (dt == QS_C128)
+    for (size_t i = 0; i < p->steps.size(); ++i)
+      if (p->steps[i].kind == 1) {
+        Tc5PassDesc& t = p->tc5desc[p->steps[i].idx];
+        t.in_pairs = i > 0 && p->steps[i - 1].kind == 1;
+        t.out_pairs = i + 1 < p->steps.size() && p->steps[i + 1].kind == 1;
+      }
   in.passes = (int64_t)p->steps.size();
   in.launches = in.passes;
   in.sweeps = (double)in.passes;

@@ -13,6 +13,8 @@ what it relies on:
 * the combination of the five levels back to FP64 (FP32 pairs joined by
   integer arithmetic) equals their exact sum to 2^-46 relative, including
   results just below a power of two;
+* the FP32-pair form kept between consecutive passes: digits taken from a
+  pair, and a row read and written as pairs, keep the same bounds;
 * a whole row: U psi through digits, exact level sums (level 5 folded into
   level 4) and the combination is within 2^-46 of the row's scale 2^E
   (|a| < 2^E <= 2 max |a|) of the FP64 product, for
@@ -22,8 +24,10 @@ what it relies on:
   tile at its tile-local index, the tiles partition the state, and stores
   go to roff(row) | coff(column) of the tile;
 * barriers: the single-buffered A and accumulator protocol (with the row
-  exponent exchange and the exponent table) has no deadlock or hazard under
-  random delays, for 1 to 54 tiles per CTA, with and without W reloads.
+  exponent exchange, the exponent table, and the two-step release of the
+  accumulators: levels 2-4 after the fold, levels 0-1 after the read-back)
+  has no deadlock or hazard under random delays, for 1 to 54 tiles per CTA,
+  with and without W reloads.
 """
 import random
 from fractions import Fraction
@@ -78,6 +82,55 @@ def digits(a, emax_b):
     return np.stack([d0, d1, d2, d3, d4, d5]).astype(np.float64)
 
 
+def digits_pair(s, e, E):
+    """t2_digits_pair: the digits of s + e (FP32 pairs) for a row of scale 2^E."""
+    hi = np.asarray(s, dtype=np.float32) * F32(2.0 ** (8 - E))
+    lo18 = np.asarray(e, dtype=np.float32) * F32(2.0 ** (26 - E))
+    d0 = rint32(hi)
+    t = hi - d0
+    u1 = t * F32(512)
+    d1 = rint32(u1)
+    t = u1 - d1
+    d2 = rint32(t * F32(512) + lo18)
+    t = (t * F32(512) - d2) + lo18
+    u3 = t * F32(512)
+    d3 = rint32(u3)
+    t = u3 - d3
+    u4 = t * F32(512)
+    d4 = rint32(u4)
+    t = u4 - d4
+    d5 = rint32(t * F32(512))
+    return np.stack([d0, d1, d2, d3, d4, d5]).astype(np.float64)
+
+
+def to_pairs(a):
+    """FP64 values as normalised FP32 pairs (s, e), s + e = a to about 2^-48."""
+    s = np.asarray(a, dtype=np.float64).astype(np.float32)
+    e = (np.asarray(a, dtype=np.float64) - s.astype(np.float64)).astype(np.float32)
+    return s, e
+
+
+def pair_row_scale(s):
+    """E of a row held as pairs: max biased FP32 exponent - 126, at least -101."""
+    ex = (np.asarray(s, dtype=np.float32).view(np.uint32) >> np.uint32(23)) & np.uint32(0xFF)
+    return max(int(ex.max()) - 126, -101)
+
+
+def pair_out(c, E):
+    """The drainer's pair output: levels folded, FastTwoSum, scaled by 2^(E - 16)."""
+    c0, c1, c2, c3, c4 = (F32(x) for x in c)
+    s, e = two_sum(c0, c1 * F32(2.0 ** -9))
+    s, e2 = two_sum(s, c2 * F32(2.0 ** -18))
+    e = e + e2
+    s, e2 = two_sum(s, c3 * F32(2.0 ** -27))
+    e = e + e2
+    e = c4 * F32(2.0 ** -36) + e
+    t = s + e
+    e = e - (t - s)
+    sc = F32(2.0 ** (E - 16))
+    return t * sc, e * sc
+
+
 def w_digits(w):
     """build_w_digits for one value: balanced digits of X = rint(w 2^53)."""
     X = int(np.rint(np.ldexp(np.float64(w), 53)))
@@ -96,7 +149,8 @@ def two_sum(a, b):
 
 
 def combine(c, emax_b):
-    """t2_combine: five level sums (float32) -> FP64 value 2^(emax_b - 1038) sum_l c_l 2^(-9 l)."""
+    """t2_join after the fold: five level sums (float32) -> FP64 value
+    2^(emax_b - 1038) sum_l c_l 2^(-9 l) (emax_b = E + 1022)."""
     c0, c1, c2, c3, c4 = (F32(x) for x in c)
     s, e = two_sum(c0, c1 * F32(2.0 ** -9))
     s, e2 = two_sum(s, c2 * F32(2.0 ** -18))
@@ -129,12 +183,20 @@ def row_emax(vals):
     return int(((u >> np.uint64(52)) & np.uint64(0x7FF)).max())
 
 
-def apply_row(U, a):
-    """One output row of the pass: U (32x32 complex) applied to a (32 complex) the kernel's way."""
+def apply_row(U, a, pairs_in=False, pairs_out=False):
+    """One output row of the pass: U (32x32 complex) applied to a (32 complex)
+    the kernel's way, reading FP64 values or FP32 pairs and writing FP64
+    values or pairs (returned joined in FP64 for comparison)."""
     reals = np.empty(64)
     reals[0::2], reals[1::2] = a.real, a.imag
-    em = row_emax(reals)
-    D = digits(reals, em)                            # 6 x 64
+    if pairs_in:
+        ps, pe = to_pairs(reals)
+        E = pair_row_scale(ps)
+        D = digits_pair(ps, pe, E)
+    else:
+        E = max(row_emax(reals) - 1022, -101)
+        D = digits(reals, np.full(64, E + 1022))
+    em = E + 1022
     assert np.abs(D).max() <= 260
     Wd = np.zeros((6, 64, 64), dtype=np.int64)       # [j][k][nn]
     for co in range(32):
@@ -159,7 +221,11 @@ def apply_row(U, a):
             if l == 4:   # level 5 folded in: A_i (2^-9 W_(5-i)), i < 5, and (2^-9 A_5) W_0
                 tot = Fraction(tot) + sum(Fraction(int((Di[i] * Wd[5 - i, :, nn]).sum()), 512) for i in range(0, 6))
             lev.append(F32(float(tot)))                # exact for levels <= 2 (checked), rounded above
-        out[nn] = combine(lev, em)
+        if pairs_out:
+            so, eo = pair_out(lev, E)
+            out[nn] = float(so) + float(eo)
+        else:
+            out[nn] = combine(lev, em)
     return out[0::2] + 1j * out[1::2], em
 
 
@@ -212,6 +278,32 @@ def test_combine_equals_the_exact_level_sum():
         got = combine(c, em)
         # relative to the result, or absolute at 2^-34 of a level-0 unit (2^(E-50) for rows scaled 2^E)
         assert abs(Fraction(got) - exact) <= abs(exact) * Fraction(2) ** -46 + Fraction(2) ** (em - 1038 - 34)
+
+
+def test_pair_digits_reconstruct_every_value_of_a_row():
+    rng = np.random.default_rng(3)
+    vals = np.concatenate([rng.standard_normal(4000) * 10.0 ** rng.integers(-12, 1, 4000),
+                           [0.0, -0.0, 1.0, -1.0, 0.5, 2.0 ** -30, 0.999999999, 1e-40]])
+    s, e = to_pairs(vals)
+    E = pair_row_scale(s)
+    assert np.all(np.abs(vals) < 2.0 ** E)
+    D = digits_pair(s, e, E)
+    assert np.abs(D).max() <= 260
+    rec = sum(D[i] * 2.0 ** (-9 * i) for i in range(6)) * 2.0 ** (E - 8)
+    # the pair holds the value to 2^-48 relative; the digits to 2^(E-46)
+    assert np.abs(rec - vals).max() <= 2.0 ** (E - 46) + 2.0 ** -47 * np.abs(vals).max()
+
+
+@pytest.mark.parametrize("pairs_in,pairs_out", [(False, True), (True, True), (True, False)])
+def test_a_whole_row_through_fp32_pairs(pairs_in, pairs_out):
+    rng = np.random.default_rng(7)
+    for trial in range(3):
+        U = haar(32, rng)
+        a = (rng.standard_normal(32) + 1j * rng.standard_normal(32)) / 8
+        if trial == 2:
+            a[::3] = 0
+        got, em = apply_row(U, a, pairs_in, pairs_out)
+        assert np.abs(got - U @ a).max() <= 2.0 ** -46 * 2.0 ** (em - 1022)
 
 
 @pytest.mark.parametrize("shape", ["random", "one", "mixed", "tiny", "powers", "zeros"])
@@ -342,14 +434,17 @@ def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True):
     state = lambda i: (t_begin + i) // tiles_per_state
     new_state = lambda i: i > 0 and state(i) != state(i - 1)
     full, empty = [_Bar(1), _Bar(1)], [_Bar(8), _Bar(8)]
-    afull, mdone, dfree = _Bar(8), _Bar(1), _Bar(8)
+    afull, mdone, dfree, dfree01 = _Bar(8), _Bar(1), _Bar(8), _Bar(8)
     efull = [_Bar(8), _Bar(8)]
     xbar = [[_Bar(2) for _ in range(4)] for _ in range(2)]
     wfull, wfree = _Bar(1), _Bar(1)
     events, now, last_finish = [], [0.0], [0.0]
     W = {"state": state(0), "writing": None}
     A = {"tile": None}                   # tile whose digits the A planes hold
-    Dacc = {"tile": None, "read": True}  # tile whose levels the accumulators hold
+    # levels 2-4 and levels 0-1 of the accumulators: tile they hold, and whether
+    # the drainers are done with them (folded, resp. read back)
+    D24 = {"tile": None, "free": True}
+    D01 = {"tile": None, "free": True}
     slot_of = {0: None, 1: None}
     xe = {}                              # (parity, quad, half) -> tile
     etab = {0: None, 1: None}
@@ -390,20 +485,27 @@ def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True):
                 yield lambda: wfull.ok(seen & 1)
                 seen += 1
             yield lambda: afull.ok(i & 1)
-            if i >= 1:
+            if i >= 1:                   # levels 2-4 first
                 yield lambda: dfree.ok((i - 1) & 1)
             if W["state"] != state(i) or W["writing"] is not None:
                 errors.append("MMA reads the wrong W")
             if A["tile"] != i:
                 errors.append("MMA reads digits of another tile")
-            if not Dacc["read"]:
-                errors.append("accumulators overwritten before they were read")
-            Dacc["tile"], Dacc["read"] = None, False
+            if not D24["free"]:
+                errors.append("levels 2-4 overwritten before they were folded")
+            D24["tile"], D24["free"] = None, False
             inflight[i] = state(i)
+            if i >= 1:                   # then levels 0-1
+                yield lambda: dfree01.ok((i - 1) & 1)
+            if not D01["free"]:
+                errors.append("levels 0-1 overwritten before they were read back")
+            if A["tile"] != i:
+                errors.append("MMA reads digits of another tile")
+            D01["tile"], D01["free"] = None, False
 
             def finish(i=i, last=(i + 1 < my and new_state(i + 1))):
                 del inflight[i]
-                Dacc["tile"] = i
+                D24["tile"] = D01["tile"] = i
                 mdone.arrive()
                 if last:
                     wfree.arrive()
@@ -444,15 +546,23 @@ def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True):
             par = i & 1
             yield lambda: mdone.ok(i & 1)
             yield lambda: efull[par].ok((i >> 1) & 1)
-            if Dacc["tile"] != i:
+            if D24["tile"] != i or D01["tile"] != i:
                 errors.append("accumulators read before their MMAs finished")
             if etab[par] != i:
                 errors.append("exponent table holds another tile")
-            yield ("sleep", rng.uniform(0, 1))
+            yield ("sleep", rng.uniform(0, 1))     # fold into levels 0-1
+            if D01["tile"] != i:
+                errors.append("folded pairs written over another tile's levels")
             dfree.arrive()
-            if dfree.pending == dfree.count:   # the eighth drainer warp: accumulators free
-                Dacc["read"] = True
-            yield ("sleep", rng.uniform(0, 4))   # combination and stores after the release
+            if dfree.pending == dfree.count:   # the eighth drainer warp: levels 2-4 free
+                D24["free"] = True
+            yield ("sleep", rng.uniform(0, 1))     # read the pairs back
+            if D01["tile"] != i:
+                errors.append("pairs read back from another tile")
+            dfree01.arrive()
+            if dfree01.pending == dfree01.count:
+                D01["free"] = True
+            yield ("sleep", rng.uniform(0, 4))   # joins and stores after the release
 
     roles = [producer(), mma()] + [converter(q, h) for h in range(2) for q in range(4)] + \
             [drainer() for _ in range(8)]
