@@ -35,6 +35,24 @@
 
 typedef double complex cplx;
 
+/* Threads for the gate loops (the CPU-baseline timing on all host cores):
+ * each iteration updates its own pair or quad of amplitudes, so any thread
+ * count gives identical results. One thread unless or_set_threads asks. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+static int g_threads = 1;
+
+int or_set_threads(int t) {
+#ifdef _OPENMP
+  g_threads = t > 0 ? t : omp_get_num_procs();
+#else
+  (void)t;
+  g_threads = 1;
+#endif
+  return g_threads;
+}
+
 static int popcount64(uint64_t v) {
   int c = 0;
   while (v) { v &= v - 1; ++c; }
@@ -115,6 +133,7 @@ static uint64_t control_mask(const or_gate *g) {
 static void apply_single_target(cplx *psi, int n, int t, uint64_t cmask, const cplx *u) {
   const uint64_t mask_t = 1ull << t;
   const uint64_t dim = 1ull << n;
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
   for (uint64_t i = 0; i < dim; ++i) {
     if ((i & cmask) != cmask) continue;
     if (i & mask_t) continue;
@@ -129,6 +148,7 @@ static void apply_single_target(cplx *psi, int n, int t, uint64_t cmask, const c
 static void apply_two_target(cplx *psi, int n, int t1, int t2, uint64_t cmask, const cplx *u) {
   const uint64_t m1 = 1ull << t1, m2 = 1ull << t2;
   const uint64_t dim = 1ull << n;
+#pragma omp parallel for schedule(static) num_threads(g_threads) if (g_threads > 1)
   for (uint64_t i = 0; i < dim; ++i) {
     if ((i & cmask) != cmask) continue;
     if (i & (m1 | m2)) continue;

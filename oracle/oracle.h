@@ -44,6 +44,9 @@ int or_gate_matrix(const or_gate *g, const double *theta, double *m);
 int or_gate_dmatrix(const or_gate *g, const double *theta, double *m);
 
 /* |x> of Eq. 1. */
+/* Threads the gate loops use (t <= 0: all processors); returns the count in
+ * effect (1 when built without OpenMP). Results do not depend on it. */
+int or_set_threads(int t);
 void or_set_basis(double *psi, int n, uint64_t x);
 /* One gate in place: Algorithm 1 / Eq. 3 (pairs i, i + 2^t) for one target,
  * Algorithm 2 / Eq. 4 (only indices whose control bits are all 1) for

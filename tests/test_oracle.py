@@ -365,3 +365,20 @@ def test_controlled_rotation_gradient_matches_fd():
     H = W.random_pauli_sum(n, 6, 1)
     e, g = O.adjoint_grad(O.basis(n, 0), n, gates, theta, *H)
     assert np.abs(g - _finite_diff(O.basis(n, 0), n, gates, theta, H)).max() < 1e-8
+
+
+def test_oracle_thread_count_does_not_change_results():
+    """The gate loops' optional threads (all-cores CPU baseline) update
+    disjoint amplitudes: a circuit with controls, two-target gates and every
+    kind gives bit-identical states on 1 thread and on all processors."""
+    L = O.lib()
+    n = 16
+    gates = W.random_gate_mix(n, 120, seed=5)
+    try:
+        assert L.or_set_threads(1) == 1
+        a = O.apply_circuit(O.basis(n, 3), n, gates)
+        L.or_set_threads(0)
+        b = O.apply_circuit(O.basis(n, 3), n, gates)
+    finally:
+        L.or_set_threads(1)
+    assert np.array_equal(a, b)
