@@ -1,12 +1,12 @@
 #!/usr/bin/env python
 """Benchmark: circuit wall time and effective HBM GB/s per state sweep, fused
-vs per-gate, on one GB300 (n = 30 random layered circuit, complex64 headline;
-complex128 and per-gate numbers alongside).
+vs per-gate, on one GB300 (n = 30 random layered circuit; complex128 headline
+on the tensor-core plan, complex64 and per-gate numbers alongside).
 
-One step = one execution of the fused circuit on the resident 2^30-amplitude
-state followed by its FP64 norm (the whole hot path: tile passes + reduction).
-The state (8 GiB complex64, 16 GiB complex128) is far larger than the 129 MB
-L2, so no flush is needed between steps.
+One step = one execution of the contracted circuit on the resident
+2^30-amplitude complex128 state (every 5-qubit block on tensor cores as exact
+fp16 digit products) followed by its FP64 norm. The state (16 GiB) is far
+larger than the 129 MB L2, so no flush is needed between steps.
 
     python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
@@ -125,27 +125,60 @@ class ClockSampler:
 
 # ----------------------------------------------------------------- oracle timing
 
-def oracle_sample(args, gates, budget_s: float = 15.0):
-    """Times the FP64 oracle (single thread) on the first gates of the same
-    circuit at the same n; returns (ms per full circuit, description, gates done)."""
+def oracle_sample(args, gates, threads: int, budget_s: float = 60.0):
+    """Times the FP64 oracle on the same circuit at the same n.
+
+    threads = 1: the first gate of each kind the circuit holds (a complete
+    gate-kind sample), scaled by the circuit's count of each kind. threads > 1
+    (0 = all processors): whole layers (every gate of layer 1, then more
+    layers while the budget lasts), scaled by the number of layers.
+    Returns (ms per full circuit, description, threads used)."""
     import ctypes as C
     import numpy as np
     import oracle as O
     n = args.n
+    L = O.lib()
+    used = L.or_set_threads(threads)
     psi = np.zeros(1 << n, dtype=np.complex128)
     psi[0] = 1
-    L = O.lib()
     packed = O.pack(gates)
     theta = (C.c_double * 1)()
     ptr = psi.ctypes.data_as(C.POINTER(C.c_double))
-    done, t0 = 0, time.perf_counter()
-    while done < len(gates) and time.perf_counter() - t0 < budget_s:
-        L.or_apply_gate(ptr, n, C.byref(packed[done]), theta)
-        done += 1
-    dt = time.perf_counter() - t0
-    ms = dt / done * len(gates) * 1e3
-    return ms, (f"oracle (plain C, FP64, 1 thread) applied the first {done} of {len(gates)} gates of the same "
-                f"circuit at n={n} in {dt:.1f} s; value scaled by {len(gates)}/{done}"), done
+
+    def kind(g):
+        return (g.kind, len(g.controls))
+    try:
+        if used == 1:
+            first, counts = {}, {}
+            for i, g in enumerate(gates):
+                counts[kind(g)] = counts.get(kind(g), 0) + 1
+                first.setdefault(kind(g), i)
+            per = {}
+            t_all = 0.0
+            for k, i in first.items():
+                t0 = time.perf_counter()
+                L.or_apply_gate(ptr, n, C.byref(packed[i]), theta)
+                per[k] = time.perf_counter() - t0
+                t_all += per[k]
+            ms = sum(per[k] * counts[k] for k in counts) * 1e3
+            kinds = ", ".join(f"{k[0]}{'+c' * k[1]} x{counts[k]}" for k in sorted(counts))
+            desc = (f"oracle (plain C, FP64) on 1 thread: one gate of each kind of the circuit at n={n} "
+                    f"({len(per)} gates, {t_all:.1f} s), scaled by the circuit's counts ({kinds})")
+        else:
+            per_layer = len(gates) // args.depth
+            t0 = time.perf_counter()
+            layers = 0
+            while layers < args.depth and (layers == 0 or time.perf_counter() - t0 < budget_s / 2):
+                for i in range(layers * per_layer, (layers + 1) * per_layer):
+                    L.or_apply_gate(ptr, n, C.byref(packed[i]), theta)
+                layers += 1
+            dt = time.perf_counter() - t0
+            ms = dt / layers * args.depth * 1e3
+            desc = (f"oracle (plain C, FP64) on {used} threads: {layers} whole layer(s) of {per_layer} gates "
+                    f"at n={n} in {dt:.1f} s, scaled to the {args.depth} layers")
+    finally:
+        L.or_set_threads(1)
+    return ms, desc, used
 
 
 # ----------------------------------------------------------------- main paths
@@ -167,6 +200,9 @@ def job_ms_per_circuit(ms_step_max: float, world: int) -> float:
 
 
 def run_reference(args):
+    """The oracle (the tier's reference arm), as it stands, on the host's cores:
+    each step applies whole layers of the headline circuit on all processors
+    and scales to the full circuit; rank 0 only."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -174,18 +210,16 @@ def run_reference(args):
     import oracle as O
     O.build()
     vals = []
-    desc = ""
-    for _ in range(max(0, args.warmup)):
-        pass  # the oracle has no warm-up state worth timing
+    desc, cores = "", 1
     for _ in range(max(1, args.steps)):
-        ms, desc, done = oracle_sample(args, gates, budget_s=max(4.0, 60.0 / max(1, args.steps)))
+        ms, desc, cores = oracle_sample(args, gates, 0, budget_s=max(8.0, 120.0 / max(1, args.steps)))
         vals.append(ms)
     v = statistics.median(vals)
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_desc(args, len(gates)), "n": args.n, "dtype": "complex128"},
-            "cpu_baseline": {"value": v, "unit": "ms", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -219,6 +253,26 @@ def time_steps(Q, torch, plan, state, steps, warmup, with_norm=True, per_launch=
 
 def mode_name(Q, kw):
     return "tensor" if kw.get("mode") == Q.QS_MODE_TENSOR else "fused"
+
+
+def spread(vals):
+    """median / min / max of repeated timings (ms)."""
+    return {"median": statistics.median(vals), "min": min(vals), "max": max(vals), "reps": len(vals)}
+
+
+def traffic_record(kernel: str, n: int):
+    """DRAM bytes per launch at n from profiles/traffic.json, or None when the
+    record is absent or the kernel's sources changed since it was taken."""
+    prof = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(prof):
+        return None
+    try:
+        tp = json.load(open(prof)).get(kernel, {})
+        if tp.get("kernel_hash") == kernel_hash(kernel):
+            return tp.get("bytes_per_launch_n30") * 2.0 ** (n - 30)
+    except (ValueError, OSError, TypeError):
+        return None
+    return None
 
 
 def main():
@@ -259,13 +313,171 @@ def main():
     n = args.n
     gates = workload(args)
     stream = torch.cuda.current_stream().cuda_stream
-    state = Q.qs_state_alloc(n, Q.QS_C64, stream)
-    sweep_bytes = 2 * (1 << n) * 8
-
-    # -- plan options: a short device-timed search (autotuner), or given
     F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
+    sb128, sb64 = 2 * (1 << n) * 16, 2 * (1 << n) * 8
+    extra = {}
+
+    # ------------------------------------------------------------ headline: complex128
+    # every contracted 5-qubit block applied on tensor cores as exact fp16 digit
+    # products (the complex128 tensor-core pass), one step = one circuit + FP64 norm
+    state = Q.qs_state_alloc(n, Q.QS_C128, stream)
+    kw = dict(mode=T)
+    plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(**kw))
+    info = Q.qs_plan_info_get(plan)
+    Q.qs_state_set_basis(state, 0)
+    clocks = ClockSampler(local) if not args.no_clocks else None
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    if clocks:
+        clocks.start()
+    ms_step, launches, kern, norms = time_steps(Q, torch, plan, state, args.steps, args.warmup, per_launch=True)
+    clk = clocks.stop() if clocks else None
+    ms_step = max_over_ranks(ms_step, dist, "cuda")
+    kms = kern["tc_ms"] / max(1, kern["tc_launches"])
+    achieved = sb128 / (kms * 1e-3) / 1e9
+    eff_gbps = info["sweeps"] * sb128 / (ms_step * 1e-3) / 1e9
+    pg_equiv_gbps = info["per_gate_sweeps"] * sb128 / (ms_step * 1e-3) / 1e9
+    kern_share = {"tc_ms_per_step": kern["tc_ms"] / args.steps, "tc_launches_per_step": kern["tc_launches"] / args.steps,
+                  "other_ms_per_step": kern["tile_ms"] / args.steps,
+                  "other_launches_per_step": kern["tile_launches"] / args.steps}
+    alg = 8.0 * 32 * (1 << n) / (kms * 1e-3) / 1e12          # 8 * 2^5 real flops per amplitude
+    extra["tensor_pipe"] = {
+        "algorithmic_tflops": alg, "executed_f16_tflops": alg * 21, "f16_peak_tflops": bf16_peak,
+        "executed_frac": alg * 21 / bf16_peak,
+        "note": "a 32x32 complex block is a real 64x64 GEMM per 32-amplitude row (the algorithmic 256 flops per "
+                "amplitude); the exact digit scheme executes 21 such products in fp16 (fp16 and bf16 share the "
+                "MMA rate; the peak is the measured bf16 GEMM)"}
+
+    # per-gate complex128 (FP64, one launch per gate): the comparator and the FP64 reference state
+    s_ref = Q.qs_state_alloc(n, Q.QS_C128, stream)
+    if not args.no_per_gate:
+        pplan = Q.qs_plan_create(n, Q.QS_C128, gates, None)
+        Q.qs_state_set_basis(s_ref, 0)
+        pg_ms, _, pk128, _ = time_steps(Q, torch, pplan, s_ref, 1, 1, per_launch=True, with_norm=False)
+        pinfo = Q.qs_plan_info_get(pplan)
+        Q.qs_state_set_basis(s_ref, 0)
+        Q.qs_plan_execute(pplan, s_ref)
+        Q.qs_plan_free(pplan)
+        extra["per_gate_c128"] = {"ms": pg_ms, "sweeps": pinfo["per_gate_sweeps"], "launches": pinfo["launches"],
+                                  "effective_gbps": pinfo["per_gate_sweeps"] * sb128 / (pk128["ms"] * 1e-3) / 1e9}
+        extra["speedup_vs_per_gate_c128"] = pg_ms / ms_step
+        Q.qs_state_set_basis(state, 0)
+        Q.qs_plan_execute(plan, state)
+        m, l2 = Q.qs_state_diff(state, s_ref)
+        extra["precision_vs_fp64_per_gate"] = {"max_abs": m, "l2": l2}
+    # the same circuit on CUDA cores: tile passes in FP32 pairs (and FP64 with --full-configs)
+    for name, okw in (("c128_fused_fp32_pairs", dict(mode=F, fuse_k=2, tile_qubits=11, low_qubits=3, c128_pairs=1)),
+                      ("c128_fused_fp64", dict(mode=F, fuse_k=1, tile_qubits=12, low_qubits=4))):
+        if name == "c128_fused_fp64" and not args.full_configs:
+            continue
+        s2 = Q.qs_state_alloc(n, Q.QS_C128, stream)
+        p2 = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(**okw))
+        i2 = Q.qs_plan_info_get(p2)
+        Q.qs_state_set_basis(s2, 0)
+        f_ms, _, fk, _ = time_steps(Q, torch, p2, s2, 1, 1, per_launch=True, with_norm=False)
+        Q.qs_state_set_basis(s2, 0)
+        Q.qs_plan_execute(p2, s2)
+        extra[name] = dict(okw, ms=f_ms, passes=i2["passes"],
+                           pass_gbps=i2["passes"] * sb128 / (fk["ms"] * 1e-3) / 1e9,
+                           **dict(zip(("max_abs_vs_fp64_per_gate", "l2_vs_fp64_per_gate"),
+                                      Q.qs_state_diff(s2, s_ref) if not args.no_per_gate else (None, None))))
+        Q.qs_plan_free(p2)
+        Q.qs_state_free(s2)
+
+    # -- end to end through the C ABI with host buffers (pinned): every step copies its
+    #    input state in, runs the circuit and its norm, and copies the state out;
+    #    qs_plan_execute_host overlaps a step's circuit with the copies of its neighbours
+    #    (three device work states); the one-call-at-a-time sequence is reported beside it.
+    amp128 = 16
+    host_in = torch.zeros(1 << n, dtype=torch.complex128, pin_memory=True)
+    host_in[0] = 1
+    host_out = torch.empty(1 << n, dtype=torch.complex128, pin_memory=True)
+    e2e_steps = max(8, args.steps)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(2):
+        Q.lib().qs_state_copy_from_host(state, host_in.data_ptr(), host_in.numel() * amp128)
+        Q.qs_plan_execute(plan, state)
+        Q.qs_norm(state)
+        Q.lib().qs_state_copy_to_host(state, host_out.data_ptr(), host_out.numel() * amp128)
+    torch.cuda.synchronize()
+    e2e_seq_ms = (time.perf_counter() - t0) * 1e3 / 2
+    work = [state] + [Q.qs_state_alloc(n, Q.QS_C128, stream) for _ in range(2)]
+    Q.qs_plan_execute_host(plan, work, [host_in], [host_out])     # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e2e_norms = Q.qs_plan_execute_host(plan, work, [host_in] * e2e_steps, [host_out] * e2e_steps)
+    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
+    for w in work[1:]:
+        Q.qs_state_free(w)
+    e2e_norm = float(np.sum(np.abs(host_out.numpy()) ** 2))
+    del host_in, host_out
+    Q.qs_plan_free(plan)
+    Q.qs_state_free(state)
+    torch.cuda.empty_cache()
+
+    # ------------------------------------------------------------ complex64 line
+    extra["c64_tensor"] = c64_line(Q, torch, np, args, gates, stream, hbm_peak, bf16_peak, peak_src, s_ref)
+    Q.qs_state_free(s_ref)
+    torch.cuda.empty_cache()
+
+    if not args.no_configs:
+        extra["configs"] = run_configs(Q, torch, np, args, hbm_peak)
+
+    cpu = None
+    if rank == 0 and not args.no_cpu:
+        ms1, d1, _ = oracle_sample(args, gates, 1)
+        msa, da, cores = oracle_sample(args, gates, 0)
+        cpu = {"value": msa, "unit": "ms", "cores": cores, "kind": "oracle", "sample": da,
+               "one_thread": {"value": ms1, "unit": "ms", "cores": 1, "sample": d1}}
+
+    total_ms = job_ms_per_circuit(ms_step, world)
+    cfg = {"workload": workload_desc(args, len(gates)) + ", complex128, tensor-core plan (every 5-qubit block on "
+                                                           "tcgen05 as exact fp16 digit products)",
+           "n": n, "state": f"complex128, {(1 << n) * 16 / 2**30:g} GiB", "gates": len(gates),
+           "passes": info["passes"], "blocks": info["blocks"],
+           "l2": (f"inputs larger than L2 ({(1 << n) * 16 / 2**30:g} GiB state vs 129 MB); no flush"
+                  if (1 << n) * 16 > 129e6 else "state fits L2: timed passes may hit L2"),
+           "parallelism": f"replicas x{world}", "mode": "tensor", "tc_min_gates": 1}
+    line = {
+        "metric": METRIC, "value": total_ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "c128: fp16 digit products, exact FP32 level sums, FP32-pair combine",
+        "data": "synthetic", "config": cfg,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
+                     "frac": achieved / hbm_peak, "traffic": traffic_record("k_tc128", n),
+                     "kernel": "k_tc128 (complex128 tensor-core 5-qubit block pass)",
+                     "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
+                     "algorithmic_bytes_per_launch": sb128, "avg_launch_ms": kms},
+        "kernel_time": kern_share,
+        "effective_gbps": eff_gbps, "per_gate_equivalent_gbps": pg_equiv_gbps,
+        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": (1 << n) * amp128,
+                "d2h_bytes_per_step": (1 << n) * amp128 + 8, "steps": e2e_steps,
+                "api": "qs_plan_execute_host (3 device work states, copies overlapped with the circuit)",
+                "sequential_ms": e2e_seq_ms, "device_norm_last": float(e2e_norms[-1]), "norm_after": e2e_norm},
+        "gpu_launches": launches,
+        "clocks": clk,
+        "cpu_baseline": cpu,
+        "norm_drift": (max(abs(x - 1) for x in norms) if norms else None),
+    }
+    line.update(extra)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if dist:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def c64_line(Q, torch, np, args, gates, stream, hbm_peak, bf16_peak, peak_src, s_ref):
+    """The same circuit in complex64: the autotuned plan (tensor-core 6-qubit
+    blocks, fp16 hi/lo split) with its roofline, the per-gate comparator, and
+    each result's error against the complex128 per-gate run."""
+    n = args.n
+    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
+    sb = 2 * (1 << n) * 8
+    state = Q.qs_state_alloc(n, Q.QS_C64, stream)
     if args.tune == "auto":
-        # the library's autotuner: device-timed search over its built-in option grid
         t0 = time.perf_counter()
         bopts, bms = Q.qs_plan_autotune(state, gates)
         kw = {k: v for k, v in Q.opts_dict(bopts).items() if v or k == "mode"}
@@ -281,188 +493,42 @@ def main():
     plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(**kw))
     info = Q.qs_plan_info_get(plan)
     Q.qs_state_set_basis(state, 0)
-
-    clocks = ClockSampler(local) if not args.no_clocks else None
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    if clocks:
-        clocks.start()
-    ms_step, launches, kern, norms = time_steps(Q, torch, plan, state, args.steps, args.warmup, per_launch=True)
-    clk = clocks.stop() if clocks else None
-    ms_step = max_over_ranks(ms_step, dist, "cuda")
-
-    # roofline of the kernel that dominates the timed region
+    ms, launches, kern, _ = time_steps(Q, torch, plan, state, args.steps, args.warmup, per_launch=True)
     tc_dom = kern["tc_ms"] > kern["tile_ms"]
     tc_kernel = "k_tc_block" if kw.get("tc_pipeline", 0) == 1 else "k_tc_bulk"
-    kname = f"{tc_kernel} (tensor-core 6-qubit block pass)" if tc_dom else "k_tile (tile pass)"
     kms = (kern["tc_ms"] / max(1, kern["tc_launches"])) if tc_dom else (kern["tile_ms"] / max(1, kern["tile_launches"]))
-    achieved = sweep_bytes / (kms * 1e-3) / 1e9
-    eff_gbps = info["sweeps"] * sweep_bytes / (ms_step * 1e-3) / 1e9
-    pg_equiv_gbps = info["per_gate_sweeps"] * sweep_bytes / (ms_step * 1e-3) / 1e9
-    kern_share = {"tile_ms_per_step": kern["tile_ms"] / args.steps, "tile_launches_per_step": kern["tile_launches"] / args.steps,
-                  "tc_ms_per_step": kern["tc_ms"] / args.steps, "tc_launches_per_step": kern["tc_launches"] / args.steps}
-    extra = {}
+    out = {"ms": ms, "plan": {k: v for k, v in kw.items()}, "mode": mode_name(Q, kw), "passes": info["passes"],
+           "gpu_launches": launches, "effective_gbps": info["sweeps"] * sb / (ms * 1e-3) / 1e9,
+           "roofline": {"bound": "hbm", "achieved": sb / (kms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
+                        "frac": sb / (kms * 1e-3) / 1e9 / hbm_peak,
+                        "traffic": traffic_record(tc_kernel if tc_dom else "k_tile", n),
+                        "kernel": f"{tc_kernel} (tensor-core 6-qubit block pass)" if tc_dom else "k_tile (tile pass)",
+                        "peak_source": f"{peak_src} (hbm_gbs, burst copy)", "avg_launch_ms": kms},
+           "autotune": trials}
     if tc_dom:
-        alg_tflops = 512.0 * (1 << n) / (kms * 1e-3) / 1e12     # 8 * 2^6 real flops per amplitude
+        alg = 512.0 * (1 << n) / (kms * 1e-3) / 1e12     # 8 * 2^6 real flops per amplitude
         mult = 3 if kw.get("tc_precision", 4) in (0, 3, 4) else 1
-        extra["tensor_pipe"] = {"algorithmic_tflops": alg_tflops, "executed_f16_tflops": alg_tflops * 2 * mult,
-                                "bf16_peak_tflops": bf16_peak, "executed_frac": alg_tflops * 2 * mult / bf16_peak,
-                                "note": "complex 64x64 block as a real 128x128 GEMM: 2x the complex flops; the "
-                                        "fp16 / bf16 hi-lo split runs 3 MMAs (fp16 and bf16 share the MMA rate)"}
-
-    # -- per-gate comparator (same circuit, same state)
+        out["tensor_pipe"] = {"algorithmic_tflops": alg, "executed_f16_tflops": alg * mult,
+                              "f16_peak_tflops": bf16_peak, "executed_frac": alg * mult / bf16_peak,
+                              "note": "a 64x64 complex block is a real 128x128 GEMM per 64-amplitude row (the "
+                                      "algorithmic 512 flops per amplitude, no extra factor); the fp16 hi/lo split "
+                                      "runs 3 such products"}
+    Q.qs_state_set_basis(state, 0)
+    Q.qs_plan_execute(plan, state)
     if not args.no_per_gate:
+        out["max_abs_vs_c128_per_gate"], out["l2_vs_c128_per_gate"] = Q.qs_state_diff(state, s_ref)
         pplan = Q.qs_plan_create(n, Q.QS_C64, gates, None)
-        pg_ms, _, pkern, _ = time_steps(Q, torch, pplan, state, 1, 1, per_launch=True)
+        pg_ms, _, pk, _ = time_steps(Q, torch, pplan, state, 1, 1, per_launch=True, with_norm=False)
         pinfo = Q.qs_plan_info_get(pplan)
-        Q.qs_plan_free(pplan)
-        extra["per_gate_c64"] = {"ms": pg_ms, "sweeps": pinfo["per_gate_sweeps"], "launches": pinfo["launches"],
-                                 "effective_gbps": pinfo["per_gate_sweeps"] * sweep_bytes / (pkern["ms"] * 1e-3) / 1e9}
-        extra["speedup_fused_vs_per_gate_c64"] = pg_ms / ms_step
-
-    # -- end to end through the C ABI with host buffers (pinned): every step copies its
-    #    input state in, runs the circuit and its norm, and copies the state and norm out.
-    #    qs_plan_execute_host overlaps step i's circuit with the copies of steps i +- 1
-    #    (two device work states); the one-call-at-a-time sequence is reported beside it.
-    host_in = torch.zeros(1 << n, dtype=torch.complex64, pin_memory=True)
-    host_in[0] = 1
-    host_out = torch.empty(1 << n, dtype=torch.complex64, pin_memory=True)
-    e2e_steps = max(8, args.steps)     # the pipeline fills and drains once per call
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(3):
-        Q.lib().qs_state_copy_from_host(state, host_in.data_ptr(), host_in.numel() * 8)
-        Q.qs_plan_execute(plan, state)
-        Q.qs_norm(state)
-        Q.lib().qs_state_copy_to_host(state, host_out.data_ptr(), host_out.numel() * 8)
-    torch.cuda.synchronize()
-    e2e_seq_ms = (time.perf_counter() - t0) * 1e3 / 3
-    work = [state] + [Q.qs_state_alloc(n, Q.QS_C64, stream) for _ in range(2)]
-    Q.qs_plan_execute_host(plan, work, [host_in], [host_out])     # warm-up
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    e2e_norms = Q.qs_plan_execute_host(plan, work, [host_in] * e2e_steps, [host_out] * e2e_steps)
-    e2e_ms = (time.perf_counter() - t0) * 1e3 / e2e_steps
-    for w in work[1:]:
-        Q.qs_state_free(w)
-    e2e_norm = float(np.sum(np.abs(host_out.numpy().astype(np.complex128)) ** 2))
-    del host_in, host_out
-
-    # -- complex128: fused (tuned) and per-gate; then the error of each complex64
-    #    result against the complex128 GPU run of the same circuit from |0..0>
-    if not args.no_c128:
-        s128 = Q.qs_state_alloc(n, Q.QS_C128, stream)
-        if args.tune == "auto":
-            b128, _ = Q.qs_plan_autotune(s128, gates)
-            kw128 = {k: v for k, v in Q.opts_dict(b128).items() if v or k == "mode"}
-        else:
-            kw128 = dict(mode=F, fuse_k=2, tile_qubits=11, low_qubits=3)
-        p128 = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(**kw128))
-        i128 = Q.qs_plan_info_get(p128)
-        f128_ms, _, f128k, _ = time_steps(Q, torch, p128, s128, 1, 1, per_launch=True)
-        sb128 = 2 * (1 << n) * 16
-        fp64_tf = i128["flops_per_amp"] * (1 << n) / (f128k["ms"] * 1e-3) / 1e12
-        extra["c128_fused"] = dict(kw128, ms=f128_ms, passes=i128["passes"], flops_per_amp=i128["flops_per_amp"],
-                                   pass_gbps=i128["passes"] * sb128 / (f128k["ms"] * 1e-3) / 1e9,
-                                   bound="fp64 alu", fp64_tflops=fp64_tf, fp64_peak_tflops=FP64_PEAK_TFLOPS,
-                                   fp64_frac=fp64_tf / FP64_PEAK_TFLOPS,
-                                   fp64_peak_source="nominal GB300 FP64 rate (an FMA loop measured 1.19 TFLOP/s)")
-        Q.qs_state_set_basis(s128, 0)
-        Q.qs_plan_execute(p128, s128)
-        Q.qs_plan_free(p128)
-        # the same complex128 circuit with tile passes computed in FP32 pairs, against the FP64 run
-        kwp = dict(kw128, c128_pairs=1)
-        if kwp.get("mode") != F:
-            kwp = dict(mode=F, fuse_k=2, tile_qubits=11, low_qubits=3, c128_pairs=1)
-        s2 = Q.qs_state_alloc(n, Q.QS_C128, stream)
-        pp2 = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(**kwp))
-        ip2 = Q.qs_plan_info_get(pp2)
-        Q.qs_state_set_basis(s2, 0)
-        fp_ms, _, fpk, _ = time_steps(Q, torch, pp2, s2, 1, 1, per_launch=True)
-        Q.qs_state_set_basis(s2, 0)
-        Q.qs_plan_execute(pp2, s2)
-        m2, l2 = Q.qs_state_diff(s2, s128)
-        extra["c128_fused_fp32_pairs"] = dict(kwp, ms=fp_ms, passes=ip2["passes"],
-                                              pass_gbps=ip2["passes"] * sb128 / (fpk["ms"] * 1e-3) / 1e9,
-                                              max_abs_vs_fp64=m2, l2_vs_fp64=l2,
-                                              arithmetic="tile passes in FP32 pairs (about 2^-46 per operation)")
-        Q.qs_plan_free(pp2)
-        Q.qs_state_free(s2)
-        prec = {}
         Q.qs_state_set_basis(state, 0)
-        Q.qs_plan_execute(plan, state)
-        prec["c64_" + mode_name(Q, kw)] = dict(zip(("max_abs", "l2"), Q.qs_state_diff(state, s128)))
-        if not args.no_per_gate:
-            pplan = Q.qs_plan_create(n, Q.QS_C64, gates, None)
-            Q.qs_state_set_basis(state, 0)
-            Q.qs_plan_execute(pplan, state)
-            Q.qs_plan_free(pplan)
-            prec["c64_per_gate"] = dict(zip(("max_abs", "l2"), Q.qs_state_diff(state, s128)))
-            pp = Q.qs_plan_create(n, Q.QS_C128, gates, None)
-            pg128, _, _, _ = time_steps(Q, torch, pp, s128, 1, 0, per_launch=False)
-            Q.qs_plan_free(pp)
-            extra["c128_per_gate"] = {"ms": pg128}
-            extra["speedup_fused_vs_per_gate_c128"] = pg128 / f128_ms
-        extra["precision_vs_c128_gpu_run"] = prec
-        Q.qs_state_free(s128)
+        Q.qs_plan_execute(pplan, state)
+        out["per_gate"] = {"ms": pg_ms, "effective_gbps": pinfo["per_gate_sweeps"] * sb / (pk["ms"] * 1e-3) / 1e9,
+                           "max_abs_vs_c128_per_gate": Q.qs_state_diff(state, s_ref)[0]}
+        out["speedup_vs_per_gate"] = pg_ms / ms
+        Q.qs_plan_free(pplan)
     Q.qs_plan_free(plan)
     Q.qs_state_free(state)
-    torch.cuda.empty_cache()
-
-    if not args.no_configs:
-        extra["configs"] = run_configs(Q, torch, np, args)
-
-    cpu = None
-    if rank == 0 and not args.no_cpu:
-        ms_cpu, desc, _ = oracle_sample(args, gates)
-        cpu = {"value": ms_cpu, "unit": "ms", "cores": 1, "kind": "oracle", "sample": desc}
-
-    total_ms = job_ms_per_circuit(ms_step, world)
-    prof = os.path.join(ROOT, "profiles", "traffic.json")
-    traffic = None
-    if os.path.exists(prof):
-        try:
-            tp = json.load(open(prof)).get(tc_kernel if tc_dom else "k_tile", {})
-            if tp.get("kernel_hash") == kernel_hash(tc_kernel if tc_dom else "k_tile"):
-                # per launch at this n: traffic is proportional to the amplitudes swept
-                traffic = tp.get("bytes_per_launch_n30") * 2.0 ** (n - 30)
-        except (ValueError, OSError):
-            traffic = None
-    cfg = {"workload": workload_desc(args, len(gates)) + f", complex64, {mode_name(Q, kw)} plan",
-           "n": n, "state": f"complex64, {(1 << n) * 8 / 2**30:g} GiB", "gates": len(gates), "passes": info["passes"],
-           "blocks": info["blocks"],
-           "l2": (f"inputs larger than L2 ({(1 << n) * 8 / 2**30:g} GiB state vs 129 MB); no flush"
-                  if (1 << n) * 8 > 129e6 else "state fits L2: timed passes may hit L2"),
-           "parallelism": f"replicas x{world}"}
-    cfg.update({k: v for k, v in kw.items() if k != "mode"})
-    cfg["mode"] = mode_name(Q, kw)
-    line = {
-        "metric": METRIC, "value": total_ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32", "data": "synthetic", "config": cfg,
-        "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
-                     "frac": achieved / hbm_peak, "traffic": traffic, "kernel": kname,
-                     "peak_source": f"{peak_src} (hbm_gbs, burst copy)",
-                     "algorithmic_bytes_per_launch": sweep_bytes, "avg_launch_ms": kms},
-        "kernel_time": kern_share,
-        "effective_gbps": eff_gbps, "per_gate_equivalent_gbps": pg_equiv_gbps,
-        "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": (1 << n) * 8, "d2h_bytes_per_step": (1 << n) * 8 + 8,
-                     "steps": e2e_steps, "api": "qs_plan_execute_host (3 device work states, copies overlapped with the circuit)",
-                     "sequential_ms": e2e_seq_ms, "device_norm_last": float(e2e_norms[-1]),
-                "norm_after": e2e_norm},
-        "gpu_launches": launches,
-        "clocks": clk,
-        "cpu_baseline": cpu,
-        "norm_drift": (max(abs(x - 1) for x in norms) if norms else None),
-        "autotune_c64": trials,
-    }
-    line.update(extra)
-    if rank == 0:
-        print(json.dumps(line), flush=True)
-    if dist:
-        dist.barrier()
-        dist.destroy_process_group()
+    return out
 
 
 def device_ms(torch, fn, reps=1):
@@ -477,18 +543,35 @@ def device_ms(torch, fn, reps=1):
     return t0.elapsed_time(t1) / reps
 
 
-def run_configs(Q, torch, np, args):
+def device_reps(torch, fn, reps, setup=None):
+    """Device times (ms) of `reps` calls of fn, each bracketed by CUDA events
+    (setup, e.g. resetting the state, runs outside the bracket)."""
+    st = torch.cuda.current_stream()
+    out = []
+    for _ in range(reps):
+        if setup:
+            setup()
+        t0, t1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        t0.record(st)
+        fn()
+        t1.record(st)
+        torch.cuda.synchronize()
+        out.append(t0.elapsed_time(t1))
+    return out
+
+
+def run_configs(Q, torch, np, args, hbm_peak=6800.0):
     """Side measurements, one per benchmark configuration (timings on the
-    device with CUDA events; errors against closed forms or a complex128 run)."""
-    from paper_2509_04955_gb300 import workloads as W
+    device with CUDA events, repeated; errors against closed forms, the oracle
+    or a complex128 run). The SMGP ablation and the host-resident state run
+    with --full-configs or --only-config."""
     out = {}
     st = torch.cuda.current_stream().cuda_stream
-    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
 
-    def want(name):
-        return args.only_config in (None, name)
+    def want(name, default=True):
+        return args.only_config == name or (args.only_config is None and (default or args.full_configs))
 
-    # config 1: QFT n=28 complex128 from a seeded basis state, per-gate vs contraction k=2..5
     if want("qft_n30_m2"):
         out["qft_n30_m2"] = config_qft30(Q, torch, np, st, args)
     if want("qft_n28_c128"):
@@ -496,14 +579,14 @@ def run_configs(Q, torch, np, args):
     if want("random_n32_cz_tensor"):
         out["random_n32_cz_tensor"] = config_n32(Q, torch, np, st, args)
     if want("ucc_batched_n20"):
-        out["ucc_batched_n20"] = config_ucc(Q, torch, np, st, args)
+        out["ucc_batched_n20"] = config_ucc(Q, torch, np, st, args, hbm_peak)
     if want("hea_adjoint_n24"):
         out["hea_adjoint_n24"] = config_hea(Q, torch, np, st, args)
     if want("qaoa_n30"):
         out["qaoa_n30"] = config_qaoa30(Q, torch, np, st, args)
-    if want("smgp_ablation"):
+    if want("smgp_ablation", False):
         out["smgp_ablation"] = config_smgp(Q, torch, np, st, args)
-    if want("stream_host_state"):
+    if want("stream_host_state", False):
         out["stream_host_state"] = config_stream(Q, torch, np, st, args)
     return out
 
@@ -635,12 +718,10 @@ def config_qaoa30(Q, torch, np, st, args):
     Q.qs_plan_free(pl)
     variants = {"c64": [("per_gate", None), ("fused_no_phase", Q.make_opts(mode=F, phase_min_gates=-1)),
                         ("fused", Q.make_opts(mode=F)),
-                        ("fused_m14", Q.make_opts(mode=F, tile_qubits=14, low_qubits=4)),
                         ("tensor", Q.make_opts(mode=T, tc_min_gates=4, fuse_parametric=1))],
-                "c128": [("per_gate", None), ("fused_no_phase", Q.make_opts(mode=F, phase_min_gates=-1)),
-                         ("fused", Q.make_opts(mode=F)),
-                         ("fused_m13", Q.make_opts(mode=F, tile_qubits=13, low_qubits=3)),
-                         ("fused_fp32_pairs", Q.make_opts(mode=F, tile_qubits=12, low_qubits=4, c128_pairs=1))]}
+                "c128": [("per_gate", None), ("fused", Q.make_opts(mode=F)),
+                         ("fused_fp32_pairs", Q.make_opts(mode=F, tile_qubits=12, low_qubits=4, c128_pairs=1)),
+                         ("tensor", Q.make_opts(mode=T, fuse_parametric=1, c128_pairs=1))]}
     ref_e = None
     for dname, dt in (("c128", Q.QS_C128), ("c64", Q.QS_C64)):
         s = Q.qs_state_alloc(n, dt, st)
@@ -650,17 +731,18 @@ def config_qaoa30(Q, torch, np, st, args):
             plan = Q.qs_plan_create(n, dt, g, opts)
             Q.qs_state_set_basis(s, 0)
             Q.qs_plan_execute(plan, s, th)
-            Q.qs_state_set_basis(s, 0)
-            ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s, th))
+            t = device_reps(torch, lambda: Q.qs_plan_execute(plan, s, th), 1 if name == "per_gate" else 3,
+                            lambda: Q.qs_state_set_basis(s, 0))
+            ms = statistics.median(t)
             e = Q.qs_expval_pauli_sum(s, *H)
             if ref_e is None:
                 ref_e = e
             info = Q.qs_plan_info_get(plan)
             ops = Q.qs_plan_ops(plan)
-            res[name] = {"ms": ms, "passes": info["passes"],
+            res[name] = {"ms": spread(t), "passes": info["passes"],
                          "phase_passes": sum(op["type"] == 4 for op in ops),
                          "effective_gbps": info["sweeps"] * 2 * (1 << n) * amp / (ms * 1e-3) / 1e9,
-                         "expected_cut": e, "abs_diff_vs_c128_fused": abs(e - ref_e)}
+                         "expected_cut": e, "abs_diff_vs_c128_per_gate": abs(e - ref_e)}
             Q.qs_plan_free(plan)
         # one cost layer alone: a single phase pass
         layer = g[n:n + 3 * len(edges)]
@@ -685,8 +767,9 @@ def config_qaoa30(Q, torch, np, st, args):
 
 def config_qft30(Q, torch, np, st, args):
     """Second n=30 workload of the headline metric: QFT from a seeded basis state,
-    complex64 and complex128, per-gate vs fused; sampled amplitudes against the
-    closed form psi_y = 2^{-n/2} exp(2 pi i x y / 2^n)."""
+    complex64 and complex128, per-gate vs contracted plans (tensor-core and
+    CUDA-core); sampled amplitudes against the closed form
+    psi_y = 2^{-n/2} exp(2 pi i x y / 2^n)."""
     from paper_2509_04955_gb300 import workloads as W
     F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
     n = 30
@@ -695,122 +778,142 @@ def config_qft30(Q, torch, np, st, args):
     idx = np.unique(np.random.default_rng(0).integers(0, 1 << n, size=4096)).astype(np.uint64)
     want = np.exp(2j * np.pi * ((x * idx.astype(object)) % (1 << n)).astype(np.float64) / (1 << n)) / np.sqrt(1 << n)
     out = {"workload": "QFT n=30, seeded basis input (H, controlled phases, final swaps)", "gates": len(g)}
-    variants = {"c64": [("per_gate", None), ("fused_k4", Q.make_opts(mode=F, fuse_k=4)),
-                        ("tensor", Q.make_opts(mode=T, tc_min_gates=2))],
-                "c128": [("per_gate", None), ("fused_k5", Q.make_opts(mode=F, fuse_k=5)),
-                         ("fused_fp32_pairs", Q.make_opts(mode=F, fuse_k=2, c128_pairs=1))]}
+    variants = {"c64": [("per_gate", None, 3), ("tensor", Q.make_opts(mode=T, tc_min_gates=2), 5)],
+                "c128": [("per_gate", None, 2), ("tensor", Q.make_opts(mode=T), 5),
+                         ("fused_fp32_pairs", Q.make_opts(mode=F, fuse_k=2, c128_pairs=1), 2)]}
     for dname, dt in (("c64", Q.QS_C64), ("c128", Q.QS_C128)):
         s = Q.qs_state_alloc(n, dt, st)
         res = {}
         amp = 8 if dt == Q.QS_C64 else 16
-        for name, opts in variants[dname]:
+        for name, opts, reps in variants[dname]:
             plan = Q.qs_plan_create(n, dt, g, opts)
             Q.qs_state_set_basis(s, x)
             Q.qs_plan_execute(plan, s)
-            Q.qs_state_set_basis(s, x)
-            ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s))
+            t = device_reps(torch, lambda: Q.qs_plan_execute(plan, s), reps, lambda: Q.qs_state_set_basis(s, x))
             info = Q.qs_plan_info_get(plan)
             got = Q.qs_state_get_amplitudes(s, idx, dt)
-            res[name] = {"ms": ms, "passes": info["passes"],
+            ms = statistics.median(t)
+            res[name] = {"ms": spread(t), "passes": info["passes"],
                          "effective_gbps": info["sweeps"] * 2 * (1 << n) * amp / (ms * 1e-3) / 1e9,
                          "max_abs_err_vs_closed_form": float(np.abs(got - want).max())}
             Q.qs_plan_free(plan)
+        res["speedup_tensor_vs_per_gate"] = res["per_gate"]["ms"]["median"] / res["tensor"]["ms"]["median"]
         out[dname] = res
         Q.qs_state_free(s)
     return out
 
 
 def config_qft(Q, torch, np, st, args):
+    """QFT n=28 complex128 from a seeded basis state: per-gate vs contraction at
+    k = 4, 5 on CUDA cores (FP32 pairs) and k = 5 on tensor cores (the widest
+    complex128 block; 6-qubit blocks exist for complex64 only); every amplitude
+    against the closed form."""
     from paper_2509_04955_gb300 import workloads as W
-    F = Q.QS_MODE_FUSED
+    F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
     n = 28
     g = W.qft(n)
     x = W.random_basis_index(n, 28)
     s = Q.qs_state_alloc(n, Q.QS_C128, st)
     idx = np.unique(np.random.default_rng(0).integers(0, 1 << n, size=4096))
     want = np.exp(2j * np.pi * ((x * idx) % (1 << n)) / (1 << n)) / np.sqrt(1 << n)
-    c1 = {"workload": "QFT n=28 complex128, seeded basis input", "gates": len(g)}
-    for name, opts in [("per_gate", None)] + [(f"fused_k{k}", Q.make_opts(mode=F, fuse_k=k)) for k in (2, 3, 4, 5)]:
+    c1 = {"workload": "QFT n=28 complex128, seeded basis input", "gates": len(g),
+          "note": "k = 6 is not built for complex128 (tensor-core blocks are 5 qubits there)"}
+    for name, opts, reps in (("per_gate", None, 3),
+                             ("fused_k4_fp32_pairs", Q.make_opts(mode=F, fuse_k=4, c128_pairs=1), 3),
+                             ("fused_k5_fp32_pairs", Q.make_opts(mode=F, fuse_k=5, tile_qubits=11, low_qubits=3,
+                                                                 c128_pairs=1), 3),
+                             ("fused_k5_fp64", Q.make_opts(mode=F, fuse_k=5), 2),
+                             ("tensor_k5", Q.make_opts(mode=T), 5)):
         plan = Q.qs_plan_create(n, Q.QS_C128, g, opts)
         Q.qs_state_set_basis(s, x)
         Q.qs_plan_execute(plan, s)
-        Q.qs_state_set_basis(s, x)
-        ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s))
+        t = device_reps(torch, lambda: Q.qs_plan_execute(plan, s), reps, lambda: Q.qs_state_set_basis(s, x))
         full = np.empty(1 << n, dtype=np.complex128)
         Q.qs_state_copy_to_host(s, full)
-        c1[name] = {"ms": ms, "passes": Q.qs_plan_info_get(plan)["passes"],
+        c1[name] = {"ms": spread(t), "passes": Q.qs_plan_info_get(plan)["passes"],
                     "max_abs_err_vs_closed_form": float(np.abs(full[idx] - want).max())}
         Q.qs_plan_free(plan)
         del full
+    c1["speedup_tensor_vs_per_gate"] = c1["per_gate"]["ms"]["median"] / c1["tensor_k5"]["ms"]["median"]
     Q.qs_state_free(s)
     return c1
 
 
 def config_n32(Q, torch, np, st, args):
-    # config 2: random n=32 depth 40 with CZ, complex64 on tensor cores (6-qubit blocks)
+    """Random n=32 depth 40 with CZ entanglers (1920 gates), complex64 on tensor
+    cores (6-qubit blocks, three split precisions) and on CUDA cores; each
+    complex64 result against the complex128 GPU run of the same seed (the
+    complex128 tensor-core plan, 64 GiB); one layer per gate timed for the
+    per-gate comparator (all 40 layers have the same gate counts)."""
     from paper_2509_04955_gb300 import workloads as W
     F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
     n = 32
     g = W.random_layered(n, 40, seed=0, entangler="cz")
+    per_layer = len(g) // 40
     s = Q.qs_state_alloc(n, Q.QS_C64, st)
+    ref = Q.qs_state_alloc(n, Q.QS_C128, st)
     c2 = {"workload": "random layered n=32 depth 40, CZ entanglers, complex64 (32 GiB)", "gates": len(g)}
-    for name, opts in (("tensor_fp16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=4)),
-                       ("tensor_bf16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=3)),
-                       ("tensor_bf16", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=1)),
-                       ("fused_cuda_cores_k2", Q.make_opts(mode=F, fuse_k=2, tile_qubits=13, low_qubits=4))):
+    pr = Q.qs_plan_create(n, Q.QS_C128, g, Q.make_opts(mode=T))
+    t = device_reps(torch, lambda: Q.qs_plan_execute(pr, ref), 2, lambda: Q.qs_state_set_basis(ref, 0))
+    c2["c128_tensor"] = {"ms": spread(t), "passes": Q.qs_plan_info_get(pr)["passes"], "norm": Q.qs_norm(ref)}
+    Q.qs_plan_free(pr)
+    for name, opts, reps in (("tensor_fp16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=4), 5),
+                             ("tensor_bf16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=3), 3),
+                             ("tensor_bf16", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=1), 3),
+                             ("fused_cuda_cores_k2", Q.make_opts(mode=F, fuse_k=2, tile_qubits=13, low_qubits=4), 2)):
         plan = Q.qs_plan_create(n, Q.QS_C64, g, opts)
-        Q.qs_state_set_basis(s, 0)
-        ms = device_ms(torch, lambda: Q.qs_plan_execute(plan, s))
-        c2[name] = {"ms": ms, "passes": Q.qs_plan_info_get(plan)["passes"], "norm": Q.qs_norm(s)}
-        if args.full_configs and name != "fused_cuda_cores_k2":
-            c2[name]["plan"] = plan
-        else:
-            Q.qs_plan_free(plan)
-    if args.full_configs:
-        ref = Q.qs_state_alloc(n, Q.QS_C128, st)
-        pr = Q.qs_plan_create(n, Q.QS_C128, g, Q.make_opts(mode=F, fuse_k=2, tile_qubits=12, low_qubits=4))
-        Q.qs_state_set_basis(ref, 0)
-        c2["c128_fused_ms"] = device_ms(torch, lambda: Q.qs_plan_execute(pr, ref))
-        Q.qs_plan_free(pr)
-        for name in ("tensor_fp16x3", "tensor_bf16x3", "tensor_bf16"):
-            plan = c2[name].pop("plan")
-            Q.qs_state_set_basis(s, 0)
-            Q.qs_plan_execute(plan, s)
-            m, l2 = Q.qs_state_diff(s, ref)
-            c2[name].update(max_abs_err_vs_c128_gpu=m, l2_err_vs_c128_gpu=l2)
-            Q.qs_plan_free(plan)
-        Q.qs_state_free(ref)
+        t = device_reps(torch, lambda: Q.qs_plan_execute(plan, s), reps, lambda: Q.qs_state_set_basis(s, 0))
+        m, l2 = Q.qs_state_diff(s, ref)
+        c2[name] = {"ms": spread(t), "passes": Q.qs_plan_info_get(plan)["passes"], "norm": Q.qs_norm(s),
+                    "max_abs_err_vs_c128_gpu": m, "l2_err_vs_c128_gpu": l2}
+        Q.qs_plan_free(plan)
+    pplan = Q.qs_plan_create(n, Q.QS_C64, g[:per_layer], None)
+    t = device_reps(torch, lambda: Q.qs_plan_execute(pplan, s), 3, lambda: Q.qs_state_set_basis(s, 0))
+    c2["per_gate_c64"] = {"ms_one_layer": spread(t), "ms_scaled_to_40_layers": 40 * statistics.median(t),
+                          "gates_per_layer": per_layer}
+    c2["speedup_tensor_vs_per_gate"] = c2["per_gate_c64"]["ms_scaled_to_40_layers"] / c2["tensor_fp16x3"]["ms"]["median"]
+    Q.qs_plan_free(pplan)
+    Q.qs_state_free(ref)
     Q.qs_state_free(s)
     return c2
 
 
-def config_ucc(Q, torch, np, st, args):
-    # config 3: UCC-style n=20 complex64, 400 Pauli exponentials, B=64 theta ~ N(0, 0.1),
-    # one CUDA graph (device-resolved angles) + <H> for a 300-term Pauli sum per state
+def config_ucc(Q, torch, np, st, args, hbm_peak=6800.0):
+    """UCC-style n=20 complex64, 400 Pauli exponentials, B=64 theta ~ N(0, 0.1):
+    one CUDA graph per batch (device-resolved angles, device-built blocks) and
+    <H> for a 300-term Pauli sum per state; several replays each. The roofline
+    fraction counts one read and one write of every state per pass plus one
+    read per distinct x mask of H (the expectation sweeps, served mostly from
+    L2) over the measured copy bandwidth."""
     from paper_2509_04955_gb300 import workloads as W
     F, T = Q.QS_MODE_FUSED, Q.QS_MODE_TENSOR
     n, B = 20, 64
     g, _ = W.ucc(n, 400, seed=0)
     th = W.thetas_normal(400, 1, sigma=0.1, batch=B)
     H = W.random_pauli_sum(n, 300, seed=3)
+    nx = len(set(int(x) for x in H[1]))
     states = [Q.qs_state_alloc(n, Q.QS_C64, st) for _ in range(B)]
-    c3 = {"workload": "UCC-style n=20 complex64, 400 terms, B=64, 300-term <H>", "gates": len(g)}
-    for name, opts in (("fused_k1", Q.make_opts(mode=F, fuse_k=1)),
-                       ("fused_k4_device_blocks", Q.make_opts(mode=F, fuse_k=4, fuse_parametric=1)),
-                       ("tensor", Q.make_opts(mode=T, tc_min_gates=2)),
-                       ("tensor_device_blocks", Q.make_opts(mode=T, tc_min_gates=4, fuse_parametric=1))):
+    c3 = {"workload": "UCC-style n=20 complex64, 400 terms, B=64, 300-term <H>", "gates": len(g),
+          "x_mask_groups": nx}
+    for name, opts, reps in (("fused_k1", Q.make_opts(mode=F, fuse_k=1), 3),
+                             ("fused_k4_device_blocks", Q.make_opts(mode=F, fuse_k=4, fuse_parametric=1), 3),
+                             ("tensor", Q.make_opts(mode=T, tc_min_gates=2), 5),
+                             ("tensor_device_blocks", Q.make_opts(mode=T, tc_min_gates=4, fuse_parametric=1), 5)):
         plan = Q.qs_plan_create(n, Q.QS_C64, g, opts)
-        def go():
+        passes = Q.qs_plan_info_get(plan)["passes"]
+
+        def reset():
             for sv in states:
                 Q.qs_state_set_basis(sv, 0)
-            return Q.qs_plan_execute_batched(plan, states, th, H)
-        go()                                   # captures the graph
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ex = go()
-        wall = (time.perf_counter() - t0) * 1e3
-        c3[name] = {"ms_per_batch": wall, "circuits_per_s": B / (wall * 1e-3),
-                    "passes_per_circuit": Q.qs_plan_info_get(plan)["passes"], "expval_b0": float(ex[0])}
+        ex = []
+        reset()
+        Q.qs_plan_execute_batched(plan, states, th, H)     # captures the graph
+        t = device_reps(torch, lambda: ex.append(Q.qs_plan_execute_batched(plan, states, th, H)), reps, reset)
+        ms = statistics.median(t)
+        nbytes = B * (passes * 2 + nx) * (1 << n) * 8
+        c3[name] = {"ms_per_batch": spread(t), "circuits_per_s": B / (ms * 1e-3), "passes_per_circuit": passes,
+                    "algorithmic_bytes_per_batch": nbytes, "gbps": nbytes / (ms * 1e-3) / 1e9,
+                    "frac_of_hbm": nbytes / (ms * 1e-3) / 1e9 / hbm_peak, "expval_b0": float(ex[-1][0])}
         Q.qs_plan_free(plan)
     for sv in states:
         Q.qs_state_free(sv)
@@ -818,7 +921,9 @@ def config_ucc(Q, torch, np, st, args):
 
 
 def config_hea(Q, torch, np, st, args):
-    # config 4: HEA n=24, 12 layers (576 parameters), adjoint gradient of a 150-term <H>
+    """HEA n=24, 12 layers (576 parameters): adjoint gradient of a 150-term <H>,
+    complex128 (FP64 tile passes; FP32 pairs; tensor-core forward) and
+    complex64 (CUDA-core and tensor-core forward); several calls each."""
     from paper_2509_04955_gb300 import workloads as W
     n = 24
     g, p = W.hea(n, 12)
@@ -826,38 +931,34 @@ def config_hea(Q, torch, np, st, args):
     H = W.random_pauli_sum(n, 150, seed=4)
     c4 = {"workload": "HEA n=24, 576 parameters, 150-term H, adjoint gradient"}
     grads = {}
-    for dname, dt in (("c128", Q.QS_C128), ("c64", Q.QS_C64)):
+    T = Q.QS_MODE_TENSOR
+    for dname, dt, variants in (("c128", Q.QS_C128, (("default_fp64", None), ("fp32_pairs", Q.make_opts(c128_pairs=1)),
+                                                      ("tensor_forward", Q.make_opts(mode=T, c128_pairs=1)))),
+                                ("c64", Q.QS_C64, (("default", None),
+                                                   ("tensor_forward", Q.make_opts(mode=T, tc_min_gates=2,
+                                                                                  fuse_parametric=1))))):
         s = Q.qs_state_alloc(n, dt, st)
-        Q.qs_adjoint_grad(s, g, th, *H)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        e, gr = Q.qs_adjoint_grad(s, g, th, *H)
-        wall = (time.perf_counter() - t0) * 1e3
-        grads[dname] = gr
-        c4[dname] = {"ms": wall, "expval": e}
-        if dt == Q.QS_C128:   # the same gradient with the tile passes in FP32 pairs
-            o = Q.make_opts(c128_pairs=1)
+        for vname, o in variants:
             Q.qs_adjoint_grad(s, g, th, *H, opts=o)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            e2, gr2 = Q.qs_adjoint_grad(s, g, th, *H, opts=o)
-            c4["c128_fp32_pairs"] = {"ms": (time.perf_counter() - t0) * 1e3, "expval": e2,
-                                     "max_abs_grad_diff_vs_fp64": float(np.abs(gr2 - gr).max())}
-        else:                 # forward on tensor cores
-            o = Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=2, fuse_parametric=1)
-            Q.qs_adjoint_grad(s, g, th, *H, opts=o)
-            torch.cuda.synchronize()
-            t0 = time.perf_counter()
-            e2, gr2 = Q.qs_adjoint_grad(s, g, th, *H, opts=o)
-            c4["c64_tensor_forward"] = {"ms": (time.perf_counter() - t0) * 1e3, "expval": e2,
-                                        "max_abs_grad_diff_vs_default": float(np.abs(gr2 - gr).max())}
+            walls = []
+            for _ in range(3):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                e, gr = Q.qs_adjoint_grad(s, g, th, *H, opts=o)
+                walls.append((time.perf_counter() - t0) * 1e3)
+            grads[(dname, vname)] = gr
+            c4[f"{dname}_{vname}"] = {"ms": spread(walls), "expval": e}
         Q.qs_state_free(s)
-    c4["max_abs_grad_diff_c64_vs_c128"] = float(np.abs(grads["c64"] - grads["c128"]).max())
+    ref = grads[("c128", "default_fp64")]
+    for k, gr in grads.items():
+        c4[f"{k[0]}_{k[1]}"]["max_abs_grad_diff_vs_c128_fp64"] = float(np.abs(gr - ref).max())
     return c4
 
 
 # The sources each kernel is compiled from (its traffic record is void once they change).
-KERNEL_SOURCES = {"k_tc_bulk": ("kernels_tc.cu", "cplx.cuh"), "k_tc_block": ("kernels_tc.cu", "cplx.cuh"),
+KERNEL_SOURCES = {"k_tc_bulk": ("kernels_tc.cu", "tcgen05.cuh", "cplx.cuh"),
+                  "k_tc_block": ("kernels_tc.cu", "tcgen05.cuh", "cplx.cuh"),
+                  "k_tc128": ("kernels_tc128.cu", "tcgen05.cuh"),
                   "k_tile": ("kernels_tile.cuh", "cplx.cuh", "dfloat.cuh", "qs_internal.h")}
 
 
