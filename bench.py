@@ -42,7 +42,8 @@ def parse():
     ap.add_argument("--n", type=int, default=30)
     ap.add_argument("--depth", type=int, default=20)
     ap.add_argument("--seed", type=int, default=0)
-    ap.add_argument("--no-c128", action="store_true")
+    ap.add_argument("--no-c128", action="store_true",
+                    help="run only the complex64 line and print it alone (profiler runs of k_tc_bulk / k_tile)")
     ap.add_argument("--no-per-gate", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-clocks", action="store_true", help="skip the nvidia-smi sampler (profiler runs)")
@@ -317,6 +318,15 @@ def main():
     sb128, sb64 = 2 * (1 << n) * 16, 2 * (1 << n) * 8
     extra = {}
 
+    if args.no_c128:
+        line = {"c64_tensor": c64_line(Q, torch, np, args, gates, stream, hbm_peak, bf16_peak, peak_src, None)}
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        if dist:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+
     # ------------------------------------------------------------ headline: complex128
     # every contracted 5-qubit block applied on tensor cores as exact fp16 digit
     # products (the complex128 tensor-core pass), one step = one circuit + FP64 norm
@@ -515,7 +525,7 @@ def c64_line(Q, torch, np, args, gates, stream, hbm_peak, bf16_peak, peak_src, s
                                       "runs 3 such products"}
     Q.qs_state_set_basis(state, 0)
     Q.qs_plan_execute(plan, state)
-    if not args.no_per_gate:
+    if not args.no_per_gate and s_ref is not None:
         out["max_abs_vs_c128_per_gate"], out["l2_vs_c128_per_gate"] = Q.qs_state_diff(state, s_ref)
         pplan = Q.qs_plan_create(n, Q.QS_C64, gates, None)
         pg_ms, _, pk, _ = time_steps(Q, torch, pplan, state, 1, 1, per_launch=True, with_norm=False)

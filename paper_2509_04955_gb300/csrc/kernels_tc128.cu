@@ -1,7 +1,7 @@
 // Tensor-core pass for complex128 states: one dense 5-qubit block (32 x 32
 // complex, FP64 entries) applied with fp16 tcgen05 MMAs whose products and
-// sums are exact, so the result carries about 45 significant bits per pass
-// with no FP64 instruction.
+// sums are exact, so a pass adds an error of about 2^-46 of the row's norm
+// (2^-48 between passes that hand over FP32 pairs) with no FP64 instruction.
 //
 // A fused block of Section 3.4 on qubits Q (|Q| = 5) is psi'[r, :] = U psi[r, :]
 // over the 2^(n-5) rows r (the other bits). Over reals with interleaved
@@ -25,9 +25,11 @@
 // which fp16 holds exactly), rounded in FP32 at about 2^-24 of level 4. The
 // levels, D = 2^(E-16) sum_l acc_l 2^(-9 l), are combined in FP32 pairs
 // (TwoSum) and written back as FP64 by their bit patterns. What is dropped
-// (A's bits below 2^-47 of its scale, W's below 2^-54, levels above 5) leaves
-// an absolute error per pass of about 2^-47 times the row's scale 2^E
-// (|a| < 2^E <= 2 max |a|).
+// (each FP64 value's mantissa bits below its 47th, W's bits below 2^-54,
+// levels above 5) bounds the error of an output by 2^-46 ||a||_2 + 2^(E-49),
+// ||a||_2 the 2-norm of its row (Cauchy-Schwarz over a unit column of W) and
+// 2^E the row's scale (|a| < 2^E <= 2 max |a|); a row read as FP32 pairs
+// (48 bits, no truncation) by 2^-48 ||a||_2 + 2^(E-49).
 //
 // Pipeline (one persistent CTA per SM, 576 threads, tiles of 128 rows x 32
 // columns = 4096 amplitudes = 64 KiB, 12 tile qubits: the block's 5 and the 7

@@ -5,7 +5,12 @@ oracle computes one by one:
 * the 30-qubit random circuit (complex64, tensor-core plan) followed by its
   inverse returns |0..0>, and the norm stays 1;
 * the 32-qubit CZ circuit (32 GiB complex64) on tensor cores: circuit x
-  inverse = identity.
+  inverse = identity;
+* complex128 on the tensor-core plan (the benchmark's headline
+  configuration): the 30-qubit circuit and the 32-qubit CZ circuit (64 GiB)
+  times their inverses = identity, bar derived from the per-pass bound of the
+  digit products; QFT n = 30 on 2^16 sampled amplitudes against the closed
+  form.
 Round-trip bar: each tensor-core block application perturbs the state by a
 relative error e per pass: bf16x3 split products keep about 16 significant
 bits (e = 2^-16: hi and lo of 8 bits each, the dropped lo*lo term 2^-16);
@@ -40,12 +45,12 @@ def built():
 EPS = {3: 2.0 ** -16, 4: 2.0 ** -21}
 
 
-def roundtrip(n, gates, opts):
+def roundtrip(n, gates, opts, dt=Q.QS_C64):
     inv = W.inverse_circuit(gates)
-    h = Q.qs_state_alloc(n, Q.QS_C64)
+    h = Q.qs_state_alloc(n, dt)
     try:
-        p1 = Q.qs_plan_create(n, Q.QS_C64, gates, opts)
-        p2 = Q.qs_plan_create(n, Q.QS_C64, inv, opts)
+        p1 = Q.qs_plan_create(n, dt, gates, opts)
+        p2 = Q.qs_plan_create(n, dt, inv, opts)
         nblocks = sum(1 for p in (p1, p2) for op in Q.qs_plan_ops(p) if op["type"] == 3)
         try:
             Q.qs_plan_execute(p1, h)
@@ -55,7 +60,7 @@ def roundtrip(n, gates, opts):
         finally:
             Q.qs_plan_free(p1)
             Q.qs_plan_free(p2)
-        z = Q.qs_state_alloc(n, Q.QS_C64)
+        z = Q.qs_state_alloc(n, dt)
         try:
             Q.qs_state_set_basis(z, 0)
             max_abs, l2 = Q.qs_state_diff(h, z)
@@ -63,6 +68,10 @@ def roundtrip(n, gates, opts):
             Q.qs_state_free(z)
     finally:
         Q.qs_state_free(h)
+    if dt == Q.QS_C128:
+        # per pass and output at most (2^-46 + 2^-48) of the row's 2-norm, so
+        # ||delta||_2 <= sqrt(32) (2^-46 + 2^-48) per pass, added up linearly
+        return norm_mid, norm_end, max_abs, l2, nblocks * np.sqrt(32) * (2.0 ** -46 + 2.0 ** -48)
     return norm_mid, norm_end, max_abs, l2, 4.0 * np.sqrt(max(1, nblocks)) * EPS[opts.tc_precision or 4]
 
 
@@ -84,6 +93,41 @@ def test_n32_cz_circuit_tensor_plan_times_inverse(prec):
                                                                   tc_precision=prec))
     assert abs(mid - 1) < 1e-4 and abs(end - 1) < 1e-4
     assert max_abs <= bar and l2 <= bar, (max_abs, l2, bar)
+
+
+@pytest.mark.parametrize("n,depth,ent", [(30, 20, "cnot"), (32, 40, "cz")])
+def test_c128_tensor_plan_times_inverse_at_full_size(n, depth, ent):
+    """Complex128 on the default tensor-core plan, the launch configuration
+    of the benchmark: the 30-qubit headline circuit (16 GiB) and the 32-qubit
+    CZ circuit (64 GiB), each followed by its inverse, return |0..0>. Bar: the
+    derived worst case of the digit-product passes for the l2 error, and the
+    complex128 bar 1e-12 for every amplitude."""
+    gates = W.random_layered(n, depth, seed=0, entangler=ent)
+    mid, end, max_abs, l2, bar = roundtrip(n, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR), Q.QS_C128)
+    assert abs(mid - 1) < 1e-12 and abs(end - 1) < 1e-12
+    assert l2 <= bar and max_abs <= min(bar, 1e-12), (max_abs, l2, bar)
+
+
+def test_c128_tensor_plan_qft_n30_sampled_closed_form():
+    """QFT on 30 qubits (16 GiB complex128) on the tensor-core plan from a
+    seeded basis state: 2^16 sampled amplitudes, gathered on the device,
+    against the closed form 2^-15 e^(2 pi i x y / 2^30), bar 1e-12."""
+    n = 30
+    x = W.random_basis_index(n, 30)
+    rng = np.random.default_rng(3)
+    idx = np.unique(rng.integers(0, 1 << n, size=1 << 16).astype(np.uint64))
+    h = Q.qs_state_alloc(n, Q.QS_C128)
+    try:
+        Q.qs_state_set_basis(h, x)
+        Q.qs_apply_circuit(h, W.qft(n), None, Q.make_opts(mode=Q.QS_MODE_TENSOR))
+        got = Q.qs_state_get_amplitudes(h, idx, Q.QS_C128)
+        assert abs(Q.qs_norm(h) - 1) < 1e-12
+    finally:
+        Q.qs_state_free(h)
+    y = idx.astype(object)
+    ph = np.array([float((x * int(v)) % (1 << n)) for v in y]) / (1 << n)
+    want = np.exp(2j * np.pi * ph) / 2.0 ** (n / 2)
+    assert np.abs(got - want).max() <= 1e-12
 
 
 @pytest.mark.parametrize("dtname,mode", [("c64", Q.QS_MODE_FUSED), ("c64", Q.QS_MODE_TENSOR),

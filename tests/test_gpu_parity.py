@@ -481,6 +481,96 @@ def test_tensor_core_config2_shape_n20_depth40_cz():
     assert np.abs(out - want).max() <= 2e-5
 
 
+class oracle_threads:
+    """Runs the oracle on every host core inside the block (its gate loops
+    split the amplitudes among threads; results are bit-identical to one
+    thread), one thread again after."""
+
+    def __enter__(self):
+        O.lib().or_set_threads(0)
+
+    def __exit__(self, *exc):
+        O.lib().or_set_threads(1)
+
+
+# 6-qubit placements at 23 qubits: inside the lowest rows, across the tile
+# boundary (tile widths 12-13), spread from qubit 0 to the top, and entirely
+# among the highest qubits (the tile-index bits of the address).
+BLOCK_SETS_N23 = [(0, 1, 2, 3, 4, 5), (9, 10, 11, 12, 13, 14), (0, 5, 11, 13, 17, 22),
+                  (17, 18, 19, 20, 21, 22), (3, 4, 12, 19, 20, 21), (1, 2, 3, 14, 15, 16)]
+
+
+@pytest.mark.parametrize("pipe", [0, 1])
+def test_tensor_core_single_state_n23_every_block_placement(pipe):
+    """A single 2^23 complex64 state (2^11 tiles, several per CTA) through
+    dense 6-qubit blocks on the placements above, on both tensor-core
+    pipelines: every amplitude against the oracle, bar 2e-5."""
+    n = 23
+    gates = W.block_circuit(BLOCK_SETS_N23, 12, seed=23)
+    psi0 = W.random_state(n, 9).astype(np.complex64)
+    with oracle_threads():
+        want = ref(n, gates, psi0=psi0.astype(complex))
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=6,
+                                                            tc_pipeline=pipe))
+    try:
+        tc_sets = [tuple(sorted(op["qubits"])) for op in Q.qs_plan_ops(plan) if op["type"] == 3]
+        assert len(tc_sets) == len(BLOCK_SETS_N23)
+        h = Q.qs_state_alloc(n, Q.QS_C64)
+        try:
+            Q.qs_state_copy_from_host(h, psi0)
+            Q.qs_plan_execute(plan, h)
+            out = np.empty(1 << n, dtype=np.complex64)
+            Q.qs_state_copy_to_host(h, out)
+        finally:
+            Q.qs_state_free(h)
+    finally:
+        Q.qs_plan_free(plan)
+    assert np.abs(out - want).max() <= 2e-5
+
+
+@pytest.mark.parametrize("n", [22, 24])
+def test_tensor_core_default_plan_random_layers_n22_n24(n):
+    """The default tensor-core plan of the layered random circuit at 22 and
+    24 qubits (a single state, one persistent CTA per SM walking many tiles):
+    every amplitude against the oracle, complex64 bar 2e-5 and complex128
+    bar 1e-12."""
+    gates = W.random_layered(n, 12, seed=n)
+    with oracle_threads():
+        want = ref(n, gates)
+    for dt in (Q.QS_C64, Q.QS_C128):
+        out = run(n, dt, gates, opts=Q.make_opts(mode=Q.QS_MODE_TENSOR))
+        assert np.abs(out - want).max() <= TOL[dt], dt
+
+
+_CZ26 = {}
+
+
+def _cz26():
+    """The 32-qubit tensor-core workload's structure (random layers, CZ
+    entanglers, depth 40) at 26 qubits and its oracle state (computed once)."""
+    if not _CZ26:
+        n = 26
+        gates = W.random_layered(n, 40, seed=0, entangler="cz")
+        with oracle_threads():
+            _CZ26["v"] = (n, gates, ref(n, gates))
+    return _CZ26["v"]
+
+
+@pytest.mark.parametrize("dtname,prec", [("c64", 4), ("c64", 3), ("c128", 0)])
+def test_tensor_core_cz_depth40_n26_against_the_oracle(dtname, prec):
+    """Depth 40 of CZ layers at 26 qubits (1560 gates, 2^14 tiles) on the
+    tensor-core plan: complex64 with the fp16 and the bf16 split products (bar
+    2e-5) and complex128 with exact digit products (bar 1e-12), every
+    amplitude against the oracle."""
+    n, gates, want = _cz26()
+    dt = DT[dtname]
+    kw = dict(mode=Q.QS_MODE_TENSOR)
+    if prec:
+        kw["tc_precision"] = prec
+    out = run(n, dt, gates, opts=Q.make_opts(**kw))
+    assert np.abs(out - want).max() <= TOL[dt]
+
+
 def _structured_pauli_sum(n, seed):
     """Every x-mask case of the batched expectation kernel: x = 0 (Z
     strings), x = 1, odd and even x with a high bit, and 11 strings sharing one

@@ -2,9 +2,10 @@
 timeout path of both tensor-core passes, through the C ABI against the FP64
 oracle.
 
-Bar: complex128 max |delta amp| <= 1e-12 element by element (the pass keeps
-about 2^-47 of each 64-real row's scale per pass, so the bar leaves a wide
-margin at these depths).
+Bar: complex128 max |delta amp| <= 1e-12 element by element (a pass adds at
+most 2^-46 of a 32-amplitude row's 2-norm plus 2^-49 of its scale to each
+output, 2^-48 of the norm between passes that hand over FP32 pairs, so the bar
+leaves a wide margin at these depths).
 """
 import numpy as np
 import pytest

@@ -16,10 +16,14 @@ what it relies on:
 * the FP32-pair form kept between consecutive passes: digits taken from a
   pair, and a row read and written as pairs, keep the same bounds;
 * a whole row: U psi through digits, exact level sums (level 5 folded into
-  level 4) and the combination is within 2^-46 of the row's scale 2^E
-  (|a| < 2^E <= 2 max |a|) of the FP64 product, for
-  Haar-random blocks and rows of every shape (random, one non-zero entry,
-  mixed magnitudes, FP64 zeros and subnormals, exact powers of two);
+  level 4) and the combination is within 2^-46 ||a||_2 + 2^(E-49) of the
+  FP64 product (2^-48 ||a||_2 + 2^(E-49) when the row is read as FP32
+  pairs), ||a||_2 the row's 2-norm and 2^E its scale (|a| < 2^E <= 2 max
+  |a|), for Haar-random blocks and rows of every shape (random, one non-zero
+  entry, mixed magnitudes, FP64 zeros and subnormals, exact powers of two);
+  the bound is tight enough that a model with one planted mistake (a digit
+  plane of A or W dropped, the level-4 accumulator lost, a level's sign
+  flipped, the block transposed) fails it;
 * indexing: runs of >= 2^7 amplitudes land every element (row, column) of a
   tile at its tile-local index, the tiles partition the state, and stores
   go to roff(row) | coff(column) of the tile;
@@ -183,10 +187,11 @@ def row_emax(vals):
     return int(((u >> np.uint64(52)) & np.uint64(0x7FF)).max())
 
 
-def apply_row(U, a, pairs_in=False, pairs_out=False):
+def apply_row(U, a, pairs_in=False, pairs_out=False, plant=None):
     """One output row of the pass: U (32x32 complex) applied to a (32 complex)
     the kernel's way, reading FP64 values or FP32 pairs and writing FP64
-    values or pairs (returned joined in FP64 for comparison)."""
+    values or pairs (returned joined in FP64 for comparison). `plant` puts one
+    deliberate mistake into the model (a test shows the bound catches it)."""
     reals = np.empty(64)
     reals[0::2], reals[1::2] = a.real, a.imag
     if pairs_in:
@@ -198,6 +203,8 @@ def apply_row(U, a, pairs_in=False, pairs_out=False):
         D = digits(reals, np.full(64, E + 1022))
     em = E + 1022
     assert np.abs(D).max() <= 260
+    if plant == "no_a_digit5":
+        D[5] = 0
     Wd = np.zeros((6, 64, 64), dtype=np.int64)       # [j][k][nn]
     for co in range(32):
         for ci in range(32):
@@ -206,6 +213,10 @@ def apply_row(U, a, pairs_in=False, pairs_out=False):
                              (2 * ci + 1, 2 * co, -u.imag), (2 * ci + 1, 2 * co + 1, u.real)):
                 Wd[:, k, nn] = w_digits(w)
     assert np.abs(Wd).max() <= 256
+    if plant == "no_w_digit5":
+        Wd[5] = 0
+    if plant == "w_transposed":
+        Wd = Wd.transpose(0, 2, 1).copy()
     Di = D.astype(np.int64)
     out = np.empty(64)
     for nn in range(64):
@@ -220,6 +231,10 @@ def apply_row(U, a, pairs_in=False, pairs_out=False):
                         assert abs(tot) < 2 ** 24, "an exact level left the FP32 integer range"
             if l == 4:   # level 5 folded in: A_i (2^-9 W_(5-i)), i < 5, and (2^-9 A_5) W_0
                 tot = Fraction(tot) + sum(Fraction(int((Di[i] * Wd[5 - i, :, nn]).sum()), 512) for i in range(0, 6))
+            if plant == "no_level4" and l == 4:
+                tot = 0
+            if plant == "level1_sign" and l == 1:
+                tot = -tot
             lev.append(F32(float(tot)))                # exact for levels <= 2 (checked), rounded above
         if pairs_out:
             so, eo = pair_out(lev, E)
@@ -227,6 +242,17 @@ def apply_row(U, a, pairs_in=False, pairs_out=False):
         else:
             out[nn] = combine(lev, em)
     return out[0::2] + 1j * out[1::2], em
+
+
+def row_bound(a, em, pairs_in=False):
+    """The per-output error bound of one pass: the digit split keeps 47 bits
+    of each FP64 value (truncation below 2^-46 relative; an FP32 pair holds
+    its value to 2^-48), which a unit column of W turns into at most that
+    fraction of the row's 2-norm (Cauchy-Schwarz); the last digit's rounding,
+    W's digit tails (2^-54 per entry) and the level-4 accumulation add less
+    than 2^(E-49)."""
+    nrm = float(np.sqrt(np.sum(np.abs(a) ** 2)))
+    return (2.0 ** -48 if pairs_in else 2.0 ** -46) * nrm + 2.0 ** (em - 1022 - 49)
 
 
 def haar(d, rng):
@@ -303,7 +329,7 @@ def test_a_whole_row_through_fp32_pairs(pairs_in, pairs_out):
         if trial == 2:
             a[::3] = 0
         got, em = apply_row(U, a, pairs_in, pairs_out)
-        assert np.abs(got - U @ a).max() <= 2.0 ** -46 * 2.0 ** (em - 1022)
+        assert np.abs(got - U @ a).max() <= row_bound(a, em, pairs_in)
 
 
 @pytest.mark.parametrize("shape", ["random", "one", "mixed", "tiny", "powers", "zeros"])
@@ -330,8 +356,23 @@ def test_a_whole_row_matches_the_fp64_product(shape):
         if np.abs(np.concatenate([a.real, a.imag])).max() == 0:
             assert np.all(got == 0)
             continue
-        scale = 2.0 ** (em - 1022)
-        assert np.abs(got - want).max() <= 2.0 ** -46 * scale + 1e-300, (shape, trial)
+        assert np.abs(got - want).max() <= row_bound(a, em) + 1e-300, (shape, trial)
+
+
+@pytest.mark.parametrize("plant", ["no_a_digit5", "no_w_digit5", "no_level4", "level1_sign", "w_transposed"])
+def test_the_row_bound_catches_a_planted_mistake(plant):
+    """The whole-row bound is tight enough to fail when the model drops the
+    last digit plane of A or of W or the level-4 accumulator, flips the sign
+    of a level, or transposes the block (rows read as FP32 pairs, the form
+    every pass after the first of a run reads): each slip gives an error
+    above the bound, the clean model one well below it."""
+    rng = np.random.default_rng(60)
+    U = haar(32, rng)
+    a = (rng.standard_normal(32) + 1j * rng.standard_normal(32)) / 8
+    got, em = apply_row(U, a, pairs_in=True, plant=plant)
+    assert np.abs(got - U @ a).max() > 2 * row_bound(a, em, pairs_in=True)
+    clean, em = apply_row(U, a, pairs_in=True)
+    assert np.abs(clean - U @ a).max() <= 0.5 * row_bound(a, em, pairs_in=True)
 
 
 def test_level_three_range_holds_for_random_rows():
