@@ -71,16 +71,38 @@ constexpr int kT2PlaneBytes = 8192;                       // W digit plane: 64 (
 constexpr int kT2WBytes = 10 * kT2PlaneBytes;           // g_0..g_4, then 2^-9 g_1..2^-9 g_5
 constexpr uint32_t kT2TmemCols = 512;
 constexpr uint32_t kT2AccCol = 192;
-// kind::f16, fp16 A and B, FP32 D, both K-major, N = 64 (bits 17-22), M = 128 (bits 24-28)
-constexpr uint32_t kT2Idesc = (1u << 4) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+// kind::f16, fp16 A and B, FP32 D, both K-major, N = 64 x nplanes (bits 17-22), M = 128 (bits 24-28)
+constexpr uint32_t t2_idesc(int nplanes) {
+  return (1u << 4) | ((64u * (uint32_t)nplanes >> 3) << 17) | ((128u >> 4) << 24);
+}
 
-__device__ __forceinline__ void t2_mma(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t acc) {
+__device__ __forceinline__ void t2_mma(uint32_t tmem_d, uint32_t tmem_a, uint64_t b, uint32_t idesc, uint32_t acc) {
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
       "setp.ne.b32 p, %4, 0;\n\t"
       "tcgen05.mma.cta_group::1.kind::f16 [%0], [%1], %2, %3, p;\n\t}\n" ::"r"(tmem_d),
-      "r"(tmem_a), "l"(b), "r"(kT2Idesc), "r"(acc));
+      "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc));
 }
+
+// The MMA schedule of a tile (per k-step; every entry runs for the 4 k-steps).
+// An entry multiplies A digit plane `a` by `nplanes` consecutive W planes
+// starting at `w` (B rows 64 x nplanes: the planes lie back to back in shared
+// memory) into as many consecutive level accumulators starting at `level`
+// (64 tensor-memory columns each, also back to back), so A_a W_j lands in
+// level a + j. Planes 5..9 hold 2^-9 W_1 .. 2^-9 W_5 (plane 9 - a pairs with
+// A_a for the level-5 products folded into level 4) and A plane 5 holds
+// 2^-9 A_5. An instruction costs about the same for N = 64 and N = 128, so
+// merging consecutive planes cuts the 21 products to 13 instructions. Phase
+// X touches levels 2-4 only (it may start once the previous tile's levels
+// have been folded), phase Y levels 0-1 only (once the folded pairs have been
+// read back); the first entry of each phase writes every level of its phase
+// without accumulating.
+struct T2Mma {
+  int a, w, nplanes, level;
+};
+__device__ constexpr T2Mma kT2PhaseX[] = {{2, 0, 3, 2}, {0, 2, 3, 2}, {1, 1, 3, 2}, {3, 0, 2, 3}, {4, 0, 1, 4}, {0, 9, 1, 4},
+                                          {1, 8, 1, 4}, {2, 7, 1, 4}, {3, 6, 1, 4}, {4, 5, 1, 4}, {5, 0, 1, 4}};
+__device__ constexpr T2Mma kT2PhaseY[] = {{0, 0, 2, 0}, {1, 0, 1, 1}};
 
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
@@ -389,25 +411,13 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         if (i >= 1 && !mbar_wait(smem_u32(dfree), (uint32_t)((i - 1) & 1), spin)) { fail(1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int l = 2; l < 5; ++l) {
-#pragma unroll
-          for (int ai = 0; ai <= l; ++ai) {
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              t2_mma(tmem + kT2AccCol + 64 * l, tmem + 32 * ai + 8 * ks,
-                     smem_desc(wb + (l - ai) * kT2PlaneBytes + 32 * ks), (ai | ks) ? 1u : 0u);
-          }
-        }
-#pragma unroll
-        for (int ai = 0; ai <= 4; ++ai) {
+        for (int e = 0; e < (int)(sizeof(kT2PhaseX) / sizeof(T2Mma)); ++e) {
+          const T2Mma m = kT2PhaseX[e];
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
-            t2_mma(tmem + kT2AccCol + 64 * 4, tmem + 32 * ai + 8 * ks, smem_desc(wb + (9 - ai) * kT2PlaneBytes + 32 * ks),
-                   1u);
+            t2_mma(tmem + kT2AccCol + 64 * m.level, tmem + 32 * m.a + 8 * ks,
+                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (e | ks) ? 1u : 0u);
         }
-#pragma unroll
-        for (int ks = 0; ks < 4; ++ks)
-          t2_mma(tmem + kT2AccCol + 64 * 4, tmem + 32 * 5 + 8 * ks, smem_desc(wb + 32 * ks), 1u);
         if (i >= 1 && !mbar_wait(smem_u32(dfree01), (uint32_t)((i - 1) & 1), spin)) {
           mma_commit(smem_u32(mdone));   // the issued MMAs complete before the abort drain below
           ++i;
@@ -416,14 +426,12 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int l = 0; l < 2; ++l) {
+        for (int e = 0; e < (int)(sizeof(kT2PhaseY) / sizeof(T2Mma)); ++e) {
+          const T2Mma m = kT2PhaseY[e];
 #pragma unroll
-          for (int ai = 0; ai <= l; ++ai) {
-#pragma unroll
-            for (int ks = 0; ks < 4; ++ks)
-              t2_mma(tmem + kT2AccCol + 64 * l, tmem + 32 * ai + 8 * ks,
-                     smem_desc(wb + (l - ai) * kT2PlaneBytes + 32 * ks), (ai | ks) ? 1u : 0u);
-          }
+          for (int ks = 0; ks < 4; ++ks)
+            t2_mma(tmem + kT2AccCol + 64 * m.level, tmem + 32 * m.a + 8 * ks,
+                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (e | ks) ? 1u : 0u);
         }
         mma_commit(smem_u32(mdone));
         if (i + 1 < my && new_state(i + 1)) mma_commit(smem_u32(wfree));   // last tile on these planes

@@ -359,6 +359,46 @@ def test_a_whole_row_matches_the_fp64_product(shape):
         assert np.abs(got - want).max() <= row_bound(a, em) + 1e-300, (shape, trial)
 
 
+def _schedule():
+    """The kernel's MMA schedule tables (kT2PhaseX, kT2PhaseY), read from its source."""
+    import os
+    import re
+    src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2509_04955_gb300", "csrc",
+                            "kernels_tc128.cu")).read()
+    out = {}
+    for name in ("kT2PhaseX", "kT2PhaseY"):
+        body = re.search(name + r"\[\] = \{(.*?)\};", src, re.S).group(1)
+        out[name] = [tuple(int(x) for x in m.groups())
+                     for m in re.finditer(r"\{\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\s*\}", body)]
+    return out["kT2PhaseX"], out["kT2PhaseY"]
+
+
+def test_mma_schedule_issues_every_digit_product_once():
+    """Each entry (a, w, nplanes, level) multiplies A plane a by W planes
+    w .. w + nplanes - 1 into levels level .. level + nplanes - 1. Together the
+    two phases must issue exactly the 21 products of the digit scheme: A_i W_j
+    into level i + j for i + j <= 4 (planes 0-4), A_i (2^-9 W_(5-i)) into level
+    4 for i <= 4 (plane 9 - i), and (2^-9 A_5) W_0 into level 4; phase X only
+    into levels 2-4 and phase Y only into levels 0-1 (the two release steps of
+    the accumulators); the first entry of each phase covers all its levels
+    (it is the one issued without accumulation); N = 64 x nplanes <= 256."""
+    X, Y = _schedule()
+    want = {(i, j, i + j) for i in range(5) for j in range(5) if i + j <= 4}
+    want |= {(i, 9 - i, 4) for i in range(5)} | {(5, 0, 4)}
+    got = []
+    for phase, levels in ((X, {2, 3, 4}), (Y, {0, 1})):
+        first = phase[0]
+        assert set(range(first[3], first[3] + first[2])) == levels
+        for a, w, npl, lev in phase:
+            assert 1 <= npl <= 4 and 0 <= a <= 5
+            assert w + npl <= 5 or npl == 1, "merged planes must be plain W planes"
+            for k in range(npl):
+                assert lev + k in levels
+                got.append((a, w + k, lev + k))
+    assert sorted(got) == sorted(want) and len(got) == 21
+    assert len(X) + len(Y) == 13
+
+
 @pytest.mark.parametrize("plant", ["no_a_digit5", "no_w_digit5", "no_level4", "level1_sign", "w_transposed"])
 def test_the_row_bound_catches_a_planted_mistake(plant):
     """The whole-row bound is tight enough to fail when the model drops the
