@@ -24,7 +24,11 @@
 // A_i W_(5-i), i = 0..5, against W planes or an A plane pre-scaled by 2^-9,
 // which fp16 holds exactly), rounded in FP32 at about 2^-24 of level 4. The
 // levels, D = 2^(E-16) sum_l acc_l 2^(-9 l), are combined in FP32 pairs
-// (TwoSum) and written back as FP64 by their bit patterns. What is dropped
+// (TwoSum) and written back as FP64 by their bit patterns. The digit chain,
+// the fold and the pair output run on (re, im) at once with the packed FP32
+// instructions of sm_100+ (f32x2), and the A digits are stored negated (one
+// instruction per chain step fewer), so the levels hold negated sums, which
+// the fold turns back; every result is bit-identical to the scalar steps. What is dropped
 // (each FP64 value's mantissa bits below its 47th, W's bits below 2^-54,
 // levels above 5) bounds the error of an output by 2^-46 ||a||_2 + 2^(E-49),
 // ||a||_2 the 2-norm of its row (Cauchy-Schwarz over a unit column of W) and
@@ -128,69 +132,82 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
       : "r"(taddr));
 }
 
-// The six digits of one FP64 value a (bit pattern whi:wlo) of a row whose
-// biased-exponent maximum is emax_b (fe_off = 134 - emax_b): s = a 2^(8 - E),
-// E = emax_b - 1022, so |s| < 256, and s ~ sum_{i<6} d_i 2^(-9 i) (d[5] is
-// returned as 2^-9 d5, the form its tensor-memory plane holds); the error is
-// below 2^-39 (the 6 FP64 mantissa bits the split drops) and 2^-46. The FP64
-// mantissa is cut by bits into hi (sign, exponent, top 23 stored bits) and lo
-// (the next 23 bits, pre-scaled by 2^18); digits come from hi with exact FP32
-// steps (x + 1.5 2^23 rounds to an integer, fma(t, 512, -d) is exact) until hi
-// is used up, lo joins at digit 2. Values with |s| < 2^-40 (and FP64 zeros /
+// The start of the six digits of one FP64 value a (bit pattern whi:wlo) of a
+// row whose biased-exponent maximum is emax_b (fe_off = 134 - emax_b):
+// s = a 2^(8 - E), E = emax_b - 1022, so |s| < 256, and s ~ sum_{i<6} d_i
+// 2^(-9 i) (d5 is held as 2^-9 d5, the form its tensor-memory plane holds);
+// the error is below 2^-39 (the 6 FP64 mantissa bits the split drops) and
+// 2^-46. The FP64 mantissa is cut by bits into hi (sign, exponent, top 23
+// stored bits) and lo18 (the next 23 bits, pre-scaled by 2^18); the digit
+// chain (t2_nchain2) takes digits from hi with exact FP32 steps until hi is
+// used up, lo18 joins at digit 2. Values with |s| < 2^-40 (and FP64 zeros /
 // subnormals) give zero digits.
-__device__ __forceinline__ void t2_digits(uint32_t whi, uint32_t wlo, int fe_off, float* d) {
+__device__ __forceinline__ void t2_hilo(uint32_t whi, uint32_t wlo, int fe_off, float& hi, float& lo18) {
   const uint32_t ex = (whi >> 20) & 0x7ffu;
   const int fe = (int)ex + fe_off;              // biased FP32 exponent of s (<= 134)
   const uint32_t se = (whi & 0x80000000u) | ((uint32_t)fe << 23);
-  float hi = __uint_as_float(se | (__funnelshift_l(wlo, whi, 3) & 0x7fffffu));
+  hi = __uint_as_float(se | (__funnelshift_l(wlo, whi, 3) & 0x7fffffu));
   // lo = m 2^(e_s - 46) with m the remainder's top 23 bits: X - 2^x with
   // X = (1 + m 2^-23) 2^x, x = e_s - 23; pre-scaled by 2^18: x = e_s - 5
   const uint32_t eb = se - (5u << 23);
-  float lo18 = __fsub_rn(__uint_as_float(eb | ((wlo & 0x1fffffffu) >> 6)), __uint_as_float(eb));
+  lo18 = __fsub_rn(__uint_as_float(eb | ((wlo & 0x1fffffffu) >> 6)), __uint_as_float(eb));
   const bool ok = ex != 0 && fe >= 87;
   hi = ok ? hi : 0.f;
   lo18 = ok ? lo18 : 0.f;
-  d[0] = __fsub_rn(__fadd_rn(hi, kT2Magic), kT2Magic);
-  float t = __fsub_rn(hi, d[0]);                // exact, |t| <= 1/2
-  d[1] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
-  t = __fmaf_rn(t, 512.f, -d[1]);               // exact
-  d[2] = __fsub_rn(__fadd_rn(__fmaf_rn(t, 512.f, lo18), kT2Magic), kT2Magic);
-  t = __fadd_rn(__fmaf_rn(t, 512.f, -d[2]), lo18);
-  d[3] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
-  t = __fmaf_rn(t, 512.f, -d[3]);
-  d[4] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
-  t = __fmaf_rn(t, 512.f, -d[4]);
-  d[5] = __fmaf_rn(__fmaf_rn(t, 512.f, kT2Magic), 0.001953125f, -kT2Magic * 0.001953125f);
 }
 
-// The same six digits from an FP32 pair s + e (|e| <= ulp(s) / 2) of a row
-// with scale 2^E: hi = s 2^(8-E) and lo = e 2^(26-E) (sc8 = 2^(8-E),
-// sc26 = 2^(26-E), exact power-of-two scalings; tiny values flush to zero).
-__device__ __forceinline__ void t2_digits_pair(float s, float e, float sc8, float sc26, float* d) {
-  const float hi = __fmul_rn(s, sc8);
-  const float lo18 = __fmul_rn(e, sc26);
-  d[0] = __fsub_rn(__fadd_rn(hi, kT2Magic), kT2Magic);
-  float t = __fsub_rn(hi, d[0]);
-  d[1] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
-  t = __fmaf_rn(t, 512.f, -d[1]);
-  d[2] = __fsub_rn(__fadd_rn(__fmaf_rn(t, 512.f, lo18), kT2Magic), kT2Magic);
-  t = __fadd_rn(__fmaf_rn(t, 512.f, -d[2]), lo18);
-  d[3] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
-  t = __fmaf_rn(t, 512.f, -d[3]);
-  d[4] = __fsub_rn(__fmaf_rn(t, 512.f, kT2Magic), kT2Magic);
-  t = __fmaf_rn(t, 512.f, -d[4]);
-  d[5] = __fmaf_rn(__fmaf_rn(t, 512.f, kT2Magic), 0.001953125f, -kT2Magic * 0.001953125f);
+// The digit chain on (re, im) at once with packed FP32 instructions, from hi
+// (|hi| < 256) and lo18 (the next bits, scaled by 2^18): nd[i] = -d_i, the
+// digits negated (nd[5] = -2^-9 d5). Every step is the exact negation of
+// rounding to an integer by x + 1.5 2^23 - 1.5 2^23 and of the exact
+// residual fma(t, 512, -d): u = t 512 + M holds M + d, M - u = -d is exact,
+// and fma(t, 512, -d) continues the chain, one packed instruction each. The
+// pass stores the negated digits: every digit product, and so every level,
+// changes sign, which the drainers undo when they fold the levels.
+__device__ __forceinline__ void t2_nchain2(float2 hi, float2 lo18, float2* nd) {
+  const float2 M = make_float2(kT2Magic, kT2Magic), N1 = make_float2(-1.f, -1.f);
+  const float2 C512 = make_float2(512.f, 512.f);
+  float2 u = __fadd2_rn(hi, M);
+  nd[0] = __ffma2_rn(u, N1, M);
+  float2 t = __fadd2_rn(hi, nd[0]);                       // hi - d0, exact, |t| <= 1/2
+  u = __ffma2_rn(t, C512, M);
+  nd[1] = __ffma2_rn(u, N1, M);
+  t = __ffma2_rn(t, C512, nd[1]);                         // exact
+  u = __fadd2_rn(__ffma2_rn(t, C512, lo18), M);
+  nd[2] = __ffma2_rn(u, N1, M);
+  t = __fadd2_rn(__ffma2_rn(t, C512, nd[2]), lo18);
+  u = __ffma2_rn(t, C512, M);
+  nd[3] = __ffma2_rn(u, N1, M);
+  t = __ffma2_rn(t, C512, nd[3]);
+  u = __ffma2_rn(t, C512, M);
+  nd[4] = __ffma2_rn(u, N1, M);
+  t = __ffma2_rn(t, C512, nd[4]);
+  u = __ffma2_rn(t, C512, M);
+  nd[5] = __ffma2_rn(u, make_float2(-0.001953125f, -0.001953125f),
+                     make_float2(kT2Magic * 0.001953125f, kT2Magic * 0.001953125f));
+}
+
+// The same six digits (negated) of (re, im) held as FP32 pairs s + e (|e| <=
+// ulp(s) / 2) of a row with scale 2^E: hi = s 2^(8-E) and lo18 = e 2^(26-E)
+// (sc8 = 2^(8-E), sc26 = 2^(26-E), exact power-of-two scalings; tiny values
+// flush to zero).
+__device__ __forceinline__ void t2_ndigits_pair2(float2 s, float2 e, float2 sc8, float2 sc26, float2* nd) {
+  t2_nchain2(__fmul2_rn(s, sc8), __fmul2_rn(e, sc26), nd);
 }
 
 // 2^k as a float (-126 <= k <= 127)
 __device__ __forceinline__ float t2_pow2(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
 
-// (s, e) += c 2^-k with TwoSum (s + e = a + b exactly, b = c 2^-k scaled inside the FMAs)
-__device__ __forceinline__ void t2_absorb(float& s, float& e, float c, float sc) {
-  const float a = s;
-  s = __fmaf_rn(c, sc, a);
-  const float bb = __fsub_rn(s, a);
-  e = __fadd_rn(e, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fmaf_rn(c, sc, -bb)));
+// (s, e) += c sc on (re, im) at once, with TwoSum (s + e = a + b exactly, b =
+// c sc formed inside the FMAs; -bb = a - s, the exact negation of s - a)
+__device__ __forceinline__ void t2_absorb2(float2& s, float2& e, float2 c, float2 sc) {
+  const float2 N1 = make_float2(-1.f, -1.f);
+  const float2 a = s;
+  s = __ffma2_rn(c, sc, a);
+  const float2 nbb = __ffma2_rn(s, N1, a);
+  const float2 x1 = __ffma2_rn(__fadd2_rn(s, nbb), N1, a);   // a - (s - bb)
+  const float2 x2 = __ffma2_rn(c, sc, nbb);                   // b - bb
+  e = __fadd2_rn(e, __fadd2_rn(x1, x2));
 }
 
 // FP64 value 2^(E - 16) (s + e) of an FP32 pair, normalised first with a
@@ -480,7 +497,8 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         // row scale 2^E, |a| < 2^E; E >= -101 keeps every scale below a float
         const int E = max(PIN ? em - 126 : em - 1022, -101);
         const int fe_off = -888 - E;                    // FP64 input: biased exponent offset of s
-        const float sc8 = t2_pow2(8 - E), sc26 = t2_pow2(26 - E);   // pair input
+        const float2 sc8 = make_float2(t2_pow2(8 - E), t2_pow2(8 - E));     // pair input
+        const float2 sc26 = make_float2(t2_pow2(26 - E), t2_pow2(26 - E));
 #pragma unroll 1
         for (int c8 = 0; c8 < 2; ++c8) {
           // digits of 8 columns; the first 8 while the previous tile's MMAs may
@@ -489,17 +507,19 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
             const uint4 v = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + 8 * c8 + j]));
-            float dr[6], di[6];
+            float2 nd[6];
             if constexpr (PIN) {
-              t2_digits_pair(__uint_as_float(v.x), __uint_as_float(v.z), sc8, sc26, dr);
-              t2_digits_pair(__uint_as_float(v.y), __uint_as_float(v.w), sc8, sc26, di);
+              t2_ndigits_pair2(make_float2(__uint_as_float(v.x), __uint_as_float(v.y)),
+                               make_float2(__uint_as_float(v.z), __uint_as_float(v.w)), sc8, sc26, nd);
             } else {
-              t2_digits(v.y, v.x, fe_off, dr);
-              t2_digits(v.w, v.z, fe_off, di);
+              float2 hi, lo18;
+              t2_hilo(v.y, v.x, fe_off, hi.x, lo18.x);
+              t2_hilo(v.w, v.z, fe_off, hi.y, lo18.y);
+              t2_nchain2(hi, lo18, nd);
             }
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
-              const __half2 hv = __floats2half2_rn(dr[q], di[q]);
+              const __half2 hv = __float22half2_rn(nd[q]);
               pl[q][j] = *(const uint32_t*)&hv;
             }
           }
@@ -552,14 +572,18 @@ __global__ void __launch_bounds__(kT2Threads, 1)
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           uint32_t ps[8], pe[8];
 #pragma unroll
-          for (int k = 0; k < 8; ++k) {
-            float sk = __uint_as_float(a[0][k]), ek = 0.f;
-            t2_absorb(sk, ek, __uint_as_float(a[1][k]), 0.001953125f);
-            t2_absorb(sk, ek, __uint_as_float(a[2][k]), 3.814697265625e-06f);
-            t2_absorb(sk, ek, __uint_as_float(a[3][k]), 7.450580596923828e-09f);
-            ek = __fmaf_rn(__uint_as_float(a[4][k]), 1.4551915228366852e-11f, ek);
-            ps[k] = __float_as_uint(sk);
-            pe[k] = __float_as_uint(ek);
+          for (int k = 0; k < 8; k += 2) {
+            // the levels hold the negated sums (the A digits are negated)
+            auto lv = [&](int l) { return make_float2(__uint_as_float(a[l][k]), __uint_as_float(a[l][k + 1])); };
+            float2 sk = __fmul2_rn(lv(0), make_float2(-1.f, -1.f)), ek = make_float2(0.f, 0.f);
+            t2_absorb2(sk, ek, lv(1), make_float2(-0.001953125f, -0.001953125f));
+            t2_absorb2(sk, ek, lv(2), make_float2(-3.814697265625e-06f, -3.814697265625e-06f));
+            t2_absorb2(sk, ek, lv(3), make_float2(-7.450580596923828e-09f, -7.450580596923828e-09f));
+            ek = __ffma2_rn(lv(4), make_float2(-1.4551915228366852e-11f, -1.4551915228366852e-11f), ek);
+            ps[k] = __float_as_uint(sk.x);
+            ps[k + 1] = __float_as_uint(sk.y);
+            pe[k] = __float_as_uint(ek.x);
+            pe[k + 1] = __float_as_uint(ek.y);
           }
           tmem_st8(col, ps);
           tmem_st8(col + 64, pe);
@@ -584,13 +608,13 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 #pragma unroll
           for (int j = 0; j < 4; ++j) {
             if constexpr (POUT) {
-              float sr = __uint_as_float(ps[2 * j]), er = __uint_as_float(pe[2 * j]);
-              float si = __uint_as_float(ps[2 * j + 1]), ei = __uint_as_float(pe[2 * j + 1]);
-              const float tr = __fadd_rn(sr, er), ti = __fadd_rn(si, ei);   // FastTwoSum
-              er = __fsub_rn(er, __fsub_rn(tr, sr));
-              ei = __fsub_rn(ei, __fsub_rn(ti, si));
-              *(float4*)(psi + (rb | coff[16 * h + 4 * c4 + j])) =
-                  make_float4(__fmul_rn(tr, osc), __fmul_rn(ti, osc), __fmul_rn(er, osc), __fmul_rn(ei, osc));
+              const float2 s2 = make_float2(__uint_as_float(ps[2 * j]), __uint_as_float(ps[2 * j + 1]));
+              const float2 e2 = make_float2(__uint_as_float(pe[2 * j]), __uint_as_float(pe[2 * j + 1]));
+              const float2 t2 = __fadd2_rn(s2, e2);                                   // FastTwoSum
+              const float2 f2 = __fadd2_rn(e2, __ffma2_rn(t2, make_float2(-1.f, -1.f), s2));   // e - (t - s)
+              const float2 osc2 = make_float2(osc, osc);
+              const float2 o1 = __fmul2_rn(t2, osc2), o2 = __fmul2_rn(f2, osc2);
+              *(float4*)(psi + (rb | coff[16 * h + 4 * c4 + j])) = make_float4(o1.x, o1.y, o2.x, o2.y);
             } else {
               double2 o;
               o.x = t2_join(__uint_as_float(ps[2 * j]), __uint_as_float(pe[2 * j]), E);
