@@ -5,7 +5,9 @@ the rounding of the kernel's __fadd_rn / __fmul_rn / __fmaf_rn steps, whose
 FMAs here only add a power-of-two multiple), the kernel's arithmetic and check
 what it relies on:
 
-* digits: every FP64 value of a row becomes six integer digits with
+* digits (the pass stores them negated, its chain being the exact negation of
+  the one restated here; a test checks that bit for bit): every FP64 value of
+  a row becomes six integer digits with
   |d| <= 260 whose sum 2^(E-8) sum_i d_i 2^(-9 i) is within 2^(E-46) of it;
   the host's W digits (six, balanced, |g| <= 256) are within 2^-54 of w;
 * exactness: the level sums of a 64-term row (levels 0..2, and 3 short of an
@@ -278,6 +280,44 @@ def test_digits_reconstruct_every_value_of_a_row():
             rec += D[i] * 2.0 ** (-9 * i)
         rec *= 2.0 ** (E - 8)
         assert np.abs(rec - vals).max() <= 2.0 ** (E - 46)
+
+
+def ndigits_pair(s, e, E):
+    """The kernel's packed chain (t2_nchain2 after t2_ndigits_pair2): the
+    negated digits, u = t 512 + M, -d = M - u, t = fma(t, 512, -d)."""
+    M = MAGIC
+    hi = np.asarray(s, dtype=np.float32) * F32(2.0 ** (8 - E))
+    lo18 = np.asarray(e, dtype=np.float32) * F32(2.0 ** (26 - E))
+    u = hi + M
+    nd0 = M - u
+    t = hi + nd0
+    u = t * F32(512) + M
+    nd1 = M - u
+    t = t * F32(512) + nd1
+    u = (t * F32(512) + lo18) + M
+    nd2 = M - u
+    t = (t * F32(512) + nd2) + lo18
+    u = t * F32(512) + M
+    nd3 = M - u
+    t = t * F32(512) + nd3
+    u = t * F32(512) + M
+    nd4 = M - u
+    t = t * F32(512) + nd4
+    u = t * F32(512) + M
+    nd5 = (M - u)                        # the kernel stores -2^-9 d5 (exact)
+    return np.stack([nd0, nd1, nd2, nd3, nd4, nd5]).astype(np.float64)
+
+
+def test_negated_digit_chain_is_the_exact_negation():
+    """The pass stores -d_i, computed by its own chain; every step is the exact
+    negation of the positive chain's (rounding is symmetric and u - M is an
+    exact integer), so the digits agree bit for bit up to sign."""
+    rng = np.random.default_rng(4)
+    vals = np.concatenate([rng.standard_normal(5000) * 10.0 ** rng.integers(-12, 1, 5000),
+                           [0.0, 1.0, -1.0, 0.5, 2.0 ** -30, 0.999999999, 1e-40]])
+    s, e = to_pairs(vals)
+    E = pair_row_scale(s)
+    assert np.array_equal(ndigits_pair(s, e, E), -digits_pair(s, e, E))
 
 
 def test_w_digits_reconstruct_within_2_pow_minus_54():
