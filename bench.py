@@ -378,7 +378,7 @@ def main():
         extra["precision_vs_fp64_per_gate"] = {"max_abs": m, "l2": l2}
     # the same circuit on CUDA cores: tile passes in FP32 pairs (and FP64 with --full-configs)
     for name, okw in (("c128_fused_fp32_pairs", dict(mode=F, fuse_k=2, tile_qubits=11, low_qubits=3, c128_pairs=1)),
-                      ("c128_fused_fp64", dict(mode=F, fuse_k=1, tile_qubits=12, low_qubits=4))):
+                      ("c128_fused_fp64", dict(mode=F, fuse_k=1, tile_qubits=12, low_qubits=4, c128_pairs=2))):
         if name == "c128_fused_fp64" and not args.full_configs:
             continue
         s2 = Q.qs_state_alloc(n, Q.QS_C128, stream)
@@ -729,7 +729,7 @@ def config_qaoa30(Q, torch, np, st, args):
     variants = {"c64": [("per_gate", None), ("fused_no_phase", Q.make_opts(mode=F, phase_min_gates=-1)),
                         ("fused", Q.make_opts(mode=F)),
                         ("tensor", Q.make_opts(mode=T, tc_min_gates=4, fuse_parametric=1))],
-                "c128": [("per_gate", None), ("fused", Q.make_opts(mode=F)),
+                "c128": [("per_gate", None), ("fused_fp64", Q.make_opts(mode=F, c128_pairs=2)),
                          ("fused_fp32_pairs", Q.make_opts(mode=F, tile_qubits=12, low_qubits=4, c128_pairs=1)),
                          ("tensor", Q.make_opts(mode=T, fuse_parametric=1, c128_pairs=1))]}
     ref_e = None
@@ -832,7 +832,7 @@ def config_qft(Q, torch, np, st, args):
                              ("fused_k4_fp32_pairs", Q.make_opts(mode=F, fuse_k=4, c128_pairs=1), 3),
                              ("fused_k5_fp32_pairs", Q.make_opts(mode=F, fuse_k=5, tile_qubits=11, low_qubits=3,
                                                                  c128_pairs=1), 3),
-                             ("fused_k5_fp64", Q.make_opts(mode=F, fuse_k=5), 2),
+                             ("fused_k5_fp64", Q.make_opts(mode=F, fuse_k=5, c128_pairs=2), 2),
                              ("tensor_k5", Q.make_opts(mode=T), 5)):
         plan = Q.qs_plan_create(n, Q.QS_C128, g, opts)
         Q.qs_state_set_basis(s, x)
@@ -942,7 +942,7 @@ def config_hea(Q, torch, np, st, args):
     c4 = {"workload": "HEA n=24, 576 parameters, 150-term H, adjoint gradient"}
     grads = {}
     T = Q.QS_MODE_TENSOR
-    for dname, dt, variants in (("c128", Q.QS_C128, (("default_fp64", None), ("fp32_pairs", Q.make_opts(c128_pairs=1)),
+    for dname, dt, variants in (("c128", Q.QS_C128, (("fused_fp64", Q.make_opts(mode=Q.QS_MODE_FUSED, c128_pairs=2)), ("default_fp32_pairs", None),
                                                       ("tensor_forward", Q.make_opts(mode=T, c128_pairs=1)))),
                                 ("c64", Q.QS_C64, (("default", None),
                                                    ("tensor_forward", Q.make_opts(mode=T, tc_min_gates=2,
@@ -959,7 +959,7 @@ def config_hea(Q, torch, np, st, args):
             grads[(dname, vname)] = gr
             c4[f"{dname}_{vname}"] = {"ms": spread(walls), "expval": e}
         Q.qs_state_free(s)
-    ref = grads[("c128", "default_fp64")]
+    ref = grads[("c128", "fused_fp64")]
     for k, gr in grads.items():
         c4[f"{k[0]}_{k[1]}"]["max_abs_grad_diff_vs_c128_fp64"] = float(np.abs(gr - ref).max())
     return c4

@@ -139,13 +139,14 @@ typedef struct {
                             the basis composes to the identity, such as a QAOA cost layer; it
                             runs as one sweep multiplying amplitude x by
                             prod_j exp(i alpha_j (-1)^popcount(mask_j & x)) (qs_plan_phase_terms).
-                            reserved[3]: QS_C128 fused plans: 0 = tile passes compute in FP64
-                            (default), 1 = in FP32 pairs ("double-float": each real held as h + l
-                            with two floats, error-free sum and product transformations, about
-                            46 significant bits, relative error near 2^-46 per operation); the
-                            state stays complex128 in memory, split into pairs when a tile is
-                            loaded and joined when it is stored. GB300's FP32 rate is about 64x
-                            its FP64 rate.
+                            reserved[3]: QS_C128 fused and tensor-core plans, arithmetic of the
+                            CUDA-core passes (tile, phase and adjoint reverse-sweep passes):
+                            0 (default) or 1 = FP32 pairs ("double-float": each real held as
+                            h + l with two floats, error-free sum and product transformations,
+                            about 46 significant bits, relative error near 2^-46 per
+                            operation); 2 = FP64. The state stays complex128 in memory, split
+                            into pairs when a tile is loaded and joined when it is stored.
+                            GB300's FP32 rate is about 64x its FP64 rate.
                             reserved[4]: qs_plan_execute_batched schedule: 0 = every pass covers
                             the whole batch (default), 1 = when at least two states fit in 64 MiB
                             (about half the L2), every pass runs on one wave of such states

@@ -207,7 +207,8 @@ def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_m
               fuse_parametric=0, tc_min_gates=0, tc_pipeline=0, phase_min_gates=0, c128_pairs=0,
               batch_l2_waves=0):
     """qs_plan_opts; tc_min_gates, tc_pipeline, phase_min_gates, c128_pairs and batch_l2_waves fill
-    reserved[0..4]."""
+    reserved[0..4] (c128_pairs: 0 or 1 = complex128 CUDA-core passes in FP32 pairs, the default;
+    2 = in FP64)."""
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
     o.paper_mode, o.tc_precision, o.fuse_parametric = paper_mode, tc_precision, fuse_parametric

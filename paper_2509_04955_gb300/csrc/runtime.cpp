@@ -777,10 +777,11 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   po.amp_bytes = (int)amp_bytes(dt);
   // GB300: FP32 FMA 128 lanes/clk/SM, FP64 about 1/59 of that (measured),
   // shared memory 128 B/clk/SM -> one byte costs one FP32 FMA slot.
-  // reserved[3] = 1: complex128 tile passes in FP32 pairs, about 15 FP32
-  // instructions per FMA (a pair product and a pair sum)
-  require(o.reserved[3] == 0 || o.reserved[3] == 1, "complex128 arithmetic (reserved[3]) must be 0 or 1");
-  p->df = dt == QS_C128 && o.reserved[3] == 1;
+  // complex128 CUDA-core passes in FP32 pairs (reserved[3] 0 or 1, the
+  // default) cost about 15 FP32 instructions per FMA (a pair product and a
+  // pair sum); reserved[3] = 2 keeps them in FP64
+  require(o.reserved[3] >= 0 && o.reserved[3] <= 2, "complex128 arithmetic (reserved[3]) must be 0, 1 or 2");
+  p->df = dt == QS_C128 && o.reserved[3] != 2;
   po.fp_weight = dt == QS_C64 ? 1.0 : (p->df ? 15.0 : 59.0);
   po.smem_weight = 1.0;
   po.fuse_parametric = o.fuse_parametric != 0;

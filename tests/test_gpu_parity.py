@@ -131,7 +131,7 @@ def test_qft_n28_c128_full_size_sampled_closed_form():
     gates = W.qft(n)
     rng = np.random.default_rng(0)
     idx = np.unique(rng.integers(0, 1 << n, size=1 << 16))
-    for opts in (Q.make_opts(fuse_k=4), None, Q.make_opts(fuse_k=2, c128_pairs=1)):
+    for opts in (Q.make_opts(fuse_k=4), None, Q.make_opts(fuse_k=2, c128_pairs=2)):
         h = Q.qs_state_alloc(n, Q.QS_C128)
         try:
             Q.qs_state_set_basis(h, x)
@@ -792,8 +792,8 @@ def test_phase_pass_matches_oracle(dtname, maker, n):
     modes = [Q.make_opts(), Q.make_opts(fuse_k=2, phase_min_gates=4)]
     if dt == Q.QS_C64 and n >= 13:
         modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
-    if dt == Q.QS_C128:   # phase and tile passes in FP32 pairs
-        modes.append(Q.make_opts(c128_pairs=1))
+    if dt == Q.QS_C128:   # phase and tile passes in FP64 (FP32 pairs are the default)
+        modes.append(Q.make_opts(c128_pairs=2))
     for opts in modes:
         plan = Q.qs_plan_create(n, dt, gates, opts)
         try:
@@ -818,8 +818,8 @@ def test_phase_pass_batched_rows_use_their_own_parameters(dtname):
     modes = [Q.make_opts(), Q.make_opts(fuse_k=4, fuse_parametric=1)]
     if dt == Q.QS_C64:
         modes.append(Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=4, fuse_parametric=1))
-    else:   # phase and tile passes in FP32 pairs, per-row angles
-        modes.append(Q.make_opts(fuse_k=2, fuse_parametric=1, c128_pairs=1))
+    else:   # phase and tile passes in FP64 (FP32 pairs are the default), per-row angles
+        modes.append(Q.make_opts(fuse_k=2, fuse_parametric=1, c128_pairs=2))
     for opts in modes:
         plan = Q.qs_plan_create(n, dt, gates, opts)
         states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
@@ -1061,7 +1061,7 @@ def test_adjoint_gradient_c128_fp32_pairs_and_options(maker):
     h = Q.qs_state_alloc(n, Q.QS_C128)
     try:
         e, g = Q.qs_adjoint_grad(h, gates, theta, *H, opts=Q.make_opts(c128_pairs=1))
-        e64, g64 = Q.qs_adjoint_grad(h, gates, theta, *H)
+        e64, g64 = Q.qs_adjoint_grad(h, gates, theta, *H, opts=Q.make_opts(c128_pairs=2))
     finally:
         Q.qs_state_free(h)
     assert abs(e - e_ref) <= 1e-12 * scale * 10
@@ -1098,8 +1098,8 @@ def test_phase_pass_complete_graph_many_terms(dtname):
 
 def test_torch_autograd_expval_with_options():
     """Q.expval through torch.autograd: the value and theta.grad equal the
-    oracle's adjoint gradient, with the default plan and with complex128 FP32
-    pairs passed as plan options."""
+    oracle's adjoint gradient, with the default plan (complex128 CUDA-core
+    passes in FP32 pairs) and with FP64 passes asked for in the plan options."""
     import torch
     n = 10
     gates, p = W.hea(n, 3)
@@ -1109,7 +1109,7 @@ def test_torch_autograd_expval_with_options():
     scale = np.abs(H[0]).sum()
     psi0 = Q.State(n, "c128")
     try:
-        for opts in (None, Q.make_opts(c128_pairs=1)):
+        for opts in (None, Q.make_opts(c128_pairs=2)):
             theta = torch.tensor(th0, requires_grad=True)
             e = Q.expval(theta, psi0, gates, H, opts)
             e.backward()

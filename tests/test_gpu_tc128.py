@@ -107,12 +107,13 @@ def test_c128_tensor_core_qft_closed_form_and_oracle():
 
 def test_c128_tensor_core_with_phase_passes_and_tile_passes():
     """QAOA (phase runs as their own passes) and tensor-core thresholds that
-    leave some blocks to CUDA-core tile passes, in FP64 and in FP32 pairs."""
+    leave some blocks to CUDA-core tile passes, in FP32 pairs (the default)
+    and in FP64."""
     n = 14
     qg, p = W.qaoa(n, 2, W.random_regular_graph(n, 3, seed=1))
     th = W.thetas_uniform(p, 3)
     want = O.apply_circuit(O.basis(n, 0), n, qg, th)
-    for tmin, pairs in ((1, 0), (4, 0), (4, 1)):
+    for tmin, pairs in ((1, 0), (4, 2), (4, 1)):
         plan = Q.qs_plan_create(n, Q.QS_C128, qg, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=tmin,
                                                                c128_pairs=pairs))
         try:

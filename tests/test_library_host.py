@@ -86,6 +86,11 @@ def test_theta_bounds_and_options_are_validated():
         Q.qs_plan_create(10, Q.QS_C128, W.qft(10), Q.make_opts(fuse_k=6))   # CUDA-core blocks: k <= 5
     with pytest.raises(Q.QsError):
         Q.qs_plan_create(10, Q.QS_C64, W.qft(10), Q.make_opts(tile_qubits=15))
+    for pairs in (-1, 3):   # complex128 arithmetic: 0 / 1 FP32 pairs (default), 2 FP64
+        with pytest.raises(Q.QsError):
+            Q.qs_plan_create(10, Q.QS_C128, W.qft(10), Q.make_opts(c128_pairs=pairs))
+    for pairs in (0, 1, 2):
+        Q.qs_plan_free(Q.qs_plan_create(10, Q.QS_C128, W.qft(10), Q.make_opts(c128_pairs=pairs)))
 
 
 def test_gate_count_limit_is_checked_before_the_list_is_read():
