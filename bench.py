@@ -969,7 +969,7 @@ def config_hea(Q, torch, np, st, args):
 KERNEL_SOURCES = {"k_tc_bulk": ("kernels_tc.cu", "tcgen05.cuh", "cplx.cuh"),
                   "k_tc_block": ("kernels_tc.cu", "tcgen05.cuh", "cplx.cuh"),
                   "k_tc128": ("kernels_tc128.cu", "tcgen05.cuh"),
-                  "k_tile": ("kernels_tile.cuh", "cplx.cuh", "dfloat.cuh", "qs_internal.h")}
+                  "k_tile": ("kernels_tile.cuh", "cplx.cuh", "dfloat.cuh", "qs_internal.h", "tcgen05.cuh")}
 
 
 def kernel_hash(kernel: str) -> str:

@@ -150,7 +150,14 @@ typedef struct {
                             reserved[4]: qs_plan_execute_batched schedule: 0 = every pass covers
                             the whole batch (default), 1 = when at least two states fit in 64 MiB
                             (about half the L2), every pass runs on one wave of such states
-                            before the next wave (passes then read L2, not HBM; more launches). */
+                            before the next wave (passes then read L2, not HBM; more launches).
+                            reserved[5]: tile passes' staging: 0 (default) or 1 = every thread
+                            loads and stores 16-byte vectors; 2 = the bulk-copy (TMA) engine
+                            moves each run of 2^low_qubits amplitudes into one of two
+                            shared-memory tile buffers (the next tile loads while the ops run
+                            on this one) and back, where the runs are at least 16 bytes and two
+                            tiles fit (complex64 and FP64 tiles; FP32-pair tiles keep the
+                            vector path). Its waits are bounded like the tensor-core passes'. */
 } qs_plan_opts;
 
 /* Statistics of a plan (Fig. 16's compression ratio uses gates/blocks). */
@@ -165,7 +172,7 @@ typedef struct {
   int32_t max_block_qubits;
   int32_t tile_qubits;
   int32_t low_qubits;
-  int32_t reserved[5];
+  int32_t reserved[5];   /* reserved[0]: tile passes staged by bulk copies (qs_plan_opts reserved[5]) */
 } qs_plan_info;
 
 typedef struct qs_state_s* qs_state_t;
@@ -464,7 +471,8 @@ qs_status qs_plan_timing_read(qs_plan_t p, double* total_ms, int64_t* launches);
 qs_status qs_plan_timing_read_kinds(qs_plan_t p, double* total_ms, int64_t* launches, double* kind_ms,
                                     int64_t* kind_launches);
 
-/* Bounded waits of the tensor-core passes: every wait of their pipelines
+/* Bounded waits of the tensor-core passes and of bulk-staged tile passes
+ * (reserved[5] = 2): every wait of their pipelines
  * (a landing slot, an operand, an accumulator) polls an mbarrier at most
  * `polls` times (0 = the default bound, 2^26 polls that may each suspend the
  * thread briefly; below 64, immediate non-blocking checks) before the pass

@@ -60,7 +60,9 @@ class QsPlanInfo(C.Structure):
                 ("reserved", C.c_int32 * 5)]
 
     def as_dict(self) -> dict:
-        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d = {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+        d["bulk_tile_passes"] = self.reserved[0]
+        return d
 
 
 class QsStreamInfo(C.Structure):
@@ -205,10 +207,10 @@ def _dptr(a):
 
 def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_mode=0, tc_precision=0,
               fuse_parametric=0, tc_min_gates=0, tc_pipeline=0, phase_min_gates=0, c128_pairs=0,
-              batch_l2_waves=0):
+              batch_l2_waves=0, tile_staging=0):
     """qs_plan_opts; tc_min_gates, tc_pipeline, phase_min_gates, c128_pairs and batch_l2_waves fill
     reserved[0..4] (c128_pairs: 0 or 1 = complex128 CUDA-core passes in FP32 pairs, the default;
-    2 = in FP64)."""
+    2 = in FP64; tile_staging fills reserved[5]: 2 = tile passes staged by bulk copies)."""
     o = QsPlanOpts()
     o.mode, o.fuse_k, o.tile_qubits, o.low_qubits = mode, fuse_k, tile_qubits, low_qubits
     o.paper_mode, o.tc_precision, o.fuse_parametric = paper_mode, tc_precision, fuse_parametric
@@ -217,6 +219,7 @@ def make_opts(mode=QS_MODE_FUSED, fuse_k=0, tile_qubits=0, low_qubits=0, paper_m
     o.reserved[2] = phase_min_gates
     o.reserved[3] = c128_pairs
     o.reserved[4] = batch_l2_waves
+    o.reserved[5] = tile_staging
     return o
 
 
@@ -332,7 +335,8 @@ def qs_tune_cache_clear():
 def opts_dict(o: QsPlanOpts) -> dict:
     return {"mode": o.mode, "fuse_k": o.fuse_k, "tile_qubits": o.tile_qubits, "low_qubits": o.low_qubits,
             "tc_min_gates": o.reserved[0], "tc_precision": o.tc_precision, "tc_pipeline": o.reserved[1],
-            "phase_min_gates": o.reserved[2], "c128_pairs": o.reserved[3]}
+            "phase_min_gates": o.reserved[2], "c128_pairs": o.reserved[3],
+            "tile_staging": o.reserved[5]}
 
 
 def qs_apply_circuit(state: int, gates, theta=None, opts: QsPlanOpts | None = None):

@@ -71,7 +71,7 @@ void check_tune_args(int n, qs_dtype dt, const qs_gate* gates, size_t ng) {
 
 std::vector<qs_plan_opts> tune_candidates(int n, qs_dtype dt) {
   std::vector<qs_plan_opts> c;
-  auto add = [&](int mode, int k, int m, int L, int tcmin) {
+  auto add = [&](int mode, int k, int m, int L, int tcmin, int staging = 0) {
     qs_plan_opts o;
     std::memset(&o, 0, sizeof(o));
     o.mode = mode;
@@ -79,6 +79,7 @@ std::vector<qs_plan_opts> tune_candidates(int n, qs_dtype dt) {
     o.tile_qubits = m;
     o.low_qubits = L;
     o.reserved[0] = tcmin;
+    o.reserved[5] = staging;
     c.push_back(o);
   };
   add(QS_MODE_PER_GATE, 0, 0, 0, 0);
@@ -87,6 +88,7 @@ std::vector<qs_plan_opts> tune_candidates(int n, qs_dtype dt) {
     if (dt == QS_C64) {
       add(QS_MODE_FUSED, k, 12, 4, 0);
       add(QS_MODE_FUSED, k, 13, 4, 0);
+      add(QS_MODE_FUSED, k, 12, 5, 0, 2);   // tiles staged by bulk copies (256-byte runs)
     } else {
       add(QS_MODE_FUSED, k, 11, 3, 0);
       add(QS_MODE_FUSED, k, 12, 4, 0);

@@ -11,20 +11,25 @@ size_t tile_smem_bytes(int m, int nhigh, int mbuf_elems, qs_dtype dt) {
   return (amp << m) + 8 * runs + amp * (size_t)(mbuf_elems < 16 ? 16 : mbuf_elems);
 }
 
+size_t tile_pass_smem_bytes(const PassDesc& p, qs_dtype dt) {
+  const size_t amp = dt == QS_C64 ? 8 : 16;
+  return tile_smem_bytes(p.m, p.nhigh, p.mbuf_elems, dt) + (p.bulk ? (amp << p.m) + 16 : 0);
+}
+
 cudaError_t launch_tile_pass_batched(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
                                      int64_t brow0, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,
                                      const double2* gtab, const double2* btab, cudaStream_t st) {
-  const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.mbuf_elems, dt);
+  const size_t smem = tile_pass_smem_bytes(p, dt);
   if (dt == QS_C64) return launch_tile_f32(p.kmax, psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem);
   if (p.df) return launch_tile_df(p.kmax, psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem);
   return launch_tile_f64(p.kmax, psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem);
 }
 
 cudaError_t prepare_tile_pass(const PassDesc& p, qs_dtype dt) {
-  const size_t smem = tile_smem_bytes(p.m, p.nhigh, p.mbuf_elems, dt);
-  if (dt == QS_C64) return prepare_tile_f32(p.kmax, smem);
-  if (p.df) return prepare_tile_df(p.kmax, smem);
-  return prepare_tile_f64(p.kmax, smem);
+  const size_t smem = tile_pass_smem_bytes(p, dt);
+  if (dt == QS_C64) return prepare_tile_f32(p.kmax, p.bulk != 0, smem);
+  if (p.df) return prepare_tile_df(p.kmax, false, smem);
+  return prepare_tile_f64(p.kmax, p.bulk != 0, smem);
 }
 
 cudaError_t launch_tile_pass(void* psi, int n, qs_dtype dt, const PassDesc& p, const DevOp* ops,

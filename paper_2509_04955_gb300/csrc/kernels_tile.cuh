@@ -27,6 +27,7 @@
 #include "cplx.cuh"
 #include "dfloat.cuh"
 #include "qs_internal.h"
+#include "tcgen05.cuh"
 
 namespace qs {
 
@@ -304,6 +305,34 @@ __device__ __forceinline__ void apply_diag_op(typename V2<R>::T* tile, int m, co
   }
 }
 
+// The ops of a pass applied, in order, to the tile in shared memory (a barrier
+// after each op).
+template <typename R, int KMAX>
+__device__ __forceinline__ void tile_apply_ops(typename V2<R>::T* tile, const PassDesc& p, const DevOp* __restrict__ ops,
+                                               const double2* __restrict__ gtab, const double2* __restrict__ btab,
+                                               int64_t brow0, int64_t bstride, uint64_t sb,
+                                               typename V2<R>::T* mbuf) {
+  const int m = p.m;
+  for (int o = p.op_begin; o < p.op_end; ++o) {
+    const DevOp op = ops[o];
+    if (op.type == OP_GATE) {
+      apply_gate_op<R>(tile, m, op, gtab, mbuf);
+    } else {
+      const double2* __restrict__ bt = op.per_row ? btab + (brow0 + (int64_t)sb) * bstride : btab;
+      if (op.type == OP_DIAG) {
+        apply_diag_op<R>(tile, m, op, bt, mbuf);
+      } else {
+        if (op.k == 1) apply_dense_op<R, 1>(tile, m, op, bt, mbuf);
+        else if (op.k == 2) apply_dense_op<R, 2>(tile, m, op, bt, mbuf);
+        if constexpr (KMAX >= 3) { if (op.k == 3) apply_dense_op<R, 3>(tile, m, op, bt, mbuf); }
+        if constexpr (KMAX >= 4) { if (op.k == 4) apply_dense_op<R, 4>(tile, m, op, bt, mbuf); }
+        if constexpr (KMAX >= 5) { if (op.k == 5) apply_dense_op<R, 5>(tile, m, op, bt, mbuf); }
+      }
+    }
+    __syncthreads();
+  }
+}
+
 // Gate-only passes (KMAX <= 2) keep two CTAs per SM (load of one tile overlaps
 // the ops of the other); wider dense ops need more registers.
 template <typename R, int KMAX>
@@ -341,51 +370,142 @@ __global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile(typena
     if constexpr (kDF) tile_io_df<true>(psi, tile, base, segoff, size, L, lmask);
     else tile_io<C, C2, VPT, true>(psi, tile, base, segoff, size, L, lmask);
     __syncthreads();
-    for (int o = p.op_begin; o < p.op_end; ++o) {
-      const DevOp op = ops[o];
-      if (op.type == OP_GATE) {
-        apply_gate_op<R>(tile, m, op, gtab, mbuf);
-      } else {
-        const double2* __restrict__ bt = op.per_row ? btab + (brow0 + (int64_t)sb) * bstride : btab;
-        if (op.type == OP_DIAG) {
-          apply_diag_op<R>(tile, m, op, bt, mbuf);
-        } else {
-          if (op.k == 1) apply_dense_op<R, 1>(tile, m, op, bt, mbuf);
-          else if (op.k == 2) apply_dense_op<R, 2>(tile, m, op, bt, mbuf);
-          if constexpr (KMAX >= 3) { if (op.k == 3) apply_dense_op<R, 3>(tile, m, op, bt, mbuf); }
-          if constexpr (KMAX >= 4) { if (op.k == 4) apply_dense_op<R, 4>(tile, m, op, bt, mbuf); }
-          if constexpr (KMAX >= 5) { if (op.k == 5) apply_dense_op<R, 5>(tile, m, op, bt, mbuf); }
-        }
-      }
-      __syncthreads();
-    }
+    tile_apply_ops<R, KMAX>(tile, p, ops, gtab, btab, brow0, bstride, sb, mbuf);
     if constexpr (kDF) tile_io_df<false>(psi, tile, base, segoff, size, L, lmask);
     else tile_io<C, C2, VPT, false>(psi, tile, base, segoff, size, L, lmask);
     __syncthreads();
   }
 }
 
+// The same pass with the tile moved by the bulk-copy (TMA) engine: each run
+// of 2^L contiguous amplitudes is one cp.async.bulk of at least 16 bytes, into
+// one of two shared-memory tile buffers, so the next tile streams in while the
+// ops run on this one, and the tile goes back to HBM by bulk stores from the
+// same buffer. Warp 0 issues the copies (its lane j takes runs j, j + 32, ...);
+// a tile buffer is loaded again only after the stores from it have been read
+// out (cp.async.bulk.wait_group.read). Waits for a tile are bounded by p.spin
+// polls: when one runs out the CTA records *p.err = 1, waits for the copies it
+// issued and returns. Complex64 and FP64 tiles only (FP32-pair tiles are
+// converted on the way in).
+template <typename R, int KMAX>
+__global__ void __launch_bounds__(kTileThreads, KMAX <= 2 ? 2 : 1) k_tile_bulk(typename V2<R>::T* __restrict__ psi0,
+                                                           void* const* __restrict__ psis, int64_t gstride,
+                                                           int64_t bstride, PassDesc p, const DevOp* __restrict__ ops,
+                                                           const double2* __restrict__ gtab0,
+                                                           const double2* __restrict__ btab, int64_t brow0,
+                                                           int lg_tiles, uint64_t total) {
+  using C = typename V2<R>::T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int m = p.m, L = p.L, nh = p.nhigh;
+  const uint32_t size = 1u << m;
+  C* tiles = (C*)smem;                                            // two buffers of 2^m amplitudes
+  uint64_t* segoff = (uint64_t*)(tiles + 2 * size);
+  C* mbuf = (C*)(segoff + ((1u << nh) < 2 ? 2 : (1u << nh)));
+  uint64_t* full = (uint64_t*)(mbuf + (p.mbuf_elems < 16 ? 16 : p.mbuf_elems));   // [2]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const uint32_t spin = p.spin ? p.spin : kTcSpinLimit;
+  const uint32_t nruns = 1u << nh, runb = (uint32_t)sizeof(C) << L;
+  for (uint32_t s = threadIdx.x; s < nruns; s += kTileThreads) {
+    uint64_t o = 0;
+    for (int k = 0; k < nh; ++k) o |= (uint64_t)((s >> k) & 1u) << p.high[k];
+    segoff[s] = o;
+  }
+  if (threadIdx.x == 0) {
+    for (int b = 0; b < 2; ++b) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(full + b)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  __syncthreads();
+  const uint64_t my = blockIdx.x < total ? (total - blockIdx.x + gridDim.x - 1) / gridDim.x : 0;
+  auto tile_at = [&](uint64_t i, C*& psi, uint64_t& base, uint64_t& sb) {
+    const uint64_t tt = blockIdx.x + i * gridDim.x;
+    sb = tt >> lg_tiles;
+    psi = psis ? (C*)psis[sb] : psi0;
+    base = insert_zero_bits((tt & ((1ull << lg_tiles) - 1)) << L, p.high, nh);
+  };
+  // warp 0 only: the runs of tile i into buffer i & 1
+  auto issue_load = [&](uint64_t i) {
+    C* psi;
+    uint64_t base, sb;
+    tile_at(i, psi, base, sb);
+    const int b = (int)(i & 1);
+    if (lane == 0)
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(full + b)),
+                   "r"((uint32_t)(size * sizeof(C)))
+                   : "memory");
+    __syncwarp();
+    for (uint32_t j = lane; j < nruns; j += 32)
+      asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                       smem_u32(tiles + (size_t)b * size + (size_t)j * (1u << L))),
+                   "l"(psi + (base | segoff[j])), "r"(runb), "r"(smem_u32(full + b))
+                   : "memory");
+  };
+  if (warp == 0 && my > 0) issue_load(0);
+  uint64_t i = 0;
+  bool timed_out = false;
+  for (; i < my; ++i) {
+    const int b = (int)(i & 1);
+    if (warp == 0 && i + 1 < my) {
+      // buffer b ^ 1 last held tile i - 1: its stores must have read it out
+      asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory");
+      issue_load(i + 1);
+    }
+    const bool ok = mbar_wait(smem_u32(full + b), (uint32_t)((i >> 1) & 1), spin);
+    if (__syncthreads_or(!ok)) {
+      timed_out = true;
+      break;
+    }
+    C* psi;
+    uint64_t base, sb;
+    tile_at(i, psi, base, sb);
+    C* tile = tiles + (size_t)b * size;
+    tile_apply_ops<R, KMAX>(tile, p, ops, gtab0 + sb * gstride, btab, brow0, bstride, sb, mbuf);
+    if (warp == 0) {
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // the ops' writes, before the bulk reads
+      for (uint32_t j = lane; j < nruns; j += 32)
+        asm volatile("cp.async.bulk.global.shared::cta.bulk_group [%0], [%1], %2;" ::"l"(psi + (base | segoff[j])),
+                     "r"(smem_u32(tile + (size_t)j * (1u << L))), "r"(runb)
+                     : "memory");
+      asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+    }
+  }
+  if (warp == 0) {
+    if (timed_out) {
+      if (lane == 0) atomicExch(p.err, 1);
+      // the loads issued for tiles i and i + 1 land before the CTA exits
+      mbar_wait(smem_u32(full + (i & 1)), (uint32_t)((i >> 1) & 1));
+      if (i + 1 < my) mbar_wait(smem_u32(full + ((i + 1) & 1)), (uint32_t)(((i + 1) >> 1) & 1));
+    }
+    asm volatile("cp.async.bulk.wait_group 0;" ::: "memory");   // stores complete
+  }
+}
+
 // Per kernel instance: the largest dynamic shared memory configured so far
 // and the resident CTAs per SM at that size. Set up by prepare_tile_pass
 // (host side, outside any stream capture) before the first launch.
-template <typename R, int KMAX>
+template <typename R, int KMAX, bool BULK>
 struct TileCfg {
   static int bytes, per_sm;
 };
-template <typename R, int KMAX> int TileCfg<R, KMAX>::bytes = 0;
-template <typename R, int KMAX> int TileCfg<R, KMAX>::per_sm = 0;
+template <typename R, int KMAX, bool BULK> int TileCfg<R, KMAX, BULK>::bytes = 0;
+template <typename R, int KMAX, bool BULK> int TileCfg<R, KMAX, BULK>::per_sm = 0;
 
-template <typename R, int KMAX>
+template <typename R, int KMAX, bool BULK>
+static const void* tile_kernel() {
+  if constexpr (BULK) return (const void*)k_tile_bulk<R, KMAX>;
+  else return (const void*)k_tile<R, KMAX>;
+}
+
+template <typename R, int KMAX, bool BULK>
 static cudaError_t prepare_tile_t(size_t smem) {
-  if ((int)smem <= TileCfg<R, KMAX>::bytes) return cudaSuccess;
-  cudaError_t e = cudaFuncSetAttribute(k_tile<R, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if ((int)smem <= TileCfg<R, KMAX, BULK>::bytes) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(tile_kernel<R, KMAX, BULK>(), cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   int per_sm = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_tile<R, KMAX>, kTileThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, tile_kernel<R, KMAX, BULK>(), kTileThreads, smem);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) return cudaErrorInvalidConfiguration;
-  TileCfg<R, KMAX>::bytes = (int)smem;
-  TileCfg<R, KMAX>::per_sm = per_sm;
+  TileCfg<R, KMAX, BULK>::bytes = (int)smem;
+  TileCfg<R, KMAX, BULK>::per_sm = per_sm;
   return cudaSuccess;
 }
 
@@ -399,18 +519,24 @@ static int sm_count() {
   return sms;
 }
 
-template <typename R, int KMAX>
+template <typename R, int KMAX, bool BULK>
 static cudaError_t launch_tile_t(void* psi, void* const* psis, int nstates, int64_t gstride, int64_t bstride,
                                  int64_t brow0, int n, const PassDesc& p, const DevOp* ops, const double2* gtab,
                                  const double2* btab, cudaStream_t st, size_t smem) {
-  if ((int)smem > TileCfg<R, KMAX>::bytes) return cudaErrorInvalidConfiguration;   // not prepared
-  const int per_sm = TileCfg<R, KMAX>::per_sm;
+  if ((int)smem > TileCfg<R, KMAX, BULK>::bytes) return cudaErrorInvalidConfiguration;   // not prepared
+  const int per_sm = TileCfg<R, KMAX, BULK>::per_sm;
   const int sms = sm_count();
   const uint64_t ntiles = 1ull << (n - p.m), total = ntiles * (uint64_t)nstates;
   uint64_t grid = (uint64_t)sms * per_sm;
   if (grid > total) grid = total;
-  k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename GAmp<R>::T*)psi, psis, gstride, bstride, p,
-                                                                ops, gtab, btab, brow0, n - p.m, total);
+  if constexpr (BULK) {
+    if (p.err == nullptr) return cudaErrorInvalidValue;
+    k_tile_bulk<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename V2<R>::T*)psi, psis, gstride, bstride,
+                                                                      p, ops, gtab, btab, brow0, n - p.m, total);
+  } else {
+    k_tile<R, KMAX><<<(unsigned)grid, kTileThreads, smem, st>>>((typename GAmp<R>::T*)psi, psis, gstride, bstride, p,
+                                                                  ops, gtab, btab, brow0, n - p.m, total);
+  }
   note_launch();
   return cudaGetLastError();
 }
@@ -428,7 +554,11 @@ static cudaError_t launch_tile_range(int kmax, void* psi, void* const* psis, int
   const int k = kmax < 2 ? 2 : kmax;
 #define QS_TILE_CASE(K)                                                                                  \
   if constexpr (KLO <= K && K <= KHI)                                                                    \
-    if (k == K) return launch_tile_t<R, K>(psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem);
+    if (k == K) {                                                                                        \
+      if constexpr (!std::is_same<R, dfl>::value)                                                        \
+        if (p.bulk) return launch_tile_t<R, K, true>(psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem); \
+      return launch_tile_t<R, K, false>(psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem); \
+    }
   QS_TILE_CASE(2)
   QS_TILE_CASE(3)
   QS_TILE_CASE(4)
@@ -438,13 +568,17 @@ static cudaError_t launch_tile_range(int kmax, void* psi, void* const* psis, int
 }
 
 template <typename R, int KLO, int KHI>
-static cudaError_t prepare_tile_range(int kmax, size_t smem) {
+static cudaError_t prepare_tile_range(int kmax, bool bulk, size_t smem) {
   sm_count();   // this translation unit's SM count, read here rather than during a stream capture
   if (kmax < 0 || kmax > 5) return cudaErrorInvalidValue;
   const int k = kmax < 2 ? 2 : kmax;
 #define QS_TILE_CASE(K)                                  \
   if constexpr (KLO <= K && K <= KHI)                    \
-    if (k == K) return prepare_tile_t<R, K>(smem);
+    if (k == K) {                                        \
+      if constexpr (!std::is_same<R, dfl>::value)        \
+        if (bulk) return prepare_tile_t<R, K, true>(smem); \
+      return prepare_tile_t<R, K, false>(smem);           \
+    }
   QS_TILE_CASE(2)
   QS_TILE_CASE(3)
   QS_TILE_CASE(4)
@@ -457,7 +591,7 @@ static cudaError_t prepare_tile_range(int kmax, size_t smem) {
   cudaError_t launch_tile_##SUFFIX(int kmax, void* psi, void* const* psis, int nstates, int64_t gstride,   \
                                    int64_t bstride, int64_t brow0, int n, const PassDesc& p, const DevOp* ops, \
                                    const double2* gtab, const double2* btab, cudaStream_t st, size_t smem); \
-  cudaError_t prepare_tile_##SUFFIX(int kmax, size_t smem);
+  cudaError_t prepare_tile_##SUFFIX(int kmax, bool bulk, size_t smem);
 QS_TILE_PART_DECL(f32)
 QS_TILE_PART_DECL(f64)
 QS_TILE_PART_DECL(df)

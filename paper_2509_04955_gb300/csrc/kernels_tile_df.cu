@@ -12,9 +12,9 @@ cudaError_t launch_tile_df(int kmax, void* psi, void* const* psis, int nstates, 
   return launch_tile_range<dfl, 2, 4>(kmax, psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem);
 }
 
-cudaError_t prepare_tile_df(int kmax, size_t smem) {
-  if (kmax == 5) return prepare_tile_df5(kmax, smem);
-  return prepare_tile_range<dfl, 2, 4>(kmax, smem);
+cudaError_t prepare_tile_df(int kmax, bool bulk, size_t smem) {
+  if (kmax == 5) return prepare_tile_df5(kmax, bulk, smem);
+  return prepare_tile_range<dfl, 2, 4>(kmax, bulk, smem);
 }
 
 }  // namespace qs

@@ -10,8 +10,8 @@ cudaError_t launch_tile_f32(int kmax, void* psi, void* const* psis, int nstates,
   return launch_tile_range<float, 2, 5>(kmax, psi, psis, nstates, gstride, bstride, brow0, n, p, ops, gtab, btab, st, smem);
 }
 
-cudaError_t prepare_tile_f32(int kmax, size_t smem) {
-  return prepare_tile_range<float, 2, 5>(kmax, smem);
+cudaError_t prepare_tile_f32(int kmax, bool bulk, size_t smem) {
+  return prepare_tile_range<float, 2, 5>(kmax, bulk, smem);
 }
 
 }  // namespace qs

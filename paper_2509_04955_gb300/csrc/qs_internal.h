@@ -166,12 +166,17 @@ struct PassDesc {
   int32_t mbuf_elems;      // matrix staging entries the pass needs (max over its ops)
   int32_t op_begin, op_end;
   int32_t df;              // complex128 tile computed in FP32 pairs (double-float), else FP64
+  int32_t bulk;            // tiles moved by bulk asynchronous copies into two shared-memory buffers
+  uint32_t spin;           // bulk staging: polls per wait for a tile (0 = default bound)
+  int* err;                // bulk staging: device error flag (set to 1 when a wait runs out)
 };
 
 // Kernel attributes / occupancy of a pass's instance; host side, never during a capture.
 cudaError_t prepare_tile_pass(const PassDesc& p, qs_dtype dt);
 // Shared memory of one tile CTA: tile + run offsets + matrix staging buffer.
 size_t tile_smem_bytes(int m, int nhigh, int mbuf_elems, qs_dtype dt);
+// The same for a pass as launched: with bulk staging, a second tile buffer and two barriers.
+size_t tile_pass_smem_bytes(const PassDesc& p, qs_dtype dt);
 
 // ---------------------------------------------------------------------------
 // Bit helpers.

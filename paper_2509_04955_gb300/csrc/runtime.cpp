@@ -165,8 +165,10 @@ void issue_circuit(qs_plan_s& p, void* psi, int row, cudaStream_t st, bool timed
     if (p.mode == QS_MODE_PER_GATE) {
       CK(launch_gate(psi, p.n, p.dt, p.dgates[i], gtab + i * 16, false, st));
     } else if (p.steps[i].kind == 0) {
-      CK(launch_tile_pass(psi, p.n, p.dt, p.pdesc[p.steps[i].idx], p.d_ops.as<DevOp>(), gtab,
-                          p.d_btab.as<double2>(), 0, st));
+      PassDesc pd = p.pdesc[p.steps[i].idx];
+      pd.err = p.d_err.as<int>();
+      pd.spin = p.tc_spin;
+      CK(launch_tile_pass(psi, p.n, p.dt, pd, p.d_ops.as<DevOp>(), gtab, p.d_btab.as<double2>(), 0, st));
     } else if (p.steps[i].kind == 2) {
       const double* th = p.theta_needed ? p.d_theta.as<double>() + (size_t)row * p.theta_stride : nullptr;
       CK(launch_phase_pass(psi, nullptr, 1, p.n, p.dt, p.d_pterms.as<DevPhaseTerm>(), p.phdesc[p.steps[i].idx], th,
@@ -214,7 +216,10 @@ void issue_circuit_batched(qs_plan_s& p, void* const* d_psis, int B, cudaStream_
                              p.theta_needed ? p.d_theta.as<double>() + (size_t)w0 * p.theta_stride : nullptr,
                              p.theta_stride, st));
       } else if (stp.kind == 0) {
-        CK(launch_tile_pass_batched(nullptr, ps, nb, (int64_t)(16 * G), p.btab_elems, w0, p.n, p.dt, p.pdesc[stp.idx],
+        PassDesc pd = p.pdesc[stp.idx];
+        pd.err = p.d_err.as<int>();
+        pd.spin = p.tc_spin;
+        CK(launch_tile_pass_batched(nullptr, ps, nb, (int64_t)(16 * G), p.btab_elems, w0, p.n, p.dt, pd,
                                     p.d_ops.as<DevOp>(), p.d_gtab.as<double2>() + (size_t)w0 * 16 * G,
                                     p.d_btab.as<double2>(), st));
       } else {
@@ -259,14 +264,14 @@ void execute(qs_plan_s& p, qs_state_s& s, const double* theta, size_t ntheta) {
 // Reads the tensor-core passes' error flag after the work queued on `st`,
 // clears it for the next execution and reports a timeout.
 void check_tc_error(qs_plan_s& p, cudaStream_t st) {
-  if (!p.has_tc()) return;
+  if (!p.has_tc() && !p.has_bulk_tiles()) return;
   int err = 0;
   CK(cudaMemcpyAsync(&err, p.d_err.p, sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   if (err) {
     CK(cudaMemsetAsync(p.d_err.p, 0, sizeof(int), st));
     CK(cudaStreamSynchronize(st));
-    throw Error(QS_ERR_TIMEOUT, "tensor-core pass: a pipeline wait ran out of polls");
+    throw Error(QS_ERR_TIMEOUT, "tensor-core or bulk-staged tile pass: a pipeline wait ran out of polls");
   }
 }
 
@@ -476,6 +481,12 @@ void emit_tile_passes(qs_plan_s& P, const std::vector<OpRec>& ops, const std::ve
     pd.op_end = (int)P.dops.size();
     require(tile_smem_bytes(pd.m, pd.nhigh, pd.mbuf_elems, dt) <= 227 * 1024,
             "tile does not fit in shared memory: lower tile_qubits");
+    // reserved[5] = 2: runs of at least 16 bytes moved by bulk copies into two
+    // tile buffers, where both fit (FP32-pair tiles keep the register path)
+    const size_t amp = dt == QS_C64 ? 8 : 16;
+    pd.bulk = (P.opts.reserved[5] == 2 && !pd.df && ((amp << pd.L) % 16) == 0) ? 1 : 0;
+    if (pd.bulk && tile_pass_smem_bytes(pd, dt) > 227 * 1024) pd.bulk = 0;
+    in.reserved[0] += pd.bulk;
     P.steps.push_back({0, (int)P.pdesc.size()});
     P.pdesc.push_back(pd);
     P.pass_tiles.push_back(pr.tile);
@@ -781,6 +792,7 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   // default) cost about 15 FP32 instructions per FMA (a pair product and a
   // pair sum); reserved[3] = 2 keeps them in FP64
   require(o.reserved[3] >= 0 && o.reserved[3] <= 2, "complex128 arithmetic (reserved[3]) must be 0, 1 or 2");
+  require(o.reserved[5] >= 0 && o.reserved[5] <= 2, "tile staging (reserved[5]) must be 0, 1 or 2");
   p->df = dt == QS_C128 && o.reserved[3] != 2;
   po.fp_weight = dt == QS_C64 ? 1.0 : (p->df ? 15.0 : 59.0);
   po.smem_weight = 1.0;

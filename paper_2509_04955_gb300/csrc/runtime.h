@@ -183,6 +183,11 @@ struct qs_plan_s {
   int64_t wimg_pass = 32768;       // uint16 elements per pass in h_wimg / d_wimg
   uint32_t tc_spin = 0;            // polls per tensor-core pipeline wait (0 = default bound)
   bool has_tc() const { return !tcdesc.empty() || !tc5desc.empty(); }
+  bool has_bulk_tiles() const {
+    for (const PassDesc& d : pdesc)
+      if (d.bulk) return true;
+    return false;
+  }
   int tc_prec = 3;
   int tc_pipe = 0;                 // single-state tensor-core pass: 0 bulk-copy staged, 1 register-staged
   bool df = false;                 // complex128 tile passes computed in FP32 pairs

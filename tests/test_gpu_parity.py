@@ -1212,3 +1212,88 @@ def test_one_shot_batched_apply(dtname, n, opts):
 def C_stream(s):
     import ctypes
     return ctypes.c_void_p(s.cuda_stream)
+
+
+BULK = [dict(fuse_k=1, tile_qubits=10, low_qubits=1), dict(fuse_k=2, tile_qubits=12, low_qubits=4),
+        dict(fuse_k=3, tile_qubits=11, low_qubits=2), dict(fuse_k=5, tile_qubits=12, low_qubits=3),
+        dict(paper_mode=1, tile_qubits=9, low_qubits=2)]
+
+
+@pytest.mark.parametrize("dtname", ["c64", "c128"])
+@pytest.mark.parametrize("n", [9, 12, 17])
+def test_bulk_staged_tile_passes_match_oracle(dtname, n):
+    """Tile passes whose tiles are moved by bulk copies into two shared-memory
+    buffers (tile_staging=2; complex128 in FP64, the tiles the bulk path
+    takes): gate mixes with controls above and below their targets, every
+    fusion width, runs of 16 bytes to 256 bytes, states of one tile up to
+    thousands of tiles per pass, against the oracle."""
+    dt = DT[dtname]
+    gates = W.random_gate_mix(n, 80, seed=n + 5) + W.random_layered(n, 4, seed=n)
+    psi0 = W.random_state(n, n)
+    want = ref(n, gates, psi0=psi0)
+    for kw in BULK:
+        kw = dict(kw, tile_qubits=min(kw["tile_qubits"], n))
+        opts = Q.make_opts(tile_staging=2, c128_pairs=2, **kw)
+        plan = Q.qs_plan_create(n, dt, gates, opts)
+        try:
+            info = Q.qs_plan_info_get(plan)
+            assert info["bulk_tile_passes"] == info["passes"] > 0, kw
+        finally:
+            Q.qs_plan_free(plan)
+        got = run(n, dt, gates, psi0=psi0, opts=opts)
+        assert np.abs(got - want).max() <= TOL[dt], (kw, np.abs(got - want).max())
+
+
+@pytest.mark.parametrize("dtname", ["c64", "c128"])
+def test_bulk_staged_tile_passes_batched_with_parameters(dtname):
+    """Batched execution (one launch per pass over all states, parametric
+    blocks rebuilt per row) with bulk-staged tiles: every row against the
+    oracle after a graph capture and a replay."""
+    dt = DT[dtname]
+    n, Bsz = 13, 6
+    gates, p = W.hea(n, 3)
+    thetas = np.stack([W.thetas_uniform(p, 60 + b) for b in range(Bsz)])
+    opts = Q.make_opts(fuse_k=3, fuse_parametric=1, tile_staging=2, c128_pairs=2)
+    plan = Q.qs_plan_create(n, dt, gates, opts)
+    states = [Q.qs_state_alloc(n, dt) for _ in range(Bsz)]
+    try:
+        assert Q.qs_plan_info_get(plan)["bulk_tile_passes"] > 0
+        for _ in range(2):
+            for s in states:
+                Q.qs_state_set_basis(s, 0)
+            Q.qs_plan_execute_batched(plan, states, thetas)
+        for b in range(Bsz):
+            out = np.empty(1 << n, dtype=Q.NP_DTYPE[dt])
+            Q.qs_state_copy_to_host(states[b], out)
+            assert np.abs(out - ref(n, gates, thetas[b])).max() <= TOL[dt], b
+    finally:
+        for s in states:
+            Q.qs_state_free(s)
+        Q.qs_plan_free(plan)
+
+
+def test_bulk_staged_tile_pass_wait_timeout_returns_error_and_recovers():
+    """Failure detection for the bulk-staged tile pass: with a wait limit of 2
+    immediate polls the first wait for a tile runs out, the CTAs let their
+    copies land and return, and the execution reports QS_ERR_TIMEOUT; with the
+    default limit the same plan then matches the oracle."""
+    n = 16
+    gates = W.random_layered(n, 4, seed=8)
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(fuse_k=2, tile_staging=2))
+    h = Q.qs_state_alloc(n, Q.QS_C64)
+    try:
+        assert Q.qs_plan_info_get(plan)["bulk_tile_passes"] > 0
+        Q.qs_plan_set_wait_limit(plan, 2)
+        Q.qs_state_set_basis(h, 0)
+        with pytest.raises(Q.QsError) as e:
+            Q.qs_plan_execute(plan, h)
+        assert e.value.status == Q.QS_ERR_TIMEOUT
+        Q.qs_plan_set_wait_limit(plan, 0)
+        Q.qs_state_set_basis(h, 0)
+        Q.qs_plan_execute(plan, h)
+        out = np.empty(1 << n, dtype=np.complex64)
+        Q.qs_state_copy_to_host(h, out)
+    finally:
+        Q.qs_state_free(h)
+        Q.qs_plan_free(plan)
+    assert np.abs(out - ref(n, gates)).max() <= 2e-5

@@ -533,3 +533,32 @@ def test_product_and_oracle_share_no_code():
         text = open(f, errors="replace").read()
         assert "qsim_gb300" not in text and "csrc" not in text, f
         assert not re.search(r"^\s*(import|from)\s+paper_2509_04955_gb300(?!\.workloads)", text, re.M), f
+
+
+def test_bulk_tile_staging_where_runs_and_buffers_allow():
+    """tile_staging=2 stages tile passes by bulk copies when a run of
+    2^low_qubits amplitudes is at least 16 bytes and two tiles fit in shared
+    memory (low_qubits >= 1, so a complex64 run is at least 16 bytes and only
+    the buffer size can rule a complex64 or FP64 tile out); FP32-pair tiles
+    keep the vector path."""
+    gates = W.random_layered(16, 6, seed=3)
+    def bulk(dt, **kw):
+        plan = Q.qs_plan_create(16, dt, gates, Q.make_opts(tile_staging=2, **kw))
+        try:
+            info = Q.qs_plan_info_get(plan)
+            return info["bulk_tile_passes"], info["passes"]
+        finally:
+            Q.qs_plan_free(plan)
+    b, n = bulk(Q.QS_C64, fuse_k=2, tile_qubits=12, low_qubits=4)
+    assert b == n > 0
+    b, n = bulk(Q.QS_C128, fuse_k=2, tile_qubits=11, low_qubits=3, c128_pairs=2)
+    assert b == n > 0
+    assert bulk(Q.QS_C128, fuse_k=2, tile_qubits=11, low_qubits=3)[0] == 0       # FP32 pairs
+    b, n = bulk(Q.QS_C64, fuse_k=1, tile_qubits=10, low_qubits=1)               # 16-byte runs
+    assert b == n > 0
+    assert bulk(Q.QS_C128, fuse_k=2, tile_qubits=13, low_qubits=4, c128_pairs=2)[0] == 0   # 2 x 128 KiB
+    plan = Q.qs_plan_create(16, Q.QS_C64, gates, Q.make_opts(fuse_k=2))
+    assert Q.qs_plan_info_get(plan)["bulk_tile_passes"] == 0                    # default: vector path
+    Q.qs_plan_free(plan)
+    with pytest.raises(Q.QsError):
+        Q.qs_plan_create(16, Q.QS_C64, gates, Q.make_opts(tile_staging=3))

@@ -83,3 +83,58 @@ def test_tile_addressing_partitions_the_state(n, dt, opts):
         assert seen_high or n == len(tile)   # some pass selects non-adjacent high qubits
     finally:
         Q.qs_plan_free(plan)
+
+
+def _bulk_tile_schedule(my, seed, wait_read=True):
+    """The bulk-staged tile pass (k_tile_bulk) as a discrete-event model: warp 0
+    issues the loads of tile i + 1 into buffer (i + 1) & 1 at the top of
+    iteration i (after cp.async.bulk.wait_group.read for the stores it issued
+    from that buffer), every thread waits for tile i's buffer, runs the ops,
+    then warp 0 issues its stores. Copies complete after random delays; the
+    model reports a buffer overwritten before its stores read it out, ops on a
+    buffer before its load landed, or a tile not stored exactly once."""
+    import random
+    rng = random.Random(seed)
+    now = 0.0
+    landed = {}            # tile -> time its load completes
+    buf_read_done = {0: 0.0, 1: 0.0}   # time the last stores from the buffer finished reading it
+    buf_tile = {0: None, 1: None}
+    stored, errors = [], []
+
+    def load(i):
+        nonlocal now
+        b = i & 1
+        if wait_read:
+            now = max(now, buf_read_done[b])
+        elif buf_read_done[b] > now:
+            errors.append("buffer loaded before its stores read it out")
+        buf_tile[b] = i
+        landed[i] = now + rng.uniform(1, 6)
+
+    if my:
+        load(0)
+    for i in range(my):
+        if i + 1 < my:
+            load(i + 1)
+        now = max(now, landed[i])                    # mbarrier wait for tile i
+        if buf_tile[i & 1] != i:
+            errors.append("ops on a buffer holding another tile")
+        now += rng.uniform(0.5, 4)                   # the ops
+        buf_read_done[i & 1] = now + rng.uniform(0.5, 5)
+        stored.append(i)
+    if stored != list(range(my)):
+        errors.append("tiles not stored exactly once in order")
+    return errors
+
+
+def test_bulk_tile_pipeline_has_no_buffer_hazard():
+    for seed in range(300):
+        for my in (0, 1, 2, 3, 7, 40):
+            assert _bulk_tile_schedule(my, seed) == [], (seed, my)
+
+
+def test_bulk_tile_pipeline_without_the_read_wait_is_caught():
+    """Dropping cp.async.bulk.wait_group.read lets a load overwrite a buffer
+    whose stores have not read it yet; the model reports it."""
+    fails = sum(1 for seed in range(200) if _bulk_tile_schedule(20, seed, wait_read=False))
+    assert fails > 100
