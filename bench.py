@@ -413,6 +413,16 @@ def main():
         Q.lib().qs_state_copy_to_host(state, host_out.data_ptr(), host_out.numel() * amp128)
     torch.cuda.synchronize()
     e2e_seq_ms = (time.perf_counter() - t0) * 1e3 / 2
+    # the host link as this run sees it: one copy each way alone (it varies with the
+    # host's other traffic, and bounds the end-to-end step together with the circuit)
+    copy_ms = {}
+    for name, fn in (("h2d", lambda: Q.lib().qs_state_copy_from_host(state, host_in.data_ptr(), host_in.numel() * amp128)),
+                     ("d2h", lambda: Q.lib().qs_state_copy_to_host(state, host_out.data_ptr(), host_out.numel() * amp128))):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        fn()
+        torch.cuda.synchronize()
+        copy_ms[name] = (time.perf_counter() - t1) * 1e3
     work = [state] + [Q.qs_state_alloc(n, Q.QS_C128, stream) for _ in range(2)]
     Q.qs_plan_execute_host(plan, work, [host_in], [host_out])     # warm-up
     torch.cuda.synchronize()
@@ -465,7 +475,9 @@ def main():
         "e2e": {"value": e2e_ms, "unit": "ms", "h2d_bytes_per_step": (1 << n) * amp128,
                 "d2h_bytes_per_step": (1 << n) * amp128 + 8, "steps": e2e_steps,
                 "api": "qs_plan_execute_host (3 device work states, copies overlapped with the circuit)",
-                "sequential_ms": e2e_seq_ms, "device_norm_last": float(e2e_norms[-1]), "norm_after": e2e_norm},
+                "sequential_ms": e2e_seq_ms, "device_norm_last": float(e2e_norms[-1]), "norm_after": e2e_norm,
+                "copy_alone_ms": copy_ms,
+                "copy_alone_gbs": {k: (1 << n) * amp128 / (v * 1e-3) / 1e9 for k, v in copy_ms.items()}},
         "gpu_launches": launches,
         "clocks": clk,
         "cpu_baseline": cpu,
