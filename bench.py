@@ -182,6 +182,29 @@ def oracle_sample(args, gates, threads: int, budget_s: float = 60.0):
     return ms, desc, used
 
 
+def oracle_prefix(n, gates, count, threads=0):
+    """The FP64 oracle (all host cores unless `threads`) applying the first
+    `count` gates of a circuit to |0..0> at n qubits: (seconds, threads used).
+    A configuration's CPU baseline: its cost per gate times the circuit's gates."""
+    import ctypes as C
+    import numpy as np
+    import oracle as O
+    L = O.lib()
+    used = L.or_set_threads(threads)
+    try:
+        psi = np.zeros(1 << n, dtype=np.complex128)
+        psi[0] = 1
+        packed = O.pack(gates[:count])
+        theta = (C.c_double * 1)()
+        ptr = psi.ctypes.data_as(C.POINTER(C.c_double))
+        t0 = time.perf_counter()
+        for i in range(count):
+            L.or_apply_gate(ptr, n, C.byref(packed[i]), theta)
+        return time.perf_counter() - t0, used
+    finally:
+        L.or_set_threads(1)
+
+
 # ----------------------------------------------------------------- main paths
 
 def max_over_ranks(value: float, dist, device: str) -> float:
@@ -857,6 +880,10 @@ def config_qft(Q, torch, np, st, args):
         Q.qs_plan_free(plan)
         del full
     c1["speedup_tensor_vs_per_gate"] = c1["per_gate"]["ms"]["median"] / c1["tensor_k5"]["ms"]["median"]
+    sec, used = oracle_prefix(n, g, 60)
+    c1["cpu_oracle"] = {"ms_scaled": sec / 60 * len(g) * 1e3, "threads": used,
+                        "sample": f"oracle (plain C, FP64) on {used} threads: the first 60 of the {len(g)} gates "
+                                  f"at n={n} in {sec:.2f} s, scaled by the gate count"}
     Q.qs_state_free(s)
     return c1
 
@@ -894,6 +921,12 @@ def config_n32(Q, torch, np, st, args):
     c2["per_gate_c64"] = {"ms_one_layer": spread(t), "ms_scaled_to_40_layers": 40 * statistics.median(t),
                           "gates_per_layer": per_layer}
     c2["speedup_tensor_vs_per_gate"] = c2["per_gate_c64"]["ms_scaled_to_40_layers"] / c2["tensor_fp16x3"]["ms"]["median"]
+    # CPU oracle on the same structure at 26 qubits (the size the oracle checks): one layer, scaled
+    g26 = W.random_layered(26, 40, seed=0, entangler="cz")
+    sec, used = oracle_prefix(26, g26, len(g26) // 40)
+    c2["cpu_oracle_n26"] = {"ms_scaled_to_40_layers": sec * 40 * 1e3, "threads": used,
+                            "sample": f"oracle (plain C, FP64) on {used} threads: layer 1 ({len(g26) // 40} gates) "
+                                      f"at n=26 in {sec:.2f} s, x 40 layers"}
     Q.qs_plan_free(pplan)
     Q.qs_state_free(ref)
     Q.qs_state_free(s)
