@@ -54,6 +54,8 @@ def parse():
     ap.add_argument("--stream-n", type=int, default=31, help="register size of the host-resident configuration")
     ap.add_argument("--smgp-ns", default="20,24,28,30", help="register sizes of the SMGP ablation (comma list)")
     ap.add_argument("--tune", default="auto", help="auto | k,m,L[,tc_min_gates[,tc_pipeline]]")
+    ap.add_argument("--tile-staging", type=int, default=0,
+                    help="with --tune k,m,L: 2 = tile passes staged by bulk copies (profiler runs of k_tile_bulk)")
     ap.add_argument("--only-config", default=None,
                     choices=["qft_n30_m2", "qft_n28_c128", "random_n32_cz_tensor", "ucc_batched_n20",
                              "hea_adjoint_n24", "qaoa_n30", "smgp_ablation", "stream_host_state"],
@@ -529,7 +531,7 @@ def c64_line(Q, torch, np, args, gates, stream, hbm_peak, bf16_peak, peak_src, s
         trials = {"chosen": Q.opts_dict(bopts), "ms": bms, "search_s": time.perf_counter() - t0}
     else:
         parts = [int(x) for x in args.tune.split(",")]
-        kw = dict(mode=F, fuse_k=parts[0], tile_qubits=parts[1], low_qubits=parts[2])
+        kw = dict(mode=F, fuse_k=parts[0], tile_qubits=parts[1], low_qubits=parts[2], tile_staging=args.tile_staging)
         if len(parts) > 3 and parts[3] > 0:
             kw.update(mode=T, tc_min_gates=parts[3])
             if len(parts) > 4:
@@ -541,13 +543,14 @@ def c64_line(Q, torch, np, args, gates, stream, hbm_peak, bf16_peak, peak_src, s
     ms, launches, kern, _ = time_steps(Q, torch, plan, state, args.steps, args.warmup, per_launch=True)
     tc_dom = kern["tc_ms"] > kern["tile_ms"]
     tc_kernel = "k_tc_block" if kw.get("tc_pipeline", 0) == 1 else "k_tc_bulk"
+    tile_kernel = "k_tile_bulk" if kw.get("tile_staging", 0) == 2 else "k_tile"
     kms = (kern["tc_ms"] / max(1, kern["tc_launches"])) if tc_dom else (kern["tile_ms"] / max(1, kern["tile_launches"]))
     out = {"ms": ms, "plan": {k: v for k, v in kw.items()}, "mode": mode_name(Q, kw), "passes": info["passes"],
            "gpu_launches": launches, "effective_gbps": info["sweeps"] * sb / (ms * 1e-3) / 1e9,
            "roofline": {"bound": "hbm", "achieved": sb / (kms * 1e-3) / 1e9, "peak": hbm_peak, "unit": "GB/s",
                         "frac": sb / (kms * 1e-3) / 1e9 / hbm_peak,
-                        "traffic": traffic_record(tc_kernel if tc_dom else "k_tile", n),
-                        "kernel": f"{tc_kernel} (tensor-core 6-qubit block pass)" if tc_dom else "k_tile (tile pass)",
+                        "traffic": traffic_record(tc_kernel if tc_dom else tile_kernel, n),
+                        "kernel": f"{tc_kernel} (tensor-core 6-qubit block pass)" if tc_dom else f"{tile_kernel} (tile pass)",
                         "peak_source": f"{peak_src} (hbm_gbs, burst copy)", "avg_launch_ms": kms},
            "autotune": trials}
     if tc_dom:
@@ -1014,7 +1017,8 @@ def config_hea(Q, torch, np, st, args):
 KERNEL_SOURCES = {"k_tc_bulk": ("kernels_tc.cu", "tcgen05.cuh", "cplx.cuh"),
                   "k_tc_block": ("kernels_tc.cu", "tcgen05.cuh", "cplx.cuh"),
                   "k_tc128": ("kernels_tc128.cu", "tcgen05.cuh"),
-                  "k_tile": ("kernels_tile.cuh", "cplx.cuh", "dfloat.cuh", "qs_internal.h", "tcgen05.cuh")}
+                  "k_tile": ("kernels_tile.cuh", "cplx.cuh", "dfloat.cuh", "qs_internal.h", "tcgen05.cuh"),
+                  "k_tile_bulk": ("kernels_tile.cuh", "cplx.cuh", "dfloat.cuh", "qs_internal.h", "tcgen05.cuh")}
 
 
 def kernel_hash(kernel: str) -> str:
