@@ -865,13 +865,15 @@ def config_qft(Q, torch, np, st, args):
     idx = np.unique(np.random.default_rng(0).integers(0, 1 << n, size=4096))
     want = np.exp(2j * np.pi * ((x * idx) % (1 << n)) / (1 << n)) / np.sqrt(1 << n)
     c1 = {"workload": "QFT n=28 complex128, seeded basis input", "gates": len(g),
-          "note": "k = 6 is not built for complex128 (tensor-core blocks are 5 qubits there)"}
+          "note": "complex128 tensor-core passes take 5-qubit blocks (k = 6 would need twice the tensor-memory "
+                  "columns); tensor_k4 contracts to 4 qubits and pads the blocks to 5"}
     for name, opts, reps in (("per_gate", None, 3),
                              ("fused_k4_fp32_pairs", Q.make_opts(mode=F, fuse_k=4, c128_pairs=1), 3),
                              ("fused_k5_fp32_pairs", Q.make_opts(mode=F, fuse_k=5, tile_qubits=11, low_qubits=3,
                                                                  c128_pairs=1), 3),
                              ("fused_k5_fp64", Q.make_opts(mode=F, fuse_k=5, c128_pairs=2), 2),
-                             ("tensor_k5", Q.make_opts(mode=T), 5)):
+                             ("tensor_k5", Q.make_opts(mode=T), 5),
+                             ("tensor_k4", Q.make_opts(mode=T, fuse_k=4), 3)):
         plan = Q.qs_plan_create(n, Q.QS_C128, g, opts)
         Q.qs_state_set_basis(s, x)
         Q.qs_plan_execute(plan, s)
@@ -910,6 +912,7 @@ def config_n32(Q, torch, np, st, args):
     c2["c128_tensor"] = {"ms": spread(t), "passes": Q.qs_plan_info_get(pr)["passes"], "norm": Q.qs_norm(ref)}
     Q.qs_plan_free(pr)
     for name, opts, reps in (("tensor_fp16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=4), 5),
+                             ("tensor_fp16x3_k5", Q.make_opts(mode=T, fuse_k=5, tc_min_gates=2, tc_precision=4), 3),
                              ("tensor_bf16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=3), 3),
                              ("tensor_bf16", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=1), 3),
                              ("fused_cuda_cores_k2", Q.make_opts(mode=F, fuse_k=2, tile_qubits=13, low_qubits=4), 2)):

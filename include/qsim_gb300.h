@@ -92,17 +92,21 @@ typedef enum {
   QS_MODE_FUSED = 1,     /* DAG contraction into k-qubit blocks + tile passes */
   QS_MODE_TENSOR = 2,    /* as FUSED, with blocks applied as dense complex GEMMs on tensor cores
                             (tcgen05), each its own pass over the state.
-                            QS_C64: 6-qubit contraction, blocks of >= reserved[0] gates (default
-                            10) as 64x64 complex blocks with FP32 accumulation (tc_precision),
-                            n >= 13 (smaller states plan as FUSED).
-                            QS_C128: 5-qubit contraction, blocks of >= reserved[0] gates (default
-                            1: every block) as 32x32 complex blocks computed exactly: each row of
-                            64 reals shares a power-of-two scale, amplitudes and W are cut into
-                            five 9-bit integer digits (fp16), the 15 digit products of the five
-                            leading levels accumulate exactly in FP32 and are combined into FP64
-                            without FP64 instructions; per pass the absolute error is about
-                            2^-43 times the largest amplitude of the 64-real row. n >= 12
-                            (smaller states plan as FUSED); tc_precision must be 0. */
+                            QS_C64: 6-qubit contraction (fuse_k = 4 or 5: that width, the blocks
+                            padded to 6 qubits), blocks of >= reserved[0] gates (default 10) as
+                            64x64 complex blocks with FP32 accumulation (tc_precision), n >= 13
+                            (smaller states plan as FUSED).
+                            QS_C128: 5-qubit contraction (fuse_k = 4: that width, padded to 5),
+                            blocks of >= reserved[0] gates (default 1: every block) as 32x32
+                            complex blocks computed exactly: each row of 64 reals shares a
+                            power-of-two scale, amplitudes are cut into six 9-bit integer
+                            digits and W into six (fp16), the 21 digit products of levels 0-5
+                            accumulate in FP32 (levels 0-2 exactly, level 5 folded into level 4)
+                            and are combined in FP32 pairs without FP64 instructions; per pass
+                            and output the error is at most 2^-46 times the 2-norm of the
+                            32-amplitude row plus 2^-49 of its scale (2^-48 of the norm between
+                            passes, which hand the state over as FP32 pairs). n >= 12 (smaller
+                            states plan as FUSED); tc_precision must be 0. */
   QS_MODE_SMGP = 3       /* staggered multi-gate parallelism (Section 3.3, Tab. 3): runs of 2, 4 or 8
                             consecutive uncontrolled one-target gates on distinct qubits become a
                             group; the state is cut into S segments by qubits no member targets,

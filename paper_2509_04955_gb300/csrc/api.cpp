@@ -97,10 +97,12 @@ std::vector<qs_plan_opts> tune_candidates(int n, qs_dtype dt) {
   if (dt == QS_C64 && n >= 13) {
     const int tm[] = {2, 4, 8};
     for (int t : tm) add(QS_MODE_TENSOR, 2, 13, 4, t);
+    add(QS_MODE_TENSOR, 5, 13, 4, 2);   // 5-qubit contraction, blocks padded to 6
   }
   if (dt == QS_C128 && n >= 12) {   // every block on tensor cores, or only those of >= 2 / 4 gates
     const int tm[] = {1, 2, 4};
     for (int t : tm) add(QS_MODE_TENSOR, 2, 11, 3, t);
+    add(QS_MODE_TENSOR, 4, 11, 3, 1);   // 4-qubit contraction, blocks padded to 5
   }
   return c;
 }

@@ -783,7 +783,10 @@ qs_plan_s* create_plan(int n, qs_dtype dt, const qs_gate* gates, size_t ng, cons
   require(o.low_qubits + std::max(widest, o.fuse_k) <= 14 || o.tile_qubits == n,
           "low_qubits + widest gate must fit a 14-qubit tile");
   PlanOptions po;
-  po.k = o.paper_mode ? 2 : (tensor ? (dt == QS_C128 ? 5 : (user_k == 5 ? 5 : 6)) : o.fuse_k);
+  // tensor mode: contraction width fuse_k = 4 or 5 (complex64) / 4 (complex128), else the pass's
+  // own width; narrower blocks are padded to the pass width below
+  po.k = o.paper_mode ? 2
+                      : (tensor ? ((user_k == 4 || (user_k == 5 && dt == QS_C64)) ? user_k : tc_width) : o.fuse_k);
   po.paper = o.paper_mode != 0;
   po.amp_bytes = (int)amp_bytes(dt);
   // GB300: FP32 FMA 128 lanes/clk/SM, FP64 about 1/59 of that (measured),

@@ -1297,3 +1297,22 @@ def test_bulk_staged_tile_pass_wait_timeout_returns_error_and_recovers():
         Q.qs_state_free(h)
         Q.qs_plan_free(plan)
     assert np.abs(out - ref(n, gates)).max() <= 2e-5
+
+
+@pytest.mark.parametrize("dtname,fuse_k", [("c64", 4), ("c64", 5), ("c128", 4)])
+def test_tensor_core_narrower_contraction_widths(dtname, fuse_k):
+    """Tensor-core plans whose contraction is narrower than the pass (4 or 5
+    qubits in complex64, 4 in complex128; blocks padded with qubits they act
+    on as the identity): layered random circuits over several tiles per CTA
+    against the oracle, complex64 bar 2e-5, complex128 1e-12."""
+    dt = DT[dtname]
+    for n, depth in ((14, 8), (22, 6)):
+        gates = W.random_layered(n, depth, seed=n + fuse_k)
+        opts = Q.make_opts(mode=Q.QS_MODE_TENSOR, fuse_k=fuse_k, tc_min_gates=2 if dt == Q.QS_C64 else 0)
+        plan = Q.qs_plan_create(n, dt, gates, opts)
+        try:
+            assert any(op["type"] == 3 for op in Q.qs_plan_ops(plan))
+        finally:
+            Q.qs_plan_free(plan)
+        got = run(n, dt, gates, opts=opts)
+        assert np.abs(got - ref(n, gates)).max() <= TOL[dt], (n, np.abs(got - ref(n, gates)).max())

@@ -332,13 +332,28 @@ def test_per_gate_sweep_accounting():
     Q.qs_plan_free(plan)
 
 
-def test_tensor_mode_plan_matches_oracle_on_a_state():
-    """Tensor-core plans (6-qubit blocks padded to 6, tile passes in between)
-    reproduce the circuit: ops applied with numpy to a random state equal the
-    oracle's gate-by-gate result."""
+def _padded_qubits(U, k):
+    """Local bits on which a 2^k x 2^k block acts as the identity."""
+    out = []
+    for b in range(k):
+        M = U.reshape([2] * (2 * k))
+        # axes: row bits k-1..0 then column bits k-1..0 (bit b of an index is axis k-1-b)
+        r, c = k - 1 - b, 2 * k - 1 - b
+        sub = np.moveaxis(M, (r, c), (0, 1))
+        if np.allclose(sub[0, 1], 0) and np.allclose(sub[1, 0], 0) and np.allclose(sub[0, 0], sub[1, 1]):
+            out.append(b)
+    return out
+
+
+@pytest.mark.parametrize("fuse_k", [0, 4, 5])
+def test_tensor_mode_plan_matches_oracle_on_a_state(fuse_k):
+    """Tensor-core plans (blocks of the 6-, 5- or 4-qubit contraction padded to
+    6 qubits, tile passes in between) reproduce the circuit: ops applied with
+    numpy to a random state equal the oracle's gate-by-gate result; with a
+    narrower contraction the blocks act as the identity on their padding."""
     n = 14
     gates = W.random_layered(n, 8, seed=3)
-    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR))
+    plan = Q.qs_plan_create(n, Q.QS_C64, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, fuse_k=fuse_k))
     try:
         ops = Q.qs_plan_ops(plan)
         assert any(op["type"] == 3 for op in ops)
@@ -352,6 +367,8 @@ def test_tensor_mode_plan_matches_oracle_on_a_state():
             else:
                 if op["type"] == 3:
                     assert len(op["qubits"]) == 6
+                    if fuse_k:
+                        assert len(_padded_qubits(np.asarray(op["matrix"]).reshape(64, 64), 6)) >= 6 - fuse_k
                 cur = apply_block(cur, n, op["qubits"], op["matrix"])
         assert np.abs(cur - O.apply_circuit(psi, n, gates)).max() < 1e-12
         for ps in Q.qs_plan_passes(plan):
@@ -362,15 +379,16 @@ def test_tensor_mode_plan_matches_oracle_on_a_state():
         Q.qs_plan_free(plan)
 
 
-@pytest.mark.parametrize("tc_min", [0, 2, 5])
-def test_complex128_tensor_plan_matches_oracle_on_a_state(tc_min):
-    """Complex128 tensor-core plans: 5-qubit contraction, blocks of >= tc_min
-    gates (0: every block) padded to 5 qubits on 12-qubit tiles, the rest as
-    CUDA-core ops; applied with numpy they reproduce the oracle's state. The
-    complex64 precision options are refused."""
+@pytest.mark.parametrize("tc_min,fuse_k", [(0, 0), (2, 0), (5, 0), (0, 4)])
+def test_complex128_tensor_plan_matches_oracle_on_a_state(tc_min, fuse_k):
+    """Complex128 tensor-core plans: 5-qubit (or, with fuse_k = 4, 4-qubit)
+    contraction, blocks of >= tc_min gates (0: every block) padded to 5 qubits
+    on 12-qubit tiles, the rest as CUDA-core ops; applied with numpy they
+    reproduce the oracle's state. The complex64 precision options are refused."""
     n = 13
     gates = W.random_layered(n, 6, seed=4)
-    plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=tc_min))
+    plan = Q.qs_plan_create(n, Q.QS_C128, gates, Q.make_opts(mode=Q.QS_MODE_TENSOR, tc_min_gates=tc_min,
+                                                             fuse_k=fuse_k))
     try:
         ops = Q.qs_plan_ops(plan)
         tc = [op for op in ops if op["type"] == 3]
@@ -387,6 +405,8 @@ def test_complex128_tensor_plan_matches_oracle_on_a_state(tc_min):
             else:
                 if op["type"] == 3:
                     assert len(op["qubits"]) == 5
+                    if fuse_k:
+                        assert len(_padded_qubits(np.asarray(op["matrix"]).reshape(32, 32), 5)) >= 5 - fuse_k
                 cur = apply_block(cur, n, op["qubits"], op["matrix"])
         assert np.abs(cur - O.apply_circuit(psi, n, gates)).max() < 1e-12
         for ps in Q.qs_plan_passes(plan):
