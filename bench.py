@@ -225,6 +225,17 @@ def job_ms_per_circuit(ms_step_max: float, world: int) -> float:
     return ms_step_max / world
 
 
+def headline_config(args, gates, world):
+    """The headline workload's `config` (both arms print the same one; the GPU
+    arm's plan is described under its own key)."""
+    n = args.n
+    return {"workload": workload_desc(args, len(gates)) + ", complex128",
+            "n": n, "state": f"complex128, {(1 << n) * 16 / 2**30:g} GiB", "gates": len(gates),
+            "l2": (f"inputs larger than L2 ({(1 << n) * 16 / 2**30:g} GiB state vs 129 MB); no flush"
+                   if (1 << n) * 16 > 129e6 else "state fits L2: timed passes may hit L2"),
+            "parallelism": f"replicas x{world}"}
+
+
 def run_reference(args):
     """The oracle (the tier's reference arm), as it stands, on the host's cores:
     each step applies whole layers of the headline circuit on all processors
@@ -235,6 +246,7 @@ def run_reference(args):
     gates = workload(args)
     import oracle as O
     O.build()
+    cfg = headline_config(args, gates, int(os.environ.get("WORLD_SIZE", "1")))
     vals = []
     desc, cores = "", 1
     for _ in range(max(1, args.steps)):
@@ -244,7 +256,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "ms", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": v, "higher_is_better": False,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_desc(args, len(gates)), "n": args.n, "dtype": "complex128"},
+            "config": cfg,
             "cpu_baseline": {"value": v, "unit": "ms", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": v, "unit": "ms", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -478,18 +490,15 @@ def main():
                "one_thread": {"value": ms1, "unit": "ms", "cores": 1, "sample": d1}}
 
     total_ms = job_ms_per_circuit(ms_step, world)
-    cfg = {"workload": workload_desc(args, len(gates)) + ", complex128, tensor-core plan (every 5-qubit block on "
-                                                           "tcgen05 as exact fp16 digit products)",
-           "n": n, "state": f"complex128, {(1 << n) * 16 / 2**30:g} GiB", "gates": len(gates),
-           "passes": info["passes"], "blocks": info["blocks"],
-           "l2": (f"inputs larger than L2 ({(1 << n) * 16 / 2**30:g} GiB state vs 129 MB); no flush"
-                  if (1 << n) * 16 > 129e6 else "state fits L2: timed passes may hit L2"),
-           "parallelism": f"replicas x{world}", "mode": "tensor", "tc_min_gates": 1}
+    cfg = headline_config(args, gates, world)
     line = {
         "metric": METRIC, "value": total_ms, "unit": "ms", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": False, "scaling": "weak",
         "vs_baseline": None, "dtype": "c128: fp16 digit products, exact FP32 level sums, FP32-pair combine",
         "data": "synthetic", "config": cfg,
+        "plan": {"mode": "tensor", "description": "every contracted 5-qubit block on tcgen05 as exact fp16 digit "
+                                                  "products", "tc_min_gates": 1, "passes": info["passes"],
+                 "blocks": info["blocks"]},
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": hbm_peak, "unit": "GB/s",
                      "frac": achieved / hbm_peak, "traffic": traffic_record("k_tc128", n),
                      "kernel": "k_tc128 (complex128 tensor-core 5-qubit block pass)",
