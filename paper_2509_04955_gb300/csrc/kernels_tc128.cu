@@ -96,17 +96,22 @@ __device__ __forceinline__ void t2_mma(uint32_t tmem_d, uint32_t tmem_a, uint64_
 // level a + j. Planes 5..9 hold 2^-9 W_1 .. 2^-9 W_5 (plane 9 - a pairs with
 // A_a for the level-5 products folded into level 4) and A plane 5 holds
 // 2^-9 A_5. An instruction costs about the same for N = 64 and N = 128, so
-// merging consecutive planes cuts the 21 products to 13 instructions. Phase
-// X touches levels 2-4 only (it may start once the previous tile's levels
-// have been folded), phase Y levels 0-1 only (once the folded pairs have been
-// read back); the first entry of each phase writes every level of its phase
-// without accumulating.
+// merging consecutive planes cuts the 21 products to 15 instructions, split
+// in three phases by the levels they write so that each may start as soon as
+// the drainers have released those levels of the previous tile.
 struct T2Mma {
-  int a, w, nplanes, level;
+  int a, w, nplanes, level, fresh;
 };
-__device__ constexpr T2Mma kT2PhaseX[] = {{2, 0, 3, 2}, {0, 2, 3, 2}, {1, 1, 3, 2}, {3, 0, 2, 3}, {4, 0, 1, 4}, {0, 9, 1, 4},
-                                          {1, 8, 1, 4}, {2, 7, 1, 4}, {3, 6, 1, 4}, {4, 5, 1, 4}, {5, 0, 1, 4}};
-__device__ constexpr T2Mma kT2PhaseY[] = {{0, 0, 2, 0}, {1, 0, 1, 1}};
+// phase X4: level 4 alone (the level-5 products folded in, then A_4 W_0), as
+// soon as the previous tile's level 4 has been read; phase X23: levels 2-3
+// (and the rest of level 4) once its levels 2-3 have been folded; phase Y:
+// levels 0-1 once the folded pairs have been read back. `fresh`: the entry's
+// first k-step overwrites its accumulators.
+__device__ constexpr T2Mma kT2PhaseX4[] = {{0, 9, 1, 4, 1}, {1, 8, 1, 4, 0}, {2, 7, 1, 4, 0}, {3, 6, 1, 4, 0},
+                                           {4, 5, 1, 4, 0}, {5, 0, 1, 4, 0}, {4, 0, 1, 4, 0}};
+__device__ constexpr T2Mma kT2PhaseX23[] = {{2, 0, 1, 2, 1}, {3, 0, 1, 3, 1}, {2, 1, 2, 3, 0},
+                                            {1, 1, 3, 2, 0}, {0, 2, 3, 2, 0}, {3, 1, 1, 4, 0}};
+__device__ constexpr T2Mma kT2PhaseY[] = {{0, 0, 2, 0, 1}, {1, 0, 1, 1, 0}};
 
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
@@ -253,9 +258,9 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   int32_t* xe = (int32_t*)(lamcol + 32);                        // [2][128][2]: half-row exponent maxima
   int32_t* etab = xe + 2 * 128 * 2;                             // [2][128]: row scale exponents E
   int32_t* qpos = etab + 2 * 128;                               // tile[12], row[7], col[5], p
-  // full[2] empty[2] afull mdone dfree efull[2] wfull wfree xbar[2][4] dfree01
+  // full[2] empty[2] afull mdone dfree efull[2] wfull wfree xbar[2][4] dfree01 dfree4
   uint64_t* bar = (uint64_t*)(qpos + 26);
-  uint32_t* tmem_slot = (uint32_t*)(bar + 20);
+  uint32_t* tmem_slot = (uint32_t*)(bar + 21);
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -270,10 +275,10 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     while (pp < 12 && p.tile[pp] == pp) ++pp;
     qpos[24] = pp;
     s_abort = 0;
-    // arrivals: full, wfull, wfree, mdone: 1 (expect_tx / commit); empty, afull, dfree, efull, dfree01:
+    // arrivals: full, wfull, wfree, mdone: 1 (expect_tx / commit); empty, afull, dfree, efull, dfree01, dfree4:
     // one per warp of 8; xbar (row-exponent exchange of converter warps quad and quad + 4): 2
-    const uint32_t cnt[20] = {1, 1, 8, 8, 8, 1, 8, 8, 8, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 8};
-    for (int i = 0; i < 20; ++i)
+    const uint32_t cnt[21] = {1, 1, 8, 8, 8, 1, 8, 8, 8, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 8, 8};
+    for (int i = 0; i < 21; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)), "r"(cnt[i]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -334,12 +339,13 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   uint64_t* empty = bar + 2;
   uint64_t* afull = bar + 4;
   uint64_t* mdone = bar + 5;
-  uint64_t* dfree = bar + 6;      // levels 2-4 of the accumulators read (folded into levels 0-1)
+  uint64_t* dfree = bar + 6;      // levels 2-3 of the accumulators read (folded into levels 0-1)
   uint64_t* efull = bar + 7;
   uint64_t* wfull = bar + 9;
   uint64_t* wfree = bar + 10;     // completes when the MMAs on a state's W planes are done
   uint64_t* xbar = bar + 11;      // [parity][quad]
   uint64_t* dfree01 = bar + 19;   // levels 0-1 (the folded FP32 pairs) read
+  uint64_t* dfree4 = bar + 20;    // level 4 read (held in registers by the drainers)
   auto tile_of = [&](uint64_t i) -> uint64_t { return t_begin + i * tstep; };
   auto state_ptr = [&](uint64_t tt) -> double2* {
     if constexpr (MULTI) return (double2*)psis[tt >> lg_tiles1];
@@ -422,21 +428,33 @@ __global__ void __launch_bounds__(kT2Threads, 1)
           ++w_seen;
         }
         if (!mbar_wait(smem_u32(afull), (uint32_t)(i & 1), spin)) { fail(1); break; }
-        // levels 2-4 (18 of the 21 products) as soon as the drainers have folded
-        // the previous tile's levels into levels 0-1, then levels 0-1 once they
-        // have read those back
-        if (i >= 1 && !mbar_wait(smem_u32(dfree), (uint32_t)((i - 1) & 1), spin)) { fail(1); break; }
+        if (i >= 1 && !mbar_wait(smem_u32(dfree4), (uint32_t)((i - 1) & 1), spin)) { fail(1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int e = 0; e < (int)(sizeof(kT2PhaseX) / sizeof(T2Mma)); ++e) {
-          const T2Mma m = kT2PhaseX[e];
+        for (int e = 0; e < (int)(sizeof(kT2PhaseX4) / sizeof(T2Mma)); ++e) {
+          const T2Mma m = kT2PhaseX4[e];
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
             t2_mma(tmem + kT2AccCol + 64 * m.level, tmem + 32 * m.a + 8 * ks,
-                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (e | ks) ? 1u : 0u);
+                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (m.fresh && ks == 0) ? 0u : 1u);
+        }
+        if (i >= 1 && !mbar_wait(smem_u32(dfree), (uint32_t)((i - 1) & 1), spin)) {
+          mma_commit(smem_u32(mdone));   // the issued MMAs complete before the abort drain below
+          ++i;
+          fail(1);
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+#pragma unroll
+        for (int e = 0; e < (int)(sizeof(kT2PhaseX23) / sizeof(T2Mma)); ++e) {
+          const T2Mma m = kT2PhaseX23[e];
+#pragma unroll
+          for (int ks = 0; ks < 4; ++ks)
+            t2_mma(tmem + kT2AccCol + 64 * m.level, tmem + 32 * m.a + 8 * ks,
+                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (m.fresh && ks == 0) ? 0u : 1u);
         }
         if (i >= 1 && !mbar_wait(smem_u32(dfree01), (uint32_t)((i - 1) & 1), spin)) {
-          mma_commit(smem_u32(mdone));   // the issued MMAs complete before the abort drain below
+          mma_commit(smem_u32(mdone));
           ++i;
           fail(1);
           break;
@@ -448,7 +466,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 #pragma unroll
           for (int ks = 0; ks < 4; ++ks)
             t2_mma(tmem + kT2AccCol + 64 * m.level, tmem + 32 * m.a + 8 * ks,
-                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (e | ks) ? 1u : 0u);
+                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (m.fresh && ks == 0) ? 0u : 1u);
         }
         mma_commit(smem_u32(mdone));
         if (i + 1 < my && new_state(i + 1)) mma_commit(smem_u32(wfree));   // last tile on these planes
@@ -560,15 +578,22 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         const uint64_t tt = tile_of(i);
         double2* __restrict__ psi = state_ptr(tt);
         const uint64_t rb = tile_base(tt & tmask1) | roff;
-        // fold: per 8 columns, the five levels into an FP32 pair (s, e) written
-        // back over levels 0 and 1, which releases levels 2-4 to the next MMAs
+        // level 4 of this thread's 32 columns first, held in registers, which
+        // releases it to the next tile's level-4 MMAs; then per 8 columns
+        // levels 0-3 folded with it into an FP32 pair written back over levels
+        // 0 and 1, which releases levels 2-3
         const uint32_t col0 = tmem + tq + kT2AccCol + 32 * h;
-#pragma unroll 1
+        float l4[32];
+        tmem_ld32(col0 + 64 * 4, l4);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(dfree4));
+#pragma unroll
         for (int c4 = 0; c4 < 4; ++c4) {
           const uint32_t col = col0 + 8 * c4;
-          uint32_t a[5][8];
+          uint32_t a[4][8];
 #pragma unroll
-          for (int l = 0; l < 5; ++l) tmem_ld8(col + 64 * l, a[l]);
+          for (int l = 0; l < 4; ++l) tmem_ld8(col + 64 * l, a[l]);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
           uint32_t ps[8], pe[8];
 #pragma unroll
@@ -579,7 +604,8 @@ __global__ void __launch_bounds__(kT2Threads, 1)
             t2_absorb2(sk, ek, lv(1), make_float2(-0.001953125f, -0.001953125f));
             t2_absorb2(sk, ek, lv(2), make_float2(-3.814697265625e-06f, -3.814697265625e-06f));
             t2_absorb2(sk, ek, lv(3), make_float2(-7.450580596923828e-09f, -7.450580596923828e-09f));
-            ek = __ffma2_rn(lv(4), make_float2(-1.4551915228366852e-11f, -1.4551915228366852e-11f), ek);
+            ek = __ffma2_rn(make_float2(l4[8 * c4 + k], l4[8 * c4 + k + 1]),
+                            make_float2(-1.4551915228366852e-11f, -1.4551915228366852e-11f), ek);
             ps[k] = __float_as_uint(sk.x);
             ps[k + 1] = __float_as_uint(sk.y);
             pe[k] = __float_as_uint(ek.x);
@@ -635,7 +661,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 
 size_t tc128_smem_bytes() {
   return 2 * (size_t)kT2SlotBytes + kT2WBytes + 4 * 256 * 8 + 32 * 8 * 2 + 32 * 4 + 2 * 128 * 2 * 4 + 2 * 128 * 4 +
-         26 * 4 + 20 * 8 + 16 + 1024;
+         26 * 4 + 21 * 8 + 16 + 1024;
 }
 
 static bool g_tc128_ready = false;

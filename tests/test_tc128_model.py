@@ -400,43 +400,53 @@ def test_a_whole_row_matches_the_fp64_product(shape):
 
 
 def _schedule():
-    """The kernel's MMA schedule tables (kT2PhaseX, kT2PhaseY), read from its source."""
+    """The kernel's MMA schedule tables (kT2PhaseX4, kT2PhaseX23, kT2PhaseY), read from its source."""
     import os
     import re
     src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2509_04955_gb300", "csrc",
                             "kernels_tc128.cu")).read()
-    out = {}
-    for name in ("kT2PhaseX", "kT2PhaseY"):
+    out = []
+    for name in ("kT2PhaseX4", "kT2PhaseX23", "kT2PhaseY"):
         body = re.search(name + r"\[\] = \{(.*?)\};", src, re.S).group(1)
-        out[name] = [tuple(int(x) for x in m.groups())
-                     for m in re.finditer(r"\{\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\s*\}", body)]
-    return out["kT2PhaseX"], out["kT2PhaseY"]
+        out.append([tuple(int(x) for x in m.groups())
+                    for m in re.finditer(r"\{\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\s*\}", body)])
+    return out
+
+
+# the levels each phase may write: the previous tile's drainers release level 4
+# first (read into registers), then levels 2-3 (folded), then levels 0-1 (the
+# folded pairs read back)
+PHASE_LEVELS = ({4}, {2, 3, 4}, {0, 1})
 
 
 def test_mma_schedule_issues_every_digit_product_once():
-    """Each entry (a, w, nplanes, level) multiplies A plane a by W planes
+    """Each entry (a, w, nplanes, level, fresh) multiplies A plane a by W planes
     w .. w + nplanes - 1 into levels level .. level + nplanes - 1. Together the
-    two phases must issue exactly the 21 products of the digit scheme: A_i W_j
+    three phases must issue exactly the 21 products of the digit scheme: A_i W_j
     into level i + j for i + j <= 4 (planes 0-4), A_i (2^-9 W_(5-i)) into level
-    4 for i <= 4 (plane 9 - i), and (2^-9 A_5) W_0 into level 4; phase X only
-    into levels 2-4 and phase Y only into levels 0-1 (the two release steps of
-    the accumulators); the first entry of each phase covers all its levels
-    (it is the one issued without accumulation); N = 64 x nplanes <= 256."""
-    X, Y = _schedule()
+    4 for i <= 4 (plane 9 - i), and (2^-9 A_5) W_0 into level 4; each phase only
+    into the levels its release step frees; an entry is `fresh` (its first
+    k-step overwrites) exactly when it is the first, in issue order, to write
+    each of its levels, and every level has one; N = 64 x nplanes <= 256."""
+    phases = _schedule()
     want = {(i, j, i + j) for i in range(5) for j in range(5) if i + j <= 4}
     want |= {(i, 9 - i, 4) for i in range(5)} | {(5, 0, 4)}
-    got = []
-    for phase, levels in ((X, {2, 3, 4}), (Y, {0, 1})):
-        first = phase[0]
-        assert set(range(first[3], first[3] + first[2])) == levels
-        for a, w, npl, lev in phase:
-            assert 1 <= npl <= 4 and 0 <= a <= 5
+    got, written = [], set()
+    for phase, levels in zip(phases, PHASE_LEVELS):
+        for a, w, npl, lev, fresh in phase:
+            assert 1 <= npl <= 4 and 0 <= a <= 5 and fresh in (0, 1)
             assert w + npl <= 5 or npl == 1, "merged planes must be plain W planes"
-            for k in range(npl):
-                assert lev + k in levels
-                got.append((a, w + k, lev + k))
+            mine = set(range(lev, lev + npl))
+            assert mine <= levels
+            if fresh:
+                assert not (mine & written), "a fresh entry would overwrite an earlier product"
+            else:
+                assert mine <= written, "an accumulating entry would add to the previous tile's level"
+            written |= mine
+            got += [(a, w + k, lev + k) for k in range(npl)]
+    assert written == {0, 1, 2, 3, 4}
     assert sorted(got) == sorted(want) and len(got) == 21
-    assert len(X) + len(Y) == 13
+    assert sum(len(p) for p in phases) == 15
 
 
 @pytest.mark.parametrize("plant", ["no_a_digit5", "no_w_digit5", "no_level4", "level1_sign", "w_transposed"])
@@ -550,21 +560,22 @@ class _Bar:
         return (self.done & 1) != parity
 
 
-def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True):
+def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True, l4_release_early=False):
     rng = random.Random(seed)
     state = lambda i: (t_begin + i) // tiles_per_state
     new_state = lambda i: i > 0 and state(i) != state(i - 1)
     full, empty = [_Bar(1), _Bar(1)], [_Bar(8), _Bar(8)]
-    afull, mdone, dfree, dfree01 = _Bar(8), _Bar(1), _Bar(8), _Bar(8)
+    afull, mdone, dfree, dfree01, dfree4 = _Bar(8), _Bar(1), _Bar(8), _Bar(8), _Bar(8)
     efull = [_Bar(8), _Bar(8)]
     xbar = [[_Bar(2) for _ in range(4)] for _ in range(2)]
     wfull, wfree = _Bar(1), _Bar(1)
     events, now, last_finish = [], [0.0], [0.0]
     W = {"state": state(0), "writing": None}
     A = {"tile": None}                   # tile whose digits the A planes hold
-    # levels 2-4 and levels 0-1 of the accumulators: tile they hold, and whether
-    # the drainers are done with them (folded, resp. read back)
-    D24 = {"tile": None, "free": True}
+    # level 4, levels 2-3 and levels 0-1 of the accumulators: tile they hold, and
+    # whether the drainers are done with them (read into registers, folded, read back)
+    D4 = {"tile": None, "free": True}
+    D23 = {"tile": None, "free": True}
     D01 = {"tile": None, "free": True}
     slot_of = {0: None, 1: None}
     xe = {}                              # (parity, quad, half) -> tile
@@ -606,16 +617,23 @@ def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True):
                 yield lambda: wfull.ok(seen & 1)
                 seen += 1
             yield lambda: afull.ok(i & 1)
-            if i >= 1:                   # levels 2-4 first
-                yield lambda: dfree.ok((i - 1) & 1)
+            if i >= 1:                   # level 4 first
+                yield lambda: dfree4.ok((i - 1) & 1)
             if W["state"] != state(i) or W["writing"] is not None:
                 errors.append("MMA reads the wrong W")
             if A["tile"] != i:
                 errors.append("MMA reads digits of another tile")
-            if not D24["free"]:
-                errors.append("levels 2-4 overwritten before they were folded")
-            D24["tile"], D24["free"] = None, False
+            if not D4["free"]:
+                errors.append("level 4 overwritten before it was read")
+            D4["tile"], D4["free"] = None, False
             inflight[i] = state(i)
+            if i >= 1:                   # then levels 2-3
+                yield lambda: dfree.ok((i - 1) & 1)
+            if not D23["free"]:
+                errors.append("levels 2-3 overwritten before they were folded")
+            if A["tile"] != i or W["state"] != state(i):
+                errors.append("MMA reads digits of another tile")
+            D23["tile"], D23["free"] = None, False
             if i >= 1:                   # then levels 0-1
                 yield lambda: dfree01.ok((i - 1) & 1)
             if not D01["free"]:
@@ -626,7 +644,7 @@ def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True):
 
             def finish(i=i, last=(i + 1 < my and new_state(i + 1))):
                 del inflight[i]
-                D24["tile"] = D01["tile"] = i
+                D4["tile"] = D23["tile"] = D01["tile"] = i
                 mdone.arrive()
                 if last:
                     wfree.arrive()
@@ -667,16 +685,28 @@ def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True):
             par = i & 1
             yield lambda: mdone.ok(i & 1)
             yield lambda: efull[par].ok((i >> 1) & 1)
-            if D24["tile"] != i or D01["tile"] != i:
+            if D4["tile"] != i or D23["tile"] != i or D01["tile"] != i:
                 errors.append("accumulators read before their MMAs finished")
             if etab[par] != i:
                 errors.append("exponent table holds another tile")
-            yield ("sleep", rng.uniform(0, 1))     # fold into levels 0-1
-            if D01["tile"] != i:
+
+            def release4():
+                dfree4.arrive()
+                if dfree4.pending == dfree4.count:   # the eighth drainer warp: level 4 free
+                    D4["free"] = True
+            if l4_release_early:
+                release4()
+            yield ("sleep", rng.uniform(0, 0.5))   # level 4 into registers
+            if D4["tile"] != i:
+                errors.append("level 4 read after the next tile's MMAs wrote it")
+            if not l4_release_early:
+                release4()
+            yield ("sleep", rng.uniform(0, 1))     # fold levels 0-3 (and the held level 4) into levels 0-1
+            if D23["tile"] != i or D01["tile"] != i:
                 errors.append("folded pairs written over another tile's levels")
             dfree.arrive()
-            if dfree.pending == dfree.count:   # the eighth drainer warp: levels 2-4 free
-                D24["free"] = True
+            if dfree.pending == dfree.count:   # levels 2-3 free
+                D23["free"] = True
             yield ("sleep", rng.uniform(0, 1))     # read the pairs back
             if D01["tile"] != i:
                 errors.append("pairs read back from another tile")
@@ -734,4 +764,11 @@ def test_exponent_table_written_before_the_mdone_wait_is_caught_by_the_model():
     """Writing tile i's row exponents before waiting for tile i - 1's MMAs lets
     them overwrite tile i - 2's entry while its drainers are still storing."""
     fails = sum(1 for seed in range(200) if _simulate(20, 1 << 20, 0, seed, etab_after_mdone=False))
+    assert fails > 20
+
+
+def test_level_four_released_before_it_is_read_is_caught_by_the_model():
+    """Releasing level 4 to the next tile's MMAs before the drainers have read
+    it into registers lets those MMAs overwrite it mid-read."""
+    fails = sum(1 for seed in range(200) if _simulate(20, 1 << 20, 0, seed, l4_release_early=True))
     assert fails > 20
