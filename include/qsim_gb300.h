@@ -101,7 +101,7 @@ typedef enum {
                             complex blocks computed exactly: each row of 64 reals shares a
                             power-of-two scale, amplitudes are cut into six 9-bit integer
                             digits and W into six (fp16), the 21 digit products of levels 0-5
-                            accumulate in FP32 (levels 0-2 exactly, level 5 folded into level 4)
+                            accumulate in FP32, one accumulator per level (levels 0-2 exactly)
                             and are combined in FP32 pairs without FP64 instructions; per pass
                             and output the error is at most 2^-46 times the 2-norm of the
                             32-amplitude row plus 2^-49 of its scale (2^-48 of the norm between

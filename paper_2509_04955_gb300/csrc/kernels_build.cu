@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_blocks(const DevBlock* 
     // complex128 pass (D = 32): digit planes of the real embedding, entry
     // (nn, k) = W[k][nn], w = 2^-8 sum_j g_j 2^(-9 j) with balanced digits of
     // X = rint(w 2^53) (the host's build_w_digits), fp16, K-major 128-byte
-    // swizzle; planes 5..9 hold 2^-9 g_1 .. 2^-9 g_5
+    // swizzle, planes g_0 .. g_5
     uint16_t* img = wimg + (int64_t)row * wstride + blk.out * wpass;
     for (int e = threadIdx.x; e < 64 * 64; e += kBuildThreads) {
       const int nn = e >> 6, kk = e & 63;
@@ -134,9 +134,7 @@ __global__ void __launch_bounds__(kBuildThreads) k_build_blocks(const DevBlock* 
       g[0] = (int)X;
       const int off = (nn * 128 + (((kk >> 3) ^ (nn & 7)) << 4) + (kk & 7) * 2) >> 1;
 #pragma unroll
-      for (int j = 0; j < 5; ++j) img[j * 4096 + off] = __half_as_ushort(__int2half_rn(g[j]));
-#pragma unroll
-      for (int j = 1; j < 6; ++j) img[(4 + j) * 4096 + off] = __half_as_ushort(__float2half_rn((float)g[j] * 0.001953125f));
+      for (int j = 0; j < 6; ++j) img[j * 4096 + off] = __half_as_ushort(__int2half_rn(g[j]));
     }
   } else {
     // W image: 16-byte chunks of 8 consecutive k (4 input columns) of output row nn,

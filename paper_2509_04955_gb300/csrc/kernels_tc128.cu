@@ -15,20 +15,19 @@
 // written as 2^(E-8) sum_{i<6} d_i 2^(-9 i) with integer digits |d_i| <= 260;
 // each W entry (|w| <= 1) as 2^-8 sum_{j<6} g_j 2^(-9 j), |g_j| <= 256. Digits
 // are small integers, exact in fp16, and a digit product is exact in the
-// MMA. The products A_i W_j with i + j = l (level l) are accumulated in FP32 in
-// tensor memory, one accumulator per level; a level sums at most 4 products
-// of K = 64 terms of magnitude <= 260 * 256, so levels 0..2 stay below 2^24 and
-// are exact integers (level 3 too, save for an adversarial alignment of all
-// 256 of its digit products, which costs at most one unit of level 3). The
-// fifth accumulator holds level 4 plus 2^-9 times level 5 (its products
-// A_i W_(5-i), i = 0..5, against W planes or an A plane pre-scaled by 2^-9,
-// which fp16 holds exactly), rounded in FP32 at about 2^-24 of level 4. The
-// levels, D = 2^(E-16) sum_l acc_l 2^(-9 l), are combined in FP32 pairs
-// (TwoSum) and written back as FP64 by their bit patterns. The digit chain,
-// the fold and the pair output run on (re, im) at once with the packed FP32
-// instructions of sm_100+ (f32x2), and the A digits are stored negated (one
-// instruction per chain step fewer), so the levels hold negated sums, which
-// the fold turns back; every result is bit-identical to the scalar steps. What is dropped
+// MMA. The products A_i W_j with i + j = l (level l, l <= 5) are accumulated
+// in FP32 in tensor memory, one accumulator per level; a level sums at most 6
+// products of K = 64 terms of magnitude <= 260 * 256, so levels 0..2 (at most
+// 3 products) stay below 2^24 and are exact integers (level 3 too, save for an
+// adversarial alignment of all 256 of its digit products, which costs at most
+// one unit of level 3); levels 4 and 5 round in FP32 at about 2^-24 of
+// themselves, far below the result's last bit. The levels,
+// D = 2^(E-16) sum_l acc_l 2^(-9 l), are combined in FP32 pairs (TwoSum) and
+// written back as FP64 by their bit patterns. The digit chain, the fold and
+// the pair output run on (re, im) at once with the packed FP32 instructions of
+// sm_100+ (f32x2), and the A digits are stored negated (one instruction per
+// chain step fewer), so the levels hold negated sums, which the fold turns
+// back; every result is bit-identical to the scalar steps. What is dropped
 // (each FP64 value's mantissa bits below its 47th, W's bits below 2^-54,
 // levels above 5) bounds the error of an output by 2^-46 ||a||_2 + 2^(E-49),
 // ||a||_2 the 2-norm of its row (Cauchy-Schwarz over a unit column of W) and
@@ -42,19 +41,22 @@
 //            one of two 64 KiB landing slots;
 //   warps 0-7 converters, thread = (row, column half): the row's exponent (the
 //            two halves exchange their maxima), then the six digit planes of
-//            the tile written to tensor memory with tcgen05.st (A operand);
-//   warp 17  one thread issues the 21 products x 4 k-steps (M = 128, N = 64,
-//            K = 16, A from tensor memory, W planes from shared memory) and
-//            commits;
-//   warps 8-15 drainers, thread = (row, column half): per 8 columns, tcgen05.ld
-//            of the five accumulators, the levels folded into an FP32 pair
-//            written back over levels 0-1 (releasing levels 2-4), then the
-//            pairs read back, joined to FP64 and stored to HBM.
-// Tensor memory (512 columns): A digit planes at 32 p (p < 6), level-l
-// accumulator at 192 + 64 l. Both are single-buffered: a tile's digits wait
-// for the previous tile's MMAs (the first 8 columns are computed before the
-// wait), its level 2-4 products for the previous tile's fold and its level
-// 0-1 products for the read-back; the landing slots keep the loads streaming.
+//            the tile: planes 0-3 written to tensor memory with tcgen05.st,
+//            planes 4-5 to shared memory (the A operand);
+//   warp 17  one thread issues the 21 products x 4 k-steps as 8 instructions
+//            per k-step (M = 128, N = 64..256, K = 16, W planes from shared
+//            memory) and commits;
+//   warps 8-15 drainers, thread = (row, column half): levels 4 and 5 of the
+//            thread's columns combined into registers (releasing them), then
+//            per 8 columns tcgen05.ld of levels 0-3 (the last load releases
+//            them), the fold into an FP32 pair, and the stores to HBM (as FP64
+//            or as the pair).
+// Tensor memory (512 columns): A digit planes 0-3 at 32 p, level-l
+// accumulator at 128 + 64 l (l < 6). Both are single-buffered: a tile's digits
+// wait for the previous tile's MMAs (the first 8 columns are computed before
+// the wait), its level 4-5 products for the previous tile's levels 4-5 to be
+// combined and its other products for the previous tile's levels 0-3 to be
+// read; the landing slots keep the loads streaming.
 //
 // Every wait is bounded (`spin` polls; the waits for copies and MMAs already in
 // flight at an abort use kTcSpinLimit): a wait that runs out records *err = 1,
@@ -72,9 +74,11 @@ constexpr int kT2Warps = 16;                              // converters + draine
 constexpr int kT2Threads = (kT2Warps + 2) * 32;           // + producer warp + MMA warp
 constexpr int kT2SlotBytes = 65536;                       // 4096 complex128
 constexpr int kT2PlaneBytes = 8192;                       // W digit plane: 64 (N) x 64 (K) fp16, SW128
-constexpr int kT2WBytes = 10 * kT2PlaneBytes;           // g_0..g_4, then 2^-9 g_1..2^-9 g_5
+constexpr int kT2WBytes = 6 * kT2PlaneBytes;              // g_0 .. g_5
+constexpr int kT2APlaneBytes = 16384;                     // A digit plane in shared memory: 128 (M) x 64 (K) fp16, SW128
+constexpr int kT2ASmem = 2 * kT2APlaneBytes;              // A planes 4 and 5
 constexpr uint32_t kT2TmemCols = 512;
-constexpr uint32_t kT2AccCol = 192;
+constexpr uint32_t kT2AccCol = 128;                       // A planes 0-3 at 32 p, level l at 128 + 64 l
 // kind::f16, fp16 A and B, FP32 D, both K-major, N = 64 x nplanes (bits 17-22), M = 128 (bits 24-28)
 constexpr uint32_t t2_idesc(int nplanes) {
   return (1u << 4) | ((64u * (uint32_t)nplanes >> 3) << 17) | ((128u >> 4) << 24);
@@ -88,30 +92,33 @@ __device__ __forceinline__ void t2_mma(uint32_t tmem_d, uint32_t tmem_a, uint64_
       "r"(tmem_a), "l"(b), "r"(idesc), "r"(acc));
 }
 
+// The same with A from shared memory (a descriptor, like B).
+__device__ __forceinline__ void t2_mma_ss(uint32_t tmem_d, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+}
+
 // The MMA schedule of a tile (per k-step; every entry runs for the 4 k-steps).
 // An entry multiplies A digit plane `a` by `nplanes` consecutive W planes
 // starting at `w` (B rows 64 x nplanes: the planes lie back to back in shared
 // memory) into as many consecutive level accumulators starting at `level`
 // (64 tensor-memory columns each, also back to back), so A_a W_j lands in
-// level a + j. Planes 5..9 hold 2^-9 W_1 .. 2^-9 W_5 (plane 9 - a pairs with
-// A_a for the level-5 products folded into level 4) and A plane 5 holds
-// 2^-9 A_5. An instruction costs about the same for N = 64 and N = 128, so
-// merging consecutive planes cuts the 21 products to 15 instructions, split
-// in three phases by the levels they write so that each may start as soon as
-// the drainers have released those levels of the previous tile.
+// level a + j, for the 21 products with a + j <= 5. An instruction costs about
+// the same for any N up to 128 (and 1.4 times that at N = 256), so each A
+// plane meets all its W planes in one or two instructions: 8 per k-step. A
+// planes 0-3 are read from tensor memory, 4 and 5 from shared memory. Phase H
+// writes levels 4-5 only, as soon as the previous tile's levels 4-5 have been
+// read; phase L the rest, once the previous tile's levels 0-3 have been read.
+// `fresh`: the entry's first k-step overwrites its accumulators (the first
+// write of each level in the tile).
 struct T2Mma {
   int a, w, nplanes, level, fresh;
 };
-// phase X4: level 4 alone (the level-5 products folded in, then A_4 W_0), as
-// soon as the previous tile's level 4 has been read; phase X23: levels 2-3
-// (and the rest of level 4) once its levels 2-3 have been folded; phase Y:
-// levels 0-1 once the folded pairs have been read back. `fresh`: the entry's
-// first k-step overwrites its accumulators.
-__device__ constexpr T2Mma kT2PhaseX4[] = {{0, 9, 1, 4, 1}, {1, 8, 1, 4, 0}, {2, 7, 1, 4, 0}, {3, 6, 1, 4, 0},
-                                           {4, 5, 1, 4, 0}, {5, 0, 1, 4, 0}, {4, 0, 1, 4, 0}};
-__device__ constexpr T2Mma kT2PhaseX23[] = {{2, 0, 1, 2, 1}, {3, 0, 1, 3, 1}, {2, 1, 2, 3, 0},
-                                            {1, 1, 3, 2, 0}, {0, 2, 3, 2, 0}, {3, 1, 1, 4, 0}};
-__device__ constexpr T2Mma kT2PhaseY[] = {{0, 0, 2, 0, 1}, {1, 0, 1, 1, 0}};
+__device__ constexpr T2Mma kT2PhaseH[] = {{0, 4, 2, 4, 1}, {1, 4, 1, 5, 0}, {4, 0, 2, 4, 0}, {5, 0, 1, 5, 0}};
+__device__ constexpr T2Mma kT2PhaseL[] = {{0, 0, 4, 0, 1}, {1, 0, 4, 1, 0}, {2, 0, 4, 2, 0}, {3, 0, 3, 3, 0}};
 
 __device__ __forceinline__ void tmem_st8(uint32_t taddr, const uint32_t* v) {
   asm volatile("tcgen05.st.sync.aligned.32x32b.x8.b32 [%0], {%1,%2,%3,%4,%5,%6,%7,%8};" ::"r"(taddr), "r"(v[0]),
@@ -140,8 +147,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t* r) {
 // The start of the six digits of one FP64 value a (bit pattern whi:wlo) of a
 // row whose biased-exponent maximum is emax_b (fe_off = 134 - emax_b):
 // s = a 2^(8 - E), E = emax_b - 1022, so |s| < 256, and s ~ sum_{i<6} d_i
-// 2^(-9 i) (d5 is held as 2^-9 d5, the form its tensor-memory plane holds);
-// the error is below 2^-39 (the 6 FP64 mantissa bits the split drops) and
+// 2^(-9 i); the error is below 2^-39 (the 6 FP64 mantissa bits the split drops) and
 // 2^-46. The FP64 mantissa is cut by bits into hi (sign, exponent, top 23
 // stored bits) and lo18 (the next 23 bits, pre-scaled by 2^18); the digit
 // chain (t2_nchain2) takes digits from hi with exact FP32 steps until hi is
@@ -163,7 +169,7 @@ __device__ __forceinline__ void t2_hilo(uint32_t whi, uint32_t wlo, int fe_off, 
 
 // The digit chain on (re, im) at once with packed FP32 instructions, from hi
 // (|hi| < 256) and lo18 (the next bits, scaled by 2^18): nd[i] = -d_i, the
-// digits negated (nd[5] = -2^-9 d5). Every step is the exact negation of
+// digits negated. Every step is the exact negation of
 // rounding to an integer by x + 1.5 2^23 - 1.5 2^23 and of the exact
 // residual fma(t, 512, -d): u = t 512 + M holds M + d, M - u = -d is exact,
 // and fma(t, 512, -d) continues the chain, one packed instruction each. The
@@ -188,8 +194,7 @@ __device__ __forceinline__ void t2_nchain2(float2 hi, float2 lo18, float2* nd) {
   nd[4] = __ffma2_rn(u, N1, M);
   t = __ffma2_rn(t, C512, nd[4]);
   u = __ffma2_rn(t, C512, M);
-  nd[5] = __ffma2_rn(u, make_float2(-0.001953125f, -0.001953125f),
-                     make_float2(kT2Magic * 0.001953125f, kT2Magic * 0.001953125f));
+  nd[5] = __ffma2_rn(u, N1, M);
 }
 
 // The same six digits (negated) of (re, im) held as FP32 pairs s + e (|e| <=
@@ -250,17 +255,18 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   extern __shared__ __align__(1024) unsigned char t2_smem_raw[];
   unsigned char* smem = (unsigned char*)(((uintptr_t)t2_smem_raw + 1023) & ~(uintptr_t)1023);
   unsigned char* slots = smem;                                  // 2 x 64 KiB
-  unsigned char* W = smem + 2 * kT2SlotBytes;                   // 10 digit planes
-  uint64_t* tbase = (uint64_t*)(W + kT2WBytes);                 // 4 x 256: tile number byte -> offset
+  unsigned char* W = smem + 2 * kT2SlotBytes;                   // 6 W digit planes
+  unsigned char* A45 = W + kT2WBytes;                           // A digit planes 4 and 5
+  uint64_t* tbase = (uint64_t*)(A45 + kT2ASmem);                // 4 x 256: tile number byte -> offset
   uint64_t* runoff = tbase + 4 * 256;                           // 32: global offset of run j
   uint64_t* coff = runoff + 32;                                 // 32: global offset of column c
   uint32_t* lamcol = (uint32_t*)(coff + 32);                    // 32: tile-local index of column c
   int32_t* xe = (int32_t*)(lamcol + 32);                        // [2][128][2]: half-row exponent maxima
   int32_t* etab = xe + 2 * 128 * 2;                             // [2][128]: row scale exponents E
   int32_t* qpos = etab + 2 * 128;                               // tile[12], row[7], col[5], p
-  // full[2] empty[2] afull mdone dfree efull[2] wfull wfree xbar[2][4] dfree01 dfree4
+  // full[2] empty[2] afull mdone dfree efull[2] wfull wfree xbar[2][4] dfree45
   uint64_t* bar = (uint64_t*)(qpos + 26);
-  uint32_t* tmem_slot = (uint32_t*)(bar + 21);
+  uint32_t* tmem_slot = (uint32_t*)(bar + 20);
   __shared__ int s_abort;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -275,10 +281,10 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     while (pp < 12 && p.tile[pp] == pp) ++pp;
     qpos[24] = pp;
     s_abort = 0;
-    // arrivals: full, wfull, wfree, mdone: 1 (expect_tx / commit); empty, afull, dfree, efull, dfree01, dfree4:
+    // arrivals: full, wfull, wfree, mdone: 1 (expect_tx / commit); empty, afull, dfree, efull, dfree45:
     // one per warp of 8; xbar (row-exponent exchange of converter warps quad and quad + 4): 2
-    const uint32_t cnt[21] = {1, 1, 8, 8, 8, 1, 8, 8, 8, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 8, 8};
-    for (int i = 0; i < 21; ++i)
+    const uint32_t cnt[20] = {1, 1, 8, 8, 8, 1, 8, 8, 8, 1, 1, 2, 2, 2, 2, 2, 2, 2, 2, 8};
+    for (int i = 0; i < 20; ++i)
       asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar + i)), "r"(cnt[i]));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -339,13 +345,12 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   uint64_t* empty = bar + 2;
   uint64_t* afull = bar + 4;
   uint64_t* mdone = bar + 5;
-  uint64_t* dfree = bar + 6;      // levels 2-3 of the accumulators read (folded into levels 0-1)
+  uint64_t* dfree = bar + 6;      // levels 0-3 of the accumulators read
   uint64_t* efull = bar + 7;
   uint64_t* wfull = bar + 9;
   uint64_t* wfree = bar + 10;     // completes when the MMAs on a state's W planes are done
   uint64_t* xbar = bar + 11;      // [parity][quad]
-  uint64_t* dfree01 = bar + 19;   // levels 0-1 (the folded FP32 pairs) read
-  uint64_t* dfree4 = bar + 20;    // level 4 read (held in registers by the drainers)
+  uint64_t* dfree45 = bar + 19;   // levels 4-5 read (combined and held in registers by the drainers)
   auto tile_of = [&](uint64_t i) -> uint64_t { return t_begin + i * tstep; };
   auto state_ptr = [&](uint64_t tt) -> double2* {
     if constexpr (MULTI) return (double2*)psis[tt >> lg_tiles1];
@@ -415,11 +420,18 @@ __global__ void __launch_bounds__(kT2Threads, 1)
       if (w_issued > 0) mbar_wait(smem_u32(wfull), (uint32_t)((w_issued - 1) & 1));
     }
   } else if (warp == kT2Warps + 1) {
-    // ---------------- MMA issue (one thread): level l = i + j gets A_i W_j; the
-    // level-4 accumulator also A_i (2^-9 W_(5-i)), i = 0..4 (planes 9 - i), and
-    // (2^-9 A_5) W_0
+    // ---------------- MMA issue (one thread): level l = i + j gets A_i W_j (i + j <= 5)
     if (lane == 0) {
-      const uint32_t wb = smem_u32(W);
+      const uint32_t wb = smem_u32(W), ab = smem_u32(A45);
+      auto issue = [&](const T2Mma& m) {
+#pragma unroll
+        for (int ks = 0; ks < 4; ++ks) {
+          const uint32_t d = tmem + kT2AccCol + 64 * m.level, acc = (m.fresh && ks == 0) ? 0u : 1u;
+          const uint64_t b = smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks);
+          if (m.a < 4) t2_mma(d, tmem + 32 * m.a + 8 * ks, b, t2_idesc(m.nplanes), acc);
+          else t2_mma_ss(d, smem_desc(ab + (m.a - 4) * kT2APlaneBytes + 32 * ks), b, t2_idesc(m.nplanes), acc);
+        }
+      };
       uint64_t i = 0, w_seen = 0;
       for (; i < my; ++i) {
         if (*(volatile int*)&s_abort) break;
@@ -428,16 +440,10 @@ __global__ void __launch_bounds__(kT2Threads, 1)
           ++w_seen;
         }
         if (!mbar_wait(smem_u32(afull), (uint32_t)(i & 1), spin)) { fail(1); break; }
-        if (i >= 1 && !mbar_wait(smem_u32(dfree4), (uint32_t)((i - 1) & 1), spin)) { fail(1); break; }
+        if (i >= 1 && !mbar_wait(smem_u32(dfree45), (uint32_t)((i - 1) & 1), spin)) { fail(1); break; }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int e = 0; e < (int)(sizeof(kT2PhaseX4) / sizeof(T2Mma)); ++e) {
-          const T2Mma m = kT2PhaseX4[e];
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            t2_mma(tmem + kT2AccCol + 64 * m.level, tmem + 32 * m.a + 8 * ks,
-                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (m.fresh && ks == 0) ? 0u : 1u);
-        }
+        for (int e = 0; e < (int)(sizeof(kT2PhaseH) / sizeof(T2Mma)); ++e) issue(kT2PhaseH[e]);
         if (i >= 1 && !mbar_wait(smem_u32(dfree), (uint32_t)((i - 1) & 1), spin)) {
           mma_commit(smem_u32(mdone));   // the issued MMAs complete before the abort drain below
           ++i;
@@ -446,28 +452,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 #pragma unroll
-        for (int e = 0; e < (int)(sizeof(kT2PhaseX23) / sizeof(T2Mma)); ++e) {
-          const T2Mma m = kT2PhaseX23[e];
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            t2_mma(tmem + kT2AccCol + 64 * m.level, tmem + 32 * m.a + 8 * ks,
-                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (m.fresh && ks == 0) ? 0u : 1u);
-        }
-        if (i >= 1 && !mbar_wait(smem_u32(dfree01), (uint32_t)((i - 1) & 1), spin)) {
-          mma_commit(smem_u32(mdone));
-          ++i;
-          fail(1);
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-#pragma unroll
-        for (int e = 0; e < (int)(sizeof(kT2PhaseY) / sizeof(T2Mma)); ++e) {
-          const T2Mma m = kT2PhaseY[e];
-#pragma unroll
-          for (int ks = 0; ks < 4; ++ks)
-            t2_mma(tmem + kT2AccCol + 64 * m.level, tmem + 32 * m.a + 8 * ks,
-                   smem_desc(wb + m.w * kT2PlaneBytes + 32 * ks), t2_idesc(m.nplanes), (m.fresh && ks == 0) ? 0u : 1u);
-        }
+        for (int e = 0; e < (int)(sizeof(kT2PhaseL) / sizeof(T2Mma)); ++e) issue(kT2PhaseL[e]);
         mma_commit(smem_u32(mdone));
         if (i + 1 < my && new_state(i + 1)) mma_commit(smem_u32(wfree));   // last tile on these planes
       }
@@ -553,10 +538,20 @@ __global__ void __launch_bounds__(kT2Threads, 1)
             if (lane == 0) mbar_arrive(smem_u32(efull + par));
           }
 #pragma unroll
-          for (int q = 0; q < 6; ++q) tmem_st8(tmem + tq + 32 * q + 16 * h + 8 * c8, pl[q]);
+          for (int q = 0; q < 4; ++q) tmem_st8(tmem + tq + 32 * q + 16 * h + 8 * c8, pl[q]);
+          // planes 4 and 5 into shared memory: this thread's row, 16-byte chunks
+          // 4h + 2c8 and 4h + 2c8 + 1 of its 128-byte K run, 128-byte swizzle
+#pragma unroll
+          for (int q = 4; q < 6; ++q) {
+            unsigned char* ap = A45 + (q - 4) * kT2APlaneBytes + row * 128;
+            const int c0 = 4 * h + 2 * c8;
+            *(uint4*)(ap + ((c0 ^ (row & 7)) << 4)) = make_uint4(pl[q][0], pl[q][1], pl[q][2], pl[q][3]);
+            *(uint4*)(ap + (((c0 + 1) ^ (row & 7)) << 4)) = make_uint4(pl[q][4], pl[q][5], pl[q][6], pl[q][7]);
+          }
         }
         if (!ok) break;
         asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");   // A planes 4-5 are read by the MMA
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         __syncwarp();
         if (lane == 0) {
@@ -578,16 +573,32 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         const uint64_t tt = tile_of(i);
         double2* __restrict__ psi = state_ptr(tt);
         const uint64_t rb = tile_base(tt & tmask1) | roff;
-        // level 4 of this thread's 32 columns first, held in registers, which
-        // releases it to the next tile's level-4 MMAs; then per 8 columns
-        // levels 0-3 folded with it into an FP32 pair written back over levels
-        // 0 and 1, which releases levels 2-3
+        // levels 4 and 5 of this thread's 32 columns first, combined into one
+        // FP32 value per column (t = -(2^-36 L4 + 2^-45 L5), the levels holding
+        // negated sums), which releases them to the next tile's phase H; then
+        // per 8 columns levels 0-3 folded with t into an FP32 pair and stored
         const uint32_t col0 = tmem + tq + kT2AccCol + 32 * h;
-        float l4[32];
-        tmem_ld32(col0 + 64 * 4, l4);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(dfree4));
+        float t45[32];
+        {
+          uint32_t l4[32], l5[32];
+          tmem_ld16(col0 + 64 * 4, l4);
+          tmem_ld16(col0 + 64 * 4 + 16, l4 + 16);
+          tmem_ld16(col0 + 64 * 5, l5);
+          tmem_ld16(col0 + 64 * 5 + 16, l5 + 16);
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) mbar_arrive(smem_u32(dfree45));
+#pragma unroll
+          for (int k = 0; k < 32; k += 2) {
+            const float2 v4 = make_float2(__uint_as_float(l4[k]), __uint_as_float(l4[k + 1]));
+            const float2 v5 = make_float2(__uint_as_float(l5[k]), __uint_as_float(l5[k + 1]));
+            const float2 t = __ffma2_rn(v5, make_float2(-2.842170943040401e-14f, -2.842170943040401e-14f),
+                                        __fmul2_rn(v4, make_float2(-1.4551915228366852e-11f, -1.4551915228366852e-11f)));
+            t45[k] = t.x;
+            t45[k + 1] = t.y;
+          }
+        }
 #pragma unroll
         for (int c4 = 0; c4 < 4; ++c4) {
           const uint32_t col = col0 + 8 * c4;
@@ -595,57 +606,32 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 #pragma unroll
           for (int l = 0; l < 4; ++l) tmem_ld8(col + 64 * l, a[l]);
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          uint32_t ps[8], pe[8];
+          if (c4 == 3) {   // levels 0-3 read; the last fold and stores follow
+            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_u32(dfree));
+          }
 #pragma unroll
           for (int k = 0; k < 8; k += 2) {
             // the levels hold the negated sums (the A digits are negated)
             auto lv = [&](int l) { return make_float2(__uint_as_float(a[l][k]), __uint_as_float(a[l][k + 1])); };
-            float2 sk = __fmul2_rn(lv(0), make_float2(-1.f, -1.f)), ek = make_float2(0.f, 0.f);
+            float2 sk = __fmul2_rn(lv(0), make_float2(-1.f, -1.f));
+            float2 ek = make_float2(t45[8 * c4 + k], t45[8 * c4 + k + 1]);
             t2_absorb2(sk, ek, lv(1), make_float2(-0.001953125f, -0.001953125f));
             t2_absorb2(sk, ek, lv(2), make_float2(-3.814697265625e-06f, -3.814697265625e-06f));
             t2_absorb2(sk, ek, lv(3), make_float2(-7.450580596923828e-09f, -7.450580596923828e-09f));
-            ek = __ffma2_rn(make_float2(l4[8 * c4 + k], l4[8 * c4 + k + 1]),
-                            make_float2(-1.4551915228366852e-11f, -1.4551915228366852e-11f), ek);
-            ps[k] = __float_as_uint(sk.x);
-            ps[k + 1] = __float_as_uint(sk.y);
-            pe[k] = __float_as_uint(ek.x);
-            pe[k + 1] = __float_as_uint(ek.y);
-          }
-          tmem_st8(col, ps);
-          tmem_st8(col + 64, pe);
-        }
-        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(dfree));
-        // the pairs back, joined to FP64 and stored
-#pragma unroll 1
-        for (int c4 = 0; c4 < 4; ++c4) {
-          const uint32_t col = col0 + 8 * c4;
-          uint32_t ps[8], pe[8];
-          tmem_ld8(col, ps);
-          tmem_ld8(col + 64, pe);
-          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (c4 == 3) {   // levels 0-1 read; the last stores follow
-            asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-            __syncwarp();
-            if (lane == 0) mbar_arrive(smem_u32(dfree01));
-          }
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
+            double2* dst = psi + (rb | coff[16 * h + 4 * c4 + (k >> 1)]);
             if constexpr (POUT) {
-              const float2 s2 = make_float2(__uint_as_float(ps[2 * j]), __uint_as_float(ps[2 * j + 1]));
-              const float2 e2 = make_float2(__uint_as_float(pe[2 * j]), __uint_as_float(pe[2 * j + 1]));
-              const float2 t2 = __fadd2_rn(s2, e2);                                   // FastTwoSum
-              const float2 f2 = __fadd2_rn(e2, __ffma2_rn(t2, make_float2(-1.f, -1.f), s2));   // e - (t - s)
+              const float2 t2 = __fadd2_rn(sk, ek);                                   // FastTwoSum
+              const float2 f2 = __fadd2_rn(ek, __ffma2_rn(t2, make_float2(-1.f, -1.f), sk));   // e - (t - s)
               const float2 osc2 = make_float2(osc, osc);
               const float2 o1 = __fmul2_rn(t2, osc2), o2 = __fmul2_rn(f2, osc2);
-              *(float4*)(psi + (rb | coff[16 * h + 4 * c4 + j])) = make_float4(o1.x, o1.y, o2.x, o2.y);
+              *(float4*)dst = make_float4(o1.x, o1.y, o2.x, o2.y);
             } else {
               double2 o;
-              o.x = t2_join(__uint_as_float(ps[2 * j]), __uint_as_float(pe[2 * j]), E);
-              o.y = t2_join(__uint_as_float(ps[2 * j + 1]), __uint_as_float(pe[2 * j + 1]), E);
-              psi[rb | coff[16 * h + 4 * c4 + j]] = o;
+              o.x = t2_join(sk.x, ek.x, E);
+              o.y = t2_join(sk.y, ek.y, E);
+              *dst = o;
             }
           }
         }
@@ -660,8 +646,8 @@ __global__ void __launch_bounds__(kT2Threads, 1)
 }
 
 size_t tc128_smem_bytes() {
-  return 2 * (size_t)kT2SlotBytes + kT2WBytes + 4 * 256 * 8 + 32 * 8 * 2 + 32 * 4 + 2 * 128 * 2 * 4 + 2 * 128 * 4 +
-         26 * 4 + 21 * 8 + 16 + 1024;
+  return 2 * (size_t)kT2SlotBytes + kT2WBytes + kT2ASmem + 4 * 256 * 8 + 32 * 8 * 2 + 32 * 4 + 2 * 128 * 2 * 4 + 2 * 128 * 4 +
+         26 * 4 + 20 * 8 + 16 + 1024;
 }
 
 static bool g_tc128_ready = false;

@@ -104,8 +104,8 @@ struct Tc5PassDesc {
   // im.e, value s + e), 0 = as complex128
   int32_t in_pairs, out_pairs;
 };
-// uint16 elements of one pass's W digit planes: g_0..g_4 and 2^-9 g_1..2^-9 g_5, 4096 each
-constexpr int64_t kTc128WElems = 10 * 4096;
+// uint16 elements of one pass's W digit planes g_0..g_5, 4096 each
+constexpr int64_t kTc128WElems = 6 * 4096;
 cudaError_t prepare_tc128_pass();
 size_t tc128_smem_bytes();
 // psis: device array of nstates state pointers (psi unused), else psi alone; wstride (uint16

@@ -358,11 +358,9 @@ float w_to_float(uint16_t v, bool half) { return half ? f16_to_float(v) : bf16_t
 // Digit planes of a 32x32 complex block U for the complex128 tensor-core pass:
 // entry (nn, k) of the N x K = 64 x 64 operand is W[k][nn] of the real
 // embedding, w = 2^-8 sum_{j<6} g_j 2^(-9 j) with balanced integer digits
-// (|g_j| <= 256; X = rint(w 2^53) split from the bottom), plane j (j < 5)
+// (|g_j| <= 256; X = rint(w 2^53) split from the bottom), plane j (j < 6)
 // stored as fp16 integers in the K-major 128-byte-swizzled layout (8 KiB per
-// plane), then planes 5..9 = 2^-9 g_1 .. 2^-9 g_5 (exact in fp16) for the
-// level-5 products the pass folds into its level-4 accumulator. The device
-// builder (kernels_build.cu) follows the same steps.
+// plane). The device builder (kernels_build.cu) follows the same steps.
 void build_w_digits(const double2* U, uint16_t* img) {
   for (uint32_t nn = 0; nn < 64; ++nn)
     for (uint32_t k = 0; k < 64; ++k) {
@@ -377,15 +375,14 @@ void build_w_digits(const double2* U, uint16_t* img) {
       }
       g[0] = (int)X;
       const size_t off = (nn * 128 + (((k >> 3) ^ (nn & 7)) << 4) + (k & 7) * 2) / 2;
-      for (int j = 0; j < 5; ++j) img[(size_t)j * 4096 + off] = f16_rne((float)g[j]);
-      for (int j = 1; j < 6; ++j) img[(size_t)(4 + j) * 4096 + off] = f16_rne(std::ldexp((float)g[j], -9));
+      for (int j = 0; j < 6; ++j) img[(size_t)j * 4096 + off] = f16_rne((float)g[j]);
     }
 }
 
 // The value an entry (nn, k) of a digit image stands for: 2^-8 sum_{j<6} g_j 2^(-9 j).
 double w_digit_value(const uint16_t* img, uint32_t nn, uint32_t k) {
   const size_t off = (nn * 128 + (((k >> 3) ^ (nn & 7)) << 4) + (k & 7) * 2) / 2;
-  double v = (double)f16_to_float(img[(size_t)9 * 4096 + off]);   // 2^-9 g_5
+  double v = (double)f16_to_float(img[(size_t)5 * 4096 + off]);
   for (int j = 4; j >= 0; --j) v = v / 512.0 + (double)f16_to_float(img[(size_t)j * 4096 + off]);
   return std::ldexp(v, -8);
 }

@@ -12,26 +12,26 @@ what it relies on:
   the host's W digits (six, balanced, |g| <= 256) are within 2^-54 of w;
 * exactness: the level sums of a 64-term row (levels 0..2, and 3 short of an
   adversarial alignment) stay below 2^24, so FP32 accumulation is exact;
-* the combination of the five levels back to FP64 (FP32 pairs joined by
+* the combination of the six levels back to FP64 (FP32 pairs joined by
   integer arithmetic) equals their exact sum to 2^-46 relative, including
   results just below a power of two;
 * the FP32-pair form kept between consecutive passes: digits taken from a
   pair, and a row read and written as pairs, keep the same bounds;
-* a whole row: U psi through digits, exact level sums (level 5 folded into
-  level 4) and the combination is within 2^-46 ||a||_2 + 2^(E-49) of the
+* a whole row: U psi through digits, level sums (six accumulators, levels 0-2
+  exact) and the combination is within 2^-46 ||a||_2 + 2^(E-49) of the
   FP64 product (2^-48 ||a||_2 + 2^(E-49) when the row is read as FP32
   pairs), ||a||_2 the row's 2-norm and 2^E its scale (|a| < 2^E <= 2 max
   |a|), for Haar-random blocks and rows of every shape (random, one non-zero
   entry, mixed magnitudes, FP64 zeros and subnormals, exact powers of two);
   the bound is tight enough that a model with one planted mistake (a digit
-  plane of A or W dropped, the level-4 accumulator lost, a level's sign
+  plane of A or W dropped, the level-4 or level-5 accumulator lost, a level's sign
   flipped, the block transposed) fails it;
 * indexing: runs of >= 2^7 amplitudes land every element (row, column) of a
   tile at its tile-local index, the tiles partition the state, and stores
   go to roff(row) | coff(column) of the tile;
 * barriers: the single-buffered A and accumulator protocol (with the row
   exponent exchange, the exponent table, and the two-step release of the
-  accumulators: levels 2-4 after the fold, levels 0-1 after the read-back)
+  accumulators: levels 4-5 once combined in registers, levels 0-3 once read)
   has no deadlock or hazard under random delays, for 1 to 54 tiles per CTA,
   with and without W reloads.
 """
@@ -84,7 +84,7 @@ def digits(a, emax_b):
     u4 = t * F32(512)
     d4 = rint32(u4)
     t = u4 - d4
-    d5 = rint32(t * F32(512))             # the kernel stores 2^-9 d5 (exact in fp16)
+    d5 = rint32(t * F32(512))
     return np.stack([d0, d1, d2, d3, d4, d5]).astype(np.float64)
 
 
@@ -122,15 +122,23 @@ def pair_row_scale(s):
     return max(int(ex.max()) - 126, -101)
 
 
+def fold(c):
+    """The drainer's fold of the six level sums (float32) into an FP32 pair
+    (s, e): levels 4 and 5 first combined into one value t (one rounding: both
+    products are exact), which starts the error word; then TwoSum of levels
+    1-3 into level 0, each TwoSum's error added to the error word."""
+    c0, c1, c2, c3, c4, c5 = (F32(x) for x in c)
+    e = c4 * F32(2.0 ** -36) + c5 * F32(2.0 ** -45)
+    s = c0
+    for l, cl in ((1, c1), (2, c2), (3, c3)):
+        s, e2 = two_sum(s, cl * F32(2.0 ** (-9 * l)))
+        e = e + e2
+    return s, e
+
+
 def pair_out(c, E):
     """The drainer's pair output: levels folded, FastTwoSum, scaled by 2^(E - 16)."""
-    c0, c1, c2, c3, c4 = (F32(x) for x in c)
-    s, e = two_sum(c0, c1 * F32(2.0 ** -9))
-    s, e2 = two_sum(s, c2 * F32(2.0 ** -18))
-    e = e + e2
-    s, e2 = two_sum(s, c3 * F32(2.0 ** -27))
-    e = e + e2
-    e = c4 * F32(2.0 ** -36) + e
+    s, e = fold(c)
     t = s + e
     e = e - (t - s)
     sc = F32(2.0 ** (E - 16))
@@ -155,15 +163,9 @@ def two_sum(a, b):
 
 
 def combine(c, emax_b):
-    """t2_join after the fold: five level sums (float32) -> FP64 value
+    """t2_join after the fold: six level sums (float32) -> FP64 value
     2^(emax_b - 1038) sum_l c_l 2^(-9 l) (emax_b = E + 1022)."""
-    c0, c1, c2, c3, c4 = (F32(x) for x in c)
-    s, e = two_sum(c0, c1 * F32(2.0 ** -9))
-    s, e2 = two_sum(s, c2 * F32(2.0 ** -18))
-    e = e + e2
-    s, e2 = two_sum(s, c3 * F32(2.0 ** -27))
-    e = e + e2
-    e = c4 * F32(2.0 ** -36) + e
+    s, e = fold(c)
     s2 = s + e
     e = e - (s2 - s)
     s = s2
@@ -223,7 +225,7 @@ def apply_row(U, a, pairs_in=False, pairs_out=False, plant=None):
     out = np.empty(64)
     for nn in range(64):
         lev = []
-        for l in range(5):
+        for l in range(6):
             tot = 0
             for i in range(l + 1):
                 # one K = 16 MMA per k-step: the accumulator after each step
@@ -231,9 +233,9 @@ def apply_row(U, a, pairs_in=False, pairs_out=False, plant=None):
                     tot += int((Di[i, 16 * ks:16 * ks + 16] * Wd[l - i, 16 * ks:16 * ks + 16, nn]).sum())
                     if l <= 2:
                         assert abs(tot) < 2 ** 24, "an exact level left the FP32 integer range"
-            if l == 4:   # level 5 folded in: A_i (2^-9 W_(5-i)), i < 5, and (2^-9 A_5) W_0
-                tot = Fraction(tot) + sum(Fraction(int((Di[i] * Wd[5 - i, :, nn]).sum()), 512) for i in range(0, 6))
             if plant == "no_level4" and l == 4:
+                tot = 0
+            if plant == "no_level5" and l == 5:
                 tot = 0
             if plant == "level1_sign" and l == 1:
                 tot = -tot
@@ -251,7 +253,7 @@ def row_bound(a, em, pairs_in=False):
     of each FP64 value (truncation below 2^-46 relative; an FP32 pair holds
     its value to 2^-48), which a unit column of W turns into at most that
     fraction of the row's 2-norm (Cauchy-Schwarz); the last digit's rounding,
-    W's digit tails (2^-54 per entry) and the level-4 accumulation add less
+    W's digit tails (2^-54 per entry) and the roundings of levels 3-5 add less
     than 2^(E-49)."""
     nrm = float(np.sqrt(np.sum(np.abs(a) ** 2)))
     return (2.0 ** -48 if pairs_in else 2.0 ** -46) * nrm + 2.0 ** (em - 1022 - 49)
@@ -304,7 +306,7 @@ def ndigits_pair(s, e, E):
     nd4 = M - u
     t = t * F32(512) + nd4
     u = t * F32(512) + M
-    nd5 = (M - u)                        # the kernel stores -2^-9 d5 (exact)
+    nd5 = M - u
     return np.stack([nd0, nd1, nd2, nd3, nd4, nd5]).astype(np.float64)
 
 
@@ -334,11 +336,13 @@ def test_combine_equals_the_exact_level_sum():
     for trial in range(3000):
         c = [float(rng.integers(-2 ** 22, 2 ** 22)), float(rng.integers(-2 ** 23, 2 ** 23)),
              float(rng.integers(-3 * 2 ** 22, 3 * 2 ** 22)), float(rng.integers(-2 ** 24, 2 ** 24)),
-             float(F32(rng.standard_normal() * 2.0 ** rng.integers(0, 24)))]
+             float(F32(rng.integers(-2 ** 25, 2 ** 25))), float(F32(rng.integers(-2 ** 25, 2 ** 25)))]
         if trial % 5 == 0:
             c[0] = 0.0
         if trial % 7 == 0:   # just below or above a power of two
-            c = [float(2 ** 20), -1.0 * rng.integers(1, 512), float(rng.integers(-2 ** 10, 2 ** 10)), 0.0, 0.0]
+            c = [float(2 ** 20), -1.0 * rng.integers(1, 512), float(rng.integers(-2 ** 10, 2 ** 10)), 0.0, 0.0, 0.0]
+        if trial % 11 == 0:  # only the low levels
+            c = [0.0, 0.0, 0.0, 0.0, float(rng.integers(-2 ** 20, 2 ** 20)), float(rng.integers(-2 ** 20, 2 ** 20))]
         em = int(rng.integers(900, 1100))
         exact = sum(Fraction(x) * Fraction(2) ** (-9 * l) for l, x in enumerate(c)) * Fraction(2) ** (em - 1038)
         got = combine(c, em)
@@ -400,42 +404,38 @@ def test_a_whole_row_matches_the_fp64_product(shape):
 
 
 def _schedule():
-    """The kernel's MMA schedule tables (kT2PhaseX4, kT2PhaseX23, kT2PhaseY), read from its source."""
+    """The kernel's MMA schedule tables (kT2PhaseH, kT2PhaseL), read from its source."""
     import os
     import re
     src = open(os.path.join(os.path.dirname(__file__), "..", "paper_2509_04955_gb300", "csrc",
                             "kernels_tc128.cu")).read()
     out = []
-    for name in ("kT2PhaseX4", "kT2PhaseX23", "kT2PhaseY"):
+    for name in ("kT2PhaseH", "kT2PhaseL"):
         body = re.search(name + r"\[\] = \{(.*?)\};", src, re.S).group(1)
         out.append([tuple(int(x) for x in m.groups())
                     for m in re.finditer(r"\{\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+),\s*(\d+)\s*\}", body)])
     return out
 
 
-# the levels each phase may write: the previous tile's drainers release level 4
-# first (read into registers), then levels 2-3 (folded), then levels 0-1 (the
-# folded pairs read back)
-PHASE_LEVELS = ({4}, {2, 3, 4}, {0, 1})
+# the levels each phase may write: the previous tile's drainers release levels
+# 4-5 first (combined into registers), then levels 0-3 (read for the fold)
+PHASE_LEVELS = ({4, 5}, {0, 1, 2, 3, 4, 5})
 
 
 def test_mma_schedule_issues_every_digit_product_once():
     """Each entry (a, w, nplanes, level, fresh) multiplies A plane a by W planes
     w .. w + nplanes - 1 into levels level .. level + nplanes - 1. Together the
-    three phases must issue exactly the 21 products of the digit scheme: A_i W_j
-    into level i + j for i + j <= 4 (planes 0-4), A_i (2^-9 W_(5-i)) into level
-    4 for i <= 4 (plane 9 - i), and (2^-9 A_5) W_0 into level 4; each phase only
-    into the levels its release step frees; an entry is `fresh` (its first
-    k-step overwrites) exactly when it is the first, in issue order, to write
-    each of its levels, and every level has one; N = 64 x nplanes <= 256."""
+    two phases must issue exactly the 21 products A_i W_j into level i + j,
+    i + j <= 5, over the six planes of each operand; phase H only into levels
+    4-5 (released first); an entry is `fresh` (its first k-step overwrites)
+    exactly when it is the first, in issue order, to write each of its levels,
+    and every level has one; N = 64 x nplanes <= 256 (four planes)."""
     phases = _schedule()
-    want = {(i, j, i + j) for i in range(5) for j in range(5) if i + j <= 4}
-    want |= {(i, 9 - i, 4) for i in range(5)} | {(5, 0, 4)}
+    want = {(i, j, i + j) for i in range(6) for j in range(6) if i + j <= 5}
     got, written = [], set()
     for phase, levels in zip(phases, PHASE_LEVELS):
         for a, w, npl, lev, fresh in phase:
-            assert 1 <= npl <= 4 and 0 <= a <= 5 and fresh in (0, 1)
-            assert w + npl <= 5 or npl == 1, "merged planes must be plain W planes"
+            assert 1 <= npl <= 4 and 0 <= a <= 5 and fresh in (0, 1) and w + npl <= 6
             mine = set(range(lev, lev + npl))
             assert mine <= levels
             if fresh:
@@ -444,15 +444,16 @@ def test_mma_schedule_issues_every_digit_product_once():
                 assert mine <= written, "an accumulating entry would add to the previous tile's level"
             written |= mine
             got += [(a, w + k, lev + k) for k in range(npl)]
-    assert written == {0, 1, 2, 3, 4}
+    assert written == {0, 1, 2, 3, 4, 5}
     assert sorted(got) == sorted(want) and len(got) == 21
-    assert sum(len(p) for p in phases) == 15
+    assert sum(len(p) for p in phases) == 8
 
 
-@pytest.mark.parametrize("plant", ["no_a_digit5", "no_w_digit5", "no_level4", "level1_sign", "w_transposed"])
+@pytest.mark.parametrize("plant", ["no_a_digit5", "no_w_digit5", "no_level4", "no_level5", "level1_sign",
+                                   "w_transposed"])
 def test_the_row_bound_catches_a_planted_mistake(plant):
     """The whole-row bound is tight enough to fail when the model drops the
-    last digit plane of A or of W or the level-4 accumulator, flips the sign
+    last digit plane of A or of W or the level-4 or level-5 accumulator, flips the sign
     of a level, or transposes the block (rows read as FP32 pairs, the form
     every pass after the first of a run reads): each slip gives an error
     above the bound, the clean model one well below it."""
@@ -560,23 +561,22 @@ class _Bar:
         return (self.done & 1) != parity
 
 
-def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True, l4_release_early=False):
+def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True, l45_release_early=False):
     rng = random.Random(seed)
     state = lambda i: (t_begin + i) // tiles_per_state
     new_state = lambda i: i > 0 and state(i) != state(i - 1)
     full, empty = [_Bar(1), _Bar(1)], [_Bar(8), _Bar(8)]
-    afull, mdone, dfree, dfree01, dfree4 = _Bar(8), _Bar(1), _Bar(8), _Bar(8), _Bar(8)
+    afull, mdone, dfree, dfree45 = _Bar(8), _Bar(1), _Bar(8), _Bar(8)
     efull = [_Bar(8), _Bar(8)]
     xbar = [[_Bar(2) for _ in range(4)] for _ in range(2)]
     wfull, wfree = _Bar(1), _Bar(1)
     events, now, last_finish = [], [0.0], [0.0]
     W = {"state": state(0), "writing": None}
     A = {"tile": None}                   # tile whose digits the A planes hold
-    # level 4, levels 2-3 and levels 0-1 of the accumulators: tile they hold, and
-    # whether the drainers are done with them (read into registers, folded, read back)
-    D4 = {"tile": None, "free": True}
-    D23 = {"tile": None, "free": True}
-    D01 = {"tile": None, "free": True}
+    # levels 4-5 and levels 0-3 of the accumulators: tile they hold, and whether
+    # the drainers are done with them (combined into registers, resp. read for the fold)
+    D45 = {"tile": None, "free": True}
+    D03 = {"tile": None, "free": True}
     slot_of = {0: None, 1: None}
     xe = {}                              # (parity, quad, half) -> tile
     etab = {0: None, 1: None}
@@ -617,34 +617,27 @@ def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True, l4_rele
                 yield lambda: wfull.ok(seen & 1)
                 seen += 1
             yield lambda: afull.ok(i & 1)
-            if i >= 1:                   # level 4 first
-                yield lambda: dfree4.ok((i - 1) & 1)
+            if i >= 1:                   # phase H: levels 4-5 first
+                yield lambda: dfree45.ok((i - 1) & 1)
             if W["state"] != state(i) or W["writing"] is not None:
                 errors.append("MMA reads the wrong W")
             if A["tile"] != i:
                 errors.append("MMA reads digits of another tile")
-            if not D4["free"]:
-                errors.append("level 4 overwritten before it was read")
-            D4["tile"], D4["free"] = None, False
+            if not D45["free"]:
+                errors.append("levels 4-5 overwritten before they were read")
+            D45["tile"], D45["free"] = None, False
             inflight[i] = state(i)
-            if i >= 1:                   # then levels 2-3
+            if i >= 1:                   # phase L: levels 0-3 (and 4-5 again)
                 yield lambda: dfree.ok((i - 1) & 1)
-            if not D23["free"]:
-                errors.append("levels 2-3 overwritten before they were folded")
+            if not D03["free"]:
+                errors.append("levels 0-3 overwritten before they were read")
             if A["tile"] != i or W["state"] != state(i):
                 errors.append("MMA reads digits of another tile")
-            D23["tile"], D23["free"] = None, False
-            if i >= 1:                   # then levels 0-1
-                yield lambda: dfree01.ok((i - 1) & 1)
-            if not D01["free"]:
-                errors.append("levels 0-1 overwritten before they were read back")
-            if A["tile"] != i:
-                errors.append("MMA reads digits of another tile")
-            D01["tile"], D01["free"] = None, False
+            D03["tile"], D03["free"] = None, False
 
             def finish(i=i, last=(i + 1 < my and new_state(i + 1))):
                 del inflight[i]
-                D4["tile"] = D23["tile"] = D01["tile"] = i
+                D45["tile"] = D03["tile"] = i
                 mdone.arrive()
                 if last:
                     wfree.arrive()
@@ -685,34 +678,28 @@ def _simulate(my, tiles_per_state, t_begin, seed, etab_after_mdone=True, l4_rele
             par = i & 1
             yield lambda: mdone.ok(i & 1)
             yield lambda: efull[par].ok((i >> 1) & 1)
-            if D4["tile"] != i or D23["tile"] != i or D01["tile"] != i:
+            if D45["tile"] != i or D03["tile"] != i:
                 errors.append("accumulators read before their MMAs finished")
             if etab[par] != i:
                 errors.append("exponent table holds another tile")
 
-            def release4():
-                dfree4.arrive()
-                if dfree4.pending == dfree4.count:   # the eighth drainer warp: level 4 free
-                    D4["free"] = True
-            if l4_release_early:
-                release4()
-            yield ("sleep", rng.uniform(0, 0.5))   # level 4 into registers
-            if D4["tile"] != i:
-                errors.append("level 4 read after the next tile's MMAs wrote it")
-            if not l4_release_early:
-                release4()
-            yield ("sleep", rng.uniform(0, 1))     # fold levels 0-3 (and the held level 4) into levels 0-1
-            if D23["tile"] != i or D01["tile"] != i:
-                errors.append("folded pairs written over another tile's levels")
+            def release45():
+                dfree45.arrive()
+                if dfree45.pending == dfree45.count:   # the eighth drainer warp: levels 4-5 free
+                    D45["free"] = True
+            if l45_release_early:
+                release45()
+            yield ("sleep", rng.uniform(0, 0.5))   # levels 4-5 into registers
+            if D45["tile"] != i:
+                errors.append("levels 4-5 read after the next tile's MMAs wrote them")
+            if not l45_release_early:
+                release45()
+            yield ("sleep", rng.uniform(0, 1))     # levels 0-3 read chunk by chunk
+            if D03["tile"] != i:
+                errors.append("levels 0-3 read after the next tile's MMAs wrote them")
             dfree.arrive()
-            if dfree.pending == dfree.count:   # levels 2-3 free
-                D23["free"] = True
-            yield ("sleep", rng.uniform(0, 1))     # read the pairs back
-            if D01["tile"] != i:
-                errors.append("pairs read back from another tile")
-            dfree01.arrive()
-            if dfree01.pending == dfree01.count:
-                D01["free"] = True
+            if dfree.pending == dfree.count:
+                D03["free"] = True
             yield ("sleep", rng.uniform(0, 4))   # joins and stores after the release
 
     roles = [producer(), mma()] + [converter(q, h) for h in range(2) for q in range(4)] + \
@@ -767,8 +754,8 @@ def test_exponent_table_written_before_the_mdone_wait_is_caught_by_the_model():
     assert fails > 20
 
 
-def test_level_four_released_before_it_is_read_is_caught_by_the_model():
-    """Releasing level 4 to the next tile's MMAs before the drainers have read
-    it into registers lets those MMAs overwrite it mid-read."""
-    fails = sum(1 for seed in range(200) if _simulate(20, 1 << 20, 0, seed, l4_release_early=True))
+def test_levels_four_five_released_before_they_are_read_is_caught_by_the_model():
+    """Releasing levels 4-5 to the next tile's MMAs before the drainers have
+    read them into registers lets those MMAs overwrite them mid-read."""
+    fails = sum(1 for seed in range(200) if _simulate(20, 1 << 20, 0, seed, l45_release_early=True))
     assert fails > 20
