@@ -263,7 +263,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
   uint32_t* lamcol = (uint32_t*)(coff + 32);                    // 32: tile-local index of column c
   int32_t* xe = (int32_t*)(lamcol + 32);                        // [2][128][2]: half-row exponent maxima
   int32_t* etab = xe + 2 * 128 * 2;                             // [2][128]: row scale exponents E
-  int32_t* qpos = etab + 2 * 128;                               // tile[12], row[7], col[5], p
+  int32_t* qpos = etab + 2 * 128;                               // tile[12], row[7], col[5], p, kq
   // full[2] empty[2] afull mdone dfree efull[2] wfull wfree xbar[2][4] dfree45
   uint64_t* bar = (uint64_t*)(qpos + 26);
   uint32_t* tmem_slot = (uint32_t*)(bar + 20);
@@ -280,6 +280,17 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     int pp = 0;
     while (pp < 12 && p.tile[pp] == pp) ++pp;
     qpos[24] = pp;
+    // how many of the three lowest tile qubits are row qubits (the others are
+    // the lowest block qubits): the slot's bank group of an element is its
+    // tile-local index mod 8, so a warp reading one column for 32 rows sees
+    // only 2^kq of the 8 groups
+    int kq = 0;
+    for (int t = 0; t < 3; ++t) {
+      bool is_col = false;
+      for (int b = 0; b < 5; ++b) is_col |= p.col[b] == p.tile[t];
+      kq += is_col ? 0 : 1;
+    }
+    qpos[25] = kq;
     s_abort = 0;
     // arrivals: full, wfull, wfree, mdone: 1 (expect_tx / commit); empty, afull, dfree, efull, dfree45:
     // one per warp of 8; xbar (row-exponent exchange of converter warps quad and quad + 4): 2
@@ -470,6 +481,12 @@ __global__ void __launch_bounds__(kT2Threads, 1)
     if (converter) {
       uint32_t lrow = 0;
       for (int b = 0; b < 7; ++b) lrow |= (uint32_t)((row >> b) & 1) << lam_of(s_row[b]);
+      // Column skew: lane l reads column j ^ sg at step j, sg taken from the
+      // lane bits above the kq row bits, so the block bits among the three
+      // lowest tile bits vary across the lanes too and every 8 lanes cover the
+      // 8 bank groups; the digit pass undoes the skew in registers.
+      const int kq = qpos[25], mbits = 3 - kq;
+      const uint32_t sg = ((uint32_t)lane >> kq) & ((1u << mbits) - 1u);
       const unsigned char* sl0 = slots;
       for (uint64_t i = 0; i < my; ++i) {
         if (__any_sync(0xffffffffu, *(volatile int*)&s_abort)) break;
@@ -481,7 +498,7 @@ __global__ void __launch_bounds__(kT2Threads, 1)
         int em = 0;
 #pragma unroll 4
         for (int j = 0; j < 16; ++j) {
-          const uint4 v = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + j]));
+          const uint4 v = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + (j ^ (int)sg)]));
           if constexpr (PIN) {
             em = max(em, (int)((v.x >> 23) & 0xffu));
             em = max(em, (int)((v.y >> 23) & 0xffu));
@@ -507,9 +524,26 @@ __global__ void __launch_bounds__(kT2Threads, 1)
           // digits of 8 columns; the first 8 while the previous tile's MMAs may
           // still read the A planes
           uint32_t pl[6][8];
+          uint4 vv[8];
+#pragma unroll
+          for (int j = 0; j < 8; ++j) vv[j] = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + 8 * c8 + (j ^ (int)sg)]));
+          // vv[j] holds column 8 c8 + (j ^ sg): swap back, one bit of sg at a time
+#pragma unroll
+          for (int b = 0; b < 3; ++b) {
+            if (b < mbits) {
+              const bool sw = (sg >> b) & 1u;
+#pragma unroll
+              for (int j = 0; j < 8; ++j)
+                if (!(j & (1 << b))) {
+                  const uint4 x = vv[j], y = vv[j | (1 << b)];
+                  vv[j] = sw ? y : x;
+                  vv[j | (1 << b)] = sw ? x : y;
+                }
+            }
+          }
 #pragma unroll
           for (int j = 0; j < 8; ++j) {
-            const uint4 v = *(const uint4*)(sl + 16u * (lrow | lamcol[16 * h + 8 * c8 + j]));
+            const uint4 v = vv[j];
             float2 nd[6];
             if constexpr (PIN) {
               t2_ndigits_pair2(make_float2(__uint_as_float(v.x), __uint_as_float(v.y)),

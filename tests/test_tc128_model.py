@@ -532,6 +532,43 @@ def test_tile_elements_land_and_store_at_their_amplitudes(Q):
     assert len(seen) == 1 << n
 
 
+def _skew(T, Q, lane):
+    """The converters' column skew: kq = row qubits among the three lowest
+    tile qubits, sg = lane bits kq .. 2 (the kernel's qpos[25] and sg)."""
+    kq = sum(1 for q in T[:3] if q not in Q)
+    return kq, (lane >> kq) & ((1 << (3 - kq)) - 1)
+
+
+@pytest.mark.parametrize("Q", PLACEMENTS + [(20, 22, 25, 27, 29), (5, 6, 7, 8, 9), (0, 1, 2, 3, 29)])
+def test_converter_slot_reads_are_bank_conflict_free(Q):
+    """Every warp-wide 16-byte read of the landing slot (32 rows, lane l at
+    step j taking column j ^ sg(l)) hits each of the 8 bank groups (index
+    mod 8) exactly 4 times, for the exponent pass (16 columns) and the digit
+    pass (8 columns per chunk); each lane still reads all its columns once,
+    and the swap network puts column j into register j."""
+    n = 30
+    Q, R, T, pr, lam, lamcol, coff = _geometry(n, Q)
+    for quad in range(4):
+        lrows = [sum((((quad * 32 + l) >> b) & 1) << lam[R[b]] for b in range(7)) for l in range(32)]
+        for h in range(2):
+            for j in range(16):
+                groups = [0] * 8
+                for l in range(32):
+                    kq, sg = _skew(T, Q, l)
+                    groups[(lrows[l] | lamcol[16 * h + (j ^ sg)]) & 7] += 1
+                assert groups == [4] * 8, (quad, h, j, groups)
+    for l in range(32):
+        kq, sg = _skew(T, Q, l)
+        assert sorted(j ^ sg for j in range(16)) == list(range(16))
+        vv = [j ^ sg for j in range(8)]            # column held after the skewed loads
+        for b in range(3 - kq):
+            if (sg >> b) & 1:
+                for j in range(8):
+                    if not j & (1 << b):
+                        vv[j], vv[j | (1 << b)] = vv[j | (1 << b)], vv[j]
+        assert vv == list(range(8))
+
+
 # ---------------------------------------------------------------- barriers
 
 class _Bar:
