@@ -917,14 +917,14 @@ def config_n32(Q, torch, np, st, args):
     ref = Q.qs_state_alloc(n, Q.QS_C128, st)
     c2 = {"workload": "random layered n=32 depth 40, CZ entanglers, complex64 (32 GiB)", "gates": len(g)}
     pr = Q.qs_plan_create(n, Q.QS_C128, g, Q.make_opts(mode=T))
-    t = device_reps(torch, lambda: Q.qs_plan_execute(pr, ref), 2, lambda: Q.qs_state_set_basis(ref, 0))
+    t = device_reps(torch, lambda: Q.qs_plan_execute(pr, ref), 5, lambda: Q.qs_state_set_basis(ref, 0))
     c2["c128_tensor"] = {"ms": spread(t), "passes": Q.qs_plan_info_get(pr)["passes"], "norm": Q.qs_norm(ref)}
     Q.qs_plan_free(pr)
     for name, opts, reps in (("tensor_fp16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=4), 5),
-                             ("tensor_fp16x3_k5", Q.make_opts(mode=T, fuse_k=5, tc_min_gates=2, tc_precision=4), 3),
-                             ("tensor_bf16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=3), 3),
-                             ("tensor_bf16", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=1), 3),
-                             ("fused_cuda_cores_k2", Q.make_opts(mode=F, fuse_k=2, tile_qubits=13, low_qubits=4), 2)):
+                             ("tensor_fp16x3_k5", Q.make_opts(mode=T, fuse_k=5, tc_min_gates=2, tc_precision=4), 5),
+                             ("tensor_bf16x3", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=3), 5),
+                             ("tensor_bf16", Q.make_opts(mode=T, tc_min_gates=2, tc_precision=1), 5),
+                             ("fused_cuda_cores_k2", Q.make_opts(mode=F, fuse_k=2, tile_qubits=13, low_qubits=4), 5)):
         plan = Q.qs_plan_create(n, Q.QS_C64, g, opts)
         t = device_reps(torch, lambda: Q.qs_plan_execute(plan, s), reps, lambda: Q.qs_state_set_basis(s, 0))
         m, l2 = Q.qs_state_diff(s, ref)
@@ -932,7 +932,7 @@ def config_n32(Q, torch, np, st, args):
                     "max_abs_err_vs_c128_gpu": m, "l2_err_vs_c128_gpu": l2}
         Q.qs_plan_free(plan)
     pplan = Q.qs_plan_create(n, Q.QS_C64, g[:per_layer], None)
-    t = device_reps(torch, lambda: Q.qs_plan_execute(pplan, s), 3, lambda: Q.qs_state_set_basis(s, 0))
+    t = device_reps(torch, lambda: Q.qs_plan_execute(pplan, s), 5, lambda: Q.qs_state_set_basis(s, 0))
     c2["per_gate_c64"] = {"ms_one_layer": spread(t), "ms_scaled_to_40_layers": 40 * statistics.median(t),
                           "gates_per_layer": per_layer}
     c2["speedup_tensor_vs_per_gate"] = c2["per_gate_c64"]["ms_scaled_to_40_layers"] / c2["tensor_fp16x3"]["ms"]["median"]
@@ -965,8 +965,8 @@ def config_ucc(Q, torch, np, st, args, hbm_peak=6800.0):
     states = [Q.qs_state_alloc(n, Q.QS_C64, st) for _ in range(B)]
     c3 = {"workload": "UCC-style n=20 complex64, 400 terms, B=64, 300-term <H>", "gates": len(g),
           "x_mask_groups": nx}
-    for name, opts, reps in (("fused_k1", Q.make_opts(mode=F, fuse_k=1), 3),
-                             ("fused_k4_device_blocks", Q.make_opts(mode=F, fuse_k=4, fuse_parametric=1), 3),
+    for name, opts, reps in (("fused_k1", Q.make_opts(mode=F, fuse_k=1), 5),
+                             ("fused_k4_device_blocks", Q.make_opts(mode=F, fuse_k=4, fuse_parametric=1), 5),
                              ("tensor", Q.make_opts(mode=T, tc_min_gates=2), 5),
                              ("tensor_device_blocks", Q.make_opts(mode=T, tc_min_gates=4, fuse_parametric=1), 5)):
         plan = Q.qs_plan_create(n, Q.QS_C64, g, opts)
@@ -1011,7 +1011,7 @@ def config_hea(Q, torch, np, st, args):
         for vname, o in variants:
             Q.qs_adjoint_grad(s, g, th, *H, opts=o)
             walls = []
-            for _ in range(3):
+            for _ in range(5):
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
                 e, gr = Q.qs_adjoint_grad(s, g, th, *H, opts=o)
