@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(kRedThreads) k_norm(const typename V2<R>::T* _
 #pragma unroll
           for (int k = 0; k < A; ++k) {
             const auto a = Vec16<R>::amp(v[u], k);
-            run += a.x * a.x + a.y * a.y;
+            run = fmac(a.y, a.y, fmac(a.x, a.x, run));   // two FMAs: the FP64 pipe bounds complex128
           }
       }
       tot += (double)run;
@@ -122,7 +122,7 @@ __global__ void __launch_bounds__(kRedThreads) k_norm(const typename V2<R>::T* _
 #pragma unroll 1
       for (int it = 0; it < kRun && i < dim; ++it, i += stride) {
         const auto v = psi[i];
-        run += v.x * v.x + v.y * v.y;
+        run = fmac(v.y, v.y, fmac(v.x, v.x, run));
       }
       tot += (double)run;
     }
